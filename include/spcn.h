@@ -1,0 +1,182 @@
+/*
+ * spcn.h -- C ABI of the B300 (sm_103a) implementation of the improved
+ * structure-preserving colour normalisation (SPCN) of Ramakrishnan, Anand &
+ * Sethi, "Fast GPU-Enabled Color Normalization for Digital Pathology"
+ * (arXiv 1901.03088).
+ *
+ * The per-pixel path, by the paper's steps:
+ *   Eq. 1      optical density  v = log(i0 / i), with the channel-wise,
+ *              image-wise i0 of §3.1 item 1;
+ *   Eq. 2      two-stain sparse NMF: the basis W from sampled non-white
+ *              pixels (§3.1 item 2, §3.2 item 2), and for every pixel the
+ *              stain densities h = argmin_{h>=0} 1/2||v - W h||^2 + lambda|h|_1;
+ *   Eq. 3      per-stain scaling by the ratio of 99th percentiles, taken over
+ *              non-white pixels (§3.1 item 2);
+ *   Eq. 4      inverse optical density i' = i0 exp(-v');
+ *   §3.1 item 3  hematoxylin is the column with the larger OD(red)-OD(blue).
+ *
+ * Conventions shared by every entry point
+ *   - Images are 8-bit RGB, interleaved (R,G,B per pixel), row-major, in
+ *     DEVICE memory unless the entry point says otherwise.  Row y starts at
+ *     data + y * pitch_bytes; pitch_bytes >= 3 * width.  Rows whose start
+ *     (and, for outputs, destination) is 16-byte aligned take the vector
+ *     path; any other layout is accepted and handled byte by byte.
+ *   - The caller owns every image, output and density buffer.  The library
+ *     never frees caller memory; it allocates only the scratch held by the
+ *     context (grown on demand, released by spcn_context_destroy).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is stream-ordered.  An entry point blocks the host
+ *     only when it returns results in host memory (documented per call).
+ *   - Return value: SPCN_OK (0) or a negative spcn_status.  On error the
+ *     output buffers hold unspecified contents.  Conditions found on the
+ *     device by an asynchronous call (no tissue, a wait that gave up) are
+ *     returned by the next call that synchronises: spcn_synchronize() or
+ *     any call returning host results.
+ *   - A context is bound to one device and is not thread-safe; use one
+ *     context per host thread.
+ */
+#ifndef SPCN_H
+#define SPCN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SPCN_OK = 0,
+  SPCN_ERR_INVALID_ARG = -1,      /* null/misaligned pointer, bad size or parameter */
+  SPCN_ERR_CUDA = -2,             /* a CUDA runtime call failed */
+  SPCN_ERR_OOM = -3,              /* device scratch allocation failed */
+  SPCN_ERR_NO_TISSUE = -4,        /* no non-white pixel where one is needed */
+  SPCN_ERR_DEGENERATE_BASIS = -5, /* stain vectors (nearly) parallel or vanished */
+  SPCN_ERR_TIMEOUT = -6           /* a grid-wide wait gave up (kernel returned) */
+} spcn_status;
+
+typedef enum {
+  SPCN_SAMPLE_ALL = 0,      /* every pixel, raster order */
+  SPCN_SAMPLE_HASH = 1,     /* round(rate*N) SplitMix64 draws with replacement */
+  SPCN_SAMPLE_PATCHES = 2   /* patches at least half non-white (§3.2 item 2) */
+} spcn_sample_mode;
+
+/* An 8-bit interleaved RGB image. */
+typedef struct {
+  const uint8_t* data;      /* device pointer to pixel (0,0) */
+  int32_t width;            /* pixels per row, >= 1 */
+  int32_t height;           /* rows, >= 1 */
+  int64_t pitch_bytes;      /* bytes between row starts, >= 3*width */
+} spcn_image;
+
+/* Method parameters; spcn_params_default() gives the paper's constants. */
+typedef struct {
+  float lambda;             /* Eq. 2 sparsity weight (0.1, §2.1), >= 0 */
+  int32_t white_thresh;     /* bright: all channels > t; non-white otherwise (220, §3.1) */
+  float i0_pct;             /* percentile of bright pixels taken as i0 (80, §3.1 item 1) */
+  float stain_pct;          /* stain-density percentile of Eq. 3 (99) */
+  int32_t i0_max_samples;   /* cap on bright pixels used for i0 (100000, §3.1 item 1) */
+  int32_t sample_mode;      /* spcn_sample_mode used by spcn_estimate_basis */
+  float sample_rate;        /* SPCN_SAMPLE_HASH: fraction of pixels drawn (0.01) */
+  int32_t n_patches;        /* SPCN_SAMPLE_PATCHES: patches kept (<= 4*n_patches tried) */
+  int32_t patch_size;       /* SPCN_SAMPLE_PATCHES: patch side in pixels */
+  int32_t max_iter;         /* dictionary-learning iteration cap (200) */
+  float tol;                /* stop when max|dW| < tol (1e-6) */
+  uint32_t flags;           /* reserved, must be 0 */
+  uint64_t seed;            /* SplitMix64 seed of the sampling */
+} spcn_params;
+
+/* Per-image statistics: everything the per-pixel passes need.  A plain host
+ * record; it can be stored and reused (e.g. one target for many sources). */
+typedef struct {
+  float W[6];               /* basis, column-major 3x2: W[0..2] = hematoxylin OD
+                               (R,G,B), W[3..5] = eosin OD; entries >= 0 */
+  float i0[3];              /* background intensity per channel, in [1, 255] */
+  double p99[2];            /* Eq. 3 percentile of each stain's density.  From
+                               spcn_estimate_basis: over the sampled non-white
+                               pixels (§3.1 item 2); from spcn_stain_percentile:
+                               exact over all non-white pixels of the image */
+  int32_t iters;            /* dictionary-learning iterations run */
+  int32_t status;           /* spcn_status of the call that produced the record */
+  int64_t n_sample;         /* pixels in the basis sample */
+  int64_t n_nonwhite;       /* non-white pixels in the sample */
+  int64_t n_bright;         /* bright pixels in the sample */
+  double objective;         /* Eq. 2 objective (1/2-scaled) at the last H-step */
+} spcn_stats;
+
+/* Fill *p with the paper's constants: lambda 0.1, threshold 220, i0 from the
+ * 80th percentile of <= 100000 bright pixels, 99th-percentile scaling, hash
+ * sampling at 1%, 200 patches of 256 px, 200 iterations, tol 1e-6, seed 0. */
+void spcn_params_default(spcn_params* p);
+
+/* Create a context on CUDA device `device`.  Allocates the fixed scratch
+ * (a few tens of MB) on that device.  *ctx is set on success. */
+int spcn_context_create(void** ctx, int device);
+
+/* Release the context and all its device scratch.  NULL is accepted. */
+int spcn_context_destroy(void* ctx);
+
+/* Basis estimation (§3.1 items 1-3, §3.2 item 2, Eq. 2): sample pixels by
+ * params->sample_mode, estimate i0 (P80 of <= i0_max_samples bright sample
+ * pixels), run the sparse NMF on the sample's non-white pixels, order the
+ * stains by OD(red)-OD(blue), and set p99 to the percentile of the sampled
+ * non-white pixels' densities.  Writes the host record *out.  Blocks the
+ * host until the stream has finished this call's work.
+ * Errors: INVALID_ARG, NO_TISSUE (no non-white sample pixel or patch),
+ * DEGENERATE_BASIS, TIMEOUT, CUDA, OOM. */
+int spcn_estimate_basis(void* ctx, const spcn_image* img, const spcn_params* params,
+                        spcn_stats* out, void* stream);
+
+/* Exact Eq. 3 percentile (params->stain_pct) of each stain's density over
+ * all non-white pixels of `img`, for the basis and i0 in *st (st->p99, if
+ * positive, only guides the search window).  Writes p99_out[2] (host).
+ * Blocks the host.  Errors: INVALID_ARG, NO_TISSUE, DEGENERATE_BASIS,
+ * TIMEOUT, CUDA. */
+int spcn_stain_percentile(void* ctx, const spcn_image* img, const spcn_stats* st,
+                          const spcn_params* params, double* p99_out, void* stream);
+
+/* Stain densities (Eq. 2 H-step for the basis and i0 in *st) of every pixel,
+ * written planar to device memory: H[j * h_stride + y * width + x] for stain
+ * j = 0 (hematoxylin), 1 (eosin); h_stride >= width*height.  Asynchronous. */
+int spcn_stain_densities(void* ctx, const spcn_image* img, const spcn_stats* st,
+                         const spcn_params* params, float* H, int64_t h_stride,
+                         void* stream);
+
+/* Normalise `src` to the target statistics (Eq. 1-4): pass 1 computes the
+ * source's exact non-white P99 per stain on the device (src_st->p99 only
+ * guides the search window), pass 2 recomputes every pixel's densities,
+ * scales them by tgt_st->p99 / P99_src, mixes them with the target basis and
+ * writes i0_tgt * exp(-v') rounded half-to-even into `out` (device, same
+ * width/height as src, row pitch out_pitch >= 3*width; must not overlap
+ * src).  If src_p99_out (host, 2 doubles) is non-NULL the call blocks and
+ * returns the source percentiles there; otherwise it is asynchronous.
+ * Errors: INVALID_ARG, DEGENERATE_BASIS, CUDA (and, when blocking,
+ * NO_TISSUE/TIMEOUT). */
+int spcn_normalize(void* ctx, const spcn_image* src, const spcn_stats* src_st,
+                   const spcn_stats* tgt_st, const spcn_params* params,
+                   uint8_t* out, int64_t out_pitch, double* src_p99_out, void* stream);
+
+/* Wait for the context's work on `stream` and return the first error any
+ * asynchronous call recorded on the device since the last synchronising
+ * call (the record is then cleared). */
+int spcn_synchronize(void* ctx, void* stream);
+
+/* Number of kernels the context has launched since creation (for launch
+ * accounting in benchmarks). */
+int64_t spcn_launch_count(void* ctx);
+
+/* Static description of a status code. */
+const char* spcn_strerror(int status);
+
+/* Test hook for failure detection: launch a cooperative kernel whose grid
+ * barrier waits for `extra_arrivals` more blocks than exist; the wait gives
+ * up after timeout_ns, the kernel records SPCN_ERR_TIMEOUT and returns, and
+ * the call (which blocks) returns that status.  extra_arrivals = 0 must
+ * return SPCN_OK.  No fault or hang is ever raised. */
+int spcn_debug_barrier_timeout(void* ctx, int32_t extra_arrivals, int64_t timeout_ns,
+                               void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPCN_H */
