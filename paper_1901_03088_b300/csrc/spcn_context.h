@@ -1,0 +1,81 @@
+// Host-side context of the SPCN library: the device scratch it owns and the
+// launch configuration measured once per device.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "spcn_internal.cuh"
+
+namespace spcn {
+
+// Device-side state of one basis estimation.
+struct BasisState {
+  u64 m;              // sample size
+  u64 n_nw, n_br;     // non-white / bright sample pixels
+  int n_acc;          // accepted patches
+  int iters;
+  int status;
+  int pad;
+  double objective;
+  double W[6];        // final basis in FP64 (ordered)
+  SelectState sel;    // percentile of the sampled non-white densities
+};
+
+struct Context {
+  int device = 0;
+  int num_sms = 0;
+  int* err = nullptr;              // first error recorded on the device
+  Model* model = nullptr;          // image / source model
+  Model* model_b = nullptr;        // basis-estimation model
+  SelectState* sel = nullptr;      // full-image percentile record
+  u64* coarse = nullptr;           // [2][kWinGroups]
+  u64* fine = nullptr;             // [2][kWinBins]
+  u64* rhist = nullptr;            // [3][kTracks][kRadixBins]
+  u64* rhist_b = nullptr;          // same, for the sample percentile
+  double* partials = nullptr;      // [2][max grid][kAcc]
+  BasisState* bs = nullptr;
+  // grown on demand
+  uint32_t* sample = nullptr;      // packed RGB of the sample
+  uint32_t* nw = nullptr;          // non-white sample pixels (stable order)
+  uint32_t* br = nullptr;          // bright sample pixels (stable order)
+  size_t sample_cap = 0;
+  unsigned* blk = nullptr;         // per-block counts for the compaction [2][nblk]
+  u64* blk_off = nullptr;          // exclusive offsets [2][nblk]
+  size_t blk_cap = 0;
+  int* cand = nullptr;             // patch candidates: counts, then accepted origins
+  int cand_cap = 0;
+  int64_t launches = 0;
+  // blocks per SM at the launch configuration of each kernel
+  int occ_window = 0, occ_recon = 0, occ_density = 0, occ_select = 0;
+  int occ_snmf = 0, occ_radix_list = 0, occ_debug = 0;
+  long long timeout_ns = 2000000000LL;   // grid-barrier give-up time
+};
+
+int ensure_sample_capacity(Context* c, size_t n);
+int ensure_candidate_capacity(Context* c, int n);
+
+#define SPCN_CUDA_TRY(expr)                         \
+  do {                                              \
+    cudaError_t e_ = (expr);                        \
+    if (e_ != cudaSuccess) {                        \
+      return e_ == cudaErrorMemoryAllocation ? SPCN_ERR_OOM : SPCN_ERR_CUDA; \
+    }                                               \
+  } while (0)
+
+#define SPCN_LAUNCH_CHECK(ctx)                      \
+  do {                                              \
+    (ctx)->launches++;                              \
+    cudaError_t e_ = cudaGetLastError();            \
+    if (e_ != cudaSuccess) return SPCN_ERR_CUDA;    \
+  } while (0)
+
+// Shared-memory sizes of the pixel kernels.
+constexpr size_t kLutSmem = sizeof(float2) * kLutEntries * kLutRep;
+constexpr size_t kWindowSmem = kLutSmem + sizeof(unsigned) * 2 * kWinGroups;
+constexpr size_t kRadixSmem = kLutSmem + sizeof(unsigned) * kTracks * kRadixBins;
+
+int configure_pixel_kernels(Context* c);
+int configure_basis_kernels(Context* c);
+
+}  // namespace spcn

@@ -1,0 +1,748 @@
+// Per-pixel passes of the improved SPCN (Eq. 1-4) on sm_103a.
+//
+// All passes stream the 8-bit RGB image in 16-pixel chunks (48 bytes = three
+// 16-byte loads per thread) from a persistent grid sized to the SM count, look
+// the optical densities up in a replicated shared-memory table (Eq. 1, already
+// projected on the basis and shifted by lambda), and solve the Eq. 2 H-step in
+// closed form (solve_pixel).  Nothing here is a dense contraction, so no
+// tensor-core path is used: the passes are bound by HBM bandwidth and
+// instruction issue.
+#include <math.h>
+#include <string.h>
+
+#include <cmath>
+
+#include "spcn_context.h"
+#include "spcn_internal.cuh"
+
+namespace spcn {
+
+// ------------------------------------------------------------ Eq. 1 table
+struct ModelIn {
+  float W[6];
+  float i0[3];
+  float lambda;
+};
+
+// One thread per (channel, intensity): v = log(i0_c / max(i,1)) in FP64, the
+// plain table and the basis-projected, lambda-shifted table (rounded once to
+// FP32).  Thread 0 also derives the closed-form H-step coefficients.
+__global__ void k_build_model(Model* m, ModelIn in, const Model* from) {
+  float W[6], i0[3];
+  const Model* src = from;
+  for (int i = 0; i < 6; ++i) W[i] = src ? src->W[i] : in.W[i];
+  for (int i = 0; i < 3; ++i) i0[i] = src ? src->i0[i] : in.i0[i];
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < kLutEntries) {
+    const int c = e >> 8, i = e & 255;
+    const double v = log((double)i0[c] / (double)(i > 0 ? i : 1));
+    double f0 = (double)W[c] * v, f1 = (double)W[3 + c] * v;
+    if (c == 0) { f0 -= (double)in.lambda; f1 -= (double)in.lambda; }
+    m->od[e] = (float)v;
+    m->proj[e] = make_float2((float)f0, (float)f1);
+  }
+  if (e == 0) {
+    double g11 = 0, g22 = 0, g12 = 0;
+    for (int c = 0; c < 3; ++c) {
+      g11 += (double)W[c] * W[c];
+      g22 += (double)W[3 + c] * W[3 + c];
+      g12 += (double)W[c] * W[3 + c];
+    }
+    const double det = g11 * g22 - g12 * g12;
+    Lasso L;
+    if (det > 1e-12) {
+      L.a11 = (float)(g22 / det);
+      L.a22 = (float)(g11 / det);
+      L.a12 = L.a21 = (float)(-g12 / det);
+      L.u1 = (float)(1.0 / g11);
+      L.u2 = (float)(1.0 / g22);
+      m->status = SPCN_OK;
+    } else {
+      L.a11 = L.a22 = L.a12 = L.a21 = L.u1 = L.u2 = 0.f;
+      m->status = SPCN_ERR_DEGENERATE_BASIS;
+    }
+    m->lasso = L;
+    if (from != m) {
+      for (int i = 0; i < 6; ++i) m->W[i] = W[i];
+      for (int i = 0; i < 3; ++i) m->i0[i] = i0[i];
+    }
+  }
+}
+
+int launch_build_model(Context* c, Model* m, const float* W, const float* i0, float lambda,
+                       const Model* from_device, cudaStream_t st) {
+  ModelIn in;
+  for (int i = 0; i < 6; ++i) in.W[i] = W ? W[i] : 0.f;
+  for (int i = 0; i < 3; ++i) in.i0[i] = i0 ? i0[i] : 0.f;
+  in.lambda = lambda;
+  k_build_model<<<3, 256, 0, st>>>(m, in, from_device);
+  SPCN_LAUNCH_CHECK(c);
+  return SPCN_OK;
+}
+
+// ------------------------------------------------------------ traversal
+struct ChunkPos {
+  u64 px;           // raster index of the chunk's first pixel
+  int64_t src_off;  // byte offset in the source
+  int64_t dst_off;  // byte offset in the destination
+  int n;            // valid pixels (16 except at row ends)
+};
+
+__device__ __forceinline__ ChunkPos chunk_pos(const Geometry& g, u64 q) {
+  ChunkPos p;
+  if (g.flat) {
+    p.px = q * kChunk;
+    const u64 left = (u64)g.npx - p.px;
+    p.n = left < (u64)kChunk ? (int)left : kChunk;
+    p.src_off = (int64_t)(p.px * 3);
+    p.dst_off = p.src_off;
+  } else {
+    const u64 y = div_chunks(q, g.cpr, g.magic);
+    const u64 x0 = (q - y * g.cpr) * kChunk;
+    const u64 left = (u64)g.width - x0;
+    p.n = left < (u64)kChunk ? (int)left : kChunk;
+    p.px = y * (u64)g.width + x0;
+    p.src_off = (int64_t)y * g.src_pitch + (int64_t)(x0 * 3);
+    p.dst_off = (int64_t)y * g.dst_pitch + (int64_t)(x0 * 3);
+  }
+  return p;
+}
+
+__device__ __forceinline__ unsigned byte_at(const unsigned (&w)[12], int i) {
+  return (w[i >> 2] >> ((i & 3) * 8)) & 0xFFu;
+}
+
+// Load a chunk into 12 little-endian words; STREAM selects the evict-first
+// policy for data read for the last time.
+template <bool STREAM>
+__device__ __forceinline__ void load_chunk(const Geometry& g, const ChunkPos& p,
+                                           unsigned (&w)[12]) {
+  const uint8_t* s = g.src + p.src_off;
+  if (p.n == kChunk && g.vec_src) {
+    const uint4* v = reinterpret_cast<const uint4*>(s);
+    uint4 a, b, c;
+    if (STREAM) {
+      a = __ldcs(v); b = __ldcs(v + 1); c = __ldcs(v + 2);
+    } else {
+      a = __ldg(v); b = __ldg(v + 1); c = __ldg(v + 2);
+    }
+    w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+    w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
+    w[8] = c.x; w[9] = c.y; w[10] = c.z; w[11] = c.w;
+  } else {
+#pragma unroll
+    for (int i = 0; i < 12; ++i) w[i] = 0u;
+    const int nb = 3 * p.n;
+#pragma unroll
+    for (int i = 0; i < 48; ++i)
+      if (i < nb) w[i >> 2] |= (unsigned)__ldg(s + i) << ((i & 3) * 8);
+  }
+}
+
+__device__ __forceinline__ void store_chunk(const Geometry& g, const ChunkPos& p,
+                                            const unsigned (&o)[12]) {
+  uint8_t* d = g.dst + p.dst_off;
+  if (p.n == kChunk && g.vec_dst) {
+    uint4* v = reinterpret_cast<uint4*>(d);
+    __stcs(v, make_uint4(o[0], o[1], o[2], o[3]));
+    __stcs(v + 1, make_uint4(o[4], o[5], o[6], o[7]));
+    __stcs(v + 2, make_uint4(o[8], o[9], o[10], o[11]));
+  } else {
+    const int nb = 3 * p.n;
+#pragma unroll
+    for (int i = 0; i < 48; ++i)
+      if (i < nb) d[i] = (uint8_t)byte_at(o, i);
+  }
+}
+
+// ------------------------------------------------------------ pass 1
+struct WindowArgs {
+  Geometry g;
+  const Model* m;
+  SelectState* sel;
+  u64* fine;
+  u64* coarse;
+  int* err;
+  unsigned thr;        // white threshold
+  unsigned lo0, lo1;   // window start keys
+  unsigned nb0, nb1;   // window widths (0 = no window)
+  double pct;
+  double tgt0, tgt1;   // target percentiles (for the scale factors)
+};
+
+template <bool FULL>
+__device__ __forceinline__ void window_chunk(const unsigned (&w)[12], int n, const float2* lut,
+                                             const Lasso& L, const WindowArgs& a,
+                                             unsigned* s_coarse, unsigned& c_nw,
+                                             unsigned& c_b0, unsigned& c_b1) {
+#pragma unroll
+  for (int k = 0; k < kChunk; ++k) {
+    if (FULL || k < n) {
+      const unsigned r = byte_at(w, 3 * k), g = byte_at(w, 3 * k + 1), b = byte_at(w, 3 * k + 2);
+      float h1, h2;
+      solve_pixel(lut, r, g, b, L, h1, h2);
+      const bool nw = min(r, min(g, b)) <= a.thr;
+      const unsigned k1 = nw ? __float_as_uint(h1) : 0xFFFFFFFFu;
+      const unsigned k2 = nw ? __float_as_uint(h2) : 0xFFFFFFFFu;
+      c_nw += nw ? 1u : 0u;
+      c_b0 += (k1 < a.lo0) ? 1u : 0u;
+      c_b1 += (k2 < a.lo1) ? 1u : 0u;
+      const unsigned rel1 = k1 - a.lo0, rel2 = k2 - a.lo1;
+      if (rel1 < a.nb0 || rel2 < a.nb1) {
+        if (rel1 < a.nb0) {
+          atomicAdd(a.fine + rel1, 1ull);
+          atomicAdd(s_coarse + (rel1 >> kWinGroupBits), 1u);
+        }
+        if (rel2 < a.nb1) {
+          atomicAdd(a.fine + kWinBins + rel2, 1ull);
+          atomicAdd(s_coarse + kWinGroups + (rel2 >> kWinGroupBits), 1u);
+        }
+      }
+    }
+  }
+}
+
+// Rank selection inside the window, run by the last block of pass 1.
+__device__ void window_select(const WindowArgs& a) {
+  SelectState* s = a.sel;
+  __shared__ u64 s_tmp[33];
+  __shared__ int s_idx, s_idx2;
+  __shared__ u64 s_before, s_before2;
+  __shared__ int s_res[kTracks];
+  const u64 n = __ldcg(&s->n_nw);
+  if (n == 0) {
+    if (threadIdx.x == 0) {
+      record_error(a.err, SPCN_ERR_NO_TISSUE);
+      for (int t = 0; t < kTracks; ++t) { s->key[t] = 0; s->resolved[t] = 1; }
+      s->p99[0] = s->p99[1] = 0.0;
+      s->scale[0] = s->scale[1] = 1.0;
+      s->t = 0.0;
+      s->all_resolved = 1;
+    }
+    return;
+  }
+  if (threadIdx.x == 0) {
+    set_ranks(s, n, a.pct);
+    s->lo[0] = a.lo0; s->lo[1] = a.lo1; s->nb[0] = a.nb0; s->nb[1] = a.nb1;
+  }
+  __syncthreads();
+  for (int t = 0; t < kTracks; ++t) {
+    const int j = t >> 1;
+    const unsigned nb = j ? a.nb1 : a.nb0;
+    const unsigned lo = j ? a.lo1 : a.lo0;
+    const u64 r = s->rank[t];
+    const u64 below = __ldcg(&s->below[j]);
+    if (threadIdx.x == 0) s_res[t] = 0;
+    __syncthreads();
+    if (nb == 0 || r < below) continue;
+    const int ngroups = (int)((nb + kWinGroup - 1) >> kWinGroupBits);
+    block_find_rank(a.coarse + j * kWinGroups, ngroups, r - below, &s_idx, &s_before, s_tmp);
+    if (s_idx < 0) continue;
+    const int gidx = s_idx;
+    const u64 r2 = r - below - s_before;
+    const unsigned gbeg = (unsigned)gidx << kWinGroupBits;
+    const int nbins = (int)min((unsigned)kWinGroup, nb - gbeg);
+    block_find_rank(a.fine + (size_t)j * kWinBins + gbeg, nbins, r2, &s_idx2, &s_before2, s_tmp);
+    if (s_idx2 < 0) continue;   // cannot happen: the group count covers r2
+    if (threadIdx.x == 0) {
+      s->key[t] = lo + gbeg + (unsigned)s_idx2;
+      s_res[t] = 1;
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int all = 1;
+    for (int t = 0; t < kTracks; ++t) { s->resolved[t] = s_res[t]; all &= s_res[t]; }
+    if (all) finish_percentiles(s, a.tgt0, a.tgt1);
+    __threadfence();
+    s->all_resolved = all;
+  }
+}
+
+__global__ void __launch_bounds__(kPassThreads) k_pass_window(WindowArgs a) {
+  extern __shared__ float2 s_dyn[];
+  unsigned* s_coarse = reinterpret_cast<unsigned*>(s_dyn + kLutEntries * kLutRep);
+  __shared__ u64 s_tmp[33];
+  __shared__ unsigned s_ticket;
+  for (int i = threadIdx.x; i < 2 * kWinGroups; i += blockDim.x) s_coarse[i] = 0u;
+  const float2* lut = load_lut(a.m, s_dyn);
+  const Lasso L = a.m->lasso;
+  unsigned c_nw = 0, c_b0 = 0, c_b1 = 0;
+  const u64 stride = (u64)gridDim.x * blockDim.x;
+  for (u64 q = (u64)blockIdx.x * blockDim.x + threadIdx.x; q < a.g.nchunks; q += stride) {
+    const ChunkPos p = chunk_pos(a.g, q);
+    unsigned w[12];
+    load_chunk<false>(a.g, p, w);
+    if (p.n == kChunk) window_chunk<true>(w, kChunk, lut, L, a, s_coarse, c_nw, c_b0, c_b1);
+    else window_chunk<false>(w, p.n, lut, L, a, s_coarse, c_nw, c_b0, c_b1);
+  }
+  const u64 t_nw = block_sum(c_nw, s_tmp);
+  const u64 t_b0 = block_sum(c_b0, s_tmp);
+  const u64 t_b1 = block_sum(c_b1, s_tmp);
+  if (threadIdx.x == 0) {
+    if (t_nw) atomicAdd(&a.sel->n_nw, t_nw);
+    if (t_b0) atomicAdd(&a.sel->below[0], t_b0);
+    if (t_b1) atomicAdd(&a.sel->below[1], t_b1);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 2 * kWinGroups; i += blockDim.x)
+    if (s_coarse[i]) atomicAdd(a.coarse + i, (u64)s_coarse[i]);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_ticket = atomicAdd(&a.sel->done_ctas, 1u);
+  __syncthreads();
+  if (s_ticket == gridDim.x - 1) {
+    __threadfence();
+    window_select(a);
+  }
+}
+
+// ------------------------------------------------------------ radix fallback
+struct ImageSource {
+  Geometry g;
+  unsigned thr;
+  template <class F>
+  __device__ __forceinline__ void for_each(F&& f) const {
+    const u64 stride = (u64)gridDim.x * blockDim.x;
+    for (u64 q = (u64)blockIdx.x * blockDim.x + threadIdx.x; q < g.nchunks; q += stride) {
+      const ChunkPos p = chunk_pos(g, q);
+      unsigned w[12];
+      load_chunk<false>(g, p, w);
+      for (int k = 0; k < p.n; ++k) {
+        const unsigned r = byte_at(w, 3 * k), gg = byte_at(w, 3 * k + 1), b = byte_at(w, 3 * k + 2);
+        f(r, gg, b, min(r, min(gg, b)) <= thr);
+      }
+    }
+  }
+};
+
+struct ListSource {
+  const uint32_t* items;   // packed R | G<<8 | B<<16, all non-white
+  u64 n;
+  template <class F>
+  __device__ __forceinline__ void for_each(F&& f) const {
+    const u64 stride = (u64)gridDim.x * blockDim.x;
+    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+      const uint32_t v = __ldg(items + i);
+      f(v & 0xFFu, (v >> 8) & 0xFFu, (v >> 16) & 0xFFu, true);
+    }
+  }
+};
+
+// Exact radix select (11/11/10-bit digits of the FP32 key) of the ranks in
+// s->rank[] whose track is not yet resolved, over every non-white pixel of
+// `src`.  All blocks of a cooperative grid call it; it uses four grid
+// barriers (counter `bar`, zeroed before the launch).  Block 0 writes the
+// keys, the percentiles and the scale factors.  Returns false if a wait gave
+// up (the error is recorded).
+template <class Src>
+__device__ bool radix_select(const Src& src, const float2* lut, const Lasso& L, SelectState* s,
+                             const u64 (&rank)[kTracks], const int (&active)[kTracks],
+                             u64* ghist, unsigned* s_hist, unsigned* bar, int* err,
+                             long long timeout_ns, double tgt0, double tgt1) {
+  __shared__ unsigned s_prefix[kTracks];
+  __shared__ u64 s_r[kTracks];
+  __shared__ int s_act[kTracks];
+  __shared__ int s_idx;
+  __shared__ u64 s_before;
+  __shared__ u64 s_tmp[33];
+  if (threadIdx.x == 0) {
+    for (int t = 0; t < kTracks; ++t) {
+      s_act[t] = active[t];
+      s_prefix[t] = 0u;
+      s_r[t] = rank[t];
+    }
+  }
+  const u64 gstride = (u64)gridDim.x * blockDim.x;
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < 3ull * kTracks * kRadixBins; i += gstride)
+    ghist[i] = 0ull;
+  unsigned target = gridDim.x;
+  if (!grid_barrier(bar, target, err, timeout_ns)) return false;
+  for (int d = 0; d < 3; ++d) {
+    const int shift = d == 0 ? 21 : (d == 1 ? 10 : 0);
+    const int hi = d == 0 ? 32 : (d == 1 ? 21 : 10);
+    const unsigned mask = d == 2 ? 0x3FFu : 0x7FFu;
+    for (int i = threadIdx.x; i < kTracks * kRadixBins; i += blockDim.x) s_hist[i] = 0u;
+    __syncthreads();
+    unsigned pre[kTracks];
+    int act[kTracks];
+#pragma unroll
+    for (int t = 0; t < kTracks; ++t) { pre[t] = s_prefix[t]; act[t] = s_act[t]; }
+    src.for_each([&](unsigned r, unsigned g, unsigned b, bool nw) {
+      if (!nw) return;
+      float h1, h2;
+      solve_pixel(lut, r, g, b, L, h1, h2);
+      const unsigned key[2] = {__float_as_uint(h1), __float_as_uint(h2)};
+#pragma unroll
+      for (int t = 0; t < kTracks; ++t) {
+        const unsigned k = key[t >> 1];
+        if (act[t] && (((u64)k >> hi) == ((u64)pre[t] >> hi)))
+          atomicAdd(s_hist + t * kRadixBins + ((k >> shift) & mask), 1u);
+      }
+    });
+    __syncthreads();
+    u64* gh = ghist + (size_t)d * kTracks * kRadixBins;
+    for (int i = threadIdx.x; i < kTracks * kRadixBins; i += blockDim.x)
+      if (s_hist[i]) atomicAdd(gh + i, (u64)s_hist[i]);
+    target += gridDim.x;
+    if (!grid_barrier(bar, target, err, timeout_ns)) return false;
+    for (int t = 0; t < kTracks; ++t) {
+      if (!s_act[t]) continue;
+      block_find_rank(gh + (size_t)t * kRadixBins, kRadixBins, s_r[t], &s_idx, &s_before, s_tmp);
+      if (threadIdx.x == 0) {
+        if (s_idx < 0) {         // fewer pixels than the rank: cannot happen
+          record_error(err, SPCN_ERR_CUDA);
+          s_act[t] = 0;
+        } else {
+          s_prefix[t] |= (unsigned)s_idx << shift;
+          s_r[t] -= s_before;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    for (int t = 0; t < kTracks; ++t)
+      if (s_act[t]) { s->key[t] = s_prefix[t]; s->resolved[t] = 1; }
+    finish_percentiles(s, tgt0, tgt1);
+    __threadfence();
+    s->all_resolved = 1;
+  }
+  return true;
+}
+
+struct SelectImageArgs {
+  ImageSource src;
+  const Model* m;
+  SelectState* sel;
+  u64* ghist;
+  int* err;
+  long long timeout_ns;
+  double tgt0, tgt1;
+};
+
+__global__ void __launch_bounds__(kPassThreads) k_select_image(SelectImageArgs a) {
+  if (*(volatile int*)&a.sel->all_resolved) return;   // uniform: every block returns
+  extern __shared__ float2 s_dyn[];
+  unsigned* s_hist = reinterpret_cast<unsigned*>(s_dyn + kLutEntries * kLutRep);
+  const float2* lut = load_lut(a.m, s_dyn);
+  const Lasso L = a.m->lasso;
+  u64 rank[kTracks];
+  int active[kTracks];
+  for (int t = 0; t < kTracks; ++t) {
+    rank[t] = __ldcg(&a.sel->rank[t]);
+    active[t] = !__ldcg(&a.sel->resolved[t]);
+  }
+  radix_select(a.src, lut, L, a.sel, rank, active, a.ghist, s_hist, &a.sel->barrier, a.err,
+               a.timeout_ns, a.tgt0, a.tgt1);
+}
+
+struct SelectListArgs {
+  const uint32_t* items;
+  const u64* n_dev;
+  const Model* m;
+  SelectState* sel;
+  u64* ghist;
+  int* err;
+  long long timeout_ns;
+  double pct;
+};
+
+// Percentile of the densities of a packed list of non-white pixels (the basis
+// sample, §3.1 item 2), radix select from scratch.
+__global__ void __launch_bounds__(kPassThreads) k_select_list(SelectListArgs a) {
+  extern __shared__ float2 s_dyn[];
+  unsigned* s_hist = reinterpret_cast<unsigned*>(s_dyn + kLutEntries * kLutRep);
+  const u64 n = __ldcg(a.n_dev);
+  if (n == 0 || a.m->status != SPCN_OK) return;   // uniform: every block returns
+  u64 rank[kTracks];
+  int active[kTracks];
+  double t;
+  type7_ranks(n, a.pct, &rank[0], &rank[1], &t);
+  rank[2] = rank[0];
+  rank[3] = rank[1];
+  for (int i = 0; i < kTracks; ++i) active[i] = 1;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.sel->n_nw = n;
+    a.sel->t = t;
+    for (int i = 0; i < kTracks; ++i) a.sel->rank[i] = rank[i];
+  }
+  const float2* lut = load_lut(a.m, s_dyn);
+  const Lasso L = a.m->lasso;
+  ListSource src{a.items, n};
+  radix_select(src, lut, L, a.sel, rank, active, a.ghist, s_hist, &a.sel->barrier, a.err,
+               a.timeout_ns, 1.0, 1.0);
+}
+
+// ------------------------------------------------------------ pass 2
+struct ReconArgs {
+  Geometry g;
+  const Model* m;
+  const SelectState* sel;
+  float Wt[6];       // target basis
+  float l2i0[3];     // log2 of the target i0
+};
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Insert byte 0 of v at byte position p (0..3) of word w.
+__device__ __forceinline__ unsigned put_byte(unsigned w, unsigned v, int p) {
+  const unsigned sel = p == 0 ? 0x3214u : (p == 1 ? 0x3240u : (p == 2 ? 0x3410u : 0x4210u));
+  return __byte_perm(w, v, sel);
+}
+
+template <bool FULL>
+__device__ __forceinline__ void recon_chunk(const unsigned (&w)[12], int n, const float2* lut,
+                                            const Lasso& L, const float (&M)[6],
+                                            const float (&l2)[3], unsigned (&o)[12]) {
+#pragma unroll
+  for (int k = 0; k < kChunk; ++k) {
+    if (FULL || k < n) {
+      const unsigned r = byte_at(w, 3 * k), g = byte_at(w, 3 * k + 1), b = byte_at(w, 3 * k + 2);
+      float h1, h2;
+      solve_pixel(lut, r, g, b, L, h1, h2);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        // Eq. 3-4: i' = i0_t 2^(-log2e * sum_j W_t[c,j] s_j h_j); M holds -log2e W_t s
+        const float e = fmaf(M[c], h1, fmaf(M[3 + c], h2, l2[c]));
+        const float x = ex2_approx(e);
+        // round half to even: adding 1.5*2^23 leaves round(x) in the low bits
+        const unsigned v = __float_as_uint(__fadd_rn(x, 12582912.0f));
+        const int i = 3 * k + c;
+        o[i >> 2] = put_byte(o[i >> 2], v, i & 3);
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kPassThreads) k_pass_recon(ReconArgs a) {
+  extern __shared__ float2 s_dyn[];
+  __shared__ float s_M[6];
+  if (threadIdx.x < 6) {
+    const int c = threadIdx.x % 3, j = threadIdx.x / 3;
+    const double sc = a.sel->scale[j];
+    s_M[threadIdx.x] = (float)(-(double)a.Wt[3 * j + c] * sc * 1.4426950408889634);
+  }
+  const float2* lut = load_lut(a.m, s_dyn);
+  const Lasso L = a.m->lasso;
+  float M[6], l2[3];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) M[i] = s_M[i];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) l2[i] = a.l2i0[i];
+  const u64 stride = (u64)gridDim.x * blockDim.x;
+  for (u64 q = (u64)blockIdx.x * blockDim.x + threadIdx.x; q < a.g.nchunks; q += stride) {
+    const ChunkPos p = chunk_pos(a.g, q);
+    unsigned w[12], o[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) o[i] = 0u;
+    load_chunk<true>(a.g, p, w);
+    if (p.n == kChunk) recon_chunk<true>(w, kChunk, lut, L, M, l2, o);
+    else recon_chunk<false>(w, p.n, lut, L, M, l2, o);
+    store_chunk(a.g, p, o);
+  }
+}
+
+// ------------------------------------------------------------ densities
+struct DensityArgs {
+  Geometry g;
+  const Model* m;
+  float* H;
+  int64_t stride;   // elements between the two planes
+};
+
+__global__ void __launch_bounds__(kPassThreads) k_pass_density(DensityArgs a) {
+  extern __shared__ float2 s_dyn[];
+  const float2* lut = load_lut(a.m, s_dyn);
+  const Lasso L = a.m->lasso;
+  const u64 stride = (u64)gridDim.x * blockDim.x;
+  const bool vec_h = ((reinterpret_cast<uintptr_t>(a.H) & 15u) == 0) && ((a.stride & 3) == 0);
+  for (u64 q = (u64)blockIdx.x * blockDim.x + threadIdx.x; q < a.g.nchunks; q += stride) {
+    const ChunkPos p = chunk_pos(a.g, q);
+    unsigned w[12];
+    load_chunk<true>(a.g, p, w);
+    float h[2][kChunk];
+#pragma unroll
+    for (int k = 0; k < kChunk; ++k) {
+      const unsigned r = byte_at(w, 3 * k), g = byte_at(w, 3 * k + 1), b = byte_at(w, 3 * k + 2);
+      solve_pixel(lut, r, g, b, L, h[0][k], h[1][k]);
+    }
+    float* d0 = a.H + p.px;
+    float* d1 = a.H + a.stride + p.px;
+    if (p.n == kChunk && vec_h && (p.px & 3) == 0) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        __stcs(reinterpret_cast<float4*>(d0) + v,
+               make_float4(h[0][4 * v], h[0][4 * v + 1], h[0][4 * v + 2], h[0][4 * v + 3]));
+        __stcs(reinterpret_cast<float4*>(d1) + v,
+               make_float4(h[1][4 * v], h[1][4 * v + 1], h[1][4 * v + 2], h[1][4 * v + 3]));
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < kChunk; ++k)
+        if (k < p.n) { d0[k] = h[0][k]; d1[k] = h[1][k]; }
+    }
+  }
+}
+
+// ------------------------------------------------------------ failure-detection hook
+__global__ void k_debug_barrier(unsigned* counter, int* err, int extra, long long timeout_ns) {
+  grid_barrier(counter, gridDim.x + (unsigned)extra, err, timeout_ns);
+}
+
+// ------------------------------------------------------------ host launchers
+static int grid_of(const Context* c, int occ) {
+  return c->num_sms * (occ > 0 ? occ : 1);
+}
+
+int configure_pixel_kernels(Context* c) {
+  SPCN_CUDA_TRY(cudaFuncSetAttribute(k_pass_window, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kWindowSmem));
+  SPCN_CUDA_TRY(cudaFuncSetAttribute(k_pass_recon, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kLutSmem));
+  SPCN_CUDA_TRY(cudaFuncSetAttribute(k_pass_density, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kLutSmem));
+  SPCN_CUDA_TRY(cudaFuncSetAttribute(k_select_image, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kRadixSmem));
+  SPCN_CUDA_TRY(cudaFuncSetAttribute(k_select_list, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kRadixSmem));
+  SPCN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->occ_window, k_pass_window,
+                                                              kPassThreads, kWindowSmem));
+  SPCN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->occ_recon, k_pass_recon,
+                                                              kPassThreads, kLutSmem));
+  SPCN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->occ_density, k_pass_density,
+                                                              kPassThreads, kLutSmem));
+  SPCN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->occ_select, k_select_image,
+                                                              kPassThreads, kRadixSmem));
+  SPCN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->occ_radix_list, k_select_list,
+                                                              kPassThreads, kRadixSmem));
+  SPCN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->occ_debug, k_debug_barrier,
+                                                              128, 0));
+  if (c->occ_window < 1 || c->occ_recon < 1 || c->occ_density < 1 || c->occ_select < 1 ||
+      c->occ_radix_list < 1 || c->occ_debug < 1)
+    return SPCN_ERR_CUDA;
+  return SPCN_OK;
+}
+
+// Window [lo, lo+nb) of FP32 keys around a percentile hint h > 0.
+static void window_of(double hint, unsigned* lo, unsigned* nb) {
+  if (!(hint > 0.0) || !std::isfinite(hint)) { *lo = 0u; *nb = 0u; return; }
+  float flo = (float)(hint * (1.0 - kWindowDelta));
+  float fhi = (float)(hint * (1.0 + kWindowDelta));
+  unsigned klo, khi, kmid;
+  float fmid = (float)hint;
+  memcpy(&klo, &flo, 4);
+  memcpy(&khi, &fhi, 4);
+  memcpy(&kmid, &fmid, 4);
+  if (klo == 0u) klo = 1u;   // key 0 (h = 0) is counted below the window
+  if (khi < klo) khi = klo;
+  u64 width = (u64)khi - klo + 1;
+  if (width > (u64)kWinBins) {
+    klo = kmid > (unsigned)(kWinBins / 2) ? kmid - (unsigned)(kWinBins / 2) : 1u;
+    width = kWinBins;
+  }
+  *lo = klo;
+  *nb = (unsigned)width;
+}
+
+// Pass 1 + select (+ radix fallback when a rank fell outside the window).
+int launch_percentile_passes(Context* c, const Geometry& g, const Model* m, int white_thresh,
+                             double pct, const double* hint, const double* tgt_p99,
+                             cudaStream_t st) {
+  WindowArgs a;
+  a.g = g;
+  a.m = m;
+  a.sel = c->sel;
+  a.fine = c->fine;
+  a.coarse = c->coarse;
+  a.err = c->err;
+  a.thr = (unsigned)white_thresh;
+  window_of(hint ? hint[0] : 0.0, &a.lo0, &a.nb0);
+  window_of(hint ? hint[1] : 0.0, &a.lo1, &a.nb1);
+  a.pct = pct;
+  a.tgt0 = tgt_p99 ? tgt_p99[0] : 1.0;
+  a.tgt1 = tgt_p99 ? tgt_p99[1] : 1.0;
+  SPCN_CUDA_TRY(cudaMemsetAsync(c->sel, 0, sizeof(SelectState), st));
+  SPCN_CUDA_TRY(cudaMemsetAsync(c->coarse, 0, sizeof(u64) * 2 * kWinGroups, st));
+  if (a.nb0) SPCN_CUDA_TRY(cudaMemsetAsync(c->fine, 0, sizeof(u64) * a.nb0, st));
+  if (a.nb1) SPCN_CUDA_TRY(cudaMemsetAsync(c->fine + kWinBins, 0, sizeof(u64) * a.nb1, st));
+  k_pass_window<<<grid_of(c, c->occ_window), kPassThreads, kWindowSmem, st>>>(a);
+  SPCN_LAUNCH_CHECK(c);
+
+  SelectImageArgs s;
+  s.src.g = g;
+  s.src.thr = (unsigned)white_thresh;
+  s.m = m;
+  s.sel = c->sel;
+  s.ghist = c->rhist;
+  s.err = c->err;
+  s.timeout_ns = c->timeout_ns;
+  s.tgt0 = a.tgt0;
+  s.tgt1 = a.tgt1;
+  void* args[] = {&s};
+  SPCN_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_select_image, grid_of(c, c->occ_select),
+                                            kPassThreads, args, kRadixSmem, st));
+  c->launches++;
+  return SPCN_OK;
+}
+
+int launch_select_list(Context* c, const uint32_t* items, const u64* n_dev, const Model* m,
+                       SelectState* sel, u64* ghist, double pct, cudaStream_t st) {
+  SelectListArgs a;
+  a.items = items;
+  a.n_dev = n_dev;
+  a.m = m;
+  a.sel = sel;
+  a.ghist = ghist;
+  a.err = c->err;
+  a.timeout_ns = c->timeout_ns;
+  a.pct = pct;
+  SPCN_CUDA_TRY(cudaMemsetAsync(sel, 0, sizeof(SelectState), st));
+  void* args[] = {&a};
+  SPCN_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_select_list, grid_of(c, c->occ_radix_list),
+                                            kPassThreads, args, kRadixSmem, st));
+  c->launches++;
+  return SPCN_OK;
+}
+
+int launch_recon(Context* c, const Geometry& g, const Model* m, const float* Wt, const float* i0t,
+                 cudaStream_t st) {
+  ReconArgs a;
+  a.g = g;
+  a.m = m;
+  a.sel = c->sel;
+  for (int i = 0; i < 6; ++i) a.Wt[i] = Wt[i];
+  for (int i = 0; i < 3; ++i) a.l2i0[i] = (float)log2((double)i0t[i]);
+  k_pass_recon<<<grid_of(c, c->occ_recon), kPassThreads, kLutSmem, st>>>(a);
+  SPCN_LAUNCH_CHECK(c);
+  return SPCN_OK;
+}
+
+int launch_density(Context* c, const Geometry& g, const Model* m, float* H, int64_t stride,
+                   cudaStream_t st) {
+  DensityArgs a;
+  a.g = g;
+  a.m = m;
+  a.H = H;
+  a.stride = stride;
+  k_pass_density<<<grid_of(c, c->occ_density), kPassThreads, kLutSmem, st>>>(a);
+  SPCN_LAUNCH_CHECK(c);
+  return SPCN_OK;
+}
+
+int launch_debug_barrier(Context* c, int extra, long long timeout_ns, cudaStream_t st) {
+  unsigned* counter = &c->sel->barrier;
+  SPCN_CUDA_TRY(cudaMemsetAsync(c->sel, 0, sizeof(SelectState), st));
+  int* err = c->err;
+  void* args[] = {&counter, &err, &extra, &timeout_ns};
+  SPCN_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_debug_barrier, c->num_sms, 128, args, 0, st));
+  c->launches++;
+  return SPCN_OK;
+}
+
+}  // namespace spcn
