@@ -164,6 +164,24 @@ int spcn_synchronize(void* ctx, void* stream);
  * accounting in benchmarks). */
 int64_t spcn_launch_count(void* ctx);
 
+/* Kernels whose launches can be timed (spcn_kernel_timing). */
+typedef enum {
+  SPCN_KERNEL_PASS1 = 0,    /* pass 1: densities, non-white count, P99 window histogram */
+  SPCN_KERNEL_SELECT = 1,   /* exact radix select for ranks outside the window */
+  SPCN_KERNEL_PASS2 = 2,    /* pass 2: densities, Eq. 3 scaling, Eq. 4, store */
+  SPCN_KERNEL_DENSITY = 3,  /* density output pass */
+  SPCN_KERNEL_COUNT = 4
+} spcn_kernel;
+
+/* Enable (1) or disable (0) CUDA-event timing of the kernels above on the
+ * streams they are launched on, and clear the accumulated times.  Timing
+ * records two events per timed launch; it does not synchronise. */
+int spcn_kernel_timing(void* ctx, int enable);
+
+/* Total device time (ms) and number of timed launches of kernel `kernel`
+ * since timing was enabled.  Waits for the recorded events. */
+int spcn_kernel_times(void* ctx, int kernel, double* total_ms, int64_t* launches);
+
 /* Static description of a status code. */
 const char* spcn_strerror(int status);
 

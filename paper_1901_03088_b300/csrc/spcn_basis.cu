@@ -1,0 +1,573 @@
+// Basis estimation of the improved SPCN on sm_103a (§3.1 items 1-3, §3.2
+// item 2, Eq. 2):
+//   sampling       all pixels / SplitMix64 draws / non-background patches,
+//                  packed as R | G<<8 | B<<16 in sample order;
+//   compaction     stable split of the sample into non-white and bright lists;
+//   i0             80th percentile per channel of <= 100000 bright pixels;
+//   sparse NMF     one cooperative persistent kernel: per-pixel closed-form
+//                  H-step, block-reduced Gram sums, a grid barrier, and the
+//                  exact column update of W computed identically by every
+//                  block in FP64;
+//   ordering       hematoxylin = larger OD(red) - OD(blue);
+//   sample P99     exact radix select over the non-white sample.
+#include <math.h>
+
+#include "spcn_context.h"
+#include "spcn_internal.cuh"
+
+namespace spcn {
+
+int launch_select_list(Context* c, const uint32_t* items, const u64* n_dev, const Model* m,
+                       SelectState* sel, u64* ghist, double pct, cudaStream_t st);
+
+constexpr int kCompactBlock = 4096;
+constexpr int kCompactThreads = 512;
+constexpr int kCompactPer = kCompactBlock / kCompactThreads;
+constexpr int kSnmfThreads = 512;
+constexpr int kMaxSnmfGrid = 4096;
+
+// ------------------------------------------------------------ SplitMix64
+// Published definition (Steele, Lea & Flood 2014): state += gamma; output
+// mix(state).  Output n of a generator seeded with s is mix(s + (n+1) gamma).
+__device__ __forceinline__ u64 sm64_mix(u64 z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ u64 sm64_output(u64 seed, u64 n) {
+  return sm64_mix(seed + (n + 1ull) * 0x9E3779B97F4A7C15ull);
+}
+
+// Lemire's multiply-high range reduction of output n to [0, bound).
+__device__ __forceinline__ u64 sm64_below(u64 seed, u64 n, u64 bound) {
+  return __umul64hi(sm64_output(seed, n), bound);
+}
+
+__device__ __forceinline__ uint32_t load_pixel(const uint8_t* data, int64_t pitch, u64 x, u64 y) {
+  const uint8_t* p = data + (int64_t)y * pitch + (int64_t)(x * 3);
+  return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16);
+}
+
+__device__ __forceinline__ bool packed_nonwhite(uint32_t v, unsigned thr) {
+  const unsigned r = v & 0xFFu, g = (v >> 8) & 0xFFu, b = (v >> 16) & 0xFFu;
+  return min(r, min(g, b)) <= thr;
+}
+
+// ------------------------------------------------------------ sampling
+struct SampleArgs {
+  const uint8_t* data;
+  int64_t pitch;
+  int64_t width, height;
+  u64 seed;
+  uint32_t* out;
+  u64 m;   // draws (all / hash)
+};
+
+__global__ void k_sample_all(SampleArgs a) {
+  const u64 n = (u64)a.width * a.height;
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x)
+    a.out[i] = load_pixel(a.data, a.pitch, i % a.width, i / a.width);
+}
+
+__global__ void k_sample_hash(SampleArgs a) {
+  const u64 n = (u64)a.width * a.height;
+  for (u64 k = (u64)blockIdx.x * blockDim.x + threadIdx.x; k < a.m; k += (u64)gridDim.x * blockDim.x) {
+    const u64 idx = sm64_below(a.seed, k, n);
+    a.out[k] = load_pixel(a.data, a.pitch, idx % a.width, idx / a.width);
+  }
+}
+
+struct PatchArgs {
+  const uint8_t* data;
+  int64_t pitch;
+  int64_t width, height;
+  u64 seed;
+  int P;
+  int n_patches;
+  int n_cand;
+  unsigned thr;
+  int* cand;          // [n_cand] non-white counts, then [n_patches] accepted candidates
+  BasisState* bs;
+  uint32_t* out;
+};
+
+__device__ __forceinline__ void patch_origin(const PatchArgs& a, int k, u64* x0, u64* y0) {
+  *x0 = sm64_below(a.seed, 2ull * (u64)k, (u64)(a.width - a.P + 1));
+  *y0 = sm64_below(a.seed, 2ull * (u64)k + 1ull, (u64)(a.height - a.P + 1));
+}
+
+// One block per candidate patch: its non-white pixel count.
+__global__ void k_patch_count(PatchArgs a) {
+  __shared__ u64 s_tmp[33];
+  const int k = blockIdx.x;
+  u64 x0, y0;
+  patch_origin(a, k, &x0, &y0);
+  const int npx = a.P * a.P;
+  unsigned cnt = 0;
+  for (int i = threadIdx.x; i < npx; i += blockDim.x) {
+    const uint32_t v = load_pixel(a.data, a.pitch, x0 + (u64)(i % a.P), y0 + (u64)(i / a.P));
+    cnt += packed_nonwhite(v, a.thr) ? 1u : 0u;
+  }
+  const u64 tot = block_sum(cnt, s_tmp);
+  if (threadIdx.x == 0) a.cand[k] = (int)tot;
+}
+
+// Keep candidates, in order, while at least half their pixels are non-white.
+__global__ void k_patch_accept(PatchArgs a) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const long long need = (long long)a.P * a.P;
+  int n = 0;
+  for (int k = 0; k < a.n_cand && n < a.n_patches; ++k)
+    if (2ll * a.cand[k] >= need) a.cand[a.n_cand + n++] = k;
+  a.bs->n_acc = n;
+  a.bs->m = (u64)n * (u64)need;
+  if (n == 0) a.bs->status = SPCN_ERR_NO_TISSUE;
+}
+
+__global__ void k_patch_gather(PatchArgs a) {
+  const u64 per = (u64)a.P * a.P;
+  const u64 m = (u64)a.bs->n_acc * per;
+  for (u64 s = (u64)blockIdx.x * blockDim.x + threadIdx.x; s < m; s += (u64)gridDim.x * blockDim.x) {
+    const int p = (int)(s / per);
+    const u64 i = s - (u64)p * per;
+    u64 x0, y0;
+    patch_origin(a, a.cand[a.n_cand + p], &x0, &y0);
+    a.out[s] = load_pixel(a.data, a.pitch, x0 + i % (u64)a.P, y0 + i / (u64)a.P);
+  }
+}
+
+// ------------------------------------------------------------ stable compaction
+struct CompactArgs {
+  const uint32_t* sample;
+  BasisState* bs;
+  unsigned thr;
+  unsigned* blk;    // [2][cap]
+  u64* blk_off;     // [2][cap]
+  u64 cap;
+  uint32_t* nw;
+  uint32_t* br;
+};
+
+__global__ void __launch_bounds__(kCompactThreads) k_classify_count(CompactArgs a) {
+  __shared__ u64 s_tmp[33];
+  const u64 m = a.bs->m;
+  const u64 base = (u64)blockIdx.x * kCompactBlock;
+  if (base >= m) return;
+  unsigned cnw = 0, cbr = 0;
+  for (int i = 0; i < kCompactPer; ++i) {
+    const u64 e = base + (u64)threadIdx.x * kCompactPer + i;
+    if (e < m) {
+      const bool nw = packed_nonwhite(a.sample[e], a.thr);
+      cnw += nw ? 1u : 0u;
+      cbr += nw ? 0u : 1u;
+    }
+  }
+  const u64 tnw = block_sum(cnw, s_tmp);
+  const u64 tbr = block_sum(cbr, s_tmp);
+  if (threadIdx.x == 0) {
+    a.blk[blockIdx.x] = (unsigned)tnw;
+    a.blk[a.cap + blockIdx.x] = (unsigned)tbr;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_scan_blocks(CompactArgs a) {
+  __shared__ u64 s_tmp[33];
+  const u64 m = a.bs->m;
+  const u64 nblk = (m + kCompactBlock - 1) / kCompactBlock;
+  for (int list = 0; list < 2; ++list) {
+    u64 run = 0;
+    for (u64 b0 = 0; b0 < nblk; b0 += blockDim.x) {
+      const u64 b = b0 + threadIdx.x;
+      const u64 v = b < nblk ? a.blk[list * a.cap + b] : 0ull;
+      u64 total;
+      const u64 ex = block_excl_scan(v, s_tmp, &total);
+      if (b < nblk) a.blk_off[list * a.cap + b] = run + ex;
+      run += total;
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      if (list == 0) a.bs->n_nw = run;
+      else a.bs->n_br = run;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kCompactThreads) k_compact(CompactArgs a) {
+  __shared__ u64 s_tmp[33];
+  const u64 m = a.bs->m;
+  const u64 base = (u64)blockIdx.x * kCompactBlock;
+  if (base >= m) return;
+  uint32_t v[kCompactPer];
+  unsigned fl = 0, cnw = 0, cbr = 0;
+  for (int i = 0; i < kCompactPer; ++i) {
+    const u64 e = base + (u64)threadIdx.x * kCompactPer + i;
+    v[i] = 0;
+    if (e < m) {
+      v[i] = a.sample[e];
+      if (packed_nonwhite(v[i], a.thr)) { fl |= 1u << i; ++cnw; }
+      else { fl |= 1u << (i + 16); ++cbr; }
+    }
+  }
+  u64 tot;
+  u64 onw = block_excl_scan(cnw, s_tmp, &tot) + a.blk_off[blockIdx.x];
+  u64 obr = block_excl_scan(cbr, s_tmp, &tot) + a.blk_off[a.cap + blockIdx.x];
+  for (int i = 0; i < kCompactPer; ++i) {
+    if (fl & (1u << i)) a.nw[onw++] = v[i];
+    else if (fl & (1u << (i + 16))) a.br[obr++] = v[i];
+  }
+}
+
+// ------------------------------------------------------------ i0 (§3.1 item 1)
+struct I0Args {
+  const uint32_t* br;
+  BasisState* bs;
+  Model* m;
+  int cap;
+  double pct;
+};
+
+__device__ double hist_rank_value(const unsigned* h, u64 rank) {
+  u64 c = 0;
+  for (int v = 0; v < 256; ++v) {
+    c += h[v];
+    if (rank < c) return (double)v;
+  }
+  return 255.0;
+}
+
+// Per channel, the type-7 percentile of every ceil(n/cap)-th bright sample
+// pixel (sample order), from a 256-bin histogram (exact for 8-bit values).
+// Also initialises the basis to the column-normalised Ruifrok-Johnston H&E
+// vectors, the starting point of the dictionary learning.
+__global__ void k_i0(I0Args a) {
+  __shared__ unsigned s_h[3][256];
+  for (int i = threadIdx.x; i < 3 * 256; i += blockDim.x) (&s_h[0][0])[i] = 0u;
+  __syncthreads();
+  const u64 nb = a.bs->n_br;
+  const u64 stride = nb ? (nb + (u64)a.cap - 1) / (u64)a.cap : 1;
+  const u64 kept = nb ? (nb + stride - 1) / stride : 0;
+  for (u64 i = threadIdx.x; i < kept; i += blockDim.x) {
+    const uint32_t v = a.br[i * stride];
+    atomicAdd(&s_h[0][v & 0xFFu], 1u);
+    atomicAdd(&s_h[1][(v >> 8) & 0xFFu], 1u);
+    atomicAdd(&s_h[2][(v >> 16) & 0xFFu], 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    const int c = threadIdx.x;
+    double val = 255.0;
+    if (kept > 0) {
+      const double pos = (double)(kept - 1) * (a.pct / 100.0);
+      u64 k = (u64)floor(pos);
+      if (k > kept - 1) k = kept - 1;
+      const double t = pos - (double)k;
+      const double lo = hist_rank_value(s_h[c], k);
+      const double hi = (k + 1 < kept) ? hist_rank_value(s_h[c], k + 1) : lo;
+      val = (k + 1 < kept) ? __dadd_rn(lo, __dmul_rn(t, __dsub_rn(hi, lo))) : lo;
+    }
+    a.m->i0[c] = (float)val;
+  }
+  if (threadIdx.x == 0) {
+    const double h[3] = {0.650, 0.704, 0.286}, e[3] = {0.072, 0.990, 0.105};
+    const double nh = sqrt(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
+    const double ne = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+    for (int c = 0; c < 3; ++c) {
+      a.bs->W[c] = h[c] / nh;
+      a.bs->W[3 + c] = e[c] / ne;
+      a.m->W[c] = (float)(h[c] / nh);
+      a.m->W[3 + c] = (float)(e[c] / ne);
+    }
+  }
+}
+
+// ------------------------------------------------------------ sparse NMF (Eq. 2)
+struct SnmfArgs {
+  const uint32_t* nw;
+  BasisState* bs;
+  Model* m;
+  double* partials;   // [2][gridDim.x][kAcc]
+  unsigned* bar;
+  int* abort;
+  int* err;
+  float lambda;
+  int max_iter;
+  double tol;
+  long long timeout_ns;
+};
+
+// Reduced sums, in this order: A11 A12 A22 | B[R,0] B[R,1] B[G,0] B[G,1]
+// B[B,0] B[B,1] | sum h1, sum h2 | sum |v|^2.
+__global__ void __launch_bounds__(kSnmfThreads) k_snmf(SnmfArgs a) {
+  __shared__ float s_od[kLutEntries];
+  __shared__ double s_W[6];
+  __shared__ double s_tot[kAcc];
+  __shared__ float s_coef[12];
+  __shared__ double s_red[kSnmfThreads / 32][kAcc];
+  __shared__ int s_flag;
+  __shared__ double s_obj;
+  const u64 n = a.bs->n_nw;
+  if (n == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.bs->status = SPCN_ERR_NO_TISSUE;
+    return;   // uniform
+  }
+  for (int i = threadIdx.x; i < kLutEntries; i += blockDim.x) s_od[i] = a.m->od[i];
+  if (threadIdx.x < 6) s_W[threadIdx.x] = a.bs->W[threadIdx.x];
+  if (threadIdx.x == 0) { s_flag = 0; s_obj = 0.0; }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const u64 gstride = (u64)gridDim.x * blockDim.x;
+  unsigned target = 0;
+  int it;
+  for (it = 1; it <= a.max_iter; ++it) {
+    if (threadIdx.x == 0) {
+      double g11 = 0, g22 = 0, g12 = 0;
+      for (int c = 0; c < 3; ++c) {
+        g11 += s_W[c] * s_W[c];
+        g22 += s_W[3 + c] * s_W[3 + c];
+        g12 += s_W[c] * s_W[3 + c];
+      }
+      const double det = g11 * g22 - g12 * g12;
+      if (!(det > 1e-12)) {
+        s_flag = -1;
+      } else {
+        for (int i = 0; i < 6; ++i) s_coef[i] = (float)s_W[i];
+        s_coef[6] = (float)(g22 / det);
+        s_coef[7] = (float)(-g12 / det);
+        s_coef[8] = (float)(-g12 / det);
+        s_coef[9] = (float)(g11 / det);
+        s_coef[10] = (float)(1.0 / g11);
+        s_coef[11] = (float)(1.0 / g22);
+      }
+    }
+    __syncthreads();
+    if (s_flag < 0) break;
+    const float w00 = s_coef[0], w10 = s_coef[1], w20 = s_coef[2];
+    const float w01 = s_coef[3], w11 = s_coef[4], w21 = s_coef[5];
+    const float a11 = s_coef[6], a12 = s_coef[7], a21 = s_coef[8], a22 = s_coef[9];
+    const float u1 = s_coef[10], u2 = s_coef[11];
+    float acc[kAcc];
+#pragma unroll
+    for (int i = 0; i < kAcc; ++i) acc[i] = 0.f;
+    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gstride) {
+      const uint32_t v = __ldg(a.nw + i);
+      const float v0 = s_od[v & 0xFFu], v1 = s_od[256 + ((v >> 8) & 0xFFu)],
+                  v2 = s_od[512 + ((v >> 16) & 0xFFu)];
+      const float d1 = fmaf(w20, v2, fmaf(w10, v1, w00 * v0)) - a.lambda;
+      const float d2 = fmaf(w21, v2, fmaf(w11, v1, w01 * v0)) - a.lambda;
+      const float t1 = fmaf(a12, fmaxf(d2, 0.f), a11 * d1);
+      const float t2 = fmaf(a21, fmaxf(d1, 0.f), a22 * d2);
+      const float h1 = fmaxf(0.f, fminf(u1 * d1, t1));
+      const float h2 = fmaxf(0.f, fminf(u2 * d2, t2));
+      acc[0] = fmaf(h1, h1, acc[0]);
+      acc[1] = fmaf(h1, h2, acc[1]);
+      acc[2] = fmaf(h2, h2, acc[2]);
+      acc[3] = fmaf(v0, h1, acc[3]);
+      acc[4] = fmaf(v0, h2, acc[4]);
+      acc[5] = fmaf(v1, h1, acc[5]);
+      acc[6] = fmaf(v1, h2, acc[6]);
+      acc[7] = fmaf(v2, h1, acc[7]);
+      acc[8] = fmaf(v2, h2, acc[8]);
+      acc[9] += h1;
+      acc[10] += h2;
+      acc[11] = fmaf(v0, v0, fmaf(v1, v1, fmaf(v2, v2, acc[11])));
+    }
+#pragma unroll
+    for (int i = 0; i < kAcc; ++i) {
+      double x = (double)acc[i];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0) s_red[warp][i] = x;
+    }
+    __syncthreads();
+    double* part = a.partials + (size_t)(it & 1) * gridDim.x * kAcc;
+    if (threadIdx.x < kAcc) {
+      double x = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x += s_red[w][threadIdx.x];
+      part[(size_t)blockIdx.x * kAcc + threadIdx.x] = x;
+    }
+    target += gridDim.x;
+    if (!grid_barrier(a.bar, target, a.abort, a.err, a.timeout_ns)) return;
+    if (threadIdx.x < kAcc) {
+      double x = 0.0;
+      for (unsigned b = 0; b < gridDim.x; ++b) x += __ldcg(part + (size_t)b * kAcc + threadIdx.x);
+      s_tot[threadIdx.x] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const double A[2][2] = {{s_tot[0], s_tot[1]}, {s_tot[1], s_tot[2]}};
+      double B[3][2];
+      for (int c = 0; c < 3; ++c) { B[c][0] = s_tot[3 + 2 * c]; B[c][1] = s_tot[4 + 2 * c]; }
+      double W[3][2], Wp[3][2];
+      for (int c = 0; c < 3; ++c) { W[c][0] = Wp[c][0] = s_W[c]; W[c][1] = Wp[c][1] = s_W[3 + c]; }
+      // objective of the H-step just taken (1/2-scaled Eq. 2)
+      double g11 = 0, g22 = 0, g12 = 0, wb = 0;
+      for (int c = 0; c < 3; ++c) {
+        g11 += Wp[c][0] * Wp[c][0];
+        g22 += Wp[c][1] * Wp[c][1];
+        g12 += Wp[c][0] * Wp[c][1];
+        wb += Wp[c][0] * B[c][0] + Wp[c][1] * B[c][1];
+      }
+      s_obj = 0.5 * s_tot[11] - wb + 0.5 * (g11 * A[0][0] + 2.0 * g12 * A[0][1] + g22 * A[1][1]) +
+              (double)a.lambda * (s_tot[9] + s_tot[10]);
+      int flag = 0;
+      for (int j = 0; j < 2 && flag == 0; ++j) {
+        if (!(A[j][j] > 0.0)) continue;
+        double u[3], nu = 0.0;
+        for (int c = 0; c < 3; ++c) {
+          u[c] = W[c][j] + (B[c][j] - (W[c][0] * A[0][j] + W[c][1] * A[1][j])) / A[j][j];
+          u[c] = u[c] > 0.0 ? u[c] : 0.0;
+          nu += u[c] * u[c];
+        }
+        nu = sqrt(nu);
+        if (!(nu > 0.0)) { flag = -1; break; }
+        for (int c = 0; c < 3; ++c) W[c][j] = u[c] / nu;
+      }
+      double dmax = 0.0;
+      for (int c = 0; c < 3; ++c)
+        for (int j = 0; j < 2; ++j) dmax = fmax(dmax, fabs(W[c][j] - Wp[c][j]));
+      for (int c = 0; c < 3; ++c) { s_W[c] = W[c][0]; s_W[3 + c] = W[c][1]; }
+      if (flag == 0 && dmax < a.tol) flag = 1;
+      s_flag = flag;
+    }
+    __syncthreads();
+    if (s_flag != 0) break;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    int status = SPCN_OK;
+    double g11 = 0, g22 = 0, g12 = 0;
+    for (int c = 0; c < 3; ++c) {
+      g11 += s_W[c] * s_W[c];
+      g22 += s_W[3 + c] * s_W[3 + c];
+      g12 += s_W[c] * s_W[3 + c];
+    }
+    if (s_flag < 0 || !(g11 * g22 - g12 * g12 > 1e-12)) status = SPCN_ERR_DEGENERATE_BASIS;
+    // §3.1 item 3: hematoxylin is the stain with the larger OD(red) - OD(blue)
+    const double d0 = s_W[0] - s_W[2], d1 = s_W[3] - s_W[5];
+    double Wo[6];
+    for (int c = 0; c < 3; ++c) {
+      Wo[c] = d1 > d0 ? s_W[3 + c] : s_W[c];
+      Wo[3 + c] = d1 > d0 ? s_W[c] : s_W[3 + c];
+    }
+    for (int i = 0; i < 6; ++i) { a.bs->W[i] = Wo[i]; a.m->W[i] = (float)Wo[i]; }
+    a.bs->iters = it > a.max_iter ? a.max_iter : it;
+    a.bs->objective = s_obj;
+    a.bs->status = status;
+  }
+}
+
+// ------------------------------------------------------------ host driver
+static int grid_for(const Context* c, int occ) { return c->num_sms * (occ > 0 ? occ : 1); }
+
+int configure_basis_kernels(Context* c) {
+  SPCN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->occ_snmf, k_snmf,
+                                                              kSnmfThreads, 0));
+  if (c->occ_snmf < 1) return SPCN_ERR_CUDA;
+  if (grid_for(c, c->occ_snmf) > kMaxSnmfGrid) c->occ_snmf = kMaxSnmfGrid / c->num_sms;
+  return SPCN_OK;
+}
+
+int run_estimate_basis(Context* c, const spcn_image* img, const spcn_params* p, spcn_stats* out,
+                       cudaStream_t st) {
+  const int64_t W = img->width, H = img->height;
+  const u64 N = (u64)W * (u64)H;
+  u64 cap = 0, m = 0;
+  int n_cand = 0;
+  if (p->sample_mode == SPCN_SAMPLE_ALL) {
+    cap = m = N;
+  } else if (p->sample_mode == SPCN_SAMPLE_HASH) {
+    m = (u64)floor((double)p->sample_rate * (double)N + 0.5);
+    if (m == 0) return SPCN_ERR_INVALID_ARG;
+    cap = m;
+  } else {
+    if (p->patch_size > W || p->patch_size > H) return SPCN_ERR_INVALID_ARG;
+    cap = (u64)p->n_patches * (u64)p->patch_size * (u64)p->patch_size;
+    n_cand = 4 * p->n_patches;
+  }
+  int rc = ensure_sample_capacity(c, (size_t)cap);
+  if (rc) return rc;
+  if (n_cand) { rc = ensure_candidate_capacity(c, n_cand + p->n_patches); if (rc) return rc; }
+
+  BasisState* bs = c->bs;
+  SPCN_CUDA_TRY(cudaMemsetAsync(bs, 0, sizeof(BasisState), st));
+  const int big_grid = c->num_sms * 8;
+  if (p->sample_mode != SPCN_SAMPLE_PATCHES) {
+    SPCN_CUDA_TRY(cudaMemcpyAsync(&bs->m, &m, sizeof(u64), cudaMemcpyHostToDevice, st));
+    SampleArgs s{img->data, img->pitch_bytes, W, H, p->seed, c->sample, m};
+    if (p->sample_mode == SPCN_SAMPLE_ALL) k_sample_all<<<big_grid, 256, 0, st>>>(s);
+    else k_sample_hash<<<big_grid, 256, 0, st>>>(s);
+    SPCN_LAUNCH_CHECK(c);
+  } else {
+    PatchArgs pa{img->data, img->pitch_bytes, W, H, p->seed, p->patch_size, p->n_patches,
+                 n_cand, (unsigned)p->white_thresh, c->cand, bs, c->sample};
+    k_patch_count<<<n_cand, 256, 0, st>>>(pa);
+    SPCN_LAUNCH_CHECK(c);
+    k_patch_accept<<<1, 32, 0, st>>>(pa);
+    SPCN_LAUNCH_CHECK(c);
+    k_patch_gather<<<big_grid, 256, 0, st>>>(pa);
+    SPCN_LAUNCH_CHECK(c);
+  }
+  const u64 nblk = (cap + kCompactBlock - 1) / kCompactBlock;
+  CompactArgs ca{c->sample, bs, (unsigned)p->white_thresh, c->blk, c->blk_off, (u64)c->blk_cap,
+                 c->nw, c->br};
+  k_classify_count<<<(unsigned)nblk, kCompactThreads, 0, st>>>(ca);
+  SPCN_LAUNCH_CHECK(c);
+  k_scan_blocks<<<1, 1024, 0, st>>>(ca);
+  SPCN_LAUNCH_CHECK(c);
+  k_compact<<<(unsigned)nblk, kCompactThreads, 0, st>>>(ca);
+  SPCN_LAUNCH_CHECK(c);
+  I0Args ia{c->br, bs, c->model_b, p->i0_max_samples, (double)p->i0_pct};
+  k_i0<<<1, 512, 0, st>>>(ia);
+  SPCN_LAUNCH_CHECK(c);
+  rc = launch_build_model(c, c->model_b, nullptr, nullptr, p->lambda, c->model_b, st);
+  if (rc) return rc;
+  // sparse NMF, one cooperative launch
+  SnmfArgs sa;
+  sa.nw = c->nw;
+  sa.bs = bs;
+  sa.m = c->model_b;
+  sa.partials = c->partials;
+  sa.bar = &c->sel->barrier;
+  sa.abort = &c->sel->abort;
+  sa.err = c->err;
+  sa.lambda = p->lambda;
+  sa.max_iter = p->max_iter;
+  sa.tol = (double)p->tol;
+  sa.timeout_ns = c->timeout_ns;
+  SPCN_CUDA_TRY(cudaMemsetAsync(c->sel, 0, sizeof(SelectState), st));
+  void* args[] = {&sa};
+  SPCN_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_snmf, grid_for(c, c->occ_snmf), kSnmfThreads,
+                                            args, 0, st));
+  c->launches++;
+  rc = launch_build_model(c, c->model_b, nullptr, nullptr, p->lambda, c->model_b, st);
+  if (rc) return rc;
+  rc = launch_select_list(c, c->nw, &bs->n_nw, c->model_b, &bs->sel, c->rhist_b,
+                          (double)p->stain_pct, st);
+  if (rc) return rc;
+
+  BasisState h;
+  Model hm;
+  int herr = 0;
+  SPCN_CUDA_TRY(cudaMemcpyAsync(&h, bs, sizeof(BasisState), cudaMemcpyDeviceToHost, st));
+  SPCN_CUDA_TRY(cudaMemcpyAsync(&hm.W, &c->model_b->W, sizeof(hm.W) + sizeof(hm.i0),
+                                cudaMemcpyDeviceToHost, st));
+  SPCN_CUDA_TRY(cudaMemcpyAsync(&herr, c->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SPCN_CUDA_TRY(cudaStreamSynchronize(st));
+  for (int i = 0; i < 6; ++i) out->W[i] = hm.W[i];
+  for (int i = 0; i < 3; ++i) out->i0[i] = hm.i0[i];
+  out->p99[0] = h.sel.p99[0];
+  out->p99[1] = h.sel.p99[1];
+  out->iters = h.iters;
+  out->n_sample = (int64_t)h.m;
+  out->n_nonwhite = (int64_t)h.n_nw;
+  out->n_bright = (int64_t)h.n_br;
+  out->objective = h.objective;
+  int status = h.status;
+  if (status == SPCN_OK && herr != 0) status = herr;
+  if (status == SPCN_OK && h.n_nw == 0) status = SPCN_ERR_NO_TISSUE;
+  out->status = status;
+  if (herr != 0) SPCN_CUDA_TRY(cudaMemsetAsync(c->err, 0, sizeof(int), st));
+  return status;
+}
+
+}  // namespace spcn

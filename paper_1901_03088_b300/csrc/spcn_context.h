@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "spcn_internal.cuh"
 
 namespace spcn {
@@ -50,7 +52,25 @@ struct Context {
   int occ_window = 0, occ_recon = 0, occ_density = 0, occ_select = 0;
   int occ_snmf = 0, occ_radix_list = 0, occ_debug = 0;
   long long timeout_ns = 2000000000LL;   // grid-barrier give-up time
+  // optional CUDA-event timing of the pixel kernels
+  struct Timed { int kernel; cudaEvent_t a, b; };
+  bool timing = false;
+  std::vector<Timed> pending;
+  std::vector<cudaEvent_t> pool;
+  double kernel_ms[SPCN_KERNEL_COUNT] = {0, 0, 0, 0};
+  int64_t kernel_n[SPCN_KERNEL_COUNT] = {0, 0, 0, 0};
 };
+
+// Brackets one launch with events when the context's timing is on.
+struct TimedLaunch {
+  Context* c;
+  int kernel;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr, b = nullptr;
+  TimedLaunch(Context* ctx, int k, cudaStream_t s);
+  ~TimedLaunch();
+};
+int drain_timing(Context* c);
 
 int ensure_sample_capacity(Context* c, size_t n);
 int ensure_candidate_capacity(Context* c, int n);

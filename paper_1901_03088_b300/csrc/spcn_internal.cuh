@@ -71,7 +71,7 @@ struct SelectState {
   int all_resolved;
   unsigned done_ctas;         // last-block ticket of pass 1
   unsigned barrier;           // grid barrier counter
-  int pad;
+  int abort;                  // set when a grid-wide wait gave up (this launch only)
   double t;                   // interpolation weight of the type-7 percentile
   double p99[2];
   double scale[2];            // tgt_p99 / p99 (1 where p99 == 0)
@@ -110,11 +110,13 @@ __device__ __forceinline__ void record_error(int* err, int code) {
 }
 
 // Grid-wide barrier for cooperative launches.  `target` is the arrival count
-// that releases this barrier (k * expected blocks for the k-th barrier).  The
-// wait gives up after timeout_ns (or as soon as another block recorded an
-// error), records SPCN_ERR_TIMEOUT and returns false; callers then return.
-__device__ __forceinline__ bool grid_barrier(unsigned* counter, unsigned target, int* err,
-                                             long long timeout_ns) {
+// that releases this barrier (k * expected blocks for the k-th barrier).
+// `abort` is a per-launch word, zeroed before the launch.  The wait gives up
+// after timeout_ns, or as soon as another block gave up; it then sets
+// *abort, records SPCN_ERR_TIMEOUT in the context's error word and returns
+// false, and the caller returns.
+__device__ __forceinline__ bool grid_barrier(unsigned* counter, unsigned target, int* abort,
+                                             int* err, long long timeout_ns) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -123,8 +125,9 @@ __device__ __forceinline__ bool grid_barrier(unsigned* counter, unsigned target,
     unsigned long long t0 = global_timer_ns();
     int ok = 1;
     while (ld_acquire(counter) < target) {
-      if (*(volatile int*)err != 0) { ok = 0; break; }
+      if (*(volatile int*)abort != 0) { ok = 0; break; }
       if ((long long)(global_timer_ns() - t0) > timeout_ns) {
+        atomicExch(abort, 1);
         record_error(err, SPCN_ERR_TIMEOUT);
         ok = 0;
         break;

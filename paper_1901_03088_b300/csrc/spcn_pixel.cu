@@ -358,7 +358,7 @@ __device__ bool radix_select(const Src& src, const float2* lut, const Lasso& L, 
   for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < 3ull * kTracks * kRadixBins; i += gstride)
     ghist[i] = 0ull;
   unsigned target = gridDim.x;
-  if (!grid_barrier(bar, target, err, timeout_ns)) return false;
+  if (!grid_barrier(bar, target, &s->abort, err, timeout_ns)) return false;
   for (int d = 0; d < 3; ++d) {
     const int shift = d == 0 ? 21 : (d == 1 ? 10 : 0);
     const int hi = d == 0 ? 32 : (d == 1 ? 21 : 10);
@@ -386,7 +386,7 @@ __device__ bool radix_select(const Src& src, const float2* lut, const Lasso& L, 
     for (int i = threadIdx.x; i < kTracks * kRadixBins; i += blockDim.x)
       if (s_hist[i]) atomicAdd(gh + i, (u64)s_hist[i]);
     target += gridDim.x;
-    if (!grid_barrier(bar, target, err, timeout_ns)) return false;
+    if (!grid_barrier(bar, target, &s->abort, err, timeout_ns)) return false;
     for (int t = 0; t < kTracks; ++t) {
       if (!s_act[t]) continue;
       block_find_rank(gh + (size_t)t * kRadixBins, kRadixBins, s_r[t], &s_idx, &s_before, s_tmp);
@@ -591,8 +591,8 @@ __global__ void __launch_bounds__(kPassThreads) k_pass_density(DensityArgs a) {
 }
 
 // ------------------------------------------------------------ failure-detection hook
-__global__ void k_debug_barrier(unsigned* counter, int* err, int extra, long long timeout_ns) {
-  grid_barrier(counter, gridDim.x + (unsigned)extra, err, timeout_ns);
+__global__ void k_debug_barrier(SelectState* s, int* err, int extra, long long timeout_ns) {
+  grid_barrier(&s->barrier, gridDim.x + (unsigned)extra, &s->abort, err, timeout_ns);
 }
 
 // ------------------------------------------------------------ host launchers
@@ -671,7 +671,10 @@ int launch_percentile_passes(Context* c, const Geometry& g, const Model* m, int 
   SPCN_CUDA_TRY(cudaMemsetAsync(c->coarse, 0, sizeof(u64) * 2 * kWinGroups, st));
   if (a.nb0) SPCN_CUDA_TRY(cudaMemsetAsync(c->fine, 0, sizeof(u64) * a.nb0, st));
   if (a.nb1) SPCN_CUDA_TRY(cudaMemsetAsync(c->fine + kWinBins, 0, sizeof(u64) * a.nb1, st));
-  k_pass_window<<<grid_of(c, c->occ_window), kPassThreads, kWindowSmem, st>>>(a);
+  {
+    TimedLaunch tl(c, SPCN_KERNEL_PASS1, st);
+    k_pass_window<<<grid_of(c, c->occ_window), kPassThreads, kWindowSmem, st>>>(a);
+  }
   SPCN_LAUNCH_CHECK(c);
 
   SelectImageArgs s;
@@ -685,8 +688,11 @@ int launch_percentile_passes(Context* c, const Geometry& g, const Model* m, int 
   s.tgt0 = a.tgt0;
   s.tgt1 = a.tgt1;
   void* args[] = {&s};
-  SPCN_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_select_image, grid_of(c, c->occ_select),
-                                            kPassThreads, args, kRadixSmem, st));
+  {
+    TimedLaunch tl(c, SPCN_KERNEL_SELECT, st);
+    SPCN_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_select_image, grid_of(c, c->occ_select),
+                                              kPassThreads, args, kRadixSmem, st));
+  }
   c->launches++;
   return SPCN_OK;
 }
@@ -718,7 +724,10 @@ int launch_recon(Context* c, const Geometry& g, const Model* m, const float* Wt,
   a.sel = c->sel;
   for (int i = 0; i < 6; ++i) a.Wt[i] = Wt[i];
   for (int i = 0; i < 3; ++i) a.l2i0[i] = (float)log2((double)i0t[i]);
-  k_pass_recon<<<grid_of(c, c->occ_recon), kPassThreads, kLutSmem, st>>>(a);
+  {
+    TimedLaunch tl(c, SPCN_KERNEL_PASS2, st);
+    k_pass_recon<<<grid_of(c, c->occ_recon), kPassThreads, kLutSmem, st>>>(a);
+  }
   SPCN_LAUNCH_CHECK(c);
   return SPCN_OK;
 }
@@ -730,16 +739,19 @@ int launch_density(Context* c, const Geometry& g, const Model* m, float* H, int6
   a.m = m;
   a.H = H;
   a.stride = stride;
-  k_pass_density<<<grid_of(c, c->occ_density), kPassThreads, kLutSmem, st>>>(a);
+  {
+    TimedLaunch tl(c, SPCN_KERNEL_DENSITY, st);
+    k_pass_density<<<grid_of(c, c->occ_density), kPassThreads, kLutSmem, st>>>(a);
+  }
   SPCN_LAUNCH_CHECK(c);
   return SPCN_OK;
 }
 
 int launch_debug_barrier(Context* c, int extra, long long timeout_ns, cudaStream_t st) {
-  unsigned* counter = &c->sel->barrier;
+  SelectState* sel = c->sel;
   SPCN_CUDA_TRY(cudaMemsetAsync(c->sel, 0, sizeof(SelectState), st));
   int* err = c->err;
-  void* args[] = {&counter, &err, &extra, &timeout_ns};
+  void* args[] = {&sel, &err, &extra, &timeout_ns};
   SPCN_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_debug_barrier, c->num_sms, 128, args, 0, st));
   c->launches++;
   return SPCN_OK;

@@ -1,0 +1,256 @@
+"""Python binding of the SPCN C ABI (include/spcn.h) over ctypes.
+
+Argument marshalling only: every step of the method runs in the CUDA library
+``libspcn.so`` built beside this file.  Torch tensors supply device memory and
+the current CUDA stream.  If the library is missing this module raises at
+import time; there is no other implementation to fall back on.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libspcn.so")
+
+SPCN_OK = 0
+STATUS_NAMES = {
+    0: "OK", -1: "INVALID_ARG", -2: "CUDA", -3: "OOM", -4: "NO_TISSUE",
+    -5: "DEGENERATE_BASIS", -6: "TIMEOUT",
+}
+SAMPLE_MODES = {"all": 0, "hash": 1, "patches": 2}
+
+
+class SpcnError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        self.kind = STATUS_NAMES.get(status, str(status))
+        msg = _lib.spcn_strerror(status).decode() if _lib is not None else self.kind
+        super().__init__(f"{where}: {self.kind} ({msg})")
+
+
+class Image(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("width", ctypes.c_int32),
+                ("height", ctypes.c_int32), ("pitch_bytes", ctypes.c_int64)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_float), ("white_thresh", ctypes.c_int32),
+                ("i0_pct", ctypes.c_float), ("stain_pct", ctypes.c_float),
+                ("i0_max_samples", ctypes.c_int32), ("sample_mode", ctypes.c_int32),
+                ("sample_rate", ctypes.c_float), ("n_patches", ctypes.c_int32),
+                ("patch_size", ctypes.c_int32), ("max_iter", ctypes.c_int32),
+                ("tol", ctypes.c_float), ("flags", ctypes.c_uint32),
+                ("seed", ctypes.c_uint64)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("W", ctypes.c_float * 6), ("i0", ctypes.c_float * 3),
+                ("p99", ctypes.c_double * 2), ("iters", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("n_sample", ctypes.c_int64),
+                ("n_nonwhite", ctypes.c_int64), ("n_bright", ctypes.c_int64),
+                ("objective", ctypes.c_double)]
+
+    @property
+    def basis(self):
+        """W as a 3x2 nested list (rows R, G, B; columns hematoxylin, eosin)."""
+        return [[self.W[c], self.W[3 + c]] for c in range(3)]
+
+    @staticmethod
+    def from_values(W, i0, p99=(0.0, 0.0)) -> "Stats":
+        """Record from a 3x2 basis (rows R,G,B), i0 (3) and p99 (2)."""
+        s = Stats()
+        for c in range(3):
+            s.W[c] = float(W[c][0])
+            s.W[3 + c] = float(W[c][1])
+            s.i0[c] = float(i0[c])
+        s.p99[0], s.p99[1] = float(p99[0]), float(p99[1])
+        return s
+
+    def copy(self) -> "Stats":
+        s = Stats()
+        ctypes.memmove(ctypes.byref(s), ctypes.byref(self), ctypes.sizeof(Stats))
+        return s
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run `python -m paper_1901_03088_b300.build`")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    P = ctypes.POINTER
+    sig = {
+        "spcn_params_default": (None, [P(Params)]),
+        "spcn_context_create": (ctypes.c_int, [P(vp), ctypes.c_int]),
+        "spcn_context_destroy": (ctypes.c_int, [vp]),
+        "spcn_estimate_basis": (ctypes.c_int, [vp, P(Image), P(Params), P(Stats), vp]),
+        "spcn_stain_percentile": (ctypes.c_int, [vp, P(Image), P(Stats), P(Params),
+                                                 P(ctypes.c_double), vp]),
+        "spcn_stain_densities": (ctypes.c_int, [vp, P(Image), P(Stats), P(Params), vp, i64, vp]),
+        "spcn_normalize": (ctypes.c_int, [vp, P(Image), P(Stats), P(Stats), P(Params), vp, i64,
+                                          P(ctypes.c_double), vp]),
+        "spcn_synchronize": (ctypes.c_int, [vp, vp]),
+        "spcn_launch_count": (i64, [vp]),
+        "spcn_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "spcn_debug_barrier_timeout": (ctypes.c_int, [vp, i32, i64, vp]),
+        "spcn_kernel_timing": (ctypes.c_int, [vp, ctypes.c_int]),
+        "spcn_kernel_times": (ctypes.c_int, [vp, ctypes.c_int, P(ctypes.c_double), P(i64)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = None
+_lib = _load()
+lib = _lib
+
+# Every name the header declares, for the export check.
+EXPORTED = ("spcn_params_default", "spcn_context_create", "spcn_context_destroy",
+            "spcn_estimate_basis", "spcn_stain_percentile", "spcn_stain_densities",
+            "spcn_normalize", "spcn_synchronize", "spcn_launch_count", "spcn_strerror",
+            "spcn_debug_barrier_timeout", "spcn_kernel_timing", "spcn_kernel_times")
+KERNELS = {"pass1": 0, "select": 1, "pass2": 2, "density": 3}
+
+
+def params(**kw) -> Params:
+    """The paper's constants (spcn_params_default) with keyword overrides;
+    ``lam`` sets lambda and ``sample_mode`` accepts 'all', 'hash', 'patches'."""
+    p = Params()
+    _lib.spcn_params_default(ctypes.byref(p))
+    for k, v in kw.items():
+        if k in ("lam", "lambda_"):
+            p.lambda_ = float(v)
+        elif k == "sample_mode" and isinstance(v, str):
+            p.sample_mode = SAMPLE_MODES[v]
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def _check(rc: int, where: str):
+    if rc != SPCN_OK:
+        raise SpcnError(rc, where)
+
+
+def image_of(t) -> Image:
+    """spcn_image view of an (H, W, 3) uint8 CUDA tensor whose pixels are
+    interleaved (channel stride 1, pixel stride 3); rows may be pitched."""
+    import torch
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.uint8 or t.dim() != 3 or t.shape[2] != 3:
+        raise ValueError("expected an (H, W, 3) uint8 tensor")
+    if not t.is_cuda:
+        raise ValueError("image must be in device memory")
+    if t.stride(2) != 1 or t.stride(1) != 3:
+        raise ValueError("pixels must be interleaved RGB (strides (pitch, 3, 1))")
+    return Image(t.data_ptr(), t.shape[1], t.shape[0], t.stride(0))
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """A library context on one CUDA device (owns the device scratch)."""
+
+    def __init__(self, device: int = 0):
+        h = ctypes.c_void_p()
+        _check(_lib.spcn_context_create(ctypes.byref(h), int(device)), "spcn_context_create")
+        self._h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.spcn_context_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def launches(self) -> int:
+        return int(_lib.spcn_launch_count(self._h))
+
+    def estimate_basis(self, img, p: Params | None = None, stream=None) -> Stats:
+        st = Stats()
+        im = image_of(img)
+        p = p or params()
+        rc = _lib.spcn_estimate_basis(self._h, ctypes.byref(im), ctypes.byref(p),
+                                      ctypes.byref(st), _stream(stream))
+        _check(rc, "spcn_estimate_basis")
+        return st
+
+    def stain_percentile(self, img, stats: Stats, p: Params | None = None, stream=None):
+        out = (ctypes.c_double * 2)()
+        im = image_of(img)
+        p = p or params()
+        rc = _lib.spcn_stain_percentile(self._h, ctypes.byref(im), ctypes.byref(stats),
+                                        ctypes.byref(p), out, _stream(stream))
+        _check(rc, "spcn_stain_percentile")
+        return float(out[0]), float(out[1])
+
+    def stain_densities(self, img, stats: Stats, p: Params | None = None, out=None, stream=None):
+        import torch
+        im = image_of(img)
+        n = im.width * im.height
+        if out is None:
+            out = torch.empty((2, n), dtype=torch.float32, device=img.device)
+        if out.dtype != torch.float32 or out.dim() != 2 or out.shape[0] != 2 or out.stride(1) != 1:
+            raise ValueError("out must be a (2, >=H*W) float32 tensor with unit inner stride")
+        p = p or params()
+        rc = _lib.spcn_stain_densities(self._h, ctypes.byref(im), ctypes.byref(stats),
+                                       ctypes.byref(p), ctypes.c_void_p(out.data_ptr()),
+                                       out.stride(0), _stream(stream))
+        _check(rc, "spcn_stain_densities")
+        return out
+
+    def normalize(self, src, src_stats: Stats, tgt_stats: Stats, p: Params | None = None,
+                  out=None, return_p99: bool = False, stream=None):
+        import torch
+        im = image_of(src)
+        if out is None:
+            out = torch.empty_like(src, memory_format=torch.contiguous_format)
+        if out.shape != src.shape or out.dtype != torch.uint8 or out.stride(2) != 1 or out.stride(1) != 3:
+            raise ValueError("out must be an (H, W, 3) uint8 interleaved tensor")
+        p = p or params()
+        p99 = (ctypes.c_double * 2)() if return_p99 else None
+        rc = _lib.spcn_normalize(self._h, ctypes.byref(im), ctypes.byref(src_stats),
+                                 ctypes.byref(tgt_stats), ctypes.byref(p),
+                                 ctypes.c_void_p(out.data_ptr()), out.stride(0),
+                                 p99, _stream(stream))
+        _check(rc, "spcn_normalize")
+        if return_p99:
+            return out, (float(p99[0]), float(p99[1]))
+        return out
+
+    def kernel_timing(self, enable: bool):
+        """Start (and reset) or stop CUDA-event timing of the pixel kernels."""
+        _check(_lib.spcn_kernel_timing(self._h, 1 if enable else 0), "spcn_kernel_timing")
+
+    def kernel_times(self, name: str):
+        """(total ms, launches) of a timed kernel: pass1, select, pass2, density."""
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        _check(_lib.spcn_kernel_times(self._h, KERNELS[name], ctypes.byref(ms), ctypes.byref(n)),
+               "spcn_kernel_times")
+        return float(ms.value), int(n.value)
+
+    def synchronize(self, stream=None):
+        _check(_lib.spcn_synchronize(self._h, _stream(stream)), "spcn_synchronize")
+
+    def debug_barrier_timeout(self, extra_arrivals: int, timeout_ns: int, stream=None) -> int:
+        """Status of the failure-detection hook (see the header)."""
+        return int(_lib.spcn_debug_barrier_timeout(self._h, int(extra_arrivals),
+                                                   int(timeout_ns), _stream(stream)))
