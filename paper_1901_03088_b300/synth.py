@@ -91,10 +91,10 @@ def make_image(height: int, width: int, seed: int, W=None, blobs: bool = False,
     I = np.asarray(white, dtype=np.float64)[:, None] * np.exp(-(W @ H))
     if noise > 0:
         I = I + rng.normal(0.0, noise, size=I.shape)
-    I = I.T.reshape(height, width, 3)
+    I = np.ascontiguousarray(I.T.reshape(height, width, 3))
     if as_float:
         return np.clip(I, 0.0, 255.0)
-    return np.clip(np.rint(I), 0, 255).astype(np.uint8)
+    return np.ascontiguousarray(np.clip(np.rint(I), 0, 255).astype(np.uint8))
 
 
 # ---------------------------------------------------------------------------
