@@ -51,7 +51,8 @@ typedef enum {
   SPCN_ERR_OOM = -3,              /* device scratch allocation failed */
   SPCN_ERR_NO_TISSUE = -4,        /* no non-white pixel where one is needed */
   SPCN_ERR_DEGENERATE_BASIS = -5, /* stain vectors (nearly) parallel or vanished */
-  SPCN_ERR_TIMEOUT = -6           /* a grid-wide wait gave up (kernel returned) */
+  SPCN_ERR_TIMEOUT = -6,          /* a grid-wide wait gave up (kernel returned) */
+  SPCN_ERR_SCRATCH_LIMIT = -7     /* request larger than spcn_estimate_basis_noalloc's fixed scratch */
 } spcn_status;
 
 typedef enum {
@@ -159,6 +160,26 @@ int spcn_normalize(void* ctx, const spcn_image* src, const spcn_stats* src_st,
  * asynchronous call recorded on the device since the last synchronising
  * call (the record is then cleared). */
 int spcn_synchronize(void* ctx, void* stream);
+
+/* Basis estimation for callers that cannot allocate device memory (no
+ * counterpart in the paper; it exists for deployment).  Hosts that own all
+ * GPU memory through their own pool, plugin hosts that forbid cudaMalloc, and
+ * pipelines that must not call the allocator (it can stall the device) cannot
+ * create a context.  This entry point needs none: it runs the same work as
+ * spcn_estimate_basis on the current device, with all scratch taken from one
+ * fixed array inside the library (about 6.8 MB, resident on every GPU that
+ * loads the library until the process exits).  It allocates nothing.
+ *   Limits: at most 524288 sample pixels (SPCN_SAMPLE_ALL: width*height;
+ *   SPCN_SAMPLE_HASH: round(rate*N); SPCN_SAMPLE_PATCHES:
+ *   n_patches*patch_size^2) and at most 4096 patches; larger requests return
+ *   SPCN_ERR_SCRATCH_LIMIT without touching the device.
+ *   The first call on a device does a one-time set-up (resolves the array's
+ *   device address, reads launch attributes); make that first call before
+ *   any stream capture.  All calls share the one array, so calls that
+ *   overlap on the GPU (other host threads, other streams) race; serialise
+ *   them.  Blocks the host like spcn_estimate_basis; same other errors. */
+int spcn_estimate_basis_noalloc(const spcn_image* img, const spcn_params* params,
+                                spcn_stats* out, void* stream);
 
 /* Number of kernels the context has launched since creation (for launch
  * accounting in benchmarks). */

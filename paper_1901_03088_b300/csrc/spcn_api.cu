@@ -232,6 +232,7 @@ const char* spcn_strerror(int status) {
     case SPCN_ERR_NO_TISSUE: return "no non-white (tissue) pixel";
     case SPCN_ERR_DEGENERATE_BASIS: return "degenerate stain basis";
     case SPCN_ERR_TIMEOUT: return "grid-wide wait timed out";
+    case SPCN_ERR_SCRATCH_LIMIT: return "request exceeds the fixed scratch of the no-allocation entry point";
     default: return "unknown status";
   }
 }

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "libspcn.so")
 SPCN_OK = 0
 STATUS_NAMES = {
     0: "OK", -1: "INVALID_ARG", -2: "CUDA", -3: "OOM", -4: "NO_TISSUE",
-    -5: "DEGENERATE_BASIS", -6: "TIMEOUT",
+    -5: "DEGENERATE_BASIS", -6: "TIMEOUT", -7: "SCRATCH_LIMIT",
 }
 SAMPLE_MODES = {"all": 0, "hash": 1, "patches": 2}
 
@@ -94,6 +94,7 @@ def _load():
         "spcn_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "spcn_debug_barrier_timeout": (ctypes.c_int, [vp, i32, i64, vp]),
         "spcn_kernel_timing": (ctypes.c_int, [vp, ctypes.c_int]),
+        "spcn_estimate_basis_noalloc": (ctypes.c_int, [P(Image), P(Params), P(Stats), vp]),
         "spcn_kernel_times": (ctypes.c_int, [vp, ctypes.c_int, P(ctypes.c_double), P(i64)]),
     }
     for name, (res, args) in sig.items():
@@ -111,7 +112,8 @@ lib = _lib
 EXPORTED = ("spcn_params_default", "spcn_context_create", "spcn_context_destroy",
             "spcn_estimate_basis", "spcn_stain_percentile", "spcn_stain_densities",
             "spcn_normalize", "spcn_synchronize", "spcn_launch_count", "spcn_strerror",
-            "spcn_debug_barrier_timeout", "spcn_kernel_timing", "spcn_kernel_times")
+            "spcn_debug_barrier_timeout", "spcn_kernel_timing", "spcn_kernel_times",
+            "spcn_estimate_basis_noalloc")
 KERNELS = {"pass1": 0, "select": 1, "pass2": 2, "density": 3}
 
 
@@ -153,6 +155,20 @@ def _stream(stream):
     if stream is None:
         stream = torch.cuda.current_stream()
     return ctypes.c_void_p(stream.cuda_stream)
+
+
+def estimate_basis_noalloc(img, p: Params | None = None, stream=None) -> Stats:
+    """Basis estimation that allocates no device memory (for hosts that cannot
+    call the CUDA allocator): same result as Context.estimate_basis, scratch
+    from a fixed array inside the library, at most 524288 sample pixels.
+    Runs on the current CUDA device; concurrent calls race."""
+    st = Stats()
+    im = image_of(img)
+    p = p or params()
+    rc = _lib.spcn_estimate_basis_noalloc(ctypes.byref(im), ctypes.byref(p), ctypes.byref(st),
+                                          _stream(stream))
+    _check(rc, "spcn_estimate_basis_noalloc")
+    return st
 
 
 class Context:
