@@ -324,7 +324,7 @@ int spcn_stain_percentile(void* ctx, const spcn_image* img, const spcn_stats* st
   if (rc) return rc;
   const double ones[2] = {1.0, 1.0};
   rc = launch_percentile_passes(c, g, c->model, params->white_thresh, (double)params->stain_pct,
-                                st->p99, ones, s);
+                                st->p99, host_table_hexp(st->W, st->i0, params->lambda), ones, s);
   if (rc) return rc;
   double p[2];
   SPCN_CUDA_TRY(cudaMemcpyAsync(p, c->sel->p99, sizeof(p), cudaMemcpyDeviceToHost, s));
@@ -377,7 +377,8 @@ int spcn_normalize(void* ctx, const spcn_image* src, const spcn_stats* src_st,
   rc = launch_build_model(c, c->model, src_st->W, src_st->i0, params->lambda, nullptr, s);
   if (rc) return rc;
   rc = launch_percentile_passes(c, g, c->model, params->white_thresh, (double)params->stain_pct,
-                                src_st->p99, tgt_st->p99, s);
+                                src_st->p99, host_table_hexp(src_st->W, src_st->i0, params->lambda),
+                                tgt_st->p99, s);
   if (rc) return rc;
   rc = launch_recon(c, g, c->model, tgt_st->W, tgt_st->i0, s);
   if (rc) return rc;

@@ -91,9 +91,8 @@ int ensure_candidate_capacity(Context* c, int n);
   } while (0)
 
 // Shared-memory sizes of the pixel kernels.
-constexpr size_t kLutSmem = sizeof(float2) * kLutEntries * kLutRep;
-constexpr size_t kWindowSmem = kLutSmem + sizeof(unsigned) * 2 * kWinGroups;
-constexpr size_t kRadixSmem = kLutSmem + sizeof(unsigned) * kTracks * kRadixBins;
+constexpr size_t kWindowSmem = kLutSmemBytes + sizeof(unsigned) * 2 * kWinGroups;
+constexpr size_t kRadixSmem = kLutSmemBytes + sizeof(unsigned) * kTracks * kRadixBins;
 
 int configure_pixel_kernels(Context* c);
 int configure_basis_kernels(Context* c);

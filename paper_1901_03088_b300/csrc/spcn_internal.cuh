@@ -24,8 +24,18 @@ namespace spcn {
 
 typedef unsigned long long u64;
 
-constexpr int kLutRep = 16;          // copies per table entry: lane l reads copy l%16
+// Shared-memory table of Eq. 1 projected on the basis: one 256-byte row per
+// 8-bit intensity, holding 16 copies (one per lane of a half-warp, so 64-bit
+// loads never conflict) of the red and green entries; a second 64 KB region
+// holds the blue entries.  The byte offset of (channel, intensity i) for lane
+// l is i*256 + (l%16)*8 + {0, 128, 65536}: one byte permute builds it from
+// the packed pixel bytes.
+constexpr int kLutRep = 16;
 constexpr int kLutEntries = 3 * 256;
+constexpr int kLutRowBytes = 256;
+constexpr int kLutOffG = 128;
+constexpr int kLutOffB = 256 * kLutRowBytes;
+constexpr int kLutSmemBytes = 2 * 256 * kLutRowBytes;
 constexpr int kChunk = 16;           // pixels per thread step (48 bytes)
 constexpr int kWinBits = 20;
 constexpr int kWinBins = 1 << kWinBits;   // exact key bins per stain in the window
@@ -34,25 +44,32 @@ constexpr int kWinGroup = 1 << kWinGroupBits;
 constexpr int kWinGroups = kWinBins >> kWinGroupBits;
 constexpr int kRadixBins = 2048;
 constexpr int kTracks = 4;           // (stain 0, rank k), (0, k+1), (1, k), (1, k+1)
-constexpr int kPassThreads = 512;
+constexpr int kPassThreads = 1024;     // one block per SM (the table fills 128 KB)
+constexpr int kHexpAuto = -1000000;
 constexpr int kAcc = 12;             // sparse-NMF reduced sums
 constexpr double kWindowDelta = 0.04;   // relative half-width of the P99 window
 
-// Closed form of the two-atom non-negative lasso for one basis:
-//   d = W'v - lambda (folded into the projected table),
-//   t1 = a11 d1 + a12 max(d2,0),  t2 = a22 d2 + a21 max(d1,0),
-//   h1 = max(0, min(u1 d1, t1)),  h2 = max(0, min(u2 d2, t2)),
-// with a11 = G22/det, a12 = a21 = -G12/det, a22 = G11/det, u_j = 1/G_jj.
-// Equal to the KKT active-set solution whenever G12 = w1.w2 >= 0, which
-// holds for non-negative bases.
+// Closed form of the two-atom non-negative lasso (Eq. 2's H-step) used by
+// every pixel pass.  With G = W'W, d_j = (w_j.v - lambda)/G_jj, rho_j =
+// G12/G_jj and kappa = G11 G22 / det G, the minimiser over h >= 0 is
+//   h_j = max(0, min(d_j, kappa (d_j - rho_j max(d_other, 0))))
+// whenever G12 >= 0 (non-negative bases); with D_j = max(0, d_j) this is
+//   h_j = min(D_j, max(0, kappa (D_j - rho_j D_other))).
+// The table stores s*d_j contributions (lambda and 1/G_jj folded in, s =
+// 2^-hexp chosen so that |s d_j| <= 1/2), so both max(0, .) become the
+// hardware saturate modifier; h_j = 2^hexp * h~_j exactly.
 struct Lasso {
-  float a11, a12, a21, a22, u1, u2;
+  float nrho1, nrho2;   // -rho_1, -rho_2
+  float kappa;
+  float hscale;         // 2^hexp
+  int hexp;
+  int pad;
 };
 
 // Per-image model in device memory.
 struct Model {
-  float2 proj[kLutEntries];   // (W[c,0] v_c(i), W[c,1] v_c(i)) - (lambda,lambda) for c == 0
-  float od[kLutEntries];      // v_c(i)
+  float2 proj[kLutEntries];   // s ((W[c,0] v_c(i) - [c==0] lambda)/G11, (W[c,1] v_c(i) - [c==0] lambda)/G22)
+  float od[kLutEntries];      // v_c(i) = log(i0_c / max(i,1))
   Lasso lasso;
   float W[6];                 // column-major 3x2
   float i0[3];
@@ -146,40 +163,116 @@ __device__ __forceinline__ u64 div_chunks(u64 q, u64 cpr, u64 magic) {
   return cpr == 1 ? q : __umul64hi(q, magic);
 }
 
-// Byte k of a 48-byte chunk held in 12 words.
-template <int I>
-__device__ __forceinline__ unsigned chunk_byte(const unsigned (&w)[12]) {
-  return (w[I >> 2] >> ((I & 3) * 8)) & 0xFFu;
+// ---------------------------------------------------------------- f32x2
+typedef unsigned long long f2;   // two packed FP32 lanes (lo, hi)
+
+__device__ __forceinline__ f2 pk(float lo, float hi) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float lo_of(f2 v) {
+  float a;
+  asm("mov.b64 {%0, _}, %1;" : "=f"(a) : "l"(v));
+  return a;
+}
+__device__ __forceinline__ float hi_of(f2 v) {
+  float b;
+  asm("mov.b64 {_, %0}, %1;" : "=f"(b) : "l"(v));
+  return b;
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+  f2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+  f2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+  f2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ float add_sat(float a, float b) {
+  float d;
+  asm("add.rn.sat.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+  return d;
+}
+__device__ __forceinline__ float mul_sat(float a, float b) {
+  float d;
+  asm("mul.rn.sat.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+  return d;
+}
+__device__ __forceinline__ float fma_sat(float a, float b, float c) {
+  float d;
+  asm("fma.rn.sat.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
 }
 
-// The Eq. 2 H-step of one pixel from its 8-bit channels.  `lut` points at
-// this lane's copy of the projected table.  Every pixel pass uses exactly
-// this arithmetic, so their densities agree bit for bit.
-__device__ __forceinline__ void solve_pixel(const float2* __restrict__ lut, unsigned r,
-                                            unsigned g, unsigned b, const Lasso& L,
-                                            float& h1, float& h2) {
-  const float2 e0 = lut[r * kLutRep];
-  const float2 e1 = lut[(256u + g) * kLutRep];
-  const float2 e2 = lut[(512u + b) * kLutRep];
-  const float d1 = (e0.x + e1.x) + e2.x;
-  const float d2 = (e0.y + e1.y) + e2.y;
-  const float t1 = fmaf(L.a12, fmaxf(d2, 0.f), L.a11 * d1);
-  const float t2 = fmaf(L.a21, fmaxf(d1, 0.f), L.a22 * d2);
-  const float m1 = fminf(L.u1 * d1, t1);
-  const float m2 = fminf(L.u2 * d2, t2);
-  // max with 0 on the bit pattern: negative values and -0 become +0
-  h1 = __int_as_float(max(__float_as_int(m1), 0));
-  h2 = __int_as_float(max(__float_as_int(m2), 0));
+// ---------------------------------------------------------------- H-step
+// Table byte offset of the intensity held in byte `s` (0..3) of `word` for
+// this lane: lanereg = (lane % 16) * 8 supplies byte 0, the intensity byte
+// lands in byte 1 (x256), bytes 2-3 are zero.
+__device__ __forceinline__ unsigned lut_addr(unsigned word, unsigned lanereg, int s) {
+  return __byte_perm(word, lanereg, 0x7604u | ((unsigned)s << 4));
 }
 
-// Copy the projected table of `m` into shared memory, replicated kLutRep
-// times (entry e, copy r at s[e * kLutRep + r]); returns this lane's base.
-__device__ __forceinline__ const float2* load_lut(const Model* __restrict__ m, float2* s) {
-  for (int i = threadIdx.x; i < kLutEntries * kLutRep; i += blockDim.x)
-    s[i] = m->proj[i / kLutRep];
+__device__ __forceinline__ float2 lut_ld(const char* lut, unsigned off) {
+  return *reinterpret_cast<const float2*>(lut + off);
+}
+
+// Scaled H-step of one pixel from its three table offsets.  Every pixel pass
+// (and solve_pair below, lane by lane) uses exactly this arithmetic, so all
+// passes produce the same densities bit for bit.
+__device__ __forceinline__ void solve_one(const char* lut, unsigned aR, unsigned aG, unsigned aB,
+                                          const Lasso& L, float& h1, float& h2) {
+  const float2 eR = lut_ld(lut, aR), eG = lut_ld(lut, aG + kLutOffG), eB = lut_ld(lut, aB + kLutOffB);
+  const float D1 = add_sat(eR.x + eG.x, eB.x);
+  const float D2 = add_sat(eR.y + eG.y, eB.y);
+  const float t1 = mul_sat(L.kappa, fmaf(L.nrho1, D2, D1));
+  const float t2 = mul_sat(L.kappa, fmaf(L.nrho2, D1, D2));
+  h1 = fminf(D1, t1);
+  h2 = fminf(D2, t2);
+}
+
+// The same for two pixels at once, packed lanes: (A, B) -> H1 = (h1_A, h1_B),
+// H2 = (h2_A, h2_B).
+__device__ __forceinline__ void solve_pair(const char* lut, unsigned aRA, unsigned aGA,
+                                           unsigned aBA, unsigned aRB, unsigned aGB, unsigned aBB,
+                                           f2 NR1, f2 NR2, float kappa, f2& H1, f2& H2) {
+  const float2 eRA = lut_ld(lut, aRA), eGA = lut_ld(lut, aGA + kLutOffG),
+               eBA = lut_ld(lut, aBA + kLutOffB);
+  const float2 eRB = lut_ld(lut, aRB), eGB = lut_ld(lut, aGB + kLutOffG),
+               eBB = lut_ld(lut, aBB + kLutOffB);
+  const f2 SA = add2(pk(eRA.x, eRA.y), pk(eGA.x, eGA.y));
+  const f2 SB = add2(pk(eRB.x, eRB.y), pk(eGB.x, eGB.y));
+  const float D1A = add_sat(lo_of(SA), eBA.x), D2A = add_sat(hi_of(SA), eBA.y);
+  const float D1B = add_sat(lo_of(SB), eBB.x), D2B = add_sat(hi_of(SB), eBB.y);
+  const f2 P1 = pk(D1A, D1B), P2 = pk(D2A, D2B);
+  const f2 Q1 = fma2(NR1, P2, P1);
+  const f2 Q2 = fma2(NR2, P1, P2);
+  const float t1A = mul_sat(kappa, lo_of(Q1)), t1B = mul_sat(kappa, hi_of(Q1));
+  const float t2A = mul_sat(kappa, lo_of(Q2)), t2B = mul_sat(kappa, hi_of(Q2));
+  H1 = pk(fminf(D1A, t1A), fminf(D1B, t1B));
+  H2 = pk(fminf(D2A, t2A), fminf(D2B, t2B));
+}
+
+// Copy the projected table of `m` into the shared-memory layout above.
+__device__ __forceinline__ void load_lut(const Model* __restrict__ m, char* s) {
+  float2* f = reinterpret_cast<float2*>(s);
+  // region 0: rows of [R x16][G x16]; region 1: rows of [B x16][unused x16]
+  for (int i = threadIdx.x; i < 2 * 256 * 32; i += blockDim.x) {
+    const int region = i >> 13, row = (i >> 5) & 255, half = (i >> 4) & 1;
+    const int c = region == 0 ? half : 2;
+    f[i] = (region == 1 && half == 1) ? make_float2(0.f, 0.f) : m->proj[c * 256 + row];
+  }
   __syncthreads();
-  return s + (threadIdx.x & (kLutRep - 1));
 }
+
+__device__ __forceinline__ unsigned lane_reg() { return (threadIdx.x & 15u) << 3; }
 
 // Inclusive warp scan of 64-bit counts.
 __device__ __forceinline__ u64 warp_incl_scan(u64 v) {
@@ -280,12 +373,14 @@ __device__ __forceinline__ void set_ranks(SelectState* s, u64 n, double pct) {
   s->rank[0] = k; s->rank[1] = k1; s->rank[2] = k; s->rank[3] = k1;
 }
 
-// Percentiles and scale factors once all four keys are known.
-__device__ __forceinline__ void finish_percentiles(SelectState* s, double tgt0, double tgt1) {
+// Percentiles and scale factors once all four keys are known.  Keys are the
+// bit patterns of the scaled densities h~; h = hscale * h~ exactly.
+__device__ __forceinline__ void finish_percentiles(SelectState* s, double tgt0, double tgt1,
+                                                   float hscale) {
   const double tg[2] = {tgt0, tgt1};
   for (int j = 0; j < 2; ++j) {
-    const double p = interp_type7(__uint_as_float(s->key[2 * j]),
-                                  __uint_as_float(s->key[2 * j + 1]), s->t);
+    const double p = interp_type7(__fmul_rn(__uint_as_float(s->key[2 * j]), hscale),
+                                  __fmul_rn(__uint_as_float(s->key[2 * j + 1]), hscale), s->t);
     s->p99[j] = p;
     s->scale[j] = (p != 0.0) ? tg[j] / p : 1.0;
   }
@@ -298,8 +393,9 @@ struct Context;
 int launch_build_model(Context* c, Model* m, const float* W, const float* i0, float lambda,
                        const Model* from_device, cudaStream_t st);
 int launch_percentile_passes(Context* c, const Geometry& g, const Model* m, int white_thresh,
-                             double pct, const double* hint, const double* tgt_p99,
+                             double pct, const double* hint, int hexp, const double* tgt_p99,
                              cudaStream_t st);
+int host_table_hexp(const float* W, const float* i0, float lambda);
 int launch_recon(Context* c, const Geometry& g, const Model* m, const float* Wt,
                  const float* i0t, cudaStream_t st);
 int launch_density(Context* c, const Geometry& g, const Model* m, float* H, int64_t stride,

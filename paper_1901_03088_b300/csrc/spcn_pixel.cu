@@ -4,7 +4,7 @@
 // 16-byte loads per thread) from a persistent grid sized to the SM count, look
 // the optical densities up in a replicated shared-memory table (Eq. 1, already
 // projected on the basis and shifted by lambda), and solve the Eq. 2 H-step in
-// closed form (solve_pixel).  Nothing here is a dense contraction, so no
+// closed form (solve_pair / solve_one).  Nothing here is a dense contraction, so no
 // tensor-core path is used: the passes are bound by HBM bandwidth and
 // instruction issue.
 #include <math.h>
@@ -22,43 +22,78 @@ struct ModelIn {
   float W[6];
   float i0[3];
   float lambda;
+  int hexp;          // power-of-two scale of the table; kHexpAuto: derive on the device
 };
 
+// Smallest e with 2^e >= 2 * (largest |d_j| any pixel can reach), so that
+// every table sum s*d_j stays within [-1/2, 1/2].  |d_j| <= |v|/|w_j| +
+// lambda/G_jj with |v_c| <= max(log i0_c, log(255/i0_c)).
+__host__ __device__ inline int table_hexp(const float* W, const float* i0, float lambda) {
+  double vv = 0.0;
+  for (int c = 0; c < 3; ++c) {
+    const double a = log((double)i0[c]), b = log(255.0 / (double)i0[c]);
+    const double m = a > b ? a : b;
+    vv += m * m;
+  }
+  const double vn = sqrt(vv);
+  double bound = 0.0;
+  for (int j = 0; j < 2; ++j) {
+    double g = 0.0;
+    for (int c = 0; c < 3; ++c) g += (double)W[3 * j + c] * W[3 * j + c];
+    if (g > 0.0) {
+      const double bj = vn / sqrt(g) + (double)lambda / g;
+      bound = bj > bound ? bj : bound;
+    }
+  }
+  if (!(bound > 0.0)) bound = 1.0;
+  int e = 0;
+  frexp(bound, &e);       // bound < 2^e
+  return e + 1;
+}
+
 // One thread per (channel, intensity): v = log(i0_c / max(i,1)) in FP64, the
-// plain table and the basis-projected, lambda-shifted table (rounded once to
-// FP32).  Thread 0 also derives the closed-form H-step coefficients.
+// plain table and the scaled table of the closed-form H-step (rounded once to
+// FP32, never -0).  Thread 0 derives the closed-form coefficients.
 __global__ void k_build_model(Model* m, ModelIn in, const Model* from) {
   float W[6], i0[3];
   const Model* src = from;
   for (int i = 0; i < 6; ++i) W[i] = src ? src->W[i] : in.W[i];
   for (int i = 0; i < 3; ++i) i0[i] = src ? src->i0[i] : in.i0[i];
+  double g11 = 0, g22 = 0, g12 = 0;
+  for (int c = 0; c < 3; ++c) {
+    g11 += (double)W[c] * W[c];
+    g22 += (double)W[3 + c] * W[3 + c];
+    g12 += (double)W[c] * W[3 + c];
+  }
+  const double det = g11 * g22 - g12 * g12;
+  const bool ok = det > 1e-12 && g11 > 0.0 && g22 > 0.0;
+  const int hexp = in.hexp == kHexpAuto ? table_hexp(W, i0, in.lambda) : in.hexp;
+  const double s = ldexp(1.0, -hexp);
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e < kLutEntries) {
     const int c = e >> 8, i = e & 255;
     const double v = log((double)i0[c] / (double)(i > 0 ? i : 1));
-    double f0 = (double)W[c] * v, f1 = (double)W[3 + c] * v;
-    if (c == 0) { f0 -= (double)in.lambda; f1 -= (double)in.lambda; }
+    const double lam = c == 0 ? (double)in.lambda : 0.0;
+    float p0 = 0.f, p1 = 0.f;
+    if (ok) {
+      p0 = (float)(s * ((double)W[c] * v - lam) / g11);
+      p1 = (float)(s * ((double)W[3 + c] * v - lam) / g22);
+    }
     m->od[e] = (float)v;
-    m->proj[e] = make_float2((float)f0, (float)f1);
+    m->proj[e] = make_float2(p0 + 0.f, p1 + 0.f);   // + 0 turns -0 into +0
   }
   if (e == 0) {
-    double g11 = 0, g22 = 0, g12 = 0;
-    for (int c = 0; c < 3; ++c) {
-      g11 += (double)W[c] * W[c];
-      g22 += (double)W[3 + c] * W[3 + c];
-      g12 += (double)W[c] * W[3 + c];
-    }
-    const double det = g11 * g22 - g12 * g12;
     Lasso L;
-    if (det > 1e-12) {
-      L.a11 = (float)(g22 / det);
-      L.a22 = (float)(g11 / det);
-      L.a12 = L.a21 = (float)(-g12 / det);
-      L.u1 = (float)(1.0 / g11);
-      L.u2 = (float)(1.0 / g22);
+    L.hexp = hexp;
+    L.hscale = (float)ldexp(1.0, hexp);
+    L.pad = 0;
+    if (ok) {
+      L.nrho1 = (float)(-g12 / g11);
+      L.nrho2 = (float)(-g12 / g22);
+      L.kappa = (float)(g11 * g22 / det);
       m->status = SPCN_OK;
     } else {
-      L.a11 = L.a22 = L.a12 = L.a21 = L.u1 = L.u2 = 0.f;
+      L.nrho1 = L.nrho2 = L.kappa = 0.f;
       m->status = SPCN_ERR_DEGENERATE_BASIS;
     }
     m->lasso = L;
@@ -69,12 +104,17 @@ __global__ void k_build_model(Model* m, ModelIn in, const Model* from) {
   }
 }
 
+int host_table_hexp(const float* W, const float* i0, float lambda) {
+  return table_hexp(W, i0, lambda);
+}
+
 int launch_build_model(Context* c, Model* m, const float* W, const float* i0, float lambda,
                        const Model* from_device, cudaStream_t st) {
   ModelIn in;
   for (int i = 0; i < 6; ++i) in.W[i] = W ? W[i] : 0.f;
-  for (int i = 0; i < 3; ++i) in.i0[i] = i0 ? i0[i] : 0.f;
+  for (int i = 0; i < 3; ++i) in.i0[i] = i0 ? i0[i] : 1.f;
   in.lambda = lambda;
+  in.hexp = (W && i0 && !from_device) ? table_hexp(W, i0, lambda) : kHexpAuto;
   k_build_model<<<3, 256, 0, st>>>(m, in, from_device);
   SPCN_LAUNCH_CHECK(c);
   return SPCN_OK;
@@ -155,6 +195,38 @@ __device__ __forceinline__ void store_chunk(const Geometry& g, const ChunkPos& p
   }
 }
 
+// Table offsets of the three channels of pixel k of a chunk.
+__device__ __forceinline__ void pixel_addr(const unsigned (&w)[12], int k, unsigned lr,
+                                           unsigned& aR, unsigned& aG, unsigned& aB) {
+  const int o = 3 * k;
+  aR = lut_addr(w[o >> 2], lr, o & 3);
+  aG = lut_addr(w[(o + 1) >> 2], lr, (o + 1) & 3);
+  aB = lut_addr(w[(o + 2) >> 2], lr, (o + 2) & 3);
+}
+
+// Persistent grid-stride loop over chunks with a one-chunk register prefetch
+// (two buffers, so no copies).  body(w, pos) is called for every chunk.
+template <bool STREAM, class Body>
+__device__ __forceinline__ void for_each_chunk(const Geometry& g, Body&& body) {
+  const u64 stride = (u64)gridDim.x * blockDim.x;
+  const u64 n = g.nchunks;
+  u64 q = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned wa[12], wb[12];
+  ChunkPos pa, pb;
+  if (q < n) { pa = chunk_pos(g, q); load_chunk<STREAM>(g, pa, wa); }
+  while (q < n) {
+    u64 qn = q + stride;
+    if (qn < n) { pb = chunk_pos(g, qn); load_chunk<STREAM>(g, pb, wb); }
+    body(wa, pa);
+    q = qn;
+    if (q >= n) break;
+    qn = q + stride;
+    if (qn < n) { pa = chunk_pos(g, qn); load_chunk<STREAM>(g, pa, wa); }
+    body(wb, pb);
+    q = qn;
+  }
+}
+
 // ------------------------------------------------------------ pass 1
 struct WindowArgs {
   Geometry g;
@@ -163,41 +235,55 @@ struct WindowArgs {
   u64* fine;
   u64* coarse;
   int* err;
-  unsigned thr;        // white threshold
-  unsigned lo0, lo1;   // window start keys
+  unsigned wthr;       // (white threshold + 1) << 8, compared with table offsets
+  unsigned lo0, lo1;   // window start keys (scaled densities)
   unsigned nb0, nb1;   // window widths (0 = no window)
+  float nk0, lk0;      // below-window test: sat(h~ * nk + lk) = [h~ < lo]
+  float nk1, lk1;
   double pct;
   double tgt0, tgt1;   // target percentiles (for the scale factors)
 };
 
+__device__ __noinline__ void window_hit(const WindowArgs& a, unsigned* s_coarse, unsigned r1,
+                                        unsigned r2) {
+  if (r1 < a.nb0) {
+    atomicAdd(a.fine + r1, 1ull);
+    atomicAdd(s_coarse + (r1 >> kWinGroupBits), 1u);
+  }
+  if (r2 < a.nb1) {
+    atomicAdd(a.fine + kWinBins + r2, 1ull);
+    atomicAdd(s_coarse + kWinGroups + (r2 >> kWinGroupBits), 1u);
+  }
+}
+
 template <bool FULL>
-__device__ __forceinline__ void window_chunk(const unsigned (&w)[12], int n, const float2* lut,
-                                             const Lasso& L, const WindowArgs& a,
-                                             unsigned* s_coarse, unsigned& c_nw,
-                                             unsigned& c_b0, unsigned& c_b1) {
+__device__ __forceinline__ void window_chunk(const unsigned (&w)[12], int n, const char* lut,
+                                             unsigned lr, f2 NR1, f2 NR2, float kappa,
+                                             const WindowArgs& a, unsigned* s_coarse, f2& c_nw,
+                                             f2& c_b0, f2& c_b1) {
 #pragma unroll
-  for (int k = 0; k < kChunk; ++k) {
-    if (FULL || k < n) {
-      const unsigned r = byte_at(w, 3 * k), g = byte_at(w, 3 * k + 1), b = byte_at(w, 3 * k + 2);
-      float h1, h2;
-      solve_pixel(lut, r, g, b, L, h1, h2);
-      const bool nw = min(r, min(g, b)) <= a.thr;
-      const unsigned k1 = nw ? __float_as_uint(h1) : 0xFFFFFFFFu;
-      const unsigned k2 = nw ? __float_as_uint(h2) : 0xFFFFFFFFu;
-      c_nw += nw ? 1u : 0u;
-      c_b0 += (k1 < a.lo0) ? 1u : 0u;
-      c_b1 += (k2 < a.lo1) ? 1u : 0u;
-      const unsigned rel1 = k1 - a.lo0, rel2 = k2 - a.lo1;
-      if (rel1 < a.nb0 || rel2 < a.nb1) {
-        if (rel1 < a.nb0) {
-          atomicAdd(a.fine + rel1, 1ull);
-          atomicAdd(s_coarse + (rel1 >> kWinGroupBits), 1u);
-        }
-        if (rel2 < a.nb1) {
-          atomicAdd(a.fine + kWinBins + rel2, 1ull);
-          atomicAdd(s_coarse + kWinGroups + (rel2 >> kWinGroupBits), 1u);
-        }
-      }
+  for (int p = 0; p < kChunk / 2; ++p) {
+    const int kA = 2 * p, kB = 2 * p + 1;
+    unsigned aRA, aGA, aBA, aRB, aGB, aBB;
+    pixel_addr(w, kA, lr, aRA, aGA, aBA);
+    pixel_addr(w, kB, lr, aRB, aGB, aBB);
+    f2 H1, H2;
+    solve_pair(lut, aRA, aGA, aBA, aRB, aGB, aBB, NR1, NR2, kappa, H1, H2);
+    bool nwA = aRA < a.wthr || aGA < a.wthr || aBA < a.wthr;
+    bool nwB = aRB < a.wthr || aGB < a.wthr || aBB < a.wthr;
+    if (!FULL) { nwA = nwA && kA < n; nwB = nwB && kB < n; }
+    const f2 NW = pk(nwA ? 1.f : 0.f, nwB ? 1.f : 0.f);
+    c_nw = add2(c_nw, NW);
+    const float h1A = lo_of(H1), h1B = hi_of(H1), h2A = lo_of(H2), h2B = hi_of(H2);
+    c_b0 = fma2(pk(fma_sat(h1A, a.nk0, a.lk0), fma_sat(h1B, a.nk0, a.lk0)), NW, c_b0);
+    c_b1 = fma2(pk(fma_sat(h2A, a.nk1, a.lk1), fma_sat(h2B, a.nk1, a.lk1)), NW, c_b1);
+    const unsigned r1A = __float_as_uint(h1A) - a.lo0, r2A = __float_as_uint(h2A) - a.lo1;
+    const unsigned r1B = __float_as_uint(h1B) - a.lo0, r2B = __float_as_uint(h2B) - a.lo1;
+    const bool hitA = nwA && (r1A < a.nb0 || r2A < a.nb1);
+    const bool hitB = nwB && (r1B < a.nb0 || r2B < a.nb1);
+    if (hitA || hitB) {
+      if (hitA) window_hit(a, s_coarse, r1A, r2A);
+      if (hitB) window_hit(a, s_coarse, r1B, r2B);
     }
   }
 }
@@ -254,32 +340,34 @@ __device__ void window_select(const WindowArgs& a) {
   if (threadIdx.x == 0) {
     int all = 1;
     for (int t = 0; t < kTracks; ++t) { s->resolved[t] = s_res[t]; all &= s_res[t]; }
-    if (all) finish_percentiles(s, a.tgt0, a.tgt1);
+    if (all) finish_percentiles(s, a.tgt0, a.tgt1, a.m->lasso.hscale);
     __threadfence();
     s->all_resolved = all;
   }
 }
 
-__global__ void __launch_bounds__(kPassThreads) k_pass_window(WindowArgs a) {
-  extern __shared__ float2 s_dyn[];
-  unsigned* s_coarse = reinterpret_cast<unsigned*>(s_dyn + kLutEntries * kLutRep);
+__global__ void __launch_bounds__(kPassThreads, 1) k_pass_window(WindowArgs a) {
+  extern __shared__ __align__(16) char s_dyn[];
+  unsigned* s_coarse = reinterpret_cast<unsigned*>(s_dyn + kLutSmemBytes);
   __shared__ u64 s_tmp[33];
   __shared__ unsigned s_ticket;
   for (int i = threadIdx.x; i < 2 * kWinGroups; i += blockDim.x) s_coarse[i] = 0u;
-  const float2* lut = load_lut(a.m, s_dyn);
+  load_lut(a.m, s_dyn);
+  const char* lut = s_dyn;
+  const unsigned lr = lane_reg();
   const Lasso L = a.m->lasso;
-  unsigned c_nw = 0, c_b0 = 0, c_b1 = 0;
-  const u64 stride = (u64)gridDim.x * blockDim.x;
-  for (u64 q = (u64)blockIdx.x * blockDim.x + threadIdx.x; q < a.g.nchunks; q += stride) {
-    const ChunkPos p = chunk_pos(a.g, q);
-    unsigned w[12];
-    load_chunk<false>(a.g, p, w);
-    if (p.n == kChunk) window_chunk<true>(w, kChunk, lut, L, a, s_coarse, c_nw, c_b0, c_b1);
-    else window_chunk<false>(w, p.n, lut, L, a, s_coarse, c_nw, c_b0, c_b1);
-  }
-  const u64 t_nw = block_sum(c_nw, s_tmp);
-  const u64 t_b0 = block_sum(c_b0, s_tmp);
-  const u64 t_b1 = block_sum(c_b1, s_tmp);
+  const f2 NR1 = pk(L.nrho1, L.nrho1), NR2 = pk(L.nrho2, L.nrho2);
+  f2 c_nw = pk(0.f, 0.f), c_b0 = pk(0.f, 0.f), c_b1 = pk(0.f, 0.f);
+  for_each_chunk<false>(a.g, [&](const unsigned (&w)[12], const ChunkPos& p) {
+    if (p.n == kChunk)
+      window_chunk<true>(w, kChunk, lut, lr, NR1, NR2, L.kappa, a, s_coarse, c_nw, c_b0, c_b1);
+    else
+      window_chunk<false>(w, p.n, lut, lr, NR1, NR2, L.kappa, a, s_coarse, c_nw, c_b0, c_b1);
+  });
+  // per-thread counts are exact in FP32 (fewer than 2^24 pixels per thread)
+  const u64 t_nw = block_sum((u64)lo_of(c_nw) + (u64)hi_of(c_nw), s_tmp);
+  const u64 t_b0 = block_sum((u64)lo_of(c_b0) + (u64)hi_of(c_b0), s_tmp);
+  const u64 t_b1 = block_sum((u64)lo_of(c_b1) + (u64)hi_of(c_b1), s_tmp);
   if (threadIdx.x == 0) {
     if (t_nw) atomicAdd(&a.sel->n_nw, t_nw);
     if (t_b0) atomicAdd(&a.sel->below[0], t_b0);
@@ -304,6 +392,7 @@ struct ImageSource {
   unsigned thr;
   template <class F>
   __device__ __forceinline__ void for_each(F&& f) const {
+    const unsigned lr = lane_reg();
     const u64 stride = (u64)gridDim.x * blockDim.x;
     for (u64 q = (u64)blockIdx.x * blockDim.x + threadIdx.x; q < g.nchunks; q += stride) {
       const ChunkPos p = chunk_pos(g, q);
@@ -311,7 +400,9 @@ struct ImageSource {
       load_chunk<false>(g, p, w);
       for (int k = 0; k < p.n; ++k) {
         const unsigned r = byte_at(w, 3 * k), gg = byte_at(w, 3 * k + 1), b = byte_at(w, 3 * k + 2);
-        f(r, gg, b, min(r, min(gg, b)) <= thr);
+        unsigned aR, aG, aB;
+        pixel_addr(w, k, lr, aR, aG, aB);
+        f(aR, aG, aB, min(r, min(gg, b)) <= thr);
       }
     }
   }
@@ -322,22 +413,23 @@ struct ListSource {
   u64 n;
   template <class F>
   __device__ __forceinline__ void for_each(F&& f) const {
+    const unsigned lr = lane_reg();
     const u64 stride = (u64)gridDim.x * blockDim.x;
     for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
       const uint32_t v = __ldg(items + i);
-      f(v & 0xFFu, (v >> 8) & 0xFFu, (v >> 16) & 0xFFu, true);
+      f(lut_addr(v, lr, 0), lut_addr(v, lr, 1), lut_addr(v, lr, 2), true);
     }
   }
 };
 
-// Exact radix select (11/11/10-bit digits of the FP32 key) of the ranks in
-// s->rank[] whose track is not yet resolved, over every non-white pixel of
-// `src`.  All blocks of a cooperative grid call it; it uses four grid
-// barriers (counter `bar`, zeroed before the launch).  Block 0 writes the
+// Exact radix select (11/11/10-bit digits of the FP32 key of the scaled
+// densities) of the ranks rank[] whose track is active, over every non-white
+// pixel of `src`.  All blocks of a cooperative grid call it; it uses four
+// grid barriers (counter `bar`, zeroed before the launch).  Block 0 writes the
 // keys, the percentiles and the scale factors.  Returns false if a wait gave
 // up (the error is recorded).
 template <class Src>
-__device__ bool radix_select(const Src& src, const float2* lut, const Lasso& L, SelectState* s,
+__device__ bool radix_select(const Src& src, const char* lut, const Lasso& L, SelectState* s,
                              const u64 (&rank)[kTracks], const int (&active)[kTracks],
                              u64* ghist, unsigned* s_hist, unsigned* bar, int* err,
                              long long timeout_ns, double tgt0, double tgt1) {
@@ -369,10 +461,10 @@ __device__ bool radix_select(const Src& src, const float2* lut, const Lasso& L, 
     int act[kTracks];
 #pragma unroll
     for (int t = 0; t < kTracks; ++t) { pre[t] = s_prefix[t]; act[t] = s_act[t]; }
-    src.for_each([&](unsigned r, unsigned g, unsigned b, bool nw) {
+    src.for_each([&](unsigned aR, unsigned aG, unsigned aB, bool nw) {
       if (!nw) return;
       float h1, h2;
-      solve_pixel(lut, r, g, b, L, h1, h2);
+      solve_one(lut, aR, aG, aB, L, h1, h2);
       const unsigned key[2] = {__float_as_uint(h1), __float_as_uint(h2)};
 #pragma unroll
       for (int t = 0; t < kTracks; ++t) {
@@ -405,7 +497,7 @@ __device__ bool radix_select(const Src& src, const float2* lut, const Lasso& L, 
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     for (int t = 0; t < kTracks; ++t)
       if (s_act[t]) { s->key[t] = s_prefix[t]; s->resolved[t] = 1; }
-    finish_percentiles(s, tgt0, tgt1);
+    finish_percentiles(s, tgt0, tgt1, L.hscale);
     __threadfence();
     s->all_resolved = 1;
   }
@@ -422,11 +514,11 @@ struct SelectImageArgs {
   double tgt0, tgt1;
 };
 
-__global__ void __launch_bounds__(kPassThreads) k_select_image(SelectImageArgs a) {
+__global__ void __launch_bounds__(kPassThreads, 1) k_select_image(SelectImageArgs a) {
   if (*(volatile int*)&a.sel->all_resolved) return;   // uniform: every block returns
-  extern __shared__ float2 s_dyn[];
-  unsigned* s_hist = reinterpret_cast<unsigned*>(s_dyn + kLutEntries * kLutRep);
-  const float2* lut = load_lut(a.m, s_dyn);
+  extern __shared__ __align__(16) char s_dyn[];
+  unsigned* s_hist = reinterpret_cast<unsigned*>(s_dyn + kLutSmemBytes);
+  load_lut(a.m, s_dyn);
   const Lasso L = a.m->lasso;
   u64 rank[kTracks];
   int active[kTracks];
@@ -434,7 +526,7 @@ __global__ void __launch_bounds__(kPassThreads) k_select_image(SelectImageArgs a
     rank[t] = __ldcg(&a.sel->rank[t]);
     active[t] = !__ldcg(&a.sel->resolved[t]);
   }
-  radix_select(a.src, lut, L, a.sel, rank, active, a.ghist, s_hist, &a.sel->barrier, a.err,
+  radix_select(a.src, s_dyn, L, a.sel, rank, active, a.ghist, s_hist, &a.sel->barrier, a.err,
                a.timeout_ns, a.tgt0, a.tgt1);
 }
 
@@ -451,9 +543,9 @@ struct SelectListArgs {
 
 // Percentile of the densities of a packed list of non-white pixels (the basis
 // sample, §3.1 item 2), radix select from scratch.
-__global__ void __launch_bounds__(kPassThreads) k_select_list(SelectListArgs a) {
-  extern __shared__ float2 s_dyn[];
-  unsigned* s_hist = reinterpret_cast<unsigned*>(s_dyn + kLutEntries * kLutRep);
+__global__ void __launch_bounds__(kPassThreads, 1) k_select_list(SelectListArgs a) {
+  extern __shared__ __align__(16) char s_dyn[];
+  unsigned* s_hist = reinterpret_cast<unsigned*>(s_dyn + kLutSmemBytes);
   const u64 n = __ldcg(a.n_dev);
   if (n == 0 || a.m->status != SPCN_OK) return;   // uniform: every block returns
   u64 rank[kTracks];
@@ -468,10 +560,10 @@ __global__ void __launch_bounds__(kPassThreads) k_select_list(SelectListArgs a) 
     a.sel->t = t;
     for (int i = 0; i < kTracks; ++i) a.sel->rank[i] = rank[i];
   }
-  const float2* lut = load_lut(a.m, s_dyn);
+  load_lut(a.m, s_dyn);
   const Lasso L = a.m->lasso;
   ListSource src{a.items, n};
-  radix_select(src, lut, L, a.sel, rank, active, a.ghist, s_hist, &a.sel->barrier, a.err,
+  radix_select(src, s_dyn, L, a.sel, rank, active, a.ghist, s_hist, &a.sel->barrier, a.err,
                a.timeout_ns, 1.0, 1.0);
 }
 
@@ -490,62 +582,71 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
-// Insert byte 0 of v at byte position p (0..3) of word w.
-__device__ __forceinline__ unsigned put_byte(unsigned w, unsigned v, int p) {
-  const unsigned sel = p == 0 ? 0x3214u : (p == 1 ? 0x3240u : (p == 2 ? 0x3410u : 0x4210u));
-  return __byte_perm(w, v, sel);
+// Four rounded values (byte 0 of each word) packed little-endian.
+__device__ __forceinline__ unsigned pack4(unsigned a, unsigned b, unsigned c, unsigned d) {
+  return __byte_perm(__byte_perm(a, b, 0x0040u), __byte_perm(c, d, 0x0040u), 0x5410u);
 }
 
+struct ReconConst {
+  f2 M1[3], M2[3], L2[3];   // exponent: e_c = L2_c + M1_c h~1 + M2_c h~2 (both lanes equal)
+};
+
 template <bool FULL>
-__device__ __forceinline__ void recon_chunk(const unsigned (&w)[12], int n, const float2* lut,
-                                            const Lasso& L, const float (&M)[6],
-                                            const float (&l2)[3], unsigned (&o)[12]) {
+__device__ __forceinline__ void recon_chunk(const unsigned (&w)[12], int n, const char* lut,
+                                            unsigned lr, f2 NR1, f2 NR2, float kappa,
+                                            const ReconConst& K, unsigned (&o)[12]) {
+  unsigned y[48];
 #pragma unroll
-  for (int k = 0; k < kChunk; ++k) {
-    if (FULL || k < n) {
-      const unsigned r = byte_at(w, 3 * k), g = byte_at(w, 3 * k + 1), b = byte_at(w, 3 * k + 2);
-      float h1, h2;
-      solve_pixel(lut, r, g, b, L, h1, h2);
+  for (int p = 0; p < kChunk / 2; ++p) {
+    const int kA = 2 * p, kB = 2 * p + 1;
+    unsigned aRA, aGA, aBA, aRB, aGB, aBB;
+    pixel_addr(w, kA, lr, aRA, aGA, aBA);
+    pixel_addr(w, kB, lr, aRB, aGB, aBB);
+    f2 H1, H2;
+    solve_pair(lut, aRA, aGA, aBA, aRB, aGB, aBB, NR1, NR2, kappa, H1, H2);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        // Eq. 3-4: i' = i0_t 2^(-log2e * sum_j W_t[c,j] s_j h_j); M holds -log2e W_t s
-        const float e = fmaf(M[c], h1, fmaf(M[3 + c], h2, l2[c]));
-        const float x = ex2_approx(e);
-        // round half to even: adding 1.5*2^23 leaves round(x) in the low bits
-        const unsigned v = __float_as_uint(__fadd_rn(x, 12582912.0f));
-        const int i = 3 * k + c;
-        o[i >> 2] = put_byte(o[i >> 2], v, i & 3);
-      }
+    for (int c = 0; c < 3; ++c) {
+      // Eq. 3-4: i' = i0_t 2^(-log2e sum_j W_t[c,j] s_j h_j)
+      const f2 E = fma2(K.M1[c], H1, fma2(K.M2[c], H2, K.L2[c]));
+      // round half to even: adding 1.5*2^23 leaves round(x) in the low bits
+      const f2 X = add2(pk(ex2_approx(lo_of(E)), ex2_approx(hi_of(E))), pk(12582912.0f, 12582912.0f));
+      y[3 * kA + c] = __float_as_uint(lo_of(X));
+      y[3 * kB + c] = __float_as_uint(hi_of(X));
     }
+    // pack every output word whose four bytes are now known
+#pragma unroll
+    for (int i = 0; i < 12; ++i)
+      if (4 * i + 3 <= 6 * p + 5 && 4 * i + 3 > 6 * p - 1)
+        o[i] = pack4(y[4 * i], y[4 * i + 1], y[4 * i + 2], y[4 * i + 3]);
   }
 }
 
-__global__ void __launch_bounds__(kPassThreads) k_pass_recon(ReconArgs a) {
-  extern __shared__ float2 s_dyn[];
+__global__ void __launch_bounds__(kPassThreads, 1) k_pass_recon(ReconArgs a) {
+  extern __shared__ __align__(16) char s_dyn[];
   __shared__ float s_M[6];
+  const Lasso L = a.m->lasso;
   if (threadIdx.x < 6) {
     const int c = threadIdx.x % 3, j = threadIdx.x / 3;
     const double sc = a.sel->scale[j];
-    s_M[threadIdx.x] = (float)(-(double)a.Wt[3 * j + c] * sc * 1.4426950408889634);
+    s_M[threadIdx.x] = (float)(-(double)a.Wt[3 * j + c] * sc * (double)L.hscale * 1.4426950408889634);
   }
-  const float2* lut = load_lut(a.m, s_dyn);
-  const Lasso L = a.m->lasso;
-  float M[6], l2[3];
+  load_lut(a.m, s_dyn);
+  const char* lut = s_dyn;
+  const unsigned lr = lane_reg();
+  ReconConst K;
 #pragma unroll
-  for (int i = 0; i < 6; ++i) M[i] = s_M[i];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) l2[i] = a.l2i0[i];
-  const u64 stride = (u64)gridDim.x * blockDim.x;
-  for (u64 q = (u64)blockIdx.x * blockDim.x + threadIdx.x; q < a.g.nchunks; q += stride) {
-    const ChunkPos p = chunk_pos(a.g, q);
-    unsigned w[12], o[12];
-#pragma unroll
-    for (int i = 0; i < 12; ++i) o[i] = 0u;
-    load_chunk<true>(a.g, p, w);
-    if (p.n == kChunk) recon_chunk<true>(w, kChunk, lut, L, M, l2, o);
-    else recon_chunk<false>(w, p.n, lut, L, M, l2, o);
+  for (int c = 0; c < 3; ++c) {
+    K.M1[c] = pk(s_M[c], s_M[c]);
+    K.M2[c] = pk(s_M[3 + c], s_M[3 + c]);
+    K.L2[c] = pk(a.l2i0[c], a.l2i0[c]);
+  }
+  const f2 NR1 = pk(L.nrho1, L.nrho1), NR2 = pk(L.nrho2, L.nrho2);
+  for_each_chunk<true>(a.g, [&](const unsigned (&w)[12], const ChunkPos& p) {
+    unsigned o[12];
+    if (p.n == kChunk) recon_chunk<true>(w, kChunk, lut, lr, NR1, NR2, L.kappa, K, o);
+    else recon_chunk<false>(w, p.n, lut, lr, NR1, NR2, L.kappa, K, o);
     store_chunk(a.g, p, o);
-  }
+  });
 }
 
 // ------------------------------------------------------------ densities
@@ -556,38 +657,45 @@ struct DensityArgs {
   int64_t stride;   // elements between the two planes
 };
 
-__global__ void __launch_bounds__(kPassThreads) k_pass_density(DensityArgs a) {
-  extern __shared__ float2 s_dyn[];
-  const float2* lut = load_lut(a.m, s_dyn);
+__global__ void __launch_bounds__(kPassThreads, 1) k_pass_density(DensityArgs a) {
+  extern __shared__ __align__(16) char s_dyn[];
+  load_lut(a.m, s_dyn);
+  const char* lut = s_dyn;
+  const unsigned lr = lane_reg();
   const Lasso L = a.m->lasso;
-  const u64 stride = (u64)gridDim.x * blockDim.x;
+  const f2 NR1 = pk(L.nrho1, L.nrho1), NR2 = pk(L.nrho2, L.nrho2);
+  const f2 HS = pk(L.hscale, L.hscale);
   const bool vec_h = ((reinterpret_cast<uintptr_t>(a.H) & 15u) == 0) && ((a.stride & 3) == 0);
-  for (u64 q = (u64)blockIdx.x * blockDim.x + threadIdx.x; q < a.g.nchunks; q += stride) {
-    const ChunkPos p = chunk_pos(a.g, q);
-    unsigned w[12];
-    load_chunk<true>(a.g, p, w);
-    float h[2][kChunk];
-#pragma unroll
-    for (int k = 0; k < kChunk; ++k) {
-      const unsigned r = byte_at(w, 3 * k), g = byte_at(w, 3 * k + 1), b = byte_at(w, 3 * k + 2);
-      solve_pixel(lut, r, g, b, L, h[0][k], h[1][k]);
-    }
+  for_each_chunk<true>(a.g, [&](const unsigned (&w)[12], const ChunkPos& p) {
     float* d0 = a.H + p.px;
     float* d1 = a.H + a.stride + p.px;
-    if (p.n == kChunk && vec_h && (p.px & 3) == 0) {
+    const bool vec = p.n == kChunk && vec_h && (p.px & 3) == 0;
 #pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        __stcs(reinterpret_cast<float4*>(d0) + v,
-               make_float4(h[0][4 * v], h[0][4 * v + 1], h[0][4 * v + 2], h[0][4 * v + 3]));
-        __stcs(reinterpret_cast<float4*>(d1) + v,
-               make_float4(h[1][4 * v], h[1][4 * v + 1], h[1][4 * v + 2], h[1][4 * v + 3]));
+    for (int v = 0; v < kChunk / 4; ++v) {
+      f2 H1[2], H2[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int k = 4 * v + 2 * q;
+        unsigned aRA, aGA, aBA, aRB, aGB, aBB;
+        pixel_addr(w, k, lr, aRA, aGA, aBA);
+        pixel_addr(w, k + 1, lr, aRB, aGB, aBB);
+        solve_pair(lut, aRA, aGA, aBA, aRB, aGB, aBB, NR1, NR2, L.kappa, H1[q], H2[q]);
+        H1[q] = mul2(H1[q], HS);     // exact: the scale is a power of two
+        H2[q] = mul2(H2[q], HS);
       }
-    } else {
+      const float4 h1 = make_float4(lo_of(H1[0]), hi_of(H1[0]), lo_of(H1[1]), hi_of(H1[1]));
+      const float4 h2 = make_float4(lo_of(H2[0]), hi_of(H2[0]), lo_of(H2[1]), hi_of(H2[1]));
+      if (vec) {
+        __stcs(reinterpret_cast<float4*>(d0) + v, h1);
+        __stcs(reinterpret_cast<float4*>(d1) + v, h2);
+      } else {
+        const float a1[4] = {h1.x, h1.y, h1.z, h1.w}, a2[4] = {h2.x, h2.y, h2.z, h2.w};
 #pragma unroll
-      for (int k = 0; k < kChunk; ++k)
-        if (k < p.n) { d0[k] = h[0][k]; d1[k] = h[1][k]; }
+        for (int k = 0; k < 4; ++k)
+          if (4 * v + k < p.n) { d0[4 * v + k] = a1[k]; d1[4 * v + k] = a2[k]; }
+      }
     }
-  }
+  });
 }
 
 // ------------------------------------------------------------ failure-detection hook
@@ -604,9 +712,9 @@ int configure_pixel_kernels(Context* c) {
   SPCN_CUDA_TRY(cudaFuncSetAttribute(k_pass_window, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)kWindowSmem));
   SPCN_CUDA_TRY(cudaFuncSetAttribute(k_pass_recon, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kLutSmem));
+                                     (int)kLutSmemBytes));
   SPCN_CUDA_TRY(cudaFuncSetAttribute(k_pass_density, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kLutSmem));
+                                     (int)kLutSmemBytes));
   SPCN_CUDA_TRY(cudaFuncSetAttribute(k_select_image, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)kRadixSmem));
   SPCN_CUDA_TRY(cudaFuncSetAttribute(k_select_list, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -614,9 +722,9 @@ int configure_pixel_kernels(Context* c) {
   SPCN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->occ_window, k_pass_window,
                                                               kPassThreads, kWindowSmem));
   SPCN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->occ_recon, k_pass_recon,
-                                                              kPassThreads, kLutSmem));
+                                                              kPassThreads, kLutSmemBytes));
   SPCN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->occ_density, k_pass_density,
-                                                              kPassThreads, kLutSmem));
+                                                              kPassThreads, kLutSmemBytes));
   SPCN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->occ_select, k_select_image,
                                                               kPassThreads, kRadixSmem));
   SPCN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->occ_radix_list, k_select_list,
@@ -629,9 +737,17 @@ int configure_pixel_kernels(Context* c) {
   return SPCN_OK;
 }
 
-// Window [lo, lo+nb) of FP32 keys around a percentile hint h > 0.
-static void window_of(double hint, unsigned* lo, unsigned* nb) {
-  if (!(hint > 0.0) || !std::isfinite(hint)) { *lo = 0u; *nb = 0u; return; }
+// Window [lo, lo+nb) of FP32 keys around a percentile hint h > 0 (in the
+// units of the scaled densities), and the constants of the exact
+// below-window test sat(h~ * nk + lk) = [h~ < lo]: with lo in [2^e, 2^e+1),
+// any h~ < lo is at least 2^(e-24) below it, so nk = -2^(24-e) makes the
+// difference >= 1 before saturation.
+static void window_of(double hint, unsigned* lo, unsigned* nb, float* nk, float* lk) {
+  *nk = -1.f;
+  *lk = 0.f;
+  if (!(hint > 0.0) || !std::isfinite(hint) || hint * (1.0 - kWindowDelta) < 0x1p-100) {
+    *lo = 0u; *nb = 0u; return;
+  }
   float flo = (float)(hint * (1.0 - kWindowDelta));
   float fhi = (float)(hint * (1.0 + kWindowDelta));
   unsigned klo, khi, kmid;
@@ -648,11 +764,18 @@ static void window_of(double hint, unsigned* lo, unsigned* nb) {
   }
   *lo = klo;
   *nb = (unsigned)width;
+  float flo_key;
+  memcpy(&flo_key, &klo, 4);
+  int ex = 0;
+  frexpf(flo_key, &ex);            // flo_key in [2^(ex-1), 2^ex)
+  const int K = 24 - (ex - 1);
+  *nk = -ldexpf(1.f, K);
+  *lk = ldexpf(flo_key, K);
 }
 
 // Pass 1 + select (+ radix fallback when a rank fell outside the window).
 int launch_percentile_passes(Context* c, const Geometry& g, const Model* m, int white_thresh,
-                             double pct, const double* hint, const double* tgt_p99,
+                             double pct, const double* hint, int hexp, const double* tgt_p99,
                              cudaStream_t st) {
   WindowArgs a;
   a.g = g;
@@ -661,9 +784,10 @@ int launch_percentile_passes(Context* c, const Geometry& g, const Model* m, int 
   a.fine = c->fine;
   a.coarse = c->coarse;
   a.err = c->err;
-  a.thr = (unsigned)white_thresh;
-  window_of(hint ? hint[0] : 0.0, &a.lo0, &a.nb0);
-  window_of(hint ? hint[1] : 0.0, &a.lo1, &a.nb1);
+  a.wthr = ((unsigned)white_thresh + 1u) << 8;
+  const double hs = ldexp(1.0, -hexp);
+  window_of(hint ? hint[0] * hs : 0.0, &a.lo0, &a.nb0, &a.nk0, &a.lk0);
+  window_of(hint ? hint[1] * hs : 0.0, &a.lo1, &a.nb1, &a.nk1, &a.lk1);
   a.pct = pct;
   a.tgt0 = tgt_p99 ? tgt_p99[0] : 1.0;
   a.tgt1 = tgt_p99 ? tgt_p99[1] : 1.0;
@@ -726,7 +850,7 @@ int launch_recon(Context* c, const Geometry& g, const Model* m, const float* Wt,
   for (int i = 0; i < 3; ++i) a.l2i0[i] = (float)log2((double)i0t[i]);
   {
     TimedLaunch tl(c, SPCN_KERNEL_PASS2, st);
-    k_pass_recon<<<grid_of(c, c->occ_recon), kPassThreads, kLutSmem, st>>>(a);
+    k_pass_recon<<<grid_of(c, c->occ_recon), kPassThreads, kLutSmemBytes, st>>>(a);
   }
   SPCN_LAUNCH_CHECK(c);
   return SPCN_OK;
@@ -741,7 +865,7 @@ int launch_density(Context* c, const Geometry& g, const Model* m, float* H, int6
   a.stride = stride;
   {
     TimedLaunch tl(c, SPCN_KERNEL_DENSITY, st);
-    k_pass_density<<<grid_of(c, c->occ_density), kPassThreads, kLutSmem, st>>>(a);
+    k_pass_density<<<grid_of(c, c->occ_density), kPassThreads, kLutSmemBytes, st>>>(a);
   }
   SPCN_LAUNCH_CHECK(c);
   return SPCN_OK;

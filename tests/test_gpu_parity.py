@@ -92,6 +92,7 @@ def test_densities_match_oracle(spcn, ctx, shape):
     H_gpu = ctx.stain_densities(to_dev(img), st).cpu().numpy()
     H_ref, margin = oracle_kkt_margin(img, as64(W), as64(i0))
     check_h(H_gpu, H_ref, margin)
+    assert not np.any(np.signbit(H_gpu))          # zeros are +0, keys stay ordered
 
 
 def test_densities_pitched_and_unaligned(spcn, ctx):
