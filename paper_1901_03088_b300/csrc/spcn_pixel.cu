@@ -244,14 +244,21 @@ struct WindowArgs {
   double tgt0, tgt1;   // target percentiles (for the scale factors)
 };
 
-__device__ __noinline__ void window_hit(const WindowArgs& a, unsigned* s_coarse, unsigned r1,
-                                        unsigned r2) {
-  if (r1 < a.nb0) {
-    atomicAdd(a.fine + r1, 1ull);
+// Per-launch constants of pass 1, held in registers by the pixel loop.
+struct WindowConst {
+  u64* fine;
+  unsigned wthr, lo0, lo1, nb0, nb1;
+  float nk0, lk0, nk1, lk1;
+};
+
+__device__ __forceinline__ void window_hit(const WindowConst& C, unsigned* s_coarse, unsigned r1,
+                                           unsigned r2) {
+  if (r1 < C.nb0) {
+    atomicAdd(C.fine + r1, 1ull);
     atomicAdd(s_coarse + (r1 >> kWinGroupBits), 1u);
   }
-  if (r2 < a.nb1) {
-    atomicAdd(a.fine + kWinBins + r2, 1ull);
+  if (r2 < C.nb1) {
+    atomicAdd(C.fine + kWinBins + r2, 1ull);
     atomicAdd(s_coarse + kWinGroups + (r2 >> kWinGroupBits), 1u);
   }
 }
@@ -259,7 +266,7 @@ __device__ __noinline__ void window_hit(const WindowArgs& a, unsigned* s_coarse,
 template <bool FULL>
 __device__ __forceinline__ void window_chunk(const unsigned (&w)[12], int n, const char* lut,
                                              unsigned lr, f2 NR1, f2 NR2, float kappa,
-                                             const WindowArgs& a, unsigned* s_coarse, f2& c_nw,
+                                             const WindowConst& a, unsigned* s_coarse, f2& c_nw,
                                              f2& c_b0, f2& c_b1) {
 #pragma unroll
   for (int p = 0; p < kChunk / 2; ++p) {
@@ -358,11 +365,13 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_window(WindowArgs a) {
   const Lasso L = a.m->lasso;
   const f2 NR1 = pk(L.nrho1, L.nrho1), NR2 = pk(L.nrho2, L.nrho2);
   f2 c_nw = pk(0.f, 0.f), c_b0 = pk(0.f, 0.f), c_b1 = pk(0.f, 0.f);
-  for_each_chunk<false>(a.g, [&](const unsigned (&w)[12], const ChunkPos& p) {
+  const WindowConst C{a.fine, a.wthr, a.lo0, a.lo1, a.nb0, a.nb1, a.nk0, a.lk0, a.nk1, a.lk1};
+  const Geometry g = a.g;
+  for_each_chunk<false>(g, [&](const unsigned (&w)[12], const ChunkPos& p) {
     if (p.n == kChunk)
-      window_chunk<true>(w, kChunk, lut, lr, NR1, NR2, L.kappa, a, s_coarse, c_nw, c_b0, c_b1);
+      window_chunk<true>(w, kChunk, lut, lr, NR1, NR2, L.kappa, C, s_coarse, c_nw, c_b0, c_b1);
     else
-      window_chunk<false>(w, p.n, lut, lr, NR1, NR2, L.kappa, a, s_coarse, c_nw, c_b0, c_b1);
+      window_chunk<false>(w, p.n, lut, lr, NR1, NR2, L.kappa, C, s_coarse, c_nw, c_b0, c_b1);
   });
   // per-thread counts are exact in FP32 (fewer than 2^24 pixels per thread)
   const u64 t_nw = block_sum((u64)lo_of(c_nw) + (u64)hi_of(c_nw), s_tmp);
