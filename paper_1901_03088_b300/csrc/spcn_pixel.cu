@@ -153,7 +153,9 @@ __device__ __forceinline__ unsigned byte_at(const unsigned (&w)[12], int i) {
 }
 
 // Load a chunk into 12 little-endian words; STREAM selects the evict-first
-// policy for data read for the last time.
+// policy for data read for the last time.  Pixels past the end of a row read
+// as white (0xFF bytes): they fall outside every count of pass 1, and their
+// outputs are never stored, so every chunk takes the same unrolled path.
 template <bool STREAM>
 __device__ __forceinline__ void load_chunk(const Geometry& g, const ChunkPos& p,
                                            unsigned (&w)[12]) {
@@ -171,11 +173,12 @@ __device__ __forceinline__ void load_chunk(const Geometry& g, const ChunkPos& p,
     w[8] = c.x; w[9] = c.y; w[10] = c.z; w[11] = c.w;
   } else {
 #pragma unroll
-    for (int i = 0; i < 12; ++i) w[i] = 0u;
+    for (int i = 0; i < 12; ++i) w[i] = 0xFFFFFFFFu;
     const int nb = 3 * p.n;
 #pragma unroll
     for (int i = 0; i < 48; ++i)
-      if (i < nb) w[i >> 2] |= (unsigned)__ldg(s + i) << ((i & 3) * 8);
+      if (i < nb) w[i >> 2] = (w[i >> 2] & ~(0xFFu << ((i & 3) * 8))) |
+                              ((unsigned)__ldg(s + i) << ((i & 3) * 8));
   }
 }
 
@@ -204,13 +207,24 @@ __device__ __forceinline__ void pixel_addr(const unsigned (&w)[12], int k, unsig
   aB = lut_addr(w[(o + 2) >> 2], lr, (o + 2) & 3);
 }
 
-// Persistent grid-stride loop over chunks with a one-chunk register prefetch
-// (two buffers, so no copies).  body(w, pos) is called for every chunk.
-template <bool STREAM, class Body>
+// Persistent grid-stride loop over chunks; body(w, pos) is called for every
+// chunk.  With PREFETCH the next chunk's loads are issued before the current
+// chunk is processed (two register buffers, so no copies); the issue-bound
+// pass 1 runs faster without it, the bandwidth-bound pass 2 with it.
+template <bool STREAM, bool PREFETCH, class Body>
 __device__ __forceinline__ void for_each_chunk(const Geometry& g, Body&& body) {
   const u64 stride = (u64)gridDim.x * blockDim.x;
   const u64 n = g.nchunks;
   u64 q = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (!PREFETCH) {
+    for (; q < n; q += stride) {
+      const ChunkPos p = chunk_pos(g, q);
+      unsigned w[12];
+      load_chunk<STREAM>(g, p, w);
+      body(w, p);
+    }
+    return;
+  }
   unsigned wa[12], wb[12];
   ChunkPos pa, pb;
   if (q < n) { pa = chunk_pos(g, q); load_chunk<STREAM>(g, pa, wa); }
@@ -263,11 +277,37 @@ __device__ __forceinline__ void window_hit(const WindowConst& C, unsigned* s_coa
   }
 }
 
-template <bool FULL>
-__device__ __forceinline__ void window_chunk(const unsigned (&w)[12], int n, const char* lut,
+struct Chunk {
+  unsigned w[12];
+};
+
+// Window histogram updates of the pixels flagged in `hits` (out of line: it
+// runs for a small fraction of chunks, and keeping it out of the unrolled
+// loop keeps that loop free of reconvergence bookkeeping and spills).
+__device__ __noinline__ void window_hits(Chunk c, unsigned hits, unsigned lr, float nrho1,
+                                         float nrho2, float kappa, WindowConst a,
+                                         const char* lut, unsigned* s_coarse) {
+  Lasso L1;
+  L1.nrho1 = nrho1;
+  L1.nrho2 = nrho2;
+  L1.kappa = kappa;
+#pragma unroll
+  for (int k = 0; k < kChunk; ++k) {
+    if (hits & (1u << k)) {
+      unsigned aR, aG, aB;
+      pixel_addr(c.w, k, lr, aR, aG, aB);
+      float h1, h2;
+      solve_one(lut, aR, aG, aB, L1, h1, h2);
+      window_hit(a, s_coarse, __float_as_uint(h1) - a.lo0, __float_as_uint(h2) - a.lo1);
+    }
+  }
+}
+
+__device__ __forceinline__ void window_chunk(const unsigned (&w)[12], const char* lut,
                                              unsigned lr, f2 NR1, f2 NR2, float kappa,
                                              const WindowConst& a, unsigned* s_coarse, f2& c_nw,
                                              f2& c_b0, f2& c_b1) {
+  unsigned hits = 0u;   // pixels of this chunk whose density falls in a window
 #pragma unroll
   for (int p = 0; p < kChunk / 2; ++p) {
     const int kA = 2 * p, kB = 2 * p + 1;
@@ -276,22 +316,23 @@ __device__ __forceinline__ void window_chunk(const unsigned (&w)[12], int n, con
     pixel_addr(w, kB, lr, aRB, aGB, aBB);
     f2 H1, H2;
     solve_pair(lut, aRA, aGA, aBA, aRB, aGB, aBB, NR1, NR2, kappa, H1, H2);
-    bool nwA = aRA < a.wthr || aGA < a.wthr || aBA < a.wthr;
-    bool nwB = aRB < a.wthr || aGB < a.wthr || aBB < a.wthr;
-    if (!FULL) { nwA = nwA && kA < n; nwB = nwB && kB < n; }
+    const bool nwA = aRA < a.wthr || aGA < a.wthr || aBA < a.wthr;
+    const bool nwB = aRB < a.wthr || aGB < a.wthr || aBB < a.wthr;
     const f2 NW = pk(nwA ? 1.f : 0.f, nwB ? 1.f : 0.f);
     c_nw = add2(c_nw, NW);
     const float h1A = lo_of(H1), h1B = hi_of(H1), h2A = lo_of(H2), h2B = hi_of(H2);
     c_b0 = fma2(pk(fma_sat(h1A, a.nk0, a.lk0), fma_sat(h1B, a.nk0, a.lk0)), NW, c_b0);
     c_b1 = fma2(pk(fma_sat(h2A, a.nk1, a.lk1), fma_sat(h2B, a.nk1, a.lk1)), NW, c_b1);
-    const unsigned r1A = __float_as_uint(h1A) - a.lo0, r2A = __float_as_uint(h2A) - a.lo1;
-    const unsigned r1B = __float_as_uint(h1B) - a.lo0, r2B = __float_as_uint(h2B) - a.lo1;
-    const bool hitA = nwA && (r1A < a.nb0 || r2A < a.nb1);
-    const bool hitB = nwB && (r1B < a.nb0 || r2B < a.nb1);
-    if (hitA || hitB) {
-      if (hitA) window_hit(a, s_coarse, r1A, r2A);
-      if (hitB) window_hit(a, s_coarse, r1B, r2B);
-    }
+    const bool hitA = nwA && (__float_as_uint(h1A) - a.lo0 < a.nb0 || __float_as_uint(h2A) - a.lo1 < a.nb1);
+    const bool hitB = nwB && (__float_as_uint(h1B) - a.lo0 < a.nb0 || __float_as_uint(h2B) - a.lo1 < a.nb1);
+    hits |= (hitA ? 1u << kA : 0u) | (hitB ? 1u << kB : 0u);
+  }
+  // Rare: recompute the hit pixels (same arithmetic, same keys) and count them.
+  if (hits) {
+    Chunk c;
+#pragma unroll
+    for (int i = 0; i < 12; ++i) c.w[i] = w[i];
+    window_hits(c, hits, lr, lo_of(NR1), lo_of(NR2), kappa, a, lut, s_coarse);
   }
 }
 
@@ -367,11 +408,8 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_window(WindowArgs a) {
   f2 c_nw = pk(0.f, 0.f), c_b0 = pk(0.f, 0.f), c_b1 = pk(0.f, 0.f);
   const WindowConst C{a.fine, a.wthr, a.lo0, a.lo1, a.nb0, a.nb1, a.nk0, a.lk0, a.nk1, a.lk1};
   const Geometry g = a.g;
-  for_each_chunk<false>(g, [&](const unsigned (&w)[12], const ChunkPos& p) {
-    if (p.n == kChunk)
-      window_chunk<true>(w, kChunk, lut, lr, NR1, NR2, L.kappa, C, s_coarse, c_nw, c_b0, c_b1);
-    else
-      window_chunk<false>(w, p.n, lut, lr, NR1, NR2, L.kappa, C, s_coarse, c_nw, c_b0, c_b1);
+  for_each_chunk<false, false>(g, [&](const unsigned (&w)[12], const ChunkPos&) {
+    window_chunk(w, lut, lr, NR1, NR2, L.kappa, C, s_coarse, c_nw, c_b0, c_b1);
   });
   // per-thread counts are exact in FP32 (fewer than 2^24 pixels per thread)
   const u64 t_nw = block_sum((u64)lo_of(c_nw) + (u64)hi_of(c_nw), s_tmp);
@@ -600,8 +638,7 @@ struct ReconConst {
   f2 M1[3], M2[3], L2[3];   // exponent: e_c = L2_c + M1_c h~1 + M2_c h~2 (both lanes equal)
 };
 
-template <bool FULL>
-__device__ __forceinline__ void recon_chunk(const unsigned (&w)[12], int n, const char* lut,
+__device__ __forceinline__ void recon_chunk(const unsigned (&w)[12], const char* lut,
                                             unsigned lr, f2 NR1, f2 NR2, float kappa,
                                             const ReconConst& K, unsigned (&o)[12]) {
   unsigned y[48];
@@ -650,10 +687,9 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_recon(ReconArgs a) {
     K.L2[c] = pk(a.l2i0[c], a.l2i0[c]);
   }
   const f2 NR1 = pk(L.nrho1, L.nrho1), NR2 = pk(L.nrho2, L.nrho2);
-  for_each_chunk<true>(a.g, [&](const unsigned (&w)[12], const ChunkPos& p) {
+  for_each_chunk<true, true>(a.g, [&](const unsigned (&w)[12], const ChunkPos& p) {
     unsigned o[12];
-    if (p.n == kChunk) recon_chunk<true>(w, kChunk, lut, lr, NR1, NR2, L.kappa, K, o);
-    else recon_chunk<false>(w, p.n, lut, lr, NR1, NR2, L.kappa, K, o);
+    recon_chunk(w, lut, lr, NR1, NR2, L.kappa, K, o);
     store_chunk(a.g, p, o);
   });
 }
@@ -675,7 +711,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_density(DensityArgs a)
   const f2 NR1 = pk(L.nrho1, L.nrho1), NR2 = pk(L.nrho2, L.nrho2);
   const f2 HS = pk(L.hscale, L.hscale);
   const bool vec_h = ((reinterpret_cast<uintptr_t>(a.H) & 15u) == 0) && ((a.stride & 3) == 0);
-  for_each_chunk<true>(a.g, [&](const unsigned (&w)[12], const ChunkPos& p) {
+  for_each_chunk<true, true>(a.g, [&](const unsigned (&w)[12], const ChunkPos& p) {
     float* d0 = a.H + p.px;
     float* d1 = a.H + a.stride + p.px;
     const bool vec = p.n == kChunk && vec_h && (p.px & 3) == 0;
