@@ -254,6 +254,8 @@ struct WindowArgs {
   unsigned nb0, nb1;   // window widths (0 = no window)
   float nk0, lk0;      // below-window test: sat(h~ * nk + lk) = [h~ < lo]
   float nk1, lk1;
+  float nh0, hk0;      // below-window-end test: sat(h~ * nh + hk) = [h~ < lo + nb]
+  float nh1, hk1;
   double pct;
   double tgt0, tgt1;   // target percentiles (for the scale factors)
 };
@@ -262,7 +264,8 @@ struct WindowArgs {
 struct WindowConst {
   u64* fine;
   unsigned wthr, lo0, lo1, nb0, nb1;
-  float nk0, lk0, nk1, lk1;
+  float nk0, lk0, nk1, lk1;   // sat(h~ nk + lk) = [h~ < lo]   (exact, see window_of)
+  float nh0, hk0, nh1, hk1;   // sat(h~ nh + hk) = [h~ < lo + nb]
 };
 
 __device__ __forceinline__ void window_hit(const WindowConst& C, unsigned* s_coarse, unsigned r1,
@@ -281,33 +284,37 @@ struct Chunk {
   unsigned w[12];
 };
 
-// Window histogram updates of the pixels flagged in `hits` (out of line: it
-// runs for a small fraction of chunks, and keeping it out of the unrolled
-// loop keeps that loop free of reconvergence bookkeeping and spills).
-__device__ __noinline__ void window_hits(Chunk c, unsigned hits, unsigned lr, float nrho1,
-                                         float nrho2, float kappa, WindowConst a,
-                                         const char* lut, unsigned* s_coarse) {
+// Window histogram updates of one chunk known to hold an in-window pixel:
+// recompute every pixel (same arithmetic, same keys) and count those in a
+// window.  Out of line: it runs for a small fraction of chunks.
+__device__ __noinline__ void window_chunk_slow(Chunk c, unsigned lr, float nrho1, float nrho2,
+                                               float kappa, WindowConst a, const char* lut,
+                                               unsigned* s_coarse) {
   Lasso L1;
   L1.nrho1 = nrho1;
   L1.nrho2 = nrho2;
   L1.kappa = kappa;
-#pragma unroll
   for (int k = 0; k < kChunk; ++k) {
-    if (hits & (1u << k)) {
-      unsigned aR, aG, aB;
-      pixel_addr(c.w, k, lr, aR, aG, aB);
-      float h1, h2;
-      solve_one(lut, aR, aG, aB, L1, h1, h2);
-      window_hit(a, s_coarse, __float_as_uint(h1) - a.lo0, __float_as_uint(h2) - a.lo1);
-    }
+    const int o = 3 * k;
+    const unsigned aR = lut_addr(c.w[o >> 2], lr, o & 3);
+    const unsigned aG = lut_addr(c.w[(o + 1) >> 2], lr, (o + 1) & 3);
+    const unsigned aB = lut_addr(c.w[(o + 2) >> 2], lr, (o + 2) & 3);
+    if (!(aR < a.wthr || aG < a.wthr || aB < a.wthr)) continue;
+    float h1, h2;
+    solve_one(lut, aR, aG, aB, L1, h1, h2);
+    window_hit(a, s_coarse, __float_as_uint(h1) - a.lo0, __float_as_uint(h2) - a.lo1);
   }
 }
 
+// Pass 1 on one chunk.  Per pixel, all on the FMA pipe: the non-white flag
+// (as 0/1), [h~ < lo] and [h~ < hi] per stain by saturated FMAs, accumulated
+// with packed FMAs.  c_t counts "below hi", c_b0 + c_b1 "below lo"; a chunk
+// that moved their difference holds an in-window pixel.
 __device__ __forceinline__ void window_chunk(const unsigned (&w)[12], const char* lut,
                                              unsigned lr, f2 NR1, f2 NR2, float kappa,
                                              const WindowConst& a, unsigned* s_coarse, f2& c_nw,
-                                             f2& c_b0, f2& c_b1) {
-  unsigned hits = 0u;   // pixels of this chunk whose density falls in a window
+                                             f2& c_b0, f2& c_b1, f2& c_t) {
+  f2 in = pk(0.f, 0.f);   // in-window pixels of this chunk (both stains)
 #pragma unroll
   for (int p = 0; p < kChunk / 2; ++p) {
     const int kA = 2 * p, kB = 2 * p + 1;
@@ -321,18 +328,21 @@ __device__ __forceinline__ void window_chunk(const unsigned (&w)[12], const char
     const f2 NW = pk(nwA ? 1.f : 0.f, nwB ? 1.f : 0.f);
     c_nw = add2(c_nw, NW);
     const float h1A = lo_of(H1), h1B = hi_of(H1), h2A = lo_of(H2), h2B = hi_of(H2);
-    c_b0 = fma2(pk(fma_sat(h1A, a.nk0, a.lk0), fma_sat(h1B, a.nk0, a.lk0)), NW, c_b0);
-    c_b1 = fma2(pk(fma_sat(h2A, a.nk1, a.lk1), fma_sat(h2B, a.nk1, a.lk1)), NW, c_b1);
-    const bool hitA = nwA && (__float_as_uint(h1A) - a.lo0 < a.nb0 || __float_as_uint(h2A) - a.lo1 < a.nb1);
-    const bool hitB = nwB && (__float_as_uint(h1B) - a.lo0 < a.nb0 || __float_as_uint(h2B) - a.lo1 < a.nb1);
-    hits |= (hitA ? 1u << kA : 0u) | (hitB ? 1u << kB : 0u);
+    const f2 B0 = pk(fma_sat(h1A, a.nk0, a.lk0), fma_sat(h1B, a.nk0, a.lk0));
+    const f2 B1 = pk(fma_sat(h2A, a.nk1, a.lk1), fma_sat(h2B, a.nk1, a.lk1));
+    const f2 T0 = pk(fma_sat(h1A, a.nh0, a.hk0), fma_sat(h1B, a.nh0, a.hk0));
+    const f2 T1 = pk(fma_sat(h2A, a.nh1, a.hk1), fma_sat(h2B, a.nh1, a.hk1));
+    c_b0 = fma2(B0, NW, c_b0);
+    c_b1 = fma2(B1, NW, c_b1);
+    // T - B is 1 exactly for an in-window density
+    in = fma2(add2(add2(T0, T1), mul2(add2(B0, B1), pk(-1.f, -1.f))), NW, in);
   }
-  // Rare: recompute the hit pixels (same arithmetic, same keys) and count them.
-  if (hits) {
+  c_t = add2(c_t, in);
+  if (lo_of(in) + hi_of(in) != 0.f) {
     Chunk c;
 #pragma unroll
     for (int i = 0; i < 12; ++i) c.w[i] = w[i];
-    window_hits(c, hits, lr, lo_of(NR1), lo_of(NR2), kappa, a, lut, s_coarse);
+    window_chunk_slow(c, lr, lo_of(NR1), lo_of(NR2), kappa, a, lut, s_coarse);
   }
 }
 
@@ -405,11 +415,12 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_window(WindowArgs a) {
   const unsigned lr = lane_reg();
   const Lasso L = a.m->lasso;
   const f2 NR1 = pk(L.nrho1, L.nrho1), NR2 = pk(L.nrho2, L.nrho2);
-  f2 c_nw = pk(0.f, 0.f), c_b0 = pk(0.f, 0.f), c_b1 = pk(0.f, 0.f);
-  const WindowConst C{a.fine, a.wthr, a.lo0, a.lo1, a.nb0, a.nb1, a.nk0, a.lk0, a.nk1, a.lk1};
+  f2 c_nw = pk(0.f, 0.f), c_b0 = pk(0.f, 0.f), c_b1 = pk(0.f, 0.f), c_t = pk(0.f, 0.f);
+  const WindowConst C{a.fine, a.wthr, a.lo0, a.lo1, a.nb0, a.nb1, a.nk0, a.lk0, a.nk1, a.lk1,
+                      a.nh0, a.hk0, a.nh1, a.hk1};
   const Geometry g = a.g;
   for_each_chunk<false, false>(g, [&](const unsigned (&w)[12], const ChunkPos&) {
-    window_chunk(w, lut, lr, NR1, NR2, L.kappa, C, s_coarse, c_nw, c_b0, c_b1);
+    window_chunk(w, lut, lr, NR1, NR2, L.kappa, C, s_coarse, c_nw, c_b0, c_b1, c_t);
   });
   // per-thread counts are exact in FP32 (fewer than 2^24 pixels per thread)
   const u64 t_nw = block_sum((u64)lo_of(c_nw) + (u64)hi_of(c_nw), s_tmp);
@@ -787,9 +798,22 @@ int configure_pixel_kernels(Context* c) {
 // below-window test sat(h~ * nk + lk) = [h~ < lo]: with lo in [2^e, 2^e+1),
 // any h~ < lo is at least 2^(e-24) below it, so nk = -2^(24-e) makes the
 // difference >= 1 before saturation.
-static void window_of(double hint, unsigned* lo, unsigned* nb, float* nk, float* lk) {
+static void below_consts(unsigned key, float* nk, float* lk) {
+  float f;
+  memcpy(&f, &key, 4);
+  int ex = 0;
+  frexpf(f, &ex);                  // f in [2^(ex-1), 2^ex)
+  const int K = 24 - (ex - 1);
+  *nk = -ldexpf(1.f, K);
+  *lk = ldexpf(f, K);
+}
+
+static void window_of(double hint, unsigned* lo, unsigned* nb, float* nk, float* lk, float* nh,
+                      float* hk) {
   *nk = -1.f;
   *lk = 0.f;
+  *nh = -1.f;
+  *hk = 0.f;
   if (!(hint > 0.0) || !std::isfinite(hint) || hint * (1.0 - kWindowDelta) < 0x1p-100) {
     *lo = 0u; *nb = 0u; return;
   }
@@ -809,13 +833,8 @@ static void window_of(double hint, unsigned* lo, unsigned* nb, float* nk, float*
   }
   *lo = klo;
   *nb = (unsigned)width;
-  float flo_key;
-  memcpy(&flo_key, &klo, 4);
-  int ex = 0;
-  frexpf(flo_key, &ex);            // flo_key in [2^(ex-1), 2^ex)
-  const int K = 24 - (ex - 1);
-  *nk = -ldexpf(1.f, K);
-  *lk = ldexpf(flo_key, K);
+  below_consts(klo, nk, lk);
+  below_consts(klo + (unsigned)width, nh, hk);
 }
 
 // Pass 1 + select (+ radix fallback when a rank fell outside the window).
@@ -831,8 +850,8 @@ int launch_percentile_passes(Context* c, const Geometry& g, const Model* m, int 
   a.err = c->err;
   a.wthr = ((unsigned)white_thresh + 1u) << 8;
   const double hs = ldexp(1.0, -hexp);
-  window_of(hint ? hint[0] * hs : 0.0, &a.lo0, &a.nb0, &a.nk0, &a.lk0);
-  window_of(hint ? hint[1] * hs : 0.0, &a.lo1, &a.nb1, &a.nk1, &a.lk1);
+  window_of(hint ? hint[0] * hs : 0.0, &a.lo0, &a.nb0, &a.nk0, &a.lk0, &a.nh0, &a.hk0);
+  window_of(hint ? hint[1] * hs : 0.0, &a.lo1, &a.nb1, &a.nk1, &a.lk1, &a.nh1, &a.hk1);
   a.pct = pct;
   a.tgt0 = tgt_p99 ? tgt_p99[0] : 1.0;
   a.tgt1 = tgt_p99 ? tgt_p99[1] : 1.0;
