@@ -280,40 +280,15 @@ __device__ __forceinline__ void window_hit(const WindowConst& C, unsigned* s_coa
   }
 }
 
-struct Chunk {
-  unsigned w[12];
-};
-
-// Window histogram updates of one chunk known to hold an in-window pixel:
-// recompute every pixel (same arithmetic, same keys) and count those in a
-// window.  Out of line: it runs for a small fraction of chunks.
-__device__ __noinline__ void window_chunk_slow(Chunk c, unsigned lr, float nrho1, float nrho2,
-                                               float kappa, WindowConst a, const char* lut,
-                                               unsigned* s_coarse) {
-  Lasso L1;
-  L1.nrho1 = nrho1;
-  L1.nrho2 = nrho2;
-  L1.kappa = kappa;
-  for (int k = 0; k < kChunk; ++k) {
-    const int o = 3 * k;
-    const unsigned aR = lut_addr(c.w[o >> 2], lr, o & 3);
-    const unsigned aG = lut_addr(c.w[(o + 1) >> 2], lr, (o + 1) & 3);
-    const unsigned aB = lut_addr(c.w[(o + 2) >> 2], lr, (o + 2) & 3);
-    if (!(aR < a.wthr || aG < a.wthr || aB < a.wthr)) continue;
-    float h1, h2;
-    solve_one(lut, aR, aG, aB, L1, h1, h2);
-    window_hit(a, s_coarse, __float_as_uint(h1) - a.lo0, __float_as_uint(h2) - a.lo1);
-  }
-}
-
 // Pass 1 on one chunk.  Per pixel, all on the FMA pipe: the non-white flag
 // (as 0/1), [h~ < lo] and [h~ < hi] per stain by saturated FMAs, accumulated
-// with packed FMAs.  c_t counts "below hi", c_b0 + c_b1 "below lo"; a chunk
-// that moved their difference holds an in-window pixel.
-__device__ __forceinline__ void window_chunk(const unsigned (&w)[12], const char* lut,
-                                             unsigned lr, f2 NR1, f2 NR2, float kappa,
-                                             const WindowConst& a, unsigned* s_coarse, f2& c_nw,
-                                             f2& c_b0, f2& c_b1, f2& c_t) {
+// with packed FMAs.  A chunk whose in-window count (sum of [h~ < hi] - [h~ <
+// lo] over non-white pixels) is non-zero is revisited pixel by pixel, reading
+// its bytes again from cache, to update the window histogram.
+__device__ __forceinline__ void window_chunk(const unsigned (&w)[12], const uint8_t* src, int n,
+                                             unsigned thr, const char* lut, unsigned lr, f2 NR1,
+                                             f2 NR2, float kappa, const WindowConst& a,
+                                             unsigned* s_coarse, f2& c_nw, f2& c_b0, f2& c_b1) {
   f2 in = pk(0.f, 0.f);   // in-window pixels of this chunk (both stains)
 #pragma unroll
   for (int p = 0; p < kChunk / 2; ++p) {
@@ -337,12 +312,19 @@ __device__ __forceinline__ void window_chunk(const unsigned (&w)[12], const char
     // T - B is 1 exactly for an in-window density
     in = fma2(add2(add2(T0, T1), mul2(add2(B0, B1), pk(-1.f, -1.f))), NW, in);
   }
-  c_t = add2(c_t, in);
   if (lo_of(in) + hi_of(in) != 0.f) {
-    Chunk c;
-#pragma unroll
-    for (int i = 0; i < 12; ++i) c.w[i] = w[i];
-    window_chunk_slow(c, lr, lo_of(NR1), lo_of(NR2), kappa, a, lut, s_coarse);
+    Lasso L1;
+    L1.nrho1 = lo_of(NR1);
+    L1.nrho2 = lo_of(NR2);
+    L1.kappa = kappa;
+#pragma unroll 1
+    for (int k = 0; k < n; ++k) {
+      const unsigned r = __ldg(src + 3 * k), g = __ldg(src + 3 * k + 1), b = __ldg(src + 3 * k + 2);
+      if (min(r, min(g, b)) > thr) continue;
+      float h1, h2;
+      solve_one(lut, (r << 8) | lr, (g << 8) | lr, (b << 8) | lr, L1, h1, h2);
+      window_hit(a, s_coarse, __float_as_uint(h1) - a.lo0, __float_as_uint(h2) - a.lo1);
+    }
   }
 }
 
@@ -415,12 +397,14 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_window(WindowArgs a) {
   const unsigned lr = lane_reg();
   const Lasso L = a.m->lasso;
   const f2 NR1 = pk(L.nrho1, L.nrho1), NR2 = pk(L.nrho2, L.nrho2);
-  f2 c_nw = pk(0.f, 0.f), c_b0 = pk(0.f, 0.f), c_b1 = pk(0.f, 0.f), c_t = pk(0.f, 0.f);
+  f2 c_nw = pk(0.f, 0.f), c_b0 = pk(0.f, 0.f), c_b1 = pk(0.f, 0.f);
   const WindowConst C{a.fine, a.wthr, a.lo0, a.lo1, a.nb0, a.nb1, a.nk0, a.lk0, a.nk1, a.lk1,
                       a.nh0, a.hk0, a.nh1, a.hk1};
   const Geometry g = a.g;
-  for_each_chunk<false, false>(g, [&](const unsigned (&w)[12], const ChunkPos&) {
-    window_chunk(w, lut, lr, NR1, NR2, L.kappa, C, s_coarse, c_nw, c_b0, c_b1, c_t);
+  const unsigned thr = (a.wthr >> 8) - 1u;
+  for_each_chunk<false, false>(g, [&](const unsigned (&w)[12], const ChunkPos& p) {
+    window_chunk(w, g.src + p.src_off, p.n, thr, lut, lr, NR1, NR2, L.kappa, C, s_coarse, c_nw,
+                 c_b0, c_b1);
   });
   // per-thread counts are exact in FP32 (fewer than 2^24 pixels per thread)
   const u64 t_nw = block_sum((u64)lo_of(c_nw) + (u64)hi_of(c_nw), s_tmp);
