@@ -91,7 +91,8 @@ int ensure_candidate_capacity(Context* c, int n);
   } while (0)
 
 // Shared-memory sizes of the pixel kernels.
-constexpr size_t kWindowSmem = kLutSmemBytes + sizeof(unsigned) * 2 * kWinGroups;
+constexpr size_t kWindowSmem = kLutSmemBytes + sizeof(unsigned) * 2 * kWinGroups +
+                               sizeof(uint2) * 8 * kPassThreads;   // chunk queue of pass 1
 constexpr size_t kRadixSmem = kLutSmemBytes + sizeof(unsigned) * kTracks * kRadixBins;
 
 int configure_pixel_kernels(Context* c);

@@ -268,28 +268,38 @@ struct WindowConst {
   float nh0, hk0, nh1, hk1;   // sat(h~ nh + hk) = [h~ < lo + nb]
 };
 
+// Fire-and-forget increments (no return value, no compiler-side aggregation).
+__device__ __forceinline__ void red_add_global(u64* p, u64 v) {
+  asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" :: "l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void red_add_shared(unsigned* p, unsigned v) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("red.shared.add.u32 [%0], %1;" :: "r"(a), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ void window_hit(const WindowConst& C, unsigned* s_coarse, unsigned r1,
                                            unsigned r2) {
   if (r1 < C.nb0) {
-    atomicAdd(C.fine + r1, 1ull);
-    atomicAdd(s_coarse + (r1 >> kWinGroupBits), 1u);
+    red_add_global(C.fine + r1, 1ull);
+    red_add_shared(s_coarse + (r1 >> kWinGroupBits), 1u);
   }
   if (r2 < C.nb1) {
-    atomicAdd(C.fine + kWinBins + r2, 1ull);
-    atomicAdd(s_coarse + kWinGroups + (r2 >> kWinGroupBits), 1u);
+    red_add_global(C.fine + kWinBins + r2, 1ull);
+    red_add_shared(s_coarse + kWinGroups + (r2 >> kWinGroupBits), 1u);
   }
 }
 
 // Pass 1 on one chunk.  Per pixel, all on the FMA pipe: the non-white flag
 // (as 0/1), [h~ < lo] and [h~ < hi] per stain by saturated FMAs, accumulated
-// with packed FMAs.  A chunk whose in-window count (sum of [h~ < hi] - [h~ <
-// lo] over non-white pixels) is non-zero is revisited pixel by pixel, reading
-// its bytes again from cache, to update the window histogram.
-__device__ __forceinline__ void window_chunk(const unsigned (&w)[12], const uint8_t* src, int n,
-                                             unsigned thr, const char* lut, unsigned lr, f2 NR1,
-                                             f2 NR2, float kappa, const WindowConst& a,
-                                             unsigned* s_coarse, f2& c_nw, f2& c_b0, f2& c_b1) {
-  f2 in = pk(0.f, 0.f);   // in-window pixels of this chunk (both stains)
+// with packed FMAs.  The number of windows a pixel falls in (0, 1 or 2) is
+// packed base 4 into `mask` (pixel pair p at digit 7-p, even pixels in the
+// low lane, odd pixels in the high lane): exact small integers in FP32.
+__device__ __forceinline__ void window_chunk(const unsigned (&w)[12], const char* lut,
+                                             unsigned lr, f2 NR1, f2 NR2, float kappa,
+                                             const WindowConst& a, f2& c_nw, f2& c_b0, f2& c_b1,
+                                             f2& mask) {
+  const f2 M1 = pk(-1.f, -1.f), FOUR = pk(4.f, 4.f);
+  mask = pk(0.f, 0.f);
 #pragma unroll
   for (int p = 0; p < kChunk / 2; ++p) {
     const int kA = 2 * p, kB = 2 * p + 1;
@@ -310,21 +320,8 @@ __device__ __forceinline__ void window_chunk(const unsigned (&w)[12], const uint
     c_b0 = fma2(B0, NW, c_b0);
     c_b1 = fma2(B1, NW, c_b1);
     // T - B is 1 exactly for an in-window density
-    in = fma2(add2(add2(T0, T1), mul2(add2(B0, B1), pk(-1.f, -1.f))), NW, in);
-  }
-  if (lo_of(in) + hi_of(in) != 0.f) {
-    Lasso L1;
-    L1.nrho1 = lo_of(NR1);
-    L1.nrho2 = lo_of(NR2);
-    L1.kappa = kappa;
-#pragma unroll 1
-    for (int k = 0; k < n; ++k) {
-      const unsigned r = __ldg(src + 3 * k), g = __ldg(src + 3 * k + 1), b = __ldg(src + 3 * k + 2);
-      if (min(r, min(g, b)) > thr) continue;
-      float h1, h2;
-      solve_one(lut, (r << 8) | lr, (g << 8) | lr, (b << 8) | lr, L1, h1, h2);
-      window_hit(a, s_coarse, __float_as_uint(h1) - a.lo0, __float_as_uint(h2) - a.lo1);
-    }
+    const f2 X = add2(fma2(B0, M1, T0), fma2(B1, M1, T1));
+    mask = fma2(mask, FOUR, mul2(X, NW));
   }
 }
 
@@ -386,12 +383,46 @@ __device__ void window_select(const WindowArgs& a) {
   }
 }
 
+constexpr int kQueueBatch = 8;                          // iterations between queue drains
+constexpr int kQueueCap = kQueueBatch * kPassThreads;     // cannot overflow
+
+// Window-histogram updates of the queued chunks: each entry is a chunk index
+// and its two base-4 masks; only flagged pixels are recomputed (same
+// arithmetic, same keys), reading their bytes again (still in L2).
+__device__ __forceinline__ void drain_queue(const uint2* queue, int count, const Geometry& g,
+                                            const char* lut, unsigned lr, const Lasso& L,
+                                            const WindowConst& a, unsigned* s_coarse) {
+  for (int e = threadIdx.x; e < count; e += blockDim.x) {
+    const uint2 ent = queue[e];
+    const ChunkPos p = chunk_pos(g, (u64)ent.x);
+    const uint8_t* src = g.src + p.src_off;
+#pragma unroll 1
+    for (int lane = 0; lane < 2; ++lane) {
+      unsigned m = lane ? (ent.y >> 16) : (ent.y & 0xFFFFu);
+#pragma unroll 1
+      while (m) {
+        const int bit = __ffs(m) - 1;
+        const int pair = 7 - (bit >> 1);
+        m &= ~(3u << (bit & ~1));
+        const int k = 2 * pair + lane;
+        const unsigned r = __ldg(src + 3 * k), gg = __ldg(src + 3 * k + 1), b = __ldg(src + 3 * k + 2);
+        float h1, h2;
+        solve_one(lut, (r << 8) | lr, (gg << 8) | lr, (b << 8) | lr, L, h1, h2);
+        window_hit(a, s_coarse, __float_as_uint(h1) - a.lo0, __float_as_uint(h2) - a.lo1);
+      }
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kPassThreads, 1) k_pass_window(WindowArgs a) {
   extern __shared__ __align__(16) char s_dyn[];
   unsigned* s_coarse = reinterpret_cast<unsigned*>(s_dyn + kLutSmemBytes);
+  uint2* s_queue = reinterpret_cast<uint2*>(s_dyn + kLutSmemBytes + 2 * kWinGroups * sizeof(unsigned));
   __shared__ u64 s_tmp[33];
   __shared__ unsigned s_ticket;
+  __shared__ int s_qn;
   for (int i = threadIdx.x; i < 2 * kWinGroups; i += blockDim.x) s_coarse[i] = 0u;
+  if (threadIdx.x == 0) s_qn = 0;
   load_lut(a.m, s_dyn);
   const char* lut = s_dyn;
   const unsigned lr = lane_reg();
@@ -401,11 +432,42 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_window(WindowArgs a) {
   const WindowConst C{a.fine, a.wthr, a.lo0, a.lo1, a.nb0, a.nb1, a.nk0, a.lk0, a.nk1, a.lk1,
                       a.nh0, a.hk0, a.nh1, a.hk1};
   const Geometry g = a.g;
-  const unsigned thr = (a.wthr >> 8) - 1u;
-  for_each_chunk<false, false>(g, [&](const unsigned (&w)[12], const ChunkPos& p) {
-    window_chunk(w, g.src + p.src_off, p.n, thr, lut, lr, NR1, NR2, L.kappa, C, s_coarse, c_nw,
-                 c_b0, c_b1);
-  });
+  const u64 stride = (u64)gridDim.x * blockDim.x;
+  const unsigned lane = threadIdx.x & 31u;
+  int it = 0;
+  // every thread of a block runs the same number of iterations (block-uniform
+  // loop), so the periodic queue drains can use block barriers
+  for (u64 base = (u64)blockIdx.x * blockDim.x; base < g.nchunks; base += stride) {
+    const u64 q = base + threadIdx.x;
+    bool hit = false;
+    unsigned packed = 0u;
+    if (q < g.nchunks) {
+      const ChunkPos p = chunk_pos(g, q);
+      unsigned w[12];
+      load_chunk<false>(g, p, w);
+      f2 mask;
+      window_chunk(w, lut, lr, NR1, NR2, L.kappa, C, c_nw, c_b0, c_b1, mask);
+      const unsigned mA = (unsigned)lo_of(mask), mB = (unsigned)hi_of(mask);
+      packed = mA | (mB << 16);
+      hit = packed != 0u;
+    }
+    // warp-aggregated append of the hit chunks
+    const unsigned ball = __ballot_sync(0xFFFFFFFFu, hit);
+    if (ball) {
+      int qbase = 0;
+      if (lane == 0) qbase = atomicAdd(&s_qn, __popc(ball));
+      qbase = __shfl_sync(0xFFFFFFFFu, qbase, 0);
+      if (hit) s_queue[qbase + __popc(ball & ((1u << lane) - 1u))] = make_uint2((unsigned)q, packed);
+    }
+    if (++it == kQueueBatch || base + stride >= g.nchunks) {
+      it = 0;
+      __syncthreads();
+      const int n = s_qn;
+      drain_queue(s_queue, n, g, lut, lr, L, C, s_coarse);
+      __syncthreads();
+      if (threadIdx.x == 0) s_qn = 0;
+    }
+  }
   // per-thread counts are exact in FP32 (fewer than 2^24 pixels per thread)
   const u64 t_nw = block_sum((u64)lo_of(c_nw) + (u64)hi_of(c_nw), s_tmp);
   const u64 t_b0 = block_sum((u64)lo_of(c_b0) + (u64)hi_of(c_b0), s_tmp);
