@@ -383,16 +383,16 @@ __device__ void window_select(const WindowArgs& a) {
   }
 }
 
-constexpr int kQueueBatch = 8;                          // iterations between queue drains
-constexpr int kQueueCap = kQueueBatch * kPassThreads;     // cannot overflow
+constexpr int kWarpQueue = 256;   // queued chunks per warp (drained before a round could overflow it)
 
 // Window-histogram updates of the queued chunks: each entry is a chunk index
 // and its two base-4 masks; only flagged pixels are recomputed (same
-// arithmetic, same keys), reading their bytes again (still in L2).
+// arithmetic, same keys), reading their bytes again (still in L2).  Called by
+// one warp for its own queue.
 __device__ __forceinline__ void drain_queue(const uint2* queue, int count, const Geometry& g,
                                             const char* lut, unsigned lr, const Lasso& L,
                                             const WindowConst& a, unsigned* s_coarse) {
-  for (int e = threadIdx.x; e < count; e += blockDim.x) {
+  for (int e = (int)(threadIdx.x & 31u); e < count; e += 32) {
     const uint2 ent = queue[e];
     const ChunkPos p = chunk_pos(g, (u64)ent.x);
     const uint8_t* src = g.src + p.src_off;
@@ -417,12 +417,11 @@ __device__ __forceinline__ void drain_queue(const uint2* queue, int count, const
 __global__ void __launch_bounds__(kPassThreads, 1) k_pass_window(WindowArgs a) {
   extern __shared__ __align__(16) char s_dyn[];
   unsigned* s_coarse = reinterpret_cast<unsigned*>(s_dyn + kLutSmemBytes);
-  uint2* s_queue = reinterpret_cast<uint2*>(s_dyn + kLutSmemBytes + 2 * kWinGroups * sizeof(unsigned));
+  uint2* s_queue = reinterpret_cast<uint2*>(s_dyn + kLutSmemBytes + 2 * kWinGroups * sizeof(unsigned)) +
+                   (threadIdx.x >> 5) * kWarpQueue;      // this warp's queue
   __shared__ u64 s_tmp[33];
   __shared__ unsigned s_ticket;
-  __shared__ int s_qn;
   for (int i = threadIdx.x; i < 2 * kWinGroups; i += blockDim.x) s_coarse[i] = 0u;
-  if (threadIdx.x == 0) s_qn = 0;
   load_lut(a.m, s_dyn);
   const char* lut = s_dyn;
   const unsigned lr = lane_reg();
@@ -434,11 +433,12 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_window(WindowArgs a) {
   const Geometry g = a.g;
   const u64 stride = (u64)gridDim.x * blockDim.x;
   const unsigned lane = threadIdx.x & 31u;
-  int it = 0;
-  // every thread of a block runs the same number of iterations (block-uniform
-  // loop), so the periodic queue drains can use block barriers
-  for (u64 base = (u64)blockIdx.x * blockDim.x; base < g.nchunks; base += stride) {
-    const u64 q = base + threadIdx.x;
+  int qn = 0;   // entries in this warp's queue (warp-uniform)
+  // every lane of a warp runs the same number of iterations (warp-uniform
+  // loop), so the queue bookkeeping needs only warp-level operations
+  for (u64 base = (u64)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < g.nchunks;
+       base += stride) {
+    const u64 q = base + lane;
     bool hit = false;
     unsigned packed = 0u;
     if (q < g.nchunks) {
@@ -451,21 +451,14 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_window(WindowArgs a) {
       packed = mA | (mB << 16);
       hit = packed != 0u;
     }
-    // warp-aggregated append of the hit chunks
     const unsigned ball = __ballot_sync(0xFFFFFFFFu, hit);
-    if (ball) {
-      int qbase = 0;
-      if (lane == 0) qbase = atomicAdd(&s_qn, __popc(ball));
-      qbase = __shfl_sync(0xFFFFFFFFu, qbase, 0);
-      if (hit) s_queue[qbase + __popc(ball & ((1u << lane) - 1u))] = make_uint2((unsigned)q, packed);
-    }
-    if (++it == kQueueBatch || base + stride >= g.nchunks) {
-      it = 0;
-      __syncthreads();
-      const int n = s_qn;
-      drain_queue(s_queue, n, g, lut, lr, L, C, s_coarse);
-      __syncthreads();
-      if (threadIdx.x == 0) s_qn = 0;
+    if (hit) s_queue[qn + __popc(ball & ((1u << lane) - 1u))] = make_uint2((unsigned)q, packed);
+    qn += __popc(ball);
+    if (qn > kWarpQueue - 32 || base + stride >= g.nchunks) {
+      __syncwarp();
+      drain_queue(s_queue, qn, g, lut, lr, L, C, s_coarse);
+      __syncwarp();
+      qn = 0;
     }
   }
   // per-thread counts are exact in FP32 (fewer than 2^24 pixels per thread)
