@@ -387,7 +387,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="wsi")
-    ap.add_argument("--oracle-side", type=int, default=2048)
+    ap.add_argument("--oracle-side", type=int, default=8192)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -397,7 +397,7 @@ def main():
     if args.impl == "reference":
         world = int(os.environ.get("WORLD_SIZE", "1"))
         rank = int(os.environ.get("RANK", "0"))
-        if args.oracle_side == 2048:
+        if args.oracle_side == 8192:
             args.oracle_side = 1024
         return run_reference(args, world, rank)
     world, rank, local = dist_setup(args)

@@ -97,17 +97,21 @@ __device__ __forceinline__ void patch_origin(const PatchArgs& a, int k, u64* x0,
   *y0 = sm64_below(a.seed, 2ull * (u64)k + 1ull, (u64)(a.height - a.P + 1));
 }
 
-// One block per candidate patch: its non-white pixel count.
+// One block per candidate patch: its non-white pixel count (rows by warps,
+// columns by lanes, no per-pixel division).
 __global__ void k_patch_count(PatchArgs a) {
   __shared__ u64 s_tmp[33];
   const int k = blockIdx.x;
   u64 x0, y0;
   patch_origin(a, k, &x0, &y0);
-  const int npx = a.P * a.P;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   unsigned cnt = 0;
-  for (int i = threadIdx.x; i < npx; i += blockDim.x) {
-    const uint32_t v = load_pixel(a.data, a.pitch, x0 + (u64)(i % a.P), y0 + (u64)(i / a.P));
-    cnt += packed_nonwhite(v, a.thr) ? 1u : 0u;
+  for (int y = warp; y < a.P; y += nwarps) {
+    const uint8_t* row = a.data + (int64_t)(y0 + (u64)y) * a.pitch + (int64_t)(x0 * 3);
+    for (int x = lane; x < a.P; x += 32) {
+      const unsigned r = row[3 * x], g = row[3 * x + 1], b = row[3 * x + 2];
+      cnt += min(r, min(g, b)) <= a.thr ? 1u : 0u;
+    }
   }
   const u64 tot = block_sum(cnt, s_tmp);
   if (threadIdx.x == 0) a.cand[k] = (int)tot;
@@ -125,15 +129,19 @@ __global__ void k_patch_accept(PatchArgs a) {
   if (n == 0) a.bs->status = SPCN_ERR_NO_TISSUE;
 }
 
+// One block per kept patch: copy its pixels, raster order, into the sample.
 __global__ void k_patch_gather(PatchArgs a) {
-  const u64 per = (u64)a.P * a.P;
-  const u64 m = (u64)a.bs->n_acc * per;
-  for (u64 s = (u64)blockIdx.x * blockDim.x + threadIdx.x; s < m; s += (u64)gridDim.x * blockDim.x) {
-    const int p = (int)(s / per);
-    const u64 i = s - (u64)p * per;
-    u64 x0, y0;
-    patch_origin(a, a.cand[a.n_cand + p], &x0, &y0);
-    a.out[s] = load_pixel(a.data, a.pitch, x0 + i % (u64)a.P, y0 + i / (u64)a.P);
+  const int p = blockIdx.x;
+  if (p >= a.bs->n_acc) return;
+  u64 x0, y0;
+  patch_origin(a, a.cand[a.n_cand + p], &x0, &y0);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  uint32_t* out = a.out + (u64)p * (u64)a.P * (u64)a.P;
+  for (int y = warp; y < a.P; y += nwarps) {
+    const uint8_t* row = a.data + (int64_t)(y0 + (u64)y) * a.pitch + (int64_t)(x0 * 3);
+    for (int x = lane; x < a.P; x += 32)
+      out[(u64)y * a.P + x] = (uint32_t)row[3 * x] | ((uint32_t)row[3 * x + 1] << 8) |
+                              ((uint32_t)row[3 * x + 2] << 16);
   }
 }
 
@@ -223,9 +231,14 @@ struct I0Args {
   const uint32_t* br;
   BasisState* bs;
   Model* m;
+  unsigned* hist;     // [3][256] global counts, zeroed before the launch
+  unsigned* ticket;   // zeroed before the launch
   int cap;
   double pct;
 };
+
+constexpr int kI0Threads = 256;
+constexpr int kI0Blocks = 64;
 
 __device__ double hist_rank_value(const unsigned* h, u64 rank) {
   u64 c = 0;
@@ -237,33 +250,50 @@ __device__ double hist_rank_value(const unsigned* h, u64 rank) {
 }
 
 // Per channel, the type-7 percentile of every ceil(n/cap)-th bright sample
-// pixel (sample order), from a 256-bin histogram (exact for 8-bit values).
-// Also initialises the basis to the column-normalised Ruifrok-Johnston H&E
-// vectors, the starting point of the dictionary learning.
-__global__ void k_i0(I0Args a) {
-  __shared__ unsigned s_h[3][256];
-  for (int i = threadIdx.x; i < 3 * 256; i += blockDim.x) (&s_h[0][0])[i] = 0u;
+// pixel (sample order), from 256-bin histograms (exact for 8-bit values).
+// Blocks count into per-warp bins, merge into global bins, and the last block
+// computes the percentiles.  Also initialises the basis to the
+// column-normalised Ruifrok-Johnston H&E vectors, the starting point of the
+// dictionary learning.
+__global__ void __launch_bounds__(kI0Threads) k_i0(I0Args a) {
+  __shared__ unsigned s_h[kI0Threads / 32][3][256];
+  __shared__ unsigned s_last;
+  unsigned* my = &s_h[threadIdx.x >> 5][0][0];
+  for (int i = threadIdx.x; i < (kI0Threads / 32) * 768; i += blockDim.x) (&s_h[0][0][0])[i] = 0u;
   __syncthreads();
   const u64 nb = a.bs->n_br;
   const u64 stride = nb ? (nb + (u64)a.cap - 1) / (u64)a.cap : 1;
   const u64 kept = nb ? (nb + stride - 1) / stride : 0;
-  for (u64 i = threadIdx.x; i < kept; i += blockDim.x) {
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < kept; i += (u64)gridDim.x * blockDim.x) {
     const uint32_t v = a.br[i * stride];
-    atomicAdd(&s_h[0][v & 0xFFu], 1u);
-    atomicAdd(&s_h[1][(v >> 8) & 0xFFu], 1u);
-    atomicAdd(&s_h[2][(v >> 16) & 0xFFu], 1u);
+    atomicAdd(my + (v & 0xFFu), 1u);
+    atomicAdd(my + 256 + ((v >> 8) & 0xFFu), 1u);
+    atomicAdd(my + 512 + ((v >> 16) & 0xFFu), 1u);
   }
   __syncthreads();
+  for (int i = threadIdx.x; i < 768; i += blockDim.x) {
+    unsigned t = 0;
+    for (int w = 0; w < kI0Threads / 32; ++w) t += (&s_h[w][0][0])[i];
+    if (t) atomicAdd(a.hist + i, t);
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(a.ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
   if (threadIdx.x < 3) {
     const int c = threadIdx.x;
+    unsigned h[256];
+    for (int v = 0; v < 256; ++v) h[v] = __ldcg(a.hist + 256 * c + v);
     double val = 255.0;
     if (kept > 0) {
       const double pos = (double)(kept - 1) * (a.pct / 100.0);
       u64 k = (u64)floor(pos);
       if (k > kept - 1) k = kept - 1;
       const double t = pos - (double)k;
-      const double lo = hist_rank_value(s_h[c], k);
-      const double hi = (k + 1 < kept) ? hist_rank_value(s_h[c], k + 1) : lo;
+      const double lo = hist_rank_value(h, k);
+      const double hi = (k + 1 < kept) ? hist_rank_value(h, k + 1) : lo;
       val = (k + 1 < kept) ? __dadd_rn(lo, __dmul_rn(t, __dsub_rn(hi, lo))) : lo;
     }
     a.m->i0[c] = (float)val;
@@ -349,8 +379,7 @@ __global__ void __launch_bounds__(kSnmfThreads) k_snmf(SnmfArgs a) {
     float acc[kAcc];
 #pragma unroll
     for (int i = 0; i < kAcc; ++i) acc[i] = 0.f;
-    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gstride) {
-      const uint32_t v = __ldg(a.nw + i);
+    auto step = [&](uint32_t v) {
       const float v0 = s_od[v & 0xFFu], v1 = s_od[256 + ((v >> 8) & 0xFFu)],
                   v2 = s_od[512 + ((v >> 16) & 0xFFu)];
       const float d1 = fmaf(w20, v2, fmaf(w10, v1, w00 * v0)) - a.lambda;
@@ -371,7 +400,19 @@ __global__ void __launch_bounds__(kSnmfThreads) k_snmf(SnmfArgs a) {
       acc[9] += h1;
       acc[10] += h2;
       acc[11] = fmaf(v0, v0, fmaf(v1, v1, fmaf(v2, v2, acc[11])));
+    };
+    // four pixels per 16-byte load (the list is 16-byte aligned), then the tail
+    const uint4* nw4 = reinterpret_cast<const uint4*>(a.nw);
+    const u64 n4 = n >> 2;
+    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += gstride) {
+      const uint4 v = __ldg(nw4 + i);
+      step(v.x);
+      step(v.y);
+      step(v.z);
+      step(v.w);
     }
+    for (u64 i = (n4 << 2) + (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gstride)
+      step(__ldg(a.nw + i));
 #pragma unroll
     for (int i = 0; i < kAcc; ++i) {
       double x = (double)acc[i];
@@ -504,7 +545,7 @@ int run_estimate_basis(Context* c, const spcn_image* img, const spcn_params* p, 
     SPCN_LAUNCH_CHECK(c);
     k_patch_accept<<<1, 32, 0, st>>>(pa);
     SPCN_LAUNCH_CHECK(c);
-    k_patch_gather<<<big_grid, 256, 0, st>>>(pa);
+    k_patch_gather<<<p->n_patches, 256, 0, st>>>(pa);
     SPCN_LAUNCH_CHECK(c);
   }
   const u64 nblk = (cap + kCompactBlock - 1) / kCompactBlock;
@@ -516,8 +557,10 @@ int run_estimate_basis(Context* c, const spcn_image* img, const spcn_params* p, 
   SPCN_LAUNCH_CHECK(c);
   k_compact<<<(unsigned)nblk, kCompactThreads, 0, st>>>(ca);
   SPCN_LAUNCH_CHECK(c);
-  I0Args ia{c->br, bs, c->model_b, p->i0_max_samples, (double)p->i0_pct};
-  k_i0<<<1, 512, 0, st>>>(ia);
+  SPCN_CUDA_TRY(cudaMemsetAsync(bs->i0_hist, 0, sizeof(bs->i0_hist) + sizeof(bs->i0_ticket), st));
+  I0Args ia{c->br, bs, c->model_b, bs->i0_hist, &bs->i0_ticket, p->i0_max_samples,
+            (double)p->i0_pct};
+  k_i0<<<kI0Blocks, kI0Threads, 0, st>>>(ia);
   SPCN_LAUNCH_CHECK(c);
   rc = launch_build_model(c, c->model_b, nullptr, nullptr, p->lambda, c->model_b, st);
   if (rc) return rc;

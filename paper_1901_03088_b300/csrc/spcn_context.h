@@ -22,6 +22,8 @@ struct BasisState {
   double objective;
   double W[6];        // final basis in FP64 (ordered)
   SelectState sel;    // percentile of the sampled non-white densities
+  unsigned i0_hist[3 * 256];
+  unsigned i0_ticket;
 };
 
 struct Context {

@@ -115,7 +115,7 @@ int launch_build_model(Context* c, Model* m, const float* W, const float* i0, fl
   for (int i = 0; i < 3; ++i) in.i0[i] = i0 ? i0[i] : 1.f;
   in.lambda = lambda;
   in.hexp = (W && i0 && !from_device) ? table_hexp(W, i0, lambda) : kHexpAuto;
-  k_build_model<<<3, 256, 0, st>>>(m, in, from_device);
+  k_build_model<<<kLutEntries / 32, 32, 0, st>>>(m, in, from_device);   // one log per thread
   SPCN_LAUNCH_CHECK(c);
   return SPCN_OK;
 }
