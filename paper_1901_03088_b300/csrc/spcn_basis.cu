@@ -129,15 +129,17 @@ __global__ void k_patch_accept(PatchArgs a) {
   if (n == 0) a.bs->status = SPCN_ERR_NO_TISSUE;
 }
 
-// One block per kept patch: copy its pixels, raster order, into the sample.
+// Eight blocks per kept patch (interleaved rows): copy its pixels, raster
+// order, into the sample.
+constexpr int kGatherSplit = 8;
 __global__ void k_patch_gather(PatchArgs a) {
-  const int p = blockIdx.x;
+  const int p = blockIdx.x / kGatherSplit, part = blockIdx.x % kGatherSplit;
   if (p >= a.bs->n_acc) return;
   u64 x0, y0;
   patch_origin(a, a.cand[a.n_cand + p], &x0, &y0);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   uint32_t* out = a.out + (u64)p * (u64)a.P * (u64)a.P;
-  for (int y = warp; y < a.P; y += nwarps) {
+  for (int y = warp * kGatherSplit + part; y < a.P; y += nwarps * kGatherSplit) {
     const uint8_t* row = a.data + (int64_t)(y0 + (u64)y) * a.pitch + (int64_t)(x0 * 3);
     for (int x = lane; x < a.P; x += 32)
       out[(u64)y * a.P + x] = (uint32_t)row[3 * x] | ((uint32_t)row[3 * x + 1] << 8) |
@@ -404,7 +406,19 @@ __global__ void __launch_bounds__(kSnmfThreads) k_snmf(SnmfArgs a) {
     // four pixels per 16-byte load (the list is 16-byte aligned), then the tail
     const uint4* nw4 = reinterpret_cast<const uint4*>(a.nw);
     const u64 n4 = n >> 2;
-    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += gstride) {
+    u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + gstride < n4; i += 2 * gstride) {   // two loads in flight
+      const uint4 v = __ldg(nw4 + i), u = __ldg(nw4 + i + gstride);
+      step(v.x);
+      step(v.y);
+      step(v.z);
+      step(v.w);
+      step(u.x);
+      step(u.y);
+      step(u.z);
+      step(u.w);
+    }
+    if (i < n4) {
       const uint4 v = __ldg(nw4 + i);
       step(v.x);
       step(v.y);
@@ -429,10 +443,15 @@ __global__ void __launch_bounds__(kSnmfThreads) k_snmf(SnmfArgs a) {
     }
     target += gridDim.x;
     if (!grid_barrier(a.bar, target, a.abort, a.err, a.timeout_ns)) return;
-    if (threadIdx.x < kAcc) {
+    // cross-block sums: warp w < kAcc adds accumulator w over all blocks in a
+    // fixed order (lane-strided partial sums, then a fixed shuffle tree), so
+    // every block gets bit-identical totals and reruns are deterministic
+    if (warp < kAcc) {
       double x = 0.0;
-      for (unsigned b = 0; b < gridDim.x; ++b) x += __ldcg(part + (size_t)b * kAcc + threadIdx.x);
-      s_tot[threadIdx.x] = x;
+      for (unsigned b = lane; b < gridDim.x; b += 32) x += __ldcg(part + (size_t)b * kAcc + warp);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0) s_tot[warp] = x;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -545,7 +564,7 @@ int run_estimate_basis(Context* c, const spcn_image* img, const spcn_params* p, 
     SPCN_LAUNCH_CHECK(c);
     k_patch_accept<<<1, 32, 0, st>>>(pa);
     SPCN_LAUNCH_CHECK(c);
-    k_patch_gather<<<p->n_patches, 256, 0, st>>>(pa);
+    k_patch_gather<<<p->n_patches * kGatherSplit, 256, 0, st>>>(pa);
     SPCN_LAUNCH_CHECK(c);
   }
   const u64 nblk = (cap + kCompactBlock - 1) / kCompactBlock;

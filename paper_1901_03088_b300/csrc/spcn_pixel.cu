@@ -555,19 +555,28 @@ __device__ bool radix_select(const Src& src, const char* lut, const Lasso& L, Se
     for (int i = threadIdx.x; i < kTracks * kRadixBins; i += blockDim.x) s_hist[i] = 0u;
     __syncthreads();
     unsigned pre[kTracks];
-    int act[kTracks];
+    int act[kTracks], own[kTracks];
 #pragma unroll
     for (int t = 0; t < kTracks; ++t) { pre[t] = s_prefix[t]; act[t] = s_act[t]; }
+    // the two ranks of a stain share one histogram while their prefixes agree
+#pragma unroll
+    for (int t = 0; t < kTracks; ++t)
+      own[t] = ((t & 1) && act[t] && act[t - 1] && pre[t] == pre[t - 1]) ? t - 1 : t;
     src.for_each([&](unsigned aR, unsigned aG, unsigned aB, bool nw) {
-      if (!nw) return;
       float h1, h2;
       solve_one(lut, aR, aG, aB, L, h1, h2);
       const unsigned key[2] = {__float_as_uint(h1), __float_as_uint(h2)};
+      const unsigned live = __activemask();
 #pragma unroll
       for (int t = 0; t < kTracks; ++t) {
+        if (own[t] != t || !act[t]) continue;   // uniform across the block
         const unsigned k = key[t >> 1];
-        if (act[t] && (((u64)k >> hi) == ((u64)pre[t] >> hi)))
-          atomicAdd(s_hist + t * kRadixBins + ((k >> shift) & mask), 1u);
+        const bool in = nw && (((u64)k >> hi) == ((u64)pre[t] >> hi));
+        // warp-aggregated increment: one atomic per distinct bin in the warp
+        const unsigned bin = in ? ((k >> shift) & mask) : 0xFFFFFFFFu;
+        const unsigned peers = __match_any_sync(live, bin);
+        if (in && (__ffs(peers) - 1) == (int)(threadIdx.x & 31u))
+          atomicAdd(s_hist + t * kRadixBins + bin, (unsigned)__popc(peers));
       }
     });
     __syncthreads();
@@ -578,7 +587,7 @@ __device__ bool radix_select(const Src& src, const char* lut, const Lasso& L, Se
     if (!grid_barrier(bar, target, &s->abort, err, timeout_ns)) return false;
     for (int t = 0; t < kTracks; ++t) {
       if (!s_act[t]) continue;
-      block_find_rank(gh + (size_t)t * kRadixBins, kRadixBins, s_r[t], &s_idx, &s_before, s_tmp);
+      block_find_rank(gh + (size_t)own[t] * kRadixBins, kRadixBins, s_r[t], &s_idx, &s_before, s_tmp);
       if (threadIdx.x == 0) {
         if (s_idx < 0) {         // fewer pixels than the rank: cannot happen
           record_error(err, SPCN_ERR_CUDA);
