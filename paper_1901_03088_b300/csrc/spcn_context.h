@@ -94,7 +94,7 @@ int ensure_candidate_capacity(Context* c, int n);
 
 // Shared-memory sizes of the pixel kernels.
 constexpr size_t kWindowSmem = kLutSmemBytes + sizeof(unsigned) * 2 * kWinGroups +
-                               sizeof(uint2) * 8 * kPassThreads;   // per-warp chunk queues of pass 1 (256 each)
+                               sizeof(uint2) * 2 * kPassThreads;   // per-warp chunk queues of pass 1 (64 each)
 constexpr size_t kRadixSmem = kLutSmemBytes + sizeof(unsigned) * kTracks * kRadixBins;
 
 int configure_pixel_kernels(Context* c);

@@ -383,7 +383,8 @@ __device__ void window_select(const WindowArgs& a) {
   }
 }
 
-constexpr int kWarpQueue = 256;   // queued chunks per warp (drained before a round could overflow it)
+constexpr int kWarpQueue = 64;    // queued chunks per warp; drained once 32 are waiting, so the
+                                  // re-read chunks are recent enough to still be in L2
 
 // Window-histogram updates of the queued chunks: each entry is a chunk index
 // and its two base-4 masks; only flagged pixels are recomputed (same
@@ -454,7 +455,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_window(WindowArgs a) {
     const unsigned ball = __ballot_sync(0xFFFFFFFFu, hit);
     if (hit) s_queue[qn + __popc(ball & ((1u << lane) - 1u))] = make_uint2((unsigned)q, packed);
     qn += __popc(ball);
-    if (qn > kWarpQueue - 32 || base + stride >= g.nchunks) {
+    if (qn >= 32 || base + stride >= g.nchunks) {
       __syncwarp();
       drain_queue(s_queue, qn, g, lut, lr, L, C, s_coarse);
       __syncwarp();
