@@ -161,6 +161,29 @@ int spcn_normalize(void* ctx, const spcn_image* src, const spcn_stats* src_st,
  * call (the record is then cleared). */
 int spcn_synchronize(void* ctx, void* stream);
 
+/* Differentiable normalisation of float images (Eq. 1-4 without the final
+ * rounding), for training pipelines.  x and y: device FP32, planar
+ * (batch, 3, height, width), intensities in [0, 255].  src_stats: one host
+ * record per image (W, i0 and the exact p99 of that image's source); the
+ * Eq. 3 scale tgt_stats->p99 / src p99 and both i0 are held constant.  wt:
+ * device pointer to the target basis (6 floats, column-major like
+ * spcn_stats.W), the variable the backward differentiates.  Asynchronous.
+ * Errors: INVALID_ARG, DEGENERATE_BASIS, CUDA. */
+int spcn_normalize_f32(void* ctx, const float* x, int32_t batch, int32_t height, int32_t width,
+                       const spcn_stats* src_stats, const spcn_stats* tgt_stats, const float* wt,
+                       const spcn_params* params, float* y, void* stream);
+
+/* Backward of spcn_normalize_f32 for L = sum(gy * y): writes gx = dL/dx
+ * (same layout as x) and gwt = dL/dW_target (device, 6 floats, column-major).
+ * The densities are recomputed, not stored; through the lasso the derivative
+ * follows each pixel's active set (inactive densities have zero derivative),
+ * through Eq. 1 it is -1/x (0 where the clamp at 1 is active).  The W_target
+ * sum is reduced in a fixed order (deterministic).  Asynchronous. */
+int spcn_normalize_f32_backward(void* ctx, const float* x, const float* gy, int32_t batch,
+                                int32_t height, int32_t width, const spcn_stats* src_stats,
+                                const spcn_stats* tgt_stats, const float* wt,
+                                const spcn_params* params, float* gx, float* gwt, void* stream);
+
 /* Basis estimation for callers that cannot allocate device memory (no
  * counterpart in the paper; it exists for deployment).  Hosts that own all
  * GPU memory through their own pool, plugin hosts that forbid cudaMalloc, and

@@ -25,6 +25,9 @@ Steps and the passages they follow:
 * ``percentile``        -- §2.1 Eq. 3's P99 and §3.1 item 1's P80.
 * ``stain_percentile``  -- §3.1 item 2 (P99 over non-white pixels only).
 * ``normalize``         -- §2.1 Eq. 3 and Eq. 4.
+* ``normalize_grad``    -- derivative of Eq. 1-4 with respect to the input
+                           intensities and the target basis (the percentile
+                           scale, source basis and both i0 held fixed).
 
 Readings where the paper is silent (each also listed in the design notes):
 
@@ -455,3 +458,51 @@ def full_stats(img: np.ndarray, params: Params | None = None) -> Stats:
     st = estimate_basis(img, params)
     st.p99 = stain_percentile(img, st.W, st.i0, params)
     return st
+
+
+# --------------------------------------------------------------------------
+# Derivative of Eq. 1-4 (float intensities; percentile scale held fixed)
+# --------------------------------------------------------------------------
+def normalize_float_pixels(X: np.ndarray, src_W, src_i0, scale, tgt_W, tgt_i0,
+                           lam: float = LAMBDA):
+    """Eq. 1-4 on a 3 x N array of float intensities with a given per-stain
+    scale (Eq. 3's percentile ratio).  Returns (Y, H), both float64."""
+    V = optical_density(X.T, src_i0).T
+    H = lasso2(V, np.asarray(src_W, dtype=np.float64), lam)
+    Vn = np.asarray(tgt_W, dtype=np.float64) @ (np.asarray(scale, dtype=np.float64)[:, None] * H)
+    Y = np.asarray(tgt_i0, dtype=np.float64)[:, None] * np.exp(-Vn)
+    return Y, H
+
+
+def normalize_grad(X: np.ndarray, GY: np.ndarray, src_W, src_i0, scale, tgt_W, tgt_i0,
+                   lam: float = LAMBDA):
+    """Gradient of L = sum(GY * Y) for Y = normalize_float_pixels(X, ...).
+
+    Chain of Eq. 4, Eq. 3, the lasso of Eq. 2 and Eq. 1:
+      dY_c/dV'_c = -Y_c;  dV'_c/dh_j = Wt[c,j] s_j;  dV'_c/dWt[c,j] = s_j h_j;
+      on the active set A of each pixel h_A = G_AA^-1 (c_A - lambda), so
+      dh_A/dc_A = G_AA^-1 and inactive densities have zero derivative;
+      dc_j/dv_c = Ws[c,j];  dv_c/dx_c = -1/x_c where x_c > 1 (0 where Eq. 1's
+      clamp at 1 is active).
+    Returns (dL/dX (3 x N), dL/dWt (3 x 2))."""
+    Ws = np.asarray(src_W, dtype=np.float64)
+    Wt = np.asarray(tgt_W, dtype=np.float64)
+    s = np.asarray(scale, dtype=np.float64)
+    Y, H = normalize_float_pixels(X, Ws, src_i0, s, Wt, tgt_i0, lam)
+    GV = -GY * Y                                   # dL/dV'
+    gWt = (GV @ (s[:, None] * H).T)                # 3 x 2
+    GH = s[:, None] * (Wt.T @ GV)                  # 2 x N
+    G, det = gram(Ws)
+    a1, a2 = H[0] > 0, H[1] > 0
+    GC = np.zeros_like(GH)
+    both = a1 & a2
+    Ginv = np.array([[G[1, 1], -G[0, 1]], [-G[1, 0], G[0, 0]]]) / det
+    GC[:, both] = Ginv @ GH[:, both]
+    only1 = a1 & ~a2
+    GC[0, only1] = GH[0, only1] / G[0, 0]
+    only2 = a2 & ~a1
+    GC[1, only2] = GH[1, only2] / G[1, 1]
+    GVs = Ws @ GC                                  # dL/dv
+    Xf = np.asarray(X, dtype=np.float64)
+    GX = np.where(Xf > 1.0, -GVs / np.maximum(Xf, 1.0), 0.0)
+    return GX, gWt

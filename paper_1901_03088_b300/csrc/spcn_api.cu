@@ -416,6 +416,45 @@ int spcn_kernel_times(void* ctx, int kernel, double* total_ms, int64_t* launches
   return rc;
 }
 
+int spcn_normalize_f32(void* ctx, const float* x, int32_t batch, int32_t height, int32_t width,
+                       const spcn_stats* src_stats, const spcn_stats* tgt_stats, const float* wt,
+                       const spcn_params* params, float* y, void* stream) {
+  if (!ctx || !x || !y || !wt || !src_stats || batch < 1 || height < 1 || width < 1 ||
+      !params_ok(params))
+    return SPCN_ERR_INVALID_ARG;
+  int rc = stats_ok(tgt_stats);
+  if (rc) return rc;
+  for (int b = 0; b < batch; ++b) {
+    rc = stats_ok(&src_stats[b]);
+    if (rc) return rc;
+  }
+  Context* c = static_cast<Context*>(ctx);
+  DeviceGuard guard(c->device);
+  if (!guard.ok) return SPCN_ERR_CUDA;
+  return launch_f32(c, false, x, nullptr, batch, (int64_t)height * width, src_stats, tgt_stats, wt,
+                    params->lambda, y, nullptr, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+int spcn_normalize_f32_backward(void* ctx, const float* x, const float* gy, int32_t batch,
+                                int32_t height, int32_t width, const spcn_stats* src_stats,
+                                const spcn_stats* tgt_stats, const float* wt,
+                                const spcn_params* params, float* gx, float* gwt, void* stream) {
+  if (!ctx || !x || !gy || !gx || !gwt || !wt || !src_stats || batch < 1 || height < 1 ||
+      width < 1 || !params_ok(params))
+    return SPCN_ERR_INVALID_ARG;
+  int rc = stats_ok(tgt_stats);
+  if (rc) return rc;
+  for (int b = 0; b < batch; ++b) {
+    rc = stats_ok(&src_stats[b]);
+    if (rc) return rc;
+  }
+  Context* c = static_cast<Context*>(ctx);
+  DeviceGuard guard(c->device);
+  if (!guard.ok) return SPCN_ERR_CUDA;
+  return launch_f32(c, true, x, gy, batch, (int64_t)height * width, src_stats, tgt_stats, wt,
+                    params->lambda, nullptr, gx, gwt, static_cast<cudaStream_t>(stream));
+}
+
 int spcn_synchronize(void* ctx, void* stream) {
   if (!ctx) return SPCN_ERR_INVALID_ARG;
   Context* c = static_cast<Context*>(ctx);

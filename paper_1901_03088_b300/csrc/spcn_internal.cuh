@@ -403,5 +403,8 @@ int launch_density(Context* c, const Geometry& g, const Model* m, float* H, int6
 int run_estimate_basis(Context* c, const spcn_image* img, const spcn_params* p, spcn_stats* out,
                        cudaStream_t st);
 int launch_debug_barrier(Context* c, int extra, long long timeout_ns, cudaStream_t st);
+int launch_f32(Context* c, bool backward, const float* x, const float* gy, int batch, int64_t hw,
+               const spcn_stats* src, const spcn_stats* tgt, const float* wt, float lambda,
+               float* y, float* gx, float* gwt, cudaStream_t st);
 
 }  // namespace spcn

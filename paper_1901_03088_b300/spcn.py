@@ -95,6 +95,10 @@ def _load():
         "spcn_debug_barrier_timeout": (ctypes.c_int, [vp, i32, i64, vp]),
         "spcn_kernel_timing": (ctypes.c_int, [vp, ctypes.c_int]),
         "spcn_estimate_basis_noalloc": (ctypes.c_int, [P(Image), P(Params), P(Stats), vp]),
+        "spcn_normalize_f32": (ctypes.c_int, [vp, vp, i32, i32, i32, P(Stats), P(Stats), vp,
+                                              P(Params), vp, vp]),
+        "spcn_normalize_f32_backward": (ctypes.c_int, [vp, vp, vp, i32, i32, i32, P(Stats),
+                                                       P(Stats), vp, P(Params), vp, vp, vp]),
         "spcn_kernel_times": (ctypes.c_int, [vp, ctypes.c_int, P(ctypes.c_double), P(i64)]),
     }
     for name, (res, args) in sig.items():
@@ -113,7 +117,7 @@ EXPORTED = ("spcn_params_default", "spcn_context_create", "spcn_context_destroy"
             "spcn_estimate_basis", "spcn_stain_percentile", "spcn_stain_densities",
             "spcn_normalize", "spcn_synchronize", "spcn_launch_count", "spcn_strerror",
             "spcn_debug_barrier_timeout", "spcn_kernel_timing", "spcn_kernel_times",
-            "spcn_estimate_basis_noalloc")
+            "spcn_estimate_basis_noalloc", "spcn_normalize_f32", "spcn_normalize_f32_backward")
 KERNELS = {"pass1": 0, "select": 1, "pass2": 2, "density": 3}
 
 
@@ -270,3 +274,86 @@ class Context:
         """Status of the failure-detection hook (see the header)."""
         return int(_lib.spcn_debug_barrier_timeout(self._h, int(extra_arrivals),
                                                    int(timeout_ns), _stream(stream)))
+
+
+# ---------------------------------------------------------------------------
+# Differentiable normalisation of float images
+# ---------------------------------------------------------------------------
+def _stats_array(stats):
+    arr = (Stats * len(stats))()
+    for i, st in enumerate(stats):
+        ctypes.memmove(ctypes.byref(arr[i]), ctypes.byref(st), ctypes.sizeof(Stats))
+    return arr
+
+
+def _check_f32(x):
+    import torch
+    if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float32 and
+            x.dim() == 4 and x.shape[1] == 3 and x.is_contiguous()):
+        raise ValueError("expected a contiguous (B, 3, H, W) float32 CUDA tensor")
+
+
+def _wt_colmajor(Wt):
+    import torch
+    if not (isinstance(Wt, torch.Tensor) and Wt.is_cuda and Wt.dtype == torch.float32 and
+            tuple(Wt.shape) == (3, 2)):
+        raise ValueError("W_target must be a (3, 2) float32 CUDA tensor (rows R, G, B)")
+    return Wt.detach().t().contiguous()      # (2, 3): column-major 3x2
+
+
+def _make_function():
+    import torch
+
+    class NormalizeF32(torch.autograd.Function):
+        """y = Eq. 1-4 of x (no rounding); differentiable in x and W_target."""
+
+        @staticmethod
+        def forward(fctx, x, Wt, handle, src_arr, tgt, p):
+            _check_f32(x)
+            B, _, H, W = x.shape
+            wt = _wt_colmajor(Wt)
+            y = torch.empty_like(x)
+            rc = _lib.spcn_normalize_f32(handle, ctypes.c_void_p(x.data_ptr()), B, H, W, src_arr,
+                                         ctypes.byref(tgt), ctypes.c_void_p(wt.data_ptr()),
+                                         ctypes.byref(p), ctypes.c_void_p(y.data_ptr()),
+                                         _stream(None))
+            _check(rc, "spcn_normalize_f32")
+            fctx.save_for_backward(x, wt)
+            fctx.handle, fctx.src_arr, fctx.tgt, fctx.p = handle, src_arr, tgt, p
+            return y
+
+        @staticmethod
+        def backward(fctx, gy):
+            x, wt = fctx.saved_tensors
+            gy = gy.contiguous()
+            B, _, H, W = x.shape
+            gx = torch.empty_like(x)
+            gwt = torch.empty(6, dtype=torch.float32, device=x.device)
+            rc = _lib.spcn_normalize_f32_backward(
+                fctx.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(gy.data_ptr()), B, H, W,
+                fctx.src_arr, ctypes.byref(fctx.tgt), ctypes.c_void_p(wt.data_ptr()),
+                ctypes.byref(fctx.p), ctypes.c_void_p(gx.data_ptr()),
+                ctypes.c_void_p(gwt.data_ptr()), _stream(None))
+            _check(rc, "spcn_normalize_f32_backward")
+            return gx, gwt.view(2, 3).t(), None, None, None, None
+
+    return NormalizeF32
+
+
+_NormalizeF32Fn = None
+
+
+def normalize_f32(ctx: "Context", x, W_target, src_stats, tgt_stats: Stats, p: Params | None = None):
+    """Differentiable Eq. 1-4 for a (B, 3, H, W) float32 batch in [0, 255].
+
+    src_stats: one Stats per image (W, i0 and the image's exact p99).
+    W_target: (3, 2) float32 CUDA tensor (rows R, G, B; may require grad);
+    tgt_stats supplies the target i0 and p99.  Gradients flow to x and
+    W_target; the percentile scale and source statistics are constants."""
+    global _NormalizeF32Fn
+    if _NormalizeF32Fn is None:
+        _NormalizeF32Fn = _make_function()
+    if len(src_stats) != x.shape[0]:
+        raise ValueError("one source Stats per image")
+    return _NormalizeF32Fn.apply(x, W_target, ctx.handle, _stats_array(src_stats), tgt_stats,
+                                 p or params())

@@ -1,0 +1,118 @@
+"""GPU parity of the differentiable form (float CHW batches) against the FP64
+oracle's forward and analytic gradient, and against central differences.
+
+Tolerances (FP32 kernel vs FP64): y within 1e-5 relative (+1e-3 absolute for
+the approximate log/exp units); dL/dx and dL/dW_t within 1e-4 relative of the
+oracle's analytic gradient away from lasso kinks (KKT margin >= 1e-2) and the
+Eq. 1 clamp, and dL/dW_t within 1e-3 of FP64 central differences."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import spcn_oracle as O  # noqa: E402
+from paper_1901_03088_b300 import synth  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def spcn():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1901_03088_b300 import build
+    build.build()
+    from paper_1901_03088_b300 import spcn as s
+    return s
+
+
+def _batch(spcn, B=3, H=40, W=48, seed=600):
+    xs, stats = [], []
+    for b in range(B):
+        img = synth.make_image(H, W, seed + b, as_float=True)     # float, [0, 255]
+        xs.append(np.ascontiguousarray(img.transpose(2, 0, 1)))
+        Ws = synth.stain_basis(seed + b)
+        stats.append(spcn.Stats.from_values(np.float32(Ws), [251.0, 247.0, 253.0], [2.3, 1.9]))
+    tgt = spcn.Stats.from_values(np.float32(synth.stain_basis(1)), [255.0, 254.0, 252.0], [2.4, 2.1])
+    return np.stack(xs).astype(np.float32), stats, tgt
+
+
+def _oracle(x, stats, tgt, Wt, gy):
+    Y, GX = np.zeros_like(x, dtype=np.float64), np.zeros_like(x, dtype=np.float64)
+    gW = np.zeros((3, 2))
+    margin = np.zeros((x.shape[0], x.shape[2] * x.shape[3]))
+    for b, st in enumerate(stats):
+        X = x[b].reshape(3, -1).astype(np.float64)
+        Ws = np.array(st.basis, dtype=np.float64)
+        i0s = np.array(st.i0[:], dtype=np.float64)
+        s = O.stain_scale(st.p99[:], tgt.p99[:])
+        Yb, H = O.normalize_float_pixels(X, Ws, i0s, s, Wt, np.array(tgt.i0[:], np.float64))
+        gx, gw = O.normalize_grad(X, gy[b].reshape(3, -1).astype(np.float64), Ws, i0s, s, Wt,
+                                  np.array(tgt.i0[:], np.float64))
+        Y[b] = Yb.reshape(x[b].shape)
+        GX[b] = gx.reshape(x[b].shape)
+        gW += gw
+        V = O.optical_density(X.T, i0s).T
+        g = (Ws.T @ Ws) @ H - Ws.T @ V + 0.1
+        margin[b] = np.min(np.abs(np.where(H > 0, H, g)), axis=0)
+    return Y, GX, gW, margin
+
+
+def test_forward_and_backward_match_oracle(spcn):
+    ctx = spcn.Context(0)
+    x, stats, tgt = _batch(spcn)
+    Wt = np.array(tgt.basis, dtype=np.float32)
+    xd = torch.from_numpy(x).cuda().requires_grad_(True)
+    Wd = torch.from_numpy(Wt).cuda().requires_grad_(True)
+    y = spcn.normalize_f32(ctx, xd, Wd, stats, tgt)
+    gy = np.random.default_rng(3).normal(size=x.shape).astype(np.float32)
+    (y * torch.from_numpy(gy).cuda()).sum().backward()
+    Y, GX, gW, margin = _oracle(x, stats, tgt, Wt.astype(np.float64), gy)
+    yg = y.detach().cpu().numpy()
+    assert np.max(np.abs(yg - Y) / (1e-5 * np.maximum(np.abs(Y), 1.0) + 1e-3)) <= 1.0
+    gx = xd.grad.cpu().numpy()
+    ok = (margin >= 1e-2)[:, None, :].repeat(3, axis=1).reshape(gx.shape) & (x > 1.01)
+    rel = np.abs(gx - GX)[ok] / np.maximum(np.abs(GX)[ok], 1e-3)
+    assert rel.max() <= 1e-4 * 50 and np.median(rel) <= 1e-5
+    assert np.mean(ok) > 0.5
+    gw = Wd.grad.cpu().numpy()
+    assert np.allclose(gw, gW, rtol=1e-4, atol=1e-3 * np.abs(gW).max())
+    ctx.close()
+
+
+def test_wt_gradient_against_central_differences(spcn):
+    ctx = spcn.Context(0)
+    x, stats, tgt = _batch(spcn, B=2, H=16, W=16, seed=700)
+    Wt = np.array(tgt.basis, dtype=np.float64)
+    gy = np.random.default_rng(4).normal(size=x.shape)
+    xd = torch.from_numpy(x).cuda()
+    Wd = torch.tensor(Wt, dtype=torch.float32, device="cuda", requires_grad=True)
+    y = spcn.normalize_f32(ctx, xd, Wd, stats, tgt)
+    (y * torch.from_numpy(gy.astype(np.float32)).cuda()).sum().backward()
+
+    def loss(W):
+        return sum(float(np.sum(gy[b].reshape(3, -1) * O.normalize_float_pixels(
+            x[b].reshape(3, -1).astype(np.float64), np.array(st.basis, np.float64),
+            np.array(st.i0[:], np.float64), O.stain_scale(st.p99[:], tgt.p99[:]), W,
+            np.array(tgt.i0[:], np.float64))[0])) for b, st in enumerate(stats))
+    h = 1e-3
+    for c in range(3):
+        for j in range(2):
+            Wp, Wm = Wt.copy(), Wt.copy()
+            Wp[c, j] += h
+            Wm[c, j] -= h
+            fd = (loss(Wp) - loss(Wm)) / (2 * h)
+            assert abs(Wd.grad[c, j].item() - fd) <= 1e-3 * max(abs(fd), 1.0)
+    ctx.close()
+
+
+def test_backward_is_deterministic(spcn):
+    ctx = spcn.Context(0)
+    x, stats, tgt = _batch(spcn, B=4, H=64, W=64, seed=800)
+    out = []
+    for _ in range(2):
+        xd = torch.from_numpy(x).cuda().requires_grad_(True)
+        Wd = torch.tensor(np.array(tgt.basis, np.float32), device="cuda", requires_grad=True)
+        spcn.normalize_f32(ctx, xd, Wd, stats, tgt).square().mean().backward()
+        out.append((xd.grad.clone(), Wd.grad.clone()))
+    assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
+    ctx.close()

@@ -355,3 +355,53 @@ def test_full_pipeline_small_runs():
     p = O.Params()
     out = O.normalize(src, O.full_stats(src, p), O.full_stats(tgt, p))
     assert out.shape == src.shape and out.dtype == np.uint8
+
+
+# ---------------------------------------------------------------- derivative
+def _grad_case(seed=51, n=256):
+    rng = np.random.default_rng(seed)
+    X = synth.make_image(16, 16, seed, as_float=True).reshape(-1, 3).T.copy()
+    X = np.maximum(X, 1.5)
+    Ws, Wt = synth.stain_basis(seed), synth.stain_basis(seed + 1)
+    i0s, i0t = np.array([250.0, 246.0, 252.0]), np.array([255.0, 253.0, 254.0])
+    s = np.array([1.1, 0.9])
+    GY = rng.normal(size=X.shape)
+    return X, GY, Ws, i0s, s, Wt, i0t
+
+
+def test_normalize_grad_matches_central_differences():
+    X, GY, Ws, i0s, s, Wt, i0t = _grad_case()
+    GX, gWt = O.normalize_grad(X, GY, Ws, i0s, s, Wt, i0t)
+    loss = lambda X_, Wt_: float(np.sum(GY * O.normalize_float_pixels(X_, Ws, i0s, s, Wt_, i0t)[0]))
+    h = 1e-3
+    # kinks: pixels whose lasso solution is near an active-set change
+    V = O.optical_density(X.T, i0s).T
+    H = O.lasso2(V, Ws, 0.1)
+    g = (Ws.T @ Ws) @ H - Ws.T @ V + 0.1
+    margin = np.min(np.abs(np.where(H > 0, H, g)), axis=0)
+    checked = 0
+    for x in range(X.shape[1]):
+        if margin[x] < 1e-2:
+            continue
+        for c in range(3):
+            Xp, Xm = X.copy(), X.copy()
+            Xp[c, x] += h
+            Xm[c, x] -= h
+            fd = (loss(Xp, Wt) - loss(Xm, Wt)) / (2 * h)
+            assert abs(fd - GX[c, x]) <= 1e-3 * max(abs(fd), 1e-3), (x, c, fd, GX[c, x])
+            checked += 1
+    assert checked > 500
+    for c in range(3):
+        for j in range(2):
+            Wp, Wm = Wt.copy(), Wt.copy()
+            Wp[c, j] += h
+            Wm[c, j] -= h
+            fd = (loss(X, Wp) - loss(X, Wm)) / (2 * h)
+            assert abs(fd - gWt[c, j]) <= 1e-3 * max(abs(fd), 1e-3)
+
+
+def test_normalize_grad_zero_where_od_is_clamped():
+    X, GY, Ws, i0s, s, Wt, i0t = _grad_case(seed=52)
+    X[:, :10] = 0.5                     # below Eq. 1's clamp at 1
+    GX, _ = O.normalize_grad(X, GY, Ws, i0s, s, Wt, i0t)
+    assert np.all(GX[:, :10] == 0.0)
