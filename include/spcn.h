@@ -214,7 +214,9 @@ typedef enum {
   SPCN_KERNEL_SELECT = 1,   /* exact radix select for ranks outside the window */
   SPCN_KERNEL_PASS2 = 2,    /* pass 2: densities, Eq. 3 scaling, Eq. 4, store */
   SPCN_KERNEL_DENSITY = 3,  /* density output pass */
-  SPCN_KERNEL_COUNT = 4
+  SPCN_KERNEL_F32_FWD = 4,  /* differentiable forward (float images) */
+  SPCN_KERNEL_F32_BWD = 5,  /* differentiable backward (float images) */
+  SPCN_KERNEL_COUNT = 6
 } spcn_kernel;
 
 /* Enable (1) or disable (0) CUDA-event timing of the kernels above on the

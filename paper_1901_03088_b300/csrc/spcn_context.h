@@ -59,8 +59,8 @@ struct Context {
   bool timing = false;
   std::vector<Timed> pending;
   std::vector<cudaEvent_t> pool;
-  double kernel_ms[SPCN_KERNEL_COUNT] = {0, 0, 0, 0};
-  int64_t kernel_n[SPCN_KERNEL_COUNT] = {0, 0, 0, 0};
+  double kernel_ms[SPCN_KERNEL_COUNT] = {};
+  int64_t kernel_n[SPCN_KERNEL_COUNT] = {};
 };
 
 // Brackets one launch with events when the context's timing is on.

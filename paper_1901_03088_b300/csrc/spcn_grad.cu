@@ -53,86 +53,162 @@ __device__ __forceinline__ float ex2_approx_g(float x) {
   return y;
 }
 
-// Densities of one pixel from its intensities (closed form of the lasso).
-__device__ __forceinline__ void f32_solve(const F32Img& I, const float (&xc)[3], float (&v)[3],
-                                          float& h1, float& h2) {
-#pragma unroll
-  for (int c = 0; c < 3; ++c) v[c] = I.l2i0[c] - lg2_approx(fmaxf(xc[c], 1.f));   // log2(i0/x)
-  const float d1 = fmaf(I.wd[2], v[2], fmaf(I.wd[1], v[1], I.wd[0] * v[0])) - I.lam[0];
-  const float d2 = fmaf(I.wd[5], v[2], fmaf(I.wd[4], v[1], I.wd[3] * v[0])) - I.lam[1];
-  const float D1 = fmaxf(d1, 0.f), D2 = fmaxf(d2, 0.f);
-  h1 = fminf(D1, fmaxf(0.f, I.kappa * fmaf(I.nrho1, D2, D1)));
-  h2 = fminf(D2, fmaxf(0.f, I.kappa * fmaf(I.nrho2, D1, D2)));
+// Per-image constants held in registers for the pixel loop.
+struct F32Reg {
+  float wd0, wd1, wd2, wd3, wd4, wd5, lam0, lam1, l20, l21, l22;
+  float nrho1, nrho2, kappa, s0, s1;
+};
+
+__device__ __forceinline__ F32Reg f32_reg(const F32Img& I) {
+  F32Reg r;
+  r.wd0 = I.wd[0]; r.wd1 = I.wd[1]; r.wd2 = I.wd[2];
+  r.wd3 = I.wd[3]; r.wd4 = I.wd[4]; r.wd5 = I.wd[5];
+  r.lam0 = I.lam[0]; r.lam1 = I.lam[1];
+  r.l20 = I.l2i0[0]; r.l21 = I.l2i0[1]; r.l22 = I.l2i0[2];
+  r.nrho1 = I.nrho1; r.nrho2 = I.nrho2; r.kappa = I.kappa;
+  r.s0 = I.s[0]; r.s1 = I.s[1];
+  return r;
 }
 
+// Densities of one pixel from its intensities (closed form of the lasso).
+__device__ __forceinline__ void f32_solve(const F32Reg& R, float x0, float x1, float x2,
+                                          float& h1, float& h2) {
+  const float v0 = R.l20 - lg2_approx(fmaxf(x0, 1.f));   // log2(i0/x); ln2 is folded into wd
+  const float v1 = R.l21 - lg2_approx(fmaxf(x1, 1.f));
+  const float v2 = R.l22 - lg2_approx(fmaxf(x2, 1.f));
+  const float d1 = fmaf(R.wd2, v2, fmaf(R.wd1, v1, fmaf(R.wd0, v0, -R.lam0)));
+  const float d2 = fmaf(R.wd5, v2, fmaf(R.wd4, v1, fmaf(R.wd3, v0, -R.lam1)));
+  const float D1 = fmaxf(d1, 0.f), D2 = fmaxf(d2, 0.f);
+  h1 = fminf(D1, fmaxf(0.f, R.kappa * fmaf(R.nrho1, D2, D1)));
+  h2 = fminf(D2, fmaxf(0.f, R.kappa * fmaf(R.nrho2, D1, D2)));
+}
+
+__device__ __forceinline__ float4 ld4(const float* p) { return __ldcs(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ void st4(float* p, float4 v) { __stcs(reinterpret_cast<float4*>(p), v); }
+__device__ __forceinline__ float& comp(float4& v, int k) {
+  return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
+}
+
+// Four consecutive pixels per thread (16-byte accesses per plane) when the
+// image size and pointers allow it, one pixel per step otherwise.
 __global__ void __launch_bounds__(kF32Threads) k_f32_forward(F32Args a) {
-  __shared__ float s_wt[6];
-  if (threadIdx.x < 6) s_wt[threadIdx.x] = a.wt[threadIdx.x];
-  __syncthreads();
-  // blockIdx.y selects the image, blockIdx.x strides over its pixels
   const int b = blockIdx.y;
-  const F32Img& I = a.img[b];
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.hw;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    const float* xb = a.x + (int64_t)b * 3 * a.hw + p;
-    const float xc[3] = {__ldcs(xb), __ldcs(xb + a.hw), __ldcs(xb + 2 * a.hw)};
-    float v[3], h1, h2;
-    f32_solve(I, xc, v, h1, h2);
-    const float sh1 = I.s[0] * h1, sh2 = I.s[1] * h2;
-    float* yb = a.y + (int64_t)b * 3 * a.hw + p;
+  const F32Reg R = f32_reg(a.img[b]);
+  float wt[6];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const float vp = fmaf(s_wt[c], sh1, s_wt[3 + c] * sh2);     // Eq. 3
-      __stcs(yb + c * a.hw, ex2_approx_g(fmaf(-1.4426950408889634f, vp, a.l2i0t[c])));   // Eq. 4
+  for (int k = 0; k < 6; ++k) wt[k] = __ldg(a.wt + k);
+  const float l2t0 = a.l2i0t[0], l2t1 = a.l2i0t[1], l2t2 = a.l2i0t[2];
+  const float* xb = a.x + (int64_t)b * 3 * a.hw;
+  float* yb = a.y + (int64_t)b * 3 * a.hw;
+  const bool vec = (a.hw & 3) == 0 && ((reinterpret_cast<uintptr_t>(a.x) | reinterpret_cast<uintptr_t>(a.y)) & 15) == 0;
+  const int64_t n4 = vec ? a.hw >> 2 : 0;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += (int64_t)gridDim.x * blockDim.x) {
+    float4 X0 = ld4(xb + 4 * q), X1 = ld4(xb + a.hw + 4 * q), X2 = ld4(xb + 2 * a.hw + 4 * q);
+    float4 Y0, Y1, Y2;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float h1, h2;
+      f32_solve(R, comp(X0, k), comp(X1, k), comp(X2, k), h1, h2);
+      const float sh1 = R.s0 * h1, sh2 = R.s1 * h2;
+      comp(Y0, k) = ex2_approx_g(fmaf(-1.4426950408889634f, fmaf(wt[0], sh1, wt[3] * sh2), l2t0));
+      comp(Y1, k) = ex2_approx_g(fmaf(-1.4426950408889634f, fmaf(wt[1], sh1, wt[4] * sh2), l2t1));
+      comp(Y2, k) = ex2_approx_g(fmaf(-1.4426950408889634f, fmaf(wt[2], sh1, wt[5] * sh2), l2t2));
     }
+    st4(yb + 4 * q, Y0);
+    st4(yb + a.hw + 4 * q, Y1);
+    st4(yb + 2 * a.hw + 4 * q, Y2);
+  }
+  for (int64_t p = 4 * n4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.hw;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    float h1, h2;
+    f32_solve(R, xb[p], xb[a.hw + p], xb[2 * a.hw + p], h1, h2);
+    const float sh1 = R.s0 * h1, sh2 = R.s1 * h2;
+    yb[p] = ex2_approx_g(fmaf(-1.4426950408889634f, fmaf(wt[0], sh1, wt[3] * sh2), l2t0));
+    yb[a.hw + p] = ex2_approx_g(fmaf(-1.4426950408889634f, fmaf(wt[1], sh1, wt[4] * sh2), l2t1));
+    yb[2 * a.hw + p] = ex2_approx_g(fmaf(-1.4426950408889634f, fmaf(wt[2], sh1, wt[5] * sh2), l2t2));
   }
 }
 
+struct F32Back {
+  float g00, g01, g11;   // G^-1
+  float ig11, ig22;
+  float ws0, ws1, ws2, ws3, ws4, ws5;
+};
+
+// One pixel of the backward: accumulates dL/dW_t into gw, returns dL/dx.
+__device__ __forceinline__ void f32_back_px(const F32Reg& R, const F32Back& B, const float (&wt)[6],
+                                            float l2t0, float l2t1, float l2t2, float x0, float x1,
+                                            float x2, float g0, float g1, float g2, float (&gw)[6],
+                                            float& gx0, float& gx1, float& gx2) {
+  float h1, h2;
+  f32_solve(R, x0, x1, x2, h1, h2);
+  const float sh1 = R.s0 * h1, sh2 = R.s1 * h2;
+  // Eq. 4 again (y is not stored), then dL/dV'_c = -g_c y_c
+  const float gv0 = -g0 * ex2_approx_g(fmaf(-1.4426950408889634f, fmaf(wt[0], sh1, wt[3] * sh2), l2t0));
+  const float gv1 = -g1 * ex2_approx_g(fmaf(-1.4426950408889634f, fmaf(wt[1], sh1, wt[4] * sh2), l2t1));
+  const float gv2 = -g2 * ex2_approx_g(fmaf(-1.4426950408889634f, fmaf(wt[2], sh1, wt[5] * sh2), l2t2));
+  gw[0] = fmaf(gv0, sh1, gw[0]);
+  gw[1] = fmaf(gv1, sh1, gw[1]);
+  gw[2] = fmaf(gv2, sh1, gw[2]);
+  gw[3] = fmaf(gv0, sh2, gw[3]);
+  gw[4] = fmaf(gv1, sh2, gw[4]);
+  gw[5] = fmaf(gv2, sh2, gw[5]);
+  const float gh1 = R.s0 * fmaf(wt[2], gv2, fmaf(wt[1], gv1, wt[0] * gv0));
+  const float gh2 = R.s1 * fmaf(wt[5], gv2, fmaf(wt[4], gv1, wt[3] * gv0));
+  // through the active-set solution of the lasso (branch-free)
+  const bool a1 = h1 > 0.f, a2 = h2 > 0.f;
+  const float gb1 = fmaf(B.g00, gh1, B.g01 * gh2), gb2 = fmaf(B.g01, gh1, B.g11 * gh2);
+  const float gc1 = (a1 && a2) ? gb1 : (a1 ? gh1 * B.ig11 : 0.f);
+  const float gc2 = (a1 && a2) ? gb2 : (a2 ? gh2 * B.ig22 : 0.f);
+  // dL/dv_c, then Eq. 1: dv_c/dx_c = -1/x_c above the clamp
+  gx0 = x0 > 1.f ? __fdividef(-fmaf(B.ws0, gc1, B.ws3 * gc2), x0) : 0.f;
+  gx1 = x1 > 1.f ? __fdividef(-fmaf(B.ws1, gc1, B.ws4 * gc2), x1) : 0.f;
+  gx2 = x2 > 1.f ? __fdividef(-fmaf(B.ws2, gc1, B.ws5 * gc2), x2) : 0.f;
+}
+
 __global__ void __launch_bounds__(kF32Threads) k_f32_backward(F32Args a) {
-  __shared__ float s_wt[6];
   __shared__ double s_red[kF32Threads / 32][6];
-  if (threadIdx.x < 6) s_wt[threadIdx.x] = a.wt[threadIdx.x];
-  __syncthreads();
-  float gw[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   const int b = blockIdx.y;
   const F32Img& I = a.img[b];
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.hw;
+  const F32Reg R = f32_reg(I);
+  F32Back B;
+  B.g00 = I.ginv[0]; B.g01 = I.ginv[1]; B.g11 = I.ginv[2];
+  B.ig11 = I.ig11; B.ig22 = I.ig22;
+  B.ws0 = I.ws[0]; B.ws1 = I.ws[1]; B.ws2 = I.ws[2];
+  B.ws3 = I.ws[3]; B.ws4 = I.ws[4]; B.ws5 = I.ws[5];
+  float wt[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) wt[k] = __ldg(a.wt + k);
+  const float l2t0 = a.l2i0t[0], l2t1 = a.l2i0t[1], l2t2 = a.l2i0t[2];
+  float gw[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  const int64_t base = (int64_t)b * 3 * a.hw;
+  const float* xb = a.x + base;
+  const float* gb = a.gy + base;
+  float* gxb = a.gx + base;
+  const bool vec = (a.hw & 3) == 0 &&
+                   ((reinterpret_cast<uintptr_t>(a.x) | reinterpret_cast<uintptr_t>(a.gy) |
+                     reinterpret_cast<uintptr_t>(a.gx)) & 15) == 0;
+  const int64_t n4 = vec ? a.hw >> 2 : 0;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += (int64_t)gridDim.x * blockDim.x) {
+    float4 X0 = ld4(xb + 4 * q), X1 = ld4(xb + a.hw + 4 * q), X2 = ld4(xb + 2 * a.hw + 4 * q);
+    float4 G0 = ld4(gb + 4 * q), G1 = ld4(gb + a.hw + 4 * q), G2 = ld4(gb + 2 * a.hw + 4 * q);
+    float4 O0, O1, O2;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      f32_back_px(R, B, wt, l2t0, l2t1, l2t2, comp(X0, k), comp(X1, k), comp(X2, k), comp(G0, k),
+                  comp(G1, k), comp(G2, k), gw, comp(O0, k), comp(O1, k), comp(O2, k));
+    st4(gxb + 4 * q, O0);
+    st4(gxb + a.hw + 4 * q, O1);
+    st4(gxb + 2 * a.hw + 4 * q, O2);
+  }
+  for (int64_t p = 4 * n4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.hw;
        p += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t off = (int64_t)b * 3 * a.hw + p;
-    const float xc[3] = {__ldcs(a.x + off), __ldcs(a.x + off + a.hw), __ldcs(a.x + off + 2 * a.hw)};
-    const float g[3] = {__ldcs(a.gy + off), __ldcs(a.gy + off + a.hw), __ldcs(a.gy + off + 2 * a.hw)};
-    float v[3], h1, h2;
-    f32_solve(I, xc, v, h1, h2);
-    const float sh1 = I.s[0] * h1, sh2 = I.s[1] * h2;
-    float gh1 = 0.f, gh2 = 0.f;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const float vp = fmaf(s_wt[c], sh1, s_wt[3 + c] * sh2);
-      const float yc = ex2_approx_g(fmaf(-1.4426950408889634f, vp, a.l2i0t[c]));
-      const float gv = -g[c] * yc;                  // dL/dV'_c
-      gw[c] = fmaf(gv, sh1, gw[c]);                 // dL/dW_t[c,0]
-      gw[3 + c] = fmaf(gv, sh2, gw[3 + c]);         // dL/dW_t[c,1]
-      gh1 = fmaf(s_wt[c], gv, gh1);
-      gh2 = fmaf(s_wt[3 + c], gv, gh2);
-    }
-    gh1 *= I.s[0];
-    gh2 *= I.s[1];
-    // through the active-set solution of the lasso
-    float gc1 = 0.f, gc2 = 0.f;
-    if (h1 > 0.f && h2 > 0.f) {
-      gc1 = fmaf(I.ginv[0], gh1, I.ginv[1] * gh2);
-      gc2 = fmaf(I.ginv[1], gh1, I.ginv[2] * gh2);
-    } else if (h1 > 0.f) {
-      gc1 = gh1 * I.ig11;
-    } else if (h2 > 0.f) {
-      gc2 = gh2 * I.ig22;
-    }
-    float* gxb = a.gx + off;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const float gvc = fmaf(I.ws[c], gc1, I.ws[3 + c] * gc2);          // dL/dv_c
-      __stcs(gxb + c * a.hw, xc[c] > 1.f ? __fdividef(-gvc, xc[c]) : 0.f);   // Eq. 1
-    }
+    float o0, o1, o2;
+    f32_back_px(R, B, wt, l2t0, l2t1, l2t2, xb[p], xb[a.hw + p], xb[2 * a.hw + p], gb[p],
+                gb[a.hw + p], gb[2 * a.hw + p], gw, o0, o1, o2);
+    gxb[p] = o0;
+    gxb[a.hw + p] = o1;
+    gxb[2 * a.hw + p] = o2;
   }
   // block sums of dL/dW_t in FP64, fixed order
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -199,7 +275,7 @@ int launch_f32(Context* c, bool backward, const float* x, const float* gy, int b
                const spcn_stats* src, const spcn_stats* tgt, const float* wt, float lambda,
                float* y, float* gx, float* gwt, cudaStream_t st) {
   F32Args a;   // ~17 KB parameter block, passed by value to each launch
-  int bx = (int)((hw + kF32Threads * 4 - 1) / (kF32Threads * 4));   // about 4 pixels per thread
+  int bx = (int)((hw + kF32Threads * 8 - 1) / (kF32Threads * 8));   // about 8 pixels per thread
   if (bx < 1) bx = 1;
   if (bx > 1024) bx = 1024;
   const int launches = (batch + kF32MaxBatch - 1) / kF32MaxBatch;
@@ -219,8 +295,11 @@ int launch_f32(Context* c, bool backward, const float* x, const float* gy, int b
     for (int k = 0; k < 3; ++k) a.l2i0t[k] = (float)log2((double)tgt->i0[k]);
     for (int i = 0; i < nb; ++i) f32_image_consts(&src[b0 + i], tgt, lambda, &a.img[i]);
     const dim3 grid(bx, nb);
-    if (backward) k_f32_backward<<<grid, kF32Threads, 0, st>>>(a);
-    else k_f32_forward<<<grid, kF32Threads, 0, st>>>(a);
+    {
+      TimedLaunch tl(c, backward ? SPCN_KERNEL_F32_BWD : SPCN_KERNEL_F32_FWD, st);
+      if (backward) k_f32_backward<<<grid, kF32Threads, 0, st>>>(a);
+      else k_f32_forward<<<grid, kF32Threads, 0, st>>>(a);
+    }
     SPCN_LAUNCH_CHECK(c);
   }
   if (backward) {

@@ -118,7 +118,7 @@ EXPORTED = ("spcn_params_default", "spcn_context_create", "spcn_context_destroy"
             "spcn_normalize", "spcn_synchronize", "spcn_launch_count", "spcn_strerror",
             "spcn_debug_barrier_timeout", "spcn_kernel_timing", "spcn_kernel_times",
             "spcn_estimate_basis_noalloc", "spcn_normalize_f32", "spcn_normalize_f32_backward")
-KERNELS = {"pass1": 0, "select": 1, "pass2": 2, "density": 3}
+KERNELS = {"pass1": 0, "select": 1, "pass2": 2, "density": 3, "f32_fwd": 4, "f32_bwd": 5}
 
 
 def params(**kw) -> Params:
@@ -279,7 +279,10 @@ class Context:
 # ---------------------------------------------------------------------------
 # Differentiable normalisation of float images
 # ---------------------------------------------------------------------------
-def _stats_array(stats):
+def stats_array(stats):
+    """Contiguous C array of Stats records (build once, pass to normalize_f32)."""
+    if isinstance(stats, ctypes.Array):
+        return stats
     arr = (Stats * len(stats))()
     for i, st in enumerate(stats):
         ctypes.memmove(ctypes.byref(arr[i]), ctypes.byref(st), ctypes.sizeof(Stats))
@@ -346,7 +349,8 @@ _NormalizeF32Fn = None
 def normalize_f32(ctx: "Context", x, W_target, src_stats, tgt_stats: Stats, p: Params | None = None):
     """Differentiable Eq. 1-4 for a (B, 3, H, W) float32 batch in [0, 255].
 
-    src_stats: one Stats per image (W, i0 and the image's exact p99).
+    src_stats: one Stats per image (W, i0 and the image's exact p99), as a
+    list or as a prebuilt ``stats_array``.
     W_target: (3, 2) float32 CUDA tensor (rows R, G, B; may require grad);
     tgt_stats supplies the target i0 and p99.  Gradients flow to x and
     W_target; the percentile scale and source statistics are constants."""
@@ -355,5 +359,5 @@ def normalize_f32(ctx: "Context", x, W_target, src_stats, tgt_stats: Stats, p: P
         _NormalizeF32Fn = _make_function()
     if len(src_stats) != x.shape[0]:
         raise ValueError("one source Stats per image")
-    return _NormalizeF32Fn.apply(x, W_target, ctx.handle, _stats_array(src_stats), tgt_stats,
+    return _NormalizeF32Fn.apply(x, W_target, ctx.handle, stats_array(src_stats), tgt_stats,
                                  p or params())

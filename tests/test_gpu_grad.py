@@ -2,9 +2,11 @@
 oracle's forward and analytic gradient, and against central differences.
 
 Tolerances (FP32 kernel vs FP64): y within 1e-5 relative (+1e-3 absolute for
-the approximate log/exp units); dL/dx and dL/dW_t within 1e-4 relative of the
-oracle's analytic gradient away from lasso kinks (KKT margin >= 1e-2) and the
-Eq. 1 clamp, and dL/dW_t within 1e-3 of FP64 central differences."""
+the approximate log/exp units); dL/dx, relative to max(|dL/dx|, 1e-3), within
+1e-6 at the median, 1e-4 at the 99.9th percentile and 1e-3 at the maximum of
+the pixels away from lasso kinks (KKT margin >= 1e-2) and the Eq. 1 clamp
+(measured: 8e-8, 5e-5, 3e-4); dL/dW_t within 1e-5 relative of the oracle
+(measured 6e-7) and within 1e-3 of FP64 central differences."""
 import numpy as np
 import pytest
 
@@ -72,10 +74,10 @@ def test_forward_and_backward_match_oracle(spcn):
     gx = xd.grad.cpu().numpy()
     ok = (margin >= 1e-2)[:, None, :].repeat(3, axis=1).reshape(gx.shape) & (x > 1.01)
     rel = np.abs(gx - GX)[ok] / np.maximum(np.abs(GX)[ok], 1e-3)
-    assert rel.max() <= 1e-4 * 50 and np.median(rel) <= 1e-5
+    assert np.median(rel) <= 1e-6 and np.quantile(rel, 0.999) <= 1e-4 and rel.max() <= 1e-3
     assert np.mean(ok) > 0.5
     gw = Wd.grad.cpu().numpy()
-    assert np.allclose(gw, gW, rtol=1e-4, atol=1e-3 * np.abs(gW).max())
+    assert np.max(np.abs(gw - gW)) <= 1e-5 * np.abs(gW).max()
     ctx.close()
 
 
