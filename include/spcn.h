@@ -204,6 +204,92 @@ int spcn_normalize_f32_backward(void* ctx, const float* x, const float* gy, int3
 int spcn_estimate_basis_noalloc(const spcn_image* img, const spcn_params* params,
                                 spcn_stats* out, void* stream);
 
+/* ------------------------------------------------------------------ batches
+ * Batched normalisation (§3.2: a batch of source images normalised to one
+ * target).  Many tiles of any sizes, each with its own source statistics (W,
+ * i0; p99 only guides the search window, as in spcn_normalize), are
+ * normalised to one target by ONE cooperative persistent launch.  Every
+ * tile's output bytes and percentiles are identical to what spcn_normalize
+ * gives for that tile alone; only the schedule differs.
+ *
+ * A batch object fixes the tile table (pointers, sizes, pitches, statistics,
+ * outputs) and owns the device state of a run; spcn_batch_run can then be
+ * repeated, and captured into a CUDA graph, as long as the buffers it names
+ * stay allocated.  The launch works through a queue of work items of
+ * `item_chunks` 16-pixel chunks: pass-1 items (densities, non-white count,
+ * keys inside the P99 window), then pass-2 items (reconstruction) of tiles
+ * whose percentile is known.  The last block to finish a tile's pass 1
+ * selects its percentile; tiles whose ranks fell outside the window are
+ * finished after the queue by an exact radix select over the whole grid. */
+
+typedef enum {
+  SPCN_SCHED_PHASED = 0,       /* all pass-1 items, then all pass-2 items */
+  SPCN_SCHED_INTERLEAVED = 1   /* groups of about group_px pixels: pass 1 of group g+1
+                                  is queued before pass 2 of group g, so pass 2
+                                  rereads recently read tiles */
+} spcn_schedule;
+
+typedef struct {
+  int32_t item_chunks;   /* chunks (16 px) per work item, >= 1024; multiple of 1024 */
+  int32_t schedule;      /* spcn_schedule */
+  int64_t group_px;      /* SPCN_SCHED_INTERLEAVED: pixels per group */
+  float ms;              /* spcn_batch_tune: measured mean time of one run */
+  int32_t pad;
+} spcn_batch_config;
+
+/* Create a batch of n >= 1 tiles on ctx's device.  tiles[i], tile_stats[i],
+ * outs[i] (device, out_pitches[i] >= 3 * width) describe tile i; tgt_st is
+ * the one target.  The host arrays are copied; the device buffers are not
+ * (the caller keeps them allocated while the batch is used).  An output must
+ * not overlap its own source (INVALID_ARG); it must not overlap another
+ * tile's source or output either (not checked: results are then undefined).
+ * Builds the per-statistics tables (tiles with bitwise-equal W and i0 share
+ * one) and allocates the batch state; blocks the host.  Errors: INVALID_ARG,
+ * DEGENERATE_BASIS, OOM, CUDA. */
+int spcn_batch_create(void* ctx, int32_t n, const spcn_image* tiles,
+                      const spcn_stats* tile_stats, const spcn_stats* tgt_st,
+                      const spcn_params* params, uint8_t* const* outs,
+                      const int64_t* out_pitches, void** batch);
+
+/* Normalise every tile of the batch: one memset of the batch state and one
+ * cooperative kernel launch on `stream`.  Asynchronous, allocates nothing and
+ * may be captured into a CUDA graph.  Errors: INVALID_ARG, CUDA. */
+int spcn_batch_run(void* batch, void* stream);
+
+/* Wait for the batch's last run on `stream` and read its results: p99_out
+ * (host, 2n doubles, tile-major: tile i's stains at 2i, 2i+1), status_out
+ * (host, n: SPCN_OK or SPCN_ERR_NO_TISSUE per tile) and fallback_out (host,
+ * n: 1 where the tile's percentile needed the exact radix select over its
+ * pixels because a rank lay below the window), each optional.  Returns
+ * SPCN_ERR_TIMEOUT if a wait of the run gave up, else SPCN_OK. */
+int spcn_batch_results(void* batch, double* p99_out, int32_t* status_out, int32_t* fallback_out,
+                       void* stream);
+
+/* Read or replace the batch's schedule (spcn_batch_set_config rebuilds the
+ * work queue; blocks the host). */
+int spcn_batch_get_config(void* batch, spcn_batch_config* cfg);
+int spcn_batch_set_config(void* batch, const spcn_batch_config* cfg);
+
+/* Autotuner: run the batch under each candidate schedule (item sizes x
+ * phased / interleaved groups), one untimed run then `reps` timed runs each
+ * (CUDA events on `stream`), keep the fastest.  trials (host, optional,
+ * max_trials entries) receives every candidate with its mean time;
+ * *n_trials the number written.  The outputs are rewritten by every run
+ * (with the same bytes).  Blocks the host. */
+int spcn_batch_tune(void* batch, int32_t reps, spcn_batch_config* trials, int32_t max_trials,
+                    int32_t* n_trials, void* stream);
+
+/* Release the batch's device state.  NULL is accepted. */
+int spcn_batch_destroy(void* batch);
+
+/* One-shot form: create, run, read the results, destroy.  p99_out and
+ * status_out as in spcn_batch_results.  Blocks the host. */
+int spcn_normalize_batched(void* ctx, int32_t n, const spcn_image* tiles,
+                           const spcn_stats* tile_stats, const spcn_stats* tgt_st,
+                           const spcn_params* params, uint8_t* const* outs,
+                           const int64_t* out_pitches, double* p99_out, int32_t* status_out,
+                           void* stream);
+
 /* Number of kernels the context has launched since creation (for launch
  * accounting in benchmarks). */
 int64_t spcn_launch_count(void* ctx);
@@ -216,7 +302,8 @@ typedef enum {
   SPCN_KERNEL_DENSITY = 3,  /* density output pass */
   SPCN_KERNEL_F32_FWD = 4,  /* differentiable forward (float images) */
   SPCN_KERNEL_F32_BWD = 5,  /* differentiable backward (float images) */
-  SPCN_KERNEL_COUNT = 6
+  SPCN_KERNEL_BATCH = 6,    /* batched persistent launch (spcn_batch_run) */
+  SPCN_KERNEL_COUNT = 7
 } spcn_kernel;
 
 /* Enable (1) or disable (0) CUDA-event timing of the kernels above on the

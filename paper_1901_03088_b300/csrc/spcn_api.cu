@@ -12,21 +12,6 @@
 
 namespace spcn {
 
-// Selects the context's device for the duration of a call and restores the
-// caller's device afterwards.
-struct DeviceGuard {
-  int prev = -1;
-  bool ok = false;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) return;
-    ok = (prev == dev) || (cudaSetDevice(dev) == cudaSuccess);
-  }
-  ~DeviceGuard() {
-    int cur = -1;
-    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-  }
-};
-
 int ensure_sample_capacity(Context* c, size_t n) {
   if (n == 0) n = 1;
   const size_t nblk = (n + 4095) / 4096;
@@ -114,14 +99,14 @@ static void free_all(Context* c) {
 }
 
 // ---------------------------------------------------------------- validation
-static bool image_ok(const spcn_image* img) {
+bool image_ok(const spcn_image* img) {
   if (!img || !img->data || img->width < 1 || img->height < 1) return false;
   if (img->pitch_bytes < 3ll * img->width) return false;
   const long long npx = (long long)img->width * img->height;
   return npx < (1ll << 36);
 }
 
-static bool params_ok(const spcn_params* p) {
+bool params_ok(const spcn_params* p) {
   if (!p) return false;
   if (!(p->lambda >= 0.f) || !std::isfinite(p->lambda)) return false;
   if (p->white_thresh < 0 || p->white_thresh > 255) return false;
@@ -141,7 +126,7 @@ static bool params_ok(const spcn_params* p) {
 }
 
 // A usable basis and i0: finite, W >= 0, columns not parallel, i0 in [1,255].
-static int stats_ok(const spcn_stats* s) {
+int stats_ok(const spcn_stats* s) {
   if (!s) return SPCN_ERR_INVALID_ARG;
   for (int i = 0; i < 6; ++i)
     if (!std::isfinite(s->W[i]) || s->W[i] < 0.f) return SPCN_ERR_INVALID_ARG;
@@ -159,7 +144,7 @@ static int stats_ok(const spcn_stats* s) {
   return SPCN_OK;
 }
 
-static Geometry make_geometry(const spcn_image* img, uint8_t* out, int64_t out_pitch) {
+Geometry make_geometry(const spcn_image* img, uint8_t* out, int64_t out_pitch) {
   Geometry g;
   memset(&g, 0, sizeof(g));
   g.src = img->data;

@@ -1,0 +1,1015 @@
+// Batched normalisation: many tiles, each with its own source statistics,
+// normalised to one target in one cooperative persistent launch (the batch
+// form of §3.2, "sources normalised to one target").  Per tile the launch
+// computes exactly what the single-image path computes (Eq. 1-4 with the
+// exact non-white P99 of Eq. 3): the same tables, the same closed-form H-step,
+// the same keys and the same reconstruction, so every output byte and every
+// percentile equals that of spcn_normalize on the tile alone.
+//
+// Schedule.  The launch works through one queue of work items (a range of a
+// tile's 16-pixel chunks and a pass), claimed with an atomic ticket:
+//   pass-1 item  densities of every pixel, non-white and below-window counts,
+//                and the FP32 keys at or above the tile's window start,
+//                appended to the tile's key lists (per-warp shared-memory
+//                buffers, flushed with one atomic reservation each);
+//   tile select  the block finishing a tile's last pass-1 item selects the
+//                wanted ranks from the key lists (radix select with 12-bit
+//                digits over key - start) and publishes the scale factors;
+//   pass-2 item  waits (bounded) for its tile's scale, then reconstructs.
+// Every pass-1 item of a tile precedes its pass-2 items in the queue, so the
+// waits end without any grid-wide barrier.
+//
+// Window.  Tiles of one slide share the slide's statistics, but each tile's
+// own P99 differs from the slide's by up to about +-25% (tissue content varies
+// from tile to tile), so a narrow two-sided window around the hint misses
+// often.  The window here is open-ended: [kOpenLow * hint, +inf).  Only ranks
+// whose density lies below the window start (or a list that overflowed)
+// leave a tile to the exact radix select over its pixels, run by the whole
+// grid after the queue, followed by the tile's pass 2.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "spcn_context.h"
+#include "spcn_internal.cuh"
+#include "spcn_pixel.cuh"
+
+namespace spcn {
+
+constexpr int kKeyBuf = 128;       // keys per stain buffered per warp before a flush
+constexpr int kSelBits = 12;       // digit width of the in-list select
+constexpr int kSelBins = 1 << kSelBits;
+constexpr double kOpenLow = 0.75;  // window start, relative to the hint
+constexpr int kWarps = kPassThreads / 32;
+constexpr size_t kBatchQueueBytes = sizeof(uint2) * kWarpQueue * kWarps;
+constexpr size_t kBatchWork = kBatchQueueBytes + sizeof(unsigned) * 2 * kKeyBuf * kWarps;
+constexpr size_t kBatchSmem = kLutSmemBytes + kBatchWork;
+static_assert(kBatchWork >= sizeof(unsigned) * kTracks * kRadixBins, "radix histograms overlay the pass-1 buffers");
+static_assert(kBatchWork >= sizeof(unsigned) * 2 * kSelBins, "select histograms overlay the pass-1 buffers");
+static_assert(kSelBins % kPassThreads == 0, "whole bins per thread");
+
+// One tile of the batch (device, read-only during a run).
+struct BatchTile {
+  Geometry g;
+  unsigned model;          // index of the tile's table
+  unsigned n_items1;       // pass-1 items of the tile
+  unsigned lo[2];          // window start key per stain (keys >= lo are listed)
+  unsigned win[2];         // 0: no window (no hint): the stain takes the exact fallback
+  float nk[2], lk[2];      // exact [h~ < lo] test (nk = 0, lk = 1 without a window)
+  unsigned* keys;          // stain-0 key list; stain 1 at keys + list_cap
+  u64 list_cap;            // keys per stain
+};
+
+// Per-tile state of a run (zeroed before every run).
+struct BatchTileState {
+  SelectState sel;         // counts, ranks, keys, percentiles, scale; fallback barrier
+  u64 list_n[2];           // keys appended (may exceed list_cap: overflow)
+  unsigned kmax[2];        // largest key appended
+  unsigned done1;          // finished pass-1 items
+  int ready;               // 0: pass 1 running, 1: scale known, 2: exact fallback needed
+  int status;              // SPCN_OK or SPCN_ERR_NO_TISSUE
+  int fallback;            // 1: the percentile needed the exact fallback
+};
+
+// Run-wide state (zeroed before every run).
+struct BatchRunState {
+  unsigned next;           // work-queue ticket
+  unsigned barrier;        // grid barrier counter of the fallback phase
+  int abort;               // a wait gave up
+  int err;                 // first error of the run
+};
+
+struct BatchItem {
+  unsigned tile;
+  unsigned pass;           // 1 or 2
+  u64 c0, c1;              // chunk range [c0, c1) of the tile
+};
+
+struct BatchArgs {
+  const BatchTile* tiles;
+  BatchTileState* state;
+  const BatchItem* items;
+  const Model* models;
+  u64* rhist;
+  BatchRunState* run;
+  unsigned n_items, n_tiles;
+  unsigned wthr;           // (white threshold + 1) << 8, compared with table offsets
+  unsigned thr;            // white threshold
+  double pct;
+  double tgt0, tgt1;       // target percentiles
+  float Wt[6];             // target basis
+  float l2i0[3];           // log2 of the target i0
+  long long timeout_ns;
+};
+
+__device__ __forceinline__ int ld_acquire_s32(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_s32(int* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+
+// Bounded wait of one thread for a tile's ready word.  Returns the word (1
+// or 2), or -1 when the run was aborted or the wait gave up (then the abort
+// word and TIMEOUT are recorded).
+__device__ int wait_ready(const int* ready, int* abort, int* err, long long timeout_ns) {
+  const unsigned long long t0 = global_timer_ns();
+  for (;;) {
+    const int v = ld_acquire_s32(ready);
+    if (v != 0) return v;
+    if (*(volatile int*)abort != 0) return -1;
+    if ((long long)(global_timer_ns() - t0) > timeout_ns) {
+      atomicExch(abort, 1);
+      record_error(err, SPCN_ERR_TIMEOUT);
+      return -1;
+    }
+    __nanosleep(256);
+  }
+}
+
+// Append a warp's buffered keys to a tile's list: one atomic reservation,
+// then coalesced stores; keys past the capacity are counted but dropped.  The
+// largest key is kept for the select's digit count.  kc is warp-uniform.
+__device__ __forceinline__ void flush_keys(const unsigned* kb, int kc, unsigned* list, u64 cap,
+                                           u64* list_n, unsigned* kmax) {
+  if (kc == 0) return;
+  const unsigned lane = threadIdx.x & 31u;
+  u64 base = 0;
+  if (lane == 0) base = atomicAdd(list_n, (u64)kc);
+  base = __shfl_sync(0xFFFFFFFFu, base, 0);
+  unsigned m = 0u;
+  for (int i = (int)lane; i < kc; i += 32) {
+    const unsigned k = kb[i];
+    m = max(m, k);
+    if (base + (u64)i < cap) list[base + i] = k;
+  }
+  m = __reduce_max_sync(0xFFFFFFFFu, m);
+  if (lane == 0) atomicMax(kmax, m);
+}
+
+// Keys of the queued chunks' flagged pixels (same arithmetic as pass 1, so
+// the same keys), appended to the warp's key buffers.  Warp-uniform: every
+// lane runs the same number of steps, one flagged pixel per lane and step.
+// The tile's list pointers are read here, not held by the pixel loop.
+template <class G>
+__device__ __noinline__ void batch_drain(const uint2* queue, int count, u64 c0, const G& g,
+                                         const char* lut, unsigned lr, const Lasso& L,
+                                         unsigned* kb0, unsigned* kb1, int& kc0, int& kc1,
+                                         const BatchTile* T, BatchTileState* S) {
+  const u64 cap = T->list_cap;
+  unsigned* list0 = T->keys;
+  unsigned* list1 = list0 + cap;
+  const unsigned lo0 = T->win[0] ? T->lo[0] : 0xFFFFFFFFu;
+  const unsigned lo1 = T->win[1] ? T->lo[1] : 0xFFFFFFFFu;
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int e0 = 0; e0 < count; e0 += 32) {
+    unsigned m = 0u;
+    const uint8_t* src = g.src;
+    if (e0 + (int)lane < count) {
+      const uint2 ent = queue[e0 + lane];
+      const ChunkPos p = chunk_pos(g, c0 + ent.x);
+      src = g.src + p.src_off;
+      m = ent.y;
+    }
+    // m: base-4 digits of the window counts, even pixels in bits 0-15 (pair
+    // p at digit 7-p), odd pixels in bits 16-31
+    while (__any_sync(0xFFFFFFFFu, m != 0u)) {
+      unsigned k0 = 0u, k1 = 0u;
+      bool in0 = false, in1 = false;
+      if (m != 0u) {
+        const int bit = __ffs(m) - 1;
+        m &= ~(3u << (bit & ~1));
+        const int k = 2 * (7 - ((bit & 15) >> 1)) + (bit >> 4);
+        const unsigned r = __ldg(src + 3 * k), gg = __ldg(src + 3 * k + 1),
+                       b = __ldg(src + 3 * k + 2);
+        float h1, h2;
+        solve_one(lut, (r << 8) | lr, (gg << 8) | lr, (b << 8) | lr, L, h1, h2);
+        k0 = __float_as_uint(h1);
+        k1 = __float_as_uint(h2);
+        in0 = k0 >= lo0;
+        in1 = k1 >= lo1;
+      }
+      const unsigned b0 = __ballot_sync(0xFFFFFFFFu, in0), b1 = __ballot_sync(0xFFFFFFFFu, in1);
+      if (in0) kb0[kc0 + __popc(b0 & lt)] = k0;
+      if (in1) kb1[kc1 + __popc(b1 & lt)] = k1;
+      kc0 += __popc(b0);
+      kc1 += __popc(b1);
+      if (kc0 > kKeyBuf - 32 || kc1 > kKeyBuf - 32) {
+        __syncwarp();
+        flush_keys(kb0, kc0, list0, cap, S->list_n, S->kmax);
+        flush_keys(kb1, kc1, list1, cap, S->list_n + 1, S->kmax + 1);
+        __syncwarp();
+        kc0 = 0;
+        kc1 = 0;
+      }
+    }
+  }
+}
+
+// First bin whose inclusive prefix exceeds r in a shared histogram of n
+// counts (n a multiple of the block size).  *s_idx = -1 if the total is <= r.
+__device__ __forceinline__ void smem_find_rank(const unsigned* hist, int n, u64 r, int* s_idx,
+                                               u64* s_before, u64* s_tmp) {
+  const int per = n / (int)blockDim.x;
+  const int beg = (int)threadIdx.x * per;
+  u64 local = 0;
+  for (int i = 0; i < per; ++i) local += hist[beg + i];
+  u64 total;
+  const u64 excl = block_excl_scan(local, s_tmp, &total);
+  if (threadIdx.x == 0) *s_idx = -1;
+  __syncthreads();
+  if (local > 0 && excl <= r && r < excl + local) {
+    u64 c = excl;
+    for (int i = 0; i < per; ++i) {
+      const u64 x = hist[beg + i];
+      if (r < c + x) { *s_idx = beg + i; *s_before = c; break; }
+      c += x;
+    }
+  }
+  __syncthreads();
+}
+
+// Percentile of one tile from its key lists, by the block that finished the
+// tile's pass 1.  Rank r of the non-white densities is rank r - below among
+// the listed keys when below <= r < below + count and the list is complete;
+// it is found by a radix select over d = key - lo, most significant 12-bit
+// digit first, as many digits as the largest listed d needs.  Ranks outside
+// leave the tile to the exact fallback.
+__device__ void batch_select(const BatchArgs& a, unsigned tile, unsigned* s_hist, u64* s_tmp) {
+  const BatchTile* T = a.tiles + tile;
+  BatchTileState* S = a.state + tile;
+  SelectState* s = &S->sel;
+  __shared__ int s_idx;
+  __shared__ u64 s_before;
+  __shared__ unsigned s_pre[2];
+  __shared__ u64 s_rr[2];
+  __shared__ int s_res[kTracks];
+  const u64 n = __ldcg(&s->n_nw);
+  if (n == 0) {
+    if (threadIdx.x == 0) {
+      S->status = SPCN_ERR_NO_TISSUE;
+      for (int t = 0; t < kTracks; ++t) { s->key[t] = 0; s->resolved[t] = 1; }
+      s->p99[0] = s->p99[1] = 0.0;
+      s->scale[0] = s->scale[1] = 1.0;
+      s->t = 0.0;
+      s->all_resolved = 1;
+      __threadfence();
+      st_release_s32(&S->ready, 1);
+    }
+    return;
+  }
+  if (threadIdx.x == 0) {
+    set_ranks(s, n, a.pct);
+    for (int j = 0; j < 2; ++j) { s->lo[j] = T->lo[j]; s->nb[j] = 0u; }
+    for (int t = 0; t < kTracks; ++t) s_res[t] = 0;
+  }
+  __syncthreads();
+  const u64 cap = T->list_cap;
+  for (int j = 0; j < 2; ++j) {
+    const unsigned lo = T->lo[j];
+    const u64 cnt = __ldcg(&S->list_n[j]);
+    const u64 below = __ldcg(&s->below[j]);
+    const unsigned* list = T->keys + (u64)j * cap;
+    bool in[2];
+    for (int u = 0; u < 2; ++u) {
+      const u64 r = s->rank[2 * j + u];
+      in[u] = T->win[j] && cnt <= cap && r >= below && r - below < cnt;
+    }
+    if (!in[0] && !in[1]) continue;   // uniform across the block
+    if (threadIdx.x == 0) {
+      for (int u = 0; u < 2; ++u) { s_pre[u] = 0u; s_rr[u] = s->rank[2 * j + u] - below; }
+    }
+    const unsigned range = __ldcg(&S->kmax[j]) - lo;   // every listed d is <= range
+    const int nbits = range ? 32 - __clz(range) : 1;
+    const int levels = (nbits + kSelBits - 1) / kSelBits;
+    bool ok[2] = {in[0], in[1]};
+    for (int lev = levels - 1; lev >= 0; --lev) {
+      const int shift = lev * kSelBits;
+      __syncthreads();
+      const unsigned pre0 = s_pre[0], pre1 = s_pre[1];
+      const bool share = !ok[0] || !ok[1] || pre0 == pre1;   // one histogram serves both
+      for (int i = threadIdx.x; i < 2 * kSelBins; i += blockDim.x) s_hist[i] = 0u;
+      __syncthreads();
+      const int hi = shift + kSelBits;
+      const u64 t0 = (u64)pre0 >> hi, t1 = (u64)pre1 >> hi;
+      // histogram 0 takes track 0's keys (or track 1's when track 0 is done);
+      // histogram 1 takes track 1's keys when the prefixes differ
+      const bool use0 = ok[0], use1 = ok[1];
+      auto count = [&](unsigned key) {
+        const unsigned d = key - lo;
+        const unsigned bin = (d >> shift) & (kSelBins - 1);
+        const u64 top = (u64)d >> hi;
+        if (use0 && top == t0) atomicAdd(s_hist + bin, 1u);
+        else if (use1 && top == t1) atomicAdd(s_hist + (share ? 0 : kSelBins) + bin, 1u);
+      };
+      // 16-byte loads, eight keys per thread and step (the lists start on
+      // 16-byte boundaries; the last partial vector is read key by key)
+      const uint4* v = reinterpret_cast<const uint4*>(list);
+      const u64 nv = cnt / 4;
+      for (u64 i = threadIdx.x; i < nv; i += 2 * blockDim.x) {
+        const uint4 x = __ldcg(v + i);
+        const bool two = i + blockDim.x < nv;
+        uint4 y = make_uint4(0u, 0u, 0u, 0u);
+        if (two) y = __ldcg(v + i + blockDim.x);
+        count(x.x); count(x.y); count(x.z); count(x.w);
+        if (two) { count(y.x); count(y.y); count(y.z); count(y.w); }
+      }
+      for (u64 i = nv * 4 + threadIdx.x; i < cnt; i += blockDim.x) count(__ldcg(list + i));
+      __syncthreads();
+      for (int u = 0; u < 2; ++u) {
+        if (!ok[u]) continue;
+        const unsigned* h = s_hist + ((share || u == 0) ? 0 : kSelBins);
+        smem_find_rank(h, kSelBins, s_rr[u], &s_idx, &s_before, s_tmp);
+        if (threadIdx.x == 0) {
+          if (s_idx < 0) {
+            ok[u] = false;   // cannot happen: the level's count covers the rank
+          } else {
+            s_pre[u] |= (unsigned)s_idx << shift;
+            s_rr[u] -= s_before;
+          }
+        }
+        __syncthreads();
+        ok[u] = ok[u] && s_idx >= 0;
+      }
+    }
+    if (threadIdx.x == 0) {
+      for (int u = 0; u < 2; ++u)
+        if (ok[u]) {
+          s->key[2 * j + u] = lo + s_pre[u];
+          s_res[2 * j + u] = 1;
+        }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    int all = 1;
+    for (int t = 0; t < kTracks; ++t) { s->resolved[t] = s_res[t]; all &= s_res[t]; }
+    if (all) finish_percentiles(s, a.tgt0, a.tgt1, a.models[T->model].lasso.hscale);
+    s->all_resolved = all;
+    __threadfence();
+    st_release_s32(&S->ready, all ? 1 : 2);
+  }
+}
+
+// Pass 1 on one chunk with open-ended windows.  Per pixel: the non-white flag
+// (0/1), [h~ < lo] per stain by saturated FMAs, accumulated with packed FMAs;
+// the number of stains at or above their window start (0, 1 or 2) of each
+// non-white pixel is packed base 4 into `mask` (pixel pair p at digit 7-p,
+// even pixels in the low lane, odd pixels in the high lane).
+__device__ __forceinline__ void open_window_chunk(const unsigned (&w)[12], const char* lut,
+                                                  unsigned lr, f2 NR1, f2 NR2, float kappa,
+                                                  unsigned wthr, float nk0, float lk0, float nk1,
+                                                  float lk1, f2& c_nw, f2& c_b0, f2& c_b1,
+                                                  f2& mask) {
+  const f2 M1 = pk(-1.f, -1.f), FOUR = pk(4.f, 4.f), TWO = pk(2.f, 2.f);
+  mask = pk(0.f, 0.f);
+#pragma unroll
+  for (int p = 0; p < kChunk / 2; ++p) {
+    const int kA = 2 * p, kB = 2 * p + 1;
+    unsigned aRA, aGA, aBA, aRB, aGB, aBB;
+    pixel_addr(w, kA, lr, aRA, aGA, aBA);
+    pixel_addr(w, kB, lr, aRB, aGB, aBB);
+    f2 H1, H2;
+    solve_pair(lut, aRA, aGA, aBA, aRB, aGB, aBB, NR1, NR2, kappa, H1, H2);
+    const bool nwA = aRA < wthr || aGA < wthr || aBA < wthr;
+    const bool nwB = aRB < wthr || aGB < wthr || aBB < wthr;
+    const f2 NW = pk(nwA ? 1.f : 0.f, nwB ? 1.f : 0.f);
+    c_nw = add2(c_nw, NW);
+    const float h1A = lo_of(H1), h1B = hi_of(H1), h2A = lo_of(H2), h2B = hi_of(H2);
+    const f2 B0 = pk(fma_sat(h1A, nk0, lk0), fma_sat(h1B, nk0, lk0));
+    const f2 B1 = pk(fma_sat(h2A, nk1, lk1), fma_sat(h2B, nk1, lk1));
+    c_b0 = fma2(B0, NW, c_b0);
+    c_b1 = fma2(B1, NW, c_b1);
+    const f2 X = fma2(B0, M1, fma2(B1, M1, TWO));   // 2 - B0 - B1, exact
+    mask = fma2(mask, FOUR, mul2(X, NW));
+  }
+}
+
+__device__ __forceinline__ ReconConst recon_const(const float* s_M, const float* l2i0) {
+  ReconConst K;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    K.M1[c] = pk(s_M[c], s_M[c]);
+    K.M2[c] = pk(s_M[3 + c], s_M[3 + c]);
+    K.L2[c] = pk(l2i0[c], l2i0[c]);
+  }
+  return K;
+}
+
+template <class G>
+__device__ __forceinline__ G geometry_as(const Geometry& g);
+template <>
+__device__ __forceinline__ Geometry geometry_as<Geometry>(const Geometry& g) { return g; }
+template <>
+__device__ __forceinline__ FlatGeometry geometry_as<FlatGeometry>(const Geometry& g) {
+  return FlatGeometry{g.src, g.dst, (u64)g.npx, g.vec_src, g.vec_dst};
+}
+
+// One pass-1 item: chunks [c0, c1) of a tile, by the whole block.
+template <class G>
+__device__ __forceinline__ void batch_pass1(const BatchArgs& a, unsigned tile, u64 c0, u64 c1,
+                                            const char* lut, unsigned lr, uint2* s_queue,
+                                            unsigned* s_kb, unsigned* s_hist, u64* s_tmp,
+                                            int* s_last) {
+  const BatchTile* T = a.tiles + tile;
+  BatchTileState* S = a.state + tile;
+  const G g = geometry_as<G>(T->g);
+  const Lasso L = a.models[T->model].lasso;
+  const float nk0 = T->nk[0], lk0 = T->lk[0], nk1 = T->nk[1], lk1 = T->lk[1];
+  const f2 NR1 = pk(L.nrho1, L.nrho1), NR2 = pk(L.nrho2, L.nrho2);
+  f2 c_nw = pk(0.f, 0.f), c_b0 = pk(0.f, 0.f), c_b1 = pk(0.f, 0.f);
+  unsigned* kb0 = s_kb;
+  unsigned* kb1 = s_kb + kKeyBuf;
+  const unsigned lane = threadIdx.x & 31u;
+  int qn = 0, kc0 = 0, kc1 = 0;   // warp-uniform
+  for (u64 base = c0 + (threadIdx.x & ~31u); base < c1; base += blockDim.x) {
+    const u64 q = base + lane;
+    bool hit = false;
+    unsigned packed = 0u;
+    if (q < c1) {
+      const ChunkPos p = chunk_pos(g, q);
+      unsigned w[12];
+      load_chunk<false>(g, p, w);
+      f2 mask;
+      open_window_chunk(w, lut, lr, NR1, NR2, L.kappa, a.wthr, nk0, lk0, nk1, lk1, c_nw, c_b0,
+                        c_b1, mask);
+      packed = (unsigned)lo_of(mask) | ((unsigned)hi_of(mask) << 16);
+      hit = packed != 0u;
+    }
+    const unsigned ball = __ballot_sync(0xFFFFFFFFu, hit);
+    if (hit) s_queue[qn + __popc(ball & ((1u << lane) - 1u))] = make_uint2((unsigned)(q - c0), packed);
+    qn += __popc(ball);
+    if (qn >= 32 || base + blockDim.x >= c1) {
+      __syncwarp();
+      batch_drain(s_queue, qn, c0, g, lut, lr, L, kb0, kb1, kc0, kc1, T, S);
+      __syncwarp();
+      qn = 0;
+    }
+  }
+  __syncwarp();
+  flush_keys(kb0, kc0, T->keys, T->list_cap, S->list_n, S->kmax);
+  flush_keys(kb1, kc1, T->keys + T->list_cap, T->list_cap, S->list_n + 1, S->kmax + 1);
+  // per-thread counts are exact in FP32 (fewer than 2^24 pixels per thread)
+  const u64 t_nw = block_sum((u64)lo_of(c_nw) + (u64)hi_of(c_nw), s_tmp);
+  const u64 t_b0 = block_sum((u64)lo_of(c_b0) + (u64)hi_of(c_b0), s_tmp);
+  const u64 t_b1 = block_sum((u64)lo_of(c_b1) + (u64)hi_of(c_b1), s_tmp);
+  if (threadIdx.x == 0) {
+    if (t_nw) atomicAdd(&S->sel.n_nw, t_nw);
+    if (t_b0) atomicAdd(&S->sel.below[0], t_b0);
+    if (t_b1) atomicAdd(&S->sel.below[1], t_b1);
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) *s_last = atomicAdd(&S->done1, 1u) == T->n_items1 - 1u;
+  __syncthreads();
+  if (*s_last) {
+    __threadfence();
+    batch_select(a, tile, s_hist, s_tmp);
+  }
+}
+
+// One pass-2 item: chunks [c0, c1) of a tile, by the whole block.
+template <class G>
+__device__ __forceinline__ void batch_pass2(const BatchArgs& a, unsigned tile, u64 c0, u64 c1,
+                                            const char* lut, unsigned lr, const float* s_M) {
+  const BatchTile* T = a.tiles + tile;
+  const G g = geometry_as<G>(T->g);
+  const Lasso L = a.models[T->model].lasso;
+  const ReconConst K = recon_const(s_M, a.l2i0);
+  const f2 NR1 = pk(L.nrho1, L.nrho1), NR2 = pk(L.nrho2, L.nrho2);
+  for_chunks<true, true>(g, c0 + threadIdx.x, c1, blockDim.x,
+                         [&](const unsigned (&w)[12], const ChunkPos& p) {
+                           unsigned o[12];
+                           recon_chunk(w, lut, lr, NR1, NR2, L.kappa, K, o);
+                           store_chunk(g, p, o);
+                         });
+}
+
+
+template <class G>
+__global__ void __launch_bounds__(kPassThreads, 1) k_batch(BatchArgs a) {
+  extern __shared__ __align__(16) char s_dyn[];
+  char* lut = s_dyn;
+  char* work = s_dyn + kLutSmemBytes;
+  const unsigned warp = threadIdx.x >> 5;
+  uint2* s_queue = reinterpret_cast<uint2*>(work) + warp * kWarpQueue;
+  unsigned* s_kb = reinterpret_cast<unsigned*>(work + kBatchQueueBytes) + warp * 2 * kKeyBuf;
+  unsigned* s_hist = reinterpret_cast<unsigned*>(work);   // select / radix histograms (overlay)
+  __shared__ u64 s_tmp[33];
+  __shared__ unsigned s_item;
+  __shared__ int s_go, s_last;
+  __shared__ float s_M[6];
+  const unsigned lr = lane_reg();
+  int cur_model = -1;
+  for (;;) {
+    __syncthreads();   // previous item done: shared words and the table may be rewritten
+    if (threadIdx.x == 0) s_item = atomicAdd(&a.run->next, 1u);
+    __syncthreads();
+    const unsigned it = s_item;
+    if (it >= a.n_items) break;
+    const BatchItem item = a.items[it];
+    const unsigned model = a.tiles[item.tile].model;
+    if (item.pass == 2) {
+      if (threadIdx.x == 0) {
+        BatchTileState* S = a.state + item.tile;
+        const int st = wait_ready(&S->ready, &a.run->abort, &a.run->err, a.timeout_ns);
+        if (st == 1) {
+          const double sc[2] = {__ldcg(&S->sel.scale[0]), __ldcg(&S->sel.scale[1])};
+          const float hs = a.models[model].lasso.hscale;
+          for (int i = 0; i < 6; ++i) s_M[i] = recon_coef(a.Wt, sc, hs, i);
+        }
+        s_go = st;
+      }
+      __syncthreads();
+      if (s_go < 0) break;     // the run was aborted
+      if (s_go != 1) continue; // tile left to the exact fallback
+    }
+    if ((int)model != cur_model) {
+      load_lut(a.models + model, lut);
+      cur_model = (int)model;
+    }
+    if (item.pass == 1)
+      batch_pass1<G>(a, item.tile, item.c0, item.c1, lut, lr, s_queue, s_kb, s_hist, s_tmp,
+                     &s_last);
+    else
+      batch_pass2<G>(a, item.tile, item.c0, item.c1, lut, lr, s_M);
+  }
+  // tiles whose ranks the windows missed: exact radix select over the whole
+  // grid, then their pass 2 (tile order; the ready words are final here)
+  if (!grid_barrier(&a.run->barrier, gridDim.x, &a.run->abort, &a.run->err, a.timeout_ns)) return;
+  unsigned target = gridDim.x;
+  for (unsigned t = 0; t < a.n_tiles; ++t) {
+    BatchTileState* S = a.state + t;
+    if (__ldcg(&S->ready) != 2) continue;   // same value in every block
+    if (blockIdx.x == 0 && threadIdx.x == 0) S->fallback = 1;
+    const BatchTile* T = a.tiles + t;
+    const unsigned model = T->model;
+    __syncthreads();
+    if ((int)model != cur_model) {
+      load_lut(a.models + model, lut);
+      cur_model = (int)model;
+    }
+    const Lasso L = a.models[model].lasso;
+    u64 rank[kTracks];
+    int active[kTracks];
+    for (int k = 0; k < kTracks; ++k) {
+      rank[k] = __ldcg(&S->sel.rank[k]);
+      active[k] = !__ldcg(&S->sel.resolved[k]);
+    }
+    const ImageSource src{T->g, a.thr};
+    if (!radix_select(src, lut, L, &S->sel, rank, active, a.rhist, s_hist, &S->sel.barrier,
+                      &a.run->err, a.timeout_ns, a.tgt0, a.tgt1))
+      return;
+    target += gridDim.x;
+    if (!grid_barrier(&a.run->barrier, target, &a.run->abort, &a.run->err, a.timeout_ns)) return;
+    if (threadIdx.x == 0) {
+      const double sc[2] = {__ldcg(&S->sel.scale[0]), __ldcg(&S->sel.scale[1])};
+      for (int i = 0; i < 6; ++i) s_M[i] = recon_coef(a.Wt, sc, L.hscale, i);
+    }
+    __syncthreads();
+    const ReconConst K = recon_const(s_M, a.l2i0);
+    const f2 NR1 = pk(L.nrho1, L.nrho1), NR2 = pk(L.nrho2, L.nrho2);
+    const Geometry g = T->g;
+    for_each_chunk<true, true>(g, [&](const unsigned (&w)[12], const ChunkPos& p) {
+      unsigned o[12];
+      recon_chunk(w, lut, lr, NR1, NR2, L.kappa, K, o);
+      store_chunk(g, p, o);
+    });
+  }
+}
+
+// ------------------------------------------------------------ host side
+struct Batch {
+  Context* c = nullptr;
+  int n = 0;
+  std::vector<BatchTile> tiles;
+  std::vector<int> tile_status;
+  int n_models = 0;
+  Model* models = nullptr;
+  BatchTile* d_tiles = nullptr;
+  BatchItem* d_items = nullptr;
+  size_t items_cap = 0;
+  unsigned n_items = 0;
+  char* d_state = nullptr;       // BatchRunState, then n BatchTileState
+  size_t state_bytes = 0;
+  unsigned* keys = nullptr;
+  u64* rhist = nullptr;
+  int grid = 0;
+  bool flat = false;             // every tile contiguous: launch the flat instantiation
+  BatchArgs args{};
+  spcn_batch_config cfg{};
+};
+
+constexpr size_t kRunStateBytes = (sizeof(BatchRunState) + 255) & ~size_t(255);
+
+template <class G>
+static int configure_batch_kernel(Context* c, int* grid) {
+  SPCN_CUDA_TRY(cudaFuncSetAttribute(k_batch<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kBatchSmem));
+  int occ = 0;
+  SPCN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<G>, kPassThreads,
+                                                              kBatchSmem));
+  if (occ < 1) return SPCN_ERR_CUDA;
+  *grid = c->num_sms * occ;
+  return SPCN_OK;
+}
+
+static bool config_ok(const spcn_batch_config* cfg) {
+  if (!cfg) return false;
+  if (cfg->item_chunks < kPassThreads || cfg->item_chunks % kPassThreads != 0) return false;
+  if (cfg->schedule != SPCN_SCHED_PHASED && cfg->schedule != SPCN_SCHED_INTERLEAVED) return false;
+  if (cfg->schedule == SPCN_SCHED_INTERLEAVED && cfg->group_px < 1) return false;
+  return true;
+}
+
+// Work queue of a schedule.  Every pass-1 item of a tile precedes the tile's
+// pass-2 items (the kernel's waits rely on it).
+static void build_items(const Batch* b, const spcn_batch_config& cfg, std::vector<BatchItem>* out,
+                        std::vector<unsigned>* n_items1) {
+  const u64 S = (u64)cfg.item_chunks;
+  out->clear();
+  n_items1->assign(b->n, 0u);
+  // largest tiles first: their list selects end early, and the small tiles
+  // even out the end of each pass
+  std::vector<int> order(b->n);
+  for (int t = 0; t < b->n; ++t) order[t] = t;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    return b->tiles[x].g.npx > b->tiles[y].g.npx;
+  });
+  auto emit = [&](int t, unsigned pass) {
+    const u64 nch = b->tiles[t].g.nchunks;
+    for (u64 c0 = 0; c0 < nch; c0 += S) out->push_back({(unsigned)t, pass, c0, std::min(nch, c0 + S)});
+    if (pass == 1) (*n_items1)[t] = (unsigned)((nch + S - 1) / S);
+  };
+  if (cfg.schedule == SPCN_SCHED_PHASED) {
+    for (int t : order) emit(t, 1);
+    for (int t : order) emit(t, 2);
+    return;
+  }
+  // groups of consecutive tiles (in size order) holding about group_px pixels
+  std::vector<std::pair<int, int>> groups;
+  int start = 0;
+  int64_t px = 0;
+  for (int k = 0; k < b->n; ++k) {
+    px += b->tiles[order[k]].g.npx;
+    if (px >= cfg.group_px || k == b->n - 1) {
+      groups.push_back({start, k + 1});
+      start = k + 1;
+      px = 0;
+    }
+  }
+  for (size_t k = 0; k <= groups.size(); ++k) {
+    if (k < groups.size())
+      for (int i = groups[k].first; i < groups[k].second; ++i) emit(order[i], 1);
+    if (k >= 1)
+      for (int i = groups[k - 1].first; i < groups[k - 1].second; ++i) emit(order[i], 2);
+  }
+}
+
+static int apply_config(Batch* b, const spcn_batch_config& cfg) {
+  std::vector<BatchItem> items;
+  std::vector<unsigned> n1;
+  build_items(b, cfg, &items, &n1);
+  if (items.size() > 0xFFFFFFF0ull) return SPCN_ERR_INVALID_ARG;
+  if (items.size() > b->items_cap) {
+    cudaFree(b->d_items);
+    b->d_items = nullptr;
+    b->items_cap = 0;
+    SPCN_CUDA_TRY(cudaMalloc(&b->d_items, items.size() * sizeof(BatchItem)));
+    b->items_cap = items.size();
+  }
+  for (int t = 0; t < b->n; ++t) b->tiles[t].n_items1 = n1[t];
+  SPCN_CUDA_TRY(cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(BatchItem),
+                           cudaMemcpyHostToDevice));
+  SPCN_CUDA_TRY(cudaMemcpy(b->d_tiles, b->tiles.data(), b->tiles.size() * sizeof(BatchTile),
+                           cudaMemcpyHostToDevice));
+  // a pageable copy may return before it lands: finish it before any launch
+  SPCN_CUDA_TRY(cudaDeviceSynchronize());
+  b->n_items = (unsigned)items.size();
+  b->args.items = b->d_items;
+  b->args.n_items = b->n_items;
+  b->cfg = cfg;
+  b->cfg.ms = 0.f;
+  return SPCN_OK;
+}
+
+static void batch_free(Batch* b) {
+  void* ptrs[] = {b->models, b->d_tiles, b->d_items, b->d_state, b->keys, b->rhist};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete b;
+}
+
+static int batch_launch(Batch* b, cudaStream_t st) {
+  Context* c = b->c;
+  SPCN_CUDA_TRY(cudaMemsetAsync(b->d_state, 0, b->state_bytes, st));
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  SPCN_CUDA_TRY(cudaStreamIsCapturing(st, &cap));
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = dim3((unsigned)b->grid);
+  lc.blockDim = dim3(kPassThreads);
+  lc.dynamicSmemBytes = kBatchSmem;
+  lc.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  lc.attrs = attr;
+  lc.numAttrs = 1;
+  cudaError_t e;
+  // contiguous tiles only: the flat traversal (fewer registers per loop)
+  auto launch = [&]() {
+    return b->flat ? cudaLaunchKernelEx(&lc, k_batch<FlatGeometry>, b->args)
+                   : cudaLaunchKernelEx(&lc, k_batch<Geometry>, b->args);
+  };
+  if (cap == cudaStreamCaptureStatusNone) {
+    TimedLaunch tl(c, SPCN_KERNEL_BATCH, st);
+    e = launch();
+  } else {
+    e = launch();
+  }
+  c->launches++;
+  if (e != cudaSuccess) return SPCN_ERR_CUDA;
+  return SPCN_OK;
+}
+
+static int batch_create(Context* c, int n, const spcn_image* tiles, const spcn_stats* tile_stats,
+                        const spcn_stats* tgt, const spcn_params* params, uint8_t* const* outs,
+                        const int64_t* out_pitches, Batch** out) {
+  Batch* b = new (std::nothrow) Batch();
+  if (!b) return SPCN_ERR_OOM;
+  b->c = c;
+  b->n = n;
+  b->tiles.resize(n);
+  // one table per distinct (W, i0): tiles of one slide share it
+  std::vector<int> rep;   // first tile of each table
+  u64 keys_total = 0;
+  for (int t = 0; t < n; ++t) {
+    BatchTile& T = b->tiles[t];
+    memset(&T, 0, sizeof(T));
+    T.g = make_geometry(&tiles[t], outs[t], out_pitches[t]);
+    int m = -1;
+    for (size_t k = 0; k < rep.size() && m < 0; ++k)
+      if (memcmp(tile_stats[rep[k]].W, tile_stats[t].W, sizeof(float) * 6) == 0 &&
+          memcmp(tile_stats[rep[k]].i0, tile_stats[t].i0, sizeof(float) * 3) == 0)
+        m = (int)k;
+    if (m < 0) {
+      m = (int)rep.size();
+      rep.push_back(t);
+    }
+    T.model = (unsigned)m;
+    const int hexp = host_table_hexp(tile_stats[t].W, tile_stats[t].i0, params->lambda);
+    const double hs = ldexp(1.0, -hexp);
+    for (int j = 0; j < 2; ++j) {
+      const double h = tile_stats[t].p99[j] * hs * kOpenLow;
+      float f = (float)h;
+      unsigned key = 0u;
+      memcpy(&key, &f, 4);
+      if (h > 0x1p-100 && std::isfinite(h) && key > 0u) {
+        T.win[j] = 1u;
+        T.lo[j] = key;
+        below_consts(key, &T.nk[j], &T.lk[j]);
+      } else {   // no window: [h~ < lo] is 1 for every pixel, nothing is listed
+        T.win[j] = 0u;
+        T.lo[j] = 0u;
+        T.nk[j] = 0.f;
+        T.lk[j] = 1.f;
+      }
+    }
+    // room for 1/8 of the pixels per stain (a window from 0.75 P99 holds a
+    // few percent; an overflowing list sends the tile to the exact fallback)
+    T.list_cap = ((u64)T.g.npx / 8 + 1024 + 3) & ~u64(3);
+    T.keys = reinterpret_cast<unsigned*>((uintptr_t)keys_total);   // offset until allocated
+    keys_total += 2 * T.list_cap;
+  }
+  b->n_models = (int)rep.size();
+  int rc = SPCN_OK;
+  auto fail = [&](int code) { batch_free(b); return code; };
+  if (cudaMalloc(&b->models, sizeof(Model) * rep.size()) != cudaSuccess) return fail(SPCN_ERR_OOM);
+  if (cudaMalloc(&b->d_tiles, sizeof(BatchTile) * n) != cudaSuccess) return fail(SPCN_ERR_OOM);
+  b->state_bytes = kRunStateBytes + sizeof(BatchTileState) * (size_t)n;
+  if (cudaMalloc(&b->d_state, b->state_bytes) != cudaSuccess) return fail(SPCN_ERR_OOM);
+  if (cudaMalloc(&b->keys, sizeof(unsigned) * keys_total) != cudaSuccess) return fail(SPCN_ERR_OOM);
+  for (BatchTile& T : b->tiles) T.keys = b->keys + reinterpret_cast<uintptr_t>(T.keys);
+  if (cudaMalloc(&b->rhist, sizeof(u64) * 3 * kTracks * kRadixBins) != cudaSuccess)
+    return fail(SPCN_ERR_OOM);
+  for (size_t k = 0; k < rep.size(); ++k) {
+    rc = launch_build_model(c, b->models + k, tile_stats[rep[k]].W, tile_stats[rep[k]].i0,
+                            params->lambda, nullptr, nullptr);
+    if (rc) return fail(rc);
+  }
+  b->flat = true;
+  for (const BatchTile& T : b->tiles) b->flat = b->flat && T.g.flat;
+  rc = b->flat ? configure_batch_kernel<FlatGeometry>(c, &b->grid)
+               : configure_batch_kernel<Geometry>(c, &b->grid);
+  if (rc) return fail(rc);
+  BatchArgs& a = b->args;
+  a.tiles = b->d_tiles;
+  a.state = reinterpret_cast<BatchTileState*>(b->d_state + kRunStateBytes);
+  a.run = reinterpret_cast<BatchRunState*>(b->d_state);
+  a.models = b->models;
+  a.rhist = b->rhist;
+  a.n_tiles = (unsigned)n;
+  a.wthr = ((unsigned)params->white_thresh + 1u) << 8;
+  a.thr = (unsigned)params->white_thresh;
+  a.pct = (double)params->stain_pct;
+  a.tgt0 = tgt->p99[0];
+  a.tgt1 = tgt->p99[1];
+  for (int i = 0; i < 6; ++i) a.Wt[i] = tgt->W[i];
+  for (int i = 0; i < 3; ++i) a.l2i0[i] = (float)log2((double)tgt->i0[i]);
+  a.timeout_ns = c->timeout_ns;
+  spcn_batch_config cfg{};
+  cfg.item_chunks = 4 * kPassThreads;
+  cfg.schedule = SPCN_SCHED_PHASED;
+  cfg.group_px = 0;
+  rc = apply_config(b, cfg);
+  if (rc) return fail(rc);
+  if (cudaDeviceSynchronize() != cudaSuccess) return fail(SPCN_ERR_CUDA);
+  *out = b;
+  return SPCN_OK;
+}
+
+static int batch_results(Batch* b, double* p99_out, int32_t* status_out, int32_t* fallback_out,
+                         cudaStream_t st) {
+  std::vector<char> h(b->state_bytes);
+  SPCN_CUDA_TRY(cudaMemcpyAsync(h.data(), b->d_state, b->state_bytes, cudaMemcpyDeviceToHost, st));
+  SPCN_CUDA_TRY(cudaStreamSynchronize(st));
+  const BatchRunState* run = reinterpret_cast<const BatchRunState*>(h.data());
+  const BatchTileState* ts = reinterpret_cast<const BatchTileState*>(h.data() + kRunStateBytes);
+  for (int t = 0; t < b->n; ++t) {
+    if (p99_out) {
+      p99_out[2 * t] = ts[t].sel.p99[0];
+      p99_out[2 * t + 1] = ts[t].sel.p99[1];
+    }
+    if (status_out) status_out[t] = ts[t].status;
+    if (fallback_out) fallback_out[t] = ts[t].fallback;
+  }
+  return run->err;
+}
+
+}  // namespace spcn
+
+using namespace spcn;
+
+extern "C" {
+
+int spcn_batch_create(void* ctx, int32_t n, const spcn_image* tiles, const spcn_stats* tile_stats,
+                      const spcn_stats* tgt_st, const spcn_params* params, uint8_t* const* outs,
+                      const int64_t* out_pitches, void** batch) {
+  if (!ctx || n < 1 || n > (1 << 20) || !tiles || !tile_stats || !tgt_st || !outs ||
+      !out_pitches || !batch || !params_ok(params))
+    return SPCN_ERR_INVALID_ARG;
+  *batch = nullptr;
+  int rc = stats_ok(tgt_st);
+  if (rc) return rc;
+  for (int t = 0; t < n; ++t) {
+    const spcn_image* s = &tiles[t];
+    if (!image_ok(s) || !outs[t] || out_pitches[t] < 3ll * s->width) return SPCN_ERR_INVALID_ARG;
+    rc = stats_ok(&tile_stats[t]);
+    if (rc) return rc;
+    const uintptr_t s0 = reinterpret_cast<uintptr_t>(s->data);
+    const uintptr_t s1 = s0 + (uintptr_t)((s->height - 1) * s->pitch_bytes + 3ll * s->width);
+    const uintptr_t d0 = reinterpret_cast<uintptr_t>(outs[t]);
+    const uintptr_t d1 = d0 + (uintptr_t)((s->height - 1) * out_pitches[t] + 3ll * s->width);
+    if (d0 < s1 && s0 < d1) return SPCN_ERR_INVALID_ARG;
+  }
+  Context* c = static_cast<Context*>(ctx);
+  DeviceGuard guard(c->device);
+  if (!guard.ok) return SPCN_ERR_CUDA;
+  Batch* b = nullptr;
+  rc = batch_create(c, n, tiles, tile_stats, tgt_st, params, outs, out_pitches, &b);
+  if (rc) return rc;
+  *batch = b;
+  return SPCN_OK;
+}
+
+int spcn_batch_run(void* batch, void* stream) {
+  if (!batch) return SPCN_ERR_INVALID_ARG;
+  Batch* b = static_cast<Batch*>(batch);
+  DeviceGuard guard(b->c->device);
+  if (!guard.ok) return SPCN_ERR_CUDA;
+  return batch_launch(b, static_cast<cudaStream_t>(stream));
+}
+
+int spcn_batch_results(void* batch, double* p99_out, int32_t* status_out, int32_t* fallback_out,
+                       void* stream) {
+  if (!batch) return SPCN_ERR_INVALID_ARG;
+  Batch* b = static_cast<Batch*>(batch);
+  DeviceGuard guard(b->c->device);
+  if (!guard.ok) return SPCN_ERR_CUDA;
+  return batch_results(b, p99_out, status_out, fallback_out, static_cast<cudaStream_t>(stream));
+}
+
+int spcn_batch_get_config(void* batch, spcn_batch_config* cfg) {
+  if (!batch || !cfg) return SPCN_ERR_INVALID_ARG;
+  *cfg = static_cast<Batch*>(batch)->cfg;
+  return SPCN_OK;
+}
+
+int spcn_batch_set_config(void* batch, const spcn_batch_config* cfg) {
+  if (!batch || !config_ok(cfg)) return SPCN_ERR_INVALID_ARG;
+  Batch* b = static_cast<Batch*>(batch);
+  DeviceGuard guard(b->c->device);
+  if (!guard.ok) return SPCN_ERR_CUDA;
+  if (cudaDeviceSynchronize() != cudaSuccess) return SPCN_ERR_CUDA;   // no run may read the old queue
+  return apply_config(b, *cfg);
+}
+
+int spcn_batch_tune(void* batch, int32_t reps, spcn_batch_config* trials, int32_t max_trials,
+                    int32_t* n_trials, void* stream) {
+  if (!batch || reps < 1 || (trials && max_trials < 0)) return SPCN_ERR_INVALID_ARG;
+  Batch* b = static_cast<Batch*>(batch);
+  DeviceGuard guard(b->c->device);
+  if (!guard.ok) return SPCN_ERR_CUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // candidates: item sizes x (phased, interleaved groups of 4, 8, 16 Mpx)
+  std::vector<spcn_batch_config> cand;
+  for (int k : {1, 2, 4, 8, 16}) {
+    spcn_batch_config c0{};
+    c0.item_chunks = k * kPassThreads;
+    c0.schedule = SPCN_SCHED_PHASED;
+    cand.push_back(c0);
+    for (int64_t g : {4ll << 20, 8ll << 20, 16ll << 20}) {
+      spcn_batch_config c1 = c0;
+      c1.schedule = SPCN_SCHED_INTERLEAVED;
+      c1.group_px = g;
+      cand.push_back(c1);
+    }
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  SPCN_CUDA_TRY(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return SPCN_ERR_CUDA; }
+  int rc = SPCN_OK;
+  int best = -1;
+  float best_ms = 0.f;
+  int written = 0;
+  const bool timing = b->c->timing;
+  b->c->timing = false;   // the tuner's own runs are not reported as kernel time
+  for (size_t k = 0; k < cand.size() && rc == SPCN_OK; ++k) {
+    if (cudaStreamSynchronize(st) != cudaSuccess) { rc = SPCN_ERR_CUDA; break; }
+    rc = apply_config(b, cand[k]);
+    if (rc) break;
+    rc = batch_launch(b, st);   // untimed run
+    for (int r = 0; r < reps && rc == SPCN_OK; ++r) {
+      if (r == 0 && cudaEventRecord(e0, st) != cudaSuccess) rc = SPCN_ERR_CUDA;
+      if (rc == SPCN_OK) rc = batch_launch(b, st);
+    }
+    if (rc) break;
+    float ms = 0.f;
+    if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      rc = SPCN_ERR_CUDA;
+      break;
+    }
+    int err = 0;
+    std::vector<char> h(kRunStateBytes);
+    if (cudaMemcpy(h.data(), b->d_state, kRunStateBytes, cudaMemcpyDeviceToHost) != cudaSuccess) {
+      rc = SPCN_ERR_CUDA;
+      break;
+    }
+    err = reinterpret_cast<const BatchRunState*>(h.data())->err;
+    if (err) { rc = err; break; }
+    cand[k].ms = ms / (float)reps;
+    if (trials && written < max_trials) trials[written++] = cand[k];
+    if (best < 0 || cand[k].ms < best_ms) { best = (int)k; best_ms = cand[k].ms; }
+  }
+  b->c->timing = timing;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (n_trials) *n_trials = written;
+  if (rc) return rc;
+  rc = apply_config(b, cand[best]);
+  b->cfg.ms = best_ms;
+  return rc;
+}
+
+int spcn_batch_destroy(void* batch) {
+  if (!batch) return SPCN_OK;
+  Batch* b = static_cast<Batch*>(batch);
+  DeviceGuard guard(b->c->device);
+  cudaDeviceSynchronize();
+  batch_free(b);
+  return SPCN_OK;
+}
+
+int spcn_normalize_batched(void* ctx, int32_t n, const spcn_image* tiles,
+                           const spcn_stats* tile_stats, const spcn_stats* tgt_st,
+                           const spcn_params* params, uint8_t* const* outs,
+                           const int64_t* out_pitches, double* p99_out, int32_t* status_out,
+                           void* stream) {
+  void* b = nullptr;
+  int rc = spcn_batch_create(ctx, n, tiles, tile_stats, tgt_st, params, outs, out_pitches, &b);
+  if (rc) return rc;
+  rc = spcn_batch_run(b, stream);
+  if (rc == SPCN_OK) rc = spcn_batch_results(b, p99_out, status_out, nullptr, stream);
+  spcn_batch_destroy(b);
+  return rc;
+}
+
+}  // extern "C"

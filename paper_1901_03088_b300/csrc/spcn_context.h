@@ -74,6 +74,27 @@ struct TimedLaunch {
 };
 int drain_timing(Context* c);
 
+// Selects the context's device for the duration of a call and restores the
+// caller's device afterwards.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) return;
+    ok = (prev == dev) || (cudaSetDevice(dev) == cudaSuccess);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// Argument checks shared by the entry points (spcn_api.cu).
+bool image_ok(const spcn_image* img);
+bool params_ok(const spcn_params* p);
+int stats_ok(const spcn_stats* s);            // SPCN_OK, INVALID_ARG or DEGENERATE_BASIS
+Geometry make_geometry(const spcn_image* img, uint8_t* out, int64_t out_pitch);
+
 int ensure_sample_capacity(Context* c, size_t n);
 int ensure_candidate_capacity(Context* c, int n);
 

@@ -1,0 +1,419 @@
+// Device code shared by the single-image pixel passes and the batched
+// persistent kernel: chunk traversal, the pass-1 window test, the exact
+// radix select, and the pass-2 reconstruction of a chunk.  Every kernel that
+// includes this header runs the same per-pixel arithmetic, so all of them
+// produce the same densities, keys and output bytes for the same pixel.
+#pragma once
+
+#include "spcn_internal.cuh"
+
+namespace spcn {
+
+// ------------------------------------------------------------ traversal
+struct ChunkPos {
+  u64 px;           // raster index of the chunk's first pixel
+  int64_t src_off;  // byte offset in the source
+  int64_t dst_off;  // byte offset in the destination
+  int n;            // valid pixels (16 except at row ends)
+};
+
+__device__ __forceinline__ ChunkPos chunk_pos(const Geometry& g, u64 q) {
+  ChunkPos p;
+  if (g.flat) {
+    p.px = q * kChunk;
+    const u64 left = (u64)g.npx - p.px;
+    p.n = left < (u64)kChunk ? (int)left : kChunk;
+    p.src_off = (int64_t)(p.px * 3);
+    p.dst_off = p.src_off;
+  } else {
+    const u64 y = div_chunks(q, g.cpr, g.magic);
+    const u64 x0 = (q - y * g.cpr) * kChunk;
+    const u64 left = (u64)g.width - x0;
+    p.n = left < (u64)kChunk ? (int)left : kChunk;
+    p.px = y * (u64)g.width + x0;
+    p.src_off = (int64_t)y * g.src_pitch + (int64_t)(x0 * 3);
+    p.dst_off = (int64_t)y * g.dst_pitch + (int64_t)(x0 * 3);
+  }
+  return p;
+}
+
+// Geometry of an image whose rows are contiguous in both source and
+// destination (one long row): the traversal needs only the two base
+// pointers and the pixel count, which keeps loops over tiles whose geometry
+// comes from memory (not from kernel parameters) within the register budget.
+struct FlatGeometry {
+  const uint8_t* src;
+  uint8_t* dst;
+  u64 npx;
+  int vec_src, vec_dst;
+};
+
+__device__ __forceinline__ ChunkPos chunk_pos(const FlatGeometry& g, u64 q) {
+  ChunkPos p;
+  p.px = q * kChunk;
+  const u64 left = g.npx - p.px;
+  p.n = left < (u64)kChunk ? (int)left : kChunk;
+  p.src_off = (int64_t)(p.px * 3);
+  p.dst_off = p.src_off;
+  return p;
+}
+
+__device__ __forceinline__ unsigned byte_at(const unsigned (&w)[12], int i) {
+  return (w[i >> 2] >> ((i & 3) * 8)) & 0xFFu;
+}
+
+// Load a chunk into 12 little-endian words; STREAM selects the evict-first
+// policy for data read for the last time.  Pixels past the end of a row read
+// as white (0xFF bytes): they fall outside every count of pass 1, and their
+// outputs are never stored, so every chunk takes the same unrolled path.
+template <bool STREAM, class G>
+__device__ __forceinline__ void load_chunk(const G& g, const ChunkPos& p,
+                                           unsigned (&w)[12]) {
+  const uint8_t* s = g.src + p.src_off;
+  if (p.n == kChunk && g.vec_src) {
+    const uint4* v = reinterpret_cast<const uint4*>(s);
+    uint4 a, b, c;
+    if (STREAM) {
+      a = __ldcs(v); b = __ldcs(v + 1); c = __ldcs(v + 2);
+    } else {
+      a = __ldg(v); b = __ldg(v + 1); c = __ldg(v + 2);
+    }
+    w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+    w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
+    w[8] = c.x; w[9] = c.y; w[10] = c.z; w[11] = c.w;
+  } else {
+#pragma unroll
+    for (int i = 0; i < 12; ++i) w[i] = 0xFFFFFFFFu;
+    const int nb = 3 * p.n;
+#pragma unroll
+    for (int i = 0; i < 48; ++i)
+      if (i < nb) w[i >> 2] = (w[i >> 2] & ~(0xFFu << ((i & 3) * 8))) |
+                              ((unsigned)__ldg(s + i) << ((i & 3) * 8));
+  }
+}
+
+template <class G>
+__device__ __forceinline__ void store_chunk(const G& g, const ChunkPos& p,
+                                            const unsigned (&o)[12]) {
+  uint8_t* d = g.dst + p.dst_off;
+  if (p.n == kChunk && g.vec_dst) {
+    uint4* v = reinterpret_cast<uint4*>(d);
+    __stcs(v, make_uint4(o[0], o[1], o[2], o[3]));
+    __stcs(v + 1, make_uint4(o[4], o[5], o[6], o[7]));
+    __stcs(v + 2, make_uint4(o[8], o[9], o[10], o[11]));
+  } else {
+    const int nb = 3 * p.n;
+#pragma unroll
+    for (int i = 0; i < 48; ++i)
+      if (i < nb) d[i] = (uint8_t)byte_at(o, i);
+  }
+}
+
+// Table offsets of the three channels of pixel k of a chunk.
+__device__ __forceinline__ void pixel_addr(const unsigned (&w)[12], int k, unsigned lr,
+                                           unsigned& aR, unsigned& aG, unsigned& aB) {
+  const int o = 3 * k;
+  aR = lut_addr(w[o >> 2], lr, o & 3);
+  aG = lut_addr(w[(o + 1) >> 2], lr, (o + 1) & 3);
+  aB = lut_addr(w[(o + 2) >> 2], lr, (o + 2) & 3);
+}
+
+// Strided loop over chunks q = q0, q0 + stride, ... < n; body(w, pos) is
+// called for every chunk.  With PREFETCH the next chunk's loads are issued
+// before the current chunk is processed (two register buffers, so no
+// copies); the issue-bound pass 1 runs faster without it, the
+// bandwidth-bound pass 2 with it.
+template <bool STREAM, bool PREFETCH, class G, class Body>
+__device__ __forceinline__ void for_chunks(const G& g, u64 q, u64 n, u64 stride,
+                                           Body&& body) {
+  if (!PREFETCH) {
+    for (; q < n; q += stride) {
+      const ChunkPos p = chunk_pos(g, q);
+      unsigned w[12];
+      load_chunk<STREAM>(g, p, w);
+      body(w, p);
+    }
+    return;
+  }
+  unsigned wa[12], wb[12];
+  ChunkPos pa, pb;
+  if (q < n) { pa = chunk_pos(g, q); load_chunk<STREAM>(g, pa, wa); }
+  while (q < n) {
+    u64 qn = q + stride;
+    if (qn < n) { pb = chunk_pos(g, qn); load_chunk<STREAM>(g, pb, wb); }
+    body(wa, pa);
+    q = qn;
+    if (q >= n) break;
+    qn = q + stride;
+    if (qn < n) { pa = chunk_pos(g, qn); load_chunk<STREAM>(g, pa, wa); }
+    body(wb, pb);
+    q = qn;
+  }
+}
+
+// Persistent grid-stride loop over all chunks of an image.
+template <bool STREAM, bool PREFETCH, class Body>
+__device__ __forceinline__ void for_each_chunk(const Geometry& g, Body&& body) {
+  for_chunks<STREAM, PREFETCH>(g, (u64)blockIdx.x * blockDim.x + threadIdx.x, g.nchunks,
+                               (u64)gridDim.x * blockDim.x, body);
+}
+
+// ------------------------------------------------------------ pass 1
+// Per-launch constants of pass 1, held in registers by the pixel loop.
+struct WindowConst {
+  u64* fine;
+  unsigned wthr, lo0, lo1, nb0, nb1;
+  float nk0, lk0, nk1, lk1;   // sat(h~ nk + lk) = [h~ < lo]   (exact, see window_of)
+  float nh0, hk0, nh1, hk1;   // sat(h~ nh + hk) = [h~ < lo + nb]
+};
+
+// Fire-and-forget increments (no return value, no compiler-side aggregation).
+__device__ __forceinline__ void red_add_global(u64* p, u64 v) {
+  asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" :: "l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void red_add_shared(unsigned* p, unsigned v) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("red.shared.add.u32 [%0], %1;" :: "r"(a), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void window_hit(const WindowConst& C, unsigned* s_coarse, unsigned r1,
+                                           unsigned r2) {
+  if (r1 < C.nb0) {
+    red_add_global(C.fine + r1, 1ull);
+    red_add_shared(s_coarse + (r1 >> kWinGroupBits), 1u);
+  }
+  if (r2 < C.nb1) {
+    red_add_global(C.fine + kWinBins + r2, 1ull);
+    red_add_shared(s_coarse + kWinGroups + (r2 >> kWinGroupBits), 1u);
+  }
+}
+
+// Pass 1 on one chunk.  Per pixel, all on the FMA pipe: the non-white flag
+// (as 0/1), [h~ < lo] and [h~ < hi] per stain by saturated FMAs, accumulated
+// with packed FMAs.  The number of windows a pixel falls in (0, 1 or 2) is
+// packed base 4 into `mask` (pixel pair p at digit 7-p, even pixels in the
+// low lane, odd pixels in the high lane): exact small integers in FP32.
+__device__ __forceinline__ void window_chunk(const unsigned (&w)[12], const char* lut,
+                                             unsigned lr, f2 NR1, f2 NR2, float kappa,
+                                             const WindowConst& a, f2& c_nw, f2& c_b0, f2& c_b1,
+                                             f2& mask) {
+  const f2 M1 = pk(-1.f, -1.f), FOUR = pk(4.f, 4.f);
+  mask = pk(0.f, 0.f);
+#pragma unroll
+  for (int p = 0; p < kChunk / 2; ++p) {
+    const int kA = 2 * p, kB = 2 * p + 1;
+    unsigned aRA, aGA, aBA, aRB, aGB, aBB;
+    pixel_addr(w, kA, lr, aRA, aGA, aBA);
+    pixel_addr(w, kB, lr, aRB, aGB, aBB);
+    f2 H1, H2;
+    solve_pair(lut, aRA, aGA, aBA, aRB, aGB, aBB, NR1, NR2, kappa, H1, H2);
+    const bool nwA = aRA < a.wthr || aGA < a.wthr || aBA < a.wthr;
+    const bool nwB = aRB < a.wthr || aGB < a.wthr || aBB < a.wthr;
+    const f2 NW = pk(nwA ? 1.f : 0.f, nwB ? 1.f : 0.f);
+    c_nw = add2(c_nw, NW);
+    const float h1A = lo_of(H1), h1B = hi_of(H1), h2A = lo_of(H2), h2B = hi_of(H2);
+    const f2 B0 = pk(fma_sat(h1A, a.nk0, a.lk0), fma_sat(h1B, a.nk0, a.lk0));
+    const f2 B1 = pk(fma_sat(h2A, a.nk1, a.lk1), fma_sat(h2B, a.nk1, a.lk1));
+    const f2 T0 = pk(fma_sat(h1A, a.nh0, a.hk0), fma_sat(h1B, a.nh0, a.hk0));
+    const f2 T1 = pk(fma_sat(h2A, a.nh1, a.hk1), fma_sat(h2B, a.nh1, a.hk1));
+    c_b0 = fma2(B0, NW, c_b0);
+    c_b1 = fma2(B1, NW, c_b1);
+    // T - B is 1 exactly for an in-window density
+    const f2 X = add2(fma2(B0, M1, T0), fma2(B1, M1, T1));
+    mask = fma2(mask, FOUR, mul2(X, NW));
+  }
+}
+
+constexpr int kWarpQueue = 64;    // queued chunks per warp; drained once 32 are waiting, so the
+                                  // re-read chunks are recent enough to still be in L2
+
+// ------------------------------------------------------------ radix fallback
+struct ImageSource {
+  Geometry g;
+  unsigned thr;
+  template <class F>
+  __device__ __forceinline__ void for_each(F&& f) const {
+    const unsigned lr = lane_reg();
+    const u64 stride = (u64)gridDim.x * blockDim.x;
+    for (u64 q = (u64)blockIdx.x * blockDim.x + threadIdx.x; q < g.nchunks; q += stride) {
+      const ChunkPos p = chunk_pos(g, q);
+      unsigned w[12];
+      load_chunk<false>(g, p, w);
+      for (int k = 0; k < p.n; ++k) {
+        const unsigned r = byte_at(w, 3 * k), gg = byte_at(w, 3 * k + 1), b = byte_at(w, 3 * k + 2);
+        unsigned aR, aG, aB;
+        pixel_addr(w, k, lr, aR, aG, aB);
+        f(aR, aG, aB, min(r, min(gg, b)) <= thr);
+      }
+    }
+  }
+};
+
+struct ListSource {
+  const uint32_t* items;   // packed R | G<<8 | B<<16, all non-white
+  u64 n;
+  template <class F>
+  __device__ __forceinline__ void for_each(F&& f) const {
+    const unsigned lr = lane_reg();
+    const u64 stride = (u64)gridDim.x * blockDim.x;
+    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+      const uint32_t v = __ldg(items + i);
+      f(lut_addr(v, lr, 0), lut_addr(v, lr, 1), lut_addr(v, lr, 2), true);
+    }
+  }
+};
+
+// Exact radix select (11/11/10-bit digits of the FP32 key of the scaled
+// densities) of the ranks rank[] whose track is active, over every non-white
+// pixel of `src`.  All blocks of a cooperative grid call it; it uses four
+// grid barriers (counter `bar`, zeroed before the launch).  Block 0 writes the
+// keys, the percentiles and the scale factors.  Returns false if a wait gave
+// up (the error is recorded).
+template <class Src>
+__device__ bool radix_select(const Src& src, const char* lut, const Lasso& L, SelectState* s,
+                             const u64 (&rank)[kTracks], const int (&active)[kTracks],
+                             u64* ghist, unsigned* s_hist, unsigned* bar, int* err,
+                             long long timeout_ns, double tgt0, double tgt1) {
+  __shared__ unsigned s_prefix[kTracks];
+  __shared__ u64 s_r[kTracks];
+  __shared__ int s_act[kTracks];
+  __shared__ int s_idx;
+  __shared__ u64 s_before;
+  __shared__ u64 s_tmp[33];
+  if (threadIdx.x == 0) {
+    for (int t = 0; t < kTracks; ++t) {
+      s_act[t] = active[t];
+      s_prefix[t] = 0u;
+      s_r[t] = rank[t];
+    }
+  }
+  const u64 gstride = (u64)gridDim.x * blockDim.x;
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < 3ull * kTracks * kRadixBins; i += gstride)
+    ghist[i] = 0ull;
+  unsigned target = gridDim.x;
+  if (!grid_barrier(bar, target, &s->abort, err, timeout_ns)) return false;
+  for (int d = 0; d < 3; ++d) {
+    const int shift = d == 0 ? 21 : (d == 1 ? 10 : 0);
+    const int hi = d == 0 ? 32 : (d == 1 ? 21 : 10);
+    const unsigned mask = d == 2 ? 0x3FFu : 0x7FFu;
+    for (int i = threadIdx.x; i < kTracks * kRadixBins; i += blockDim.x) s_hist[i] = 0u;
+    __syncthreads();
+    unsigned pre[kTracks];
+    int act[kTracks], own[kTracks];
+#pragma unroll
+    for (int t = 0; t < kTracks; ++t) { pre[t] = s_prefix[t]; act[t] = s_act[t]; }
+    // the two ranks of a stain share one histogram while their prefixes agree
+#pragma unroll
+    for (int t = 0; t < kTracks; ++t)
+      own[t] = ((t & 1) && act[t] && act[t - 1] && pre[t] == pre[t - 1]) ? t - 1 : t;
+    src.for_each([&](unsigned aR, unsigned aG, unsigned aB, bool nw) {
+      float h1, h2;
+      solve_one(lut, aR, aG, aB, L, h1, h2);
+      const unsigned key[2] = {__float_as_uint(h1), __float_as_uint(h2)};
+      const unsigned live = __activemask();
+#pragma unroll
+      for (int t = 0; t < kTracks; ++t) {
+        if (own[t] != t || !act[t]) continue;   // uniform across the block
+        const unsigned k = key[t >> 1];
+        const bool in = nw && (((u64)k >> hi) == ((u64)pre[t] >> hi));
+        // warp-aggregated increment: one atomic per distinct bin in the warp
+        const unsigned bin = in ? ((k >> shift) & mask) : 0xFFFFFFFFu;
+        const unsigned peers = __match_any_sync(live, bin);
+        if (in && (__ffs(peers) - 1) == (int)(threadIdx.x & 31u))
+          atomicAdd(s_hist + t * kRadixBins + bin, (unsigned)__popc(peers));
+      }
+    });
+    __syncthreads();
+    u64* gh = ghist + (size_t)d * kTracks * kRadixBins;
+    for (int i = threadIdx.x; i < kTracks * kRadixBins; i += blockDim.x)
+      if (s_hist[i]) atomicAdd(gh + i, (u64)s_hist[i]);
+    target += gridDim.x;
+    if (!grid_barrier(bar, target, &s->abort, err, timeout_ns)) return false;
+    for (int t = 0; t < kTracks; ++t) {
+      if (!s_act[t]) continue;
+      block_find_rank(gh + (size_t)own[t] * kRadixBins, kRadixBins, s_r[t], &s_idx, &s_before, s_tmp);
+      if (threadIdx.x == 0) {
+        if (s_idx < 0) {         // fewer pixels than the rank: cannot happen
+          record_error(err, SPCN_ERR_CUDA);
+          s_act[t] = 0;
+        } else {
+          s_prefix[t] |= (unsigned)s_idx << shift;
+          s_r[t] -= s_before;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    for (int t = 0; t < kTracks; ++t)
+      if (s_act[t]) { s->key[t] = s_prefix[t]; s->resolved[t] = 1; }
+    finish_percentiles(s, tgt0, tgt1, L.hscale);
+    __threadfence();
+    s->all_resolved = 1;
+  }
+  return true;
+}
+
+// ------------------------------------------------------------ pass 2
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Four rounded values (byte 0 of each word) packed little-endian.
+__device__ __forceinline__ unsigned pack4(unsigned a, unsigned b, unsigned c, unsigned d) {
+  return __byte_perm(__byte_perm(a, b, 0x0040u), __byte_perm(c, d, 0x0040u), 0x5410u);
+}
+
+struct ReconConst {
+  f2 M1[3], M2[3], L2[3];   // exponent: e_c = L2_c + M1_c h~1 + M2_c h~2 (both lanes equal)
+};
+
+__device__ __forceinline__ void recon_chunk(const unsigned (&w)[12], const char* lut,
+                                            unsigned lr, f2 NR1, f2 NR2, float kappa,
+                                            const ReconConst& K, unsigned (&o)[12]) {
+  unsigned y[48];
+#pragma unroll
+  for (int p = 0; p < kChunk / 2; ++p) {
+    const int kA = 2 * p, kB = 2 * p + 1;
+    unsigned aRA, aGA, aBA, aRB, aGB, aBB;
+    pixel_addr(w, kA, lr, aRA, aGA, aBA);
+    pixel_addr(w, kB, lr, aRB, aGB, aBB);
+    f2 H1, H2;
+    solve_pair(lut, aRA, aGA, aBA, aRB, aGB, aBB, NR1, NR2, kappa, H1, H2);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      // Eq. 3-4: i' = i0_t 2^(-log2e sum_j W_t[c,j] s_j h_j)
+      const f2 E = fma2(K.M1[c], H1, fma2(K.M2[c], H2, K.L2[c]));
+      // round half to even: adding 1.5*2^23 leaves round(x) in the low bits
+      const f2 X = add2(pk(ex2_approx(lo_of(E)), ex2_approx(hi_of(E))), pk(12582912.0f, 12582912.0f));
+      y[3 * kA + c] = __float_as_uint(lo_of(X));
+      y[3 * kB + c] = __float_as_uint(hi_of(X));
+    }
+    // pack every output word whose four bytes are now known
+#pragma unroll
+    for (int i = 0; i < 12; ++i)
+      if (4 * i + 3 <= 6 * p + 5 && 4 * i + 3 > 6 * p - 1)
+        o[i] = pack4(y[4 * i], y[4 * i + 1], y[4 * i + 2], y[4 * i + 3]);
+  }
+}
+
+// Pass-2 exponent coefficients of one image: M[3j+c] = -log2(e) W_t[c,j] s_j
+// 2^hexp (Eq. 3-4 with the table's power-of-two scale folded in).  Computed in
+// FP64 and rounded once, identically by every kernel that reconstructs.
+__device__ __forceinline__ float recon_coef(const float* Wt, const double* scale, float hscale,
+                                            int i) {
+  const int c = i % 3, j = i / 3;
+  return (float)(-(double)Wt[3 * j + c] * scale[j] * (double)hscale * 1.4426950408889634);
+}
+
+// Constants of the exact test sat(h~ * nk + lk) = [h~ < key] (host side).
+void below_consts(unsigned key, float* nk, float* lk);
+
+// Window [lo, lo+nb) of FP32 keys around a percentile hint, and the constants
+// of its exact below-window and below-window-end tests (host side).
+void window_of(double hint, unsigned* lo, unsigned* nb, float* nk, float* lk, float* nh,
+               float* hk);
+
+}  // namespace spcn

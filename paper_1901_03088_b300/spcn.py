@@ -73,6 +73,20 @@ class Stats(ctypes.Structure):
         return s
 
 
+class BatchConfig(ctypes.Structure):
+    _fields_ = [("item_chunks", ctypes.c_int32), ("schedule", ctypes.c_int32),
+                ("group_px", ctypes.c_int64), ("ms", ctypes.c_float), ("pad", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {"item_chunks": int(self.item_chunks),
+                "schedule": SCHEDULES_INV.get(int(self.schedule), int(self.schedule)),
+                "group_px": int(self.group_px), "ms": float(self.ms)}
+
+
+SCHEDULES = {"phased": 0, "interleaved": 1}
+SCHEDULES_INV = {v: k for k, v in SCHEDULES.items()}
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: run `python -m paper_1901_03088_b300.build`")
@@ -100,6 +114,17 @@ def _load():
         "spcn_normalize_f32_backward": (ctypes.c_int, [vp, vp, vp, i32, i32, i32, P(Stats),
                                                        P(Stats), vp, P(Params), vp, vp, vp]),
         "spcn_kernel_times": (ctypes.c_int, [vp, ctypes.c_int, P(ctypes.c_double), P(i64)]),
+        "spcn_batch_create": (ctypes.c_int, [vp, i32, P(Image), P(Stats), P(Stats), P(Params),
+                                             P(vp), P(i64), P(vp)]),
+        "spcn_batch_run": (ctypes.c_int, [vp, vp]),
+        "spcn_batch_results": (ctypes.c_int, [vp, P(ctypes.c_double), P(i32), P(i32), vp]),
+        "spcn_batch_get_config": (ctypes.c_int, [vp, P(BatchConfig)]),
+        "spcn_batch_set_config": (ctypes.c_int, [vp, P(BatchConfig)]),
+        "spcn_batch_tune": (ctypes.c_int, [vp, i32, P(BatchConfig), i32, P(i32), vp]),
+        "spcn_batch_destroy": (ctypes.c_int, [vp]),
+        "spcn_normalize_batched": (ctypes.c_int, [vp, i32, P(Image), P(Stats), P(Stats),
+                                                  P(Params), P(vp), P(i64), P(ctypes.c_double),
+                                                  P(i32), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -117,8 +142,12 @@ EXPORTED = ("spcn_params_default", "spcn_context_create", "spcn_context_destroy"
             "spcn_estimate_basis", "spcn_stain_percentile", "spcn_stain_densities",
             "spcn_normalize", "spcn_synchronize", "spcn_launch_count", "spcn_strerror",
             "spcn_debug_barrier_timeout", "spcn_kernel_timing", "spcn_kernel_times",
-            "spcn_estimate_basis_noalloc", "spcn_normalize_f32", "spcn_normalize_f32_backward")
-KERNELS = {"pass1": 0, "select": 1, "pass2": 2, "density": 3, "f32_fwd": 4, "f32_bwd": 5}
+            "spcn_estimate_basis_noalloc", "spcn_normalize_f32", "spcn_normalize_f32_backward",
+            "spcn_batch_create", "spcn_batch_run", "spcn_batch_results", "spcn_batch_get_config",
+            "spcn_batch_set_config", "spcn_batch_tune", "spcn_batch_destroy",
+            "spcn_normalize_batched")
+KERNELS = {"pass1": 0, "select": 1, "pass2": 2, "density": 3, "f32_fwd": 4, "f32_bwd": 5,
+           "batch": 6}
 
 
 def params(**kw) -> Params:
@@ -361,3 +390,105 @@ def normalize_f32(ctx: "Context", x, W_target, src_stats, tgt_stats: Stats, p: P
         raise ValueError("one source Stats per image")
     return _NormalizeF32Fn.apply(x, W_target, ctx.handle, stats_array(src_stats), tgt_stats,
                                  p or params())
+
+
+# ---------------------------------------------------------------------------
+# Batches: many tiles, one target, one persistent launch
+# ---------------------------------------------------------------------------
+def _batch_arrays(tiles, tile_stats, outs):
+    n = len(tiles)
+    if n < 1 or len(tile_stats) != n or len(outs) != n:
+        raise ValueError("one source Stats and one output per tile")
+    imgs = (Image * n)()
+    out_p = (ctypes.c_void_p * n)()
+    pitches = (ctypes.c_int64 * n)()
+    for i, (t, o) in enumerate(zip(tiles, outs)):
+        imgs[i] = image_of(t)
+        if (tuple(o.shape) != tuple(t.shape) or o.dtype != t.dtype or o.stride(2) != 1 or
+                o.stride(1) != 3 or not o.is_cuda):
+            raise ValueError("each output must be an (H, W, 3) uint8 interleaved CUDA tensor "
+                             "of its tile's size")
+        out_p[i] = o.data_ptr()
+        pitches[i] = o.stride(0)
+    return imgs, stats_array(tile_stats), out_p, pitches
+
+
+class Batch:
+    """A fixed table of tiles (each with its own source Stats) normalised to
+    one target by one cooperative persistent launch (spcn_batch_*).
+
+    ``run`` is asynchronous and allocation-free, so it can be captured into a
+    CUDA graph; the tiles and outputs must stay allocated while the batch is
+    used (this object keeps references to them)."""
+
+    def __init__(self, ctx: "Context", tiles, tile_stats, tgt_stats: Stats, outs,
+                 p: Params | None = None):
+        imgs, st, out_p, pitches = _batch_arrays(tiles, tile_stats, outs)
+        self.p = p or params()
+        self.tgt = tgt_stats.copy()
+        h = ctypes.c_void_p()
+        rc = _lib.spcn_batch_create(ctx.handle, len(tiles), imgs, st, ctypes.byref(self.tgt),
+                                    ctypes.byref(self.p), out_p, pitches, ctypes.byref(h))
+        _check(rc, "spcn_batch_create")
+        self._h = h
+        self.n = len(tiles)
+        self._keep = (ctx, list(tiles), list(outs), imgs, st, out_p, pitches)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.spcn_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, stream=None):
+        _check(_lib.spcn_batch_run(self._h, _stream(stream)), "spcn_batch_run")
+
+    def results(self, stream=None, fallback: bool = False):
+        """(p99 as a list of (p0, p1) per tile, status per tile[, fallback
+        flag per tile]); waits."""
+        p99 = (ctypes.c_double * (2 * self.n))()
+        status = (ctypes.c_int32 * self.n)()
+        fb = (ctypes.c_int32 * self.n)()
+        _check(_lib.spcn_batch_results(self._h, p99, status, fb, _stream(stream)),
+               "spcn_batch_results")
+        out = ([(p99[2 * i], p99[2 * i + 1]) for i in range(self.n)], list(status))
+        return out + (list(fb),) if fallback else out
+
+    @property
+    def config(self) -> dict:
+        c = BatchConfig()
+        _check(_lib.spcn_batch_get_config(self._h, ctypes.byref(c)), "spcn_batch_get_config")
+        return c.as_dict()
+
+    def set_config(self, item_chunks: int, schedule: str = "phased", group_px: int = 0):
+        c = BatchConfig(int(item_chunks), SCHEDULES[schedule], int(group_px), 0.0, 0)
+        _check(_lib.spcn_batch_set_config(self._h, ctypes.byref(c)), "spcn_batch_set_config")
+
+    def tune(self, reps: int = 3, stream=None):
+        """Run the library's autotuner; returns every trial (dicts with the
+        mean ms per run) and leaves the fastest schedule selected."""
+        trials = (BatchConfig * 64)()
+        n = ctypes.c_int32()
+        _check(_lib.spcn_batch_tune(self._h, int(reps), trials, 64, ctypes.byref(n),
+                                    _stream(stream)), "spcn_batch_tune")
+        return [trials[i].as_dict() for i in range(n.value)]
+
+
+def normalize_batched(ctx: "Context", tiles, tile_stats, tgt_stats: Stats, outs,
+                      p: Params | None = None, stream=None):
+    """One-shot batch (create, run, results, destroy); returns (p99, status)
+    as in Batch.results.  Blocks."""
+    imgs, st, out_p, pitches = _batch_arrays(tiles, tile_stats, outs)
+    p = p or params()
+    n = len(tiles)
+    p99 = (ctypes.c_double * (2 * n))()
+    status = (ctypes.c_int32 * n)()
+    rc = _lib.spcn_normalize_batched(ctx.handle, n, imgs, st, ctypes.byref(tgt_stats),
+                                     ctypes.byref(p), out_p, pitches, p99, status, _stream(stream))
+    _check(rc, "spcn_normalize_batched")
+    return [(p99[2 * i], p99[2 * i + 1]) for i in range(n)], list(status)

@@ -184,3 +184,19 @@ def make_image_torch(height: int, width: int, seed: int, W=None, device="cpu",
         out[r0:r1].copy_(torch.clamp(torch.round(I), 0, 255).to(torch.uint8))
         del I
     return out
+
+
+def batch_layout(n_slides: int, per_slide: int, side_lo: int, side_hi: int, seed: int):
+    """Tile sizes of a batch of uneven tiles: for each of ``n_slides`` slides,
+    ``per_slide`` tiles whose width and height are drawn independently,
+    log-uniformly in [side_lo, side_hi].  Returns (slide, height, width)
+    triples, slide-major; slide s uses the basis ``stain_basis(2000 + s)``
+    and tile k the image seed ``3000 + k``."""
+    rng = np.random.default_rng(seed)
+    lo, hi = math.log(side_lo), math.log(side_hi)
+    out = []
+    for s in range(n_slides):
+        for _ in range(per_slide):
+            h, w = (int(round(math.exp(rng.uniform(lo, hi)))) for _ in range(2))
+            out.append((s, min(max(h, side_lo), side_hi), min(max(w, side_lo), side_hi)))
+    return out

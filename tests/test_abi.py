@@ -55,16 +55,19 @@ int main(void) {
   printf("%zu %zu %zu %zu\n", offsetof(spcn_stats, p99), offsetof(spcn_stats, iters),
          offsetof(spcn_stats, n_sample), offsetof(spcn_stats, objective));
   printf("%zu %zu\n", offsetof(spcn_params, seed), offsetof(spcn_params, flags));
+  printf("%zu %zu %zu\n", sizeof(spcn_batch_config), offsetof(spcn_batch_config, group_px),
+         offsetof(spcn_batch_config, ms));
   return 0;
 }
 ''')
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
     got = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
-    S, P, I = lib.Stats, lib.Params, lib.Image
+    S, P, I, B = lib.Stats, lib.Params, lib.Image, lib.BatchConfig
     want = [ctypes.sizeof(I), ctypes.sizeof(P), ctypes.sizeof(S),
             S.p99.offset, S.iters.offset, S.n_sample.offset, S.objective.offset,
-            P.seed.offset, P.flags.offset]
+            P.seed.offset, P.flags.offset,
+            ctypes.sizeof(B), B.group_px.offset, B.ms.offset]
     assert [int(x) for x in got] == want
 
 
@@ -81,3 +84,6 @@ def test_strerror_and_no_device_behaviour(lib):
     assert lib.lib.spcn_context_create(None, 0) == -1
     assert lib.lib.spcn_estimate_basis(None, None, None, None, None) == -1
     assert lib.lib.spcn_synchronize(None, None) == -1
+    assert lib.lib.spcn_batch_create(None, 0, None, None, None, None, None, None, None) == -1
+    assert lib.lib.spcn_batch_run(None, None) == -1
+    assert lib.lib.spcn_batch_destroy(None) == 0
