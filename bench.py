@@ -362,7 +362,8 @@ def run_batch(args, world, rank, local):
     torch.cuda.set_device(dev)
     wl = WORKLOADS["batch"]
     t0 = time.time()
-    layout = synth.batch_layout(wl["slides"], wl["per_slide"], wl["side_lo"], wl["side_hi"],
+    n_slides = args.slides or wl["slides"]
+    layout = synth.batch_layout(n_slides, wl["per_slide"], wl["side_lo"], wl["side_hi"],
                                 seed=3 + rank)
     tiles = [synth.make_image_torch(h, w, 3000 + 256 * rank + k,
                                     W=synth.stain_basis(2000 + s), device=dev, blobs=True)
@@ -371,7 +372,7 @@ def run_batch(args, world, rank, local):
     ctx = spcn.Context(local)
     p = spcn.params(sample_mode="hash", sample_rate=wl["sample_rate"], seed=0)
     slide_st = []
-    for s in range(wl["slides"]):
+    for s in range(n_slides):
         smp = synth.make_image_torch(wl["slide_sample"], wl["slide_sample"], 2100 + s,
                                      W=synth.stain_basis(2000 + s), device=dev, blobs=True)
         slide_st.append(ctx.estimate_basis(smp, p))
@@ -395,7 +396,7 @@ def run_batch(args, world, rank, local):
     b = spcn.Batch(ctx, tiles, stats, t_st, outs, p)
     create_ms = 1e3 * (time.perf_counter() - t1)
     t1 = time.perf_counter()
-    trials = b.tune(reps=3)
+    trials = [] if args.no_tune else b.tune(reps=3)
     tune_s = time.perf_counter() - t1
     side = torch.cuda.Stream(device=dev)
     side.wait_stream(torch.cuda.current_stream())
@@ -492,7 +493,7 @@ def run_batch(args, world, rank, local):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {
-            "workload": f"batch: {len(tiles)} uint8 RGB tiles from {wl['slides']} slides, sides "
+            "workload": f"batch: {len(tiles)} uint8 RGB tiles from {n_slides} slides, sides "
                         f"log-uniform in [{wl['side_lo']}, {wl['side_hi']}], {npx / 1e6:.1f} Mpx, "
                         f"per-slide statistics (1% hash sample of a {wl['slide_sample']}^2 slide "
                         f"sample), {wl['tgt']}x{wl['tgt']} target",
@@ -694,6 +695,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--slides", type=int, default=0,
+                    help="batch workload: number of slides (default 32, 8 tiles each)")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="batch workload: keep the default schedule (no autotuner runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")

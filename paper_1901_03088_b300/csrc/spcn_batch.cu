@@ -40,17 +40,25 @@
 
 namespace spcn {
 
+#ifndef SPCN_BATCH_THREADS
+#define SPCN_BATCH_THREADS 1024
+#endif
+constexpr int kBatchThreads = SPCN_BATCH_THREADS;   // one block per SM (shared memory)
 constexpr int kKeyBuf = 128;       // keys per stain buffered per warp before a flush
 constexpr int kSelBits = 12;       // digit width of the in-list select
 constexpr int kSelBins = 1 << kSelBits;
 constexpr double kOpenLow = 0.75;  // window start, relative to the hint
-constexpr int kWarps = kPassThreads / 32;
+constexpr int kWarps = kBatchThreads / 32;
 constexpr size_t kBatchQueueBytes = sizeof(uint2) * kWarpQueue * kWarps;
-constexpr size_t kBatchWork = kBatchQueueBytes + sizeof(unsigned) * 2 * kKeyBuf * kWarps;
+constexpr size_t cmax(size_t x, size_t y) { return x > y ? x : y; }
+// per-warp queues and key buffers (pass 1), overlaid by the select and the
+// fallback's radix histograms
+constexpr size_t kBatchWork = cmax(kBatchQueueBytes + sizeof(unsigned) * 2 * kKeyBuf * kWarps,
+                                   cmax(sizeof(unsigned) * kTracks * kRadixBins,
+                                        sizeof(unsigned) * 2 * kSelBins));
 constexpr size_t kBatchSmem = kLutSmemBytes + kBatchWork;
 static_assert(kBatchWork >= sizeof(unsigned) * kTracks * kRadixBins, "radix histograms overlay the pass-1 buffers");
 static_assert(kBatchWork >= sizeof(unsigned) * 2 * kSelBins, "select histograms overlay the pass-1 buffers");
-static_assert(kSelBins % kPassThreads == 0, "whole bins per thread");
 
 // One tile of the batch (device, read-only during a run).
 struct BatchTile {
@@ -73,6 +81,8 @@ struct BatchTileState {
   int ready;               // 0: pass 1 running, 1: scale known, 2: exact fallback needed
   int status;              // SPCN_OK or SPCN_ERR_NO_TISSUE
   int fallback;            // 1: the percentile needed the exact fallback
+  float M[6];              // pass-2 coefficients (recon_coef), set with ready = 1
+  int pad2[2];
 };
 
 // Run-wide state (zeroed before every run).
@@ -84,8 +94,10 @@ struct BatchRunState {
 };
 
 struct BatchItem {
-  unsigned tile;
+  unsigned tile;           // ~0u: no item (end of the queue)
   unsigned pass;           // 1 or 2
+  unsigned model;          // the tile's table
+  unsigned n_items1;       // pass-1 items of the tile
   u64 c0, c1;              // chunk range [c0, c1) of the tile
 };
 
@@ -105,6 +117,19 @@ struct BatchArgs {
   float l2i0[3];           // log2 of the target i0
   long long timeout_ns;
 };
+
+// 32-byte item descriptor, global -> shared, without holding registers.
+__device__ __forceinline__ void copy_item_async(BatchItem* dst, const BatchItem* src) {
+  static_assert(sizeof(BatchItem) == 32, "two 16-byte copies");
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const char* g = reinterpret_cast<const char*>(src);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" :: "r"(d), "l"(g) : "memory");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" :: "r"(d + 16u), "l"(g + 16) : "memory");
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
 
 __device__ __forceinline__ int ld_acquire_s32(const int* p) {
   int v;
@@ -154,9 +179,12 @@ __device__ __forceinline__ void flush_keys(const unsigned* kb, int kc, unsigned*
 }
 
 // Keys of the queued chunks' flagged pixels (same arithmetic as pass 1, so
-// the same keys), appended to the warp's key buffers.  Warp-uniform: every
-// lane runs the same number of steps, one flagged pixel per lane and step.
-// The tile's list pointers are read here, not held by the pixel loop.
+// the same keys), appended to the warp's key buffers.  The flagged pixels of
+// up to 32 queue entries are numbered by a warp prefix sum, and each step
+// gives every lane one of them (its entry by a binary search over the
+// prefix sums, its pixel as the n-th set bit of the entry's mask), so no
+// lane idles while another entry still has pixels left.  Warp-uniform.  The
+// tile's list pointers are read here, not held by the pixel loop.
 template <class G>
 __device__ __noinline__ void batch_drain(const uint2* queue, int count, u64 c0, const G& g,
                                          const char* lut, unsigned lr, const Lasso& L,
@@ -170,25 +198,43 @@ __device__ __noinline__ void batch_drain(const uint2* queue, int count, u64 c0, 
   const unsigned lane = threadIdx.x & 31u;
   const unsigned lt = (1u << lane) - 1u;
   for (int e0 = 0; e0 < count; e0 += 32) {
-    unsigned m = 0u;
-    const uint8_t* src = g.src;
+    // d: bit 2i set when digit i of the entry's mask is non-zero (digits
+    // 0-7: even pixels, pair 7-i; digits 8-15: odd pixels, pair 15-i)
+    unsigned d = 0u, q = 0u;
     if (e0 + (int)lane < count) {
       const uint2 ent = queue[e0 + lane];
-      const ChunkPos p = chunk_pos(g, c0 + ent.x);
-      src = g.src + p.src_off;
-      m = ent.y;
+      q = ent.x;
+      d = (ent.y | (ent.y >> 1)) & 0x55555555u;
     }
-    // m: base-4 digits of the window counts, even pixels in bits 0-15 (pair
-    // p at digit 7-p), odd pixels in bits 16-31
-    while (__any_sync(0xFFFFFFFFu, m != 0u)) {
+    const unsigned n = __popc(d);
+    unsigned incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned t = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if ((int)lane >= o) incl += t;
+    }
+    const unsigned total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    const unsigned excl = incl - n;
+    for (unsigned s0 = 0; s0 < total; s0 += 32) {
+      const unsigned sl = s0 + lane;
+      // owner entry: the first lane whose inclusive sum exceeds sl
+      int j = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const unsigned v = __shfl_sync(0xFFFFFFFFu, incl, j + step - 1);
+        if (v <= sl) j += step;
+      }
+      const unsigned dj = __shfl_sync(0xFFFFFFFFu, d, j & 31);
+      const unsigned qj = __shfl_sync(0xFFFFFFFFu, q, j & 31);
+      const unsigned ej = __shfl_sync(0xFFFFFFFFu, excl, j & 31);
       unsigned k0 = 0u, k1 = 0u;
       bool in0 = false, in1 = false;
-      if (m != 0u) {
-        const int bit = __ffs(m) - 1;
-        m &= ~(3u << (bit & ~1));
-        const int k = 2 * (7 - ((bit & 15) >> 1)) + (bit >> 4);
-        const unsigned r = __ldg(src + 3 * k), gg = __ldg(src + 3 * k + 1),
-                       b = __ldg(src + 3 * k + 2);
+      if (sl < total) {
+        const int i = (int)__fns(dj, 0u, (int)(sl - ej) + 1) >> 1;
+        const int k = 2 * (7 - (i & 7)) + (i >> 3);
+        const ChunkPos p = chunk_pos(g, c0 + qj);
+        const uint8_t* src = g.src + p.src_off + 3 * k;
+        const unsigned r = __ldg(src), gg = __ldg(src + 1), b = __ldg(src + 2);
         float h1, h2;
         solve_one(lut, (r << 8) | lr, (gg << 8) | lr, (b << 8) | lr, L, h1, h2);
         k0 = __float_as_uint(h1);
@@ -214,20 +260,21 @@ __device__ __noinline__ void batch_drain(const uint2* queue, int count, u64 c0, 
 }
 
 // First bin whose inclusive prefix exceeds r in a shared histogram of n
-// counts (n a multiple of the block size).  *s_idx = -1 if the total is <= r.
+// counts.  *s_idx = -1 if the total is <= r.
 __device__ __forceinline__ void smem_find_rank(const unsigned* hist, int n, u64 r, int* s_idx,
                                                u64* s_before, u64* s_tmp) {
-  const int per = n / (int)blockDim.x;
-  const int beg = (int)threadIdx.x * per;
+  const int per = (n + (int)blockDim.x - 1) / (int)blockDim.x;
+  const int beg = min(n, (int)threadIdx.x * per);
+  const int cnt = min(per, n - beg);
   u64 local = 0;
-  for (int i = 0; i < per; ++i) local += hist[beg + i];
+  for (int i = 0; i < cnt; ++i) local += hist[beg + i];
   u64 total;
   const u64 excl = block_excl_scan(local, s_tmp, &total);
   if (threadIdx.x == 0) *s_idx = -1;
   __syncthreads();
   if (local > 0 && excl <= r && r < excl + local) {
     u64 c = excl;
-    for (int i = 0; i < per; ++i) {
+    for (int i = 0; i < cnt; ++i) {
       const u64 x = hist[beg + i];
       if (r < c + x) { *s_idx = beg + i; *s_before = c; break; }
       c += x;
@@ -260,6 +307,8 @@ __device__ void batch_select(const BatchArgs& a, unsigned tile, unsigned* s_hist
       s->scale[0] = s->scale[1] = 1.0;
       s->t = 0.0;
       s->all_resolved = 1;
+      const float hs = a.models[T->model].lasso.hscale;
+      for (int i = 0; i < 6; ++i) S->M[i] = recon_coef(a.Wt, s->scale, hs, i);
       __threadfence();
       st_release_s32(&S->ready, 1);
     }
@@ -351,7 +400,11 @@ __device__ void batch_select(const BatchArgs& a, unsigned tile, unsigned* s_hist
   if (threadIdx.x == 0) {
     int all = 1;
     for (int t = 0; t < kTracks; ++t) { s->resolved[t] = s_res[t]; all &= s_res[t]; }
-    if (all) finish_percentiles(s, a.tgt0, a.tgt1, a.models[T->model].lasso.hscale);
+    if (all) {
+      const float hs = a.models[T->model].lasso.hscale;
+      finish_percentiles(s, a.tgt0, a.tgt1, hs);
+      for (int i = 0; i < 6; ++i) S->M[i] = recon_coef(a.Wt, s->scale, hs, i);
+    }
     s->all_resolved = all;
     __threadfence();
     st_release_s32(&S->ready, all ? 1 : 2);
@@ -414,10 +467,9 @@ __device__ __forceinline__ FlatGeometry geometry_as<FlatGeometry>(const Geometry
 
 // One pass-1 item: chunks [c0, c1) of a tile, by the whole block.
 template <class G>
-__device__ __forceinline__ void batch_pass1(const BatchArgs& a, unsigned tile, u64 c0, u64 c1,
-                                            const char* lut, unsigned lr, uint2* s_queue,
-                                            unsigned* s_kb, unsigned* s_hist, u64* s_tmp,
-                                            int* s_last) {
+__device__ __forceinline__ unsigned batch_pass1(const BatchArgs& a, unsigned tile, u64 c0,
+                                                u64 c1, const char* lut, unsigned lr,
+                                                uint2* s_queue, unsigned* s_kb, unsigned* s_cnt) {
   const BatchTile* T = a.tiles + tile;
   BatchTileState* S = a.state + tile;
   const G g = geometry_as<G>(T->g);
@@ -456,23 +508,37 @@ __device__ __forceinline__ void batch_pass1(const BatchArgs& a, unsigned tile, u
   __syncwarp();
   flush_keys(kb0, kc0, T->keys, T->list_cap, S->list_n, S->kmax);
   flush_keys(kb1, kc1, T->keys + T->list_cap, T->list_cap, S->list_n + 1, S->kmax + 1);
-  // per-thread counts are exact in FP32 (fewer than 2^24 pixels per thread)
-  const u64 t_nw = block_sum((u64)lo_of(c_nw) + (u64)hi_of(c_nw), s_tmp);
-  const u64 t_b0 = block_sum((u64)lo_of(c_b0) + (u64)hi_of(c_b0), s_tmp);
-  const u64 t_b1 = block_sum((u64)lo_of(c_b1) + (u64)hi_of(c_b1), s_tmp);
+  // per-thread counts are exact in FP32 (fewer than 2^24 pixels per thread),
+  // per-warp sums fit 32 bits; one shared-memory round gives thread 0 the
+  // block's counts
+  unsigned v0 = (unsigned)lo_of(c_nw) + (unsigned)hi_of(c_nw);
+  unsigned v1 = (unsigned)lo_of(c_b0) + (unsigned)hi_of(c_b0);
+  unsigned v2 = (unsigned)lo_of(c_b1) + (unsigned)hi_of(c_b1);
+  v0 = __reduce_add_sync(0xFFFFFFFFu, v0);
+  v1 = __reduce_add_sync(0xFFFFFFFFu, v1);
+  v2 = __reduce_add_sync(0xFFFFFFFFu, v2);
+  if (lane == 0) {
+    s_cnt[3 * (threadIdx.x >> 5)] = v0;
+    s_cnt[3 * (threadIdx.x >> 5) + 1] = v1;
+    s_cnt[3 * (threadIdx.x >> 5) + 2] = v2;
+  }
+  __threadfence();   // this thread's key stores before the completion ticket
+  __syncthreads();
+  unsigned ticket = 0u;
   if (threadIdx.x == 0) {
+    u64 t_nw = 0, t_b0 = 0, t_b1 = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      t_nw += s_cnt[3 * w];
+      t_b0 += s_cnt[3 * w + 1];
+      t_b1 += s_cnt[3 * w + 2];
+    }
     if (t_nw) atomicAdd(&S->sel.n_nw, t_nw);
     if (t_b0) atomicAdd(&S->sel.below[0], t_b0);
     if (t_b1) atomicAdd(&S->sel.below[1], t_b1);
-  }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) *s_last = atomicAdd(&S->done1, 1u) == T->n_items1 - 1u;
-  __syncthreads();
-  if (*s_last) {
     __threadfence();
-    batch_select(a, tile, s_hist, s_tmp);
+    ticket = atomicAdd(&S->done1, 1u);   // read at the next loop top
   }
+  return ticket;
 }
 
 // One pass-2 item: chunks [c0, c1) of a tile, by the whole block.
@@ -494,7 +560,7 @@ __device__ __forceinline__ void batch_pass2(const BatchArgs& a, unsigned tile, u
 
 
 template <class G>
-__global__ void __launch_bounds__(kPassThreads, 1) k_batch(BatchArgs a) {
+__global__ void __launch_bounds__(kBatchThreads, 1) k_batch(BatchArgs a) {
   extern __shared__ __align__(16) char s_dyn[];
   char* lut = s_dyn;
   char* work = s_dyn + kLutSmemBytes;
@@ -503,43 +569,77 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_batch(BatchArgs a) {
   unsigned* s_kb = reinterpret_cast<unsigned*>(work + kBatchQueueBytes) + warp * 2 * kKeyBuf;
   unsigned* s_hist = reinterpret_cast<unsigned*>(work);   // select / radix histograms (overlay)
   __shared__ u64 s_tmp[33];
-  __shared__ unsigned s_item;
-  __shared__ int s_go, s_last;
+  __shared__ unsigned s_cnt[3 * 32];
+  __shared__ __align__(16) BatchItem s_items[2];   // current item and the prefetched next one
+  __shared__ int s_go, s_sel_tile;
   __shared__ float s_M[6];
   const unsigned lr = lane_reg();
   int cur_model = -1;
+  // Thread 0 runs the queue one item ahead: the next item's descriptor is
+  // copied into shared memory asynchronously (cp.async) and the ticket of the
+  // one after it is in flight while the block works; the completion ticket of
+  // a pass-1 item is read at the next loop top.
+  unsigned t_next = 0u, pend_tile = ~0u, pend_ticket = 0u, pend_last = 0u;
+  int cur = 0;
+  if (threadIdx.x == 0) {
+    const unsigned t1 = atomicAdd(&a.run->next, 1u);
+    if (t1 < a.n_items) copy_item_async(&s_items[1], a.items + t1);
+    else s_items[1].tile = ~0u;
+    t_next = atomicAdd(&a.run->next, 1u);
+  }
   for (;;) {
-    __syncthreads();   // previous item done: shared words and the table may be rewritten
-    if (threadIdx.x == 0) s_item = atomicAdd(&a.run->next, 1u);
+    cur ^= 1;
+    if (threadIdx.x == 0) {
+      s_sel_tile = (pend_tile != ~0u && pend_ticket == pend_last) ? (int)pend_tile : -1;
+      pend_tile = ~0u;
+      cp_async_wait_all();
+      BatchItem* nx = &s_items[cur ^ 1];   // read by nobody until the next loop top
+      if (s_items[cur].tile != ~0u && t_next < a.n_items) {
+        copy_item_async(nx, a.items + t_next);
+        t_next = atomicAdd(&a.run->next, 1u);
+      } else {
+        nx->tile = ~0u;
+      }
+    }
     __syncthreads();
-    const unsigned it = s_item;
-    if (it >= a.n_items) break;
-    const BatchItem item = a.items[it];
-    const unsigned model = a.tiles[item.tile].model;
+    if (s_sel_tile >= 0) {   // this block finished the tile's last pass-1 item
+      __threadfence();
+      batch_select(a, (unsigned)s_sel_tile, s_hist, s_tmp);
+      __syncthreads();
+    }
+    const BatchItem item = s_items[cur];
+    if (item.tile == ~0u) break;
     if (item.pass == 2) {
       if (threadIdx.x == 0) {
         BatchTileState* S = a.state + item.tile;
         const int st = wait_ready(&S->ready, &a.run->abort, &a.run->err, a.timeout_ns);
-        if (st == 1) {
-          const double sc[2] = {__ldcg(&S->sel.scale[0]), __ldcg(&S->sel.scale[1])};
-          const float hs = a.models[model].lasso.hscale;
-          for (int i = 0; i < 6; ++i) s_M[i] = recon_coef(a.Wt, sc, hs, i);
-        }
+        if (st == 1)
+          for (int i = 0; i < 6; ++i) s_M[i] = __ldcg(&S->M[i]);
         s_go = st;
       }
       __syncthreads();
       if (s_go < 0) break;     // the run was aborted
-      if (s_go != 1) continue; // tile left to the exact fallback
+      if (s_go != 1) {         // tile left to the exact fallback
+        __syncthreads();
+        continue;
+      }
     }
-    if ((int)model != cur_model) {
-      load_lut(a.models + model, lut);
-      cur_model = (int)model;
+    if ((int)item.model != cur_model) {
+      load_lut(a.models + item.model, lut);
+      cur_model = (int)item.model;
     }
-    if (item.pass == 1)
-      batch_pass1<G>(a, item.tile, item.c0, item.c1, lut, lr, s_queue, s_kb, s_hist, s_tmp,
-                     &s_last);
-    else
+    if (item.pass == 1) {
+      const unsigned tk = batch_pass1<G>(a, item.tile, item.c0, item.c1, lut, lr, s_queue, s_kb,
+                                         s_cnt);
+      if (threadIdx.x == 0) {
+        pend_tile = item.tile;
+        pend_ticket = tk;
+        pend_last = item.n_items1 - 1u;
+      }
+    } else {
       batch_pass2<G>(a, item.tile, item.c0, item.c1, lut, lr, s_M);
+    }
+    __syncthreads();   // the item is done: shared words and the table may be rewritten
   }
   // tiles whose ranks the windows missed: exact radix select over the whole
   // grid, then their pass 2 (tile order; the ready words are final here)
@@ -614,7 +714,7 @@ static int configure_batch_kernel(Context* c, int* grid) {
   SPCN_CUDA_TRY(cudaFuncSetAttribute(k_batch<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)kBatchSmem));
   int occ = 0;
-  SPCN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<G>, kPassThreads,
+  SPCN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<G>, kBatchThreads,
                                                               kBatchSmem));
   if (occ < 1) return SPCN_ERR_CUDA;
   *grid = c->num_sms * occ;
@@ -645,12 +745,23 @@ static void build_items(const Batch* b, const spcn_batch_config& cfg, std::vecto
   });
   auto emit = [&](int t, unsigned pass) {
     const u64 nch = b->tiles[t].g.nchunks;
-    for (u64 c0 = 0; c0 < nch; c0 += S) out->push_back({(unsigned)t, pass, c0, std::min(nch, c0 + S)});
-    if (pass == 1) (*n_items1)[t] = (unsigned)((nch + S - 1) / S);
+    const unsigned n1 = (unsigned)((nch + S - 1) / S);
+    for (u64 c0 = 0; c0 < nch; c0 += S)
+      out->push_back({(unsigned)t, pass, b->tiles[t].model, n1, c0, std::min(nch, c0 + S)});
+    if (pass == 1) (*n_items1)[t] = n1;
   };
   if (cfg.schedule == SPCN_SCHED_PHASED) {
+    // pass 2 needs no particular order: tiles sharing a table go together
+    // (fewer table reloads), largest first within a table
+    std::vector<int> rank(b->n_models, -1), order2 = order;
+    int r = 0;
+    for (int t : order)
+      if (rank[b->tiles[t].model] < 0) rank[b->tiles[t].model] = r++;
+    std::stable_sort(order2.begin(), order2.end(), [&](int x, int y) {
+      return rank[b->tiles[x].model] < rank[b->tiles[y].model];
+    });
     for (int t : order) emit(t, 1);
-    for (int t : order) emit(t, 2);
+    for (int t : order2) emit(t, 2);
     return;
   }
   // groups of consecutive tiles (in size order) holding about group_px pixels
@@ -714,7 +825,7 @@ static int batch_launch(Batch* b, cudaStream_t st) {
   SPCN_CUDA_TRY(cudaStreamIsCapturing(st, &cap));
   cudaLaunchConfig_t lc = {};
   lc.gridDim = dim3((unsigned)b->grid);
-  lc.blockDim = dim3(kPassThreads);
+  lc.blockDim = dim3(kBatchThreads);
   lc.dynamicSmemBytes = kBatchSmem;
   lc.stream = st;
   cudaLaunchAttribute attr[1];
@@ -825,7 +936,7 @@ static int batch_create(Context* c, int n, const spcn_image* tiles, const spcn_s
   for (int i = 0; i < 3; ++i) a.l2i0[i] = (float)log2((double)tgt->i0[i]);
   a.timeout_ns = c->timeout_ns;
   spcn_batch_config cfg{};
-  cfg.item_chunks = 4 * kPassThreads;
+  cfg.item_chunks = 16 * kPassThreads;
   cfg.schedule = SPCN_SCHED_PHASED;
   cfg.group_px = 0;
   rc = apply_config(b, cfg);
@@ -928,19 +1039,21 @@ int spcn_batch_tune(void* batch, int32_t reps, spcn_batch_config* trials, int32_
   DeviceGuard guard(b->c->device);
   if (!guard.ok) return SPCN_ERR_CUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  // candidates: item sizes x (phased, interleaved groups of 4, 8, 16 Mpx)
+  // candidates: item sizes (2K-64K chunks) x (phased, interleaved groups of
+  // 16 Mpx); sizes above the largest tile's chunk count are skipped
+  u64 max_chunks = 0;
+  for (const BatchTile& T : b->tiles) max_chunks = std::max(max_chunks, (u64)T.g.nchunks);
   std::vector<spcn_batch_config> cand;
-  for (int k : {1, 2, 4, 8, 16}) {
+  for (int k : {2, 4, 8, 16, 32, 64}) {
+    if (k > 2 && (u64)k * kPassThreads > 2 * max_chunks) break;
     spcn_batch_config c0{};
     c0.item_chunks = k * kPassThreads;
     c0.schedule = SPCN_SCHED_PHASED;
     cand.push_back(c0);
-    for (int64_t g : {4ll << 20, 8ll << 20, 16ll << 20}) {
-      spcn_batch_config c1 = c0;
-      c1.schedule = SPCN_SCHED_INTERLEAVED;
-      c1.group_px = g;
-      cand.push_back(c1);
-    }
+    spcn_batch_config c1 = c0;
+    c1.schedule = SPCN_SCHED_INTERLEAVED;
+    c1.group_px = 16ll << 20;
+    cand.push_back(c1);
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   SPCN_CUDA_TRY(cudaEventCreate(&e0));
