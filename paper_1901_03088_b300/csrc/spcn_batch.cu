@@ -76,7 +76,6 @@ struct BatchTile {
 struct BatchTileState {
   SelectState sel;         // counts, ranks, keys, percentiles, scale; fallback barrier
   u64 list_n[2];           // keys appended (may exceed list_cap: overflow)
-  unsigned kmax[2];        // largest key appended
   unsigned done1;          // finished pass-1 items
   int ready;               // 0: pass 1 running, 1: scale known, 2: exact fallback needed
   int status;              // SPCN_OK or SPCN_ERR_NO_TISSUE
@@ -106,6 +105,7 @@ struct BatchArgs {
   BatchTileState* state;
   const BatchItem* items;
   const Model* models;
+  unsigned* hist1;         // per tile and stain: first-digit histogram of listed keys
   u64* rhist;
   BatchRunState* run;
   unsigned n_items, n_tiles;
@@ -159,23 +159,26 @@ __device__ int wait_ready(const int* ready, int* abort, int* err, long long time
 }
 
 // Append a warp's buffered keys to a tile's list: one atomic reservation,
-// then coalesced stores; keys past the capacity are counted but dropped.  The
-// largest key is kept for the select's digit count.  kc is warp-uniform.
+// then coalesced stores; keys past the capacity are counted but dropped.
+// Every key also counts in the tile's first-digit histogram of d = key - lo
+// (bin min(d >> 12, 4095), fire-and-forget reductions spread over all
+// blocks), so the select needs only one pass over the list.  kc is
+// warp-uniform.
+__device__ __forceinline__ void red_add_u32(unsigned* p, unsigned v) {
+  asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
 __device__ __forceinline__ void flush_keys(const unsigned* kb, int kc, unsigned* list, u64 cap,
-                                           u64* list_n, unsigned* kmax) {
+                                           u64* list_n, unsigned* hist1, unsigned lo) {
   if (kc == 0) return;
   const unsigned lane = threadIdx.x & 31u;
   u64 base = 0;
   if (lane == 0) base = atomicAdd(list_n, (u64)kc);
   base = __shfl_sync(0xFFFFFFFFu, base, 0);
-  unsigned m = 0u;
   for (int i = (int)lane; i < kc; i += 32) {
     const unsigned k = kb[i];
-    m = max(m, k);
     if (base + (u64)i < cap) list[base + i] = k;
+    red_add_u32(hist1 + min((k - lo) >> kSelBits, (unsigned)(kSelBins - 1)), 1u);
   }
-  m = __reduce_max_sync(0xFFFFFFFFu, m);
-  if (lane == 0) atomicMax(kmax, m);
 }
 
 // Keys of the queued chunks' flagged pixels (same arithmetic as pass 1, so
@@ -189,7 +192,7 @@ template <class G>
 __device__ __noinline__ void batch_drain(const uint2* queue, int count, u64 c0, const G& g,
                                          const char* lut, unsigned lr, const Lasso& L,
                                          unsigned* kb0, unsigned* kb1, int& kc0, int& kc1,
-                                         const BatchTile* T, BatchTileState* S) {
+                                         const BatchTile* T, BatchTileState* S, unsigned* h1) {
   const u64 cap = T->list_cap;
   unsigned* list0 = T->keys;
   unsigned* list1 = list0 + cap;
@@ -249,8 +252,8 @@ __device__ __noinline__ void batch_drain(const uint2* queue, int count, u64 c0, 
       kc1 += __popc(b1);
       if (kc0 > kKeyBuf - 32 || kc1 > kKeyBuf - 32) {
         __syncwarp();
-        flush_keys(kb0, kc0, list0, cap, S->list_n, S->kmax);
-        flush_keys(kb1, kc1, list1, cap, S->list_n + 1, S->kmax + 1);
+        flush_keys(kb0, kc0, list0, cap, S->list_n, h1, lo0);
+        flush_keys(kb1, kc1, list1, cap, S->list_n + 1, h1 + kSelBins, lo1);
         __syncwarp();
         kc0 = 0;
         kc1 = 0;
@@ -285,17 +288,18 @@ __device__ __forceinline__ void smem_find_rank(const unsigned* hist, int n, u64 
 
 // Percentile of one tile from its key lists, by the block that finished the
 // tile's pass 1.  Rank r of the non-white densities is rank r - below among
-// the listed keys when below <= r < below + count and the list is complete;
-// it is found by a radix select over d = key - lo, most significant 12-bit
-// digit first, as many digits as the largest listed d needs.  Ranks outside
-// leave the tile to the exact fallback.
+// the listed keys when below <= r < below + count and the list is complete.
+// Its first 12-bit digit of d = key - lo comes from the histogram built
+// during pass 1, its last 12 bits from one pass over the list.  Ranks
+// outside, or in the histogram's top (overflow) bin, leave the tile to the
+// exact fallback.
 __device__ void batch_select(const BatchArgs& a, unsigned tile, unsigned* s_hist, u64* s_tmp) {
   const BatchTile* T = a.tiles + tile;
   BatchTileState* S = a.state + tile;
   SelectState* s = &S->sel;
   __shared__ int s_idx;
   __shared__ u64 s_before;
-  __shared__ unsigned s_pre[2];
+  __shared__ int s_bin[2];
   __shared__ u64 s_rr[2];
   __shared__ int s_res[kTracks];
   const u64 n = __ldcg(&s->n_nw);
@@ -332,70 +336,63 @@ __device__ void batch_select(const BatchArgs& a, unsigned tile, unsigned* s_hist
       in[u] = T->win[j] && cnt <= cap && r >= below && r - below < cnt;
     }
     if (!in[0] && !in[1]) continue;   // uniform across the block
-    if (threadIdx.x == 0) {
-      for (int u = 0; u < 2; ++u) { s_pre[u] = 0u; s_rr[u] = s->rank[2 * j + u] - below; }
-    }
-    const unsigned range = __ldcg(&S->kmax[j]) - lo;   // every listed d is <= range
-    const int nbits = range ? 32 - __clz(range) : 1;
-    const int levels = (nbits + kSelBits - 1) / kSelBits;
-    bool ok[2] = {in[0], in[1]};
-    for (int lev = levels - 1; lev >= 0; --lev) {
-      const int shift = lev * kSelBits;
-      __syncthreads();
-      const unsigned pre0 = s_pre[0], pre1 = s_pre[1];
-      const bool share = !ok[0] || !ok[1] || pre0 == pre1;   // one histogram serves both
-      for (int i = threadIdx.x; i < 2 * kSelBins; i += blockDim.x) s_hist[i] = 0u;
-      __syncthreads();
-      const int hi = shift + kSelBits;
-      const u64 t0 = (u64)pre0 >> hi, t1 = (u64)pre1 >> hi;
-      // histogram 0 takes track 0's keys (or track 1's when track 0 is done);
-      // histogram 1 takes track 1's keys when the prefixes differ
-      const bool use0 = ok[0], use1 = ok[1];
-      auto count = [&](unsigned key) {
-        const unsigned d = key - lo;
-        const unsigned bin = (d >> shift) & (kSelBins - 1);
-        const u64 top = (u64)d >> hi;
-        if (use0 && top == t0) atomicAdd(s_hist + bin, 1u);
-        else if (use1 && top == t1) atomicAdd(s_hist + (share ? 0 : kSelBins) + bin, 1u);
-      };
-      // 16-byte loads, eight keys per thread and step (the lists start on
-      // 16-byte boundaries; the last partial vector is read key by key)
-      const uint4* v = reinterpret_cast<const uint4*>(list);
-      const u64 nv = cnt / 4;
-      for (u64 i = threadIdx.x; i < nv; i += 2 * blockDim.x) {
-        const uint4 x = __ldcg(v + i);
-        const bool two = i + blockDim.x < nv;
-        uint4 y = make_uint4(0u, 0u, 0u, 0u);
-        if (two) y = __ldcg(v + i + blockDim.x);
-        count(x.x); count(x.y); count(x.z); count(x.w);
-        if (two) { count(y.x); count(y.y); count(y.z); count(y.w); }
-      }
-      for (u64 i = nv * 4 + threadIdx.x; i < cnt; i += blockDim.x) count(__ldcg(list + i));
-      __syncthreads();
-      for (int u = 0; u < 2; ++u) {
-        if (!ok[u]) continue;
-        const unsigned* h = s_hist + ((share || u == 0) ? 0 : kSelBins);
-        smem_find_rank(h, kSelBins, s_rr[u], &s_idx, &s_before, s_tmp);
-        if (threadIdx.x == 0) {
-          if (s_idx < 0) {
-            ok[u] = false;   // cannot happen: the level's count covers the rank
-          } else {
-            s_pre[u] |= (unsigned)s_idx << shift;
-            s_rr[u] -= s_before;
-          }
-        }
-        __syncthreads();
-        ok[u] = ok[u] && s_idx >= 0;
-      }
-    }
-    if (threadIdx.x == 0) {
-      for (int u = 0; u < 2; ++u)
-        if (ok[u]) {
-          s->key[2 * j + u] = lo + s_pre[u];
-          s_res[2 * j + u] = 1;
-        }
-    }
+    // first digit: the pass-1 histogram
+    const unsigned* h1 = a.hist1 + ((size_t)tile * 2 + j) * kSelBins;
+    for (int i = threadIdx.x; i < kSelBins; i += blockDim.x) s_hist[i] = __ldcg(h1 + i);
+    if (threadIdx.x == 0)
+      for (int u = 0; u < 2; ++u) s_rr[u] = s->rank[2 * j + u] - below;
     __syncthreads();
+    for (int u = 0; u < 2; ++u) {
+      if (!in[u]) continue;
+      smem_find_rank(s_hist, kSelBins, s_rr[u], &s_idx, &s_before, s_tmp);
+      if (threadIdx.x == 0) {
+        s_bin[u] = s_idx;
+        if (s_idx >= 0) s_rr[u] -= s_before;
+      }
+      __syncthreads();
+    }
+    bool ok[2];
+    for (int u = 0; u < 2; ++u) ok[u] = in[u] && s_bin[u] >= 0 && s_bin[u] < kSelBins - 1;
+    if (!ok[0] && !ok[1]) { __syncthreads(); continue; }
+    // second digit: one pass over the list, counting the keys of each
+    // track's first-digit bin (one histogram when both bins agree)
+    const int b0 = ok[0] ? s_bin[0] : -1, b1 = ok[1] ? s_bin[1] : -1;
+    const bool share = b0 == b1 || b0 < 0 || b1 < 0;
+    const int bb = b0 >= 0 ? b0 : b1;
+    __syncthreads();
+    for (int i = threadIdx.x; i < 2 * kSelBins; i += blockDim.x) s_hist[i] = 0u;
+    __syncthreads();
+    auto count = [&](unsigned key) {
+      const unsigned d = key - lo;
+      const int hb = (int)min(d >> kSelBits, (unsigned)(kSelBins - 1));
+      const unsigned low = d & (kSelBins - 1);
+      if (hb == bb) atomicAdd(s_hist + low, 1u);
+      else if (!share && hb == b1) atomicAdd(s_hist + kSelBins + low, 1u);
+    };
+    // 16-byte loads, eight keys per thread and step (the lists start on
+    // 16-byte boundaries; the last partial vector is read key by key)
+    const uint4* v = reinterpret_cast<const uint4*>(list);
+    const u64 nv = cnt / 4;
+    for (u64 i = threadIdx.x; i < nv; i += 2 * blockDim.x) {
+      const uint4 x = __ldcg(v + i);
+      const bool two = i + blockDim.x < nv;
+      uint4 y = make_uint4(0u, 0u, 0u, 0u);
+      if (two) y = __ldcg(v + i + blockDim.x);
+      count(x.x); count(x.y); count(x.z); count(x.w);
+      if (two) { count(y.x); count(y.y); count(y.z); count(y.w); }
+    }
+    for (u64 i = nv * 4 + threadIdx.x; i < cnt; i += blockDim.x) count(__ldcg(list + i));
+    __syncthreads();
+    for (int u = 0; u < 2; ++u) {
+      if (!ok[u]) continue;
+      const unsigned* h = s_hist + ((share || u == 0) ? 0 : kSelBins);
+      smem_find_rank(h, kSelBins, s_rr[u], &s_idx, &s_before, s_tmp);
+      if (threadIdx.x == 0 && s_idx >= 0) {
+        s->key[2 * j + u] = lo + ((unsigned)s_bin[u] << kSelBits) + (unsigned)s_idx;
+        s_res[2 * j + u] = 1;
+      }
+      __syncthreads();
+    }
   }
   if (threadIdx.x == 0) {
     int all = 1;
@@ -469,19 +466,28 @@ __device__ __forceinline__ FlatGeometry geometry_as<FlatGeometry>(const Geometry
 template <class G>
 __device__ __forceinline__ unsigned batch_pass1(const BatchArgs& a, unsigned tile, u64 c0,
                                                 u64 c1, const char* lut, unsigned lr,
-                                                uint2* s_queue, unsigned* s_kb, unsigned* s_cnt) {
+                                                uint2* s_queue, unsigned* s_kb, unsigned* s_cnt,
+                                                unsigned* s_piece) {
   const BatchTile* T = a.tiles + tile;
   BatchTileState* S = a.state + tile;
   const G g = geometry_as<G>(T->g);
   const Lasso L = a.models[T->model].lasso;
   const float nk0 = T->nk[0], lk0 = T->lk[0], nk1 = T->nk[1], lk1 = T->lk[1];
+  unsigned* h1 = a.hist1 + (size_t)tile * 2 * kSelBins;
   const f2 NR1 = pk(L.nrho1, L.nrho1), NR2 = pk(L.nrho2, L.nrho2);
   f2 c_nw = pk(0.f, 0.f), c_b0 = pk(0.f, 0.f), c_b1 = pk(0.f, 0.f);
   unsigned* kb0 = s_kb;
   unsigned* kb1 = s_kb + kKeyBuf;
   const unsigned lane = threadIdx.x & 31u;
   int qn = 0, kc0 = 0, kc1 = 0;   // warp-uniform
-  for (u64 base = c0 + (threadIdx.x & ~31u); base < c1; base += blockDim.x) {
+  // warps claim 32-chunk pieces of the item from a shared counter, so a warp
+  // that spends time draining its queue takes fewer pieces and all warps
+  // reach the end of the item together
+  for (;;) {
+    unsigned piece = 0u;
+    if (lane == 0) piece = atomicAdd(s_piece, 1u);
+    const u64 base = c0 + 32ull * __shfl_sync(0xFFFFFFFFu, piece, 0);
+    if (base >= c1) break;
     const u64 q = base + lane;
     bool hit = false;
     unsigned packed = 0u;
@@ -498,16 +504,22 @@ __device__ __forceinline__ unsigned batch_pass1(const BatchArgs& a, unsigned til
     const unsigned ball = __ballot_sync(0xFFFFFFFFu, hit);
     if (hit) s_queue[qn + __popc(ball & ((1u << lane) - 1u))] = make_uint2((unsigned)(q - c0), packed);
     qn += __popc(ball);
-    if (qn >= 32 || base + blockDim.x >= c1) {
+    if (qn >= 32) {
       __syncwarp();
-      batch_drain(s_queue, qn, c0, g, lut, lr, L, kb0, kb1, kc0, kc1, T, S);
+      batch_drain(s_queue, qn, c0, g, lut, lr, L, kb0, kb1, kc0, kc1, T, S, h1);
       __syncwarp();
       qn = 0;
     }
   }
   __syncwarp();
-  flush_keys(kb0, kc0, T->keys, T->list_cap, S->list_n, S->kmax);
-  flush_keys(kb1, kc1, T->keys + T->list_cap, T->list_cap, S->list_n + 1, S->kmax + 1);
+  if (qn > 0) batch_drain(s_queue, qn, c0, g, lut, lr, L, kb0, kb1, kc0, kc1, T, S, h1);
+  __syncwarp();
+  {
+    unsigned* h1 = a.hist1 + (size_t)tile * 2 * kSelBins;
+    flush_keys(kb0, kc0, T->keys, T->list_cap, S->list_n, h1, T->lo[0]);
+    flush_keys(kb1, kc1, T->keys + T->list_cap, T->list_cap, S->list_n + 1, h1 + kSelBins,
+               T->lo[1]);
+  }
   // per-thread counts are exact in FP32 (fewer than 2^24 pixels per thread),
   // per-warp sums fit 32 bits; one shared-memory round gives thread 0 the
   // block's counts
@@ -572,6 +584,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch(BatchArgs a) {
   __shared__ unsigned s_cnt[3 * 32];
   __shared__ __align__(16) BatchItem s_items[2];   // current item and the prefetched next one
   __shared__ int s_go, s_sel_tile;
+  __shared__ unsigned s_piece;
   __shared__ float s_M[6];
   const unsigned lr = lane_reg();
   int cur_model = -1;
@@ -592,6 +605,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch(BatchArgs a) {
     if (threadIdx.x == 0) {
       s_sel_tile = (pend_tile != ~0u && pend_ticket == pend_last) ? (int)pend_tile : -1;
       pend_tile = ~0u;
+      s_piece = 0u;
       cp_async_wait_all();
       BatchItem* nx = &s_items[cur ^ 1];   // read by nobody until the next loop top
       if (s_items[cur].tile != ~0u && t_next < a.n_items) {
@@ -630,7 +644,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch(BatchArgs a) {
     }
     if (item.pass == 1) {
       const unsigned tk = batch_pass1<G>(a, item.tile, item.c0, item.c1, lut, lr, s_queue, s_kb,
-                                         s_cnt);
+                                         s_cnt, &s_piece);
       if (threadIdx.x == 0) {
         pend_tile = item.tile;
         pend_ticket = tk;
@@ -904,7 +918,8 @@ static int batch_create(Context* c, int n, const spcn_image* tiles, const spcn_s
   auto fail = [&](int code) { batch_free(b); return code; };
   if (cudaMalloc(&b->models, sizeof(Model) * rep.size()) != cudaSuccess) return fail(SPCN_ERR_OOM);
   if (cudaMalloc(&b->d_tiles, sizeof(BatchTile) * n) != cudaSuccess) return fail(SPCN_ERR_OOM);
-  b->state_bytes = kRunStateBytes + sizeof(BatchTileState) * (size_t)n;
+  b->state_bytes = kRunStateBytes + sizeof(BatchTileState) * (size_t)n +
+                   sizeof(unsigned) * 2 * kSelBins * (size_t)n;
   if (cudaMalloc(&b->d_state, b->state_bytes) != cudaSuccess) return fail(SPCN_ERR_OOM);
   if (cudaMalloc(&b->keys, sizeof(unsigned) * keys_total) != cudaSuccess) return fail(SPCN_ERR_OOM);
   for (BatchTile& T : b->tiles) T.keys = b->keys + reinterpret_cast<uintptr_t>(T.keys);
@@ -923,6 +938,8 @@ static int batch_create(Context* c, int n, const spcn_image* tiles, const spcn_s
   BatchArgs& a = b->args;
   a.tiles = b->d_tiles;
   a.state = reinterpret_cast<BatchTileState*>(b->d_state + kRunStateBytes);
+  a.hist1 = reinterpret_cast<unsigned*>(b->d_state + kRunStateBytes +
+                                        sizeof(BatchTileState) * (size_t)n);
   a.run = reinterpret_cast<BatchRunState*>(b->d_state);
   a.models = b->models;
   a.rhist = b->rhist;
@@ -948,8 +965,9 @@ static int batch_create(Context* c, int n, const spcn_image* tiles, const spcn_s
 
 static int batch_results(Batch* b, double* p99_out, int32_t* status_out, int32_t* fallback_out,
                          cudaStream_t st) {
-  std::vector<char> h(b->state_bytes);
-  SPCN_CUDA_TRY(cudaMemcpyAsync(h.data(), b->d_state, b->state_bytes, cudaMemcpyDeviceToHost, st));
+  const size_t bytes = kRunStateBytes + sizeof(BatchTileState) * (size_t)b->n;
+  std::vector<char> h(bytes);
+  SPCN_CUDA_TRY(cudaMemcpyAsync(h.data(), b->d_state, bytes, cudaMemcpyDeviceToHost, st));
   SPCN_CUDA_TRY(cudaStreamSynchronize(st));
   const BatchRunState* run = reinterpret_cast<const BatchRunState*>(h.data());
   const BatchTileState* ts = reinterpret_cast<const BatchTileState*>(h.data() + kRunStateBytes);
