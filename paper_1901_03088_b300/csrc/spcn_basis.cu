@@ -351,28 +351,31 @@ __global__ void __launch_bounds__(kSnmfThreads) k_snmf(SnmfArgs a) {
   const u64 gstride = (u64)gridDim.x * blockDim.x;
   unsigned target = 0;
   int it;
-  for (it = 1; it <= a.max_iter; ++it) {
-    if (threadIdx.x == 0) {
-      double g11 = 0, g22 = 0, g12 = 0;
-      for (int c = 0; c < 3; ++c) {
-        g11 += s_W[c] * s_W[c];
-        g22 += s_W[3 + c] * s_W[3 + c];
-        g12 += s_W[c] * s_W[3 + c];
-      }
-      const double det = g11 * g22 - g12 * g12;
-      if (!(det > 1e-12)) {
-        s_flag = -1;
-      } else {
-        for (int i = 0; i < 6; ++i) s_coef[i] = (float)s_W[i];
-        s_coef[6] = (float)(g22 / det);
-        s_coef[7] = (float)(-g12 / det);
-        s_coef[8] = (float)(-g12 / det);
-        s_coef[9] = (float)(g11 / det);
-        s_coef[10] = (float)(1.0 / g11);
-        s_coef[11] = (float)(1.0 / g22);
-      }
+  // closed-form H-step coefficients of the current basis (thread 0); -1 in
+  // s_flag when the basis is degenerate
+  auto set_coef = [&]() {
+    double g11 = 0, g22 = 0, g12 = 0;
+    for (int c = 0; c < 3; ++c) {
+      g11 += s_W[c] * s_W[c];
+      g22 += s_W[3 + c] * s_W[3 + c];
+      g12 += s_W[c] * s_W[3 + c];
     }
-    __syncthreads();
+    const double det = g11 * g22 - g12 * g12;
+    if (!(det > 1e-12)) {
+      s_flag = -1;
+    } else {
+      for (int i = 0; i < 6; ++i) s_coef[i] = (float)s_W[i];
+      s_coef[6] = (float)(g22 / det);
+      s_coef[7] = (float)(-g12 / det);
+      s_coef[8] = (float)(-g12 / det);
+      s_coef[9] = (float)(g11 / det);
+      s_coef[10] = (float)(1.0 / g11);
+      s_coef[11] = (float)(1.0 / g22);
+    }
+  };
+  if (threadIdx.x == 0) set_coef();
+  __syncthreads();
+  for (it = 1; it <= a.max_iter; ++it) {
     if (s_flag < 0) break;
     const float w00 = s_coef[0], w10 = s_coef[1], w20 = s_coef[2];
     const float w01 = s_coef[3], w11 = s_coef[4], w21 = s_coef[5];
@@ -427,12 +430,15 @@ __global__ void __launch_bounds__(kSnmfThreads) k_snmf(SnmfArgs a) {
     }
     for (u64 i = (n4 << 2) + (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gstride)
       step(__ldg(a.nw + i));
+    // warp sums in FP32 (a fixed shuffle tree: deterministic), FP64 from the
+    // warp totals on; FP64 arithmetic is a small fraction of FP32 throughput
+    // on this GPU, so the per-thread work stays in FP32
 #pragma unroll
     for (int i = 0; i < kAcc; ++i) {
-      double x = (double)acc[i];
+      float x = acc[i];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-      if (lane == 0) s_red[warp][i] = x;
+      if (lane == 0) s_red[warp][i] = (double)x;
     }
     __syncthreads();
     double* part = a.partials + (size_t)(it & 1) * gridDim.x * kAcc;
@@ -489,6 +495,7 @@ __global__ void __launch_bounds__(kSnmfThreads) k_snmf(SnmfArgs a) {
       for (int c = 0; c < 3; ++c) { s_W[c] = W[c][0]; s_W[3 + c] = W[c][1]; }
       if (flag == 0 && dmax < a.tol) flag = 1;
       s_flag = flag;
+      if (flag == 0) set_coef();   // the next iteration's coefficients
     }
     __syncthreads();
     if (s_flag != 0) break;

@@ -207,8 +207,8 @@ __device__ __forceinline__ void window_chunk(const unsigned (&w)[12], const char
     pixel_addr(w, kB, lr, aRB, aGB, aBB);
     f2 H1, H2;
     solve_pair(lut, aRA, aGA, aBA, aRB, aGB, aBB, NR1, NR2, kappa, H1, H2);
-    const bool nwA = aRA < a.wthr || aGA < a.wthr || aBA < a.wthr;
-    const bool nwB = aRB < a.wthr || aGB < a.wthr || aBB < a.wthr;
+    const bool nwA = min(min(aRA, aGA), aBA) < a.wthr;
+    const bool nwB = min(min(aRB, aGB), aBB) < a.wthr;
     const f2 NW = pk(nwA ? 1.f : 0.f, nwB ? 1.f : 0.f);
     c_nw = add2(c_nw, NW);
     const float h1A = lo_of(H1), h1B = hi_of(H1), h2A = lo_of(H2), h2B = hi_of(H2);
