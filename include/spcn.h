@@ -156,6 +156,21 @@ int spcn_normalize(void* ctx, const spcn_image* src, const spcn_stats* src_st,
                    const spcn_stats* tgt_st, const spcn_params* params,
                    uint8_t* out, int64_t out_pitch, double* src_p99_out, void* stream);
 
+/* Basis estimation and normalisation of `src` in one stream-ordered call:
+ * the work of spcn_estimate_basis followed by spcn_normalize with the
+ * estimated statistics, except that the statistics stay on the device (the
+ * source table is built from the estimated basis and i0, and the P99 search
+ * window from the sample percentile) so there is no host round trip between
+ * the two.  The output bytes are those of the two calls in sequence.
+ * If src_st_out (host) is non-NULL the call blocks and returns the estimated
+ * source statistics there, with p99 = the exact percentile of the whole
+ * source; otherwise it is asynchronous and errors of the estimation (no
+ * tissue, degenerate basis) are returned by the next synchronising call.
+ * Errors: as spcn_estimate_basis and spcn_normalize. */
+int spcn_normalize_estimated(void* ctx, const spcn_image* src, const spcn_stats* tgt_st,
+                             const spcn_params* params, uint8_t* out, int64_t out_pitch,
+                             spcn_stats* src_st_out, void* stream);
+
 /* Wait for the context's work on `stream` and return the first error any
  * asynchronous call recorded on the device since the last synchronising
  * call (the record is then cleared). */

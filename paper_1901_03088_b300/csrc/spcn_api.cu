@@ -9,6 +9,7 @@
 
 #include "spcn_context.h"
 #include "spcn_internal.cuh"
+#include "spcn_pixel.cuh"
 
 namespace spcn {
 
@@ -92,7 +93,7 @@ static void free_all(Context* c) {
   for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
   c->pool.clear();
   void* ptrs[] = {c->err, c->model, c->model_b, c->sel, c->coarse, c->fine, c->rhist,
-                  c->rhist_b, c->partials, c->bs, c->sample, c->nw, c->br, c->blk,
+                  c->rhist_b, c->partials, c->bs, c->wdev, c->sample, c->nw, c->br, c->blk,
                   c->blk_off, c->cand};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -252,6 +253,7 @@ int spcn_context_create(void** out, int device) {
     ALLOC(c->rhist_b, sizeof(u64) * 3 * kTracks * kRadixBins);
     ALLOC(c->partials, sizeof(double) * 2 * 4096 * kAcc);
     ALLOC(c->bs, sizeof(BasisState));
+    ALLOC(c->wdev, sizeof(Window));
 #undef ALLOC
     if (cudaMemset(c->err, 0, sizeof(int)) != cudaSuccess) { rc = SPCN_ERR_CUDA; break; }
     rc = configure_pixel_kernels(c);
@@ -438,6 +440,55 @@ int spcn_normalize_f32_backward(void* ctx, const float* x, const float* gy, int3
   if (!guard.ok) return SPCN_ERR_CUDA;
   return launch_f32(c, true, x, gy, batch, (int64_t)height * width, src_stats, tgt_stats, wt,
                     params->lambda, nullptr, gx, gwt, static_cast<cudaStream_t>(stream));
+}
+
+int spcn_normalize_estimated(void* ctx, const spcn_image* src, const spcn_stats* tgt_st,
+                             const spcn_params* params, uint8_t* out, int64_t out_pitch,
+                             spcn_stats* src_st_out, void* stream) {
+  if (!ctx || !image_ok(src) || !params_ok(params) || !out) return SPCN_ERR_INVALID_ARG;
+  if (out_pitch < 3ll * src->width) return SPCN_ERR_INVALID_ARG;
+  int rc = stats_ok(tgt_st);
+  if (rc) return rc;
+  {
+    const uintptr_t s0 = reinterpret_cast<uintptr_t>(src->data);
+    const uintptr_t s1 = s0 + (uintptr_t)((src->height - 1) * src->pitch_bytes + 3ll * src->width);
+    const uintptr_t d0 = reinterpret_cast<uintptr_t>(out);
+    const uintptr_t d1 = d0 + (uintptr_t)((src->height - 1) * out_pitch + 3ll * src->width);
+    if (d0 < s1 && s0 < d1) return SPCN_ERR_INVALID_ARG;
+  }
+  Context* c = static_cast<Context*>(ctx);
+  DeviceGuard guard(c->device);
+  if (!guard.ok) return SPCN_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // basis estimation, left on the device
+  rc = launch_estimate_basis(c, src, params, s);
+  if (rc) return rc;
+  // source table from the estimated basis and i0, window from the sample P99
+  rc = launch_build_model(c, c->model, nullptr, nullptr, params->lambda, c->model_b, s);
+  if (rc) return rc;
+  Window* wdev = static_cast<Window*>(c->wdev);
+  rc = launch_window_from_basis(c, c->model, &c->bs->sel, &c->bs->status, wdev, s);
+  if (rc) return rc;
+  const Geometry g = make_geometry(src, out, out_pitch);
+  rc = launch_percentile_passes_dev(c, g, c->model, params->white_thresh,
+                                    (double)params->stain_pct, wdev, tgt_st->p99, s);
+  if (rc) return rc;
+  rc = launch_recon(c, g, c->model, tgt_st->W, tgt_st->i0, s);
+  if (rc) return rc;
+  if (src_st_out) {
+    memset(src_st_out, 0, sizeof(*src_st_out));
+    rc = finish_estimate_basis(c, src_st_out, s);   // waits; basis status
+    double p[2];
+    SPCN_CUDA_TRY(cudaMemcpyAsync(p, c->sel->p99, sizeof(p), cudaMemcpyDeviceToHost, s));
+    int err = 0;
+    const int rc2 = read_error(c, s, &err);
+    if (rc2) return rc2;
+    src_st_out->p99[0] = p[0];   // the exact percentile of the whole source
+    src_st_out->p99[1] = p[1];
+    src_st_out->status = rc ? rc : err;
+    return rc ? rc : err;
+  }
+  return SPCN_OK;
 }
 
 int spcn_synchronize(void* ctx, void* stream) {

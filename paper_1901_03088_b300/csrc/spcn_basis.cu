@@ -534,8 +534,11 @@ int configure_basis_kernels(Context* c) {
   return SPCN_OK;
 }
 
-int run_estimate_basis(Context* c, const spcn_image* img, const spcn_params* p, spcn_stats* out,
-                       cudaStream_t st) {
+// Every launch of a basis estimation (sampling, i0, sparse NMF, stain order,
+// sample percentile) on `st`, without waiting: the results stay on the
+// device (c->bs, c->model_b) until finish_estimate_basis reads them.
+int launch_estimate_basis(Context* c, const spcn_image* img, const spcn_params* p,
+                          cudaStream_t st) {
   const int64_t W = img->width, H = img->height;
   const u64 N = (u64)W * (u64)H;
   u64 cap = 0, m = 0;
@@ -610,10 +613,13 @@ int run_estimate_basis(Context* c, const spcn_image* img, const spcn_params* p, 
   c->launches++;
   rc = launch_build_model(c, c->model_b, nullptr, nullptr, p->lambda, c->model_b, st);
   if (rc) return rc;
-  rc = launch_select_list(c, c->nw, &bs->n_nw, c->model_b, &bs->sel, c->rhist_b,
-                          (double)p->stain_pct, st);
-  if (rc) return rc;
+  return launch_select_list(c, c->nw, &bs->n_nw, c->model_b, &bs->sel, c->rhist_b,
+                            (double)p->stain_pct, st);
+}
 
+// Wait for the estimation launched on `st` and fill the host record.
+int finish_estimate_basis(Context* c, spcn_stats* out, cudaStream_t st) {
+  BasisState* bs = c->bs;
   BasisState h;
   Model hm;
   int herr = 0;
@@ -637,6 +643,13 @@ int run_estimate_basis(Context* c, const spcn_image* img, const spcn_params* p, 
   out->status = status;
   if (herr != 0) SPCN_CUDA_TRY(cudaMemsetAsync(c->err, 0, sizeof(int), st));
   return status;
+}
+
+int run_estimate_basis(Context* c, const spcn_image* img, const spcn_params* p, spcn_stats* out,
+                       cudaStream_t st) {
+  const int rc = launch_estimate_basis(c, img, p, st);
+  if (rc) return rc;
+  return finish_estimate_basis(c, out, st);
 }
 
 }  // namespace spcn

@@ -39,6 +39,7 @@ struct Context {
   u64* rhist_b = nullptr;          // same, for the sample percentile
   double* partials = nullptr;      // [2][max grid][kAcc]
   BasisState* bs = nullptr;
+  void* wdev = nullptr;            // P99 window computed on the device (struct Window)
   // grown on demand
   uint32_t* sample = nullptr;      // packed RGB of the sample
   uint32_t* nw = nullptr;          // non-white sample pixels (stable order)

@@ -400,6 +400,9 @@ int launch_recon(Context* c, const Geometry& g, const Model* m, const float* Wt,
                  const float* i0t, cudaStream_t st);
 int launch_density(Context* c, const Geometry& g, const Model* m, float* H, int64_t stride,
                    cudaStream_t st);
+int launch_estimate_basis(Context* c, const spcn_image* img, const spcn_params* p,
+                          cudaStream_t st);
+int finish_estimate_basis(Context* c, spcn_stats* out, cudaStream_t st);
 int run_estimate_basis(Context* c, const spcn_image* img, const spcn_params* p, spcn_stats* out,
                        cudaStream_t st);
 int launch_debug_barrier(Context* c, int extra, long long timeout_ns, cudaStream_t st);

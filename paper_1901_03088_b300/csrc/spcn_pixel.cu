@@ -131,19 +131,15 @@ struct WindowArgs {
   u64* coarse;
   int* err;
   unsigned wthr;       // (white threshold + 1) << 8, compared with table offsets
-  unsigned lo0, lo1;   // window start keys (scaled densities)
-  unsigned nb0, nb1;   // window widths (0 = no window)
-  float nk0, lk0;      // below-window test: sat(h~ * nk + lk) = [h~ < lo]
-  float nk1, lk1;
-  float nh0, hk0;      // below-window-end test: sat(h~ * nh + hk) = [h~ < lo + nb]
-  float nh1, hk1;
+  Window w;            // P99 window (scaled densities), unless wdev is set
+  const Window* wdev;  // window computed on the device (read at the kernel's start)
   double pct;
   double tgt0, tgt1;   // target percentiles (for the scale factors)
 };
 
 
 // Rank selection inside the window, run by the last block of pass 1.
-__device__ void window_select(const WindowArgs& a) {
+__device__ void window_select(const WindowArgs& a, const Window& W) {
   SelectState* s = a.sel;
   __shared__ u64 s_tmp[33];
   __shared__ int s_idx, s_idx2;
@@ -163,13 +159,13 @@ __device__ void window_select(const WindowArgs& a) {
   }
   if (threadIdx.x == 0) {
     set_ranks(s, n, a.pct);
-    s->lo[0] = a.lo0; s->lo[1] = a.lo1; s->nb[0] = a.nb0; s->nb[1] = a.nb1;
+    s->lo[0] = W.lo0; s->lo[1] = W.lo1; s->nb[0] = W.nb0; s->nb[1] = W.nb1;
   }
   __syncthreads();
   for (int t = 0; t < kTracks; ++t) {
     const int j = t >> 1;
-    const unsigned nb = j ? a.nb1 : a.nb0;
-    const unsigned lo = j ? a.lo1 : a.lo0;
+    const unsigned nb = j ? W.nb1 : W.nb0;
+    const unsigned lo = j ? W.lo1 : W.lo0;
     const u64 r = s->rank[t];
     const u64 below = __ldcg(&s->below[j]);
     if (threadIdx.x == 0) s_res[t] = 0;
@@ -244,8 +240,9 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_window(WindowArgs a) {
   const Lasso L = a.m->lasso;
   const f2 NR1 = pk(L.nrho1, L.nrho1), NR2 = pk(L.nrho2, L.nrho2);
   f2 c_nw = pk(0.f, 0.f), c_b0 = pk(0.f, 0.f), c_b1 = pk(0.f, 0.f);
-  const WindowConst C{a.fine, a.wthr, a.lo0, a.lo1, a.nb0, a.nb1, a.nk0, a.lk0, a.nk1, a.lk1,
-                      a.nh0, a.hk0, a.nh1, a.hk1};
+  const Window W = a.wdev ? *a.wdev : a.w;
+  const WindowConst C{a.fine, a.wthr, W.lo0, W.lo1, W.nb0, W.nb1, W.nk0, W.lk0, W.nk1, W.lk1,
+                      W.nh0, W.hk0, W.nh1, W.hk1};
   const Geometry g = a.g;
   const u64 stride = (u64)gridDim.x * blockDim.x;
   const unsigned lane = threadIdx.x & 31u;
@@ -295,7 +292,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_window(WindowArgs a) {
   __syncthreads();
   if (s_ticket == gridDim.x - 1) {
     __threadfence();
-    window_select(a);
+    window_select(a, W);
   }
 }
 
@@ -486,54 +483,35 @@ int configure_pixel_kernels(Context* c) {
   return SPCN_OK;
 }
 
-// Window [lo, lo+nb) of FP32 keys around a percentile hint h > 0 (in the
-// units of the scaled densities), and the constants of the exact
-// below-window test sat(h~ * nk + lk) = [h~ < lo]: with lo in [2^e, 2^e+1),
-// any h~ < lo is at least 2^(e-24) below it, so nk = -2^(24-e) makes the
-// difference >= 1 before saturation.
-void below_consts(unsigned key, float* nk, float* lk) {
-  float f;
-  memcpy(&f, &key, 4);
-  int ex = 0;
-  frexpf(f, &ex);                  // f in [2^(ex-1), 2^ex)
-  const int K = 24 - (ex - 1);
-  *nk = -ldexpf(1.f, K);
-  *lk = ldexpf(f, K);
+// Window of the source's P99 from the basis estimated on the device (the
+// sample percentile as the hint, in the units of the source table), so that a
+// normalisation can follow a basis estimation without a host round trip.  A
+// failed estimation is recorded in the error word and leaves no window (the
+// exact fallback then runs; the outputs are computed but the call reports
+// the error).
+__global__ void k_window_from_basis(const Model* m, const SelectState* sample_sel,
+                                    const int* basis_status, Window* w, int* err) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  int st = *basis_status;
+  if (st == SPCN_OK) st = m->status;
+  if (st != SPCN_OK) record_error(err, st);
+  const double hs = ldexp(1.0, -m->lasso.hexp);
+  *w = st == SPCN_OK ? window_for(sample_sel->p99[0] * hs, sample_sel->p99[1] * hs)
+                     : window_for(0.0, 0.0);
 }
 
-void window_of(double hint, unsigned* lo, unsigned* nb, float* nk, float* lk, float* nh,
-                      float* hk) {
-  *nk = -1.f;
-  *lk = 0.f;
-  *nh = -1.f;
-  *hk = 0.f;
-  if (!(hint > 0.0) || !std::isfinite(hint) || hint * (1.0 - kWindowDelta) < 0x1p-100) {
-    *lo = 0u; *nb = 0u; return;
-  }
-  float flo = (float)(hint * (1.0 - kWindowDelta));
-  float fhi = (float)(hint * (1.0 + kWindowDelta));
-  unsigned klo, khi, kmid;
-  float fmid = (float)hint;
-  memcpy(&klo, &flo, 4);
-  memcpy(&khi, &fhi, 4);
-  memcpy(&kmid, &fmid, 4);
-  if (klo == 0u) klo = 1u;   // key 0 (h = 0) is counted below the window
-  if (khi < klo) khi = klo;
-  u64 width = (u64)khi - klo + 1;
-  if (width > (u64)kWinBins) {
-    klo = kmid > (unsigned)(kWinBins / 2) ? kmid - (unsigned)(kWinBins / 2) : 1u;
-    width = kWinBins;
-  }
-  *lo = klo;
-  *nb = (unsigned)width;
-  below_consts(klo, nk, lk);
-  below_consts(klo + (unsigned)width, nh, hk);
+int launch_window_from_basis(Context* c, const Model* m, const SelectState* sample_sel,
+                             const int* basis_status, Window* w, cudaStream_t st) {
+  k_window_from_basis<<<1, 32, 0, st>>>(m, sample_sel, basis_status, w, c->err);
+  SPCN_LAUNCH_CHECK(c);
+  return SPCN_OK;
 }
 
 // Pass 1 + select (+ radix fallback when a rank fell outside the window).
-int launch_percentile_passes(Context* c, const Geometry& g, const Model* m, int white_thresh,
-                             double pct, const double* hint, int hexp, const double* tgt_p99,
-                             cudaStream_t st) {
+// The window comes from a host hint, or (wdev) from device memory.
+static int percentile_passes(Context* c, const Geometry& g, const Model* m, int white_thresh,
+                             double pct, const Window& w, const Window* wdev,
+                             const double* tgt_p99, cudaStream_t st) {
   WindowArgs a;
   a.g = g;
   a.m = m;
@@ -542,16 +520,17 @@ int launch_percentile_passes(Context* c, const Geometry& g, const Model* m, int 
   a.coarse = c->coarse;
   a.err = c->err;
   a.wthr = ((unsigned)white_thresh + 1u) << 8;
-  const double hs = ldexp(1.0, -hexp);
-  window_of(hint ? hint[0] * hs : 0.0, &a.lo0, &a.nb0, &a.nk0, &a.lk0, &a.nh0, &a.hk0);
-  window_of(hint ? hint[1] * hs : 0.0, &a.lo1, &a.nb1, &a.nk1, &a.lk1, &a.nh1, &a.hk1);
+  a.w = w;
+  a.wdev = wdev;
   a.pct = pct;
   a.tgt0 = tgt_p99 ? tgt_p99[0] : 1.0;
   a.tgt1 = tgt_p99 ? tgt_p99[1] : 1.0;
   SPCN_CUDA_TRY(cudaMemsetAsync(c->sel, 0, sizeof(SelectState), st));
   SPCN_CUDA_TRY(cudaMemsetAsync(c->coarse, 0, sizeof(u64) * 2 * kWinGroups, st));
-  if (a.nb0) SPCN_CUDA_TRY(cudaMemsetAsync(c->fine, 0, sizeof(u64) * a.nb0, st));
-  if (a.nb1) SPCN_CUDA_TRY(cudaMemsetAsync(c->fine + kWinBins, 0, sizeof(u64) * a.nb1, st));
+  // the window's bins (all of them when the width is known on the device only)
+  const unsigned nb0 = wdev ? (unsigned)kWinBins : w.nb0, nb1 = wdev ? (unsigned)kWinBins : w.nb1;
+  if (nb0) SPCN_CUDA_TRY(cudaMemsetAsync(c->fine, 0, sizeof(u64) * nb0, st));
+  if (nb1) SPCN_CUDA_TRY(cudaMemsetAsync(c->fine + kWinBins, 0, sizeof(u64) * nb1, st));
   {
     TimedLaunch tl(c, SPCN_KERNEL_PASS1, st);
     k_pass_window<<<grid_of(c, c->occ_window), kPassThreads, kWindowSmem, st>>>(a);
@@ -576,6 +555,20 @@ int launch_percentile_passes(Context* c, const Geometry& g, const Model* m, int 
   }
   c->launches++;
   return SPCN_OK;
+}
+
+int launch_percentile_passes(Context* c, const Geometry& g, const Model* m, int white_thresh,
+                             double pct, const double* hint, int hexp, const double* tgt_p99,
+                             cudaStream_t st) {
+  const double hs = ldexp(1.0, -hexp);
+  const Window w = window_for(hint ? hint[0] * hs : 0.0, hint ? hint[1] * hs : 0.0);
+  return percentile_passes(c, g, m, white_thresh, pct, w, nullptr, tgt_p99, st);
+}
+
+int launch_percentile_passes_dev(Context* c, const Geometry& g, const Model* m, int white_thresh,
+                                 double pct, const Window* wdev, const double* tgt_p99,
+                                 cudaStream_t st) {
+  return percentile_passes(c, g, m, white_thresh, pct, window_for(0.0, 0.0), wdev, tgt_p99, st);
 }
 
 int launch_select_list(Context* c, const uint32_t* items, const u64* n_dev, const Model* m,

@@ -5,6 +5,8 @@
 // produce the same densities, keys and output bytes for the same pixel.
 #pragma once
 
+#include <string.h>
+
 #include "spcn_internal.cuh"
 
 namespace spcn {
@@ -250,13 +252,24 @@ struct ImageSource {
 };
 
 struct ListSource {
-  const uint32_t* items;   // packed R | G<<8 | B<<16, all non-white
+  const uint32_t* items;   // packed R | G<<8 | B<<16, all non-white; 16-byte aligned
   u64 n;
   template <class F>
   __device__ __forceinline__ void for_each(F&& f) const {
     const unsigned lr = lane_reg();
     const u64 stride = (u64)gridDim.x * blockDim.x;
-    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    // four items per 16-byte load, then the tail
+    const uint4* v4 = reinterpret_cast<const uint4*>(items);
+    const u64 n4 = n >> 2;
+    for (u64 i = t; i < n4; i += stride) {
+      const uint4 v = __ldg(v4 + i);
+      f(lut_addr(v.x, lr, 0), lut_addr(v.x, lr, 1), lut_addr(v.x, lr, 2), true);
+      f(lut_addr(v.y, lr, 0), lut_addr(v.y, lr, 1), lut_addr(v.y, lr, 2), true);
+      f(lut_addr(v.z, lr, 0), lut_addr(v.z, lr, 1), lut_addr(v.z, lr, 2), true);
+      f(lut_addr(v.w, lr, 0), lut_addr(v.w, lr, 1), lut_addr(v.w, lr, 2), true);
+    }
+    for (u64 i = (n4 << 2) + t; i < n; i += stride) {
       const uint32_t v = __ldg(items + i);
       f(lut_addr(v, lr, 0), lut_addr(v, lr, 1), lut_addr(v, lr, 2), true);
     }
@@ -408,12 +421,75 @@ __device__ __forceinline__ float recon_coef(const float* Wt, const double* scale
   return (float)(-(double)Wt[3 * j + c] * scale[j] * (double)hscale * 1.4426950408889634);
 }
 
-// Constants of the exact test sat(h~ * nk + lk) = [h~ < key] (host side).
-void below_consts(unsigned key, float* nk, float* lk);
+// P99 window of both stains and the constants of its exact tests:
+// sat(h~ nk + lk) = [h~ < lo] and sat(h~ nh + hk) = [h~ < lo + nb].
+struct Window {
+  unsigned lo0, lo1, nb0, nb1;   // window start keys and widths (nb = 0: no window)
+  float nk0, lk0, nk1, lk1;
+  float nh0, hk0, nh1, hk1;
+};
 
-// Window [lo, lo+nb) of FP32 keys around a percentile hint, and the constants
-// of its exact below-window and below-window-end tests (host side).
-void window_of(double hint, unsigned* lo, unsigned* nb, float* nk, float* lk, float* nh,
-               float* hk);
+__host__ __device__ inline unsigned key_of(float f) {
+  unsigned u;
+  memcpy(&u, &f, 4);
+  return u;
+}
+
+// Constants of the exact test sat(h~ * nk + lk) = [h~ < key]: with key in
+// [2^e, 2^(e+1)), any h~ < key is at least 2^(e-23) below it, so nk =
+// -2^(24-e) makes the difference >= 1 before saturation.  Host and device
+// (the same arithmetic on both).
+__host__ __device__ inline void below_consts(unsigned key, float* nk, float* lk) {
+  float f;
+  memcpy(&f, &key, 4);
+  int ex = 0;
+  frexpf(f, &ex);                  // f in [2^(ex-1), 2^ex)
+  const int K = 24 - (ex - 1);
+  *nk = -ldexpf(1.f, K);
+  *lk = ldexpf(f, K);
+}
+
+// Window [lo, lo+nb) of FP32 keys around a percentile hint h > 0 (in the
+// units of the scaled densities): +-kWindowDelta relative, at most kWinBins
+// keys; no window for a non-positive, non-finite or tiny hint.
+__host__ __device__ inline void window_of(double hint, unsigned* lo, unsigned* nb, float* nk,
+                                          float* lk, float* nh, float* hk) {
+  *nk = -1.f;
+  *lk = 0.f;
+  *nh = -1.f;
+  *hk = 0.f;
+  if (!(hint > 0.0) || !(hint <= 1.7976931348623157e308) ||
+      hint * (1.0 - kWindowDelta) < 0x1p-100) {
+    *lo = 0u; *nb = 0u; return;
+  }
+  unsigned klo = key_of((float)(hint * (1.0 - kWindowDelta)));
+  unsigned khi = key_of((float)(hint * (1.0 + kWindowDelta)));
+  const unsigned kmid = key_of((float)hint);
+  if (klo == 0u) klo = 1u;   // key 0 (h = 0) is counted below the window
+  if (khi < klo) khi = klo;
+  u64 width = (u64)khi - klo + 1;
+  if (width > (u64)kWinBins) {
+    klo = kmid > (unsigned)(kWinBins / 2) ? kmid - (unsigned)(kWinBins / 2) : 1u;
+    width = kWinBins;
+  }
+  *lo = klo;
+  *nb = (unsigned)width;
+  below_consts(klo, nk, lk);
+  below_consts(klo + (unsigned)width, nh, hk);
+}
+
+__host__ __device__ inline Window window_for(double hint0, double hint1) {
+  Window w;
+  window_of(hint0, &w.lo0, &w.nb0, &w.nk0, &w.lk0, &w.nh0, &w.hk0);
+  window_of(hint1, &w.lo1, &w.nb1, &w.nk1, &w.lk1, &w.nh1, &w.hk1);
+  return w;
+}
+
+// Host launchers that take a window (spcn_pixel.cu).
+int launch_window_from_basis(Context* c, const Model* m, const SelectState* sample_sel,
+                             const int* basis_status, Window* w, cudaStream_t st);
+int launch_percentile_passes_dev(Context* c, const Geometry& g, const Model* m, int white_thresh,
+                                 double pct, const Window* wdev, const double* tgt_p99,
+                                 cudaStream_t st);
 
 }  // namespace spcn

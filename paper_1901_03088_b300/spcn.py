@@ -103,6 +103,8 @@ def _load():
         "spcn_stain_densities": (ctypes.c_int, [vp, P(Image), P(Stats), P(Params), vp, i64, vp]),
         "spcn_normalize": (ctypes.c_int, [vp, P(Image), P(Stats), P(Stats), P(Params), vp, i64,
                                           P(ctypes.c_double), vp]),
+        "spcn_normalize_estimated": (ctypes.c_int, [vp, P(Image), P(Stats), P(Params), vp, i64,
+                                                    P(Stats), vp]),
         "spcn_synchronize": (ctypes.c_int, [vp, vp]),
         "spcn_launch_count": (i64, [vp]),
         "spcn_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -140,7 +142,7 @@ lib = _lib
 # Every name the header declares, for the export check.
 EXPORTED = ("spcn_params_default", "spcn_context_create", "spcn_context_destroy",
             "spcn_estimate_basis", "spcn_stain_percentile", "spcn_stain_densities",
-            "spcn_normalize", "spcn_synchronize", "spcn_launch_count", "spcn_strerror",
+            "spcn_normalize", "spcn_normalize_estimated", "spcn_synchronize", "spcn_launch_count", "spcn_strerror",
             "spcn_debug_barrier_timeout", "spcn_kernel_timing", "spcn_kernel_times",
             "spcn_estimate_basis_noalloc", "spcn_normalize_f32", "spcn_normalize_f32_backward",
             "spcn_batch_create", "spcn_batch_run", "spcn_batch_results", "spcn_batch_get_config",
@@ -283,6 +285,27 @@ class Context:
         if return_p99:
             return out, (float(p99[0]), float(p99[1]))
         return out
+
+    def normalize_estimated(self, src, tgt_stats: Stats, p: Params | None = None, out=None,
+                            return_stats: bool = False, stream=None):
+        """Estimate the source's statistics and normalise it in one
+        stream-ordered call (no host round trip in between).  With
+        return_stats the call waits and also returns the source Stats (p99 =
+        the exact percentile of the whole source)."""
+        import torch
+        im = image_of(src)
+        if out is None:
+            out = torch.empty_like(src, memory_format=torch.contiguous_format)
+        if out.shape != src.shape or out.dtype != torch.uint8 or out.stride(2) != 1 or out.stride(1) != 3:
+            raise ValueError("out must be an (H, W, 3) uint8 interleaved tensor")
+        p = p or params()
+        st = Stats() if return_stats else None
+        rc = _lib.spcn_normalize_estimated(self._h, ctypes.byref(im), ctypes.byref(tgt_stats),
+                                           ctypes.byref(p), ctypes.c_void_p(out.data_ptr()),
+                                           out.stride(0), ctypes.byref(st) if st is not None else None,
+                                           _stream(stream))
+        _check(rc, "spcn_normalize_estimated")
+        return (out, st) if return_stats else out
 
     def kernel_timing(self, enable: bool):
         """Start (and reset) or stop CUDA-event timing of the pixel kernels."""

@@ -287,3 +287,42 @@ def test_grid_wait_gives_up_without_fault(spcn, ctx):
     st = spcn.Stats.from_values(synth.stain_basis(9), [255, 255, 255])
     ctx.stain_densities(img, st)
     ctx.synchronize()
+
+
+# ------------------------------------------------------------------ estimate + normalise, one call
+@pytest.mark.parametrize("mode", ["all", "hash", "patches"])
+def test_normalize_estimated_matches_two_calls(spcn, ctx, mode):
+    # the device-resident hand-off gives the bytes and statistics of
+    # spcn_estimate_basis followed by spcn_normalize
+    src = to_dev(synth.make_image(300, 420, 1007, blobs=True))
+    tgt = to_dev(synth.make_image(256, 256, 1))
+    p = spcn.params(sample_mode=mode, sample_rate=0.2, n_patches=12, patch_size=48, seed=3)
+    t_st = ctx.estimate_basis(tgt, spcn.params(sample_mode="all"))
+    t_st.p99[0], t_st.p99[1] = ctx.stain_percentile(tgt, t_st)
+    s_st = ctx.estimate_basis(src, p)
+    ref, ref_p99 = ctx.normalize(src, s_st, t_st, p, return_p99=True)
+    out, st = ctx.normalize_estimated(src, t_st, p, return_stats=True)
+    assert torch.equal(out, ref)
+    assert list(st.W) == list(s_st.W) and list(st.i0) == list(s_st.i0)
+    assert (st.p99[0], st.p99[1]) == ref_p99
+    assert st.iters == s_st.iters and st.n_nonwhite == s_st.n_nonwhite
+    # asynchronous form
+    out2 = ctx.normalize_estimated(src, t_st, p)
+    ctx.synchronize()
+    assert torch.equal(out2, ref)
+
+
+def test_normalize_estimated_reports_no_tissue(spcn, ctx):
+    white = torch.full((64, 80, 3), 250, dtype=torch.uint8, device="cuda")
+    tgt = to_dev(synth.make_image(128, 128, 1))
+    t_st = ctx.estimate_basis(tgt, spcn.params(sample_mode="all"))
+    with pytest.raises(spcn.SpcnError) as e:
+        ctx.normalize_estimated(white, t_st, spcn.params(sample_mode="all"), return_stats=True)
+    assert e.value.kind == "NO_TISSUE"
+    ctx.normalize_estimated(white, t_st, spcn.params(sample_mode="all"))
+    with pytest.raises(spcn.SpcnError):
+        ctx.synchronize()
+    # the context stays usable
+    out = ctx.normalize_estimated(tgt, t_st, spcn.params(sample_mode="all"))
+    ctx.synchronize()
+    assert out.shape == tgt.shape
