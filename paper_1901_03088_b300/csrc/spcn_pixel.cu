@@ -139,7 +139,10 @@ struct WindowArgs {
 
 
 // Rank selection inside the window, run by the last block of pass 1.
-__device__ void window_select(const WindowArgs& a, const Window& W) {
+template <bool DEV>
+__device__ void window_select(const WindowArgs& a) {
+  const unsigned lo0 = DEV ? a.wdev->lo0 : a.w.lo0, lo1 = DEV ? a.wdev->lo1 : a.w.lo1;
+  const unsigned nb0 = DEV ? a.wdev->nb0 : a.w.nb0, nb1 = DEV ? a.wdev->nb1 : a.w.nb1;
   SelectState* s = a.sel;
   __shared__ u64 s_tmp[33];
   __shared__ int s_idx, s_idx2;
@@ -159,13 +162,13 @@ __device__ void window_select(const WindowArgs& a, const Window& W) {
   }
   if (threadIdx.x == 0) {
     set_ranks(s, n, a.pct);
-    s->lo[0] = W.lo0; s->lo[1] = W.lo1; s->nb[0] = W.nb0; s->nb[1] = W.nb1;
+    s->lo[0] = lo0; s->lo[1] = lo1; s->nb[0] = nb0; s->nb[1] = nb1;
   }
   __syncthreads();
   for (int t = 0; t < kTracks; ++t) {
     const int j = t >> 1;
-    const unsigned nb = j ? W.nb1 : W.nb0;
-    const unsigned lo = j ? W.lo1 : W.lo0;
+    const unsigned nb = j ? nb1 : nb0;
+    const unsigned lo = j ? lo1 : lo0;
     const u64 r = s->rank[t];
     const u64 below = __ldcg(&s->below[j]);
     if (threadIdx.x == 0) s_res[t] = 0;
@@ -226,6 +229,10 @@ __device__ __forceinline__ void drain_queue(const uint2* queue, int count, const
   }
 }
 
+// DEV: the window is read from device memory (computed there); otherwise it
+// is a kernel parameter, which the pixel loop uses without holding it in
+// registers.
+template <bool DEV>
 __global__ void __launch_bounds__(kPassThreads, 1) k_pass_window(WindowArgs a) {
   extern __shared__ __align__(16) char s_dyn[];
   unsigned* s_coarse = reinterpret_cast<unsigned*>(s_dyn + kLutSmemBytes);
@@ -240,9 +247,13 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_window(WindowArgs a) {
   const Lasso L = a.m->lasso;
   const f2 NR1 = pk(L.nrho1, L.nrho1), NR2 = pk(L.nrho2, L.nrho2);
   f2 c_nw = pk(0.f, 0.f), c_b0 = pk(0.f, 0.f), c_b1 = pk(0.f, 0.f);
-  const Window W = a.wdev ? *a.wdev : a.w;
-  const WindowConst C{a.fine, a.wthr, W.lo0, W.lo1, W.nb0, W.nb1, W.nk0, W.lk0, W.nk1, W.lk1,
-                      W.nh0, W.hk0, W.nh1, W.hk1};
+  // field by field, straight from the parameter (no reference to it, which
+  // would make the compiler copy the parameters to local memory)
+#define SPCN_WF(f) (DEV ? a.wdev->f : a.w.f)
+  const WindowConst C{a.fine,       a.wthr,       SPCN_WF(lo0), SPCN_WF(lo1), SPCN_WF(nb0),
+                      SPCN_WF(nb1), SPCN_WF(nk0), SPCN_WF(lk0), SPCN_WF(nk1), SPCN_WF(lk1),
+                      SPCN_WF(nh0), SPCN_WF(hk0), SPCN_WF(nh1), SPCN_WF(hk1)};
+#undef SPCN_WF
   const Geometry g = a.g;
   const u64 stride = (u64)gridDim.x * blockDim.x;
   const unsigned lane = threadIdx.x & 31u;
@@ -292,7 +303,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_window(WindowArgs a) {
   __syncthreads();
   if (s_ticket == gridDim.x - 1) {
     __threadfence();
-    window_select(a, W);
+    window_select<DEV>(a);
   }
 }
 
@@ -455,8 +466,10 @@ static int grid_of(const Context* c, int occ) {
 }
 
 int configure_pixel_kernels(Context* c) {
-  SPCN_CUDA_TRY(cudaFuncSetAttribute(k_pass_window, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kWindowSmem));
+  SPCN_CUDA_TRY(cudaFuncSetAttribute(k_pass_window<false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWindowSmem));
+  SPCN_CUDA_TRY(cudaFuncSetAttribute(k_pass_window<true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWindowSmem));
   SPCN_CUDA_TRY(cudaFuncSetAttribute(k_pass_recon, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)kLutSmemBytes));
   SPCN_CUDA_TRY(cudaFuncSetAttribute(k_pass_density, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -465,7 +478,7 @@ int configure_pixel_kernels(Context* c) {
                                      (int)kRadixSmem));
   SPCN_CUDA_TRY(cudaFuncSetAttribute(k_select_list, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)kRadixSmem));
-  SPCN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->occ_window, k_pass_window,
+  SPCN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->occ_window, k_pass_window<false>,
                                                               kPassThreads, kWindowSmem));
   SPCN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->occ_recon, k_pass_recon,
                                                               kPassThreads, kLutSmemBytes));
@@ -533,7 +546,10 @@ static int percentile_passes(Context* c, const Geometry& g, const Model* m, int 
   if (nb1) SPCN_CUDA_TRY(cudaMemsetAsync(c->fine + kWinBins, 0, sizeof(u64) * nb1, st));
   {
     TimedLaunch tl(c, SPCN_KERNEL_PASS1, st);
-    k_pass_window<<<grid_of(c, c->occ_window), kPassThreads, kWindowSmem, st>>>(a);
+    if (wdev)
+      k_pass_window<true><<<grid_of(c, c->occ_window), kPassThreads, kWindowSmem, st>>>(a);
+    else
+      k_pass_window<false><<<grid_of(c, c->occ_window), kPassThreads, kWindowSmem, st>>>(a);
   }
   SPCN_LAUNCH_CHECK(c);
 
