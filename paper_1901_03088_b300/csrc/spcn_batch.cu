@@ -553,19 +553,23 @@ __device__ __forceinline__ unsigned batch_pass1(const BatchArgs& a, unsigned til
   return ticket;
 }
 
-// One pass-2 item: chunks [c0, c1) of a tile, by the whole block.
+// One pass-2 item: chunks [c0, c1) of a tile, by the whole block.  The
+// block's table must be the tile's optical-density table.
 template <class G>
 __device__ __forceinline__ void batch_pass2(const BatchArgs& a, unsigned tile, u64 c0, u64 c1,
-                                            const char* lut, unsigned lr, const float* s_M) {
+                                            const char* lut, const float* s_M) {
   const BatchTile* T = a.tiles + tile;
   const G g = geometry_as<G>(T->g);
-  const Lasso L = a.models[T->model].lasso;
+  const Model* m = a.models + T->model;
+  const Lasso L = m->lasso;
+  const ProjConst P = proj_const(m);
   const ReconConst K = recon_const(s_M, a.l2i0);
   const f2 NR1 = pk(L.nrho1, L.nrho1), NR2 = pk(L.nrho2, L.nrho2);
+  const unsigned lr = lane_reg_od();
   for_chunks<true, true>(g, c0 + threadIdx.x, c1, blockDim.x,
                          [&](const unsigned (&w)[12], const ChunkPos& p) {
                            unsigned o[12];
-                           recon_chunk(w, lut, lr, NR1, NR2, L.kappa, K, o);
+                           recon_chunk(w, lut, lr, P, NR1, NR2, L.kappa, K, o);
                            store_chunk(g, p, o);
                          });
 }
@@ -587,7 +591,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch(BatchArgs a) {
   __shared__ unsigned s_piece;
   __shared__ float s_M[6];
   const unsigned lr = lane_reg();
-  int cur_model = -1;
+  int cur_table = -1;   // table in shared memory: 2 * model + (1: optical densities, 0: projected)
   // Thread 0 runs the queue one item ahead: the next item's descriptor is
   // copied into shared memory asynchronously (cp.async) and the ticket of the
   // one after it is in flight while the block works; the completion ticket of
@@ -638,9 +642,11 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch(BatchArgs a) {
         continue;
       }
     }
-    if ((int)item.model != cur_model) {
-      load_lut(a.models + item.model, lut);
-      cur_model = (int)item.model;
+    const int want = 2 * (int)item.model + (item.pass == 2 ? 1 : 0);
+    if (want != cur_table) {
+      if (item.pass == 2) load_od_lut(a.models + item.model, lut);
+      else load_lut(a.models + item.model, lut);
+      cur_table = want;
     }
     if (item.pass == 1) {
       const unsigned tk = batch_pass1<G>(a, item.tile, item.c0, item.c1, lut, lr, s_queue, s_kb,
@@ -651,7 +657,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch(BatchArgs a) {
         pend_last = item.n_items1 - 1u;
       }
     } else {
-      batch_pass2<G>(a, item.tile, item.c0, item.c1, lut, lr, s_M);
+      batch_pass2<G>(a, item.tile, item.c0, item.c1, lut, s_M);
     }
     __syncthreads();   // the item is done: shared words and the table may be rewritten
   }
@@ -666,9 +672,9 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch(BatchArgs a) {
     const BatchTile* T = a.tiles + t;
     const unsigned model = T->model;
     __syncthreads();
-    if ((int)model != cur_model) {
+    if (2 * (int)model != cur_table) {   // the select reads the projected table
       load_lut(a.models + model, lut);
-      cur_model = (int)model;
+      cur_table = 2 * (int)model;
     }
     const Lasso L = a.models[model].lasso;
     u64 rank[kTracks];
@@ -688,12 +694,18 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch(BatchArgs a) {
       for (int i = 0; i < 6; ++i) s_M[i] = recon_coef(a.Wt, sc, L.hscale, i);
     }
     __syncthreads();
+    // the tile's pass 2 over the whole grid, from its optical-density table
+    __syncthreads();
+    load_od_lut(a.models + model, lut);
+    cur_table = 2 * (int)model + 1;
+    const ProjConst P = proj_const(a.models + model);
     const ReconConst K = recon_const(s_M, a.l2i0);
     const f2 NR1 = pk(L.nrho1, L.nrho1), NR2 = pk(L.nrho2, L.nrho2);
+    const unsigned lro = lane_reg_od();
     const Geometry g = T->g;
     for_each_chunk<true, true>(g, [&](const unsigned (&w)[12], const ChunkPos& p) {
       unsigned o[12];
-      recon_chunk(w, lut, lr, NR1, NR2, L.kappa, K, o);
+      recon_chunk(w, lut, lro, P, NR1, NR2, L.kappa, K, o);
       store_chunk(g, p, o);
     });
   }

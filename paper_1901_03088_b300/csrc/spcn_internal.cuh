@@ -71,6 +71,8 @@ struct Model {
   float2 proj[kLutEntries];   // s ((W[c,0] v_c(i) - [c==0] lambda)/G11, (W[c,1] v_c(i) - [c==0] lambda)/G22)
   float od[kLutEntries];      // v_c(i) = log(i0_c / max(i,1))
   Lasso lasso;
+  float pa[6];                // s W[c,j] / G_jj, index 3 j + c (pass 2 projects OD with FMAs)
+  float pb[2];                // -s lambda / G_jj
   float W[6];                 // column-major 3x2
   float i0[3];
   int status;
@@ -273,6 +275,23 @@ __device__ __forceinline__ void load_lut(const Model* __restrict__ m, char* s) {
 }
 
 __device__ __forceinline__ unsigned lane_reg() { return (threadIdx.x & 15u) << 3; }
+
+// Optical-density table for pass 2: the same 256-byte rows, but 4-byte
+// entries v_c(i) with one copy per lane of the warp (32 copies: a 4-byte
+// load by 32 lanes is one conflict-free wavefront, half the wavefronts of
+// the projected table's 8-byte loads).  Row i of the first 64 KB holds R
+// then G, the second 64 KB holds B; lane l's entry is at i*256 + 4 l.
+__device__ __forceinline__ void load_od_lut(const Model* __restrict__ m, char* s) {
+  float* f = reinterpret_cast<float*>(s);
+  for (int i = threadIdx.x; i < 2 * 256 * 64; i += blockDim.x) {
+    const int region = i >> 14, row = (i >> 6) & 255, half = (i >> 5) & 1;
+    const int c = region == 0 ? half : 2;
+    f[i] = (region == 1 && half == 1) ? 0.f : m->od[c * 256 + row];
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ unsigned lane_reg_od() { return (threadIdx.x & 31u) << 2; }
 
 // Inclusive warp scan of 64-bit counts.
 __device__ __forceinline__ u64 warp_incl_scan(u64 v) {

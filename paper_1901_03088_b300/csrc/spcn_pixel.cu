@@ -98,6 +98,12 @@ __global__ void k_build_model(Model* m, ModelIn in, const Model* from) {
       m->status = SPCN_ERR_DEGENERATE_BASIS;
     }
     m->lasso = L;
+    for (int j = 0; j < 2; ++j) {
+      const double gjj = j ? g22 : g11;
+      for (int c = 0; c < 3; ++c)
+        m->pa[3 * j + c] = ok ? (float)(s * (double)W[3 * j + c] / gjj) + 0.f : 0.f;
+      m->pb[j] = ok ? (float)(-s * (double)in.lambda / gjj) + 0.f : 0.f;
+    }
     if (from != m) {
       for (int i = 0; i < 6; ++i) m->W[i] = W[i];
       for (int i = 0; i < 3; ++i) m->i0[i] = i0[i];
@@ -388,9 +394,10 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_recon(ReconArgs a) {
   if (threadIdx.x < 6) {
     s_M[threadIdx.x] = recon_coef(a.Wt, a.sel->scale, L.hscale, threadIdx.x);
   }
-  load_lut(a.m, s_dyn);
+  load_od_lut(a.m, s_dyn);
   const char* lut = s_dyn;
-  const unsigned lr = lane_reg();
+  const unsigned lr = lane_reg_od();
+  const ProjConst P = proj_const(a.m);
   ReconConst K;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -401,7 +408,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_recon(ReconArgs a) {
   const f2 NR1 = pk(L.nrho1, L.nrho1), NR2 = pk(L.nrho2, L.nrho2);
   for_each_chunk<true, true>(a.g, [&](const unsigned (&w)[12], const ChunkPos& p) {
     unsigned o[12];
-    recon_chunk(w, lut, lr, NR1, NR2, L.kappa, K, o);
+    recon_chunk(w, lut, lr, P, NR1, NR2, L.kappa, K, o);
     store_chunk(a.g, p, o);
   });
 }

@@ -383,9 +383,56 @@ struct ReconConst {
   f2 M1[3], M2[3], L2[3];   // exponent: e_c = L2_c + M1_c h~1 + M2_c h~2 (both lanes equal)
 };
 
+// Eq. 1-2 projection of pass 2: d_j = sum_c pa[3j+c] v_c + pb[j], i.e. the
+// projected table's s (W[:,j].v - lambda) / G_jj computed with FMAs from the
+// optical densities (FP32; within a few ulp of the table's single rounding).
+struct ProjConst {
+  f2 A10, A11, A20, A21, B1, B2;   // pa[0], pa[1], pa[3], pa[4], pb[0], pb[1] in both lanes
+  float a12, a22;                  // pa[2], pa[5]
+};
+
+__device__ __forceinline__ ProjConst proj_const(const Model* m) {
+  ProjConst P;
+  P.A10 = pk(m->pa[0], m->pa[0]);
+  P.A11 = pk(m->pa[1], m->pa[1]);
+  P.a12 = m->pa[2];
+  P.A20 = pk(m->pa[3], m->pa[3]);
+  P.A21 = pk(m->pa[4], m->pa[4]);
+  P.a22 = m->pa[5];
+  P.B1 = pk(m->pb[0], m->pb[0]);
+  P.B2 = pk(m->pb[1], m->pb[1]);
+  return P;
+}
+
+__device__ __forceinline__ float od_ld(const char* lut, unsigned off) {
+  return *reinterpret_cast<const float*>(lut + off);
+}
+
+// The closed-form H-step of two pixels from the optical-density table.
+__device__ __forceinline__ void solve_pair_od(const char* lut, unsigned aRA, unsigned aGA,
+                                              unsigned aBA, unsigned aRB, unsigned aGB,
+                                              unsigned aBB, const ProjConst& P, f2 NR1, f2 NR2,
+                                              float kappa, f2& H1, f2& H2) {
+  const float vRA = od_ld(lut, aRA), vGA = od_ld(lut, aGA + kLutOffG), vBA = od_ld(lut, aBA + kLutOffB);
+  const float vRB = od_ld(lut, aRB), vGB = od_ld(lut, aGB + kLutOffG), vBB = od_ld(lut, aBB + kLutOffB);
+  const f2 VR = pk(vRA, vRB), VG = pk(vGA, vGB);
+  const f2 S1 = fma2(P.A11, VG, fma2(P.A10, VR, P.B1));
+  const f2 S2 = fma2(P.A21, VG, fma2(P.A20, VR, P.B2));
+  const float D1A = fma_sat(P.a12, vBA, lo_of(S1)), D1B = fma_sat(P.a12, vBB, hi_of(S1));
+  const float D2A = fma_sat(P.a22, vBA, lo_of(S2)), D2B = fma_sat(P.a22, vBB, hi_of(S2));
+  const f2 P1 = pk(D1A, D1B), P2 = pk(D2A, D2B);
+  const f2 Q1 = fma2(NR1, P2, P1);
+  const f2 Q2 = fma2(NR2, P1, P2);
+  const float t1A = mul_sat(kappa, lo_of(Q1)), t1B = mul_sat(kappa, hi_of(Q1));
+  const float t2A = mul_sat(kappa, lo_of(Q2)), t2B = mul_sat(kappa, hi_of(Q2));
+  H1 = pk(fminf(D1A, t1A), fminf(D1B, t1B));
+  H2 = pk(fminf(D2A, t2A), fminf(D2B, t2B));
+}
+
+// Pass 2 on one chunk (optical-density table, lane register lane_reg_od()).
 __device__ __forceinline__ void recon_chunk(const unsigned (&w)[12], const char* lut,
-                                            unsigned lr, f2 NR1, f2 NR2, float kappa,
-                                            const ReconConst& K, unsigned (&o)[12]) {
+                                            unsigned lr, const ProjConst& P, f2 NR1, f2 NR2,
+                                            float kappa, const ReconConst& K, unsigned (&o)[12]) {
   unsigned y[48];
 #pragma unroll
   for (int p = 0; p < kChunk / 2; ++p) {
@@ -394,7 +441,7 @@ __device__ __forceinline__ void recon_chunk(const unsigned (&w)[12], const char*
     pixel_addr(w, kA, lr, aRA, aGA, aBA);
     pixel_addr(w, kB, lr, aRB, aGB, aBB);
     f2 H1, H2;
-    solve_pair(lut, aRA, aGA, aBA, aRB, aGB, aBB, NR1, NR2, kappa, H1, H2);
+    solve_pair_od(lut, aRA, aGA, aBA, aRB, aGB, aBB, P, NR1, NR2, kappa, H1, H2);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       // Eq. 3-4: i' = i0_t 2^(-log2e sum_j W_t[c,j] s_j h_j)
