@@ -463,17 +463,17 @@ int spcn_normalize_estimated(void* ctx, const spcn_image* src, const spcn_stats*
   // basis estimation, left on the device
   rc = launch_estimate_basis(c, src, params, s);
   if (rc) return rc;
-  // source table from the estimated basis and i0, window from the sample P99
-  rc = launch_build_model(c, c->model, nullptr, nullptr, params->lambda, c->model_b, s);
-  if (rc) return rc;
+  // the basis estimation's final table (estimated basis and i0, this lambda)
+  // is the source table; the window comes from the sample P99
+  const Model* m = c->model_b;
   Window* wdev = static_cast<Window*>(c->wdev);
-  rc = launch_window_from_basis(c, c->model, &c->bs->sel, &c->bs->status, wdev, s);
+  rc = launch_window_from_basis(c, m, &c->bs->sel, &c->bs->status, wdev, s);
   if (rc) return rc;
   const Geometry g = make_geometry(src, out, out_pitch);
-  rc = launch_percentile_passes_dev(c, g, c->model, params->white_thresh,
-                                    (double)params->stain_pct, wdev, tgt_st->p99, s);
+  rc = launch_percentile_passes_dev(c, g, m, params->white_thresh, (double)params->stain_pct,
+                                    wdev, tgt_st->p99, s);
   if (rc) return rc;
-  rc = launch_recon(c, g, c->model, tgt_st->W, tgt_st->i0, s);
+  rc = launch_recon(c, g, m, tgt_st->W, tgt_st->i0, s);
   if (rc) return rc;
   if (src_st_out) {
     memset(src_st_out, 0, sizeof(*src_st_out));

@@ -117,16 +117,28 @@ __global__ void k_patch_count(PatchArgs a) {
   if (threadIdx.x == 0) a.cand[k] = (int)tot;
 }
 
-// Keep candidates, in order, while at least half their pixels are non-white.
+// Keep candidates, in order, while at least half their pixels are non-white:
+// one warp scans them 32 at a time (ballot + prefix counts), the same list as
+// a sequential scan.
 __global__ void k_patch_accept(PatchArgs a) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+  const unsigned lane = threadIdx.x;
   const long long need = (long long)a.P * a.P;
   int n = 0;
-  for (int k = 0; k < a.n_cand && n < a.n_patches; ++k)
-    if (2ll * a.cand[k] >= need) a.cand[a.n_cand + n++] = k;
-  a.bs->n_acc = n;
-  a.bs->m = (u64)n * (u64)need;
-  if (n == 0) a.bs->status = SPCN_ERR_NO_TISSUE;
+  for (int k0 = 0; k0 < a.n_cand && n < a.n_patches; k0 += 32) {
+    const int k = k0 + (int)lane;
+    const bool ok = k < a.n_cand && 2ll * a.cand[k] >= need;
+    const unsigned ball = __ballot_sync(0xFFFFFFFFu, ok);
+    const int pos = n + __popc(ball & ((1u << lane) - 1u));
+    if (ok && pos < a.n_patches) a.cand[a.n_cand + pos] = k;
+    n += __popc(ball);
+  }
+  if (n > a.n_patches) n = a.n_patches;
+  if (lane == 0) {
+    a.bs->n_acc = n;
+    a.bs->m = (u64)n * (u64)need;
+    if (n == 0) a.bs->status = SPCN_ERR_NO_TISSUE;
+  }
 }
 
 // Eight blocks per kept patch (interleaved rows): copy its pixels, raster
