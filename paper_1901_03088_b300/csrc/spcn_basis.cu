@@ -342,6 +342,24 @@ struct SnmfArgs {
 
 // Reduced sums, in this order: A11 A12 A22 | B[R,0] B[R,1] B[G,0] B[G,1]
 // B[B,0] B[B,1] | sum h1, sum h2 | sum |v|^2.
+// The W update runs on one thread per block between two grid barriers, so
+// its dependent FP64 chain is on the critical path of every iteration; an
+// FP64 division or square root costs an order of magnitude more latency than
+// an FMA on this GPU.  Reciprocals and inverse square roots therefore start
+// from the FP32 instruction and take one Newton step in FP64 (relative error
+// about 1.5 e0^2 for a seed error e0 <= 2^-22, i.e. below 1e-13), with the
+// exact FP64 operation outside the range where the FP32 seed is accurate.
+__device__ __forceinline__ double rcp_nr(double x) {
+  if (!(x > 1e-30 && x < 1e30)) return 1.0 / x;
+  const double e = (double)(1.0f / (float)x);
+  return fma(e, fma(-x, e, 1.0), e);            // e (2 - x e)
+}
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  if (!(x > 1e-30 && x < 1e30)) return 1.0 / sqrt(x);
+  const double r = (double)rsqrtf((float)x);
+  return r * fma(-0.5 * x, r * r, 1.5);         // r (3 - x r^2) / 2
+}
+
 __global__ void __launch_bounds__(kSnmfThreads) k_snmf(SnmfArgs a) {
   __shared__ float s_od[kLutEntries];
   __shared__ double s_W[6];
@@ -350,6 +368,8 @@ __global__ void __launch_bounds__(kSnmfThreads) k_snmf(SnmfArgs a) {
   __shared__ double s_red[kSnmfThreads / 32][kAcc];
   __shared__ int s_flag;
   __shared__ double s_obj;
+  __shared__ double s_Wp[6];   // the basis the last H-step used (for the objective)
+  __shared__ int s_have;
   const u64 n = a.bs->n_nw;
   if (n == 0) {
     if (blockIdx.x == 0 && threadIdx.x == 0) a.bs->status = SPCN_ERR_NO_TISSUE;
@@ -357,7 +377,7 @@ __global__ void __launch_bounds__(kSnmfThreads) k_snmf(SnmfArgs a) {
   }
   for (int i = threadIdx.x; i < kLutEntries; i += blockDim.x) s_od[i] = a.m->od[i];
   if (threadIdx.x < 6) s_W[threadIdx.x] = a.bs->W[threadIdx.x];
-  if (threadIdx.x == 0) { s_flag = 0; s_obj = 0.0; }
+  if (threadIdx.x == 0) { s_flag = 0; s_obj = 0.0; s_have = 0; }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const u64 gstride = (u64)gridDim.x * blockDim.x;
@@ -376,13 +396,14 @@ __global__ void __launch_bounds__(kSnmfThreads) k_snmf(SnmfArgs a) {
     if (!(det > 1e-12)) {
       s_flag = -1;
     } else {
+      const double id = rcp_nr(det);
       for (int i = 0; i < 6; ++i) s_coef[i] = (float)s_W[i];
-      s_coef[6] = (float)(g22 / det);
-      s_coef[7] = (float)(-g12 / det);
-      s_coef[8] = (float)(-g12 / det);
-      s_coef[9] = (float)(g11 / det);
-      s_coef[10] = (float)(1.0 / g11);
-      s_coef[11] = (float)(1.0 / g22);
+      s_coef[6] = (float)(g22 * id);
+      s_coef[7] = (float)(-g12 * id);
+      s_coef[8] = (float)(-g12 * id);
+      s_coef[9] = (float)(g11 * id);
+      s_coef[10] = (float)rcp_nr(g11);
+      s_coef[11] = (float)rcp_nr(g22);
     }
   };
   if (threadIdx.x == 0) set_coef();
@@ -418,28 +439,57 @@ __global__ void __launch_bounds__(kSnmfThreads) k_snmf(SnmfArgs a) {
       acc[10] += h2;
       acc[11] = fmaf(v0, v0, fmaf(v1, v1, fmaf(v2, v2, acc[11])));
     };
+    // Two pixels per packed FP32x2 instruction: each lane rounds exactly as
+    // the scalar step does; the lanes accumulate apart and are added at the end.
+    const f2 W00 = pk(w00, w00), W10 = pk(w10, w10), W20 = pk(w20, w20);
+    const f2 W01 = pk(w01, w01), W11 = pk(w11, w11), W21 = pk(w21, w21);
+    const f2 A11 = pk(a11, a11), A12 = pk(a12, a12), A21 = pk(a21, a21), A22 = pk(a22, a22);
+    const f2 U1 = pk(u1, u1), U2 = pk(u2, u2), NL = pk(-a.lambda, -a.lambda);
+    f2 pacc[kAcc];
+#pragma unroll
+    for (int i = 0; i < kAcc; ++i) pacc[i] = 0ull;
+    auto step2 = [&](uint32_t v, uint32_t u) {
+      const f2 V0 = pk(s_od[v & 0xFFu], s_od[u & 0xFFu]);
+      const f2 V1 = pk(s_od[256 + ((v >> 8) & 0xFFu)], s_od[256 + ((u >> 8) & 0xFFu)]);
+      const f2 V2 = pk(s_od[512 + ((v >> 16) & 0xFFu)], s_od[512 + ((u >> 16) & 0xFFu)]);
+      const f2 D1 = add2(fma2(W20, V2, fma2(W10, V1, mul2(W00, V0))), NL);
+      const f2 D2 = add2(fma2(W21, V2, fma2(W11, V1, mul2(W01, V0))), NL);
+      const f2 T1 = fma2(A12, pk(fmaxf(lo_of(D2), 0.f), fmaxf(hi_of(D2), 0.f)), mul2(A11, D1));
+      const f2 T2 = fma2(A21, pk(fmaxf(lo_of(D1), 0.f), fmaxf(hi_of(D1), 0.f)), mul2(A22, D2));
+      const f2 X1 = mul2(U1, D1), X2 = mul2(U2, D2);
+      const f2 H1 = pk(fmaxf(0.f, fminf(lo_of(X1), lo_of(T1))), fmaxf(0.f, fminf(hi_of(X1), hi_of(T1))));
+      const f2 H2 = pk(fmaxf(0.f, fminf(lo_of(X2), lo_of(T2))), fmaxf(0.f, fminf(hi_of(X2), hi_of(T2))));
+      pacc[0] = fma2(H1, H1, pacc[0]);
+      pacc[1] = fma2(H1, H2, pacc[1]);
+      pacc[2] = fma2(H2, H2, pacc[2]);
+      pacc[3] = fma2(V0, H1, pacc[3]);
+      pacc[4] = fma2(V0, H2, pacc[4]);
+      pacc[5] = fma2(V1, H1, pacc[5]);
+      pacc[6] = fma2(V1, H2, pacc[6]);
+      pacc[7] = fma2(V2, H1, pacc[7]);
+      pacc[8] = fma2(V2, H2, pacc[8]);
+      pacc[9] = add2(pacc[9], H1);
+      pacc[10] = add2(pacc[10], H2);
+      pacc[11] = fma2(V0, V0, fma2(V1, V1, fma2(V2, V2, pacc[11])));
+    };
     // four pixels per 16-byte load (the list is 16-byte aligned), then the tail
     const uint4* nw4 = reinterpret_cast<const uint4*>(a.nw);
     const u64 n4 = n >> 2;
     u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x;
     for (; i + gstride < n4; i += 2 * gstride) {   // two loads in flight
       const uint4 v = __ldg(nw4 + i), u = __ldg(nw4 + i + gstride);
-      step(v.x);
-      step(v.y);
-      step(v.z);
-      step(v.w);
-      step(u.x);
-      step(u.y);
-      step(u.z);
-      step(u.w);
+      step2(v.x, v.y);
+      step2(v.z, v.w);
+      step2(u.x, u.y);
+      step2(u.z, u.w);
     }
     if (i < n4) {
       const uint4 v = __ldg(nw4 + i);
-      step(v.x);
-      step(v.y);
-      step(v.z);
-      step(v.w);
+      step2(v.x, v.y);
+      step2(v.z, v.w);
     }
+#pragma unroll
+    for (int i = 0; i < kAcc; ++i) acc[i] = lo_of(pacc[i]) + hi_of(pacc[i]);
     for (u64 i = (n4 << 2) + (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gstride)
       step(__ldg(a.nw + i));
     // warp sums in FP32 (a fixed shuffle tree: deterministic), FP64 from the
@@ -454,10 +504,15 @@ __global__ void __launch_bounds__(kSnmfThreads) k_snmf(SnmfArgs a) {
     }
     __syncthreads();
     double* part = a.partials + (size_t)(it & 1) * gridDim.x * kAcc;
-    if (threadIdx.x < kAcc) {
-      double x = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x += s_red[w][threadIdx.x];
-      part[(size_t)blockIdx.x * kAcc + threadIdx.x] = x;
+    if (threadIdx.x < kAcc) {   // a fixed pairwise tree over the warps
+      double x[kSnmfThreads / 32];
+#pragma unroll
+      for (int w = 0; w < kSnmfThreads / 32; ++w) x[w] = s_red[w][threadIdx.x];
+#pragma unroll
+      for (int h = kSnmfThreads / 64; h > 0; h >>= 1)
+#pragma unroll
+        for (int w = 0; w < h; ++w) x[w] += x[w + h];
+      part[(size_t)blockIdx.x * kAcc + threadIdx.x] = x[0];
     }
     target += gridDim.x;
     if (!grid_barrier(a.bar, target, a.abort, a.err, a.timeout_ns)) return;
@@ -466,7 +521,16 @@ __global__ void __launch_bounds__(kSnmfThreads) k_snmf(SnmfArgs a) {
     // every block gets bit-identical totals and reruns are deterministic
     if (warp < kAcc) {
       double x = 0.0;
-      for (unsigned b = lane; b < gridDim.x; b += 32) x += __ldcg(part + (size_t)b * kAcc + warp);
+      for (unsigned b0 = lane; b0 < gridDim.x; b0 += 32u * 8u) {   // eight loads in flight
+        double v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const unsigned b = b0 + 32u * k;
+          v[k] = b < gridDim.x ? __ldcg(part + (size_t)b * kAcc + warp) : 0.0;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x += v[k];
+      }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
       if (lane == 0) s_tot[warp] = x;
@@ -478,28 +542,21 @@ __global__ void __launch_bounds__(kSnmfThreads) k_snmf(SnmfArgs a) {
       for (int c = 0; c < 3; ++c) { B[c][0] = s_tot[3 + 2 * c]; B[c][1] = s_tot[4 + 2 * c]; }
       double W[3][2], Wp[3][2];
       for (int c = 0; c < 3; ++c) { W[c][0] = Wp[c][0] = s_W[c]; W[c][1] = Wp[c][1] = s_W[3 + c]; }
-      // objective of the H-step just taken (1/2-scaled Eq. 2)
-      double g11 = 0, g22 = 0, g12 = 0, wb = 0;
-      for (int c = 0; c < 3; ++c) {
-        g11 += Wp[c][0] * Wp[c][0];
-        g22 += Wp[c][1] * Wp[c][1];
-        g12 += Wp[c][0] * Wp[c][1];
-        wb += Wp[c][0] * B[c][0] + Wp[c][1] * B[c][1];
-      }
-      s_obj = 0.5 * s_tot[11] - wb + 0.5 * (g11 * A[0][0] + 2.0 * g12 * A[0][1] + g22 * A[1][1]) +
-              (double)a.lambda * (s_tot[9] + s_tot[10]);
+      for (int i = 0; i < 6; ++i) s_Wp[i] = s_W[i];   // objective taken at the end
+      s_have = 1;
+      const double iA[2] = {rcp_nr(A[0][0]), rcp_nr(A[1][1])};
       int flag = 0;
       for (int j = 0; j < 2 && flag == 0; ++j) {
         if (!(A[j][j] > 0.0)) continue;
         double u[3], nu = 0.0;
         for (int c = 0; c < 3; ++c) {
-          u[c] = W[c][j] + (B[c][j] - (W[c][0] * A[0][j] + W[c][1] * A[1][j])) / A[j][j];
+          u[c] = W[c][j] + (B[c][j] - (W[c][0] * A[0][j] + W[c][1] * A[1][j])) * iA[j];
           u[c] = u[c] > 0.0 ? u[c] : 0.0;
           nu += u[c] * u[c];
         }
-        nu = sqrt(nu);
         if (!(nu > 0.0)) { flag = -1; break; }
-        for (int c = 0; c < 3; ++c) W[c][j] = u[c] / nu;
+        const double r = rsqrt_nr(nu);
+        for (int c = 0; c < 3; ++c) W[c][j] = u[c] * r;
       }
       double dmax = 0.0;
       for (int c = 0; c < 3; ++c)
@@ -513,6 +570,18 @@ __global__ void __launch_bounds__(kSnmfThreads) k_snmf(SnmfArgs a) {
     if (s_flag != 0) break;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (s_have) {   // objective of the last H-step taken (1/2-scaled Eq. 2)
+      double g11 = 0, g22 = 0, g12 = 0, wb = 0;
+      for (int c = 0; c < 3; ++c) {
+        g11 += s_Wp[c] * s_Wp[c];
+        g22 += s_Wp[3 + c] * s_Wp[3 + c];
+        g12 += s_Wp[c] * s_Wp[3 + c];
+        wb += s_Wp[c] * s_tot[3 + 2 * c] + s_Wp[3 + c] * s_tot[4 + 2 * c];
+      }
+      s_obj = 0.5 * s_tot[11] - wb +
+              0.5 * (g11 * s_tot[0] + 2.0 * g12 * s_tot[1] + g22 * s_tot[2]) +
+              (double)a.lambda * (s_tot[9] + s_tot[10]);
+    }
     int status = SPCN_OK;
     double g11 = 0, g22 = 0, g12 = 0;
     for (int c = 0; c < 3; ++c) {

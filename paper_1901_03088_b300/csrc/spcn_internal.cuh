@@ -141,9 +141,12 @@ __device__ __forceinline__ bool grid_barrier(unsigned* counter, unsigned target,
   if (threadIdx.x == 0) {
     __threadfence();
     atomicAdd(counter, 1u);
-    unsigned long long t0 = global_timer_ns();
+    const unsigned long long t0 = global_timer_ns();
     int ok = 1;
-    while (ld_acquire(counter) < target) {
+    // back-to-back acquire polls (the acquire orders this block's later
+    // reads); the abort word and the clock every 16th poll
+    for (unsigned polls = 1; ld_acquire(counter) < target; ++polls) {
+      if ((polls & 15u) != 0u) continue;
       if (*(volatile int*)abort != 0) { ok = 0; break; }
       if ((long long)(global_timer_ns() - t0) > timeout_ns) {
         atomicExch(abort, 1);
@@ -151,9 +154,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* counter, unsigned target,
         ok = 0;
         break;
       }
-      __nanosleep(100);
     }
-    __threadfence();
     s_ok = ok;
   }
   __syncthreads();
