@@ -115,8 +115,10 @@ int ensure_candidate_capacity(Context* c, int n);
   } while (0)
 
 // Shared-memory sizes of the pixel kernels.
+constexpr int kChunkStack = 32;   // per-warp stack of tissue chunks in pass 1 (at most 31 used)
 constexpr size_t kWindowSmem = kLutSmemBytes + sizeof(unsigned) * 2 * kWinGroups +
-                               sizeof(uint2) * 2 * kPassThreads;   // per-warp chunk queues of pass 1 (64 each)
+                               sizeof(uint2) * 2 * kPassThreads +   // per-warp hit queues (64 each)
+                               (3 * sizeof(uint4) + sizeof(unsigned)) * kChunkStack * (kPassThreads / 32);
 constexpr size_t kRadixSmem = kLutSmemBytes + sizeof(unsigned) * kTracks * kRadixBins;
 
 int configure_pixel_kernels(Context* c);

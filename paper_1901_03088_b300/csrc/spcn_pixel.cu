@@ -137,6 +137,7 @@ struct WindowArgs {
   u64* coarse;
   int* err;
   unsigned wthr;       // (white threshold + 1) << 8, compared with table offsets
+  unsigned wm, we;     // all-white test of a full chunk: (AND of its words & wm) == we
   Window w;            // P99 window (scaled densities), unless wdev is set
   const Window* wdev;  // window computed on the device (read at the kernel's start)
   double pct;
@@ -235,15 +236,108 @@ __device__ __forceinline__ void drain_queue(const uint2* queue, int count, const
   }
 }
 
+// Per-warp stack of full tissue chunks (data and chunk index).
+__device__ __forceinline__ void stack_put(uint4* stk, unsigned* stq, int slot,
+                                          const unsigned (&w)[12], unsigned qi) {
+  uint4* d = stk + 3 * slot;
+  d[0] = make_uint4(w[0], w[1], w[2], w[3]);
+  d[1] = make_uint4(w[4], w[5], w[6], w[7]);
+  d[2] = make_uint4(w[8], w[9], w[10], w[11]);
+  stq[slot] = qi;
+}
+__device__ __forceinline__ void stack_get(const uint4* stk, const unsigned* stq, int slot,
+                                          unsigned (&w)[12], unsigned& qi) {
+  const uint4* d = stk + 3 * slot;
+  const uint4 a = d[0], b = d[1], c = d[2];
+  w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+  w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
+  w[8] = c.x; w[9] = c.y; w[10] = c.z; w[11] = c.w;
+  qi = stq[slot];
+}
+
+// Window arithmetic of one full chunk per lane (lanes with have = false take
+// no part), then the hit queue: called by the whole warp.
+__device__ __forceinline__ void pass1_chunk(const unsigned (&w)[12], unsigned qi, bool have,
+                                            const char* lut, unsigned lr, f2 NR1, f2 NR2,
+                                            const Lasso& L, const WindowConst& C,
+                                            const Geometry& g, uint2* s_queue,
+                                            unsigned* s_coarse, int& qn, f2& c_nw, f2& c_b0,
+                                            f2& c_b1) {
+  unsigned packed = 0u;
+  if (have) {
+    f2 mask;
+    window_chunk(w, lut, lr, NR1, NR2, L.kappa, C, c_nw, c_b0, c_b1, mask);
+    packed = (unsigned)lo_of(mask) | ((unsigned)hi_of(mask) << 16);
+  }
+  const bool hit = packed != 0u;
+  const unsigned ball = __ballot_sync(0xFFFFFFFFu, hit);
+  const unsigned lane = threadIdx.x & 31u;
+  if (hit) s_queue[qn + __popc(ball & ((1u << lane) - 1u))] = make_uint2(qi, packed);
+  qn += __popc(ball);
+  if (qn >= 32) {
+    __syncwarp();
+    drain_queue(s_queue, qn, g, lut, lr, L, C, s_coarse);
+    __syncwarp();
+    qn = 0;
+  }
+}
+
+// A row's last chunk when it holds fewer than 16 pixels: pixel by pixel with
+// the same keys as the vector path, counting only the pixels that exist (the
+// padding bytes are not pixels, whatever the white threshold).  The bytes are
+// read again (L1 hits) so that no register array is indexed at run time.
+__device__ __forceinline__ void partial_chunk(const uint8_t* src, int n, const char* lut,
+                                              unsigned lr, const Lasso& L, const WindowConst& C,
+                                              unsigned* s_coarse, f2& c_nw, f2& c_b0, f2& c_b1) {
+  const float lof0 = __uint_as_float(C.lo0), lof1 = __uint_as_float(C.lo1);
+  float nw = 0.f, b0 = 0.f, b1 = 0.f;
+#pragma unroll 1
+  for (int k = 0; k < n; ++k) {
+    const unsigned aR = ((unsigned)__ldg(src + 3 * k) << 8) | lr;
+    const unsigned aG = ((unsigned)__ldg(src + 3 * k + 1) << 8) | lr;
+    const unsigned aB = ((unsigned)__ldg(src + 3 * k + 2) << 8) | lr;
+    if (min(min(aR, aG), aB) >= C.wthr) continue;   // white
+    float h1, h2;
+    solve_one(lut, aR, aG, aB, L, h1, h2);
+    nw += 1.f;
+    b0 += h1 < lof0 ? 1.f : 0.f;   // [h~ < lo], as the saturated FMA tests
+    b1 += h2 < lof1 ? 1.f : 0.f;
+    window_hit(C, s_coarse, __float_as_uint(h1) - C.lo0, __float_as_uint(h2) - C.lo1);
+  }
+  c_nw = add2(c_nw, pk(nw, 0.f));
+  c_b0 = add2(c_b0, pk(b0, 0.f));
+  c_b1 = add2(c_b1, pk(b1, 0.f));
+}
+
+// Conservative all-white test of a full chunk: every byte has the top bits
+// of wm set, which puts it above the white threshold (no padding in a full
+// chunk).  Such chunks add nothing to any count of pass 1.
+__device__ __forceinline__ bool chunk_white(const unsigned (&w)[12], unsigned wm, unsigned we) {
+  unsigned acc = w[0];
+#pragma unroll
+  for (int i = 1; i < 12; ++i) acc &= w[i];
+  return (acc & wm) == we;
+}
+
 // DEV: the window is read from device memory (computed there); otherwise it
 // is a kernel parameter, which the pixel loop uses without holding it in
 // registers.
+//
+// Each warp loads 32 chunks at a time; all-white chunks are dropped and the
+// others wait on a per-warp stack (at most 31 deep, in shared memory) until
+// a full warp of them is ready: lanes holding a tissue chunk take their own,
+// the others pop one from the stack, so the window arithmetic runs on full
+// warps of tissue.
 template <bool DEV>
 __global__ void __launch_bounds__(kPassThreads, 1) k_pass_window(WindowArgs a) {
   extern __shared__ __align__(16) char s_dyn[];
   unsigned* s_coarse = reinterpret_cast<unsigned*>(s_dyn + kLutSmemBytes);
-  uint2* s_queue = reinterpret_cast<uint2*>(s_dyn + kLutSmemBytes + 2 * kWinGroups * sizeof(unsigned)) +
-                   (threadIdx.x >> 5) * kWarpQueue;      // this warp's queue
+  char* s_after = s_dyn + kLutSmemBytes + 2 * kWinGroups * sizeof(unsigned);
+  uint2* s_queue = reinterpret_cast<uint2*>(s_after) + (threadIdx.x >> 5) * kWarpQueue;  // this warp's queue
+  s_after += sizeof(uint2) * kWarpQueue * (kPassThreads / 32);
+  uint4* s_stk = reinterpret_cast<uint4*>(s_after) + (threadIdx.x >> 5) * (3 * kChunkStack);
+  s_after += sizeof(uint4) * 3 * kChunkStack * (kPassThreads / 32);
+  unsigned* s_stq = reinterpret_cast<unsigned*>(s_after) + (threadIdx.x >> 5) * kChunkStack;
   __shared__ u64 s_tmp[33];
   __shared__ unsigned s_ticket;
   for (int i = threadIdx.x; i < 2 * kWinGroups; i += blockDim.x) s_coarse[i] = 0u;
@@ -263,33 +357,49 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_window(WindowArgs a) {
   const Geometry g = a.g;
   const u64 stride = (u64)gridDim.x * blockDim.x;
   const unsigned lane = threadIdx.x & 31u;
-  int qn = 0;   // entries in this warp's queue (warp-uniform)
+  const unsigned lt = (1u << lane) - 1u;
+  const unsigned wm = a.wm, we = a.we;
+  int qn = 0;   // entries in this warp's hit queue (warp-uniform)
+  int ns = 0;   // tissue chunks on this warp's stack (warp-uniform)
   // every lane of a warp runs the same number of iterations (warp-uniform
-  // loop), so the queue bookkeeping needs only warp-level operations
+  // loop), so the queue and stack bookkeeping needs only warp-level operations
   for (u64 base = (u64)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < g.nchunks;
        base += stride) {
     const u64 q = base + lane;
-    bool hit = false;
-    unsigned packed = 0u;
+    unsigned w[12];
+    unsigned qi = (unsigned)q;
+    bool tissue = false;
     if (q < g.nchunks) {
       const ChunkPos p = chunk_pos(g, q);
-      unsigned w[12];
       load_chunk<false>(g, p, w);
-      f2 mask;
-      window_chunk(w, lut, lr, NR1, NR2, L.kappa, C, c_nw, c_b0, c_b1, mask);
-      const unsigned mA = (unsigned)lo_of(mask), mB = (unsigned)hi_of(mask);
-      packed = mA | (mB << 16);
-      hit = packed != 0u;
+      if (p.n == kChunk)
+        tissue = !chunk_white(w, wm, we);
+      else
+        partial_chunk(g.src + p.src_off, p.n, lut, lr, L, C, s_coarse, c_nw, c_b0, c_b1);
     }
-    const unsigned ball = __ballot_sync(0xFFFFFFFFu, hit);
-    if (hit) s_queue[qn + __popc(ball & ((1u << lane) - 1u))] = make_uint2((unsigned)q, packed);
-    qn += __popc(ball);
-    if (qn >= 32 || base + stride >= g.nchunks) {
-      __syncwarp();
-      drain_queue(s_queue, qn, g, lut, lr, L, C, s_coarse);
-      __syncwarp();
-      qn = 0;
+    const unsigned ball = __ballot_sync(0xFFFFFFFFu, tissue);
+    const int cnt = __popc(ball);
+    __syncwarp();   // the stack's previous reads and writes are done
+    if (ns + cnt < 32) {   // not a full warp yet: stack them
+      if (tissue) stack_put(s_stk, s_stq, ns + __popc(ball & lt), w, qi);
+      ns += cnt;
+      continue;
     }
+    if (!tissue) stack_get(s_stk, s_stq, ns - 1 - __popc(~ball & lt), w, qi);
+    ns -= 32 - cnt;
+    pass1_chunk(w, qi, true, lut, lr, NR1, NR2, L, C, g, s_queue, s_coarse, qn, c_nw, c_b0, c_b1);
+  }
+  __syncwarp();
+  if (ns > 0) {   // the rest of the stack (fewer than 32)
+    const bool have = lane < (unsigned)ns;
+    unsigned w[12];
+    unsigned qi = 0u;
+    if (have) stack_get(s_stk, s_stq, (int)lane, w, qi);
+    pass1_chunk(w, qi, have, lut, lr, NR1, NR2, L, C, g, s_queue, s_coarse, qn, c_nw, c_b0, c_b1);
+  }
+  if (qn > 0) {
+    __syncwarp();
+    drain_queue(s_queue, qn, g, lut, lr, L, C, s_coarse);
   }
   // per-thread counts are exact in FP32 (fewer than 2^24 pixels per thread)
   const u64 t_nw = block_sum((u64)lo_of(c_nw) + (u64)hi_of(c_nw), s_tmp);
@@ -527,6 +637,22 @@ int launch_window_from_basis(Context* c, const Model* m, const SelectState* samp
   return SPCN_OK;
 }
 
+// Constants of the conservative all-white test of a full chunk: every byte
+// has its top k bits set, with k the smallest for which that puts a byte
+// above the threshold T (256 - 2^(8-k) > T).  With T = 255 nothing is white
+// and the test never passes (mask 0, expected 1).
+void white_test_consts(int T, unsigned* wm, unsigned* we) {
+  *wm = 0u;
+  *we = 1u;
+  for (int k = 1; k <= 8; ++k) {
+    if (256 - (1 << (8 - k)) > T) {
+      const unsigned byte = (0xFFu << (8 - k)) & 0xFFu;
+      *wm = *we = byte * 0x01010101u;
+      return;
+    }
+  }
+}
+
 // Pass 1 + select (+ radix fallback when a rank fell outside the window).
 // The window comes from a host hint, or (wdev) from device memory.
 static int percentile_passes(Context* c, const Geometry& g, const Model* m, int white_thresh,
@@ -540,6 +666,7 @@ static int percentile_passes(Context* c, const Geometry& g, const Model* m, int 
   a.coarse = c->coarse;
   a.err = c->err;
   a.wthr = ((unsigned)white_thresh + 1u) << 8;
+  white_test_consts(white_thresh, &a.wm, &a.we);
   a.w = w;
   a.wdev = wdev;
   a.pct = pct;

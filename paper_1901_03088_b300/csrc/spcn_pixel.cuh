@@ -535,6 +535,9 @@ __host__ __device__ inline Window window_for(double hint0, double hint1) {
 // Host launchers that take a window (spcn_pixel.cu).
 int launch_window_from_basis(Context* c, const Model* m, const SelectState* sample_sel,
                              const int* basis_status, Window* w, cudaStream_t st);
+// Constants (wm, we) of the conservative all-white test of a full chunk of
+// pass 1: the AND of its twelve words, masked by wm, equals we.
+void white_test_consts(int white_thresh, unsigned* wm, unsigned* we);
 int launch_percentile_passes_dev(Context* c, const Geometry& g, const Model* m, int white_thresh,
                                  double pct, const Window* wdev, const double* tgt_p99,
                                  cudaStream_t st);
