@@ -442,6 +442,36 @@ __device__ __forceinline__ void open_window_chunk(const unsigned (&w)[12], const
   }
 }
 
+// open_window_chunk for a row's last chunk with fewer than 16 pixels, pixel
+// by pixel (the same tests; the padding bytes are not pixels): the counts,
+// and the mask in the same base-4 layout for the hit queue.
+__device__ __forceinline__ unsigned open_window_partial(const uint8_t* src, int n, const char* lut,
+                                                        unsigned lr, const Lasso& L, unsigned wthr,
+                                                        float nk0, float lk0, float nk1, float lk1,
+                                                        f2& c_nw, f2& c_b0, f2& c_b1) {
+  float nw = 0.f, b0 = 0.f, b1 = 0.f;
+  unsigned mA = 0u, mB = 0u;
+#pragma unroll 1
+  for (int k = 0; k < n; ++k) {
+    const unsigned aR = ((unsigned)__ldg(src + 3 * k) << 8) | lr;
+    const unsigned aG = ((unsigned)__ldg(src + 3 * k + 1) << 8) | lr;
+    const unsigned aB = ((unsigned)__ldg(src + 3 * k + 2) << 8) | lr;
+    if (min(min(aR, aG), aB) >= wthr) continue;   // white
+    float h1, h2;
+    solve_one(lut, aR, aG, aB, L, h1, h2);
+    const float B0 = fma_sat(h1, nk0, lk0), B1 = fma_sat(h2, nk1, lk1);
+    nw += 1.f;
+    b0 += B0;
+    b1 += B1;
+    const unsigned d = (unsigned)(2.f - B0 - B1) << (2 * (7 - (k >> 1)));
+    if (k & 1) mB |= d; else mA |= d;
+  }
+  c_nw = add2(c_nw, pk(nw, 0.f));
+  c_b0 = add2(c_b0, pk(b0, 0.f));
+  c_b1 = add2(c_b1, pk(b1, 0.f));
+  return mA | (mB << 16);
+}
+
 __device__ __forceinline__ ReconConst recon_const(const float* s_M, const float* l2i0) {
   ReconConst K;
 #pragma unroll
@@ -489,18 +519,22 @@ __device__ __forceinline__ unsigned batch_pass1(const BatchArgs& a, unsigned til
     const u64 base = c0 + 32ull * __shfl_sync(0xFFFFFFFFu, piece, 0);
     if (base >= c1) break;
     const u64 q = base + lane;
-    bool hit = false;
     unsigned packed = 0u;
     if (q < c1) {
       const ChunkPos p = chunk_pos(g, q);
       unsigned w[12];
       load_chunk<false>(g, p, w);
-      f2 mask;
-      open_window_chunk(w, lut, lr, NR1, NR2, L.kappa, a.wthr, nk0, lk0, nk1, lk1, c_nw, c_b0,
-                        c_b1, mask);
-      packed = (unsigned)lo_of(mask) | ((unsigned)hi_of(mask) << 16);
-      hit = packed != 0u;
+      if (p.n == kChunk) {
+        f2 mask;
+        open_window_chunk(w, lut, lr, NR1, NR2, L.kappa, a.wthr, nk0, lk0, nk1, lk1, c_nw, c_b0,
+                          c_b1, mask);
+        packed = (unsigned)lo_of(mask) | ((unsigned)hi_of(mask) << 16);
+      } else {
+        packed = open_window_partial(g.src + p.src_off, p.n, lut, lr, L, a.wthr, nk0, lk0, nk1,
+                                     lk1, c_nw, c_b0, c_b1);
+      }
     }
+    const bool hit = packed != 0u;
     const unsigned ball = __ballot_sync(0xFFFFFFFFu, hit);
     if (hit) s_queue[qn + __popc(ball & ((1u << lane) - 1u))] = make_uint2((unsigned)(q - c0), packed);
     qn += __popc(ball);

@@ -236,25 +236,6 @@ __device__ __forceinline__ void drain_queue(const uint2* queue, int count, const
   }
 }
 
-// Per-warp stack of full tissue chunks (data and chunk index).
-__device__ __forceinline__ void stack_put(uint4* stk, unsigned* stq, int slot,
-                                          const unsigned (&w)[12], unsigned qi) {
-  uint4* d = stk + 3 * slot;
-  d[0] = make_uint4(w[0], w[1], w[2], w[3]);
-  d[1] = make_uint4(w[4], w[5], w[6], w[7]);
-  d[2] = make_uint4(w[8], w[9], w[10], w[11]);
-  stq[slot] = qi;
-}
-__device__ __forceinline__ void stack_get(const uint4* stk, const unsigned* stq, int slot,
-                                          unsigned (&w)[12], unsigned& qi) {
-  const uint4* d = stk + 3 * slot;
-  const uint4 a = d[0], b = d[1], c = d[2];
-  w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
-  w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
-  w[8] = c.x; w[9] = c.y; w[10] = c.z; w[11] = c.w;
-  qi = stq[slot];
-}
-
 // Window arithmetic of one full chunk per lane (lanes with have = false take
 // no part), then the hit queue: called by the whole warp.
 __device__ __forceinline__ void pass1_chunk(const unsigned (&w)[12], unsigned qi, bool have,
@@ -289,7 +270,6 @@ __device__ __forceinline__ void pass1_chunk(const unsigned (&w)[12], unsigned qi
 __device__ __forceinline__ void partial_chunk(const uint8_t* src, int n, const char* lut,
                                               unsigned lr, const Lasso& L, const WindowConst& C,
                                               unsigned* s_coarse, f2& c_nw, f2& c_b0, f2& c_b1) {
-  const float lof0 = __uint_as_float(C.lo0), lof1 = __uint_as_float(C.lo1);
   float nw = 0.f, b0 = 0.f, b1 = 0.f;
 #pragma unroll 1
   for (int k = 0; k < n; ++k) {
@@ -300,23 +280,13 @@ __device__ __forceinline__ void partial_chunk(const uint8_t* src, int n, const c
     float h1, h2;
     solve_one(lut, aR, aG, aB, L, h1, h2);
     nw += 1.f;
-    b0 += h1 < lof0 ? 1.f : 0.f;   // [h~ < lo], as the saturated FMA tests
-    b1 += h2 < lof1 ? 1.f : 0.f;
+    b0 += fma_sat(h1, C.nk0, C.lk0);   // [h~ < lo], the vector path's test
+    b1 += fma_sat(h2, C.nk1, C.lk1);
     window_hit(C, s_coarse, __float_as_uint(h1) - C.lo0, __float_as_uint(h2) - C.lo1);
   }
   c_nw = add2(c_nw, pk(nw, 0.f));
   c_b0 = add2(c_b0, pk(b0, 0.f));
   c_b1 = add2(c_b1, pk(b1, 0.f));
-}
-
-// Conservative all-white test of a full chunk: every byte has the top bits
-// of wm set, which puts it above the white threshold (no padding in a full
-// chunk).  Such chunks add nothing to any count of pass 1.
-__device__ __forceinline__ bool chunk_white(const unsigned (&w)[12], unsigned wm, unsigned we) {
-  unsigned acc = w[0];
-#pragma unroll
-  for (int i = 1; i < 12; ++i) acc &= w[i];
-  return (acc & wm) == we;
 }
 
 // DEV: the window is read from device memory (computed there); otherwise it

@@ -226,6 +226,35 @@ __device__ __forceinline__ void window_chunk(const unsigned (&w)[12], const char
   }
 }
 
+// Per-warp stack of full tissue chunks (data and chunk index).
+__device__ __forceinline__ void stack_put(uint4* stk, unsigned* stq, int slot,
+                                          const unsigned (&w)[12], unsigned qi) {
+  uint4* d = stk + 3 * slot;
+  d[0] = make_uint4(w[0], w[1], w[2], w[3]);
+  d[1] = make_uint4(w[4], w[5], w[6], w[7]);
+  d[2] = make_uint4(w[8], w[9], w[10], w[11]);
+  stq[slot] = qi;
+}
+__device__ __forceinline__ void stack_get(const uint4* stk, const unsigned* stq, int slot,
+                                          unsigned (&w)[12], unsigned& qi) {
+  const uint4* d = stk + 3 * slot;
+  const uint4 a = d[0], b = d[1], c = d[2];
+  w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+  w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
+  w[8] = c.x; w[9] = c.y; w[10] = c.z; w[11] = c.w;
+  qi = stq[slot];
+}
+
+// Conservative all-white test of a full chunk: every byte has the top bits
+// of wm set, which puts it above the white threshold (no padding in a full
+// chunk).  Such chunks add nothing to any count of pass 1.
+__device__ __forceinline__ bool chunk_white(const unsigned (&w)[12], unsigned wm, unsigned we) {
+  unsigned acc = w[0];
+#pragma unroll
+  for (int i = 1; i < 12; ++i) acc &= w[i];
+  return (acc & wm) == we;
+}
+
 constexpr int kWarpQueue = 64;    // queued chunks per warp; drained once 32 are waiting, so the
                                   // re-read chunks are recent enough to still be in L2
 

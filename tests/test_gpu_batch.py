@@ -225,3 +225,35 @@ def test_batch_rejects_overlapping_output(spcn, ctx, setup):
     with pytest.raises(spcn.SpcnError) as e:
         spcn.normalize_batched(ctx, [tiles[3]], [stats[3]], tgt, [tiles[3]], p)
     assert e.value.kind == "INVALID_ARG"
+
+
+@pytest.mark.parametrize("thresh", [220, 255])
+def test_batch_white_regions(spcn, ctx, setup, thresh):
+    """Tiles with large white regions (blob background plus painted white
+    rectangles) and ragged widths: pass 1 drops all-white chunks and counts
+    row-end partial chunks pixel by pixel; at threshold 255 no pixel is white
+    and the padding of partial chunks must not be counted.  Bit-identical to
+    the single-image path."""
+    _, slide_stats, tgt, _ = setup
+    sizes = [(700, 999), (333, 1201), (1024, 1024), (45, 2000), (1500, 17), (600, 641)]
+    g = torch.Generator(device="cpu")
+    g.manual_seed(11)
+    tiles = []
+    for k, (h, w) in enumerate(sizes):
+        t = synth.make_image_torch(h, w, 5000 + k, W=synth.stain_basis(2000 + k % 4),
+                                   device="cuda", blobs=min(h, w) >= 256)
+        for _ in range(6):
+            rh = int(torch.randint(1, h, (1,), generator=g))
+            rw = int(torch.randint(1, w, (1,), generator=g))
+            y = int(torch.randint(0, h - rh + 1, (1,), generator=g))
+            x = int(torch.randint(0, w - rw + 1, (1,), generator=g))
+            t[y:y + rh, x:x + rw] = torch.randint(236, 256, (rh, rw, 3), generator=g,
+                                                  dtype=torch.int32).to(torch.uint8).cuda()
+        tiles.append(t)
+    stats = [slide_stats[k % 4] for k in range(len(tiles))]
+    p = spcn.params(white_thresh=thresh)
+    ref_outs, ref_p99 = sequential(ctx, tiles, stats, tgt, p)
+    outs = [torch.empty_like(t) for t in tiles]
+    p99, status = spcn.normalize_batched(ctx, tiles, stats, tgt, outs, p)
+    assert status == [0] * len(tiles)
+    assert_same(outs, ref_outs, p99, ref_p99)
