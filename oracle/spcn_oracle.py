@@ -51,6 +51,22 @@ R10 Output rounding is round-half-even, clamped to [0, 255].
 R11 Random choices use SplitMix64 outputs (Steele, Lea & Flood 2014) mapped
     to [0, n) by the multiply-high range reduction (Lemire 2019).
 
+Variants of the paper's own earlier choices, each off by default (Params):
+
+i0_fixed_255      §2.1 Eq. 1: i0 = 255 for every channel (the original method)
+                  instead of §3.1 item 1's estimate.
+order="blue"      §3.1 item 3's original heuristic, read as: hematoxylin is the
+                  column with the larger blue optical density (R14).
+p99_patch_median  §3.2 item 4: the reported P99 is, per stain, the median over
+                  the kept patches of each patch's non-white P99 (patches
+                  sampling only).
+h_solve="pinv"    §2.1: H = pinv(W) v (unconstrained, may be negative) for the
+                  densities that are scaled and reconstructed; the basis itself
+                  is still learnt with Eq. 2.
+Normalising with the P99 that ``estimate_basis`` reports (§3.1 item 2's
+sub-sampled percentile) instead of the exact one is ``normalize`` called with
+those statistics.
+
 Parity pins (tests/test_oracle.py): OD(i0) = 0; KKT conditions of every lasso
 solution; brute-force enumeration on a grid; soft-threshold closed form for
 orthogonal W; lambda = 0 against scipy's NNLS; identity reconstruction;
@@ -106,6 +122,10 @@ class Params:
     max_iter: int = 200
     tol: float = 1e-6
     seed: int = 0
+    i0_fixed_255: bool = False
+    order: str = "red_blue"       # "red_blue" (§3.1 item 3) | "blue" (original)
+    p99_patch_median: bool = False
+    h_solve: str = "lasso"        # "lasso" (Eq. 2) | "pinv" (§2.1)
 
 
 @dataclass
@@ -243,25 +263,35 @@ def select_sample(img: np.ndarray, params: Params) -> np.ndarray:
         idx = rand_below(params.seed, np.arange(m, dtype=np.uint64), n).astype(np.int64)
         return flat[idx]
     if mode == "patches":
-        P = params.patch_size
-        x0, y0 = patch_origins(w, h, params)
-        kept = []
-        for k in range(x0.size):
-            patch = img[y0[k]:y0[k] + P, x0[k]:x0[k] + P]
-            nw = int(np.count_nonzero(nonwhite_mask(patch, params.white_thresh)))
-            if 2 * nw >= P * P:
-                kept.append(patch.reshape(-1, 3))
-                if len(kept) == params.n_patches:
-                    break
-        if not kept:
-            raise SpcnError("NO_TISSUE", "no patch is at least half non-white")
-        return np.concatenate(kept, axis=0)
+        return np.concatenate(select_patches(img, params), axis=0)
     raise SpcnError("INVALID_ARG", f"unknown sample mode {mode!r}")
+
+
+def select_patches(img: np.ndarray, params: Params) -> list:
+    """The kept patches of the ``patches`` sample, each P*P x 3 in raster
+    order, in candidate order."""
+    h, w, _ = img.shape
+    P = params.patch_size
+    x0, y0 = patch_origins(w, h, params)
+    kept = []
+    for k in range(x0.size):
+        patch = img[y0[k]:y0[k] + P, x0[k]:x0[k] + P]
+        nw = int(np.count_nonzero(nonwhite_mask(patch, params.white_thresh)))
+        if 2 * nw >= P * P:
+            kept.append(patch.reshape(-1, 3))
+            if len(kept) == params.n_patches:
+                break
+    if not kept:
+        raise SpcnError("NO_TISSUE", "no patch is at least half non-white")
+    return kept
 
 
 def estimate_i0(sample: np.ndarray, params: Params) -> np.ndarray:
     """§3.1 item 1: per channel, the 80th percentile of at most 100,000 sample
-    pixels brighter than the threshold (reading R9 for the cap)."""
+    pixels brighter than the threshold (reading R9 for the cap).  With
+    ``i0_fixed_255``, §2.1's original i0 = 255."""
+    if params.i0_fixed_255:
+        return np.full(3, 255.0)
     bright = sample[bright_mask(sample, params.white_thresh)]
     nb = bright.shape[0]
     if nb == 0:
@@ -321,6 +351,23 @@ def lasso2(V: np.ndarray, W: np.ndarray, lam: float) -> np.ndarray:
     return H
 
 
+def pinv_densities(V: np.ndarray, W: np.ndarray) -> np.ndarray:
+    """§2.1: H = pinv(W) V, the least-squares densities without sign or
+    sparsity constraint (2 x n)."""
+    gram(W)
+    return np.linalg.pinv(np.asarray(W, dtype=np.float64)) @ V
+
+
+def solve_h(V: np.ndarray, W: np.ndarray, params: "Params") -> np.ndarray:
+    """The densities that are scaled and reconstructed: Eq. 2's lasso, or the
+    pseudo-inverse variant."""
+    if params.h_solve == "pinv":
+        return pinv_densities(V, W)
+    if params.h_solve != "lasso":
+        raise SpcnError("INVALID_ARG", f"unknown H solve {params.h_solve!r}")
+    return lasso2(V, W, params.lam)
+
+
 def lasso_objective(V: np.ndarray, W: np.ndarray, H: np.ndarray, lam: float) -> float:
     """Eq. 2 with the 1/2 of reading R3."""
     R = V - W @ H
@@ -367,11 +414,18 @@ def snmf(V: np.ndarray, lam: float, max_iter: int, tol: float, W0=None):
     return W, it, objective
 
 
-def order_stains(W: np.ndarray) -> np.ndarray:
+def order_stains(W: np.ndarray, rule: str = "red_blue") -> np.ndarray:
     """§3.1 item 3 (reading R6): column 0 is hematoxylin, the stain whose OD
-    red minus OD blue is larger; ties keep the order."""
-    d0 = W[0, 0] - W[2, 0]
-    d1 = W[0, 1] - W[2, 1]
+    red minus OD blue is larger; ties keep the order.  rule="blue" is the
+    original heuristic the paper replaces (reading R14): the column with the
+    larger blue OD is hematoxylin."""
+    if rule == "red_blue":
+        d0 = W[0, 0] - W[2, 0]
+        d1 = W[0, 1] - W[2, 1]
+    elif rule == "blue":
+        d0, d1 = W[2, 0], W[2, 1]
+    else:
+        raise SpcnError("INVALID_ARG", f"unknown ordering rule {rule!r}")
     return W[:, ::-1].copy() if d1 > d0 else W.copy()
 
 
@@ -380,8 +434,12 @@ def order_stains(W: np.ndarray) -> np.ndarray:
 # --------------------------------------------------------------------------
 def estimate_basis(img: np.ndarray, params: Params | None = None) -> Stats:
     """Sample -> i0 -> OD -> SNMF -> ordering -> P99 of the sampled non-white
-    pixels' densities (§3.1 item 2's sub-sampled percentile)."""
+    pixels' densities (§3.1 item 2's sub-sampled percentile), or with
+    ``p99_patch_median`` the median over the kept patches of each patch's
+    non-white P99 (§3.2 item 4)."""
     params = params or Params()
+    if params.p99_patch_median and params.sample_mode != "patches":
+        raise SpcnError("INVALID_ARG", "the patch median needs patches sampling")
     sample = select_sample(img, params)
     i0 = estimate_i0(sample, params)
     nw = sample[nonwhite_mask(sample, params.white_thresh)]
@@ -389,9 +447,18 @@ def estimate_basis(img: np.ndarray, params: Params | None = None) -> Stats:
         raise SpcnError("NO_TISSUE", "no non-white sample pixel")
     V = optical_density(nw, i0).T                       # 3 x m
     W, iters, obj = snmf(V, params.lam, params.max_iter, params.tol)
-    W = order_stains(W)
-    H = lasso2(V, W, params.lam)
-    p99 = np.array([percentile(H[j], params.stain_pct) for j in range(2)])
+    W = order_stains(W, params.order)
+    if params.p99_patch_median:
+        per_patch = []
+        for patch in select_patches(img, params):
+            pnw = patch[nonwhite_mask(patch, params.white_thresh)]
+            Hp = solve_h(optical_density(pnw, i0).T, W, params)
+            per_patch.append([percentile(Hp[j], params.stain_pct) for j in range(2)])
+        per_patch = np.array(per_patch)
+        p99 = np.array([percentile(per_patch[:, j], 50.0) for j in range(2)])
+    else:
+        H = solve_h(V, W, params)
+        p99 = np.array([percentile(H[j], params.stain_pct) for j in range(2)])
     return Stats(W=W, i0=i0, p99=p99, iters=iters, objective=obj,
                  n_sample=sample.shape[0], n_nonwhite=nw.shape[0],
                  n_bright=int(np.count_nonzero(bright_mask(sample, params.white_thresh))))
@@ -400,10 +467,12 @@ def estimate_basis(img: np.ndarray, params: Params | None = None) -> Stats:
 # --------------------------------------------------------------------------
 # Full-image stain densities and their percentile
 # --------------------------------------------------------------------------
-def stain_densities(img: np.ndarray, W, i0, lam: float = LAMBDA) -> np.ndarray:
+def stain_densities(img: np.ndarray, W, i0, lam: float = LAMBDA,
+                    h_solve: str = "lasso") -> np.ndarray:
     """H (2 x N, raster order) of every pixel for a given basis and i0."""
     V = optical_density(img.reshape(-1, 3), i0).T
-    return lasso2(V, np.asarray(W, dtype=np.float64), lam)
+    W = np.asarray(W, dtype=np.float64)
+    return pinv_densities(V, W) if h_solve == "pinv" else lasso2(V, W, lam)
 
 
 def stain_percentile(img: np.ndarray, W, i0, params: Params | None = None,
@@ -412,7 +481,7 @@ def stain_percentile(img: np.ndarray, W, i0, params: Params | None = None,
     image (§3.1 item 2; reading R7)."""
     params = params or Params()
     if H is None:
-        H = stain_densities(img, W, i0, params.lam)
+        H = stain_densities(img, W, i0, params.lam, params.h_solve)
     nw = nonwhite_mask(img.reshape(-1, 3), params.white_thresh)
     if not np.any(nw):
         raise SpcnError("NO_TISSUE", "no non-white pixel")
@@ -430,10 +499,10 @@ def stain_scale(p99_src, p99_tgt) -> np.ndarray:
 
 
 def normalize_float(img: np.ndarray, src_W, src_i0, src_p99, tgt_W, tgt_i0,
-                    tgt_p99, lam: float = LAMBDA) -> np.ndarray:
+                    tgt_p99, lam: float = LAMBDA, h_solve: str = "lasso") -> np.ndarray:
     """Eq. 3 then Eq. 4 (reading R8) for every pixel; H x W x 3 float64."""
     h, w, _ = img.shape
-    H = stain_densities(img, src_W, src_i0, lam)
+    H = stain_densities(img, src_W, src_i0, lam, h_solve)
     s = stain_scale(src_p99, tgt_p99)
     Vn = np.asarray(tgt_W, dtype=np.float64) @ (s[:, None] * H)   # 3 x N
     I = np.asarray(tgt_i0, dtype=np.float64)[:, None] * np.exp(-Vn)
@@ -445,11 +514,14 @@ def to_uint8(I: np.ndarray) -> np.ndarray:
     return np.clip(np.rint(I), 0, 255).astype(np.uint8)
 
 
-def normalize(img: np.ndarray, src: Stats, tgt: Stats, lam: float = LAMBDA) -> np.ndarray:
-    """The full per-pixel path on a uint8 image with the source's exact P99
-    (src.p99 must hold it) and the target's statistics."""
+def normalize(img: np.ndarray, src: Stats, tgt: Stats, lam: float = LAMBDA,
+              h_solve: str = "lasso") -> np.ndarray:
+    """The full per-pixel path on a uint8 image with the source's P99 as
+    src.p99 holds it (the exact one for the method; the sampled one of
+    ``estimate_basis`` for the one-pass variant) and the target's
+    statistics."""
     return to_uint8(normalize_float(img, src.W, src.i0, src.p99,
-                                    tgt.W, tgt.i0, tgt.p99, lam))
+                                    tgt.W, tgt.i0, tgt.p99, lam, h_solve))
 
 
 def full_stats(img: np.ndarray, params: Params | None = None) -> Stats:

@@ -405,3 +405,98 @@ def test_normalize_grad_zero_where_od_is_clamped():
     X[:, :10] = 0.5                     # below Eq. 1's clamp at 1
     GX, _ = O.normalize_grad(X, GY, Ws, i0s, s, Wt, i0t)
     assert np.all(GX[:, :10] == 0.0)
+
+
+# ---------------------------------------------------------------- variants (paper-faithful flags)
+def test_order_blue_rule_agrees_on_classic_he_and_fails_on_blue_eosin():
+    """§3.1 item 3: the original heuristic (hematoxylin = larger blue OD,
+    reading R14) orders the Ruifrok H&E vectors correctly, and swaps the
+    stains when the eosin-like column carries the larger blue OD -- the
+    failure the red-minus-blue rule was introduced for."""
+    W = O.ruifrok_init()
+    for Win in (W, W[:, ::-1]):
+        assert np.array_equal(O.order_stains(Win, "blue"), W)
+        assert np.array_equal(O.order_stains(Win, "red_blue"), W)
+    hema = np.array([0.75, 0.45, 0.49]); hema /= np.linalg.norm(hema)
+    eosin = np.array([0.10, 0.80, 0.59]); eosin /= np.linalg.norm(eosin)
+    Wo = O.order_stains(np.column_stack([hema, eosin]), "blue")
+    assert np.allclose(Wo[:, 0], eosin) and np.allclose(Wo[:, 1], hema)
+
+
+def test_i0_255_equals_default_when_no_pixel_is_bright():
+    """With no pixel above the threshold the default estimate is i0 = 255
+    (reading R9), so the i0 = 255 variant must give identical statistics;
+    on an image with bright pixels it differs only through i0."""
+    img = synth.make_image(48, 48, 1201, background=0.0)
+    img = np.minimum(img, 200).astype(np.uint8)
+    a = O.estimate_basis(img, O.Params())
+    b = O.estimate_basis(img, O.Params(i0_fixed_255=True))
+    assert np.array_equal(a.i0, [255.0, 255.0, 255.0])
+    assert np.array_equal(a.W, b.W) and np.array_equal(a.p99, b.p99) and a.iters == b.iters
+    img2 = synth.make_image(64, 64, 1202, white=(240.0, 235.0, 245.0))
+    c = O.estimate_basis(img2, O.Params(i0_fixed_255=True))
+    d = O.estimate_basis(img2, O.Params())
+    assert np.array_equal(c.i0, [255.0, 255.0, 255.0]) and np.all(d.i0 < 250.0)
+
+
+def test_patch_median_single_patch_is_the_sampled_percentile():
+    """§3.2 item 4 with one patch: the median of one per-patch P99 is that
+    patch's P99, i.e. the plain sampled P99 of a one-patch sample."""
+    img = synth.make_image(300, 400, 1203, blobs=True)
+    p = dict(sample_mode="patches", n_patches=1, patch_size=64, seed=5)
+    a = O.estimate_basis(img, O.Params(**p))
+    b = O.estimate_basis(img, O.Params(p99_patch_median=True, **p))
+    assert np.array_equal(a.W, b.W)
+    assert np.allclose(a.p99, b.p99, rtol=0, atol=0)
+
+
+def test_patch_median_is_the_middle_patch_value():
+    """Three kept patches: the reported value is, per stain, one of the three
+    per-patch P99s, with one at or below it and one at or above it."""
+    img = synth.make_image(300, 400, 1204, blobs=True)
+    p = O.Params(sample_mode="patches", n_patches=3, patch_size=48, seed=6, p99_patch_median=True)
+    st = O.estimate_basis(img, p)
+    per = []
+    for patch in O.select_patches(img, p):
+        nw = patch[O.nonwhite_mask(patch)]
+        H = O.lasso2(O.optical_density(nw, st.i0).T, st.W, p.lam)
+        per.append([np.percentile(H[j], 99.0) for j in range(2)])
+    per = np.array(per)
+    assert per.shape == (3, 2)
+    for j in range(2):
+        assert np.min(np.abs(per[:, j] - st.p99[j])) <= 1e-12 * max(1.0, st.p99[j])
+        assert np.sum(per[:, j] <= st.p99[j] + 1e-15) >= 2
+        assert np.sum(per[:, j] >= st.p99[j] - 1e-15) >= 2
+
+
+def test_patch_median_needs_patch_sampling():
+    img = synth.make_image(64, 64, 1205)
+    with pytest.raises(O.SpcnError):
+        O.estimate_basis(img, O.Params(p99_patch_median=True))
+
+
+def test_pinv_recovers_signed_planted_densities():
+    """§2.1 pseudo-inverse: for v = W h exactly, pinv(W) v = h, negative
+    entries included; it matches the least-squares routine on arbitrary v."""
+    rng = np.random.default_rng(1206)
+    W = synth.stain_basis(1206)
+    H = rng.normal(0.0, 1.0, size=(2, 500))
+    assert np.allclose(O.pinv_densities(W @ H, W), H, atol=1e-12)
+    V = rng.normal(0.3, 0.4, size=(3, 200))
+    ref = np.linalg.lstsq(W, V, rcond=None)[0]
+    assert np.allclose(O.pinv_densities(V, W), ref, atol=1e-12)
+
+
+def test_pinv_identity_normalisation_reproduces_in_span_pixels():
+    """Source = target statistics and pixels in the span of W (noise-free,
+    float): pinv densities reconstruct every pixel exactly (the lasso would
+    shrink them by lambda)."""
+    W = synth.stain_basis(1207)
+    I = synth.make_image(30, 40, 1207, W=W, noise=0.0, as_float=True)
+    inside = np.all(I >= 1.0, axis=-1)
+    i0 = np.full(3, 255.0)
+    p99 = np.array([1.1, 0.9])
+    out = O.normalize_float(I, W, i0, p99, W, i0, p99, h_solve="pinv")
+    assert np.max(np.abs(out - I)[inside]) < 1e-9
+    lasso = O.normalize_float(I, W, i0, p99, W, i0, p99)
+    assert np.max(np.abs(lasso - I)[inside]) > 1.0
