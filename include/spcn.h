@@ -61,6 +61,33 @@ typedef enum {
   SPCN_SAMPLE_PATCHES = 2   /* patches at least half non-white (§3.2 item 2) */
 } spcn_sample_mode;
 
+/* Variants of the method, bits of spcn_params.flags.  With no bit set the
+ * library computes the improved method as the rest of this header describes
+ * it; each bit restores one of the paper's earlier choices (for A/B
+ * comparisons).  Unknown bits are rejected with SPCN_ERR_INVALID_ARG.
+ *
+ * SPCN_FLAG_I0_255: spcn_estimate_basis (and the estimation inside
+ *   spcn_normalize_estimated) sets i0 = 255 for every channel, the original
+ *   method's fixed maximum intensity (§2.1 Eq. 1), instead of the P80 of the
+ *   bright sample pixels (§3.1 item 1).
+ * SPCN_FLAG_ORDER_BLUE: the stains are ordered by the original heuristic
+ *   that §3.1 item 3 replaces: hematoxylin is the column with the larger
+ *   blue optical density (ties keep the learnt order).
+ * SPCN_FLAG_P99_SAMPLED: spcn_normalize and spcn_normalize_estimated scale
+ *   with the source percentile that basis estimation reports (over the
+ *   sub-sampled non-white pixels, §3.1 item 2; or the patch median below)
+ *   instead of the exact whole-image percentile: pass 1 is skipped and the
+ *   step reads and writes each pixel once.  spcn_normalize takes that value
+ *   from src_st->p99 (> 0 where a stain is present; 0 gives scale 1).
+ * SPCN_FLAG_P99_PATCH_MEDIAN: basis estimation reports, per stain, the
+ *   median over the kept patches of each patch's non-white percentile
+ *   (§3.2 item 4) as p99.  Requires SPCN_SAMPLE_PATCHES and n_patches <= 4096.
+ */
+#define SPCN_FLAG_I0_255 0x1u
+#define SPCN_FLAG_ORDER_BLUE 0x2u
+#define SPCN_FLAG_P99_SAMPLED 0x4u
+#define SPCN_FLAG_P99_PATCH_MEDIAN 0x8u
+
 /* An 8-bit interleaved RGB image. */
 typedef struct {
   const uint8_t* data;      /* device pointer to pixel (0,0) */
@@ -82,7 +109,7 @@ typedef struct {
   int32_t patch_size;       /* SPCN_SAMPLE_PATCHES: patch side in pixels */
   int32_t max_iter;         /* dictionary-learning iteration cap (200) */
   float tol;                /* stop when max|dW| < tol (1e-6) */
-  uint32_t flags;           /* reserved, must be 0 */
+  uint32_t flags;           /* SPCN_FLAG_* variants (0: the improved method) */
   uint64_t seed;            /* SplitMix64 seed of the sampling */
 } spcn_params;
 
@@ -120,7 +147,8 @@ int spcn_context_destroy(void* ctx);
  * params->sample_mode, estimate i0 (P80 of <= i0_max_samples bright sample
  * pixels), run the sparse NMF on the sample's non-white pixels, order the
  * stains by OD(red)-OD(blue), and set p99 to the percentile of the sampled
- * non-white pixels' densities.  Writes the host record *out.  Blocks the
+ * non-white pixels' densities (SPCN_FLAG_I0_255, SPCN_FLAG_ORDER_BLUE and
+ * SPCN_FLAG_P99_PATCH_MEDIAN select the paper's earlier choices for these).  Writes the host record *out.  Blocks the
  * host until the stream has finished this call's work.
  * Errors: INVALID_ARG, NO_TISSUE (no non-white sample pixel or patch),
  * DEGENERATE_BASIS, TIMEOUT, CUDA, OOM. */
@@ -129,7 +157,8 @@ int spcn_estimate_basis(void* ctx, const spcn_image* img, const spcn_params* par
 
 /* Exact Eq. 3 percentile (params->stain_pct) of each stain's density over
  * all non-white pixels of `img`, for the basis and i0 in *st (st->p99, if
- * positive, only guides the search window).  Writes p99_out[2] (host).
+ * positive, only guides the search window; SPCN_FLAG_P99_SAMPLED does not
+ * apply to this call).  Writes p99_out[2] (host).
  * Blocks the host.  Errors: INVALID_ARG, NO_TISSUE, DEGENERATE_BASIS,
  * TIMEOUT, CUDA. */
 int spcn_stain_percentile(void* ctx, const spcn_image* img, const spcn_stats* st,
@@ -150,6 +179,8 @@ int spcn_stain_densities(void* ctx, const spcn_image* img, const spcn_stats* st,
  * width/height as src, row pitch out_pitch >= 3*width; must not overlap
  * src).  If src_p99_out (host, 2 doubles) is non-NULL the call blocks and
  * returns the source percentiles there; otherwise it is asynchronous.
+ * With SPCN_FLAG_P99_SAMPLED there is no pass 1: src_st->p99 (finite, >= 0)
+ * is the source percentile.
  * Errors: INVALID_ARG, DEGENERATE_BASIS, CUDA (and, when blocking,
  * NO_TISSUE/TIMEOUT). */
 int spcn_normalize(void* ctx, const spcn_image* src, const spcn_stats* src_st,
@@ -163,8 +194,9 @@ int spcn_normalize(void* ctx, const spcn_image* src, const spcn_stats* src_st,
  * window from the sample percentile) so there is no host round trip between
  * the two.  The output bytes are those of the two calls in sequence.
  * If src_st_out (host) is non-NULL the call blocks and returns the estimated
- * source statistics there, with p99 = the exact percentile of the whole
- * source; otherwise it is asynchronous and errors of the estimation (no
+ * source statistics there, with p99 = the percentile the scale used (the
+ * exact one of the whole source; with SPCN_FLAG_P99_SAMPLED the sample's,
+ * and no pass 1 runs); otherwise it is asynchronous and errors of the estimation (no
  * tissue, degenerate basis) are returned by the next synchronising call.
  * Errors: as spcn_estimate_basis and spcn_normalize. */
 int spcn_normalize_estimated(void* ctx, const spcn_image* src, const spcn_stats* tgt_st,
@@ -259,7 +291,9 @@ typedef struct {
  * not overlap its own source (INVALID_ARG); it must not overlap another
  * tile's source or output either (not checked: results are then undefined).
  * Builds the per-statistics tables (tiles with bitwise-equal W and i0 share
- * one) and allocates the batch state; blocks the host.  Errors: INVALID_ARG,
+ * one) and allocates the batch state; blocks the host.  Every tile's
+ * percentile is measured (SPCN_FLAG_P99_SAMPLED is rejected; the other flags
+ * concern basis estimation and have no effect here).  Errors: INVALID_ARG,
  * DEGENERATE_BASIS, OOM, CUDA. */
 int spcn_batch_create(void* ctx, int32_t n, const spcn_image* tiles,
                       const spcn_stats* tile_stats, const spcn_stats* tgt_st,

@@ -122,7 +122,12 @@ bool params_ok(const spcn_params* p) {
     return false;
   if (p->max_iter < 1 || p->max_iter > 1000000) return false;
   if (!(p->tol >= 0.f) || !std::isfinite(p->tol)) return false;
-  if (p->flags != 0u) return false;
+  const uint32_t known = SPCN_FLAG_I0_255 | SPCN_FLAG_ORDER_BLUE | SPCN_FLAG_P99_SAMPLED |
+                         SPCN_FLAG_P99_PATCH_MEDIAN;
+  if (p->flags & ~known) return false;
+  if ((p->flags & SPCN_FLAG_P99_PATCH_MEDIAN) &&
+      (p->sample_mode != SPCN_SAMPLE_PATCHES || p->n_patches > 4096))
+    return false;
   return true;
 }
 
@@ -348,6 +353,9 @@ int spcn_normalize(void* ctx, const spcn_image* src, const spcn_stats* src_st,
   if (rc) return rc;
   rc = stats_ok(tgt_st);
   if (rc) return rc;
+  if (params->flags & SPCN_FLAG_P99_SAMPLED)
+    for (int j = 0; j < 2; ++j)
+      if (!(src_st->p99[j] >= 0.0) || !std::isfinite(src_st->p99[j])) return SPCN_ERR_INVALID_ARG;
   // out must not overlap the source rows
   {
     const uintptr_t s0 = reinterpret_cast<uintptr_t>(src->data);
@@ -363,9 +371,13 @@ int spcn_normalize(void* ctx, const spcn_image* src, const spcn_stats* src_st,
   const Geometry g = make_geometry(src, out, out_pitch);
   rc = launch_build_model(c, c->model, src_st->W, src_st->i0, params->lambda, nullptr, s);
   if (rc) return rc;
-  rc = launch_percentile_passes(c, g, c->model, params->white_thresh, (double)params->stain_pct,
-                                src_st->p99, host_table_hexp(src_st->W, src_st->i0, params->lambda),
-                                tgt_st->p99, s);
+  if (params->flags & SPCN_FLAG_P99_SAMPLED)   // the given percentile, no pass 1
+    rc = launch_scale_given(c, src_st->p99, tgt_st->p99, s);
+  else
+    rc = launch_percentile_passes(c, g, c->model, params->white_thresh, (double)params->stain_pct,
+                                  src_st->p99,
+                                  host_table_hexp(src_st->W, src_st->i0, params->lambda),
+                                  tgt_st->p99, s);
   if (rc) return rc;
   rc = launch_recon(c, g, c->model, tgt_st->W, tgt_st->i0, s);
   if (rc) return rc;
@@ -466,13 +478,18 @@ int spcn_normalize_estimated(void* ctx, const spcn_image* src, const spcn_stats*
   // the basis estimation's final table (estimated basis and i0, this lambda)
   // is the source table; the window comes from the sample P99
   const Model* m = c->model_b;
-  Window* wdev = static_cast<Window*>(c->wdev);
-  rc = launch_window_from_basis(c, m, &c->bs->sel, &c->bs->status, wdev, s);
-  if (rc) return rc;
   const Geometry g = make_geometry(src, out, out_pitch);
-  rc = launch_percentile_passes_dev(c, g, m, params->white_thresh, (double)params->stain_pct,
-                                    wdev, tgt_st->p99, s);
-  if (rc) return rc;
+  if (params->flags & SPCN_FLAG_P99_SAMPLED) {   // the sample percentile, no pass 1
+    rc = launch_scale_from_basis(c, m, &c->bs->sel, &c->bs->status, tgt_st->p99, s);
+    if (rc) return rc;
+  } else {
+    Window* wdev = static_cast<Window*>(c->wdev);
+    rc = launch_window_from_basis(c, m, &c->bs->sel, &c->bs->status, wdev, s);
+    if (rc) return rc;
+    rc = launch_percentile_passes_dev(c, g, m, params->white_thresh, (double)params->stain_pct,
+                                      wdev, tgt_st->p99, s);
+    if (rc) return rc;
+  }
   rc = launch_recon(c, g, m, tgt_st->W, tgt_st->i0, s);
   if (rc) return rc;
   if (src_st_out) {
@@ -483,7 +500,7 @@ int spcn_normalize_estimated(void* ctx, const spcn_image* src, const spcn_stats*
     int err = 0;
     const int rc2 = read_error(c, s, &err);
     if (rc2) return rc2;
-    src_st_out->p99[0] = p[0];   // the exact percentile of the whole source
+    src_st_out->p99[0] = p[0];   // the percentile the scale used (exact unless sampled)
     src_st_out->p99[1] = p[1];
     src_st_out->status = rc ? rc : err;
     return rc ? rc : err;

@@ -249,6 +249,7 @@ struct I0Args {
   unsigned* ticket;   // zeroed before the launch
   int cap;
   double pct;
+  int fixed255;       // §2.1 Eq. 1's original i0 = 255 instead of the estimate
 };
 
 constexpr int kI0Threads = 256;
@@ -301,7 +302,7 @@ __global__ void __launch_bounds__(kI0Threads) k_i0(I0Args a) {
     unsigned h[256];
     for (int v = 0; v < 256; ++v) h[v] = __ldcg(a.hist + 256 * c + v);
     double val = 255.0;
-    if (kept > 0) {
+    if (kept > 0 && !a.fixed255) {
       const double pos = (double)(kept - 1) * (a.pct / 100.0);
       u64 k = (u64)floor(pos);
       if (k > kept - 1) k = kept - 1;
@@ -338,6 +339,7 @@ struct SnmfArgs {
   int max_iter;
   double tol;
   long long timeout_ns;
+  int order_blue;     // the original ordering heuristic (larger blue OD is hematoxylin)
 };
 
 // Reduced sums, in this order: A11 A12 A22 | B[R,0] B[R,1] B[G,0] B[G,1]
@@ -590,8 +592,10 @@ __global__ void __launch_bounds__(kSnmfThreads) k_snmf(SnmfArgs a) {
       g12 += s_W[c] * s_W[3 + c];
     }
     if (s_flag < 0 || !(g11 * g22 - g12 * g12 > 1e-12)) status = SPCN_ERR_DEGENERATE_BASIS;
-    // §3.1 item 3: hematoxylin is the stain with the larger OD(red) - OD(blue)
-    const double d0 = s_W[0] - s_W[2], d1 = s_W[3] - s_W[5];
+    // §3.1 item 3: hematoxylin is the stain with the larger OD(red) - OD(blue);
+    // the original heuristic compares the blue OD alone
+    const double d0 = a.order_blue ? s_W[2] : s_W[0] - s_W[2];
+    const double d1 = a.order_blue ? s_W[5] : s_W[3] - s_W[5];
     double Wo[6];
     for (int c = 0; c < 3; ++c) {
       Wo[c] = d1 > d0 ? s_W[3 + c] : s_W[c];
@@ -604,6 +608,161 @@ __global__ void __launch_bounds__(kSnmfThreads) k_snmf(SnmfArgs a) {
   }
 }
 
+// ------------------------------------------------------------ median of per-patch percentiles
+// §3.2 item 4 (SPCN_FLAG_P99_PATCH_MEDIAN): for every kept patch the exact
+// type-7 percentile of each stain's density over the patch's non-white
+// pixels, then per stain the median (type-7 50th percentile) of those values
+// over the patches.  The non-white list is the stable compaction of the
+// sample, which holds the kept patches one after another, so patch p's
+// non-white pixels are one segment of it, placed by the candidates' counts.
+constexpr int kPatchSelThreads = 1024;
+constexpr int kPatchSelBins = 2048;   // 11/11/10-bit digits of the FP32 key
+constexpr size_t kPatchSelSmem = kLutSmemBytes + sizeof(unsigned) * 4 * kPatchSelBins;
+constexpr int kMaxMedianPatches = 4096;
+
+struct PatchP99Args {
+  const uint32_t* nw;
+  const int* cand;     // [n_cand] non-white counts, then the accepted candidates
+  int n_cand;
+  const BasisState* bs;
+  const Model* m;
+  double pct;
+  double* per_patch;   // [n_acc][2]
+};
+
+// The bin of a shared 2048-bin histogram that holds rank r (-1 if none) and
+// the count before it.  Whole block.
+__device__ void shared_rank_bin(const unsigned* h, u64 r, int* s_idx, u64* s_before,
+                                u64* s_tmp) {
+  const int per = (kPatchSelBins + (int)blockDim.x - 1) / (int)blockDim.x;
+  const int beg = threadIdx.x * per, end = min(kPatchSelBins, beg + per);
+  u64 local = 0;
+  for (int i = beg; i < end; ++i) local += h[i];
+  u64 total;
+  const u64 excl = block_excl_scan(local, s_tmp, &total);
+  if (threadIdx.x == 0) *s_idx = -1;
+  __syncthreads();
+  if (local > 0 && excl <= r && r < excl + local) {
+    u64 c = excl;
+    for (int i = beg; i < end; ++i) {
+      if (r < c + h[i]) { *s_idx = i; *s_before = c; break; }
+      c += h[i];
+    }
+  }
+  __syncthreads();
+}
+
+// One block per kept patch: radix select (11/11/10-bit digits of the FP32
+// key of the scaled density) of ranks k and k+1 of both stains over the
+// patch's segment of the non-white list.
+__global__ void __launch_bounds__(kPatchSelThreads, 1) k_patch_p99(PatchP99Args a) {
+  extern __shared__ __align__(16) char s_dyn[];
+  unsigned* s_hist = reinterpret_cast<unsigned*>(s_dyn + kLutSmemBytes);   // [4][bins]
+  __shared__ u64 s_tmp[33];
+  __shared__ unsigned s_pre[4];
+  __shared__ u64 s_r[4];
+  __shared__ int s_idx;
+  __shared__ u64 s_before;
+  const int p = blockIdx.x;
+  if (p >= a.bs->n_acc || a.bs->status != SPCN_OK || a.m->status != SPCN_OK) return;   // uniform
+  u64 part = 0;
+  for (int i = threadIdx.x; i < p; i += blockDim.x) part += (u64)a.cand[a.cand[a.n_cand + i]];
+  const u64 off = block_sum(part, s_tmp);
+  const u64 n = (u64)a.cand[a.cand[a.n_cand + p]];   // >= 1: a kept patch is half non-white
+  u64 k, k1;
+  double t;
+  type7_ranks(n, a.pct, &k, &k1, &t);
+  if (threadIdx.x < 4) {
+    s_pre[threadIdx.x] = 0u;
+    s_r[threadIdx.x] = (threadIdx.x & 1) ? k1 : k;
+  }
+  load_lut(a.m, s_dyn);
+  const char* lut = s_dyn;
+  const unsigned lr = lane_reg();
+  const Lasso L = a.m->lasso;
+  const uint32_t* items = a.nw + off;
+  for (int d = 0; d < 3; ++d) {
+    const int shift = d == 0 ? 21 : (d == 1 ? 10 : 0);
+    const int hi = d == 0 ? 32 : (d == 1 ? 21 : 10);
+    const unsigned mask = d == 2 ? 0x3FFu : 0x7FFu;
+    for (int i = threadIdx.x; i < 4 * kPatchSelBins; i += blockDim.x) s_hist[i] = 0u;
+    __syncthreads();
+    unsigned pre[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) pre[q] = s_pre[q];
+    for (u64 i = threadIdx.x; i < n; i += blockDim.x) {
+      const uint32_t v = __ldg(items + i);
+      float h1, h2;
+      solve_one(lut, lut_addr(v, lr, 0), lut_addr(v, lr, 1), lut_addr(v, lr, 2), L, h1, h2);
+      const unsigned key[2] = {__float_as_uint(h1), __float_as_uint(h2)};
+      const unsigned live = __activemask();
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const unsigned kk = key[q >> 1];
+        const bool in = ((u64)kk >> hi) == ((u64)pre[q] >> hi);
+        // warp-aggregated increment: one shared atomic per distinct bin
+        const unsigned bin = in ? ((kk >> shift) & mask) : 0xFFFFFFFFu;
+        const unsigned peers = __match_any_sync(live, bin);
+        if (in && (__ffs(peers) - 1) == (int)(threadIdx.x & 31u))
+          atomicAdd(s_hist + q * kPatchSelBins + bin, (unsigned)__popc(peers));
+      }
+    }
+    __syncthreads();
+    for (int q = 0; q < 4; ++q) {
+      shared_rank_bin(s_hist + q * kPatchSelBins, s_r[q], &s_idx, &s_before, s_tmp);
+      if (threadIdx.x == 0 && s_idx >= 0) {
+        s_pre[q] |= (unsigned)s_idx << shift;
+        s_r[q] -= s_before;
+      }
+      __syncthreads();
+    }
+  }
+  if (threadIdx.x < 2) {
+    const int j = threadIdx.x;
+    a.per_patch[2 * p + j] = interp_type7(__fmul_rn(__uint_as_float(s_pre[2 * j]), L.hscale),
+                                          __fmul_rn(__uint_as_float(s_pre[2 * j + 1]), L.hscale), t);
+  }
+}
+
+// Per stain, the type-7 50th percentile of the per-patch values, written as
+// the reported sample percentile: one block sorts them (bitonic, in shared
+// memory; at most 4096 patches).
+__global__ void __launch_bounds__(1024) k_patch_median(const double* per_patch, BasisState* bs,
+                                                       const Model* m) {
+  __shared__ double s_v[kMaxMedianPatches];
+  const int n = bs->n_acc;
+  if (n <= 0 || n > kMaxMedianPatches || bs->status != SPCN_OK || m->status != SPCN_OK) return;
+  int np2 = 1;
+  while (np2 < n) np2 <<= 1;
+  for (int j = 0; j < 2; ++j) {
+    for (int i = threadIdx.x; i < np2; i += blockDim.x)
+      s_v[i] = i < n ? per_patch[2 * i + j] : __longlong_as_double(0x7FF0000000000000ll);
+    __syncthreads();
+    for (int size = 2; size <= np2; size <<= 1) {
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        for (int i = threadIdx.x; i < np2; i += blockDim.x) {
+          const int o = i ^ stride;
+          if (o > i) {
+            const bool up = (i & size) == 0;
+            const double x = s_v[i], y = s_v[o];
+            if ((x > y) == up) { s_v[i] = y; s_v[o] = x; }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    if (threadIdx.x == 0) {
+      const double pos = (double)(n - 1) * 0.5;
+      const int k = (int)floor(pos);
+      const int k1 = k + 1 <= n - 1 ? k + 1 : k;
+      const double t = pos - (double)k;
+      const double lo = s_v[k], hi = s_v[k1];
+      bs->sel.p99[j] = __dadd_rn(lo, __dmul_rn(t, __dsub_rn(hi, lo)));
+    }
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------------ host driver
 static int grid_for(const Context* c, int occ) { return c->num_sms * (occ > 0 ? occ : 1); }
 
@@ -611,6 +770,8 @@ int configure_basis_kernels(Context* c) {
   SPCN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->occ_snmf, k_snmf,
                                                               kSnmfThreads, 0));
   if (c->occ_snmf < 1) return SPCN_ERR_CUDA;
+  SPCN_CUDA_TRY(cudaFuncSetAttribute(k_patch_p99, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kPatchSelSmem));
   if (grid_for(c, c->occ_snmf) > kMaxSnmfGrid) c->occ_snmf = kMaxSnmfGrid / c->num_sms;
   return SPCN_OK;
 }
@@ -669,7 +830,7 @@ int launch_estimate_basis(Context* c, const spcn_image* img, const spcn_params* 
   SPCN_LAUNCH_CHECK(c);
   SPCN_CUDA_TRY(cudaMemsetAsync(bs->i0_hist, 0, sizeof(bs->i0_hist) + sizeof(bs->i0_ticket), st));
   I0Args ia{c->br, bs, c->model_b, bs->i0_hist, &bs->i0_ticket, p->i0_max_samples,
-            (double)p->i0_pct};
+            (double)p->i0_pct, (p->flags & SPCN_FLAG_I0_255) ? 1 : 0};
   k_i0<<<kI0Blocks, kI0Threads, 0, st>>>(ia);
   SPCN_LAUNCH_CHECK(c);
   rc = launch_build_model(c, c->model_b, nullptr, nullptr, p->lambda, c->model_b, st);
@@ -687,6 +848,7 @@ int launch_estimate_basis(Context* c, const spcn_image* img, const spcn_params* 
   sa.max_iter = p->max_iter;
   sa.tol = (double)p->tol;
   sa.timeout_ns = c->timeout_ns;
+  sa.order_blue = (p->flags & SPCN_FLAG_ORDER_BLUE) ? 1 : 0;
   SPCN_CUDA_TRY(cudaMemsetAsync(c->sel, 0, sizeof(SelectState), st));
   void* args[] = {&sa};
   SPCN_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_snmf, grid_for(c, c->occ_snmf), kSnmfThreads,
@@ -694,6 +856,15 @@ int launch_estimate_basis(Context* c, const spcn_image* img, const spcn_params* 
   c->launches++;
   rc = launch_build_model(c, c->model_b, nullptr, nullptr, p->lambda, c->model_b, st);
   if (rc) return rc;
+  if (p->flags & SPCN_FLAG_P99_PATCH_MEDIAN) {   // patches sampling (checked by the caller)
+    SPCN_CUDA_TRY(cudaMemsetAsync(&bs->sel, 0, sizeof(SelectState), st));
+    PatchP99Args pp{c->nw, c->cand, n_cand, bs, c->model_b, (double)p->stain_pct, c->partials};
+    k_patch_p99<<<p->n_patches, kPatchSelThreads, kPatchSelSmem, st>>>(pp);
+    SPCN_LAUNCH_CHECK(c);
+    k_patch_median<<<1, 1024, 0, st>>>(c->partials, bs, c->model_b);
+    SPCN_LAUNCH_CHECK(c);
+    return SPCN_OK;
+  }
   return launch_select_list(c, c->nw, &bs->n_nw, c->model_b, &bs->sel, c->rhist_b,
                             (double)p->stain_pct, st);
 }

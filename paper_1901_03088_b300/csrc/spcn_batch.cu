@@ -1040,6 +1040,7 @@ int spcn_batch_create(void* ctx, int32_t n, const spcn_image* tiles, const spcn_
   if (!ctx || n < 1 || n > (1 << 20) || !tiles || !tile_stats || !tgt_st || !outs ||
       !out_pitches || !batch || !params_ok(params))
     return SPCN_ERR_INVALID_ARG;
+  if (params->flags & SPCN_FLAG_P99_SAMPLED) return SPCN_ERR_INVALID_ARG;   // pass 1 always runs
   *batch = nullptr;
   int rc = stats_ok(tgt_st);
   if (rc) return rc;

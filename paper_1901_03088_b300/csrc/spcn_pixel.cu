@@ -607,6 +607,50 @@ int launch_window_from_basis(Context* c, const Model* m, const SelectState* samp
   return SPCN_OK;
 }
 
+// SPCN_FLAG_P99_SAMPLED: the source percentile is not measured but given,
+// either by the caller or by the basis estimation on the device; the Eq. 3
+// factors are then formed exactly as after a measured percentile.
+__device__ __forceinline__ void set_given_percentiles(SelectState* s, double p0, double p1,
+                                                      double t0, double t1) {
+  const double p[2] = {p0, p1}, tg[2] = {t0, t1};
+  for (int j = 0; j < 2; ++j) {
+    s->p99[j] = p[j];
+    s->scale[j] = (p[j] != 0.0) ? tg[j] / p[j] : 1.0;
+  }
+  s->all_resolved = 1;
+}
+
+__global__ void k_scale_given(SelectState* s, double p0, double p1, double t0, double t1) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) set_given_percentiles(s, p0, p1, t0, t1);
+}
+
+// From the basis estimation left on the device; a failed estimation is
+// recorded in the error word and leaves scale 1.
+__global__ void k_scale_from_basis(const Model* m, const SelectState* sample_sel,
+                                   const int* basis_status, SelectState* s, double t0, double t1,
+                                   int* err) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  int st = *basis_status;
+  if (st == SPCN_OK) st = m->status;
+  if (st != SPCN_OK) record_error(err, st);
+  set_given_percentiles(s, st == SPCN_OK ? sample_sel->p99[0] : 0.0,
+                        st == SPCN_OK ? sample_sel->p99[1] : 0.0, t0, t1);
+}
+
+int launch_scale_given(Context* c, const double* p99, const double* tgt, cudaStream_t st) {
+  k_scale_given<<<1, 32, 0, st>>>(c->sel, p99[0], p99[1], tgt[0], tgt[1]);
+  SPCN_LAUNCH_CHECK(c);
+  return SPCN_OK;
+}
+
+int launch_scale_from_basis(Context* c, const Model* m, const SelectState* sample_sel,
+                            const int* basis_status, const double* tgt, cudaStream_t st) {
+  k_scale_from_basis<<<1, 32, 0, st>>>(m, sample_sel, basis_status, c->sel, tgt[0], tgt[1],
+                                       c->err);
+  SPCN_LAUNCH_CHECK(c);
+  return SPCN_OK;
+}
+
 // Constants of the conservative all-white test of a full chunk: every byte
 // has its top k bits set, with k the smallest for which that puts a byte
 // above the threshold T (256 - 2^(8-k) > T).  With T = 255 nothing is white

@@ -20,6 +20,12 @@ STATUS_NAMES = {
 }
 SAMPLE_MODES = {"all": 0, "hash": 1, "patches": 2}
 
+# spcn_params.flags bits (include/spcn.h): the paper's earlier choices
+FLAG_I0_255 = 0x1
+FLAG_ORDER_BLUE = 0x2
+FLAG_P99_SAMPLED = 0x4
+FLAG_P99_PATCH_MEDIAN = 0x8
+
 
 class SpcnError(RuntimeError):
     def __init__(self, status: int, where: str):

@@ -1,0 +1,178 @@
+"""The paper's earlier choices as flags (spcn_params.flags), each against the
+FP64 oracle's matching option, through the C ABI.
+
+* SPCN_FLAG_I0_255           -- §2.1 Eq. 1, i0 fixed at 255;
+* SPCN_FLAG_ORDER_BLUE       -- §3.1 item 3's original heuristic (reading R14);
+* SPCN_FLAG_P99_SAMPLED      -- §3.1 item 2's sub-sampled percentile used for
+                                Eq. 3 (no pass 1);
+* SPCN_FLAG_P99_PATCH_MEDIAN -- §3.2 item 4, median of per-patch percentiles.
+
+Tolerances are those of the default path: basis 1e-5, uint8 within 1 on
+>= 99.99% of pixels; the patch median is also checked bit for bit against the
+type-7 statistics of the library's own FP32 densities of each patch.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import spcn_oracle as O  # noqa: E402
+from paper_1901_03088_b300 import synth  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def spcn():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1901_03088_b300 import build
+    build.build()
+    from paper_1901_03088_b300 import spcn as s
+    return s
+
+
+@pytest.fixture(scope="module")
+def ctx(spcn):
+    c = spcn.Context(0)
+    yield c
+    c.close()
+
+
+def to_dev(img):
+    return torch.from_numpy(np.ascontiguousarray(img)).cuda()
+
+
+def type7(a, p):
+    a = np.sort(np.asarray(a, dtype=np.float32)).astype(np.float64)
+    n = a.size
+    pos = (n - 1) * (p / 100.0)
+    k = int(math.floor(pos))
+    t = pos - k
+    if k + 1 >= n:
+        return float(a[n - 1])
+    return float(a[k]) + t * (float(a[k + 1]) - float(a[k]))
+
+
+def close_uint8(a, b):
+    d = np.abs(a.astype(int) - b.astype(int))
+    assert (d > 1).mean() <= 1e-4, d.max()
+
+
+def test_i0_255(spcn, ctx):
+    img = synth.make_image(512, 512, 1301, white=(240.0, 232.0, 247.0))
+    o = O.estimate_basis(img, O.Params(sample_mode="all", i0_fixed_255=True))
+    g = ctx.estimate_basis(to_dev(img), spcn.params(sample_mode="all", flags=spcn.FLAG_I0_255))
+    assert list(g.i0) == [255.0, 255.0, 255.0]
+    assert np.max(np.abs(np.array(g.basis) - o.W)) <= 1e-5
+    for j in range(2):
+        assert abs(g.p99[j] - o.p99[j]) <= 1e-4 * o.p99[j]
+    d = ctx.estimate_basis(to_dev(img), spcn.params(sample_mode="all"))
+    assert max(d.i0) < 250.0
+
+
+def test_order_blue_swaps_blue_tinged_eosin(spcn, ctx):
+    hema = np.array([0.75, 0.45, 0.49]); hema /= np.linalg.norm(hema)
+    eosin = np.array([0.10, 0.80, 0.59]); eosin /= np.linalg.norm(eosin)
+    W = np.column_stack([hema, eosin])
+    img = synth.make_image(384, 384, 1302, W=W, pure=True)
+    o_rb = O.estimate_basis(img, O.Params(sample_mode="all"))
+    o_b = O.estimate_basis(img, O.Params(sample_mode="all", order="blue"))
+    assert np.allclose(o_b.W, o_rb.W[:, ::-1])
+    g_rb = ctx.estimate_basis(to_dev(img), spcn.params(sample_mode="all"))
+    g_b = ctx.estimate_basis(to_dev(img), spcn.params(sample_mode="all", flags=spcn.FLAG_ORDER_BLUE))
+    assert np.max(np.abs(np.array(g_rb.basis) - o_rb.W)) <= 1e-5
+    assert np.max(np.abs(np.array(g_b.basis) - o_b.W)) <= 1e-5
+    for j in range(2):
+        assert abs(g_b.p99[j] - o_b.p99[j]) <= 1e-4 * o_b.p99[j]
+
+
+@pytest.mark.parametrize("shape", [(512, 512), (77, 123)])
+def test_p99_sampled_normalize(spcn, ctx, shape):
+    h, w = shape
+    img = synth.make_image(h, w, 1303 + h)
+    tgt_img = synth.make_image(256, 256, 1)
+    p = spcn.params(sample_mode="all")
+    src = ctx.estimate_basis(to_dev(img), p)          # p99 over the sampled non-white pixels
+    tgt = ctx.estimate_basis(to_dev(tgt_img), p)
+    pf = spcn.params(sample_mode="all", flags=spcn.FLAG_P99_SAMPLED)
+    ctx.kernel_timing(True)
+    out, used = ctx.normalize(to_dev(img), src, tgt, pf, return_p99=True)
+    assert ctx.kernel_times("pass1")[1] == 0
+    ctx.kernel_timing(False)
+    assert used[0] == src.p99[0] and used[1] == src.p99[1]
+    so = O.Stats(W=np.array(src.basis, dtype=np.float32).astype(np.float64),
+                 i0=np.float32(src.i0).astype(np.float64), p99=np.array(src.p99[:]))
+    to = O.Stats(W=np.array(tgt.basis, dtype=np.float32).astype(np.float64),
+                 i0=np.float32(tgt.i0).astype(np.float64), p99=np.array(tgt.p99[:]))
+    close_uint8(out.cpu().numpy(), O.normalize(img, so, to))
+    # the one-call path with the flag gives the same bytes and reports the sampled percentile
+    out2, st2 = ctx.normalize_estimated(to_dev(img), tgt, pf, return_stats=True)
+    assert torch.equal(out, out2)
+    assert st2.p99[0] == src.p99[0] and st2.p99[1] == src.p99[1]
+
+
+def test_p99_sampled_rejects_negative_percentile(spcn, ctx):
+    img = to_dev(synth.make_image(64, 64, 1304))
+    st = ctx.estimate_basis(img, spcn.params(sample_mode="all"))
+    st.p99[0] = -1.0
+    with pytest.raises(spcn.SpcnError):
+        ctx.normalize(img, st, st, spcn.params(flags=spcn.FLAG_P99_SAMPLED))
+
+
+def test_patch_median_against_oracle_and_own_densities(spcn, ctx):
+    img = synth.make_image(600, 700, 1305, blobs=True)
+    kw = dict(sample_mode="patches", n_patches=7, patch_size=64, seed=9)
+    o = O.estimate_basis(img, O.Params(p99_patch_median=True, **kw))
+    g = ctx.estimate_basis(to_dev(img), spcn.params(flags=spcn.FLAG_P99_PATCH_MEDIAN, **kw))
+    assert np.max(np.abs(np.array(g.basis) - o.W)) <= 1e-5
+    for j in range(2):
+        assert abs(g.p99[j] - o.p99[j]) <= 1e-4 * o.p99[j]
+    # bit for bit: per kept patch the type-7 P99 of the library's own FP32
+    # densities over its non-white pixels, then the type-7 median
+    pp = O.Params(**kw)
+    per = []
+    for patch in O.select_patches(img, pp):
+        P = 64
+        pim = patch.reshape(P, P, 3)
+        Hd = ctx.stain_densities(to_dev(pim), g).cpu().numpy()
+        nw = O.nonwhite_mask(patch)
+        per.append([type7(Hd[j][nw], 99.0) for j in range(2)])
+    per = np.array(per)
+    for j in range(2):
+        v = np.sort(per[:, j])
+        n = v.size
+        pos = (n - 1) * 0.5
+        k = int(math.floor(pos))
+        t = pos - k
+        med = v[k] if k + 1 >= n else v[k] + t * (v[k + 1] - v[k])
+        assert g.p99[j] == med, (j, g.p99[j], med)
+
+
+def test_patch_median_with_even_count_and_one_patch(spcn, ctx):
+    img = synth.make_image(600, 700, 1306, blobs=True)
+    for n in (1, 6):
+        kw = dict(sample_mode="patches", n_patches=n, patch_size=48, seed=4)
+        o = O.estimate_basis(img, O.Params(p99_patch_median=True, **kw))
+        g = ctx.estimate_basis(to_dev(img), spcn.params(flags=spcn.FLAG_P99_PATCH_MEDIAN, **kw))
+        for j in range(2):
+            assert abs(g.p99[j] - o.p99[j]) <= 1e-4 * o.p99[j]
+    one = ctx.estimate_basis(to_dev(img), spcn.params(sample_mode="patches", n_patches=1,
+                                                      patch_size=48, seed=4))
+    med = ctx.estimate_basis(to_dev(img), spcn.params(sample_mode="patches", n_patches=1,
+                                                      patch_size=48, seed=4,
+                                                      flags=spcn.FLAG_P99_PATCH_MEDIAN))
+    assert one.p99[0] == med.p99[0] and one.p99[1] == med.p99[1]
+
+
+def test_flag_validation(spcn, ctx):
+    img = to_dev(synth.make_image(64, 64, 1307))
+    with pytest.raises(spcn.SpcnError):
+        ctx.estimate_basis(img, spcn.params(sample_mode="all", flags=spcn.FLAG_P99_PATCH_MEDIAN))
+    with pytest.raises(spcn.SpcnError):
+        ctx.estimate_basis(img, spcn.params(sample_mode="all", flags=0x100))
+    st = ctx.estimate_basis(img, spcn.params(sample_mode="all"))
+    out = torch.empty_like(img)
+    with pytest.raises(spcn.SpcnError):
+        spcn.normalize_batched(ctx, [img], [st], st, [out], spcn.params(flags=spcn.FLAG_P99_SAMPLED))
