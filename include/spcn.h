@@ -82,11 +82,18 @@ typedef enum {
  * SPCN_FLAG_P99_PATCH_MEDIAN: basis estimation reports, per stain, the
  *   median over the kept patches of each patch's non-white percentile
  *   (§3.2 item 4) as p99.  Requires SPCN_SAMPLE_PATCHES and n_patches <= 4096.
+ * SPCN_FLAG_H_PINV: the densities that are measured, scaled and reconstructed
+ *   are H = pinv(W) v (§2.1) instead of the non-negative lasso of Eq. 2: in
+ *   the reported and exact percentiles, spcn_stain_densities, and both
+ *   passes.  They are signed, so a percentile can be negative; outputs above
+ *   255 are clamped.  The basis itself is still learnt with Eq. 2.  Not
+ *   available for batches and the float (differentiable) entry points.
  */
 #define SPCN_FLAG_I0_255 0x1u
 #define SPCN_FLAG_ORDER_BLUE 0x2u
 #define SPCN_FLAG_P99_SAMPLED 0x4u
 #define SPCN_FLAG_P99_PATCH_MEDIAN 0x8u
+#define SPCN_FLAG_H_PINV 0x10u
 
 /* An 8-bit interleaved RGB image. */
 typedef struct {
@@ -179,8 +186,8 @@ int spcn_stain_densities(void* ctx, const spcn_image* img, const spcn_stats* st,
  * width/height as src, row pitch out_pitch >= 3*width; must not overlap
  * src).  If src_p99_out (host, 2 doubles) is non-NULL the call blocks and
  * returns the source percentiles there; otherwise it is asynchronous.
- * With SPCN_FLAG_P99_SAMPLED there is no pass 1: src_st->p99 (finite, >= 0)
- * is the source percentile.
+ * With SPCN_FLAG_P99_SAMPLED there is no pass 1: src_st->p99 (finite, and
+ * >= 0 unless SPCN_FLAG_H_PINV) is the source percentile.
  * Errors: INVALID_ARG, DEGENERATE_BASIS, CUDA (and, when blocking,
  * NO_TISSUE/TIMEOUT). */
 int spcn_normalize(void* ctx, const spcn_image* src, const spcn_stats* src_st,

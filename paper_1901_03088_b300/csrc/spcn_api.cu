@@ -123,7 +123,7 @@ bool params_ok(const spcn_params* p) {
   if (p->max_iter < 1 || p->max_iter > 1000000) return false;
   if (!(p->tol >= 0.f) || !std::isfinite(p->tol)) return false;
   const uint32_t known = SPCN_FLAG_I0_255 | SPCN_FLAG_ORDER_BLUE | SPCN_FLAG_P99_SAMPLED |
-                         SPCN_FLAG_P99_PATCH_MEDIAN;
+                         SPCN_FLAG_P99_PATCH_MEDIAN | SPCN_FLAG_H_PINV;
   if (p->flags & ~known) return false;
   if ((p->flags & SPCN_FLAG_P99_PATCH_MEDIAN) &&
       (p->sample_mode != SPCN_SAMPLE_PATCHES || p->n_patches > 4096))
@@ -132,14 +132,14 @@ bool params_ok(const spcn_params* p) {
 }
 
 // A usable basis and i0: finite, W >= 0, columns not parallel, i0 in [1,255].
-int stats_ok(const spcn_stats* s) {
+int stats_ok(const spcn_stats* s, bool signed_p99) {
   if (!s) return SPCN_ERR_INVALID_ARG;
   for (int i = 0; i < 6; ++i)
     if (!std::isfinite(s->W[i]) || s->W[i] < 0.f) return SPCN_ERR_INVALID_ARG;
   for (int i = 0; i < 3; ++i)
     if (!(s->i0[i] >= 1.f && s->i0[i] <= 255.f)) return SPCN_ERR_INVALID_ARG;
   for (int i = 0; i < 2; ++i)
-    if (!std::isfinite(s->p99[i]) || s->p99[i] < 0.0) return SPCN_ERR_INVALID_ARG;
+    if (!std::isfinite(s->p99[i]) || (!signed_p99 && s->p99[i] < 0.0)) return SPCN_ERR_INVALID_ARG;
   double g11 = 0, g22 = 0, g12 = 0;
   for (int c = 0; c < 3; ++c) {
     g11 += (double)s->W[c] * s->W[c];
@@ -305,18 +305,20 @@ int spcn_estimate_basis(void* ctx, const spcn_image* img, const spcn_params* par
 int spcn_stain_percentile(void* ctx, const spcn_image* img, const spcn_stats* st,
                           const spcn_params* params, double* p99_out, void* stream) {
   if (!ctx || !image_ok(img) || !params_ok(params) || !p99_out) return SPCN_ERR_INVALID_ARG;
-  int rc = stats_ok(st);
+  int rc = stats_ok(st, (params->flags & SPCN_FLAG_H_PINV) != 0);
   if (rc) return rc;
   Context* c = static_cast<Context*>(ctx);
   DeviceGuard guard(c->device);
   if (!guard.ok) return SPCN_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const Geometry g = make_geometry(img, nullptr, 0);
-  rc = launch_build_model(c, c->model, st->W, st->i0, params->lambda, nullptr, s);
+  const bool pinv = (params->flags & SPCN_FLAG_H_PINV) != 0;
+  rc = launch_build_model(c, c->model, st->W, st->i0, params->lambda, nullptr, s, pinv);
   if (rc) return rc;
   const double ones[2] = {1.0, 1.0};
   rc = launch_percentile_passes(c, g, c->model, params->white_thresh, (double)params->stain_pct,
-                                st->p99, host_table_hexp(st->W, st->i0, params->lambda), ones, s);
+                                st->p99, host_table_hexp(st->W, st->i0, params->lambda), ones, s,
+                                pinv);
   if (rc) return rc;
   double p[2];
   SPCN_CUDA_TRY(cudaMemcpyAsync(p, c->sel->p99, sizeof(p), cudaMemcpyDeviceToHost, s));
@@ -332,16 +334,17 @@ int spcn_stain_densities(void* ctx, const spcn_image* img, const spcn_stats* st,
                          const spcn_params* params, float* H, int64_t h_stride, void* stream) {
   if (!ctx || !image_ok(img) || !params_ok(params) || !H) return SPCN_ERR_INVALID_ARG;
   if (h_stride < (int64_t)img->width * img->height) return SPCN_ERR_INVALID_ARG;
-  int rc = stats_ok(st);
+  int rc = stats_ok(st, true);   // the percentiles are not used here
   if (rc) return rc;
   Context* c = static_cast<Context*>(ctx);
   DeviceGuard guard(c->device);
   if (!guard.ok) return SPCN_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const Geometry g = make_geometry(img, nullptr, 0);
-  rc = launch_build_model(c, c->model, st->W, st->i0, params->lambda, nullptr, s);
+  const bool pinv = (params->flags & SPCN_FLAG_H_PINV) != 0;
+  rc = launch_build_model(c, c->model, st->W, st->i0, params->lambda, nullptr, s, pinv);
   if (rc) return rc;
-  return launch_density(c, g, c->model, H, h_stride, s);
+  return launch_density(c, g, c->model, H, h_stride, s, pinv);
 }
 
 int spcn_normalize(void* ctx, const spcn_image* src, const spcn_stats* src_st,
@@ -349,13 +352,16 @@ int spcn_normalize(void* ctx, const spcn_image* src, const spcn_stats* src_st,
                    int64_t out_pitch, double* src_p99_out, void* stream) {
   if (!ctx || !image_ok(src) || !params_ok(params) || !out) return SPCN_ERR_INVALID_ARG;
   if (out_pitch < 3ll * src->width) return SPCN_ERR_INVALID_ARG;
-  int rc = stats_ok(src_st);
+  const bool signed_p99 = (params->flags & SPCN_FLAG_H_PINV) != 0;
+  int rc = stats_ok(src_st, signed_p99);
   if (rc) return rc;
-  rc = stats_ok(tgt_st);
+  rc = stats_ok(tgt_st, signed_p99);
   if (rc) return rc;
-  if (params->flags & SPCN_FLAG_P99_SAMPLED)
+  if (params->flags & SPCN_FLAG_P99_SAMPLED)   // signed only for the pseudo-inverse
     for (int j = 0; j < 2; ++j)
-      if (!(src_st->p99[j] >= 0.0) || !std::isfinite(src_st->p99[j])) return SPCN_ERR_INVALID_ARG;
+      if (!std::isfinite(src_st->p99[j]) ||
+          (!(params->flags & SPCN_FLAG_H_PINV) && !(src_st->p99[j] >= 0.0)))
+        return SPCN_ERR_INVALID_ARG;
   // out must not overlap the source rows
   {
     const uintptr_t s0 = reinterpret_cast<uintptr_t>(src->data);
@@ -369,7 +375,8 @@ int spcn_normalize(void* ctx, const spcn_image* src, const spcn_stats* src_st,
   if (!guard.ok) return SPCN_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const Geometry g = make_geometry(src, out, out_pitch);
-  rc = launch_build_model(c, c->model, src_st->W, src_st->i0, params->lambda, nullptr, s);
+  const bool pinv = (params->flags & SPCN_FLAG_H_PINV) != 0;
+  rc = launch_build_model(c, c->model, src_st->W, src_st->i0, params->lambda, nullptr, s, pinv);
   if (rc) return rc;
   if (params->flags & SPCN_FLAG_P99_SAMPLED)   // the given percentile, no pass 1
     rc = launch_scale_given(c, src_st->p99, tgt_st->p99, s);
@@ -377,9 +384,9 @@ int spcn_normalize(void* ctx, const spcn_image* src, const spcn_stats* src_st,
     rc = launch_percentile_passes(c, g, c->model, params->white_thresh, (double)params->stain_pct,
                                   src_st->p99,
                                   host_table_hexp(src_st->W, src_st->i0, params->lambda),
-                                  tgt_st->p99, s);
+                                  tgt_st->p99, s, pinv);
   if (rc) return rc;
-  rc = launch_recon(c, g, c->model, tgt_st->W, tgt_st->i0, s);
+  rc = launch_recon(c, g, c->model, tgt_st->W, tgt_st->i0, s, pinv);
   if (rc) return rc;
   if (src_p99_out) {
     double p[2];
@@ -419,7 +426,7 @@ int spcn_normalize_f32(void* ctx, const float* x, int32_t batch, int32_t height,
                        const spcn_stats* src_stats, const spcn_stats* tgt_stats, const float* wt,
                        const spcn_params* params, float* y, void* stream) {
   if (!ctx || !x || !y || !wt || !src_stats || batch < 1 || height < 1 || width < 1 ||
-      !params_ok(params))
+      !params_ok(params) || (params->flags & SPCN_FLAG_H_PINV))
     return SPCN_ERR_INVALID_ARG;
   int rc = stats_ok(tgt_stats);
   if (rc) return rc;
@@ -439,7 +446,7 @@ int spcn_normalize_f32_backward(void* ctx, const float* x, const float* gy, int3
                                 const spcn_stats* tgt_stats, const float* wt,
                                 const spcn_params* params, float* gx, float* gwt, void* stream) {
   if (!ctx || !x || !gy || !gx || !gwt || !wt || !src_stats || batch < 1 || height < 1 ||
-      width < 1 || !params_ok(params))
+      width < 1 || !params_ok(params) || (params->flags & SPCN_FLAG_H_PINV))
     return SPCN_ERR_INVALID_ARG;
   int rc = stats_ok(tgt_stats);
   if (rc) return rc;
@@ -459,7 +466,7 @@ int spcn_normalize_estimated(void* ctx, const spcn_image* src, const spcn_stats*
                              spcn_stats* src_st_out, void* stream) {
   if (!ctx || !image_ok(src) || !params_ok(params) || !out) return SPCN_ERR_INVALID_ARG;
   if (out_pitch < 3ll * src->width) return SPCN_ERR_INVALID_ARG;
-  int rc = stats_ok(tgt_st);
+  int rc = stats_ok(tgt_st, (params->flags & SPCN_FLAG_H_PINV) != 0);
   if (rc) return rc;
   {
     const uintptr_t s0 = reinterpret_cast<uintptr_t>(src->data);
@@ -479,6 +486,7 @@ int spcn_normalize_estimated(void* ctx, const spcn_image* src, const spcn_stats*
   // is the source table; the window comes from the sample P99
   const Model* m = c->model_b;
   const Geometry g = make_geometry(src, out, out_pitch);
+  const bool pinv = (params->flags & SPCN_FLAG_H_PINV) != 0;
   if (params->flags & SPCN_FLAG_P99_SAMPLED) {   // the sample percentile, no pass 1
     rc = launch_scale_from_basis(c, m, &c->bs->sel, &c->bs->status, tgt_st->p99, s);
     if (rc) return rc;
@@ -487,10 +495,10 @@ int spcn_normalize_estimated(void* ctx, const spcn_image* src, const spcn_stats*
     rc = launch_window_from_basis(c, m, &c->bs->sel, &c->bs->status, wdev, s);
     if (rc) return rc;
     rc = launch_percentile_passes_dev(c, g, m, params->white_thresh, (double)params->stain_pct,
-                                      wdev, tgt_st->p99, s);
+                                      wdev, tgt_st->p99, s, pinv);
     if (rc) return rc;
   }
-  rc = launch_recon(c, g, m, tgt_st->W, tgt_st->i0, s);
+  rc = launch_recon(c, g, m, tgt_st->W, tgt_st->i0, s, pinv);
   if (rc) return rc;
   if (src_st_out) {
     memset(src_st_out, 0, sizeof(*src_st_out));

@@ -18,7 +18,8 @@
 namespace spcn {
 
 int launch_select_list(Context* c, const uint32_t* items, const u64* n_dev, const Model* m,
-                       SelectState* sel, u64* ghist, double pct, cudaStream_t st);
+                       SelectState* sel, u64* ghist, double pct, cudaStream_t st,
+                       bool pinv = false);
 
 constexpr int kCompactBlock = 4096;
 constexpr int kCompactThreads = 512;
@@ -653,8 +654,10 @@ __device__ void shared_rank_bin(const unsigned* h, u64 r, int* s_idx, u64* s_bef
 }
 
 // One block per kept patch: radix select (11/11/10-bit digits of the FP32
-// key of the scaled density) of ranks k and k+1 of both stains over the
-// patch's segment of the non-white list.
+// key of the scaled density; order-preserving signed keys for the
+// pseudo-inverse) of ranks k and k+1 of both stains over the patch's segment
+// of the non-white list.
+template <bool PINV>
 __global__ void __launch_bounds__(kPatchSelThreads, 1) k_patch_p99(PatchP99Args a) {
   extern __shared__ __align__(16) char s_dyn[];
   unsigned* s_hist = reinterpret_cast<unsigned*>(s_dyn + kLutSmemBytes);   // [4][bins]
@@ -693,8 +696,9 @@ __global__ void __launch_bounds__(kPatchSelThreads, 1) k_patch_p99(PatchP99Args 
     for (u64 i = threadIdx.x; i < n; i += blockDim.x) {
       const uint32_t v = __ldg(items + i);
       float h1, h2;
-      solve_one(lut, lut_addr(v, lr, 0), lut_addr(v, lr, 1), lut_addr(v, lr, 2), L, h1, h2);
-      const unsigned key[2] = {__float_as_uint(h1), __float_as_uint(h2)};
+      solve_one<PINV>(lut, lut_addr(v, lr, 0), lut_addr(v, lr, 1), lut_addr(v, lr, 2), L, h1, h2);
+      const unsigned key[2] = {PINV ? signed_key(__float_as_uint(h1)) : __float_as_uint(h1),
+                               PINV ? signed_key(__float_as_uint(h2)) : __float_as_uint(h2)};
       const unsigned live = __activemask();
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -719,8 +723,10 @@ __global__ void __launch_bounds__(kPatchSelThreads, 1) k_patch_p99(PatchP99Args 
   }
   if (threadIdx.x < 2) {
     const int j = threadIdx.x;
-    a.per_patch[2 * p + j] = interp_type7(__fmul_rn(__uint_as_float(s_pre[2 * j]), L.hscale),
-                                          __fmul_rn(__uint_as_float(s_pre[2 * j + 1]), L.hscale), t);
+    const unsigned ka = PINV ? signed_key_inv(s_pre[2 * j]) : s_pre[2 * j];
+    const unsigned kb = PINV ? signed_key_inv(s_pre[2 * j + 1]) : s_pre[2 * j + 1];
+    a.per_patch[2 * p + j] = interp_type7(__fmul_rn(__uint_as_float(ka), L.hscale),
+                                          __fmul_rn(__uint_as_float(kb), L.hscale), t);
   }
 }
 
@@ -770,8 +776,10 @@ int configure_basis_kernels(Context* c) {
   SPCN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->occ_snmf, k_snmf,
                                                               kSnmfThreads, 0));
   if (c->occ_snmf < 1) return SPCN_ERR_CUDA;
-  SPCN_CUDA_TRY(cudaFuncSetAttribute(k_patch_p99, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kPatchSelSmem));
+  SPCN_CUDA_TRY(cudaFuncSetAttribute(k_patch_p99<false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPatchSelSmem));
+  SPCN_CUDA_TRY(cudaFuncSetAttribute(k_patch_p99<true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPatchSelSmem));
   if (grid_for(c, c->occ_snmf) > kMaxSnmfGrid) c->occ_snmf = kMaxSnmfGrid / c->num_sms;
   return SPCN_OK;
 }
@@ -854,19 +862,24 @@ int launch_estimate_basis(Context* c, const spcn_image* img, const spcn_params* 
   SPCN_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_snmf, grid_for(c, c->occ_snmf), kSnmfThreads,
                                             args, 0, st));
   c->launches++;
-  rc = launch_build_model(c, c->model_b, nullptr, nullptr, p->lambda, c->model_b, st);
+  // the final table: the learnt basis, and the densities that are scaled
+  const bool pinv = (p->flags & SPCN_FLAG_H_PINV) != 0;
+  rc = launch_build_model(c, c->model_b, nullptr, nullptr, p->lambda, c->model_b, st, pinv);
   if (rc) return rc;
   if (p->flags & SPCN_FLAG_P99_PATCH_MEDIAN) {   // patches sampling (checked by the caller)
     SPCN_CUDA_TRY(cudaMemsetAsync(&bs->sel, 0, sizeof(SelectState), st));
     PatchP99Args pp{c->nw, c->cand, n_cand, bs, c->model_b, (double)p->stain_pct, c->partials};
-    k_patch_p99<<<p->n_patches, kPatchSelThreads, kPatchSelSmem, st>>>(pp);
+    if (pinv)
+      k_patch_p99<true><<<p->n_patches, kPatchSelThreads, kPatchSelSmem, st>>>(pp);
+    else
+      k_patch_p99<false><<<p->n_patches, kPatchSelThreads, kPatchSelSmem, st>>>(pp);
     SPCN_LAUNCH_CHECK(c);
     k_patch_median<<<1, 1024, 0, st>>>(c->partials, bs, c->model_b);
     SPCN_LAUNCH_CHECK(c);
     return SPCN_OK;
   }
   return launch_select_list(c, c->nw, &bs->n_nw, c->model_b, &bs->sel, c->rhist_b,
-                            (double)p->stain_pct, st);
+                            (double)p->stain_pct, st, pinv);
 }
 
 // Wait for the estimation launched on `st` and fill the host record.

@@ -718,7 +718,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch(BatchArgs a) {
       active[k] = !__ldcg(&S->sel.resolved[k]);
     }
     const ImageSource src{T->g, a.thr};
-    if (!radix_select(src, lut, L, &S->sel, rank, active, a.rhist, s_hist, &S->sel.barrier,
+    if (!radix_select<false>(src, lut, L, &S->sel, rank, active, a.rhist, s_hist, &S->sel.barrier,
                       &a.run->err, a.timeout_ns, a.tgt0, a.tgt1))
       return;
     target += gridDim.x;
@@ -1040,7 +1040,8 @@ int spcn_batch_create(void* ctx, int32_t n, const spcn_image* tiles, const spcn_
   if (!ctx || n < 1 || n > (1 << 20) || !tiles || !tile_stats || !tgt_st || !outs ||
       !out_pitches || !batch || !params_ok(params))
     return SPCN_ERR_INVALID_ARG;
-  if (params->flags & SPCN_FLAG_P99_SAMPLED) return SPCN_ERR_INVALID_ARG;   // pass 1 always runs
+  // pass 1 always runs, with the lasso densities
+  if (params->flags & (SPCN_FLAG_P99_SAMPLED | SPCN_FLAG_H_PINV)) return SPCN_ERR_INVALID_ARG;
   *batch = nullptr;
   int rc = stats_ok(tgt_st);
   if (rc) return rc;

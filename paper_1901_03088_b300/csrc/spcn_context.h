@@ -93,7 +93,9 @@ struct DeviceGuard {
 // Argument checks shared by the entry points (spcn_api.cu).
 bool image_ok(const spcn_image* img);
 bool params_ok(const spcn_params* p);
-int stats_ok(const spcn_stats* s);            // SPCN_OK, INVALID_ARG or DEGENERATE_BASIS
+// SPCN_OK, INVALID_ARG or DEGENERATE_BASIS; signed_p99: the percentiles may
+// be negative (pseudo-inverse densities)
+int stats_ok(const spcn_stats* s, bool signed_p99 = false);
 Geometry make_geometry(const spcn_image* img, uint8_t* out, int64_t out_pitch);
 
 int ensure_sample_capacity(Context* c, size_t n);

@@ -63,7 +63,7 @@ struct Lasso {
   float kappa;
   float hscale;         // 2^hexp
   int hexp;
-  int pad;
+  int pinv;             // the table holds pseudo-inverse rows (SPCN_FLAG_H_PINV)
 };
 
 // Per-image model in device memory.
@@ -229,10 +229,18 @@ __device__ __forceinline__ float2 lut_ld(const char* lut, unsigned off) {
 
 // Scaled H-step of one pixel from its three table offsets.  Every pixel pass
 // (and solve_pair below, lane by lane) uses exactly this arithmetic, so all
-// passes produce the same densities bit for bit.
+// passes produce the same densities bit for bit.  PINV: the table holds the
+// rows of pinv(W) times the optical density (§2.1), and the densities are the
+// plain sums (signed, no sparsity).
+template <bool PINV = false>
 __device__ __forceinline__ void solve_one(const char* lut, unsigned aR, unsigned aG, unsigned aB,
                                           const Lasso& L, float& h1, float& h2) {
   const float2 eR = lut_ld(lut, aR), eG = lut_ld(lut, aG + kLutOffG), eB = lut_ld(lut, aB + kLutOffB);
+  if (PINV) {
+    h1 = (eR.x + eG.x) + eB.x;
+    h2 = (eR.y + eG.y) + eB.y;
+    return;
+  }
   const float D1 = add_sat(eR.x + eG.x, eB.x);
   const float D2 = add_sat(eR.y + eG.y, eB.y);
   const float t1 = mul_sat(L.kappa, fmaf(L.nrho1, D2, D1));
@@ -243,6 +251,7 @@ __device__ __forceinline__ void solve_one(const char* lut, unsigned aR, unsigned
 
 // The same for two pixels at once, packed lanes: (A, B) -> H1 = (h1_A, h1_B),
 // H2 = (h2_A, h2_B).
+template <bool PINV = false>
 __device__ __forceinline__ void solve_pair(const char* lut, unsigned aRA, unsigned aGA,
                                            unsigned aBA, unsigned aRB, unsigned aGB, unsigned aBB,
                                            f2 NR1, f2 NR2, float kappa, f2& H1, f2& H2) {
@@ -252,6 +261,11 @@ __device__ __forceinline__ void solve_pair(const char* lut, unsigned aRA, unsign
                eBB = lut_ld(lut, aBB + kLutOffB);
   const f2 SA = add2(pk(eRA.x, eRA.y), pk(eGA.x, eGA.y));
   const f2 SB = add2(pk(eRB.x, eRB.y), pk(eGB.x, eGB.y));
+  if (PINV) {
+    H1 = pk(lo_of(SA) + eBA.x, lo_of(SB) + eBB.x);
+    H2 = pk(hi_of(SA) + eBA.y, hi_of(SB) + eBB.y);
+    return;
+  }
   const float D1A = add_sat(lo_of(SA), eBA.x), D2A = add_sat(hi_of(SA), eBA.y);
   const float D1B = add_sat(lo_of(SB), eBB.x), D2B = add_sat(hi_of(SB), eBB.y);
   const f2 P1 = pk(D1A, D1B), P2 = pk(D2A, D2B);
@@ -261,6 +275,16 @@ __device__ __forceinline__ void solve_pair(const char* lut, unsigned aRA, unsign
   const float t2A = mul_sat(kappa, lo_of(Q2)), t2B = mul_sat(kappa, hi_of(Q2));
   H1 = pk(fminf(D1A, t1A), fminf(D1B, t1B));
   H2 = pk(fminf(D2A, t2A), fminf(D2B, t2B));
+}
+
+// Order-preserving map of FP32 bit patterns to unsigned keys for signed
+// densities (pseudo-inverse): negative values reversed below the positive
+// ones.  The non-negative densities of the lasso use the raw bits.
+__device__ __forceinline__ unsigned signed_key(unsigned b) {
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ unsigned signed_key_inv(unsigned k) {
+  return (k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k;
 }
 
 // Copy the projected table of `m` into the shared-memory layout above.
@@ -410,16 +434,18 @@ __device__ __forceinline__ void finish_percentiles(SelectState* s, double tgt0, 
 struct Context;
 
 // Launchers (defined in the .cu files); all return spcn_status.
+// pinv: the pseudo-inverse variant of the densities (SPCN_FLAG_H_PINV); the
+// model must have been built with the same choice.
 int launch_build_model(Context* c, Model* m, const float* W, const float* i0, float lambda,
-                       const Model* from_device, cudaStream_t st);
+                       const Model* from_device, cudaStream_t st, bool pinv = false);
 int launch_percentile_passes(Context* c, const Geometry& g, const Model* m, int white_thresh,
                              double pct, const double* hint, int hexp, const double* tgt_p99,
-                             cudaStream_t st);
+                             cudaStream_t st, bool pinv = false);
 int host_table_hexp(const float* W, const float* i0, float lambda);
 int launch_recon(Context* c, const Geometry& g, const Model* m, const float* Wt,
-                 const float* i0t, cudaStream_t st);
+                 const float* i0t, cudaStream_t st, bool pinv = false);
 int launch_density(Context* c, const Geometry& g, const Model* m, float* H, int64_t stride,
-                   cudaStream_t st);
+                   cudaStream_t st, bool pinv = false);
 int launch_estimate_basis(Context* c, const spcn_image* img, const spcn_params* p,
                           cudaStream_t st);
 int finish_estimate_basis(Context* c, spcn_stats* out, cudaStream_t st);

@@ -24,6 +24,7 @@ struct ModelIn {
   float i0[3];
   float lambda;
   int hexp;          // power-of-two scale of the table; kHexpAuto: derive on the device
+  int pinv;          // pseudo-inverse rows instead of the lasso's projections
 };
 
 // Smallest e with 2^e >= 2 * (largest |d_j| any pixel can reach), so that
@@ -76,7 +77,10 @@ __global__ void k_build_model(Model* m, ModelIn in, const Model* from) {
     const double v = log((double)i0[c] / (double)(i > 0 ? i : 1));
     const double lam = c == 0 ? (double)in.lambda : 0.0;
     float p0 = 0.f, p1 = 0.f;
-    if (ok) {
+    if (ok && in.pinv) {   // s (pinv(W))[j,c] v, pinv(W) = G^-1 W^T (§2.1)
+      p0 = (float)(s * (((double)W[c] * g22 - (double)W[3 + c] * g12) / det) * v);
+      p1 = (float)(s * (((double)W[3 + c] * g11 - (double)W[c] * g12) / det) * v);
+    } else if (ok) {
       p0 = (float)(s * ((double)W[c] * v - lam) / g11);
       p1 = (float)(s * ((double)W[3 + c] * v - lam) / g22);
     }
@@ -87,7 +91,7 @@ __global__ void k_build_model(Model* m, ModelIn in, const Model* from) {
     Lasso L;
     L.hexp = hexp;
     L.hscale = (float)ldexp(1.0, hexp);
-    L.pad = 0;
+    L.pinv = in.pinv;
     if (ok) {
       L.nrho1 = (float)(-g12 / g11);
       L.nrho2 = (float)(-g12 / g22);
@@ -100,9 +104,13 @@ __global__ void k_build_model(Model* m, ModelIn in, const Model* from) {
     m->lasso = L;
     for (int j = 0; j < 2; ++j) {
       const double gjj = j ? g22 : g11;
-      for (int c = 0; c < 3; ++c)
-        m->pa[3 * j + c] = ok ? (float)(s * (double)W[3 * j + c] / gjj) + 0.f : 0.f;
-      m->pb[j] = ok ? (float)(-s * (double)in.lambda / gjj) + 0.f : 0.f;
+      for (int c = 0; c < 3; ++c) {
+        const double pj = in.pinv ? (j ? ((double)W[3 + c] * g11 - (double)W[c] * g12) / det
+                                       : ((double)W[c] * g22 - (double)W[3 + c] * g12) / det)
+                                  : (double)W[3 * j + c] / gjj;
+        m->pa[3 * j + c] = ok ? (float)(s * pj) + 0.f : 0.f;
+      }
+      m->pb[j] = (ok && !in.pinv) ? (float)(-s * (double)in.lambda / gjj) + 0.f : 0.f;
     }
     if (from != m) {
       for (int i = 0; i < 6; ++i) m->W[i] = W[i];
@@ -116,8 +124,9 @@ int host_table_hexp(const float* W, const float* i0, float lambda) {
 }
 
 int launch_build_model(Context* c, Model* m, const float* W, const float* i0, float lambda,
-                       const Model* from_device, cudaStream_t st) {
+                       const Model* from_device, cudaStream_t st, bool pinv) {
   ModelIn in;
+  in.pinv = pinv ? 1 : 0;
   for (int i = 0; i < 6; ++i) in.W[i] = W ? W[i] : 0.f;
   for (int i = 0; i < 3; ++i) in.i0[i] = i0 ? i0[i] : 1.f;
   in.lambda = lambda;
@@ -211,6 +220,7 @@ __device__ void window_select(const WindowArgs& a) {
 // and its two base-4 masks; only flagged pixels are recomputed (same
 // arithmetic, same keys), reading their bytes again (still in L2).  Called by
 // one warp for its own queue.
+template <bool PINV>
 __device__ __forceinline__ void drain_queue(const uint2* queue, int count, const Geometry& g,
                                             const char* lut, unsigned lr, const Lasso& L,
                                             const WindowConst& a, unsigned* s_coarse) {
@@ -229,7 +239,7 @@ __device__ __forceinline__ void drain_queue(const uint2* queue, int count, const
         const int k = 2 * pair + lane;
         const unsigned r = __ldg(src + 3 * k), gg = __ldg(src + 3 * k + 1), b = __ldg(src + 3 * k + 2);
         float h1, h2;
-        solve_one(lut, (r << 8) | lr, (gg << 8) | lr, (b << 8) | lr, L, h1, h2);
+        solve_one<PINV>(lut, (r << 8) | lr, (gg << 8) | lr, (b << 8) | lr, L, h1, h2);
         window_hit(a, s_coarse, __float_as_uint(h1) - a.lo0, __float_as_uint(h2) - a.lo1);
       }
     }
@@ -238,6 +248,7 @@ __device__ __forceinline__ void drain_queue(const uint2* queue, int count, const
 
 // Window arithmetic of one full chunk per lane (lanes with have = false take
 // no part), then the hit queue: called by the whole warp.
+template <bool PINV>
 __device__ __forceinline__ void pass1_chunk(const unsigned (&w)[12], unsigned qi, bool have,
                                             const char* lut, unsigned lr, f2 NR1, f2 NR2,
                                             const Lasso& L, const WindowConst& C,
@@ -247,7 +258,7 @@ __device__ __forceinline__ void pass1_chunk(const unsigned (&w)[12], unsigned qi
   unsigned packed = 0u;
   if (have) {
     f2 mask;
-    window_chunk(w, lut, lr, NR1, NR2, L.kappa, C, c_nw, c_b0, c_b1, mask);
+    window_chunk<PINV>(w, lut, lr, NR1, NR2, L.kappa, C, c_nw, c_b0, c_b1, mask);
     packed = (unsigned)lo_of(mask) | ((unsigned)hi_of(mask) << 16);
   }
   const bool hit = packed != 0u;
@@ -257,7 +268,7 @@ __device__ __forceinline__ void pass1_chunk(const unsigned (&w)[12], unsigned qi
   qn += __popc(ball);
   if (qn >= 32) {
     __syncwarp();
-    drain_queue(s_queue, qn, g, lut, lr, L, C, s_coarse);
+    drain_queue<PINV>(s_queue, qn, g, lut, lr, L, C, s_coarse);
     __syncwarp();
     qn = 0;
   }
@@ -267,6 +278,7 @@ __device__ __forceinline__ void pass1_chunk(const unsigned (&w)[12], unsigned qi
 // the same keys as the vector path, counting only the pixels that exist (the
 // padding bytes are not pixels, whatever the white threshold).  The bytes are
 // read again (L1 hits) so that no register array is indexed at run time.
+template <bool PINV>
 __device__ __forceinline__ void partial_chunk(const uint8_t* src, int n, const char* lut,
                                               unsigned lr, const Lasso& L, const WindowConst& C,
                                               unsigned* s_coarse, f2& c_nw, f2& c_b0, f2& c_b1) {
@@ -278,7 +290,7 @@ __device__ __forceinline__ void partial_chunk(const uint8_t* src, int n, const c
     const unsigned aB = ((unsigned)__ldg(src + 3 * k + 2) << 8) | lr;
     if (min(min(aR, aG), aB) >= C.wthr) continue;   // white
     float h1, h2;
-    solve_one(lut, aR, aG, aB, L, h1, h2);
+    solve_one<PINV>(lut, aR, aG, aB, L, h1, h2);
     nw += 1.f;
     b0 += fma_sat(h1, C.nk0, C.lk0);   // [h~ < lo], the vector path's test
     b1 += fma_sat(h2, C.nk1, C.lk1);
@@ -298,7 +310,7 @@ __device__ __forceinline__ void partial_chunk(const uint8_t* src, int n, const c
 // a full warp of them is ready: lanes holding a tissue chunk take their own,
 // the others pop one from the stack, so the window arithmetic runs on full
 // warps of tissue.
-template <bool DEV>
+template <bool DEV, bool PINV>
 __global__ void __launch_bounds__(kPassThreads, 1) k_pass_window(WindowArgs a) {
   extern __shared__ __align__(16) char s_dyn[];
   unsigned* s_coarse = reinterpret_cast<unsigned*>(s_dyn + kLutSmemBytes);
@@ -345,7 +357,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_window(WindowArgs a) {
       if (p.n == kChunk)
         tissue = !chunk_white(w, wm, we);
       else
-        partial_chunk(g.src + p.src_off, p.n, lut, lr, L, C, s_coarse, c_nw, c_b0, c_b1);
+        partial_chunk<PINV>(g.src + p.src_off, p.n, lut, lr, L, C, s_coarse, c_nw, c_b0, c_b1);
     }
     const unsigned ball = __ballot_sync(0xFFFFFFFFu, tissue);
     const int cnt = __popc(ball);
@@ -357,7 +369,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_window(WindowArgs a) {
     }
     if (!tissue) stack_get(s_stk, s_stq, ns - 1 - __popc(~ball & lt), w, qi);
     ns -= 32 - cnt;
-    pass1_chunk(w, qi, true, lut, lr, NR1, NR2, L, C, g, s_queue, s_coarse, qn, c_nw, c_b0, c_b1);
+    pass1_chunk<PINV>(w, qi, true, lut, lr, NR1, NR2, L, C, g, s_queue, s_coarse, qn, c_nw, c_b0, c_b1);
   }
   __syncwarp();
   if (ns > 0) {   // the rest of the stack (fewer than 32)
@@ -365,11 +377,11 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_window(WindowArgs a) {
     unsigned w[12];
     unsigned qi = 0u;
     if (have) stack_get(s_stk, s_stq, (int)lane, w, qi);
-    pass1_chunk(w, qi, have, lut, lr, NR1, NR2, L, C, g, s_queue, s_coarse, qn, c_nw, c_b0, c_b1);
+    pass1_chunk<PINV>(w, qi, have, lut, lr, NR1, NR2, L, C, g, s_queue, s_coarse, qn, c_nw, c_b0, c_b1);
   }
   if (qn > 0) {
     __syncwarp();
-    drain_queue(s_queue, qn, g, lut, lr, L, C, s_coarse);
+    drain_queue<PINV>(s_queue, qn, g, lut, lr, L, C, s_coarse);
   }
   // per-thread counts are exact in FP32 (fewer than 2^24 pixels per thread)
   const u64 t_nw = block_sum((u64)lo_of(c_nw) + (u64)hi_of(c_nw), s_tmp);
@@ -404,6 +416,7 @@ struct SelectImageArgs {
   double tgt0, tgt1;
 };
 
+template <bool PINV>
 __global__ void __launch_bounds__(kPassThreads, 1) k_select_image(SelectImageArgs a) {
   if (*(volatile int*)&a.sel->all_resolved) return;   // uniform: every block returns
   extern __shared__ __align__(16) char s_dyn[];
@@ -416,7 +429,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_select_image(SelectImageArg
     rank[t] = __ldcg(&a.sel->rank[t]);
     active[t] = !__ldcg(&a.sel->resolved[t]);
   }
-  radix_select(a.src, s_dyn, L, a.sel, rank, active, a.ghist, s_hist, &a.sel->barrier, a.err,
+  radix_select<PINV>(a.src, s_dyn, L, a.sel, rank, active, a.ghist, s_hist, &a.sel->barrier, a.err,
                a.timeout_ns, a.tgt0, a.tgt1);
 }
 
@@ -433,6 +446,7 @@ struct SelectListArgs {
 
 // Percentile of the densities of a packed list of non-white pixels (the basis
 // sample, §3.1 item 2), radix select from scratch.
+template <bool PINV>
 __global__ void __launch_bounds__(kPassThreads, 1) k_select_list(SelectListArgs a) {
   extern __shared__ __align__(16) char s_dyn[];
   unsigned* s_hist = reinterpret_cast<unsigned*>(s_dyn + kLutSmemBytes);
@@ -453,7 +467,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_select_list(SelectListArgs 
   load_lut(a.m, s_dyn);
   const Lasso L = a.m->lasso;
   ListSource src{a.items, n};
-  radix_select(src, s_dyn, L, a.sel, rank, active, a.ghist, s_hist, &a.sel->barrier, a.err,
+  radix_select<PINV>(src, s_dyn, L, a.sel, rank, active, a.ghist, s_hist, &a.sel->barrier, a.err,
                a.timeout_ns, 1.0, 1.0);
 }
 
@@ -467,6 +481,7 @@ struct ReconArgs {
 };
 
 
+template <bool PINV>
 __global__ void __launch_bounds__(kPassThreads, 1) k_pass_recon(ReconArgs a) {
   extern __shared__ __align__(16) char s_dyn[];
   __shared__ float s_M[6];
@@ -488,7 +503,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_recon(ReconArgs a) {
   const f2 NR1 = pk(L.nrho1, L.nrho1), NR2 = pk(L.nrho2, L.nrho2);
   for_each_chunk<true, true>(a.g, [&](const unsigned (&w)[12], const ChunkPos& p) {
     unsigned o[12];
-    recon_chunk(w, lut, lr, P, NR1, NR2, L.kappa, K, o);
+    recon_chunk<PINV>(w, lut, lr, P, NR1, NR2, L.kappa, K, o);
     store_chunk(a.g, p, o);
   });
 }
@@ -501,6 +516,7 @@ struct DensityArgs {
   int64_t stride;   // elements between the two planes
 };
 
+template <bool PINV>
 __global__ void __launch_bounds__(kPassThreads, 1) k_pass_density(DensityArgs a) {
   extern __shared__ __align__(16) char s_dyn[];
   load_lut(a.m, s_dyn);
@@ -523,7 +539,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_density(DensityArgs a)
         unsigned aRA, aGA, aBA, aRB, aGB, aBB;
         pixel_addr(w, k, lr, aRA, aGA, aBA);
         pixel_addr(w, k + 1, lr, aRB, aGB, aBB);
-        solve_pair(lut, aRA, aGA, aBA, aRB, aGB, aBB, NR1, NR2, L.kappa, H1[q], H2[q]);
+        solve_pair<PINV>(lut, aRA, aGA, aBA, aRB, aGB, aBB, NR1, NR2, L.kappa, H1[q], H2[q]);
         H1[q] = mul2(H1[q], HS);     // exact: the scale is a power of two
         H2[q] = mul2(H2[q], HS);
       }
@@ -552,31 +568,53 @@ static int grid_of(const Context* c, int occ) {
   return c->num_sms * (occ > 0 ? occ : 1);
 }
 
+// Shared-memory limit of a kernel and its blocks per SM (the smaller over the
+// instantiations that share one grid size).
+template <class K>
+static int smem_attr(K* k, size_t smem) {
+  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+                 cudaSuccess ? SPCN_OK : SPCN_ERR_CUDA;
+}
+template <class K>
+static int occ_min(int* occ, K* k, int threads, size_t smem) {
+  int o = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, threads, smem) != cudaSuccess)
+    return SPCN_ERR_CUDA;
+  if (*occ == 0 || o < *occ) *occ = o;
+  return SPCN_OK;
+}
+
 int configure_pixel_kernels(Context* c) {
-  SPCN_CUDA_TRY(cudaFuncSetAttribute(k_pass_window<false>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWindowSmem));
-  SPCN_CUDA_TRY(cudaFuncSetAttribute(k_pass_window<true>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWindowSmem));
-  SPCN_CUDA_TRY(cudaFuncSetAttribute(k_pass_recon, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kLutSmemBytes));
-  SPCN_CUDA_TRY(cudaFuncSetAttribute(k_pass_density, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kLutSmemBytes));
-  SPCN_CUDA_TRY(cudaFuncSetAttribute(k_select_image, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kRadixSmem));
-  SPCN_CUDA_TRY(cudaFuncSetAttribute(k_select_list, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kRadixSmem));
-  SPCN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->occ_window, k_pass_window<false>,
-                                                              kPassThreads, kWindowSmem));
-  SPCN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->occ_recon, k_pass_recon,
-                                                              kPassThreads, kLutSmemBytes));
-  SPCN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->occ_density, k_pass_density,
-                                                              kPassThreads, kLutSmemBytes));
-  SPCN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->occ_select, k_select_image,
-                                                              kPassThreads, kRadixSmem));
-  SPCN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->occ_radix_list, k_select_list,
-                                                              kPassThreads, kRadixSmem));
-  SPCN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->occ_debug, k_debug_barrier,
-                                                              128, 0));
+  int rc = 0;
+  rc |= smem_attr(k_pass_window<false, false>, kWindowSmem);
+  rc |= smem_attr(k_pass_window<true, false>, kWindowSmem);
+  rc |= smem_attr(k_pass_window<false, true>, kWindowSmem);
+  rc |= smem_attr(k_pass_window<true, true>, kWindowSmem);
+  rc |= smem_attr(k_pass_recon<false>, kLutSmemBytes);
+  rc |= smem_attr(k_pass_recon<true>, kLutSmemBytes);
+  rc |= smem_attr(k_pass_density<false>, kLutSmemBytes);
+  rc |= smem_attr(k_pass_density<true>, kLutSmemBytes);
+  rc |= smem_attr(k_select_image<false>, kRadixSmem);
+  rc |= smem_attr(k_select_image<true>, kRadixSmem);
+  rc |= smem_attr(k_select_list<false>, kRadixSmem);
+  rc |= smem_attr(k_select_list<true>, kRadixSmem);
+  if (rc) return SPCN_ERR_CUDA;
+  c->occ_window = c->occ_recon = c->occ_density = c->occ_select = c->occ_radix_list = 0;
+  c->occ_debug = 0;
+  rc |= occ_min(&c->occ_window, k_pass_window<false, false>, kPassThreads, kWindowSmem);
+  rc |= occ_min(&c->occ_window, k_pass_window<true, false>, kPassThreads, kWindowSmem);
+  rc |= occ_min(&c->occ_window, k_pass_window<false, true>, kPassThreads, kWindowSmem);
+  rc |= occ_min(&c->occ_window, k_pass_window<true, true>, kPassThreads, kWindowSmem);
+  rc |= occ_min(&c->occ_recon, k_pass_recon<false>, kPassThreads, kLutSmemBytes);
+  rc |= occ_min(&c->occ_recon, k_pass_recon<true>, kPassThreads, kLutSmemBytes);
+  rc |= occ_min(&c->occ_density, k_pass_density<false>, kPassThreads, kLutSmemBytes);
+  rc |= occ_min(&c->occ_density, k_pass_density<true>, kPassThreads, kLutSmemBytes);
+  rc |= occ_min(&c->occ_select, k_select_image<false>, kPassThreads, kRadixSmem);
+  rc |= occ_min(&c->occ_select, k_select_image<true>, kPassThreads, kRadixSmem);
+  rc |= occ_min(&c->occ_radix_list, k_select_list<false>, kPassThreads, kRadixSmem);
+  rc |= occ_min(&c->occ_radix_list, k_select_list<true>, kPassThreads, kRadixSmem);
+  rc |= occ_min(&c->occ_debug, k_debug_barrier, 128, 0);
+  if (rc) return SPCN_ERR_CUDA;
   if (c->occ_window < 1 || c->occ_recon < 1 || c->occ_density < 1 || c->occ_select < 1 ||
       c->occ_radix_list < 1 || c->occ_debug < 1)
     return SPCN_ERR_CUDA;
@@ -671,7 +709,7 @@ void white_test_consts(int T, unsigned* wm, unsigned* we) {
 // The window comes from a host hint, or (wdev) from device memory.
 static int percentile_passes(Context* c, const Geometry& g, const Model* m, int white_thresh,
                              double pct, const Window& w, const Window* wdev,
-                             const double* tgt_p99, cudaStream_t st) {
+                             const double* tgt_p99, cudaStream_t st, bool pinv) {
   WindowArgs a;
   a.g = g;
   a.m = m;
@@ -694,10 +732,15 @@ static int percentile_passes(Context* c, const Geometry& g, const Model* m, int 
   if (nb1) SPCN_CUDA_TRY(cudaMemsetAsync(c->fine + kWinBins, 0, sizeof(u64) * nb1, st));
   {
     TimedLaunch tl(c, SPCN_KERNEL_PASS1, st);
-    if (wdev)
-      k_pass_window<true><<<grid_of(c, c->occ_window), kPassThreads, kWindowSmem, st>>>(a);
+    const int grid = grid_of(c, c->occ_window);
+    if (wdev && pinv)
+      k_pass_window<true, true><<<grid, kPassThreads, kWindowSmem, st>>>(a);
+    else if (wdev)
+      k_pass_window<true, false><<<grid, kPassThreads, kWindowSmem, st>>>(a);
+    else if (pinv)
+      k_pass_window<false, true><<<grid, kPassThreads, kWindowSmem, st>>>(a);
     else
-      k_pass_window<false><<<grid_of(c, c->occ_window), kPassThreads, kWindowSmem, st>>>(a);
+      k_pass_window<false, false><<<grid, kPassThreads, kWindowSmem, st>>>(a);
   }
   SPCN_LAUNCH_CHECK(c);
 
@@ -714,8 +757,9 @@ static int percentile_passes(Context* c, const Geometry& g, const Model* m, int 
   void* args[] = {&s};
   {
     TimedLaunch tl(c, SPCN_KERNEL_SELECT, st);
-    SPCN_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_select_image, grid_of(c, c->occ_select),
-                                              kPassThreads, args, kRadixSmem, st));
+    SPCN_CUDA_TRY(cudaLaunchCooperativeKernel(
+        pinv ? (void*)k_select_image<true> : (void*)k_select_image<false>,
+        grid_of(c, c->occ_select), kPassThreads, args, kRadixSmem, st));
   }
   c->launches++;
   return SPCN_OK;
@@ -723,20 +767,21 @@ static int percentile_passes(Context* c, const Geometry& g, const Model* m, int 
 
 int launch_percentile_passes(Context* c, const Geometry& g, const Model* m, int white_thresh,
                              double pct, const double* hint, int hexp, const double* tgt_p99,
-                             cudaStream_t st) {
+                             cudaStream_t st, bool pinv) {
   const double hs = ldexp(1.0, -hexp);
   const Window w = window_for(hint ? hint[0] * hs : 0.0, hint ? hint[1] * hs : 0.0);
-  return percentile_passes(c, g, m, white_thresh, pct, w, nullptr, tgt_p99, st);
+  return percentile_passes(c, g, m, white_thresh, pct, w, nullptr, tgt_p99, st, pinv);
 }
 
 int launch_percentile_passes_dev(Context* c, const Geometry& g, const Model* m, int white_thresh,
                                  double pct, const Window* wdev, const double* tgt_p99,
-                                 cudaStream_t st) {
-  return percentile_passes(c, g, m, white_thresh, pct, window_for(0.0, 0.0), wdev, tgt_p99, st);
+                                 cudaStream_t st, bool pinv) {
+  return percentile_passes(c, g, m, white_thresh, pct, window_for(0.0, 0.0), wdev, tgt_p99, st,
+                           pinv);
 }
 
 int launch_select_list(Context* c, const uint32_t* items, const u64* n_dev, const Model* m,
-                       SelectState* sel, u64* ghist, double pct, cudaStream_t st) {
+                       SelectState* sel, u64* ghist, double pct, cudaStream_t st, bool pinv) {
   SelectListArgs a;
   a.items = items;
   a.n_dev = n_dev;
@@ -748,14 +793,15 @@ int launch_select_list(Context* c, const uint32_t* items, const u64* n_dev, cons
   a.pct = pct;
   SPCN_CUDA_TRY(cudaMemsetAsync(sel, 0, sizeof(SelectState), st));
   void* args[] = {&a};
-  SPCN_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_select_list, grid_of(c, c->occ_radix_list),
-                                            kPassThreads, args, kRadixSmem, st));
+  SPCN_CUDA_TRY(cudaLaunchCooperativeKernel(
+      pinv ? (void*)k_select_list<true> : (void*)k_select_list<false>,
+      grid_of(c, c->occ_radix_list), kPassThreads, args, kRadixSmem, st));
   c->launches++;
   return SPCN_OK;
 }
 
 int launch_recon(Context* c, const Geometry& g, const Model* m, const float* Wt, const float* i0t,
-                 cudaStream_t st) {
+                 cudaStream_t st, bool pinv) {
   ReconArgs a;
   a.g = g;
   a.m = m;
@@ -764,14 +810,17 @@ int launch_recon(Context* c, const Geometry& g, const Model* m, const float* Wt,
   for (int i = 0; i < 3; ++i) a.l2i0[i] = (float)log2((double)i0t[i]);
   {
     TimedLaunch tl(c, SPCN_KERNEL_PASS2, st);
-    k_pass_recon<<<grid_of(c, c->occ_recon), kPassThreads, kLutSmemBytes, st>>>(a);
+    if (pinv)
+      k_pass_recon<true><<<grid_of(c, c->occ_recon), kPassThreads, kLutSmemBytes, st>>>(a);
+    else
+      k_pass_recon<false><<<grid_of(c, c->occ_recon), kPassThreads, kLutSmemBytes, st>>>(a);
   }
   SPCN_LAUNCH_CHECK(c);
   return SPCN_OK;
 }
 
 int launch_density(Context* c, const Geometry& g, const Model* m, float* H, int64_t stride,
-                   cudaStream_t st) {
+                   cudaStream_t st, bool pinv) {
   DensityArgs a;
   a.g = g;
   a.m = m;
@@ -779,7 +828,10 @@ int launch_density(Context* c, const Geometry& g, const Model* m, float* H, int6
   a.stride = stride;
   {
     TimedLaunch tl(c, SPCN_KERNEL_DENSITY, st);
-    k_pass_density<<<grid_of(c, c->occ_density), kPassThreads, kLutSmemBytes, st>>>(a);
+    if (pinv)
+      k_pass_density<true><<<grid_of(c, c->occ_density), kPassThreads, kLutSmemBytes, st>>>(a);
+    else
+      k_pass_density<false><<<grid_of(c, c->occ_density), kPassThreads, kLutSmemBytes, st>>>(a);
   }
   SPCN_LAUNCH_CHECK(c);
   return SPCN_OK;

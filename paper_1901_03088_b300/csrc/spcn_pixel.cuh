@@ -195,6 +195,7 @@ __device__ __forceinline__ void window_hit(const WindowConst& C, unsigned* s_coa
 // with packed FMAs.  The number of windows a pixel falls in (0, 1 or 2) is
 // packed base 4 into `mask` (pixel pair p at digit 7-p, even pixels in the
 // low lane, odd pixels in the high lane): exact small integers in FP32.
+template <bool PINV = false>
 __device__ __forceinline__ void window_chunk(const unsigned (&w)[12], const char* lut,
                                              unsigned lr, f2 NR1, f2 NR2, float kappa,
                                              const WindowConst& a, f2& c_nw, f2& c_b0, f2& c_b1,
@@ -208,7 +209,7 @@ __device__ __forceinline__ void window_chunk(const unsigned (&w)[12], const char
     pixel_addr(w, kA, lr, aRA, aGA, aBA);
     pixel_addr(w, kB, lr, aRB, aGB, aBB);
     f2 H1, H2;
-    solve_pair(lut, aRA, aGA, aBA, aRB, aGB, aBB, NR1, NR2, kappa, H1, H2);
+    solve_pair<PINV>(lut, aRA, aGA, aBA, aRB, aGB, aBB, NR1, NR2, kappa, H1, H2);
     const bool nwA = min(min(aRA, aGA), aBA) < a.wthr;
     const bool nwB = min(min(aRB, aGB), aBB) < a.wthr;
     const f2 NW = pk(nwA ? 1.f : 0.f, nwB ? 1.f : 0.f);
@@ -311,7 +312,7 @@ struct ListSource {
 // grid barriers (counter `bar`, zeroed before the launch).  Block 0 writes the
 // keys, the percentiles and the scale factors.  Returns false if a wait gave
 // up (the error is recorded).
-template <class Src>
+template <bool PINV, class Src>
 __device__ bool radix_select(const Src& src, const char* lut, const Lasso& L, SelectState* s,
                              const u64 (&rank)[kTracks], const int (&active)[kTracks],
                              u64* ghist, unsigned* s_hist, unsigned* bar, int* err,
@@ -350,8 +351,9 @@ __device__ bool radix_select(const Src& src, const char* lut, const Lasso& L, Se
       own[t] = ((t & 1) && act[t] && act[t - 1] && pre[t] == pre[t - 1]) ? t - 1 : t;
     src.for_each([&](unsigned aR, unsigned aG, unsigned aB, bool nw) {
       float h1, h2;
-      solve_one(lut, aR, aG, aB, L, h1, h2);
-      const unsigned key[2] = {__float_as_uint(h1), __float_as_uint(h2)};
+      solve_one<PINV>(lut, aR, aG, aB, L, h1, h2);
+      const unsigned key[2] = {PINV ? signed_key(__float_as_uint(h1)) : __float_as_uint(h1),
+                               PINV ? signed_key(__float_as_uint(h2)) : __float_as_uint(h2)};
       const unsigned live = __activemask();
 #pragma unroll
       for (int t = 0; t < kTracks; ++t) {
@@ -388,7 +390,7 @@ __device__ bool radix_select(const Src& src, const char* lut, const Lasso& L, Se
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     for (int t = 0; t < kTracks; ++t)
-      if (s_act[t]) { s->key[t] = s_prefix[t]; s->resolved[t] = 1; }
+      if (s_act[t]) { s->key[t] = PINV ? signed_key_inv(s_prefix[t]) : s_prefix[t]; s->resolved[t] = 1; }
     finish_percentiles(s, tgt0, tgt1, L.hscale);
     __threadfence();
     s->all_resolved = 1;
@@ -438,6 +440,7 @@ __device__ __forceinline__ float od_ld(const char* lut, unsigned off) {
 }
 
 // The closed-form H-step of two pixels from the optical-density table.
+template <bool PINV = false>
 __device__ __forceinline__ void solve_pair_od(const char* lut, unsigned aRA, unsigned aGA,
                                               unsigned aBA, unsigned aRB, unsigned aGB,
                                               unsigned aBB, const ProjConst& P, f2 NR1, f2 NR2,
@@ -447,6 +450,11 @@ __device__ __forceinline__ void solve_pair_od(const char* lut, unsigned aRA, uns
   const f2 VR = pk(vRA, vRB), VG = pk(vGA, vGB);
   const f2 S1 = fma2(P.A11, VG, fma2(P.A10, VR, P.B1));
   const f2 S2 = fma2(P.A21, VG, fma2(P.A20, VR, P.B2));
+  if (PINV) {   // pinv(W) v with FMAs (B = 0): signed, no sparsity
+    H1 = pk(fmaf(P.a12, vBA, lo_of(S1)), fmaf(P.a12, vBB, hi_of(S1)));
+    H2 = pk(fmaf(P.a22, vBA, lo_of(S2)), fmaf(P.a22, vBB, hi_of(S2)));
+    return;
+  }
   const float D1A = fma_sat(P.a12, vBA, lo_of(S1)), D1B = fma_sat(P.a12, vBB, hi_of(S1));
   const float D2A = fma_sat(P.a22, vBA, lo_of(S2)), D2B = fma_sat(P.a22, vBB, hi_of(S2));
   const f2 P1 = pk(D1A, D1B), P2 = pk(D2A, D2B);
@@ -459,6 +467,9 @@ __device__ __forceinline__ void solve_pair_od(const char* lut, unsigned aRA, uns
 }
 
 // Pass 2 on one chunk (optical-density table, lane register lane_reg_od()).
+// With the lasso every exponent is <= log2(i0) <= 8, so the value stays in
+// [0, 255]; signed pseudo-inverse densities can exceed i0 and are clamped.
+template <bool PINV = false>
 __device__ __forceinline__ void recon_chunk(const unsigned (&w)[12], const char* lut,
                                             unsigned lr, const ProjConst& P, f2 NR1, f2 NR2,
                                             float kappa, const ReconConst& K, unsigned (&o)[12]) {
@@ -470,13 +481,18 @@ __device__ __forceinline__ void recon_chunk(const unsigned (&w)[12], const char*
     pixel_addr(w, kA, lr, aRA, aGA, aBA);
     pixel_addr(w, kB, lr, aRB, aGB, aBB);
     f2 H1, H2;
-    solve_pair_od(lut, aRA, aGA, aBA, aRB, aGB, aBB, P, NR1, NR2, kappa, H1, H2);
+    solve_pair_od<PINV>(lut, aRA, aGA, aBA, aRB, aGB, aBB, P, NR1, NR2, kappa, H1, H2);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       // Eq. 3-4: i' = i0_t 2^(-log2e sum_j W_t[c,j] s_j h_j)
       const f2 E = fma2(K.M1[c], H1, fma2(K.M2[c], H2, K.L2[c]));
       // round half to even: adding 1.5*2^23 leaves round(x) in the low bits
-      const f2 X = add2(pk(ex2_approx(lo_of(E)), ex2_approx(hi_of(E))), pk(12582912.0f, 12582912.0f));
+      float xa = ex2_approx(lo_of(E)), xb = ex2_approx(hi_of(E));
+      if (PINV) {
+        xa = fminf(xa, 255.f);
+        xb = fminf(xb, 255.f);
+      }
+      const f2 X = add2(pk(xa, xb), pk(12582912.0f, 12582912.0f));
       y[3 * kA + c] = __float_as_uint(lo_of(X));
       y[3 * kB + c] = __float_as_uint(hi_of(X));
     }
@@ -574,6 +590,6 @@ int launch_scale_from_basis(Context* c, const Model* m, const SelectState* sampl
                             const int* basis_status, const double* tgt, cudaStream_t st);
 int launch_percentile_passes_dev(Context* c, const Geometry& g, const Model* m, int white_thresh,
                                  double pct, const Window* wdev, const double* tgt_p99,
-                                 cudaStream_t st);
+                                 cudaStream_t st, bool pinv = false);
 
 }  // namespace spcn

@@ -176,3 +176,101 @@ def test_flag_validation(spcn, ctx):
     out = torch.empty_like(img)
     with pytest.raises(spcn.SpcnError):
         spcn.normalize_batched(ctx, [img], [st], st, [out], spcn.params(flags=spcn.FLAG_P99_SAMPLED))
+
+
+# ---------------------------------------------------------------- SPCN_FLAG_H_PINV (§2.1)
+def pinv_stats(spcn, img_seed=1310):
+    W = synth.stain_basis(img_seed)
+    i0 = np.array([250.0, 247.0, 253.0])
+    return W, i0, spcn.Stats.from_values(W, i0)
+
+
+def test_pinv_densities_match_oracle(spcn, ctx):
+    img = synth.make_image(130, 257, 1310)
+    W, i0, st = pinv_stats(spcn)
+    p = spcn.params(flags=spcn.FLAG_H_PINV)
+    Hg = ctx.stain_densities(to_dev(img), st, p).cpu().numpy()
+    Ho = O.stain_densities(img, np.float32(W).astype(np.float64), np.float32(i0).astype(np.float64),
+                           h_solve="pinv")
+    assert (Ho < 0).mean() > 0.05                      # signed densities really occur
+    assert np.all(np.abs(Hg - Ho) <= 1e-5 * np.maximum(np.abs(Ho), 1.0)), np.max(np.abs(Hg - Ho))
+
+
+@pytest.mark.parametrize("pct,hint", [(99.0, "exact"), (99.0, "none"), (1.0, "none"), (1.0, "exact"),
+                                      (50.0, "exact")])
+def test_pinv_percentile_bit_exact(spcn, ctx, pct, hint):
+    img = synth.make_image(300, 411, 1311)
+    W, i0, st = pinv_stats(spcn)
+    p = spcn.params(flags=spcn.FLAG_H_PINV, stain_pct=pct)
+    dev = to_dev(img)
+    Hg = ctx.stain_densities(dev, st, p).cpu().numpy()
+    nw = O.nonwhite_mask(img.reshape(-1, 3))
+    ref = [type7(Hg[j][nw], pct) for j in range(2)]
+    if pct == 1.0:
+        assert ref[0] < 0 or ref[1] < 0                # the signed keys are exercised
+    if hint == "exact":
+        st.p99[0], st.p99[1] = ref
+    got = ctx.stain_percentile(dev, st, p)
+    assert got[0] == ref[0] and got[1] == ref[1], (got, ref)
+    o = O.stain_percentile(img, np.float32(W).astype(np.float64), np.float32(i0).astype(np.float64),
+                           O.Params(h_solve="pinv", stain_pct=pct))
+    for j in range(2):
+        assert abs(got[j] - o[j]) <= 1e-5 * max(abs(o[j]), 1.0)
+
+
+def test_pinv_normalize_matches_oracle(spcn, ctx):
+    img = synth.make_image(256, 320, 1312)
+    tgt_img = synth.make_image(128, 128, 1)
+    pe = spcn.params(sample_mode="all")
+    src = ctx.estimate_basis(to_dev(img), pe)
+    tgt = ctx.estimate_basis(to_dev(tgt_img), pe)
+    p = spcn.params(flags=spcn.FLAG_H_PINV)
+    tgt.p99[0], tgt.p99[1] = ctx.stain_percentile(to_dev(tgt_img), tgt, p)
+    out, p99 = ctx.normalize(to_dev(img), src, tgt, p, return_p99=True)
+    so = O.Stats(W=np.array(src.basis, dtype=np.float32).astype(np.float64),
+                 i0=np.float32(src.i0).astype(np.float64), p99=np.array(p99))
+    to = O.Stats(W=np.array(tgt.basis, dtype=np.float32).astype(np.float64),
+                 i0=np.float32(tgt.i0).astype(np.float64), p99=np.array(tgt.p99[:]))
+    ref = O.normalize(img, so, to, h_solve="pinv")
+    op = O.stain_percentile(img, so.W, so.i0, O.Params(h_solve="pinv"))
+    for j in range(2):
+        assert abs(p99[j] - op[j]) <= 1e-5 * max(abs(op[j]), 1.0)
+    close_uint8(out.cpu().numpy(), ref)
+    # pixels the pseudo-inverse makes brighter than the target white are clamped
+    raw = O.normalize_float(img, so.W, so.i0, so.p99, to.W, to.i0, to.p99, h_solve="pinv")
+    assert np.any(raw > 255.0)
+
+
+def test_pinv_estimate_and_one_call_path(spcn, ctx):
+    img = synth.make_image(600, 700, 1313, blobs=True)
+    tgt = ctx.estimate_basis(to_dev(synth.make_image(128, 128, 1)), spcn.params(sample_mode="all"))
+    for kw in (dict(sample_mode="all"), dict(sample_mode="patches", n_patches=9, patch_size=64,
+                                             seed=2)):
+        o = O.estimate_basis(img, O.Params(h_solve="pinv", **{k: v for k, v in kw.items()}))
+        p = spcn.params(flags=spcn.FLAG_H_PINV, **kw)
+        g = ctx.estimate_basis(to_dev(img), p)
+        assert np.max(np.abs(np.array(g.basis) - o.W)) <= 1e-5
+        for j in range(2):
+            assert abs(g.p99[j] - o.p99[j]) <= 1e-4 * max(abs(o.p99[j]), 1.0)
+        out1, p99 = ctx.normalize(to_dev(img), g, tgt, p, return_p99=True)
+        out2, st2 = ctx.normalize_estimated(to_dev(img), tgt, p, return_stats=True)
+        assert torch.equal(out1, out2) and st2.p99[0] == p99[0] and st2.p99[1] == p99[1]
+    # with the patch median
+    kw = dict(sample_mode="patches", n_patches=9, patch_size=64, seed=2)
+    o = O.estimate_basis(img, O.Params(h_solve="pinv", p99_patch_median=True, **kw))
+    g = ctx.estimate_basis(to_dev(img), spcn.params(
+        flags=spcn.FLAG_H_PINV | spcn.FLAG_P99_PATCH_MEDIAN, **kw))
+    for j in range(2):
+        assert abs(g.p99[j] - o.p99[j]) <= 1e-4 * max(abs(o.p99[j]), 1.0)
+
+
+def test_pinv_rejected_where_not_available(spcn, ctx):
+    img = to_dev(synth.make_image(64, 64, 1314))
+    st = ctx.estimate_basis(img, spcn.params(sample_mode="all"))
+    out = torch.empty_like(img)
+    with pytest.raises(spcn.SpcnError):
+        spcn.normalize_batched(ctx, [img], [st], st, [out], spcn.params(flags=spcn.FLAG_H_PINV))
+    x = torch.rand((1, 3, 8, 8), device="cuda") * 255
+    wt = torch.tensor(np.array(st.basis, dtype=np.float32), device="cuda")
+    with pytest.raises(spcn.SpcnError):
+        spcn.normalize_f32(ctx, x, wt, [st], st, p=spcn.params(flags=spcn.FLAG_H_PINV))
