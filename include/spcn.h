@@ -178,6 +178,20 @@ int spcn_stain_densities(void* ctx, const spcn_image* img, const spcn_stats* st,
                          const spcn_params* params, float* H, int64_t h_stride,
                          void* stream);
 
+/* Stain separation of a whole image in one stream-ordered call (the
+ * §4.3 use of the densities as a module of their own): the work of
+ * spcn_estimate_basis, then spcn_stain_densities with the estimated basis
+ * and i0, whose table stays on the device (no host round trip).  H, h_stride
+ * as for spcn_stain_densities; the values are those of the two calls in
+ * sequence.  If st_out (host) is non-NULL the call blocks and returns the
+ * estimated statistics there (p99: the sample percentile); otherwise it is
+ * asynchronous and an estimation error is returned by the next synchronising
+ * call (the densities of a failed estimation are zeros).
+ * Errors: as spcn_estimate_basis and spcn_stain_densities. */
+int spcn_stain_densities_estimated(void* ctx, const spcn_image* img, const spcn_params* params,
+                                   float* H, int64_t h_stride, spcn_stats* st_out,
+                                   void* stream);
+
 /* Normalise `src` to the target statistics (Eq. 1-4): pass 1 computes the
  * source's exact non-white P99 per stain on the device (src_st->p99 only
  * guides the search window), pass 2 recomputes every pixel's densities,

@@ -516,6 +516,36 @@ int spcn_normalize_estimated(void* ctx, const spcn_image* src, const spcn_stats*
   return SPCN_OK;
 }
 
+int spcn_stain_densities_estimated(void* ctx, const spcn_image* img, const spcn_params* params,
+                                   float* H, int64_t h_stride, spcn_stats* st_out,
+                                   void* stream) {
+  if (!ctx || !image_ok(img) || !params_ok(params) || !H) return SPCN_ERR_INVALID_ARG;
+  if (h_stride < (int64_t)img->width * img->height) return SPCN_ERR_INVALID_ARG;
+  Context* c = static_cast<Context*>(ctx);
+  DeviceGuard guard(c->device);
+  if (!guard.ok) return SPCN_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc = launch_estimate_basis(c, img, params, s);
+  if (rc) return rc;
+  // the basis estimation's final table is the density table
+  rc = launch_check_basis(c, c->model_b, &c->bs->status, s);
+  if (rc) return rc;
+  const Geometry g = make_geometry(img, nullptr, 0);
+  rc = launch_density(c, g, c->model_b, H, h_stride, s, (params->flags & SPCN_FLAG_H_PINV) != 0);
+  if (rc) return rc;
+  if (st_out) {
+    memset(st_out, 0, sizeof(*st_out));
+    rc = finish_estimate_basis(c, st_out, s);   // waits; clears the error word it reports
+    if (rc) return rc;
+    int err = 0;
+    rc = read_error(c, s, &err);
+    if (rc) return rc;
+    st_out->status = err;
+    return err;
+  }
+  return SPCN_OK;
+}
+
 int spcn_synchronize(void* ctx, void* stream) {
   if (!ctx) return SPCN_ERR_INVALID_ARG;
   Context* c = static_cast<Context*>(ctx);

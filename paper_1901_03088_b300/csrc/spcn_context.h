@@ -122,6 +122,8 @@ constexpr size_t kWindowSmem = kLutSmemBytes + sizeof(unsigned) * 2 * kWinGroups
                                sizeof(uint2) * 2 * kPassThreads +   // per-warp hit queues (64 each)
                                (3 * sizeof(uint4) + sizeof(unsigned)) * kChunkStack * (kPassThreads / 32);
 constexpr size_t kRadixSmem = kLutSmemBytes + sizeof(unsigned) * kTracks * kRadixBins;
+// the density pass stages one plane of a warp's 512 pixels (2 KB per warp)
+constexpr size_t kDensitySmem = kLutSmemBytes + 2048 * (kPassThreads / 32);
 
 int configure_pixel_kernels(Context* c);
 int configure_basis_kernels(Context* c);

@@ -516,46 +516,94 @@ struct DensityArgs {
   int64_t stride;   // elements between the two planes
 };
 
+// Densities of the pixels of one chunk (lane), scaled back (exact: the scale
+// is a power of two): h1[k], h2[k] for pixel k of the chunk.
+template <bool PINV>
+__device__ __forceinline__ void density_chunk(const unsigned (&w)[12], const char* lut,
+                                              unsigned lr, f2 NR1, f2 NR2, float kappa, f2 HS,
+                                              float (&h1)[kChunk], float (&h2)[kChunk]) {
+#pragma unroll
+  for (int q = 0; q < kChunk / 2; ++q) {
+    unsigned aRA, aGA, aBA, aRB, aGB, aBB;
+    pixel_addr(w, 2 * q, lr, aRA, aGA, aBA);
+    pixel_addr(w, 2 * q + 1, lr, aRB, aGB, aBB);
+    f2 H1, H2;
+    solve_pair<PINV>(lut, aRA, aGA, aBA, aRB, aGB, aBB, NR1, NR2, kappa, H1, H2);
+    H1 = mul2(H1, HS);
+    H2 = mul2(H2, HS);
+    h1[2 * q] = lo_of(H1);
+    h1[2 * q + 1] = hi_of(H1);
+    h2[2 * q] = lo_of(H2);
+    h2[2 * q + 1] = hi_of(H2);
+  }
+}
+
+// One plane of a warp's 32 consecutive full chunks (512 pixels from px0),
+// staged through shared memory so that each store writes 512 contiguous
+// bytes (the lanes' own 64-byte runs would each half-fill 32 sectors).
+__device__ __forceinline__ void store_plane_coalesced(float* dst, const float (&h)[kChunk],
+                                                      float4* stage, unsigned lane) {
+  float4* mine = stage + 4 * lane;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) mine[v] = make_float4(h[4 * v], h[4 * v + 1], h[4 * v + 2], h[4 * v + 3]);
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < 4; ++k) __stcs(reinterpret_cast<float4*>(dst) + 32 * k + lane, stage[32 * k + lane]);
+  __syncwarp();
+}
+
 template <bool PINV>
 __global__ void __launch_bounds__(kPassThreads, 1) k_pass_density(DensityArgs a) {
   extern __shared__ __align__(16) char s_dyn[];
+  float4* stage = reinterpret_cast<float4*>(s_dyn + kLutSmemBytes) + (threadIdx.x >> 5) * 128;
   load_lut(a.m, s_dyn);
   const char* lut = s_dyn;
   const unsigned lr = lane_reg();
+  const unsigned lane = threadIdx.x & 31u;
   const Lasso L = a.m->lasso;
   const f2 NR1 = pk(L.nrho1, L.nrho1), NR2 = pk(L.nrho2, L.nrho2);
   const f2 HS = pk(L.hscale, L.hscale);
   const bool vec_h = ((reinterpret_cast<uintptr_t>(a.H) & 15u) == 0) && ((a.stride & 3) == 0);
-  for_each_chunk<true, true>(a.g, [&](const unsigned (&w)[12], const ChunkPos& p) {
-    float* d0 = a.H + p.px;
-    float* d1 = a.H + a.stride + p.px;
-    const bool vec = p.n == kChunk && vec_h && (p.px & 3) == 0;
+  const Geometry g = a.g;
+  const u64 stride = (u64)gridDim.x * blockDim.x;
+  // warp-uniform loop: a warp handles 32 consecutive chunks per iteration
+  for (u64 base = (u64)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < g.nchunks;
+       base += stride) {
+    const u64 q = base + lane;
+    const bool have = q < g.nchunks;
+    ChunkPos p;
+    p.px = 0;
+    p.n = 0;
+    float h1[kChunk], h2[kChunk];
+    if (have) {
+      p = chunk_pos(g, q);
+      unsigned w[12];
+      load_chunk<true>(g, p, w);
+      density_chunk<PINV>(w, lut, lr, NR1, NR2, L.kappa, HS, h1, h2);
+    }
+    const u64 px0 = __shfl_sync(0xFFFFFFFFu, p.px, 0);
+    const bool run = __all_sync(0xFFFFFFFFu, have && p.n == kChunk && p.px == px0 + 16u * lane);
+    if (run && vec_h && (px0 & 3) == 0) {
+      store_plane_coalesced(a.H + px0, h1, stage, lane);
+      store_plane_coalesced(a.H + a.stride + px0, h2, stage, lane);
+    } else if (have) {
+      float* d0 = a.H + p.px;
+      float* d1 = a.H + a.stride + p.px;
+      if (p.n == kChunk && vec_h && (p.px & 3) == 0) {
 #pragma unroll
-    for (int v = 0; v < kChunk / 4; ++v) {
-      f2 H1[2], H2[2];
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const int k = 4 * v + 2 * q;
-        unsigned aRA, aGA, aBA, aRB, aGB, aBB;
-        pixel_addr(w, k, lr, aRA, aGA, aBA);
-        pixel_addr(w, k + 1, lr, aRB, aGB, aBB);
-        solve_pair<PINV>(lut, aRA, aGA, aBA, aRB, aGB, aBB, NR1, NR2, L.kappa, H1[q], H2[q]);
-        H1[q] = mul2(H1[q], HS);     // exact: the scale is a power of two
-        H2[q] = mul2(H2[q], HS);
-      }
-      const float4 h1 = make_float4(lo_of(H1[0]), hi_of(H1[0]), lo_of(H1[1]), hi_of(H1[1]));
-      const float4 h2 = make_float4(lo_of(H2[0]), hi_of(H2[0]), lo_of(H2[1]), hi_of(H2[1]));
-      if (vec) {
-        __stcs(reinterpret_cast<float4*>(d0) + v, h1);
-        __stcs(reinterpret_cast<float4*>(d1) + v, h2);
+        for (int v = 0; v < 4; ++v) {
+          __stcs(reinterpret_cast<float4*>(d0) + v,
+                 make_float4(h1[4 * v], h1[4 * v + 1], h1[4 * v + 2], h1[4 * v + 3]));
+          __stcs(reinterpret_cast<float4*>(d1) + v,
+                 make_float4(h2[4 * v], h2[4 * v + 1], h2[4 * v + 2], h2[4 * v + 3]));
+        }
       } else {
-        const float a1[4] = {h1.x, h1.y, h1.z, h1.w}, a2[4] = {h2.x, h2.y, h2.z, h2.w};
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-          if (4 * v + k < p.n) { d0[4 * v + k] = a1[k]; d1[4 * v + k] = a2[k]; }
+        for (int k = 0; k < kChunk; ++k)
+          if (k < p.n) { d0[k] = h1[k]; d1[k] = h2[k]; }
       }
     }
-  });
+  }
 }
 
 // ------------------------------------------------------------ failure-detection hook
@@ -592,8 +640,8 @@ int configure_pixel_kernels(Context* c) {
   rc |= smem_attr(k_pass_window<true, true>, kWindowSmem);
   rc |= smem_attr(k_pass_recon<false>, kLutSmemBytes);
   rc |= smem_attr(k_pass_recon<true>, kLutSmemBytes);
-  rc |= smem_attr(k_pass_density<false>, kLutSmemBytes);
-  rc |= smem_attr(k_pass_density<true>, kLutSmemBytes);
+  rc |= smem_attr(k_pass_density<false>, kDensitySmem);
+  rc |= smem_attr(k_pass_density<true>, kDensitySmem);
   rc |= smem_attr(k_select_image<false>, kRadixSmem);
   rc |= smem_attr(k_select_image<true>, kRadixSmem);
   rc |= smem_attr(k_select_list<false>, kRadixSmem);
@@ -607,8 +655,8 @@ int configure_pixel_kernels(Context* c) {
   rc |= occ_min(&c->occ_window, k_pass_window<true, true>, kPassThreads, kWindowSmem);
   rc |= occ_min(&c->occ_recon, k_pass_recon<false>, kPassThreads, kLutSmemBytes);
   rc |= occ_min(&c->occ_recon, k_pass_recon<true>, kPassThreads, kLutSmemBytes);
-  rc |= occ_min(&c->occ_density, k_pass_density<false>, kPassThreads, kLutSmemBytes);
-  rc |= occ_min(&c->occ_density, k_pass_density<true>, kPassThreads, kLutSmemBytes);
+  rc |= occ_min(&c->occ_density, k_pass_density<false>, kPassThreads, kDensitySmem);
+  rc |= occ_min(&c->occ_density, k_pass_density<true>, kPassThreads, kDensitySmem);
   rc |= occ_min(&c->occ_select, k_select_image<false>, kPassThreads, kRadixSmem);
   rc |= occ_min(&c->occ_select, k_select_image<true>, kPassThreads, kRadixSmem);
   rc |= occ_min(&c->occ_radix_list, k_select_list<false>, kPassThreads, kRadixSmem);
@@ -673,6 +721,21 @@ __global__ void k_scale_from_basis(const Model* m, const SelectState* sample_sel
   if (st != SPCN_OK) record_error(err, st);
   set_given_percentiles(s, st == SPCN_OK ? sample_sel->p99[0] : 0.0,
                         st == SPCN_OK ? sample_sel->p99[1] : 0.0, t0, t1);
+}
+
+// A failed basis estimation left on the device goes to the error word (for
+// calls whose later kernels do not read its percentile).
+__global__ void k_check_basis(const Model* m, const int* basis_status, int* err) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  int st = *basis_status;
+  if (st == SPCN_OK) st = m->status;
+  if (st != SPCN_OK) record_error(err, st);
+}
+
+int launch_check_basis(Context* c, const Model* m, const int* basis_status, cudaStream_t st) {
+  k_check_basis<<<1, 32, 0, st>>>(m, basis_status, c->err);
+  SPCN_LAUNCH_CHECK(c);
+  return SPCN_OK;
 }
 
 int launch_scale_given(Context* c, const double* p99, const double* tgt, cudaStream_t st) {
@@ -829,9 +892,9 @@ int launch_density(Context* c, const Geometry& g, const Model* m, float* H, int6
   {
     TimedLaunch tl(c, SPCN_KERNEL_DENSITY, st);
     if (pinv)
-      k_pass_density<true><<<grid_of(c, c->occ_density), kPassThreads, kLutSmemBytes, st>>>(a);
+      k_pass_density<true><<<grid_of(c, c->occ_density), kPassThreads, kDensitySmem, st>>>(a);
     else
-      k_pass_density<false><<<grid_of(c, c->occ_density), kPassThreads, kLutSmemBytes, st>>>(a);
+      k_pass_density<false><<<grid_of(c, c->occ_density), kPassThreads, kDensitySmem, st>>>(a);
   }
   SPCN_LAUNCH_CHECK(c);
   return SPCN_OK;

@@ -586,6 +586,7 @@ void white_test_consts(int white_thresh, unsigned* wm, unsigned* we);
 // The Eq. 3 factors from a given source percentile (SPCN_FLAG_P99_SAMPLED):
 // host values, or the basis estimation's sample percentile on the device.
 int launch_scale_given(Context* c, const double* p99, const double* tgt, cudaStream_t st);
+int launch_check_basis(Context* c, const Model* m, const int* basis_status, cudaStream_t st);
 int launch_scale_from_basis(Context* c, const Model* m, const SelectState* sample_sel,
                             const int* basis_status, const double* tgt, cudaStream_t st);
 int launch_percentile_passes_dev(Context* c, const Geometry& g, const Model* m, int white_thresh,

@@ -108,6 +108,8 @@ def _load():
         "spcn_stain_percentile": (ctypes.c_int, [vp, P(Image), P(Stats), P(Params),
                                                  P(ctypes.c_double), vp]),
         "spcn_stain_densities": (ctypes.c_int, [vp, P(Image), P(Stats), P(Params), vp, i64, vp]),
+        "spcn_stain_densities_estimated": (ctypes.c_int, [vp, P(Image), P(Params), vp, i64,
+                                                          P(Stats), vp]),
         "spcn_normalize": (ctypes.c_int, [vp, P(Image), P(Stats), P(Stats), P(Params), vp, i64,
                                           P(ctypes.c_double), vp]),
         "spcn_normalize_estimated": (ctypes.c_int, [vp, P(Image), P(Stats), P(Params), vp, i64,
@@ -154,7 +156,7 @@ EXPORTED = ("spcn_params_default", "spcn_context_create", "spcn_context_destroy"
             "spcn_estimate_basis_noalloc", "spcn_normalize_f32", "spcn_normalize_f32_backward",
             "spcn_batch_create", "spcn_batch_run", "spcn_batch_results", "spcn_batch_get_config",
             "spcn_batch_set_config", "spcn_batch_tune", "spcn_batch_destroy",
-            "spcn_normalize_batched")
+            "spcn_normalize_batched", "spcn_stain_densities_estimated")
 KERNELS = {"pass1": 0, "select": 1, "pass2": 2, "density": 3, "f32_fwd": 4, "f32_bwd": 5,
            "batch": 6}
 
@@ -273,6 +275,26 @@ class Context:
                                        out.stride(0), _stream(stream))
         _check(rc, "spcn_stain_densities")
         return out
+
+    def stain_densities_estimated(self, img, p: Params | None = None, out=None,
+                                  return_stats: bool = False, stream=None):
+        """Basis estimation and the densities of every pixel in one call; with
+        return_stats the call waits and also returns the estimated Stats."""
+        import torch
+        im = image_of(img)
+        n = im.width * im.height
+        if out is None:
+            out = torch.empty((2, n), dtype=torch.float32, device=img.device)
+        if out.dtype != torch.float32 or out.dim() != 2 or out.shape[0] != 2 or out.stride(1) != 1:
+            raise ValueError("out must be a (2, >=H*W) float32 tensor with unit inner stride")
+        p = p or params()
+        st = Stats() if return_stats else None
+        rc = _lib.spcn_stain_densities_estimated(self._h, ctypes.byref(im), ctypes.byref(p),
+                                                 ctypes.c_void_p(out.data_ptr()), out.stride(0),
+                                                 ctypes.byref(st) if st is not None else None,
+                                                 _stream(stream))
+        _check(rc, "spcn_stain_densities_estimated")
+        return (out, st) if return_stats else out
 
     def normalize(self, src, src_stats: Stats, tgt_stats: Stats, p: Params | None = None,
                   out=None, return_p99: bool = False, stream=None):
