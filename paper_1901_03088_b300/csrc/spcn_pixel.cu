@@ -541,14 +541,19 @@ __device__ __forceinline__ void density_chunk(const unsigned (&w)[12], const cha
 // One plane of a warp's 32 consecutive full chunks (512 pixels from px0),
 // staged through shared memory so that each store writes 512 contiguous
 // bytes (the lanes' own 64-byte runs would each half-fill 32 sectors).
+// The 16-byte slots are XOR-swizzled so that every 8-lane phase of both the
+// lane-strided writes and the contiguous reads hits 8 distinct bank groups:
+// slot 4L+v (lane L's vector v) lives at (4L+v) ^ ((L>>1)&3).
 __device__ __forceinline__ void store_plane_coalesced(float* dst, const float (&h)[kChunk],
                                                       float4* stage, unsigned lane) {
-  float4* mine = stage + 4 * lane;
+  const unsigned sw = (lane >> 1) & 3u;
 #pragma unroll
-  for (int v = 0; v < 4; ++v) mine[v] = make_float4(h[4 * v], h[4 * v + 1], h[4 * v + 2], h[4 * v + 3]);
+  for (int v = 0; v < 4; ++v)
+    stage[(4u * lane + v) ^ sw] = make_float4(h[4 * v], h[4 * v + 1], h[4 * v + 2], h[4 * v + 3]);
   __syncwarp();
 #pragma unroll
-  for (int k = 0; k < 4; ++k) __stcs(reinterpret_cast<float4*>(dst) + 32 * k + lane, stage[32 * k + lane]);
+  for (int k = 0; k < 4; ++k)
+    __stcs(reinterpret_cast<float4*>(dst) + 32 * k + lane, stage[(32u * k + lane) ^ (lane >> 3)]);
   __syncwarp();
 }
 
