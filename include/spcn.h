@@ -21,6 +21,8 @@
  *     data + y * pitch_bytes; pitch_bytes >= 3 * width.  Rows whose start
  *     (and, for outputs, destination) is 16-byte aligned take the vector
  *     path; any other layout is accepted and handled byte by byte.
+ *     Limits: width * height < 2^36 pixels and height * ceil(width / 16)
+ *     < 2^32 (chunk indices are 32-bit); larger images are INVALID_ARG.
  *   - The caller owns every image, output and density buffer.  The library
  *     never frees caller memory; it allocates only the scratch held by the
  *     context (grown on demand, released by spcn_context_destroy).

@@ -104,7 +104,10 @@ bool image_ok(const spcn_image* img) {
   if (!img || !img->data || img->width < 1 || img->height < 1) return false;
   if (img->pitch_bytes < 3ll * img->width) return false;
   const long long npx = (long long)img->width * img->height;
-  return npx < (1ll << 36);
+  if (npx >= (1ll << 36)) return false;
+  // chunk indices are kept in 32 bits (pitched images: 16-pixel chunks per row)
+  const long long chunks = (long long)img->height * ((img->width + 15) / 16);
+  return chunks < (1ll << 32);
 }
 
 bool params_ok(const spcn_params* p) {
