@@ -741,7 +741,7 @@ def run_separation(args, world, rank, local):
     return 0
 
 
-FLAG_NAMES = ("i0_255", "order_blue", "p99_sampled", "p99_patch_median", "h_pinv")
+FLAG_NAMES = ("i0_255", "order_blue", "p99_sampled", "p99_patch_median", "h_pinv", "i0_out_255")
 
 
 def variant_flags(spcn, names):

@@ -90,12 +90,17 @@ typedef enum {
  *   passes.  They are signed, so a percentile can be negative; outputs above
  *   255 are clamped.  The basis itself is still learnt with Eq. 2.  Not
  *   available for batches and the float (differentiable) entry points.
+ * SPCN_FLAG_I0_OUT_255: Eq. 4 reconstructs with the neutral white 255 in
+ *   every channel instead of the target's i0 (so background maps to white,
+ *   not to the target's background tint); in spcn_normalize,
+ *   spcn_normalize_estimated, batches and the float entry points.
  */
 #define SPCN_FLAG_I0_255 0x1u
 #define SPCN_FLAG_ORDER_BLUE 0x2u
 #define SPCN_FLAG_P99_SAMPLED 0x4u
 #define SPCN_FLAG_P99_PATCH_MEDIAN 0x8u
 #define SPCN_FLAG_H_PINV 0x10u
+#define SPCN_FLAG_I0_OUT_255 0x20u
 
 /* An 8-bit interleaved RGB image. */
 typedef struct {

@@ -60,6 +60,8 @@ order="blue"      §3.1 item 3's original heuristic, read as: hematoxylin is the
 p99_patch_median  §3.2 item 4: the reported P99 is, per stain, the median over
                   the kept patches of each patch's non-white P99 (patches
                   sampling only).
+i0_out_255        Eq. 4 reconstructs with the neutral white 255 instead of the
+                  target's i0 (the alternative to reading R8).
 h_solve="pinv"    §2.1: H = pinv(W) v (unconstrained, may be negative) for the
                   densities that are scaled and reconstructed; the basis itself
                   is still learnt with Eq. 2.
@@ -499,8 +501,12 @@ def stain_scale(p99_src, p99_tgt) -> np.ndarray:
 
 
 def normalize_float(img: np.ndarray, src_W, src_i0, src_p99, tgt_W, tgt_i0,
-                    tgt_p99, lam: float = LAMBDA, h_solve: str = "lasso") -> np.ndarray:
-    """Eq. 3 then Eq. 4 (reading R8) for every pixel; H x W x 3 float64."""
+                    tgt_p99, lam: float = LAMBDA, h_solve: str = "lasso",
+                    i0_out_255: bool = False) -> np.ndarray:
+    """Eq. 3 then Eq. 4 (reading R8) for every pixel; H x W x 3 float64.
+    With i0_out_255 Eq. 4 uses 255 for every channel instead of tgt_i0."""
+    if i0_out_255:
+        tgt_i0 = np.full(3, 255.0)
     h, w, _ = img.shape
     H = stain_densities(img, src_W, src_i0, lam, h_solve)
     s = stain_scale(src_p99, tgt_p99)
@@ -515,13 +521,13 @@ def to_uint8(I: np.ndarray) -> np.ndarray:
 
 
 def normalize(img: np.ndarray, src: Stats, tgt: Stats, lam: float = LAMBDA,
-              h_solve: str = "lasso") -> np.ndarray:
+              h_solve: str = "lasso", i0_out_255: bool = False) -> np.ndarray:
     """The full per-pixel path on a uint8 image with the source's P99 as
     src.p99 holds it (the exact one for the method; the sampled one of
     ``estimate_basis`` for the one-pass variant) and the target's
     statistics."""
     return to_uint8(normalize_float(img, src.W, src.i0, src.p99,
-                                    tgt.W, tgt.i0, tgt.p99, lam, h_solve))
+                                    tgt.W, tgt.i0, tgt.p99, lam, h_solve, i0_out_255))
 
 
 def full_stats(img: np.ndarray, params: Params | None = None) -> Stats:

@@ -126,12 +126,21 @@ bool params_ok(const spcn_params* p) {
   if (p->max_iter < 1 || p->max_iter > 1000000) return false;
   if (!(p->tol >= 0.f) || !std::isfinite(p->tol)) return false;
   const uint32_t known = SPCN_FLAG_I0_255 | SPCN_FLAG_ORDER_BLUE | SPCN_FLAG_P99_SAMPLED |
-                         SPCN_FLAG_P99_PATCH_MEDIAN | SPCN_FLAG_H_PINV;
+                         SPCN_FLAG_P99_PATCH_MEDIAN | SPCN_FLAG_H_PINV | SPCN_FLAG_I0_OUT_255;
   if (p->flags & ~known) return false;
   if ((p->flags & SPCN_FLAG_P99_PATCH_MEDIAN) &&
       (p->sample_mode != SPCN_SAMPLE_PATCHES || p->n_patches > 4096))
     return false;
   return true;
+}
+
+// The target record as Eq. 4 uses it: with SPCN_FLAG_I0_OUT_255 the output
+// white is 255 in every channel instead of the target's i0.
+spcn_stats output_target(const spcn_stats* t, const spcn_params* p) {
+  spcn_stats o = *t;
+  if (p->flags & SPCN_FLAG_I0_OUT_255)
+    for (int c = 0; c < 3; ++c) o.i0[c] = 255.f;
+  return o;
 }
 
 // A usable basis and i0: finite, W >= 0, columns not parallel, i0 in [1,255].
@@ -389,7 +398,8 @@ int spcn_normalize(void* ctx, const spcn_image* src, const spcn_stats* src_st,
                                   host_table_hexp(src_st->W, src_st->i0, params->lambda),
                                   tgt_st->p99, s, pinv);
   if (rc) return rc;
-  rc = launch_recon(c, g, c->model, tgt_st->W, tgt_st->i0, s, pinv);
+  const spcn_stats to = output_target(tgt_st, params);
+  rc = launch_recon(c, g, c->model, to.W, to.i0, s, pinv);
   if (rc) return rc;
   if (src_p99_out) {
     double p[2];
@@ -440,7 +450,8 @@ int spcn_normalize_f32(void* ctx, const float* x, int32_t batch, int32_t height,
   Context* c = static_cast<Context*>(ctx);
   DeviceGuard guard(c->device);
   if (!guard.ok) return SPCN_ERR_CUDA;
-  return launch_f32(c, false, x, nullptr, batch, (int64_t)height * width, src_stats, tgt_stats, wt,
+  const spcn_stats to = output_target(tgt_stats, params);
+  return launch_f32(c, false, x, nullptr, batch, (int64_t)height * width, src_stats, &to, wt,
                     params->lambda, y, nullptr, nullptr, static_cast<cudaStream_t>(stream));
 }
 
@@ -460,7 +471,8 @@ int spcn_normalize_f32_backward(void* ctx, const float* x, const float* gy, int3
   Context* c = static_cast<Context*>(ctx);
   DeviceGuard guard(c->device);
   if (!guard.ok) return SPCN_ERR_CUDA;
-  return launch_f32(c, true, x, gy, batch, (int64_t)height * width, src_stats, tgt_stats, wt,
+  const spcn_stats to = output_target(tgt_stats, params);
+  return launch_f32(c, true, x, gy, batch, (int64_t)height * width, src_stats, &to, wt,
                     params->lambda, nullptr, gx, gwt, static_cast<cudaStream_t>(stream));
 }
 
@@ -501,7 +513,8 @@ int spcn_normalize_estimated(void* ctx, const spcn_image* src, const spcn_stats*
                                       wdev, tgt_st->p99, s, pinv);
     if (rc) return rc;
   }
-  rc = launch_recon(c, g, m, tgt_st->W, tgt_st->i0, s, pinv);
+  const spcn_stats to = output_target(tgt_st, params);
+  rc = launch_recon(c, g, m, to.W, to.i0, s, pinv);
   if (rc) return rc;
   if (src_st_out) {
     memset(src_st_out, 0, sizeof(*src_st_out));

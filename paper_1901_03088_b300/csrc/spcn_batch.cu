@@ -1060,7 +1060,8 @@ int spcn_batch_create(void* ctx, int32_t n, const spcn_image* tiles, const spcn_
   DeviceGuard guard(c->device);
   if (!guard.ok) return SPCN_ERR_CUDA;
   Batch* b = nullptr;
-  rc = batch_create(c, n, tiles, tile_stats, tgt_st, params, outs, out_pitches, &b);
+  const spcn_stats to = output_target(tgt_st, params);
+  rc = batch_create(c, n, tiles, tile_stats, &to, params, outs, out_pitches, &b);
   if (rc) return rc;
   *batch = b;
   return SPCN_OK;

@@ -96,6 +96,7 @@ bool params_ok(const spcn_params* p);
 // SPCN_OK, INVALID_ARG or DEGENERATE_BASIS; signed_p99: the percentiles may
 // be negative (pseudo-inverse densities)
 int stats_ok(const spcn_stats* s, bool signed_p99 = false);
+spcn_stats output_target(const spcn_stats* t, const spcn_params* p);   // Eq. 4's target record
 Geometry make_geometry(const spcn_image* img, uint8_t* out, int64_t out_pitch);
 
 int ensure_sample_capacity(Context* c, size_t n);

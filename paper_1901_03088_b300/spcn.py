@@ -26,6 +26,7 @@ FLAG_ORDER_BLUE = 0x2
 FLAG_P99_SAMPLED = 0x4
 FLAG_P99_PATCH_MEDIAN = 0x8
 FLAG_H_PINV = 0x10
+FLAG_I0_OUT_255 = 0x20
 
 
 class SpcnError(RuntimeError):

@@ -274,3 +274,41 @@ def test_pinv_rejected_where_not_available(spcn, ctx):
     wt = torch.tensor(np.array(st.basis, dtype=np.float32), device="cuda")
     with pytest.raises(spcn.SpcnError):
         spcn.normalize_f32(ctx, x, wt, [st], st, p=spcn.params(flags=spcn.FLAG_H_PINV))
+
+
+# ---------------------------------------------------------------- SPCN_FLAG_I0_OUT_255 (Eq. 4)
+def test_i0_out_255_all_entry_points(spcn, ctx):
+    img = synth.make_image(300, 411, 1320)
+    tgt_img = synth.make_image(128, 128, 1, white=(232.0, 240.0, 246.0))
+    pe = spcn.params(sample_mode="all")
+    src = ctx.estimate_basis(to_dev(img), pe)
+    tgt = ctx.estimate_basis(to_dev(tgt_img), pe)
+    tgt.p99[0], tgt.p99[1] = ctx.stain_percentile(to_dev(tgt_img), tgt, pe)
+    assert max(tgt.i0) < 250
+    pf = spcn.params(sample_mode="all", flags=spcn.FLAG_I0_OUT_255)
+    out, p99 = ctx.normalize(to_dev(img), src, tgt, pf, return_p99=True)
+    so = O.Stats(W=np.array(src.basis, dtype=np.float32).astype(np.float64),
+                 i0=np.float32(src.i0).astype(np.float64), p99=np.array(p99))
+    to = O.Stats(W=np.array(tgt.basis, dtype=np.float32).astype(np.float64),
+                 i0=np.float32(tgt.i0).astype(np.float64), p99=np.array(tgt.p99[:]))
+    close_uint8(out.cpu().numpy(), O.normalize(img, so, to, i0_out_255=True))
+    bg = ~O.nonwhite_mask(img.reshape(-1, 3))
+    assert np.mean(out.cpu().numpy().reshape(-1, 3)[bg] >= 250) > 0.9   # white maps to white
+    out2 = ctx.normalize_estimated(to_dev(img), tgt, pf)
+    out3 = ctx.normalize(to_dev(img), src, tgt, pf)
+    assert torch.equal(out2, out3)
+    # batch: bit-identical to the single-image path with the flag
+    tiles = [to_dev(img), to_dev(synth.make_image(97, 130, 1321))]
+    stats = [src, ctx.estimate_basis(tiles[1], pe)]
+    outs = [torch.empty_like(t) for t in tiles]
+    spcn.normalize_batched(ctx, tiles, stats, tgt, outs, pf)
+    for t, s_, o in zip(tiles, stats, outs):
+        assert torch.equal(o, ctx.normalize(t, s_, tgt, pf))
+    # float path: i0_t replaced by 255 scales every output channel by 255 / i0_t
+    x = torch.from_numpy(np.ascontiguousarray(img[:64, :64].transpose(2, 0, 1)[None]).astype(np.float32)).cuda()
+    wt = torch.tensor(np.array(tgt.basis, dtype=np.float32), device="cuda")
+    src.p99[0], src.p99[1] = p99
+    y0 = spcn.normalize_f32(ctx, x, wt, [src], tgt, p=pe)
+    y1 = spcn.normalize_f32(ctx, x, wt, [src], tgt, p=pf)
+    ratio = torch.tensor([255.0 / v for v in tgt.i0], device="cuda").view(1, 3, 1, 1)
+    assert torch.allclose(y1, y0 * ratio, rtol=1e-5, atol=1e-3)

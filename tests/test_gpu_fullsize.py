@@ -12,7 +12,10 @@ as the benchmark's step.  The FP64 oracle cannot process 8 Gpx, so:
 * densities and output bytes of 20000 seeded random pixels are compared with
   the oracle computed pixel by pixel from the returned statistics: densities
   within 1e-5 max(|h|, 1) (KKT-margin exceptions at most 1e-4 of the
-  sample), output within 1 on >= 99.99% of the sampled pixels.
+  sample), output within 1 on >= 99.99% of the sampled pixels;
+* the output of 16 seeded 256 x 256 tiles (1 Mpx) is compared with the
+  oracle's normalisation of the same tiles from the same statistics: within
+  1 on >= 99.99% of the tiles' pixels.
 """
 import math
 
@@ -104,4 +107,18 @@ def test_full_slide_in_the_benchmark_configuration(spcn):
     got = out[torch.from_numpy(ys).to(dev), torch.from_numpy(xs).to(dev)].cpu().numpy()
     diff = np.abs(got.astype(int) - ref.astype(int))
     assert diff.max() <= 1 or np.mean(np.any(diff > 1, axis=-1)) <= 1e-4, diff.max()
+
+    # 16 seeded whole tiles
+    T = 256
+    ty = rng.integers(0, HEIGHT - T + 1, 16)
+    tx = rng.integers(0, WIDTH - T + 1, 16)
+    bad = 0
+    for y0, x0 in zip(ty, tx):
+        tile = src[y0:y0 + T, x0:x0 + T].cpu().numpy()
+        ref = O.to_uint8(O.normalize_float(tile, W, i0, np.array(p99), Wt, i0t,
+                                           np.array(t_st.p99[:]), p.lambda_))
+        got = out[y0:y0 + T, x0:x0 + T].cpu().numpy()
+        d = np.abs(got.astype(int) - ref.astype(int))
+        bad += int(np.count_nonzero(np.any(d > 1, axis=-1)))
+    assert bad <= 1e-4 * 16 * T * T, bad
     ctx.close()

@@ -500,3 +500,19 @@ def test_pinv_identity_normalisation_reproduces_in_span_pixels():
     assert np.max(np.abs(out - I)[inside]) < 1e-9
     lasso = O.normalize_float(I, W, i0, p99, W, i0, p99)
     assert np.max(np.abs(lasso - I)[inside]) > 1.0
+
+
+def test_i0_out_255_maps_background_to_neutral_white():
+    """Eq. 4 with i0 = 255 (the alternative to reading R8): a pixel with no
+    stain (h = 0) comes out as exactly 255 in every channel, where the
+    default gives the target's white; stained pixels scale by 255 / i0_t."""
+    W = synth.stain_basis(1208)
+    src = O.Stats(W=W, i0=np.full(3, 250.0), p99=np.array([1.0, 1.0]))
+    tgt = O.Stats(W=W, i0=np.array([230.0, 240.0, 250.0]), p99=np.array([1.0, 1.0]))
+    bg = np.full((1, 1, 3), 250, np.uint8)                  # OD 0 -> h = 0
+    assert np.array_equal(O.normalize(bg, src, tgt, i0_out_255=True)[0, 0], [255, 255, 255])
+    assert np.array_equal(O.normalize(bg, src, tgt)[0, 0], [230, 240, 250])
+    img = synth.make_image(16, 16, 1208, W=W)
+    a = O.normalize_float(img, W, src.i0, src.p99, W, tgt.i0, tgt.p99, i0_out_255=True)
+    b = O.normalize_float(img, W, src.i0, src.p99, W, tgt.i0, tgt.p99)
+    assert np.allclose(a, b * (255.0 / tgt.i0), rtol=1e-12)
