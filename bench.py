@@ -579,21 +579,21 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
 
     stream = torch.cuda.current_stream()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     ctx.kernel_timing(True)
     launches0 = ctx.launches
     with ClockSampler(local) as clk:
         barrier(world)
         torch.cuda.synchronize()
-        ev0.record(stream)
-        for _ in range(args.steps):
+        evs[0].record(stream)
+        for i in range(args.steps):
             step()
-        ev1.record(stream)
+            evs[i + 1].record(stream)
         torch.cuda.synchronize()
         barrier(world)
     launches = ctx.launches - launches0
-    ms_local = ev0.elapsed_time(ev1) / args.steps
+    ms_local = evs[0].elapsed_time(evs[-1]) / args.steps
+    per_step = sorted(evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps))
     ms = max_over_ranks(ms_local, world, dev)
     ktimes = {k: ctx.kernel_times(k) for k in ("pass1", "select", "pass2")}
     ctx.kernel_timing(False)
@@ -634,6 +634,8 @@ def run_ours(args, world, rank, local):
             "pixels_per_step": npx, "parallelism": f"replicas x{world}",
             "l2": f"inputs ({3 * npx / 1e9:.1f} GB) larger than L2 (126 MB); no flush",
             "target_stats_ms_once": round(tgt_ms, 3), "generate_s": round(gen_s, 2),
+            "ms_per_step_best": round(per_step[0], 4),
+            "ms_per_step_median": round(per_step[len(per_step) // 2], 4),
             "kernel_ms_per_step": {k: round(v[0] / max(1, v[1]), 4) for k, v in ktimes.items()},
             "select_fallback_launches": ktimes["select"][1],
             "src_p99": [round(p99[0], 6), round(p99[1], 6)], "snmf_iters": s_st.iters,
