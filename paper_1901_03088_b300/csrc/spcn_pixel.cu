@@ -354,10 +354,18 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_window(WindowArgs a) {
     if (q < g.nchunks) {
       const ChunkPos p = chunk_pos(g, q);
       load_chunk<false>(g, p, w);
-      if (p.n == kChunk)
-        tissue = !chunk_white(w, wm, we);
-      else
+      if (p.n != kChunk) {
         partial_chunk<PINV>(g.src + p.src_off, p.n, lut, lr, L, C, s_coarse, c_nw, c_b0, c_b1);
+      } else if (!chunk_white(w, wm, we)) {
+        if (!PINV && chunk_below_window(w, lut, lr, C)) {   // counts only, no lasso
+          const f2 n = pk(chunk_nonwhite(w, lr, C.wthr), 0.f);
+          c_nw = add2(c_nw, n);
+          c_b0 = add2(c_b0, n);
+          c_b1 = add2(c_b1, n);
+        } else {
+          tissue = true;
+        }
+      }
     }
     const unsigned ball = __ballot_sync(0xFFFFFFFFu, tissue);
     const int cnt = __popc(ball);

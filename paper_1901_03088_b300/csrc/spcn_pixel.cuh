@@ -256,6 +256,73 @@ __device__ __forceinline__ bool chunk_white(const unsigned (&w)[12], unsigned wm
   return (acc & wm) == we;
 }
 
+// Lane-wise minimum of two 16-bit pairs (native on this GPU).  The high
+// byte of a 16-bit minimum is the minimum of the high bytes whatever the low
+// bytes hold, which the per-channel minima below rely on.
+__device__ __forceinline__ unsigned min_u16x2(unsigned a, unsigned b) {
+  unsigned r;
+  asm("min.u16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
+
+// Per-channel minima of a full chunk (16 interleaved RGB pixels in 12
+// words): words 3i, 3i+1, 3i+2 carry the byte patterns [R G B R],
+// [G B R G], [B R G B].  16-bit minima of the words give the minima of their
+// bytes 1 and 3, of the byte-swapped words those of bytes 0 and 2; the
+// twelve candidates are then regathered into high bytes and reduced.  Returns
+// (min R, min G) in bytes 1 and 3 of *rg and min B in byte 1 of *bb.
+__device__ __forceinline__ void chunk_channel_min(const unsigned (&w)[12], unsigned* rg,
+                                                  unsigned* bb) {
+  unsigned A[3], B[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    A[k] = min_u16x2(min_u16x2(w[k], w[k + 3]), min_u16x2(w[k + 6], w[k + 9]));
+    B[k] = min_u16x2(min_u16x2(__byte_perm(w[k], 0u, 0x2301u), __byte_perm(w[k + 3], 0u, 0x2301u)),
+                     min_u16x2(__byte_perm(w[k + 6], 0u, 0x2301u), __byte_perm(w[k + 9], 0u, 0x2301u)));
+  }
+  const unsigned x1 = __byte_perm(B[0], A[0], 0x5010u);   // R: B0.b1   G: A0.b1
+  const unsigned x2 = __byte_perm(A[0], B[1], 0x5030u);   // R: A0.b3   G: B1.b1
+  const unsigned x3 = __byte_perm(B[1], A[1], 0x7030u);   // R: B1.b3   G: A1.b3
+  const unsigned x4 = __byte_perm(A[2], B[2], 0x7010u);   // R: A2.b1   G: B2.b3
+  *rg = min_u16x2(min_u16x2(x1, x2), min_u16x2(x3, x4));
+  const unsigned y = min_u16x2(__byte_perm(B[0], A[1], 0x5030u),    // B0.b3, A1.b1
+                               __byte_perm(A[2], B[2], 0x5030u));   // A2.b3, B2.b1
+  *bb = min_u16x2(y, y >> 16);
+}
+
+// True when every pixel of a full chunk is below both window starts: the
+// densities' bound D~ at the chunk's per-channel minima (the same table
+// sums and saturation as solve_one) passes the window's exact test.  Every
+// table entry is non-increasing in the intensity (W >= 0), FP32 addition and
+// the saturation are monotone, and h~ = min(D~, t) <= D~, so each pixel's
+// test gives the same 1.  (Not for the pseudo-inverse, whose rows may be
+// negative.)
+__device__ __forceinline__ bool chunk_below_window(const unsigned (&w)[12], const char* lut,
+                                                   unsigned lr, const WindowConst& C) {
+  unsigned rg, bb;
+  chunk_channel_min(w, &rg, &bb);
+  // table offsets: the intensity in byte 1, the lane's copy in byte 0
+  const float2 eR = lut_ld(lut, __byte_perm(rg, lr, 0x5514u));
+  const float2 eG = lut_ld(lut, __byte_perm(rg, lr, 0x5534u) + kLutOffG);
+  const float2 eB = lut_ld(lut, __byte_perm(bb, lr, 0x5514u) + kLutOffB);
+  const float D1 = add_sat(eR.x + eG.x, eB.x);
+  const float D2 = add_sat(eR.y + eG.y, eB.y);
+  return fma_sat(D1, C.nk0, C.lk0) == 1.f && fma_sat(D2, C.nk1, C.lk1) == 1.f;
+}
+
+// Non-white pixels of a full chunk (some channel at or below the threshold).
+__device__ __forceinline__ float chunk_nonwhite(const unsigned (&w)[12], unsigned lr,
+                                                unsigned wthr) {
+  float n = 0.f;
+#pragma unroll
+  for (int k = 0; k < kChunk; ++k) {
+    unsigned aR, aG, aB;
+    pixel_addr(w, k, lr, aR, aG, aB);
+    n += min(min(aR, aG), aB) < wthr ? 1.f : 0.f;
+  }
+  return n;
+}
+
 constexpr int kWarpQueue = 64;    // queued chunks per warp; drained once 32 are waiting, so the
                                   // re-read chunks are recent enough to still be in L2
 
