@@ -341,6 +341,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_window(WindowArgs a) {
   const unsigned lane = threadIdx.x & 31u;
   const unsigned lt = (1u << lane) - 1u;
   const unsigned wm = a.wm, we = a.we;
+  const WhiteBytes wb = white_bytes((a.wthr >> 8) - 1u);
   int qn = 0;   // entries in this warp's hit queue (warp-uniform)
   int ns = 0;   // tissue chunks on this warp's stack (warp-uniform)
   // every lane of a warp runs the same number of iterations (warp-uniform
@@ -358,7 +359,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_window(WindowArgs a) {
         partial_chunk<PINV>(g.src + p.src_off, p.n, lut, lr, L, C, s_coarse, c_nw, c_b0, c_b1);
       } else if (!chunk_white(w, wm, we)) {
         if (!PINV && chunk_below_window(w, lut, lr, C)) {   // counts only, no lasso
-          const f2 n = pk(chunk_nonwhite(w, lr, C.wthr), 0.f);
+          const f2 n = pk(chunk_nonwhite(w, wb), 0.f);
           c_nw = add2(c_nw, n);
           c_b0 = add2(c_b0, n);
           c_b1 = add2(c_b1, n);

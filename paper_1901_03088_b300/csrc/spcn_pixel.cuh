@@ -310,17 +310,38 @@ __device__ __forceinline__ bool chunk_below_window(const unsigned (&w)[12], cons
   return fma_sat(D1, C.nk0, C.lk0) == 1.f && fma_sat(D2, C.nk1, C.lk1) == 1.f;
 }
 
+// Constants of the byte test "above the white threshold T" used by
+// chunk_nonwhite: with t = (b & 0x7F) + k, bit 7 of (b & (t | m)) | (t & m)
+// is set exactly when b > T (k = 255 - T, m = 0 for T >= 127: b needs its top
+// bit and the low bits must carry; k = 127 - T, m = ~0 below: either does).
+struct WhiteBytes {
+  unsigned k, m;
+};
+__device__ __forceinline__ WhiteBytes white_bytes(unsigned T) {
+  return T >= 127u ? WhiteBytes{(255u - T) * 0x01010101u, 0u}
+                   : WhiteBytes{(127u - T) * 0x01010101u, 0xFFFFFFFFu};
+}
+
 // Non-white pixels of a full chunk (some channel at or below the threshold).
-__device__ __forceinline__ float chunk_nonwhite(const unsigned (&w)[12], unsigned lr,
-                                                unsigned wthr) {
-  float n = 0.f;
+// Four pixels are three words: their bytes' flags are regrouped by channel
+// with byte permutes, and a pixel is white when its three flags are set.
+__device__ __forceinline__ float chunk_nonwhite(const unsigned (&w)[12], const WhiteBytes& t) {
+  unsigned white = 0u;
 #pragma unroll
-  for (int k = 0; k < kChunk; ++k) {
-    unsigned aR, aG, aB;
-    pixel_addr(w, k, lr, aR, aG, aB);
-    n += min(min(aR, aG), aB) < wthr ? 1.f : 0.f;
+  for (int j = 0; j < 4; ++j) {
+    unsigned f[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const unsigned x = w[3 * j + i];
+      const unsigned s = (x & 0x7F7F7F7Fu) + t.k;
+      f[i] = (x & (s | t.m)) | (s & t.m);
+    }
+    const unsigned r = __byte_perm(__byte_perm(f[0], f[1], 0x0630u), f[2], 0x5210u);
+    const unsigned g = __byte_perm(__byte_perm(f[0], f[1], 0x0741u), f[2], 0x6210u);
+    const unsigned b = __byte_perm(__byte_perm(f[0], f[1], 0x0052u), f[2], 0x7410u);
+    white += __popc(r & g & b & 0x80808080u);
   }
-  return n;
+  return (float)(kChunk - (int)white);
 }
 
 constexpr int kWarpQueue = 64;    // queued chunks per warp; drained once 32 are waiting, so the

@@ -69,7 +69,7 @@ def type7(values, p):
     return lo + t * (hi - lo)
 
 
-@pytest.mark.parametrize("thresh", [220, 128, 254, 255])
+@pytest.mark.parametrize("thresh", [220, 128, 100, 254, 255])
 @pytest.mark.parametrize("hint", ["exact", "none"])
 def test_percentile_with_white_regions(spcn, ctx, image, thresh, hint):
     st = spcn.Stats.from_values(synth.stain_basis(4242), [255.0, 255.0, 255.0])
