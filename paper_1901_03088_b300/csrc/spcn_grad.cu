@@ -166,7 +166,7 @@ __device__ __forceinline__ void f32_back_px(const F32Reg& R, const F32Back& B, c
   gx2 = x2 > 1.f ? __fdividef(-fmaf(B.ws2, gc1, B.ws5 * gc2), x2) : 0.f;
 }
 
-__global__ void __launch_bounds__(kF32Threads) k_f32_backward(F32Args a) {
+__global__ void __launch_bounds__(kF32Threads, 4) k_f32_backward(F32Args a) {
   __shared__ double s_red[kF32Threads / 32][6];
   const int b = blockIdx.y;
   const F32Img& I = a.img[b];
@@ -227,16 +227,37 @@ __global__ void __launch_bounds__(kF32Threads) k_f32_backward(F32Args a) {
   }
 }
 
-// Sum of all block partials in a fixed order (warp k sums entry k with a
-// fixed lane-strided pattern and shuffle tree); writes gwt (column-major).
-__global__ void k_f32_reduce(const double* partials, int nblocks, float* gwt) {
-  const int lane = threadIdx.x & 31, k = threadIdx.x >> 5;
-  if (k >= 6) return;
+// Sum of all block partials in a fixed order; writes gwt (column-major).
+// kReduceLanes threads per entry k each add a fixed strided subset (loads
+// issued eight at a time), then a fixed pairwise tree in shared memory adds
+// their results: the same order on every run.
+constexpr int kReduceLanes = 160;   // 6 x 160 = 960 threads
+__global__ void __launch_bounds__(6 * kReduceLanes) k_f32_reduce(const double* partials,
+                                                                  int nblocks, float* gwt) {
+  __shared__ double s_part[6][256];
+  const int k = threadIdx.x / kReduceLanes, i = threadIdx.x % kReduceLanes;
   double x = 0.0;
-  for (int b = lane; b < nblocks; b += 32) x += partials[(size_t)b * 6 + k];
+  for (int b0 = i; b0 < nblocks; b0 += 8 * kReduceLanes) {
+    double v[8];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-  if (lane == 0) gwt[k] = (float)x;
+    for (int u = 0; u < 8; ++u) {
+      const int b = b0 + u * kReduceLanes;
+      v[u] = b < nblocks ? partials[(size_t)b * 6 + k] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) x += v[u];
+  }
+  s_part[k][i] = x;
+  if (i < 256 - kReduceLanes) s_part[k][kReduceLanes + i] = 0.0;   // pad to 256
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    for (int j = threadIdx.x; j < 6 * h; j += blockDim.x) {
+      const int kk = j / h, jj = j % h;
+      s_part[kk][jj] += s_part[kk][jj + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 6) gwt[threadIdx.x] = (float)s_part[threadIdx.x][0];
 }
 
 // ------------------------------------------------------------ host side
@@ -303,7 +324,7 @@ int launch_f32(Context* c, bool backward, const float* x, const float* gy, int b
     SPCN_LAUNCH_CHECK(c);
   }
   if (backward) {
-    k_f32_reduce<<<1, 6 * 32, 0, st>>>(c->partials, (int)nblocks, gwt);
+    k_f32_reduce<<<1, 6 * kReduceLanes, 0, st>>>(c->partials, (int)nblocks, gwt);
     SPCN_LAUNCH_CHECK(c);
   }
   return SPCN_OK;
