@@ -66,8 +66,9 @@ __device__ __forceinline__ unsigned byte_at(const unsigned (&w)[12], int i) {
 
 // Load a chunk into 12 little-endian words; STREAM selects the evict-first
 // policy for data read for the last time.  Pixels past the end of a row read
-// as white (0xFF bytes): they fall outside every count of pass 1, and their
-// outputs are never stored, so every chunk takes the same unrolled path.
+// as 0xFF bytes, so every chunk takes the same unrolled path: their outputs
+// are never stored, and pass 1 counts a row's partial chunk pixel by pixel
+// (at white threshold 255 the padding would not read as white).
 template <bool STREAM, class G>
 __device__ __forceinline__ void load_chunk(const G& g, const ChunkPos& p,
                                            unsigned (&w)[12]) {
