@@ -494,8 +494,9 @@ int spcn_normalize_estimated(void* ctx, const spcn_image* src, const spcn_stats*
   DeviceGuard guard(c->device);
   if (!guard.ok) return SPCN_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  // basis estimation, left on the device
-  rc = launch_estimate_basis(c, src, params, s);
+  // basis estimation, left on the device; unless the sample percentile is
+  // the one Eq. 3 uses, it only places pass 1's window
+  rc = launch_estimate_basis(c, src, params, s, !(params->flags & SPCN_FLAG_P99_SAMPLED));
   if (rc) return rc;
   // the basis estimation's final table (estimated basis and i0, this lambda)
   // is the source table; the window comes from the sample P99

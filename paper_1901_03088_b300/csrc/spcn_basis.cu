@@ -19,7 +19,7 @@ namespace spcn {
 
 int launch_select_list(Context* c, const uint32_t* items, const u64* n_dev, const Model* m,
                        SelectState* sel, u64* ghist, double pct, cudaStream_t st,
-                       bool pinv = false);
+                       bool pinv = false, unsigned sub = 1);
 
 constexpr int kCompactBlock = 4096;
 constexpr int kCompactThreads = 512;
@@ -788,7 +788,7 @@ int configure_basis_kernels(Context* c) {
 // sample percentile) on `st`, without waiting: the results stay on the
 // device (c->bs, c->model_b) until finish_estimate_basis reads them.
 int launch_estimate_basis(Context* c, const spcn_image* img, const spcn_params* p,
-                          cudaStream_t st) {
+                          cudaStream_t st, bool hint_only) {
   const int64_t W = img->width, H = img->height;
   const u64 N = (u64)W * (u64)H;
   u64 cap = 0, m = 0;
@@ -878,8 +878,10 @@ int launch_estimate_basis(Context* c, const spcn_image* img, const spcn_params* 
     SPCN_LAUNCH_CHECK(c);
     return SPCN_OK;
   }
+  // hint_only: the percentile only places the search window of an exact
+  // whole-image percentile; every 16th group of four sample pixels suffices
   return launch_select_list(c, c->nw, &bs->n_nw, c->model_b, &bs->sel, c->rhist_b,
-                            (double)p->stain_pct, st, pinv);
+                            (double)p->stain_pct, st, pinv, hint_only ? 16u : 1u);
 }
 
 // Wait for the estimation launched on `st` and fill the host record.

@@ -446,8 +446,10 @@ int launch_recon(Context* c, const Geometry& g, const Model* m, const float* Wt,
                  const float* i0t, cudaStream_t st, bool pinv = false);
 int launch_density(Context* c, const Geometry& g, const Model* m, float* H, int64_t stride,
                    cudaStream_t st, bool pinv = false);
+// hint_only: the sample percentile is needed only as a search hint (a
+// regular sub-sample is then selected instead of the whole sample)
 int launch_estimate_basis(Context* c, const spcn_image* img, const spcn_params* p,
-                          cudaStream_t st);
+                          cudaStream_t st, bool hint_only = false);
 int finish_estimate_basis(Context* c, spcn_stats* out, cudaStream_t st);
 int run_estimate_basis(Context* c, const spcn_image* img, const spcn_params* p, spcn_stats* out,
                        cudaStream_t st);

@@ -451,16 +451,20 @@ struct SelectListArgs {
   int* err;
   long long timeout_ns;
   double pct;
+  unsigned sub;   // 1: the whole list; s > 1: every s-th group of four (a hint only)
 };
 
 // Percentile of the densities of a packed list of non-white pixels (the basis
-// sample, §3.1 item 2), radix select from scratch.
+// sample, §3.1 item 2), radix select from scratch; with sub > 1 of a regular
+// sub-sample of the list (used only as the search window's hint).
 template <bool PINV>
 __global__ void __launch_bounds__(kPassThreads, 1) k_select_list(SelectListArgs a) {
   extern __shared__ __align__(16) char s_dyn[];
   unsigned* s_hist = reinterpret_cast<unsigned*>(s_dyn + kLutSmemBytes);
-  const u64 n = __ldcg(a.n_dev);
-  if (n == 0 || a.m->status != SPCN_OK) return;   // uniform: every block returns
+  const u64 n_all = __ldcg(a.n_dev);
+  if (n_all == 0 || a.m->status != SPCN_OK) return;   // uniform: every block returns
+  const unsigned sub = (n_all >> 2) >= 64ull * a.sub ? a.sub : 1u;   // small lists: all of it
+  const u64 n = ListSource::visited(n_all, sub);
   u64 rank[kTracks];
   int active[kTracks];
   double t;
@@ -475,7 +479,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_select_list(SelectListArgs 
   }
   load_lut(a.m, s_dyn);
   const Lasso L = a.m->lasso;
-  ListSource src{a.items, n};
+  ListSource src{a.items, n_all, sub};
   radix_select<PINV>(src, s_dyn, L, a.sel, rank, active, a.ghist, s_hist, &a.sel->barrier, a.err,
                a.timeout_ns, 1.0, 1.0);
 }
@@ -858,7 +862,8 @@ int launch_percentile_passes_dev(Context* c, const Geometry& g, const Model* m, 
 }
 
 int launch_select_list(Context* c, const uint32_t* items, const u64* n_dev, const Model* m,
-                       SelectState* sel, u64* ghist, double pct, cudaStream_t st, bool pinv) {
+                       SelectState* sel, u64* ghist, double pct, cudaStream_t st, bool pinv,
+                       unsigned sub) {
   SelectListArgs a;
   a.items = items;
   a.n_dev = n_dev;
@@ -868,6 +873,7 @@ int launch_select_list(Context* c, const uint32_t* items, const u64* n_dev, cons
   a.err = c->err;
   a.timeout_ns = c->timeout_ns;
   a.pct = pct;
+  a.sub = sub < 1 ? 1 : sub;
   SPCN_CUDA_TRY(cudaMemsetAsync(sel, 0, sizeof(SelectState), st));
   void* args[] = {&a};
   SPCN_CUDA_TRY(cudaLaunchCooperativeKernel(

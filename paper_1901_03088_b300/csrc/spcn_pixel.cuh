@@ -373,6 +373,11 @@ struct ImageSource {
 struct ListSource {
   const uint32_t* items;   // packed R | G<<8 | B<<16, all non-white; 16-byte aligned
   u64 n;
+  unsigned sub;            // 1: every item; s > 1: the groups of four items 0, s, 2s, ... only
+  // Items visited (the population the select ranks).
+  __host__ __device__ static u64 visited(u64 n, unsigned sub) {
+    return sub > 1 ? 4 * (((n >> 2) + sub - 1) / sub) : n;
+  }
   template <class F>
   __device__ __forceinline__ void for_each(F&& f) const {
     const unsigned lr = lane_reg();
@@ -381,13 +386,14 @@ struct ListSource {
     // four items per 16-byte load, then the tail
     const uint4* v4 = reinterpret_cast<const uint4*>(items);
     const u64 n4 = n >> 2;
-    for (u64 i = t; i < n4; i += stride) {
+    for (u64 i = t * sub; i < n4; i += stride * sub) {
       const uint4 v = __ldg(v4 + i);
       f(lut_addr(v.x, lr, 0), lut_addr(v.x, lr, 1), lut_addr(v.x, lr, 2), true);
       f(lut_addr(v.y, lr, 0), lut_addr(v.y, lr, 1), lut_addr(v.y, lr, 2), true);
       f(lut_addr(v.z, lr, 0), lut_addr(v.z, lr, 1), lut_addr(v.z, lr, 2), true);
       f(lut_addr(v.w, lr, 0), lut_addr(v.w, lr, 1), lut_addr(v.w, lr, 2), true);
     }
+    if (sub > 1) return;
     for (u64 i = (n4 << 2) + t; i < n; i += stride) {
       const uint32_t v = __ldg(items + i);
       f(lut_addr(v, lr, 0), lut_addr(v, lr, 1), lut_addr(v, lr, 2), true);
