@@ -324,25 +324,30 @@ __device__ __forceinline__ WhiteBytes white_bytes(unsigned T) {
 }
 
 // Non-white pixels of a full chunk (some channel at or below the threshold).
-// Four pixels are three words: their bytes' flags are regrouped by channel
-// with byte permutes, and a pixel is white when its three flags are set.
+// Four pixels are three words a = [R0 G0 B0 R1], b = [G1 B1 R2 G2],
+// c = [B2 R3 G3 B3].  Three words per pixel pair carry the pair's channels in
+// the high bytes of their 16-bit lanes (a itself, two byte permutes of a and
+// b for pixels 0-1; c << 8 and two permutes of b and c for pixels 2-3), so two
+// 16-bit minima give each pixel's smallest channel; the four minima are
+// gathered into one word and tested once (white: minimum above T).  The four
+// groups' flags are merged into bits 7..4 of each byte for one bit count.
 __device__ __forceinline__ float chunk_nonwhite(const unsigned (&w)[12], const WhiteBytes& t) {
-  unsigned white = 0u;
+  unsigned f[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    unsigned f[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      const unsigned x = w[3 * j + i];
-      const unsigned s = (x & 0x7F7F7F7Fu) + t.k;
-      f[i] = (x & (s | t.m)) | (s & t.m);
-    }
-    const unsigned r = __byte_perm(__byte_perm(f[0], f[1], 0x0630u), f[2], 0x5210u);
-    const unsigned g = __byte_perm(__byte_perm(f[0], f[1], 0x0741u), f[2], 0x6210u);
-    const unsigned b = __byte_perm(__byte_perm(f[0], f[1], 0x0052u), f[2], 0x7410u);
-    white += __popc(r & g & b & 0x80808080u);
+    const unsigned a = w[3 * j], b = w[3 * j + 1], c = w[3 * j + 2];
+    const unsigned m01 = min_u16x2(min_u16x2(a, __byte_perm(a, b, 0x4400u)),   // G0 R1, R0 G1
+                                   __byte_perm(a, b, 0x5520u));                 // B0 B1
+    const unsigned m23 = min_u16x2(min_u16x2(c << 8, __byte_perm(b, c, 0x5520u)),   // B2 G3, R2 R3
+                                   __byte_perm(b, c, 0x7330u));                      // G2 B3
+    const unsigned z = __byte_perm(m01, m23, 0x7531u);   // the four pixels' minima
+    const unsigned s = (z & 0x7F7F7F7Fu) + t.k;
+    f[j] = (z & (s | t.m)) | (s & t.m);   // bit 7 of each byte: the pixel is white
   }
-  return (float)(kChunk - (int)white);
+  unsigned x = (f[0] & 0x80808080u) | ((f[1] >> 1) & 0x7F7F7F7Fu);
+  x = (x & 0xC0C0C0C0u) | ((f[2] >> 2) & 0x3F3F3F3Fu);
+  x = (x & 0xE0E0E0E0u) | ((f[3] >> 3) & 0x1F1F1F1Fu);
+  return (float)(kChunk - __popc(x & 0xF0F0F0F0u));
 }
 
 constexpr int kWarpQueue = 64;    // queued chunks per warp; drained once 32 are waiting, so the
