@@ -248,7 +248,7 @@ __device__ __forceinline__ void drain_queue(const uint2* queue, int count, const
 
 // Window arithmetic of one full chunk per lane (lanes with have = false take
 // no part), then the hit queue: called by the whole warp.
-template <bool PINV>
+template <bool PINV, bool WHITES_BELOW>
 __device__ __forceinline__ void pass1_chunk(const unsigned (&w)[12], unsigned qi, bool have,
                                             const char* lut, unsigned lr, f2 NR1, f2 NR2,
                                             const Lasso& L, const WindowConst& C,
@@ -258,7 +258,7 @@ __device__ __forceinline__ void pass1_chunk(const unsigned (&w)[12], unsigned qi
   unsigned packed = 0u;
   if (have) {
     f2 mask;
-    window_chunk<PINV>(w, lut, lr, NR1, NR2, L.kappa, C, c_nw, c_b0, c_b1, mask);
+    window_chunk<PINV, WHITES_BELOW>(w, lut, lr, NR1, NR2, L.kappa, C, c_nw, c_b0, c_b1, mask);
     packed = (unsigned)lo_of(mask) | ((unsigned)hi_of(mask) << 16);
   }
   const bool hit = packed != 0u;
@@ -342,6 +342,9 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_window(WindowArgs a) {
   const unsigned lt = (1u << lane) - 1u;
   const unsigned wm = a.wm, we = a.we;
   const WhiteBytes wb = white_bytes((a.wthr >> 8) - 1u);
+  // every white pixel below both window starts: the lasso of a tissue chunk
+  // then skips the per-pixel non-white masks (the same on every thread)
+  const bool wbelow = !PINV && whites_below((a.wthr >> 8) - 1u, lut, lr, C);
   int qn = 0;   // entries in this warp's hit queue (warp-uniform)
   int ns = 0;   // tissue chunks on this warp's stack (warp-uniform)
   // every lane of a warp runs the same number of iterations (warp-uniform
@@ -358,14 +361,18 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_window(WindowArgs a) {
       if (p.n != kChunk) {
         partial_chunk<PINV>(g.src + p.src_off, p.n, lut, lr, L, C, s_coarse, c_nw, c_b0, c_b1);
       } else if (!chunk_white(w, wm, we)) {
-        if (!PINV && chunk_below_window(w, lut, lr, C)) {   // counts only, no lasso
-          const f2 n = pk(chunk_nonwhite(w, wb), 0.f);
-          c_nw = add2(c_nw, n);
-          c_b0 = add2(c_b0, n);
-          c_b1 = add2(c_b1, n);
-        } else {
-          tissue = true;
+        const bool below = !PINV && chunk_below_window(w, lut, lr, C);   // counts only, no lasso
+        if (below || wbelow) {
+          // the non-white count; with wbelow a tissue chunk's lasso counts all
+          // 16 pixels below both windows (its white ones included), so its
+          // white pixels are taken off here
+          const float nw = chunk_nonwhite(w, wb);
+          const f2 nb = pk(below ? nw : nw - (float)kChunk, 0.f);
+          c_nw = add2(c_nw, pk(nw, 0.f));
+          c_b0 = add2(c_b0, nb);
+          c_b1 = add2(c_b1, nb);
         }
+        tissue = !below;
       }
     }
     const unsigned ball = __ballot_sync(0xFFFFFFFFu, tissue);
@@ -378,7 +385,10 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_window(WindowArgs a) {
     }
     if (!tissue) stack_get(s_stk, s_stq, ns - 1 - __popc(~ball & lt), w, qi);
     ns -= 32 - cnt;
-    pass1_chunk<PINV>(w, qi, true, lut, lr, NR1, NR2, L, C, g, s_queue, s_coarse, qn, c_nw, c_b0, c_b1);
+    if (wbelow)
+      pass1_chunk<PINV, true>(w, qi, true, lut, lr, NR1, NR2, L, C, g, s_queue, s_coarse, qn, c_nw, c_b0, c_b1);
+    else
+      pass1_chunk<PINV, false>(w, qi, true, lut, lr, NR1, NR2, L, C, g, s_queue, s_coarse, qn, c_nw, c_b0, c_b1);
   }
   __syncwarp();
   if (ns > 0) {   // the rest of the stack (fewer than 32)
@@ -386,16 +396,23 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_window(WindowArgs a) {
     unsigned w[12];
     unsigned qi = 0u;
     if (have) stack_get(s_stk, s_stq, (int)lane, w, qi);
-    pass1_chunk<PINV>(w, qi, have, lut, lr, NR1, NR2, L, C, g, s_queue, s_coarse, qn, c_nw, c_b0, c_b1);
+    if (wbelow)
+      pass1_chunk<PINV, true>(w, qi, have, lut, lr, NR1, NR2, L, C, g, s_queue, s_coarse, qn, c_nw, c_b0, c_b1);
+    else
+      pass1_chunk<PINV, false>(w, qi, have, lut, lr, NR1, NR2, L, C, g, s_queue, s_coarse, qn, c_nw, c_b0, c_b1);
   }
   if (qn > 0) {
     __syncwarp();
     drain_queue<PINV>(s_queue, qn, g, lut, lr, L, C, s_coarse);
   }
-  // per-thread counts are exact in FP32 (fewer than 2^24 pixels per thread)
+  // per-thread counts are exact in FP32 (fewer than 2^24 pixels per thread).
+  // A thread's below counts can be negative (a tissue chunk's white pixels
+  // are taken off by the lane that classified it, and counted by the lane
+  // that runs its lasso); the sums wrap modulo 2^64 to the block's exact total.
+  auto as_u64 = [](float x) { return (u64)(long long)x; };
   const u64 t_nw = block_sum((u64)lo_of(c_nw) + (u64)hi_of(c_nw), s_tmp);
-  const u64 t_b0 = block_sum((u64)lo_of(c_b0) + (u64)hi_of(c_b0), s_tmp);
-  const u64 t_b1 = block_sum((u64)lo_of(c_b1) + (u64)hi_of(c_b1), s_tmp);
+  const u64 t_b0 = block_sum(as_u64(lo_of(c_b0)) + as_u64(hi_of(c_b0)), s_tmp);
+  const u64 t_b1 = block_sum(as_u64(lo_of(c_b1)) + as_u64(hi_of(c_b1)), s_tmp);
   if (threadIdx.x == 0) {
     if (t_nw) atomicAdd(&a.sel->n_nw, t_nw);
     if (t_b0) atomicAdd(&a.sel->below[0], t_b0);

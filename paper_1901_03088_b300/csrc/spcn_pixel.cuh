@@ -196,7 +196,12 @@ __device__ __forceinline__ void window_hit(const WindowConst& C, unsigned* s_coa
 // with packed FMAs.  The number of windows a pixel falls in (0, 1 or 2) is
 // packed base 4 into `mask` (pixel pair p at digit 7-p, even pixels in the
 // low lane, odd pixels in the high lane): exact small integers in FP32.
-template <bool PINV = false>
+// WHITES_BELOW: every white pixel is known to lie below both window starts
+// (see whites_below), so the pixels are not masked by their non-white flag:
+// a white pixel adds 1 to each below count, which the caller has subtracted
+// (with the chunk's non-white count added) when it classified the chunk, and
+// is never in a window.
+template <bool PINV = false, bool WHITES_BELOW = false>
 __device__ __forceinline__ void window_chunk(const unsigned (&w)[12], const char* lut,
                                              unsigned lr, f2 NR1, f2 NR2, float kappa,
                                              const WindowConst& a, f2& c_nw, f2& c_b0, f2& c_b1,
@@ -211,20 +216,26 @@ __device__ __forceinline__ void window_chunk(const unsigned (&w)[12], const char
     pixel_addr(w, kB, lr, aRB, aGB, aBB);
     f2 H1, H2;
     solve_pair<PINV>(lut, aRA, aGA, aBA, aRB, aGB, aBB, NR1, NR2, kappa, H1, H2);
-    const bool nwA = min(min(aRA, aGA), aBA) < a.wthr;
-    const bool nwB = min(min(aRB, aGB), aBB) < a.wthr;
-    const f2 NW = pk(nwA ? 1.f : 0.f, nwB ? 1.f : 0.f);
-    c_nw = add2(c_nw, NW);
     const float h1A = lo_of(H1), h1B = hi_of(H1), h2A = lo_of(H2), h2B = hi_of(H2);
     const f2 B0 = pk(fma_sat(h1A, a.nk0, a.lk0), fma_sat(h1B, a.nk0, a.lk0));
     const f2 B1 = pk(fma_sat(h2A, a.nk1, a.lk1), fma_sat(h2B, a.nk1, a.lk1));
     const f2 T0 = pk(fma_sat(h1A, a.nh0, a.hk0), fma_sat(h1B, a.nh0, a.hk0));
     const f2 T1 = pk(fma_sat(h2A, a.nh1, a.hk1), fma_sat(h2B, a.nh1, a.hk1));
-    c_b0 = fma2(B0, NW, c_b0);
-    c_b1 = fma2(B1, NW, c_b1);
     // T - B is 1 exactly for an in-window density
     const f2 X = add2(fma2(B0, M1, T0), fma2(B1, M1, T1));
-    mask = fma2(mask, FOUR, mul2(X, NW));
+    if (WHITES_BELOW) {
+      c_b0 = add2(c_b0, B0);
+      c_b1 = add2(c_b1, B1);
+      mask = fma2(mask, FOUR, X);
+    } else {
+      const bool nwA = min(min(aRA, aGA), aBA) < a.wthr;
+      const bool nwB = min(min(aRB, aGB), aBB) < a.wthr;
+      const f2 NW = pk(nwA ? 1.f : 0.f, nwB ? 1.f : 0.f);
+      c_nw = add2(c_nw, NW);
+      c_b0 = fma2(B0, NW, c_b0);
+      c_b1 = fma2(B1, NW, c_b1);
+      mask = fma2(mask, FOUR, mul2(X, NW));
+    }
   }
 }
 
@@ -292,16 +303,15 @@ __device__ __forceinline__ void chunk_channel_min(const unsigned (&w)[12], unsig
 }
 
 // True when every pixel of a full chunk is below both window starts: the
-// densities' bound D~ at the chunk's per-channel minima (the same table
-// sums and saturation as solve_one) passes the window's exact test.  Every
+// densities' bound D~ at the per-channel minima rg (R in byte 1, G in byte 3)
+// and bb (B in byte 1), with the same table sums and saturation as
+// solve_one, passes the window's exact test.  Every
 // table entry is non-increasing in the intensity (W >= 0), FP32 addition and
 // the saturation are monotone, and h~ = min(D~, t) <= D~, so each pixel's
 // test gives the same 1.  (Not for the pseudo-inverse, whose rows may be
 // negative.)
-__device__ __forceinline__ bool chunk_below_window(const unsigned (&w)[12], const char* lut,
-                                                   unsigned lr, const WindowConst& C) {
-  unsigned rg, bb;
-  chunk_channel_min(w, &rg, &bb);
+__device__ __forceinline__ bool below_bound(unsigned rg, unsigned bb, const char* lut,
+                                            unsigned lr, const WindowConst& C) {
   // table offsets: the intensity in byte 1, the lane's copy in byte 0
   const float2 eR = lut_ld(lut, __byte_perm(rg, lr, 0x5514u));
   const float2 eG = lut_ld(lut, __byte_perm(rg, lr, 0x5534u) + kLutOffG);
@@ -309,6 +319,23 @@ __device__ __forceinline__ bool chunk_below_window(const unsigned (&w)[12], cons
   const float D1 = add_sat(eR.x + eG.x, eB.x);
   const float D2 = add_sat(eR.y + eG.y, eB.y);
   return fma_sat(D1, C.nk0, C.lk0) == 1.f && fma_sat(D2, C.nk1, C.lk1) == 1.f;
+}
+__device__ __forceinline__ bool chunk_below_window(const unsigned (&w)[12], const char* lut,
+                                                   unsigned lr, const WindowConst& C) {
+  unsigned rg, bb;
+  chunk_channel_min(w, &rg, &bb);
+  return below_bound(rg, bb, lut, lr, C);
+}
+
+// True when every white pixel (all channels above the threshold T) lies
+// below both window starts: the same bound at the intensities (T+1, T+1,
+// T+1), which every white pixel's channels reach or exceed.  At T = 255 no
+// pixel is white.  The same value on every thread.
+__device__ __forceinline__ bool whites_below(unsigned T, const char* lut, unsigned lr,
+                                             const WindowConst& C) {
+  if (T >= 255u) return true;
+  const unsigned t1 = T + 1u;
+  return below_bound((t1 << 8) | (t1 << 24), t1 << 8, lut, lr, C);
 }
 
 // Constants of the byte test "above the white threshold T" used by
