@@ -91,3 +91,41 @@ def test_white_chunks_are_a_real_share(image):
     white_chunk = (px.amin(dim=(2, 3)) > 220)
     frac = white_chunk.float().mean().item()
     assert 0.2 < frac < 0.8
+
+
+def faint_colour_image(h, w, seed, dev):
+    """Half light-gray pixels (channels 140-255), half faintly red ones
+    (R 100-128, G and B 200-255), drawn independently per pixel."""
+    g = torch.Generator(device="cpu")
+    g.manual_seed(seed)
+    gray = torch.randint(140, 256, (h, w, 3), generator=g)
+    red = torch.stack([torch.randint(100, 129, (h, w), generator=g),
+                       torch.randint(200, 256, (h, w), generator=g),
+                       torch.randint(200, 256, (h, w), generator=g)], dim=-1)
+    pick = torch.rand((h, w), generator=g) < 0.5
+    return torch.where(pick.unsqueeze(-1), gray, red).to(torch.uint8).to(dev)
+
+
+def test_percentile_when_white_pixels_reach_the_window(spcn, ctx):
+    """Pass 1 may count a tissue chunk without testing each pixel for white
+    only when every white pixel provably lies below both window starts.  Here
+    the first stain points along the gray direction, so at threshold 128 the
+    light-gray (white) pixels get larger densities than the 99th percentile of
+    the faintly coloured non-white ones: the per-pixel masks are needed, and
+    the window (an exact hint) holds the ranks.  The image is 1037 wide, so
+    every row ends with a partial chunk."""
+    dev = torch.device("cuda", 0)
+    img = faint_colour_image(1024, 1037, 11, dev)
+    W = np.array([[1.0, 0.1], [1.0, 0.7], [1.0, 0.7]])
+    W = W / np.linalg.norm(W, axis=0)
+    st = spcn.Stats.from_values(W, [255.0, 255.0, 255.0])
+    thresh = 128
+    Hd = ctx.stain_densities(img, st)
+    nw = (img.reshape(-1, 3).amin(dim=1) <= thresh)
+    assert 0.3 < nw.float().mean().item() < 0.7
+    ref = [type7(Hd[j][nw], 99.0) for j in range(2)]
+    # the premise: white pixels reach above the first stain's percentile
+    assert Hd[0][~nw].max().item() > ref[0]
+    st.p99[0], st.p99[1] = ref
+    got = ctx.stain_percentile(img, st, spcn.params(white_thresh=thresh))
+    assert got[0] == ref[0] and got[1] == ref[1]
