@@ -202,6 +202,14 @@ def crop_for_oracle(src, side):
     return np.ascontiguousarray(src[y0:y0 + side, x0:x0 + side].cpu().numpy())
 
 
+def normalize_workload_desc(name, wl):
+    """The normalisation workload as both arms name it in their config."""
+    return (f"{name}: {wl['width']}x{wl['height']} uint8 RGB source, "
+            f"{wl['tgt']}x{wl['tgt']} target, basis from "
+            + (f"{wl['n_patches']} patches of {wl['patch_size']}^2"
+               if wl["sample_mode"] == "patches" else f"{wl['sample_rate']:.0%} hash sample"))
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
@@ -227,8 +235,9 @@ def run_reference(args, world, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": args.workload, "oracle_crop": f"{side}x{side}",
-                   "l2": "per-step inputs far smaller than the host caches' effect is irrelevant to the oracle"},
+        "config": {"workload": (normalize_workload_desc(args.workload, wl) if "tgt" in wl
+                                else args.workload), "oracle_crop": f"{side}x{side}",
+                   "l2": "not applicable: the oracle runs on the host cores"},
         "cpu_baseline": {"value": gpx, "unit": "Gpx/s", "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": gpx, "unit": "Gpx/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -627,10 +636,7 @@ def run_ours(args, world, rank, local):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {
-            "workload": f"{args.workload}: {Wd}x{Hd} uint8 RGB source, "
-                        f"{wl['tgt']}x{wl['tgt']} target, basis from "
-                        + (f"{wl['n_patches']} patches of {wl['patch_size']}^2"
-                           if wl["sample_mode"] == "patches" else f"{wl['sample_rate']:.0%} hash sample"),
+            "workload": normalize_workload_desc(args.workload, wl),
             "pixels_per_step": npx, "parallelism": f"replicas x{world}",
             "l2": f"inputs ({3 * npx / 1e9:.1f} GB) larger than L2 (126 MB); no flush",
             "target_stats_ms_once": round(tgt_ms, 3), "generate_s": round(gen_s, 2),
