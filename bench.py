@@ -176,22 +176,142 @@ def max_over_ranks(x, world, device):
 
 
 # ----------------------------------------------------------------- oracle arm
-def oracle_sample_run(src_np, tgt_np, wl, seed):
-    """The oracle's full path on a bounded crop: basis + exact P99 of source
-    and target, then normalisation.  Returns seconds."""
+# The oracle, as it stands, timed on every host core.  Its per-pixel steps
+# (densities of every pixel for the exact P99, then Eq. 3-4 and rounding) are
+# elementwise, so rows of the image are split into bands and each band runs
+# through the oracle's own functions in a worker process; the percentile is
+# the oracle's, over the concatenated non-white densities in raster order, so
+# every value equals the single-process result.  Basis estimation (sampling,
+# i0, sparse NMF, ordering) is one process, as the oracle defines it.  Arrays
+# travel through memory-mapped files, not pickles.
+BAND_PX = 1 << 20          # pixels per band (bounds each worker's temporaries)
+
+
+def _oracle_import(_):
+    """Worker warm-up: the imports a band needs."""
+    import numpy  # noqa: F401
+    from oracle import spcn_oracle  # noqa: F401
+    return os.getpid()
+
+
+def _oracle_band(task):
+    """Worker: one band of rows through the oracle.  kind 'dens' writes the
+    band's densities (2 x n) and non-white mask; kind 'norm' writes the
+    band's normalised uint8 pixels."""
+    import numpy as np
     from oracle import spcn_oracle as O
-    h, w, _ = src_np.shape
-    if wl["sample_mode"] == "patches":
-        # the slide's patch density (200 patches of 256^2 over 8 Gpx) scaled to the crop
-        p = O.Params(sample_mode="patches", n_patches=max(1, min(8, int(200 * h * w / 8e9) + 1)),
-                     patch_size=min(256, h, w), seed=seed)
+    kind, d, shape, r0, r1, a, b = task
+    h, w = shape
+    img = np.memmap(os.path.join(d, "src.u8"), np.uint8, "r", shape=(h, w, 3))
+    band = np.ascontiguousarray(img[r0:r1])
+    if kind == "dens":
+        W, i0, lam, thr = a
+        Hs = np.memmap(os.path.join(d, "H.f64"), np.float64, "r+", shape=(2, h * w))
+        nw = np.memmap(os.path.join(d, "nw.b"), np.bool_, "r+", shape=(h * w,))
+        Hs[:, r0 * w:r1 * w] = O.stain_densities(band, W, i0, lam)
+        nw[r0 * w:r1 * w] = O.nonwhite_mask(band.reshape(-1, 3), thr)
     else:
-        p = O.Params(sample_mode="hash", sample_rate=wl["sample_rate"], seed=seed)
-    t0 = time.perf_counter()
-    s_st = O.full_stats(src_np, p)
-    t_st = O.full_stats(tgt_np, O.Params(sample_mode="hash", sample_rate=wl["sample_rate"]))
-    O.normalize(src_np, s_st, t_st)
-    return time.perf_counter() - t0, p
+        out = np.memmap(os.path.join(d, "out.u8"), np.uint8, "r+", shape=(h, w, 3))
+        out[r0:r1] = O.normalize(band, a, b)
+    return r1 - r0   # shared file mappings: the parent sees the pages without msync
+
+
+class OraclePool:
+    """A spawn-started process pool over every host core (safe after CUDA is
+    initialised), with a scratch directory for the shared arrays."""
+
+    def __init__(self):
+        import multiprocessing as mp
+        import tempfile
+        self.cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") \
+            else (os.cpu_count() or 1)
+        saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS",
+                                                 "MKL_NUM_THREADS")}
+        for k in saved:
+            os.environ[k] = "1"            # one thread per worker; the pool supplies the cores
+        try:
+            self.pool = mp.get_context("spawn").Pool(self.cores)
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        shm = "/dev/shm"
+        roomy = os.path.isdir(shm) and os.statvfs(shm).f_bavail * os.statvfs(shm).f_frsize > 4e9
+        self.dir = tempfile.mkdtemp(prefix="spcn_oracle_", dir=shm if roomy else None)
+        self.pool.map(_oracle_import, range(4 * self.cores), chunksize=1)   # workers imported
+
+    def close(self):
+        import shutil
+        self.pool.terminate()
+        self.pool.join()
+        shutil.rmtree(self.dir, ignore_errors=True)
+
+    def bands(self, h, w):
+        """Row bands: at least four per worker, at most BAND_PX pixels each."""
+        rows = max(1, min(BAND_PX // max(1, w), -(-h // (4 * self.cores))))
+        return [(r, min(h, r + rows)) for r in range(0, h, rows)]
+
+    def step(self, img, tgt_st, p):
+        """One oracle step on the host image `img` (h x w x 3 uint8): basis
+        estimation with the oracle's Params p, exact non-white P99 of the
+        whole image (parallel densities), normalisation (parallel).  Returns
+        the seconds of each part, the statistics and the output."""
+        import numpy as np
+        from oracle import spcn_oracle as O
+        h, w, _ = img.shape
+        src = np.memmap(os.path.join(self.dir, "src.u8"), np.uint8, "w+", shape=(h, w, 3))
+        src[:] = img
+        for name, dt, shp in (("H.f64", np.float64, (2, h * w)), ("nw.b", np.bool_, (h * w,)),
+                              ("out.u8", np.uint8, (h, w, 3))):
+            np.memmap(os.path.join(self.dir, name), dt, "w+", shape=shp)
+        t0 = time.perf_counter()
+        st = O.estimate_basis(img, p)
+        t1 = time.perf_counter()
+        bands = self.bands(h, w)
+        self.pool.map(_oracle_band, [("dens", self.dir, (h, w), r0, r1,
+                                      (st.W, st.i0, p.lam, p.white_thresh), None)
+                                     for r0, r1 in bands], chunksize=1)
+        Hs = np.memmap(os.path.join(self.dir, "H.f64"), np.float64, "r", shape=(2, h * w))
+        nw = np.memmap(os.path.join(self.dir, "nw.b"), np.bool_, "r", shape=(h * w,))
+        mask = np.array(nw)
+        st.p99 = np.array([O.percentile(np.asarray(Hs[j])[mask], p.stain_pct) for j in range(2)])
+        t2 = time.perf_counter()
+        self.pool.map(_oracle_band, [("norm", self.dir, (h, w), r0, r1, st, tgt_st)
+                                     for r0, r1 in bands], chunksize=1)
+        t3 = time.perf_counter()
+        out = np.array(np.memmap(os.path.join(self.dir, "out.u8"), np.uint8, "r", shape=(h, w, 3)))
+        return {"basis_s": t1 - t0, "p99_s": t2 - t1, "normalize_s": t3 - t2}, st, out
+
+
+def oracle_target_stats(tgt_np, wl):
+    """The target's statistics, once, as the GPU step has them (basis from a
+    hash sample, exact P99)."""
+    from oracle import spcn_oracle as O
+    return O.full_stats(tgt_np, O.Params(sample_mode="hash", sample_rate=wl["sample_rate"],
+                                         seed=1))
+
+
+def oracle_params(wl, side, n_patches):
+    """The oracle's sampling for a crop of `side`^2 and the factor that scales
+    its sample to the slide's: patches (n_patches of the workload's size) or
+    the workload's hash rate (sample proportional to the pixels)."""
+    from oracle import spcn_oracle as O
+    if wl["sample_mode"] == "patches":
+        ps = min(wl["patch_size"], side)      # a crop smaller than a patch takes smaller patches
+        return (O.Params(sample_mode="patches", n_patches=n_patches, patch_size=ps, seed=0),
+                wl["n_patches"] * wl["patch_size"] ** 2 / (n_patches * ps * ps))
+    return (O.Params(sample_mode="hash", sample_rate=wl["sample_rate"], seed=0),
+            wl["width"] * wl["height"] / (side * side))
+
+
+def oracle_step_rate(parts, crop_px, slide_px, basis_scale):
+    """Seconds of one slide step from one timed oracle step: the basis time
+    scaled to the slide's sample (the sparse NMF's work is linear in it), the
+    per-pixel time scaled to the slide's pixels."""
+    return (parts["basis_s"] * basis_scale
+            + (parts["p99_s"] + parts["normalize_s"]) * slide_px / crop_px)
 
 
 def crop_for_oracle(src, side):
@@ -210,35 +330,66 @@ def normalize_workload_desc(name, wl):
                if wl["sample_mode"] == "patches" else f"{wl['sample_rate']:.0%} hash sample"))
 
 
+def normalize_config(name, wl, world):
+    """The config object of a normalisation line, the same in both arms."""
+    npx = wl["width"] * wl["height"]
+    return {"workload": normalize_workload_desc(name, wl), "pixels_per_step": npx,
+            "parallelism": f"replicas x{world}",
+            "l2": f"inputs ({3 * npx / 1e9:.1f} GB) larger than L2 (126 MB); no flush"}
+
+
+def oracle_sample_desc(side, p, basis_scale, wl, parts, cores, scaled_s):
+    smp = (f"{p.n_patches} patches of {p.patch_size}^2" if p.sample_mode == "patches"
+           else f"a {p.sample_rate:.0%} hash sample of the crop")
+    return (f"per step: oracle basis estimation from {smp} (one process; scaled "
+            f"x{basis_scale:g} to the slide's sample), then the exact non-white P99 and the "
+            f"normalisation of a "
+            f"{side}x{side} centre crop of the synthetic slide in row bands over {cores} worker "
+            f"processes (scaled to the slide's pixels); timed {parts['basis_s']:.2f} + "
+            f"{parts['p99_s']:.2f} + {parts['normalize_s']:.2f} s -> {scaled_s:.1f} s per slide; "
+            "numpy FP64")
+
+
 def run_reference(args, world, rank):
+    """The oracle arm: each step one bounded sample of the slide workload
+    (basis from 25 of the 200 patches, per-pixel steps of a 2048^2 crop over
+    every host core), scaled to one slide."""
     if rank != 0:
         return 0
     import numpy as np
     from paper_1901_03088_b300 import synth
     wl = WORKLOADS[args.workload]
-    side = args.oracle_side
+    if "n_patches" not in wl or "tgt" not in wl:
+        print(json.dumps({"impl": "reference", "unavailable":
+                          f"the oracle arm times the normalisation workloads, not {args.workload}"}))
+        return 0
+    side = min(args.oracle_side, wl["width"], wl["height"])
+    p, scale = oracle_params(wl, side, max(1, wl["n_patches"] // 8))
     src = synth.make_image(side, side, 1000, blobs=True)
-    tgt = synth.make_image(512, 512, 1, blobs=True)
-    for _ in range(args.warmup):
-        oracle_sample_run(src, tgt, wl, 0)
-    times = []
-    p = None
-    for _ in range(args.steps):
-        t, p = oracle_sample_run(src, tgt, wl, 0)
-        times.append(t)
-    ms = 1e3 * statistics.mean(times)
-    gpx = side * side / (ms / 1e3) / 1e9
-    sample = (f"{side}x{side} synthetic crop (blobs), full oracle path per step: basis "
-              f"({p.sample_mode}), exact P99 of source and a 512x512 target, normalisation")
+    tgt = synth.make_image(wl["tgt"], wl["tgt"], 1, blobs=True)
+    t_st = oracle_target_stats(tgt, wl)
+    pool = OraclePool()
+    try:
+        for _ in range(args.warmup):
+            pool.step(src, t_st, p)
+        per = []
+        parts = None
+        for _ in range(args.steps):
+            parts, _, _ = pool.step(src, t_st, p)
+            per.append(oracle_step_rate(parts, side * side, wl["width"] * wl["height"], scale))
+    finally:
+        pool.close()
+    npx = wl["width"] * wl["height"]
+    sec = statistics.mean(per)
+    gpx = npx / sec / 1e9
+    sample = oracle_sample_desc(side, p, scale, wl, parts, pool.cores, sec)
     line = {
         "impl": "reference", "metric": METRIC, "value": gpx, "unit": "Gpx/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": (normalize_workload_desc(args.workload, wl) if "tgt" in wl
-                                else args.workload), "oracle_crop": f"{side}x{side}",
-                   "l2": "not applicable: the oracle runs on the host cores"},
-        "cpu_baseline": {"value": gpx, "unit": "Gpx/s", "cores": 1, "kind": "oracle",
+        "config": normalize_config(args.workload, wl, world),
+        "cpu_baseline": {"value": gpx, "unit": "Gpx/s", "cores": pool.cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": gpx, "unit": "Gpx/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -247,9 +398,10 @@ def run_reference(args, world, rank):
 
 
 # ----------------------------------------------------------------- CUDA arm
-def run_grad(args, world, rank, local):
+def run_grad(args, world, rank, local, leg=False):
     """Forward + hand-written backward of the differentiable normalisation on a
-    batch of 64 float32 3x256x256 images, against forward only."""
+    batch of 64 float32 3x256x256 images, against forward only.  As a leg of
+    the default run it returns a summary instead of printing a line."""
     import numpy as np
     import torch
     from paper_1901_03088_b300 import build
@@ -335,6 +487,20 @@ def run_grad(args, world, rank, local):
     peak, peak_kind = read_peaks()
     bytes_fb = 60 * npx          # forward 12 in + 12 out, backward 12 (x) + 12 (gy) + 12 (gx)
     kf_ms, kb_ms = k_f / max(1, n_f), k_b / max(1, n_b)
+    if leg:
+        ctx.close()
+        return {"workload": f"{B} x 3 x {H} x {W} float32, own source statistics per image",
+                "fwd_ms": round(ms_f, 5), "fwd_bwd_ms": round(ms_fb, 5),
+                "ratio": round(ms_fb / ms_f, 3),
+                "fwd_gpx_s": world * npx / (ms_f / 1e3) / 1e9,
+                "fwd_bwd_gpx_s": world * npx / (ms_fb / 1e3) / 1e9,
+                "kernel_ms": {"forward": round(kf_ms, 5), "backward": round(kb_ms, 5)},
+                "roofline_frac": bytes_fb / (ms_fb / 1e3) / 1e9 / peak,
+                "roofline_bytes_per_px": 60,
+                "backward_roofline_frac": 36 * npx / (kb_ms / 1e3) / 1e9 / peak,
+                "timing": "CUDA-graph replays of the autograd step (forward only / forward + "
+                          "backward), CUDA events",
+                "gpu_launches_per_step": launches // max(1, args.steps), "clocks": clk.summary()}
     line = {
         "metric": METRIC, "value": world * npx / (ms_fb / 1e3) / 1e9, "unit": "Gpx/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_fb,
@@ -361,11 +527,12 @@ def run_grad(args, world, rank, local):
     return 0
 
 
-def run_batch(args, world, rank, local):
+def run_batch(args, world, rank, local, leg=False):
     """256 uneven tiles from 32 slides (own source statistics each), one
     target: one cooperative persistent launch per step (schedule from the
     library's autotuner, replayed from a CUDA graph), against the same tiles
-    normalised by 256 sequential spcn_normalize calls."""
+    normalised by 256 sequential spcn_normalize calls.  As a leg of the
+    default run it returns a summary instead of printing a line."""
     import numpy as np
     import torch
     from paper_1901_03088_b300 import build
@@ -454,6 +621,26 @@ def run_batch(args, world, rank, local):
     k_ms /= max(1, k_n)
     peak, peak_kind = read_peaks()
     achieved = 9 * npx / (k_ms / 1e3) / 1e9
+
+    if leg:
+        out = {"workload": f"{len(tiles)} uint8 RGB tiles from {n_slides} slides, sides "
+                           f"log-uniform in [{wl['side_lo']}, {wl['side_hi']}], {npx / 1e6:.1f} Mpx, "
+                           f"one {wl['tgt']}x{wl['tgt']} target",
+               "ms": round(ms, 4), "gpx_s": world * npx / (ms / 1e3) / 1e9,
+               "plain_ms": round(ms_seq, 4), "plain_gpx_s": world * npx / (ms_seq / 1e3) / 1e9,
+               "speedup": ms_seq / ms, "kernel_ms": round(k_ms, 4),
+               "roofline_frac": achieved / peak, "roofline_bytes_per_px": 9,
+               "outputs_identical_to_plain": identical,
+               "tiles_exact_fallback": sum(fallback), "schedule": b.config,
+               "tune_s": round(tune_s, 2),
+               "timing": "CUDA-graph replays of one cooperative persistent launch vs "
+                         f"{len(tiles)} sequential spcn_normalize calls, CUDA events",
+               "gpu_launches_per_step": per_run, "clocks": clocks}
+        b.close()
+        ctx.close()
+        del tiles, outs, ref
+        torch.cuda.empty_cache()
+        return out
 
     # end to end: host tiles copied in, the batch run, outputs copied out
     e2e = None
@@ -579,9 +766,18 @@ def run_ours(args, world, rank, local):
         t_st.p99[0], t_st.p99[1] = ctx.stain_percentile(tgt, t_st, pt)
     tgt_ms = 1e3 * (time.perf_counter() - t1)
 
-    def step():
-        # basis estimation + both passes, statistics kept on the device
-        ctx.normalize_estimated(src, t_st, p, out=out)
+    if args.hint == "none":
+        def step():
+            # the exact fallback on record: the source's sampled percentile is
+            # dropped, so pass 1 runs without a window and the radix select over
+            # the image resolves both ranks (a host round trip separates the calls)
+            s_st = ctx.estimate_basis(src, p)
+            s_st.p99[0] = s_st.p99[1] = 0.0
+            ctx.normalize(src, s_st, t_st, p, out=out)
+    else:
+        def step():
+            # basis estimation + both passes, statistics kept on the device
+            ctx.normalize_estimated(src, t_st, p, out=out)
 
     for _ in range(args.warmup):
         step()
@@ -591,6 +787,7 @@ def run_ours(args, world, rank, local):
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     ctx.kernel_timing(True)
     launches0 = ctx.launches
+    fallbacks0 = ctx.exact_fallbacks
     with ClockSampler(local) as clk:
         barrier(world)
         torch.cuda.synchronize()
@@ -601,6 +798,7 @@ def run_ours(args, world, rank, local):
         torch.cuda.synchronize()
         barrier(world)
     launches = ctx.launches - launches0
+    fallbacks = ctx.exact_fallbacks - fallbacks0
     ms_local = evs[0].elapsed_time(evs[-1]) / args.steps
     per_step = sorted(evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps))
     ms = max_over_ranks(ms_local, world, dev)
@@ -611,6 +809,9 @@ def run_ours(args, world, rank, local):
     # the statistics of one step (bench output is not a parity test)
     _, s_st = ctx.normalize_estimated(src, t_st, p, out=out, return_stats=True)
     p99 = (s_st.p99[0], s_st.p99[1])
+    if args.hint == "none":
+        sampled_st = ctx.estimate_basis(src, p)
+        s_st.iters = sampled_st.iters
 
     # roofline of the dominant kernel
     dom = max(("pass1", "pass2"), key=lambda k: ktimes[k][0])
@@ -624,6 +825,13 @@ def run_ours(args, world, rank, local):
     if not args.no_e2e:
         e2e = run_e2e(args, ctx, spcn, src, t_st, p, dev, npx)
 
+    # the other two legs of the metric on the same GPU: the batched launch
+    # against plain calls, and forward + backward against forward only
+    legs = {}
+    if args.workload == "wsi" and not args.no_legs and not flags and args.hint == "sample":
+        legs["batched"] = run_batch(args, world, rank, local, leg=True)
+        legs["fwd_bwd"] = run_grad(args, world, rank, local, leg=True)
+
     cpu = None
     if rank == 0 and not args.no_cpu and not flags:
         cpu = cpu_baseline(src, tgt, wl, args)
@@ -635,15 +843,19 @@ def run_ours(args, world, rank, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {
-            "workload": normalize_workload_desc(args.workload, wl),
-            "pixels_per_step": npx, "parallelism": f"replicas x{world}",
-            "l2": f"inputs ({3 * npx / 1e9:.1f} GB) larger than L2 (126 MB); no flush",
+        "config": (normalize_config(args.workload, wl, world) if not flags
+                   and args.hint == "sample" else dict(normalize_config(args.workload, wl, world),
+                                                       variant=args.flags or "improved method",
+                                                       p99_window=args.hint)),
+        "details": {
             "target_stats_ms_once": round(tgt_ms, 3), "generate_s": round(gen_s, 2),
             "ms_per_step_best": round(per_step[0], 4),
             "ms_per_step_median": round(per_step[len(per_step) // 2], 4),
             "kernel_ms_per_step": {k: round(v[0] / max(1, v[1]), 4) for k, v in ktimes.items()},
-            "select_fallback_launches": ktimes["select"][1],
+            "select_kernel_launches": ktimes["select"][1],
+            "exact_fallback_steps": fallbacks,
+            "p99_window": ("none: sampled percentile dropped, exact radix select every step"
+                           if args.hint == "none" else "from the basis sample's percentile"),
             "src_p99": [round(p99[0], 6), round(p99[1], 6)], "snmf_iters": s_st.iters,
             "variant": args.flags or "improved method (no flags)",
         },
@@ -658,6 +870,7 @@ def run_ours(args, world, rank, local):
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    line.update(legs)
     if rank == 0:
         print(json.dumps(line))
     ctx.close()
@@ -829,15 +1042,23 @@ def run_e2e(args, ctx, spcn, src, t_st, p, dev, npx):
 
 
 def cpu_baseline(src, tgt, wl, args):
-    """The oracle, as it stands, on a bounded crop of the same slide."""
-    side = args.oracle_side
+    """The oracle, as it stands, on every host core: basis estimation at the
+    slide's own sampling (200 patches of 256^2, 13.1 Mpx) and the per-pixel
+    steps of an 8192^2 centre crop, scaled to the slide."""
+    import numpy as np
+    side = min(args.oracle_side, wl["width"], wl["height"])
     s = crop_for_oracle(src, side)
-    t = crop_for_oracle(tgt, 512)
-    dt, p = oracle_sample_run(s, t, wl, 0)
-    return {"value": side * side / dt / 1e9, "unit": "Gpx/s", "cores": 1, "kind": "oracle",
-            "sample": f"{side}x{side} centre crop of the slide (+512x512 target crop), full "
-                      f"oracle path: basis ({p.sample_mode}), exact P99, normalisation; "
-                      f"{dt:.1f} s single-threaded numpy FP64"}
+    t_st = oracle_target_stats(np.ascontiguousarray(tgt.cpu().numpy()), wl)
+    p, scale = oracle_params(wl, side, wl["n_patches"])
+    pool = OraclePool()
+    try:
+        parts, _, _ = pool.step(s, t_st, p)
+    finally:
+        pool.close()
+    sec = oracle_step_rate(parts, side * side, wl["width"] * wl["height"], scale)
+    return {"value": wl["width"] * wl["height"] / sec / 1e9, "unit": "Gpx/s",
+            "cores": pool.cores, "kind": "oracle",
+            "sample": oracle_sample_desc(side, p, scale, wl, parts, pool.cores, sec)}
 
 
 def main():
@@ -859,6 +1080,11 @@ def main():
                          + ", ".join(FLAG_NAMES) + "); p99_sampled is the one-pass step")
     ap.add_argument("--no-tune", action="store_true",
                     help="batch workload: keep the default schedule (no autotuner runs)")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="wsi workload: skip the batched and forward+backward legs")
+    ap.add_argument("--hint", choices=["sample", "none"], default="sample",
+                    help="wsi/tile workloads: 'none' drops the sampled percentile, so every "
+                         "step takes the exact radix-select fallback (its cost on record)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")
@@ -866,7 +1092,7 @@ def main():
         world = int(os.environ.get("WORLD_SIZE", "1"))
         rank = int(os.environ.get("RANK", "0"))
         if args.oracle_side == 8192:
-            args.oracle_side = 1024
+            args.oracle_side = 2048     # each of the K + W steps is a bounded sample
         return run_reference(args, world, rank)
     world, rank, local = dist_setup(args)
     rc = run_ours(args, world, rank, local)

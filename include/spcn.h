@@ -253,7 +253,9 @@ int spcn_normalize_f32(void* ctx, const float* x, int32_t batch, int32_t height,
  * The densities are recomputed, not stored; through the lasso the derivative
  * follows each pixel's active set (inactive densities have zero derivative),
  * through Eq. 1 it is -1/x (0 where the clamp at 1 is active).  The W_target
- * sum is reduced in a fixed order (deterministic).  Asynchronous. */
+ * sum is reduced in a fixed order (deterministic), in FP64, launch by launch
+ * for batches larger than one launch; any batch the forward accepts is
+ * accepted.  Asynchronous.  Errors: INVALID_ARG, DEGENERATE_BASIS, CUDA. */
 int spcn_normalize_f32_backward(void* ctx, const float* x, const float* gy, int32_t batch,
                                 int32_t height, int32_t width, const spcn_stats* src_stats,
                                 const spcn_stats* tgt_stats, const float* wt,
@@ -270,7 +272,8 @@ int spcn_normalize_f32_backward(void* ctx, const float* x, const float* gy, int3
  *   Limits: at most 524288 sample pixels (SPCN_SAMPLE_ALL: width*height;
  *   SPCN_SAMPLE_HASH: round(rate*N); SPCN_SAMPLE_PATCHES:
  *   n_patches*patch_size^2) and at most 4096 patches; larger requests return
- *   SPCN_ERR_SCRATCH_LIMIT without touching the device.
+ *   SPCN_ERR_SCRATCH_LIMIT without touching the device.  Invalid images or
+ *   parameters return SPCN_ERR_INVALID_ARG before any size is derived.
  *   The first call on a device does a one-time set-up (resolves the array's
  *   device address, reads launch attributes); make that first call before
  *   any stream capture.  All calls share the one array, so calls that
@@ -370,6 +373,12 @@ int spcn_normalize_batched(void* ctx, int32_t n, const spcn_image* tiles,
 /* Number of kernels the context has launched since creation (for launch
  * accounting in benchmarks). */
 int64_t spcn_launch_count(void* ctx);
+
+/* Number of whole-image percentiles (Eq. 3's exact P99, §3.1 item 2) that
+ * this context resolved with the exact radix select over the image because a
+ * rank fell outside pass 1's window, since the context was created.  Waits
+ * for the context's device.  Errors: INVALID_ARG, CUDA. */
+int spcn_exact_fallbacks(void* ctx, int64_t* count);
 
 /* Kernels whose launches can be timed (spcn_kernel_timing). */
 typedef enum {

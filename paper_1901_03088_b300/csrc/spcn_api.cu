@@ -16,6 +16,7 @@ namespace spcn {
 int ensure_sample_capacity(Context* c, size_t n) {
   if (n == 0) n = 1;
   const size_t nblk = (n + 4095) / 4096;
+  if (c->fixed_scratch && (n > c->sample_cap || nblk > c->blk_cap)) return SPCN_ERR_SCRATCH_LIMIT;
   if (n > c->sample_cap) {
     cudaFree(c->sample);
     cudaFree(c->nw);
@@ -41,6 +42,7 @@ int ensure_sample_capacity(Context* c, size_t n) {
 }
 
 int ensure_candidate_capacity(Context* c, int n) {
+  if (c->fixed_scratch && n > c->cand_cap) return SPCN_ERR_SCRATCH_LIMIT;
   if (n > c->cand_cap) {
     cudaFree(c->cand);
     c->cand = nullptr;
@@ -94,7 +96,7 @@ static void free_all(Context* c) {
   c->pool.clear();
   void* ptrs[] = {c->err, c->model, c->model_b, c->sel, c->coarse, c->fine, c->rhist,
                   c->rhist_b, c->partials, c->bs, c->wdev, c->sample, c->nw, c->br, c->blk,
-                  c->blk_off, c->cand};
+                  c->blk_off, c->cand, c->fallbacks};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -271,8 +273,10 @@ int spcn_context_create(void** out, int device) {
     ALLOC(c->partials, sizeof(double) * 2 * 4096 * kAcc);
     ALLOC(c->bs, sizeof(BasisState));
     ALLOC(c->wdev, sizeof(Window));
+    ALLOC(c->fallbacks, sizeof(u64));
 #undef ALLOC
     if (cudaMemset(c->err, 0, sizeof(int)) != cudaSuccess) { rc = SPCN_ERR_CUDA; break; }
+    if (cudaMemset(c->fallbacks, 0, sizeof(u64)) != cudaSuccess) { rc = SPCN_ERR_CUDA; break; }
     rc = configure_pixel_kernels(c);
     if (rc) break;
     rc = configure_basis_kernels(c);
@@ -300,6 +304,18 @@ int spcn_context_destroy(void* ctx) {
 
 int64_t spcn_launch_count(void* ctx) {
   return ctx ? static_cast<Context*>(ctx)->launches : 0;
+}
+
+int spcn_exact_fallbacks(void* ctx, int64_t* count) {
+  if (!ctx || !count) return SPCN_ERR_INVALID_ARG;
+  Context* c = static_cast<Context*>(ctx);
+  DeviceGuard guard(c->device);
+  u64 n = 0;
+  if (cudaDeviceSynchronize() != cudaSuccess ||
+      cudaMemcpy(&n, c->fallbacks, sizeof(u64), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return SPCN_ERR_CUDA;
+  *count = (int64_t)n;
+  return SPCN_OK;
 }
 
 int spcn_estimate_basis(void* ctx, const spcn_image* img, const spcn_params* params,

@@ -40,6 +40,7 @@ struct Context {
   double* partials = nullptr;      // [2][max grid][kAcc]
   BasisState* bs = nullptr;
   void* wdev = nullptr;            // P99 window computed on the device (struct Window)
+  u64* fallbacks = nullptr;        // whole-image percentiles resolved by the exact radix select
   // grown on demand
   uint32_t* sample = nullptr;      // packed RGB of the sample
   uint32_t* nw = nullptr;          // non-white sample pixels (stable order)
@@ -50,6 +51,9 @@ struct Context {
   size_t blk_cap = 0;
   int* cand = nullptr;             // patch candidates: counts, then accepted origins
   int cand_cap = 0;
+  // buffers point into memory the context does not own (the allocation-free
+  // entry point): a request beyond their capacity is refused, never regrown
+  bool fixed_scratch = false;
   int64_t launches = 0;
   // blocks per SM at the launch configuration of each kernel
   int occ_window = 0, occ_recon = 0, occ_density = 0, occ_select = 0;

@@ -227,13 +227,16 @@ __global__ void __launch_bounds__(kF32Threads, 4) k_f32_backward(F32Args a) {
   }
 }
 
-// Sum of all block partials in a fixed order; writes gwt (column-major).
-// kReduceLanes threads per entry k each add a fixed strided subset (loads
-// issued eight at a time), then a fixed pairwise tree in shared memory adds
-// their results: the same order on every run.
+// Sum of one launch's block partials in a fixed order.  kReduceLanes threads
+// per entry k each add a fixed strided subset (loads issued eight at a time),
+// then a fixed pairwise tree in shared memory adds their results.  A batch
+// larger than one launch carries its FP64 running sum in acc from launch to
+// launch (stream-ordered, so the order is the same on every run); the last
+// launch writes gwt (column-major).
 constexpr int kReduceLanes = 160;   // 6 x 160 = 960 threads
 __global__ void __launch_bounds__(6 * kReduceLanes) k_f32_reduce(const double* partials,
-                                                                  int nblocks, float* gwt) {
+                                                                  int nblocks, double* acc,
+                                                                  int first, int last, float* gwt) {
   __shared__ double s_part[6][256];
   const int k = threadIdx.x / kReduceLanes, i = threadIdx.x % kReduceLanes;
   double x = 0.0;
@@ -257,7 +260,12 @@ __global__ void __launch_bounds__(6 * kReduceLanes) k_f32_reduce(const double* p
     }
     __syncthreads();
   }
-  if (threadIdx.x < 6) gwt[threadIdx.x] = (float)s_part[threadIdx.x][0];
+  if (threadIdx.x < 6) {
+    double v = s_part[threadIdx.x][0];
+    if (!first) v += acc[threadIdx.x];
+    if (last) gwt[threadIdx.x] = (float)v;
+    else acc[threadIdx.x] = v;
+  }
 }
 
 // ------------------------------------------------------------ host side
@@ -292,40 +300,49 @@ static void f32_image_consts(const spcn_stats* src, const spcn_stats* tgt, float
     o->s[j] = (float)(src->p99[j] != 0.0 ? tgt->p99[j] / src->p99[j] : 1.0);
 }
 
+// The backward's block partials live in the context's partials buffer
+// (2 * 4096 * kAcc doubles): 6 per block, plus 6 for the running sum of a
+// batch that takes several launches.  Each launch is reduced before the next
+// one starts, so the blocks of one launch are capped, not those of a batch.
+constexpr size_t kF32PartialDoubles = (size_t)2 * 4096 * kAcc;
+constexpr int kF32MaxBlocks = (int)((kF32PartialDoubles - 8) / 6);
+
 int launch_f32(Context* c, bool backward, const float* x, const float* gy, int batch, int64_t hw,
                const spcn_stats* src, const spcn_stats* tgt, const float* wt, float lambda,
                float* y, float* gx, float* gwt, cudaStream_t st) {
-  F32Args a;   // ~17 KB parameter block, passed by value to each launch
+  F32Args a;   // ~21 KB parameter block, passed by value to each launch
   int bx = (int)((hw + kF32Threads * 8 - 1) / (kF32Threads * 8));   // about 8 pixels per thread
   if (bx < 1) bx = 1;
   if (bx > 1024) bx = 1024;
   const int launches = (batch + kF32MaxBatch - 1) / kF32MaxBatch;
-  const size_t nblocks = (size_t)bx * batch;
-  if (backward && nblocks * 6 > (size_t)2 * 4096 * kAcc) return SPCN_ERR_INVALID_ARG;
+  double* acc = c->partials + kF32PartialDoubles - 8;
   for (int l = 0; l < launches; ++l) {
     const int b0 = l * kF32MaxBatch;
     const int nb = batch - b0 < kF32MaxBatch ? batch - b0 : kF32MaxBatch;
+    int bxl = bx;
+    if (backward && bxl * nb > kF32MaxBlocks) bxl = kF32MaxBlocks / nb;   // nb <= 192: bxl >= 85
     a.x = x + (int64_t)b0 * 3 * hw;
     a.gy = gy ? gy + (int64_t)b0 * 3 * hw : nullptr;
     a.y = y ? y + (int64_t)b0 * 3 * hw : nullptr;
     a.gx = gx ? gx + (int64_t)b0 * 3 * hw : nullptr;
     a.wt = wt;
-    a.partials = c->partials + (size_t)b0 * bx * 6;
+    a.partials = c->partials;
     a.hw = hw;
     a.batch = nb;
     for (int k = 0; k < 3; ++k) a.l2i0t[k] = (float)log2((double)tgt->i0[k]);
     for (int i = 0; i < nb; ++i) f32_image_consts(&src[b0 + i], tgt, lambda, &a.img[i]);
-    const dim3 grid(bx, nb);
+    const dim3 grid(bxl, nb);
     {
       TimedLaunch tl(c, backward ? SPCN_KERNEL_F32_BWD : SPCN_KERNEL_F32_FWD, st);
       if (backward) k_f32_backward<<<grid, kF32Threads, 0, st>>>(a);
       else k_f32_forward<<<grid, kF32Threads, 0, st>>>(a);
     }
     SPCN_LAUNCH_CHECK(c);
-  }
-  if (backward) {
-    k_f32_reduce<<<1, 6 * kReduceLanes, 0, st>>>(c->partials, (int)nblocks, gwt);
-    SPCN_LAUNCH_CHECK(c);
+    if (backward) {
+      k_f32_reduce<<<1, 6 * kReduceLanes, 0, st>>>(c->partials, bxl * nb, acc, l == 0,
+                                                   l == launches - 1, gwt);
+      SPCN_LAUNCH_CHECK(c);
+    }
   }
   return SPCN_OK;
 }

@@ -80,6 +80,7 @@ static int noalloc_setup(int dev, Context** out) {
     c->nw = reinterpret_cast<uint32_t*>(base + kOffNw);
     c->br = reinterpret_cast<uint32_t*>(base + kOffBr);
     c->sample_cap = kNoAllocMaxSample;
+    c->fixed_scratch = true;
     int rc = configure_pixel_kernels(c);
     if (rc) return rc;
     rc = configure_basis_kernels(c);
@@ -99,18 +100,18 @@ using namespace spcn;
 
 extern "C" int spcn_estimate_basis_noalloc(const spcn_image* img, const spcn_params* params,
                                            spcn_stats* out, void* stream) {
-  if (!img || !params || !out || !img->data || img->width < 1 || img->height < 1 ||
-      img->pitch_bytes < 3ll * img->width)
-    return SPCN_ERR_INVALID_ARG;
-  // the sample must fit the static scratch
+  // the arguments are checked before any size is derived from them
+  if (!out || !image_ok(img) || !params_ok(params)) return SPCN_ERR_INVALID_ARG;
+  // the sample must fit the static scratch (a first, early answer: the
+  // capacity checks inside the estimation refuse anything larger as well,
+  // because this context's buffers are marked fixed)
   const u64 N = (u64)img->width * (u64)img->height;
   u64 need = 0;
   if (params->sample_mode == SPCN_SAMPLE_ALL) {
     need = N;
   } else if (params->sample_mode == SPCN_SAMPLE_HASH) {
     need = (u64)((double)params->sample_rate * (double)N + 0.5);
-  } else if (params->sample_mode == SPCN_SAMPLE_PATCHES) {
-    if (params->n_patches < 1 || params->patch_size < 1) return SPCN_ERR_INVALID_ARG;
+  } else {
     if (params->n_patches > kNoAllocMaxPatches) return SPCN_ERR_SCRATCH_LIMIT;
     need = (u64)params->n_patches * (u64)params->patch_size * (u64)params->patch_size;
   }

@@ -437,6 +437,7 @@ struct SelectImageArgs {
   const Model* m;
   SelectState* sel;
   u64* ghist;
+  u64* fallbacks;   // counts the launches that had a rank to resolve
   int* err;
   long long timeout_ns;
   double tgt0, tgt1;
@@ -445,6 +446,7 @@ struct SelectImageArgs {
 template <bool PINV>
 __global__ void __launch_bounds__(kPassThreads, 1) k_select_image(SelectImageArgs a) {
   if (*(volatile int*)&a.sel->all_resolved) return;   // uniform: every block returns
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(a.fallbacks, 1ull);
   extern __shared__ __align__(16) char s_dyn[];
   unsigned* s_hist = reinterpret_cast<unsigned*>(s_dyn + kLutSmemBytes);
   load_lut(a.m, s_dyn);
@@ -848,6 +850,7 @@ static int percentile_passes(Context* c, const Geometry& g, const Model* m, int 
   s.m = m;
   s.sel = c->sel;
   s.ghist = c->rhist;
+  s.fallbacks = c->fallbacks;
   s.err = c->err;
   s.timeout_ns = c->timeout_ns;
   s.tgt0 = a.tgt0;

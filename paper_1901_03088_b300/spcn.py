@@ -117,6 +117,7 @@ def _load():
                                                     P(Stats), vp]),
         "spcn_synchronize": (ctypes.c_int, [vp, vp]),
         "spcn_launch_count": (i64, [vp]),
+        "spcn_exact_fallbacks": (ctypes.c_int, [vp, P(i64)]),
         "spcn_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "spcn_debug_barrier_timeout": (ctypes.c_int, [vp, i32, i64, vp]),
         "spcn_kernel_timing": (ctypes.c_int, [vp, ctypes.c_int]),
@@ -152,7 +153,8 @@ lib = _lib
 # Every name the header declares, for the export check.
 EXPORTED = ("spcn_params_default", "spcn_context_create", "spcn_context_destroy",
             "spcn_estimate_basis", "spcn_stain_percentile", "spcn_stain_densities",
-            "spcn_normalize", "spcn_normalize_estimated", "spcn_synchronize", "spcn_launch_count", "spcn_strerror",
+            "spcn_normalize", "spcn_normalize_estimated", "spcn_synchronize", "spcn_launch_count",
+            "spcn_exact_fallbacks", "spcn_strerror",
             "spcn_debug_barrier_timeout", "spcn_kernel_timing", "spcn_kernel_times",
             "spcn_estimate_basis_noalloc", "spcn_normalize_f32", "spcn_normalize_f32_backward",
             "spcn_batch_create", "spcn_batch_run", "spcn_batch_results", "spcn_batch_get_config",
@@ -243,6 +245,14 @@ class Context:
     @property
     def launches(self) -> int:
         return int(_lib.spcn_launch_count(self._h))
+
+    @property
+    def exact_fallbacks(self) -> int:
+        """Whole-image percentiles resolved by the exact radix select (a rank
+        outside pass 1's window) since the context was created."""
+        n = ctypes.c_int64()
+        _check(_lib.spcn_exact_fallbacks(self._h, ctypes.byref(n)), "spcn_exact_fallbacks")
+        return int(n.value)
 
     def estimate_basis(self, img, p: Params | None = None, stream=None) -> Stats:
         st = Stats()

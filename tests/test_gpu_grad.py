@@ -1,12 +1,16 @@
 """GPU parity of the differentiable form (float CHW batches) against the FP64
 oracle's forward and analytic gradient, and against central differences.
 
-Tolerances (FP32 kernel vs FP64): y within 1e-5 relative (+1e-3 absolute for
-the approximate log/exp units); dL/dx, relative to max(|dL/dx|, 1e-3), within
-1e-6 at the median, 1e-4 at the 99.9th percentile and 1e-3 at the maximum of
-the pixels away from lasso kinks (KKT margin >= 1e-2) and the Eq. 1 clamp
-(measured: 8e-8, 5e-5, 3e-4); dL/dW_t within 1e-5 relative of the oracle
-(measured 6e-7) and within 1e-3 of FP64 central differences."""
+Tolerances (FP32 kernel vs FP64):
+* y within 1e-5 relative.
+* dL/dx within 1e-4 of max(|dL/dx|, S), S the componentwise condition scale
+  of the chain (tests/grad_measure.py), on the pixels away from lasso kinks
+  (KKT margin >= 1e-2) and the Eq. 1 clamp.  Measured against |dL/dx| alone
+  (floor 1e-3) the error also has a median within 1e-6 and a 99.9th
+  percentile within 1e-4; its maximum there is set by cancellation, which no
+  FP32 evaluation avoids (tests/test_grad_tolerance.py pins that).
+* dL/dW_t within 1e-5 relative of the oracle and within 1e-3 of FP64 central
+  differences."""
 import numpy as np
 import pytest
 
@@ -15,6 +19,7 @@ pytestmark = pytest.mark.gpu
 
 from oracle import spcn_oracle as O  # noqa: E402
 from paper_1901_03088_b300 import synth  # noqa: E402
+from grad_measure import condition_scale, kkt_margin  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -40,23 +45,23 @@ def _batch(spcn, B=3, H=40, W=48, seed=600):
 
 def _oracle(x, stats, tgt, Wt, gy):
     Y, GX = np.zeros_like(x, dtype=np.float64), np.zeros_like(x, dtype=np.float64)
+    S = np.zeros_like(x, dtype=np.float64)
     gW = np.zeros((3, 2))
     margin = np.zeros((x.shape[0], x.shape[2] * x.shape[3]))
     for b, st in enumerate(stats):
         X = x[b].reshape(3, -1).astype(np.float64)
+        G = gy[b].reshape(3, -1).astype(np.float64)
         Ws = np.array(st.basis, dtype=np.float64)
         i0s = np.array(st.i0[:], dtype=np.float64)
         s = O.stain_scale(st.p99[:], tgt.p99[:])
         Yb, H = O.normalize_float_pixels(X, Ws, i0s, s, Wt, np.array(tgt.i0[:], np.float64))
-        gx, gw = O.normalize_grad(X, gy[b].reshape(3, -1).astype(np.float64), Ws, i0s, s, Wt,
-                                  np.array(tgt.i0[:], np.float64))
+        gx, gw = O.normalize_grad(X, G, Ws, i0s, s, Wt, np.array(tgt.i0[:], np.float64))
         Y[b] = Yb.reshape(x[b].shape)
         GX[b] = gx.reshape(x[b].shape)
+        S[b] = condition_scale(X, G, Yb, H, Ws, s, Wt).reshape(x[b].shape)
         gW += gw
-        V = O.optical_density(X.T, i0s).T
-        g = (Ws.T @ Ws) @ H - Ws.T @ V + 0.1
-        margin[b] = np.min(np.abs(np.where(H > 0, H, g)), axis=0)
-    return Y, GX, gW, margin
+        margin[b] = kkt_margin(X, H, Ws, i0s, 0.1, O.optical_density)
+    return Y, GX, S, gW, margin
 
 
 def test_forward_and_backward_match_oracle(spcn):
@@ -68,14 +73,18 @@ def test_forward_and_backward_match_oracle(spcn):
     y = spcn.normalize_f32(ctx, xd, Wd, stats, tgt)
     gy = np.random.default_rng(3).normal(size=x.shape).astype(np.float32)
     (y * torch.from_numpy(gy).cuda()).sum().backward()
-    Y, GX, gW, margin = _oracle(x, stats, tgt, Wt.astype(np.float64), gy)
+    Y, GX, S, gW, margin = _oracle(x, stats, tgt, Wt.astype(np.float64), gy)
     yg = y.detach().cpu().numpy()
-    assert np.max(np.abs(yg - Y) / (1e-5 * np.maximum(np.abs(Y), 1.0) + 1e-3)) <= 1.0
+    assert np.max(np.abs(yg - Y) / np.abs(Y)) <= 1e-5
     gx = xd.grad.cpu().numpy()
     ok = (margin >= 1e-2)[:, None, :].repeat(3, axis=1).reshape(gx.shape) & (x > 1.01)
-    rel = np.abs(gx - GX)[ok] / np.maximum(np.abs(GX)[ok], 1e-3)
-    assert np.median(rel) <= 1e-6 and np.quantile(rel, 0.999) <= 1e-4 and rel.max() <= 1e-3
     assert np.mean(ok) > 0.5
+    err = np.abs(gx - GX)[ok]
+    den = np.maximum(np.abs(GX), S)[ok]
+    assert np.all(err[den == 0] == 0)           # no active stain: exactly zero
+    assert np.max(err[den > 0] / den[den > 0]) <= 1e-4
+    rel = err / np.maximum(np.abs(GX)[ok], 1e-3)
+    assert np.median(rel) <= 1e-6 and np.quantile(rel, 0.999) <= 1e-4
     gw = Wd.grad.cpu().numpy()
     assert np.max(np.abs(gw - gW)) <= 1e-5 * np.abs(gW).max()
     ctx.close()
@@ -117,4 +126,31 @@ def test_backward_is_deterministic(spcn):
         spcn.normalize_f32(ctx, xd, Wd, stats, tgt).square().mean().backward()
         out.append((xd.grad.clone(), Wd.grad.clone()))
     assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
+    ctx.close()
+
+
+@pytest.mark.parametrize("B,H,W", [(64, 1024, 1024), (200, 64, 64)])
+def test_backward_of_large_batches_equals_per_image_calls(spcn, B, H, W):
+    # 64 x 1024^2 needs more block partials than one launch may hold (the
+    # blocks are capped); 200 images take two launches whose sums are carried
+    # in FP64.  Per pixel the arithmetic is the same as for one image alone, so
+    # dL/dx must be bitwise equal; dL/dW_t is the same sum in another order.
+    ctx = spcn.Context(0)
+    rng = np.random.default_rng(B)
+    base, stats, tgt = _batch(spcn, B=4, H=H, W=W, seed=900)
+    x = torch.from_numpy(base[rng.integers(0, 4, size=B)]).cuda()
+    st = [stats[i % 4] for i in range(B)]
+    Wd = torch.tensor(np.array(tgt.basis, np.float32), device="cuda", requires_grad=True)
+    gy = torch.randn(x.shape, device="cuda", generator=torch.Generator("cuda").manual_seed(B))
+    xd = x.clone().requires_grad_(True)
+    spcn.normalize_f32(ctx, xd, Wd, st, tgt).backward(gy)
+    gx_all, gw_all = xd.grad.clone(), Wd.grad.double().clone()
+    gw_sum = torch.zeros_like(gw_all)
+    for b in range(B):
+        xb = x[b:b + 1].clone().requires_grad_(True)
+        Wd.grad = None
+        spcn.normalize_f32(ctx, xb, Wd, [st[b]], tgt).backward(gy[b:b + 1])
+        assert torch.equal(xb.grad[0], gx_all[b])
+        gw_sum += Wd.grad.double()
+    assert torch.max(torch.abs(gw_all - gw_sum)).item() <= 1e-5 * torch.max(torch.abs(gw_sum)).item()
     ctx.close()

@@ -63,6 +63,14 @@ st_out = spcn.Stats()
 out["noalloc_sample_beyond_scratch"] = lib.spcn_estimate_basis_noalloc(
     ctypes.byref(image(1024, 1024)), ctypes.byref(spcn.params(sample_mode="all")),
     ctypes.byref(st_out), None)
+# the rate is validated before the sample size is derived from it
+for key, rate in (("noalloc_nan_rate", float("nan")), ("noalloc_negative_rate", -0.5)):
+    p = spcn.params(sample_mode="hash")
+    p.sample_rate = rate
+    out[key] = lib.spcn_estimate_basis_noalloc(ctypes.byref(image(1024, 1024)), ctypes.byref(p),
+                                               ctypes.byref(st_out), None)
+out["noalloc_null_image"] = lib.spcn_estimate_basis_noalloc(
+    None, ctypes.byref(spcn.params()), ctypes.byref(st_out), None)
 print(json.dumps(out))
 """
 
@@ -81,6 +89,9 @@ EXPECTED = {
     "patch_median_too_many_patches": INVALID,
     "normalize_out_pitch": INVALID,
     "noalloc_sample_beyond_scratch": SCRATCH,   # 1 Mpx sample, above 524,288
+    "noalloc_nan_rate": INVALID,
+    "noalloc_negative_rate": INVALID,
+    "noalloc_null_image": INVALID,
 }
 
 

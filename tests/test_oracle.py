@@ -312,6 +312,25 @@ def test_identity_reconstruction_uint8_within_one():
     assert np.max(np.abs(out.astype(int) - img.astype(int))) <= 1
 
 
+def test_to_uint8_rounds_half_to_even_and_clamps():
+    rows = _rows("round_half_even.txt")
+    x = np.array([float(r[0]) for r in rows])
+    want = np.array([int(r[1]) for r in rows], dtype=np.uint8)
+    assert np.array_equal(O.to_uint8(x), want)
+
+
+def test_background_maps_to_target_white_with_ties_to_even():
+    # a pixel brighter than the source i0 has negative OD, so its lasso
+    # solution is h = 0 (lambda > 0) and Eq. 4 gives exactly the target's i0;
+    # a type-7 P80 can be a half-integer, so the output rounding decides it
+    W = synth.stain_basis(34)
+    img = np.full((2, 3, 3), 250, dtype=np.uint8)
+    src = O.Stats(W=W, i0=np.array([240.0, 240.0, 240.0]), p99=np.array([1.0, 1.0]))
+    tgt = O.Stats(W=W, i0=np.array([200.5, 201.5, 254.5]), p99=np.array([1.0, 1.0]))
+    out = O.normalize(img, src, tgt)
+    assert np.array_equal(out.reshape(-1, 3), np.tile([200, 202, 254], (6, 1)))
+
+
 def test_scale_is_ratio_of_percentiles_and_one_for_zero():
     assert np.allclose(O.stain_scale([2.0, 0.0], [1.0, 3.0]), [0.5, 1.0])
 
