@@ -90,6 +90,7 @@ struct SelectState {
   int all_resolved;
   unsigned done_ctas;         // last-block ticket of pass 1
   unsigned barrier;           // grid barrier counter
+  unsigned barrier2;          // grid barrier counter of the window-miss recovery
   int abort;                  // set when a grid-wide wait gave up (this launch only)
   double t;                   // interpolation weight of the type-7 percentile
   double p99[2];

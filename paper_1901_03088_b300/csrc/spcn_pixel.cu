@@ -437,7 +437,7 @@ struct SelectImageArgs {
   const Model* m;
   SelectState* sel;
   u64* ghist;
-  u64* fallbacks;   // counts the launches that had a rank to resolve
+  u64* fallbacks;   // counts the launches that had a rank to resolve (or null)
   int* err;
   long long timeout_ns;
   double tgt0, tgt1;
@@ -446,7 +446,7 @@ struct SelectImageArgs {
 template <bool PINV>
 __global__ void __launch_bounds__(kPassThreads, 1) k_select_image(SelectImageArgs a) {
   if (*(volatile int*)&a.sel->all_resolved) return;   // uniform: every block returns
-  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(a.fallbacks, 1ull);
+  if (a.fallbacks && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(a.fallbacks, 1ull);
   extern __shared__ __align__(16) char s_dyn[];
   unsigned* s_hist = reinterpret_cast<unsigned*>(s_dyn + kLutSmemBytes);
   load_lut(a.m, s_dyn);
@@ -459,6 +459,319 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_select_image(SelectImageArg
   }
   radix_select<PINV>(a.src, s_dyn, L, a.sel, rank, active, a.ghist, s_hist, &a.sel->barrier, a.err,
                a.timeout_ns, a.tgt0, a.tgt1);
+}
+
+// ------------------------------------------------------------ window-miss recovery
+// When a rank fell outside pass 1's window it is found by counting passes
+// instead of the radix select over every key.  A round counts, for each stain
+// with an unresolved rank, the non-white pixels in 32 consecutive key ranges
+// of 2^shift keys each (a ladder), with warp ballots into per-lane counters:
+// no atomics per pixel.  The ranges are walked with the exact count of pixels
+// below them to find the range that holds each unresolved rank; the union of
+// a stain's ranges is the next round's span.  Once a stain's span is at most
+// kWinBins keys, one more pass histograms the keys of that span exactly (as
+// pass 1 does its window) and the ranks are selected there.  The first round
+// starts next to the missed window: descending from its start, or ascending
+// from its end (with no window, descending from the key of 1.0, above every
+// scaled lasso density).  Every pixel's key is computed by pass 1's
+// arithmetic, so the keys are those of every other pass, bit for bit.  A rank
+// not found this way (ranks far apart, or a failed wait) is left to the radix
+// select that follows.  Not for the pseudo-inverse (signed keys).
+constexpr int kLadderBins = 32;
+constexpr int kLadderRounds = 6;
+constexpr unsigned kKeyInf = 0x7F800000u;    // +inf: above every density
+constexpr unsigned kKeyOne = 0x3F800000u;    // 1.0: above every scaled lasso density
+constexpr size_t kLadderSmem = kLutSmemBytes + sizeof(unsigned) * 2 * kWinGroups;
+// scratch of the recovery inside the context's radix histograms
+constexpr int kLadderCountOff = 0;                                  // [rounds][2][32] u64
+constexpr int kLadderCoarseOff = 2 * kLadderBins * kLadderRounds;   // [2][kWinGroups] u64
+constexpr int kLadderScratch = kLadderCoarseOff + 2 * kWinGroups;
+static_assert(kLadderScratch <= 3 * kTracks * kRadixBins, "recovery scratch fits");
+
+struct LadderArgs {
+  Geometry g;
+  unsigned wthr;        // (white threshold + 1) << 8, compared with table offsets
+  const Model* m;
+  SelectState* sel;
+  const u64* win_coarse;   // pass 1's window counts [2][kWinGroups] (read before any write)
+  u64* scratch;         // kLadderScratch u64 (counts, final coarse bins)
+  u64* fine;            // [2][kWinBins], the final span's exact bins
+  u64* misses;          // launches that had a rank to find
+  int* err;
+  long long timeout_ns;
+  double tgt0, tgt1;
+};
+
+// Per stain: the key span [lo, hi) that holds its unresolved ranks, the exact
+// count of non-white pixels below lo, and the ladder of the next round.
+struct LadderSpan {
+  unsigned lo, hi;
+  u64 below_lo;         // pixels with key < lo
+  u64 below_hi;         // pixels with key < hi (descending ladders)
+  int dir;              // -1: ranges [hi - (b+1) 2^shift, hi - b 2^shift); +1: [lo + b 2^shift, ...)
+  int shift;
+  int state;            // 0: nothing to find, 1: counting, 2: final (hi - lo <= kWinBins), 3: given up
+};
+
+__device__ __forceinline__ unsigned ladder_bin(unsigned k, const LadderSpan& s) {
+  if (s.state != 1) return 32u;
+  if (s.dir < 0) return k < s.hi ? (s.hi - 1u - k) >> s.shift : 32u;   // >= 32 beyond the ladder
+  return k >= s.lo ? (k - s.lo) >> s.shift : 32u;
+}
+
+// Ranges of ladder bin b (64-bit, clamped to [0, kKeyInf]).
+__device__ __forceinline__ void ladder_range(const LadderSpan& s, int b, long long* lo,
+                                             long long* hi) {
+  const long long w = 1ll << s.shift;
+  if (s.dir < 0) {
+    *hi = (long long)s.hi - (long long)b * w;
+    *lo = *hi - w;
+  } else {
+    *lo = (long long)s.lo + (long long)b * w;
+    *hi = *lo + w;
+  }
+  if (*lo < 0) *lo = 0;
+  if (*hi > (long long)kKeyInf) *hi = kKeyInf;
+}
+
+__device__ __forceinline__ int shift_for(u64 width) {
+  int s = 0;
+  while (((u64)kLadderBins << s) < width) ++s;
+  return s;
+}
+
+// Find the range of each unresolved track of stain j from a round's counts
+// and narrow the stain's span to their union.
+__device__ void ladder_update(LadderSpan& S, const u64* cnt, const SelectState* s, int j) {
+  long long nlo = -1, nhi = -1;
+  u64 nbelow = 0;
+  for (int t = 2 * j; t < 2 * j + 2; ++t) {
+    if (__ldcg(&s->resolved[t])) continue;
+    const u64 r = __ldcg(&s->rank[t]);
+    long long blo = -1, bhi = -1;
+    u64 bb = 0;
+    if (S.dir < 0) {
+      u64 c = S.below_hi;
+      for (int b = 0; b < kLadderBins; ++b) {
+        c -= __ldcg(cnt + b);
+        if (r >= c) { ladder_range(S, b, &blo, &bhi); bb = c; break; }
+      }
+      if (blo < 0) {   // below the ladder
+        long long l0, h0;
+        ladder_range(S, kLadderBins - 1, &l0, &h0);
+        blo = 0; bhi = l0; bb = 0;
+      }
+    } else {
+      u64 c = S.below_lo;
+      for (int b = 0; b < kLadderBins; ++b) {
+        const u64 x = __ldcg(cnt + b);
+        if (r < c + x) { ladder_range(S, b, &blo, &bhi); bb = c; break; }
+        c += x;
+      }
+      if (blo < 0) {   // above the ladder
+        long long l0, h0;
+        ladder_range(S, kLadderBins - 1, &l0, &h0);
+        blo = h0; bhi = kKeyInf; bb = c;
+      }
+    }
+    if (nlo < 0 || blo < nlo) { nlo = blo; nbelow = bb; }
+    if (bhi > nhi) nhi = bhi;
+  }
+  if (nlo < 0 || nhi <= nlo) { S.state = 3; return; }   // cannot happen for valid counts
+  S.lo = (unsigned)nlo;
+  S.hi = (unsigned)nhi;
+  S.below_lo = nbelow;
+  S.dir = 1;
+  const u64 width = (u64)(nhi - nlo);
+  if (width <= (u64)kWinBins) { S.state = 2; return; }
+  S.shift = shift_for(width);
+}
+
+// Warp-uniform traversal of every pixel (all lanes call body for each of the
+// 16 pixel slots of their chunk; nw is false for slots without a pixel).
+template <class Body>
+__device__ __forceinline__ void ladder_pixels(const LadderArgs& a, const char* lut, const Lasso& L,
+                                              Body&& body) {
+  const Geometry& g = a.g;
+  const unsigned lr = lane_reg();
+  const unsigned lane = threadIdx.x & 31u;
+  const u64 stride = (u64)gridDim.x * blockDim.x;
+  for (u64 base = (u64)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < g.nchunks;
+       base += stride) {
+    const u64 q = base + lane;
+    unsigned w[12];
+    int n = 0;
+    if (q < g.nchunks) {
+      const ChunkPos p = chunk_pos(g, q);
+      load_chunk<false>(g, p, w);
+      n = p.n;
+    } else {
+#pragma unroll
+      for (int i = 0; i < 12; ++i) w[i] = 0xFFFFFFFFu;
+    }
+#pragma unroll
+    for (int k = 0; k < kChunk; ++k) {
+      unsigned aR, aG, aB;
+      pixel_addr(w, k, lr, aR, aG, aB);
+      const bool nw = k < n && min(min(aR, aG), aB) < a.wthr;
+      float h1, h2;
+      solve_one<false>(lut, aR, aG, aB, L, h1, h2);
+      body(nw, __float_as_uint(h1), __float_as_uint(h2));
+    }
+  }
+}
+
+// Lane b of the warp adds the number of lanes whose bin is b.
+__device__ __forceinline__ void ballot_count(unsigned bin, unsigned lane, unsigned& cnt) {
+#pragma unroll
+  for (int b = 0; b < kLadderBins; ++b) {
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, bin == (unsigned)b);
+    if (lane == (unsigned)b) cnt += (unsigned)__popc(m);
+  }
+}
+
+__global__ void __launch_bounds__(kPassThreads, 1) k_select_ladder(LadderArgs a) {
+  SelectState* s = a.sel;
+  if (*(volatile int*)&s->all_resolved) return;   // uniform: every block returns
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(a.misses, 1ull);
+  extern __shared__ __align__(16) char s_dyn[];
+  unsigned* s_coarse = reinterpret_cast<unsigned*>(s_dyn + kLutSmemBytes);   // [2][kWinGroups]
+  __shared__ unsigned s_cnt[2][kLadderBins];
+  __shared__ u64 s_tmp[33];
+  __shared__ int s_idx, s_idx2;
+  __shared__ u64 s_before, s_before2;
+  const u64 n = __ldcg(&s->n_nw);
+  // pass 1's in-window counts (its coarse groups), one block sum per stain
+  u64 inwin[2];
+  for (int j = 0; j < 2; ++j) {
+    u64 part = 0;
+    for (int i = threadIdx.x; i < kWinGroups; i += blockDim.x)
+      part += __ldcg(a.win_coarse + j * kWinGroups + i);
+    inwin[j] = block_sum(part, s_tmp);
+  }
+  // first spans, from pass 1's outcome (the same in every block)
+  LadderSpan S[2];
+  for (int j = 0; j < 2; ++j) {
+    LadderSpan& X = S[j];
+    X.state = 0;
+    const int u0 = !__ldcg(&s->resolved[2 * j]), u1 = !__ldcg(&s->resolved[2 * j + 1]);
+    if (!u0 && !u1) continue;
+    const unsigned lo = __ldcg(&s->lo[j]), nb = __ldcg(&s->nb[j]);
+    const u64 below = __ldcg(&s->below[j]);
+    bool under = true, over = true;
+    for (int t = 2 * j; t < 2 * j + 2; ++t) {
+      if (__ldcg(&s->resolved[t])) continue;
+      const u64 r = __ldcg(&s->rank[t]);
+      under = under && r < below;
+      over = over && r >= below + inwin[j];
+    }
+    X.state = 1;
+    if (nb == 0) {                     // no window: below the key of 1.0, 8 binades
+      X.lo = 0; X.hi = kKeyOne; X.below_lo = 0; X.below_hi = n; X.dir = -1; X.shift = 21;
+    } else if (under) {                // below the window: two binades under its start
+      X.lo = 0; X.hi = lo; X.below_lo = 0; X.below_hi = below; X.dir = -1; X.shift = 19;
+    } else if (over) {                 // above the window: two binades over its end
+      X.lo = lo + nb; X.hi = kKeyInf; X.below_lo = below + inwin[j]; X.below_hi = n;
+      X.dir = 1; X.shift = 19;
+    } else {                           // cannot happen (adjacent ranks); search everything
+      X.lo = 0; X.hi = kKeyInf; X.below_lo = 0; X.below_hi = n; X.dir = 1;
+      X.shift = shift_for(kKeyInf);
+    }
+  }
+  // zero the counts and the final bins (pass 1's are no longer needed)
+  const u64 gtid = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+  const u64 gstride = (u64)gridDim.x * blockDim.x;
+  for (u64 i = gtid; i < (u64)kLadderScratch; i += gstride) a.scratch[i] = 0ull;
+  for (u64 i = gtid; i < 2ull * kWinBins; i += gstride) a.fine[i] = 0ull;
+  unsigned target = gridDim.x;
+  if (!grid_barrier(&s->barrier2, target, &s->abort, a.err, a.timeout_ns)) return;
+  load_lut(a.m, s_dyn);
+  const char* lut = s_dyn;
+  const Lasso L = a.m->lasso;
+  const unsigned lane = threadIdx.x & 31u;
+  for (int round = 0; round < kLadderRounds; ++round) {
+    if (S[0].state != 1 && S[1].state != 1) break;   // uniform
+    for (int i = threadIdx.x; i < 2 * kLadderBins; i += blockDim.x) (&s_cnt[0][0])[i] = 0u;
+    __syncthreads();
+    unsigned c0 = 0u, c1 = 0u;
+    const LadderSpan S0 = S[0], S1 = S[1];
+    ladder_pixels(a, lut, L, [&](bool nw, unsigned k1, unsigned k2) {
+      const unsigned b1 = nw ? ladder_bin(k1, S0) : 32u;
+      const unsigned b2 = nw ? ladder_bin(k2, S1) : 32u;
+      if (__any_sync(0xFFFFFFFFu, b1 < 32u)) ballot_count(b1, lane, c0);
+      if (__any_sync(0xFFFFFFFFu, b2 < 32u)) ballot_count(b2, lane, c1);
+    });
+    if (c0) atomicAdd(&s_cnt[0][lane], c0);
+    if (c1) atomicAdd(&s_cnt[1][lane], c1);
+    __syncthreads();
+    u64* cnt = a.scratch + kLadderCountOff + (size_t)round * 2 * kLadderBins;
+    if (threadIdx.x < 2 * kLadderBins) {
+      const unsigned v = (&s_cnt[0][0])[threadIdx.x];
+      if (v) atomicAdd(cnt + threadIdx.x, (u64)v);
+    }
+    target += gridDim.x;
+    if (!grid_barrier(&s->barrier2, target, &s->abort, a.err, a.timeout_ns)) return;
+    for (int j = 0; j < 2; ++j)
+      if (S[j].state == 1) ladder_update(S[j], cnt + j * kLadderBins, s, j);
+  }
+  // the final spans: exact bins of every key, coarse groups per block
+  if (S[0].state != 2 && S[1].state != 2) return;   // uniform: left to the radix select
+  for (int i = threadIdx.x; i < 2 * kWinGroups; i += blockDim.x) s_coarse[i] = 0u;
+  __syncthreads();
+  {
+    const unsigned lo0 = S[0].state == 2 ? S[0].lo : 0u, lo1 = S[1].state == 2 ? S[1].lo : 0u;
+    const unsigned w0 = S[0].state == 2 ? S[0].hi - S[0].lo : 0u;
+    const unsigned w1 = S[1].state == 2 ? S[1].hi - S[1].lo : 0u;
+    u64* fine = a.fine;
+    ladder_pixels(a, lut, L, [&](bool nw, unsigned k1, unsigned k2) {
+      if (!nw) return;
+      const unsigned r1 = k1 - lo0, r2 = k2 - lo1;
+      if (r1 < w0) {
+        red_add_global(fine + r1, 1ull);
+        red_add_shared(s_coarse + (r1 >> kWinGroupBits), 1u);
+      }
+      if (r2 < w1) {
+        red_add_global(fine + kWinBins + r2, 1ull);
+        red_add_shared(s_coarse + kWinGroups + (r2 >> kWinGroupBits), 1u);
+      }
+    });
+  }
+  __syncthreads();
+  u64* coarse = a.scratch + kLadderCoarseOff;
+  for (int i = threadIdx.x; i < 2 * kWinGroups; i += blockDim.x)
+    if (s_coarse[i]) atomicAdd(coarse + i, (u64)s_coarse[i]);
+  target += gridDim.x;
+  if (!grid_barrier(&s->barrier2, target, &s->abort, a.err, a.timeout_ns)) return;
+  if (blockIdx.x != 0) return;
+  for (int t = 0; t < kTracks; ++t) {
+    const int j = t >> 1;
+    if (S[j].state != 2 || __ldcg(&s->resolved[t])) continue;   // uniform within the block
+    const u64 r = __ldcg(&s->rank[t]) - S[j].below_lo;
+    const unsigned width = S[j].hi - S[j].lo;
+    const int ngroups = (int)((width + kWinGroup - 1) >> kWinGroupBits);
+    block_find_rank(coarse + j * kWinGroups, ngroups, r, &s_idx, &s_before, s_tmp);
+    if (s_idx < 0) continue;
+    const unsigned gbeg = (unsigned)s_idx << kWinGroupBits;
+    const int nbins = (int)min((unsigned)kWinGroup, width - gbeg);
+    block_find_rank(a.fine + (size_t)j * kWinBins + gbeg, nbins, r - s_before, &s_idx2,
+                    &s_before2, s_tmp);
+    if (s_idx2 < 0) continue;
+    if (threadIdx.x == 0) {
+      s->key[t] = S[j].lo + gbeg + (unsigned)s_idx2;
+      s->resolved[t] = 1;
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int all = 1;
+    for (int t = 0; t < kTracks; ++t) all &= s->resolved[t];
+    if (all) {
+      finish_percentiles(s, a.tgt0, a.tgt1, L.hscale);
+      __threadfence();
+      s->all_resolved = 1;
+    }
+  }
 }
 
 struct SelectListArgs {
@@ -683,6 +996,7 @@ int configure_pixel_kernels(Context* c) {
   rc |= smem_attr(k_select_image<true>, kRadixSmem);
   rc |= smem_attr(k_select_list<false>, kRadixSmem);
   rc |= smem_attr(k_select_list<true>, kRadixSmem);
+  rc |= smem_attr(k_select_ladder, kLadderSmem);
   if (rc) return SPCN_ERR_CUDA;
   c->occ_window = c->occ_recon = c->occ_density = c->occ_select = c->occ_radix_list = 0;
   c->occ_debug = 0;
@@ -696,6 +1010,7 @@ int configure_pixel_kernels(Context* c) {
   rc |= occ_min(&c->occ_density, k_pass_density<true>, kPassThreads, kDensitySmem);
   rc |= occ_min(&c->occ_select, k_select_image<false>, kPassThreads, kRadixSmem);
   rc |= occ_min(&c->occ_select, k_select_image<true>, kPassThreads, kRadixSmem);
+  rc |= occ_min(&c->occ_select, k_select_ladder, kPassThreads, kLadderSmem);
   rc |= occ_min(&c->occ_radix_list, k_select_list<false>, kPassThreads, kRadixSmem);
   rc |= occ_min(&c->occ_radix_list, k_select_list<true>, kPassThreads, kRadixSmem);
   rc |= occ_min(&c->occ_debug, k_debug_barrier, 128, 0);
@@ -844,13 +1159,33 @@ static int percentile_passes(Context* c, const Geometry& g, const Model* m, int 
   }
   SPCN_LAUNCH_CHECK(c);
 
+  if (!pinv) {   // a rank outside the window: counting passes first
+    LadderArgs l;
+    l.g = g;
+    l.wthr = a.wthr;
+    l.m = m;
+    l.sel = c->sel;
+    l.win_coarse = c->coarse;
+    l.scratch = c->rhist;
+    l.fine = c->fine;
+    l.misses = c->fallbacks;
+    l.err = c->err;
+    l.timeout_ns = c->timeout_ns;
+    l.tgt0 = a.tgt0;
+    l.tgt1 = a.tgt1;
+    void* largs[] = {&l};
+    TimedLaunch tl(c, SPCN_KERNEL_SELECT, st);
+    SPCN_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_select_ladder, grid_of(c, c->occ_select),
+                                              kPassThreads, largs, kLadderSmem, st));
+    c->launches++;
+  }
   SelectImageArgs s;
   s.src.g = g;
   s.src.thr = (unsigned)white_thresh;
   s.m = m;
   s.sel = c->sel;
   s.ghist = c->rhist;
-  s.fallbacks = c->fallbacks;
+  s.fallbacks = pinv ? c->fallbacks : nullptr;   // the lasso's misses are counted by the recovery
   s.err = c->err;
   s.timeout_ns = c->timeout_ns;
   s.tgt0 = a.tgt0;
