@@ -802,7 +802,7 @@ def run_ours(args, world, rank, local):
     ms_local = evs[0].elapsed_time(evs[-1]) / args.steps
     per_step = sorted(evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps))
     ms = max_over_ranks(ms_local, world, dev)
-    ktimes = {k: ctx.kernel_times(k) for k in ("pass1", "select", "pass2")}
+    ktimes = {k: ctx.kernel_times(k) for k in ("pass1", "ladder", "select", "pass2")}
     ctx.kernel_timing(False)
     clocks = clk.summary()
 
@@ -853,8 +853,9 @@ def run_ours(args, world, rank, local):
             "ms_per_step_median": round(per_step[len(per_step) // 2], 4),
             "kernel_ms_per_step": {k: round(v[0] / max(1, v[1]), 4) for k, v in ktimes.items()},
             "select_kernel_launches": ktimes["select"][1],
+            "ladder_kernel_launches": ktimes["ladder"][1],
             "exact_fallback_steps": fallbacks,
-            "p99_window": ("none: sampled percentile dropped, exact radix select every step"
+            "p99_window": ("none: sampled percentile dropped, every step takes the window-miss recovery"
                            if args.hint == "none" else "from the basis sample's percentile"),
             "src_p99": [round(p99[0], 6), round(p99[1], 6)], "snmf_iters": s_st.iters,
             "variant": args.flags or "improved method (no flags)",

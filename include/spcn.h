@@ -389,7 +389,8 @@ typedef enum {
   SPCN_KERNEL_F32_FWD = 4,  /* differentiable forward (float images) */
   SPCN_KERNEL_F32_BWD = 5,  /* differentiable backward (float images) */
   SPCN_KERNEL_BATCH = 6,    /* batched persistent launch (spcn_batch_run) */
-  SPCN_KERNEL_COUNT = 7
+  SPCN_KERNEL_LADDER = 7,   /* window-miss recovery: counting passes over key ladders */
+  SPCN_KERNEL_COUNT = 8
 } spcn_kernel;
 
 /* Enable (1) or disable (0) CUDA-event timing of the kernels above on the

@@ -513,12 +513,6 @@ struct LadderSpan {
   int state;            // 0: nothing to find, 1: counting, 2: final (hi - lo <= kWinBins), 3: given up
 };
 
-__device__ __forceinline__ unsigned ladder_bin(unsigned k, const LadderSpan& s) {
-  if (s.state != 1) return 32u;
-  if (s.dir < 0) return k < s.hi ? (s.hi - 1u - k) >> s.shift : 32u;   // >= 32 beyond the ladder
-  return k >= s.lo ? (k - s.lo) >> s.shift : 32u;
-}
-
 // Ranges of ladder bin b (64-bit, clamped to [0, kKeyInf]).
 __device__ __forceinline__ void ladder_range(const LadderSpan& s, int b, long long* lo,
                                              long long* hi) {
@@ -621,13 +615,16 @@ __device__ __forceinline__ void ladder_pixels(const LadderArgs& a, const char* l
   }
 }
 
-// Lane b of the warp adds the number of lanes whose bin is b.
-__device__ __forceinline__ void ballot_count(unsigned bin, unsigned lane, unsigned& cnt) {
+// Lane b of the warp adds the number of lanes whose bin is b (bins >= 32 are
+// not counted): the lanes with a bin, then one ballot per bit of the bin,
+// each kept or inverted by the matching bit of the lane's own index (flip[i]
+// is all ones where bit i of the lane index is 0).
+__device__ __forceinline__ void ballot_count(unsigned bin, const unsigned (&flip)[5],
+                                             unsigned& cnt) {
+  unsigned m = __ballot_sync(0xFFFFFFFFu, bin < (unsigned)kLadderBins);
 #pragma unroll
-  for (int b = 0; b < kLadderBins; ++b) {
-    const unsigned m = __ballot_sync(0xFFFFFFFFu, bin == (unsigned)b);
-    if (lane == (unsigned)b) cnt += (unsigned)__popc(m);
-  }
+  for (int i = 0; i < 5; ++i) m &= __ballot_sync(0xFFFFFFFFu, (bin >> i) & 1u) ^ flip[i];
+  cnt += (unsigned)__popc(m);
 }
 
 __global__ void __launch_bounds__(kPassThreads, 1) k_select_ladder(LadderArgs a) {
@@ -689,17 +686,29 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_select_ladder(LadderArgs a)
   const char* lut = s_dyn;
   const Lasso L = a.m->lasso;
   const unsigned lane = threadIdx.x & 31u;
+  unsigned flip[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) flip[i] = ((lane >> i) & 1u) ? 0u : 0xFFFFFFFFu;
   for (int round = 0; round < kLadderRounds; ++round) {
     if (S[0].state != 1 && S[1].state != 1) break;   // uniform
     for (int i = threadIdx.x; i < 2 * kLadderBins; i += blockDim.x) (&s_cnt[0][0])[i] = 0u;
     __syncthreads();
     unsigned c0 = 0u, c1 = 0u;
-    const LadderSpan S0 = S[0], S1 = S[1];
+    // each stain's ladder as bin = (key - base) >> shift (ascending) or
+    // (base - key) >> shift (descending, base = hi - 1), in plain registers
+    const unsigned base0 = S[0].dir < 0 ? S[0].hi - 1u : S[0].lo;
+    const unsigned base1 = S[1].dir < 0 ? S[1].hi - 1u : S[1].lo;
+    const unsigned sh0 = (unsigned)S[0].shift, sh1 = (unsigned)S[1].shift;
+    const bool desc0 = S[0].dir < 0, desc1 = S[1].dir < 0;
+    const bool on0 = S[0].state == 1, on1 = S[1].state == 1;
     ladder_pixels(a, lut, L, [&](bool nw, unsigned k1, unsigned k2) {
-      const unsigned b1 = nw ? ladder_bin(k1, S0) : 32u;
-      const unsigned b2 = nw ? ladder_bin(k2, S1) : 32u;
-      if (__any_sync(0xFFFFFFFFu, b1 < 32u)) ballot_count(b1, lane, c0);
-      if (__any_sync(0xFFFFFFFFu, b2 < 32u)) ballot_count(b2, lane, c1);
+      unsigned b1 = 32u, b2 = 32u;
+      if (nw && on0 && (desc0 ? k1 <= base0 : k1 >= base0))
+        b1 = min((desc0 ? base0 - k1 : k1 - base0) >> sh0, 32u);
+      if (nw && on1 && (desc1 ? k2 <= base1 : k2 >= base1))
+        b2 = min((desc1 ? base1 - k2 : k2 - base1) >> sh1, 32u);
+      if (on0) ballot_count(b1, flip, c0);
+      if (on1) ballot_count(b2, flip, c1);
     });
     if (c0) atomicAdd(&s_cnt[0][lane], c0);
     if (c1) atomicAdd(&s_cnt[1][lane], c1);
@@ -1174,7 +1183,7 @@ static int percentile_passes(Context* c, const Geometry& g, const Model* m, int 
     l.tgt0 = a.tgt0;
     l.tgt1 = a.tgt1;
     void* largs[] = {&l};
-    TimedLaunch tl(c, SPCN_KERNEL_SELECT, st);
+    TimedLaunch tl(c, SPCN_KERNEL_LADDER, st);
     SPCN_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_select_ladder, grid_of(c, c->occ_select),
                                               kPassThreads, largs, kLadderSmem, st));
     c->launches++;

@@ -161,7 +161,7 @@ EXPORTED = ("spcn_params_default", "spcn_context_create", "spcn_context_destroy"
             "spcn_batch_set_config", "spcn_batch_tune", "spcn_batch_destroy",
             "spcn_normalize_batched", "spcn_stain_densities_estimated")
 KERNELS = {"pass1": 0, "select": 1, "pass2": 2, "density": 3, "f32_fwd": 4, "f32_bwd": 5,
-           "batch": 6}
+           "batch": 6, "ladder": 7}
 
 
 def params(**kw) -> Params:

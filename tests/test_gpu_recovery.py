@@ -54,8 +54,9 @@ def check(spcn, ctx, img, st, p=None, pct=99.0):
     H = ctx.stain_densities(dev, st).cpu().numpy()
     thr = p.white_thresh if p is not None else 220
     nw = O.nonwhite_mask(img.reshape(-1, 3), thr)
+    level = float(np.float32(pct))   # spcn_params.stain_pct is an FP32 level
     for j in range(2):
-        assert got[j] == type7_of_f32(H[j][nw], pct), (j, got[j])
+        assert got[j] == type7_of_f32(H[j][nw], level), (j, got[j])
     return misses
 
 
