@@ -766,13 +766,17 @@ def run_ours(args, world, rank, local):
         t_st.p99[0], t_st.p99[1] = ctx.stain_percentile(tgt, t_st, pt)
     tgt_ms = 1e3 * (time.perf_counter() - t1)
 
-    if args.hint == "none":
+    if args.hint != "sample":
+        # the window-miss recovery on record: the sampled percentile is dropped
+        # ("none": pass 1 has no window) or scaled by a factor (a window that
+        # misses the percentile), so every step takes the recovery; a host
+        # round trip separates the two calls
+        factor = 0.0 if args.hint == "none" else float(args.hint)
+
         def step():
-            # the exact fallback on record: the source's sampled percentile is
-            # dropped, so pass 1 runs without a window and the radix select over
-            # the image resolves both ranks (a host round trip separates the calls)
             s_st = ctx.estimate_basis(src, p)
-            s_st.p99[0] = s_st.p99[1] = 0.0
+            s_st.p99[0] *= factor
+            s_st.p99[1] *= factor
             ctx.normalize(src, s_st, t_st, p, out=out)
     else:
         def step():
@@ -809,7 +813,7 @@ def run_ours(args, world, rank, local):
     # the statistics of one step (bench output is not a parity test)
     _, s_st = ctx.normalize_estimated(src, t_st, p, out=out, return_stats=True)
     p99 = (s_st.p99[0], s_st.p99[1])
-    if args.hint == "none":
+    if args.hint != "sample":
         sampled_st = ctx.estimate_basis(src, p)
         s_st.iters = sampled_st.iters
 
@@ -855,8 +859,9 @@ def run_ours(args, world, rank, local):
             "select_kernel_launches": ktimes["select"][1],
             "ladder_kernel_launches": ktimes["ladder"][1],
             "exact_fallback_steps": fallbacks,
-            "p99_window": ("none: sampled percentile dropped, every step takes the window-miss recovery"
-                           if args.hint == "none" else "from the basis sample's percentile"),
+            "p99_window": ("from the basis sample's percentile" if args.hint == "sample" else
+                           "none: the sampled percentile dropped" if args.hint == "none" else
+                           f"the sampled percentile x {args.hint} (a window that misses)"),
             "src_p99": [round(p99[0], 6), round(p99[1], 6)], "snmf_iters": s_st.iters,
             "variant": args.flags or "improved method (no flags)",
         },
@@ -1083,10 +1088,16 @@ def main():
                     help="batch workload: keep the default schedule (no autotuner runs)")
     ap.add_argument("--no-legs", action="store_true",
                     help="wsi workload: skip the batched and forward+backward legs")
-    ap.add_argument("--hint", choices=["sample", "none"], default="sample",
-                    help="wsi/tile workloads: 'none' drops the sampled percentile, so every "
-                         "step takes the exact radix-select fallback (its cost on record)")
+    ap.add_argument("--hint", default="sample",
+                    help="wsi/tile workloads: 'sample' (the method), 'none' (no window) or a "
+                         "factor applied to the sampled percentile (a window that misses): "
+                         "every step then takes the window-miss recovery (its cost on record)")
     args = ap.parse_args()
+    if args.hint not in ("sample", "none"):
+        try:
+            float(args.hint)
+        except ValueError:
+            ap.error("--hint: 'sample', 'none' or a factor")
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")
     if args.impl == "reference":

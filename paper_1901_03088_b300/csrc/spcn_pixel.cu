@@ -491,6 +491,7 @@ static_assert(kLadderScratch <= 3 * kTracks * kRadixBins, "recovery scratch fits
 struct LadderArgs {
   Geometry g;
   unsigned wthr;        // (white threshold + 1) << 8, compared with table offsets
+  unsigned wm, we;      // all-white test of a full chunk, as in pass 1
   const Model* m;
   SelectState* sel;
   const u64* win_coarse;   // pass 1's window counts [2][kWinGroups] (read before any write)
@@ -581,11 +582,16 @@ __device__ void ladder_update(LadderSpan& S, const u64* cnt, const SelectState* 
   S.shift = shift_for(width);
 }
 
-// Warp-uniform traversal of every pixel (all lanes call body for each of the
-// 16 pixel slots of their chunk; nw is false for slots without a pixel).
+// Warp-uniform traversal of the pixels that may matter: a chunk is skipped
+// when it is all white or when its density bound (every pixel's key is at
+// most the bound's, see below_bound) lies below low0 and low1, the lowest
+// keys the caller counts for each stain; a warp skips its 32 chunks when none
+// is kept.  Otherwise every lane calls body for each of the 16 pixel slots of
+// its chunk (nw is false for slots without a counted pixel), so body may use
+// warp-wide operations.
 template <class Body>
 __device__ __forceinline__ void ladder_pixels(const LadderArgs& a, const char* lut, const Lasso& L,
-                                              Body&& body) {
+                                              unsigned low0, unsigned low1, Body&& body) {
   const Geometry& g = a.g;
   const unsigned lr = lane_reg();
   const unsigned lane = threadIdx.x & 31u;
@@ -598,11 +604,13 @@ __device__ __forceinline__ void ladder_pixels(const LadderArgs& a, const char* l
     if (q < g.nchunks) {
       const ChunkPos p = chunk_pos(g, q);
       load_chunk<false>(g, p, w);
-      n = p.n;
-    } else {
-#pragma unroll
-      for (int i = 0; i < 12; ++i) w[i] = 0xFFFFFFFFu;
+      if (!chunk_white(w, a.wm, a.we)) {   // padding bytes read white and lower no minimum
+        unsigned b1, b2;
+        chunk_bound_keys(w, lut, lr, &b1, &b2);
+        if (b1 >= low0 || b2 >= low1) n = p.n;
+      }
     }
+    if (!__any_sync(0xFFFFFFFFu, n > 0)) continue;
 #pragma unroll
     for (int k = 0; k < kChunk; ++k) {
       unsigned aR, aG, aB;
@@ -701,14 +709,19 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_select_ladder(LadderArgs a)
     const unsigned sh0 = (unsigned)S[0].shift, sh1 = (unsigned)S[1].shift;
     const bool desc0 = S[0].dir < 0, desc1 = S[1].dir < 0;
     const bool on0 = S[0].state == 1, on1 = S[1].state == 1;
-    ladder_pixels(a, lut, L, [&](bool nw, unsigned k1, unsigned k2) {
+    // lowest key each stain's ladder counts (none: above every key)
+    const unsigned low0 = !on0 ? 0xFFFFFFFFu : (desc0 ? (unsigned)max(0ll, (long long)base0 + 1ll -
+                                                                       (32ll << sh0)) : base0);
+    const unsigned low1 = !on1 ? 0xFFFFFFFFu : (desc1 ? (unsigned)max(0ll, (long long)base1 + 1ll -
+                                                                       (32ll << sh1)) : base1);
+    ladder_pixels(a, lut, L, low0, low1, [&](bool nw, unsigned k1, unsigned k2) {
       unsigned b1 = 32u, b2 = 32u;
       if (nw && on0 && (desc0 ? k1 <= base0 : k1 >= base0))
         b1 = min((desc0 ? base0 - k1 : k1 - base0) >> sh0, 32u);
       if (nw && on1 && (desc1 ? k2 <= base1 : k2 >= base1))
         b2 = min((desc1 ? base1 - k2 : k2 - base1) >> sh1, 32u);
-      if (on0) ballot_count(b1, flip, c0);
-      if (on1) ballot_count(b2, flip, c1);
+      if (on0 && __any_sync(0xFFFFFFFFu, b1 < 32u)) ballot_count(b1, flip, c0);
+      if (on1 && __any_sync(0xFFFFFFFFu, b2 < 32u)) ballot_count(b2, flip, c1);
     });
     if (c0) atomicAdd(&s_cnt[0][lane], c0);
     if (c1) atomicAdd(&s_cnt[1][lane], c1);
@@ -732,7 +745,8 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_select_ladder(LadderArgs a)
     const unsigned w0 = S[0].state == 2 ? S[0].hi - S[0].lo : 0u;
     const unsigned w1 = S[1].state == 2 ? S[1].hi - S[1].lo : 0u;
     u64* fine = a.fine;
-    ladder_pixels(a, lut, L, [&](bool nw, unsigned k1, unsigned k2) {
+    ladder_pixels(a, lut, L, w0 ? lo0 : 0xFFFFFFFFu, w1 ? lo1 : 0xFFFFFFFFu,
+                  [&](bool nw, unsigned k1, unsigned k2) {
       if (!nw) return;
       const unsigned r1 = k1 - lo0, r2 = k2 - lo1;
       if (r1 < w0) {
@@ -1172,6 +1186,8 @@ static int percentile_passes(Context* c, const Geometry& g, const Model* m, int 
     LadderArgs l;
     l.g = g;
     l.wthr = a.wthr;
+    l.wm = a.wm;
+    l.we = a.we;
     l.m = m;
     l.sel = c->sel;
     l.win_coarse = c->coarse;

@@ -327,6 +327,19 @@ __device__ __forceinline__ bool chunk_below_window(const unsigned (&w)[12], cons
   return below_bound(rg, bb, lut, lr, C);
 }
 
+// The bound itself: D~ of both stains at the chunk's per-channel minima, as
+// FP32 bit patterns (keys), at or above the key of every pixel's density.
+__device__ __forceinline__ void chunk_bound_keys(const unsigned (&w)[12], const char* lut,
+                                                 unsigned lr, unsigned* k1, unsigned* k2) {
+  unsigned rg, bb;
+  chunk_channel_min(w, &rg, &bb);
+  const float2 eR = lut_ld(lut, __byte_perm(rg, lr, 0x5514u));
+  const float2 eG = lut_ld(lut, __byte_perm(rg, lr, 0x5534u) + kLutOffG);
+  const float2 eB = lut_ld(lut, __byte_perm(bb, lr, 0x5514u) + kLutOffB);
+  *k1 = __float_as_uint(add_sat(eR.x + eG.x, eB.x));
+  *k2 = __float_as_uint(add_sat(eR.y + eG.y, eB.y));
+}
+
 // True when every white pixel (all channels above the threshold T) lies
 // below both window starts: the same bound at the intensities (T+1, T+1,
 // T+1), which every white pixel's channels reach or exceed.  At T = 255 no
