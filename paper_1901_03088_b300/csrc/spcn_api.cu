@@ -96,7 +96,7 @@ static void free_all(Context* c) {
   c->pool.clear();
   void* ptrs[] = {c->err, c->model, c->model_b, c->sel, c->coarse, c->fine, c->rhist,
                   c->rhist_b, c->partials, c->bs, c->wdev, c->sample, c->nw, c->br, c->blk,
-                  c->blk_off, c->cand, c->fallbacks};
+                  c->blk_off, c->cand, c->fallbacks, c->f32_ticket};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -274,12 +274,16 @@ int spcn_context_create(void** out, int device) {
     ALLOC(c->bs, sizeof(BasisState));
     ALLOC(c->wdev, sizeof(Window));
     ALLOC(c->fallbacks, sizeof(u64));
+    ALLOC(c->f32_ticket, sizeof(unsigned));
 #undef ALLOC
     if (cudaMemset(c->err, 0, sizeof(int)) != cudaSuccess) { rc = SPCN_ERR_CUDA; break; }
     if (cudaMemset(c->fallbacks, 0, sizeof(u64)) != cudaSuccess) { rc = SPCN_ERR_CUDA; break; }
+    if (cudaMemset(c->f32_ticket, 0, sizeof(unsigned)) != cudaSuccess) { rc = SPCN_ERR_CUDA; break; }
     rc = configure_pixel_kernels(c);
     if (rc) break;
     rc = configure_basis_kernels(c);
+    if (rc) break;
+    rc = configure_grad_kernels(c);
     if (rc) break;
     if (cudaDeviceSynchronize() != cudaSuccess) { rc = SPCN_ERR_CUDA; break; }
   } while (0);

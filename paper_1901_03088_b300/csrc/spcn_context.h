@@ -40,7 +40,8 @@ struct Context {
   double* partials = nullptr;      // [2][max grid][kAcc]
   BasisState* bs = nullptr;
   void* wdev = nullptr;            // P99 window computed on the device (struct Window)
-  u64* fallbacks = nullptr;        // whole-image percentiles resolved by the exact radix select
+  u64* fallbacks = nullptr;        // whole-image percentile launches that missed pass 1's window
+  unsigned* f32_ticket = nullptr;  // last-block ticket of the float backward (0 between launches)
   // grown on demand
   uint32_t* sample = nullptr;      // packed RGB of the sample
   uint32_t* nw = nullptr;          // non-white sample pixels (stable order)
@@ -58,6 +59,7 @@ struct Context {
   // blocks per SM at the launch configuration of each kernel
   int occ_window = 0, occ_recon = 0, occ_density = 0, occ_select = 0;
   int occ_snmf = 0, occ_radix_list = 0, occ_debug = 0;
+  int occ_f32_fwd = 0, occ_f32_bwd = 0;
   long long timeout_ns = 2000000000LL;   // grid-barrier give-up time
   // optional CUDA-event timing of the pixel kernels
   struct Timed { int kernel; cudaEvent_t a, b; };
@@ -132,5 +134,6 @@ constexpr size_t kDensitySmem = kLutSmemBytes + 2048 * (kPassThreads / 32);
 
 int configure_pixel_kernels(Context* c);
 int configure_basis_kernels(Context* c);
+int configure_grad_kernels(Context* c);
 
 }  // namespace spcn

@@ -36,6 +36,10 @@ struct F32Args {
   float* gx;
   const float* wt;        // target basis, device, column-major (6)
   double* partials;       // [grid][6] dL/dW_t block sums (backward)
+  double* acc;            // FP64 running sum of a batch that takes several launches
+  float* gwt;             // dL/dW_t (written by the last launch)
+  unsigned* ticket;       // last-block ticket (returns to 0 after every launch)
+  int first, last;        // this launch is the first / last of its batch
   int64_t hw;             // pixels per image
   int batch;              // images in this launch
   float l2i0t[3];         // log2 i0_t
@@ -166,8 +170,19 @@ __device__ __forceinline__ void f32_back_px(const F32Reg& R, const F32Back& B, c
   gx2 = x2 > 1.f ? __fdividef(-fmaf(B.ws2, gc1, B.ws5 * gc2), x2) : 0.f;
 }
 
-__global__ void __launch_bounds__(kF32Threads, 4) k_f32_backward(F32Args a) {
+__device__ __forceinline__ float2 ld2(const float* p) { return __ldcs(reinterpret_cast<const float2*>(p)); }
+__device__ __forceinline__ void st2(float* p, float2 v) { __stcs(reinterpret_cast<float2*>(p), v); }
+
+// One wave of blocks (blockIdx.y = image, so the image's constants are
+// uniform), each looping over its image two pixels at a time (8-byte accesses
+// per plane) when the size and pointers allow it, one pixel otherwise.  The
+// dL/dW_t block sums go to `partials`; the block that finishes last (a
+// ticket that returns to zero) adds them in block order with a fixed tree,
+// so reruns are bit-identical, and writes gwt or the running sum.
+constexpr int kF32BwdBlocksPerSm = 5;
+__global__ void __launch_bounds__(kF32Threads, kF32BwdBlocksPerSm) k_f32_backward(F32Args a) {
   __shared__ double s_red[kF32Threads / 32][6];
+  __shared__ int s_last;
   const int b = blockIdx.y;
   const F32Img& I = a.img[b];
   const F32Reg R = f32_reg(I);
@@ -185,24 +200,22 @@ __global__ void __launch_bounds__(kF32Threads, 4) k_f32_backward(F32Args a) {
   const float* xb = a.x + base;
   const float* gb = a.gy + base;
   float* gxb = a.gx + base;
-  const bool vec = (a.hw & 3) == 0 &&
+  const bool vec = (a.hw & 1) == 0 &&
                    ((reinterpret_cast<uintptr_t>(a.x) | reinterpret_cast<uintptr_t>(a.gy) |
-                     reinterpret_cast<uintptr_t>(a.gx)) & 15) == 0;
-  const int64_t n4 = vec ? a.hw >> 2 : 0;
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += (int64_t)gridDim.x * blockDim.x) {
-    float4 X0 = ld4(xb + 4 * q), X1 = ld4(xb + a.hw + 4 * q), X2 = ld4(xb + 2 * a.hw + 4 * q);
-    float4 G0 = ld4(gb + 4 * q), G1 = ld4(gb + a.hw + 4 * q), G2 = ld4(gb + 2 * a.hw + 4 * q);
-    float4 O0, O1, O2;
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-      f32_back_px(R, B, wt, l2t0, l2t1, l2t2, comp(X0, k), comp(X1, k), comp(X2, k), comp(G0, k),
-                  comp(G1, k), comp(G2, k), gw, comp(O0, k), comp(O1, k), comp(O2, k));
-    st4(gxb + 4 * q, O0);
-    st4(gxb + a.hw + 4 * q, O1);
-    st4(gxb + 2 * a.hw + 4 * q, O2);
+                     reinterpret_cast<uintptr_t>(a.gx)) & 7) == 0;
+  const int64_t n2 = vec ? a.hw >> 1 : 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n2; q += stride) {
+    const float2 X0 = ld2(xb + 2 * q), X1 = ld2(xb + a.hw + 2 * q), X2 = ld2(xb + 2 * a.hw + 2 * q);
+    const float2 G0 = ld2(gb + 2 * q), G1 = ld2(gb + a.hw + 2 * q), G2 = ld2(gb + 2 * a.hw + 2 * q);
+    float2 O0, O1, O2;
+    f32_back_px(R, B, wt, l2t0, l2t1, l2t2, X0.x, X1.x, X2.x, G0.x, G1.x, G2.x, gw, O0.x, O1.x, O2.x);
+    f32_back_px(R, B, wt, l2t0, l2t1, l2t2, X0.y, X1.y, X2.y, G0.y, G1.y, G2.y, gw, O0.y, O1.y, O2.y);
+    st2(gxb + 2 * q, O0);
+    st2(gxb + a.hw + 2 * q, O1);
+    st2(gxb + 2 * a.hw + 2 * q, O2);
   }
-  for (int64_t p = 4 * n4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.hw;
-       p += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t p = 2 * n2 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.hw; p += stride) {
     float o0, o1, o2;
     f32_back_px(R, B, wt, l2t0, l2t1, l2t2, xb[p], xb[a.hw + p], xb[2 * a.hw + p], gb[p],
                 gb[a.hw + p], gb[2 * a.hw + p], gw, o0, o1, o2);
@@ -220,51 +233,39 @@ __global__ void __launch_bounds__(kF32Threads, 4) k_f32_backward(F32Args a) {
     if (lane == 0) s_red[warp][k] = x;
   }
   __syncthreads();
+  const unsigned nblocks = gridDim.x * gridDim.y;
   if (threadIdx.x < 6) {
     double x = 0.0;
     for (int w = 0; w < kF32Threads / 32; ++w) x += s_red[w][threadIdx.x];
     a.partials[((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 6 + threadIdx.x] = x;
+    __threadfence();
   }
-}
-
-// Sum of one launch's block partials in a fixed order.  kReduceLanes threads
-// per entry k each add a fixed strided subset (loads issued eight at a time),
-// then a fixed pairwise tree in shared memory adds their results.  A batch
-// larger than one launch carries its FP64 running sum in acc from launch to
-// launch (stream-ordered, so the order is the same on every run); the last
-// launch writes gwt (column-major).
-constexpr int kReduceLanes = 160;   // 6 x 160 = 960 threads
-__global__ void __launch_bounds__(6 * kReduceLanes) k_f32_reduce(const double* partials,
-                                                                  int nblocks, double* acc,
-                                                                  int first, int last, float* gwt) {
-  __shared__ double s_part[6][256];
-  const int k = threadIdx.x / kReduceLanes, i = threadIdx.x % kReduceLanes;
-  double x = 0.0;
-  for (int b0 = i; b0 < nblocks; b0 += 8 * kReduceLanes) {
-    double v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int b = b0 + u * kReduceLanes;
-      v[u] = b < nblocks ? partials[(size_t)b * 6 + k] : 0.0;
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) x += v[u];
-  }
-  s_part[k][i] = x;
-  if (i < 256 - kReduceLanes) s_part[k][kReduceLanes + i] = 0.0;   // pad to 256
   __syncthreads();
-  for (int h = 128; h > 0; h >>= 1) {
-    for (int j = threadIdx.x; j < 6 * h; j += blockDim.x) {
-      const int kk = j / h, jj = j % h;
-      s_part[kk][jj] += s_part[kk][jj + h];
-    }
-    __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicInc(a.ticket, nblocks - 1u) == nblocks - 1u;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // the last block: every partial, thread t taking blocks t, t + 256, ...
+  double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  for (unsigned i = threadIdx.x; i < nblocks; i += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) v[k] += __ldcg(a.partials + (size_t)i * 6 + k);
   }
+  __syncthreads();   // s_red is reused
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    double x = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) s_red[warp][k] = x;
+  }
+  __syncthreads();
   if (threadIdx.x < 6) {
-    double v = s_part[threadIdx.x][0];
-    if (!first) v += acc[threadIdx.x];
-    if (last) gwt[threadIdx.x] = (float)v;
-    else acc[threadIdx.x] = v;
+    double x = 0.0;
+    for (int w = 0; w < kF32Threads / 32; ++w) x += s_red[w][threadIdx.x];
+    if (!a.first) x += a.acc[threadIdx.x];
+    if (a.last) a.gwt[threadIdx.x] = (float)x;
+    else a.acc[threadIdx.x] = x;
   }
 }
 
@@ -302,47 +303,61 @@ static void f32_image_consts(const spcn_stats* src, const spcn_stats* tgt, float
 
 // The backward's block partials live in the context's partials buffer
 // (2 * 4096 * kAcc doubles): 6 per block, plus 6 for the running sum of a
-// batch that takes several launches.  Each launch is reduced before the next
-// one starts, so the blocks of one launch are capped, not those of a batch.
+// batch that takes several launches.  Each launch is reduced by its own last
+// block before the next one starts, so the blocks of one launch are capped,
+// not those of a batch.
 constexpr size_t kF32PartialDoubles = (size_t)2 * 4096 * kAcc;
 constexpr int kF32MaxBlocks = (int)((kF32PartialDoubles - 8) / 6);
+
+int configure_grad_kernels(Context* c) {
+  c->occ_f32_fwd = c->occ_f32_bwd = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->occ_f32_fwd, k_f32_forward, kF32Threads,
+                                                    0) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->occ_f32_bwd, k_f32_backward, kF32Threads,
+                                                    0) != cudaSuccess)
+    return SPCN_ERR_CUDA;
+  return (c->occ_f32_fwd < 1 || c->occ_f32_bwd < 1) ? SPCN_ERR_CUDA : SPCN_OK;
+}
 
 int launch_f32(Context* c, bool backward, const float* x, const float* gy, int batch, int64_t hw,
                const spcn_stats* src, const spcn_stats* tgt, const float* wt, float lambda,
                float* y, float* gx, float* gwt, cudaStream_t st) {
   F32Args a;   // ~21 KB parameter block, passed by value to each launch
-  int bx = (int)((hw + kF32Threads * 8 - 1) / (kF32Threads * 8));   // about 8 pixels per thread
-  if (bx < 1) bx = 1;
-  if (bx > 1024) bx = 1024;
+  // at most about 8 pixels per thread, and no more blocks than one wave holds
+  int bx_work = (int)((hw + kF32Threads * 8 - 1) / (kF32Threads * 8));
+  if (bx_work < 1) bx_work = 1;
+  const int resident = c->num_sms * (backward ? c->occ_f32_bwd : c->occ_f32_fwd);
   const int launches = (batch + kF32MaxBatch - 1) / kF32MaxBatch;
   double* acc = c->partials + kF32PartialDoubles - 8;
   for (int l = 0; l < launches; ++l) {
     const int b0 = l * kF32MaxBatch;
     const int nb = batch - b0 < kF32MaxBatch ? batch - b0 : kF32MaxBatch;
-    int bxl = bx;
-    if (backward && bxl * nb > kF32MaxBlocks) bxl = kF32MaxBlocks / nb;   // nb <= 192: bxl >= 85
+    int bx = resident / nb;
+    if (bx > bx_work) bx = bx_work;
+    if (bx < 1) bx = 1;
+    if (backward && bx * nb > kF32MaxBlocks) bx = kF32MaxBlocks / nb;   // nb <= 192: bx >= 85
     a.x = x + (int64_t)b0 * 3 * hw;
     a.gy = gy ? gy + (int64_t)b0 * 3 * hw : nullptr;
     a.y = y ? y + (int64_t)b0 * 3 * hw : nullptr;
     a.gx = gx ? gx + (int64_t)b0 * 3 * hw : nullptr;
     a.wt = wt;
     a.partials = c->partials;
+    a.acc = acc;
+    a.gwt = gwt;
+    a.ticket = c->f32_ticket;
+    a.first = l == 0;
+    a.last = l == launches - 1;
     a.hw = hw;
     a.batch = nb;
     for (int k = 0; k < 3; ++k) a.l2i0t[k] = (float)log2((double)tgt->i0[k]);
     for (int i = 0; i < nb; ++i) f32_image_consts(&src[b0 + i], tgt, lambda, &a.img[i]);
-    const dim3 grid(bxl, nb);
+    const dim3 grid(bx, nb);
     {
       TimedLaunch tl(c, backward ? SPCN_KERNEL_F32_BWD : SPCN_KERNEL_F32_FWD, st);
       if (backward) k_f32_backward<<<grid, kF32Threads, 0, st>>>(a);
       else k_f32_forward<<<grid, kF32Threads, 0, st>>>(a);
     }
     SPCN_LAUNCH_CHECK(c);
-    if (backward) {
-      k_f32_reduce<<<1, 6 * kReduceLanes, 0, st>>>(c->partials, bxl * nb, acc, l == 0,
-                                                   l == launches - 1, gwt);
-      SPCN_LAUNCH_CHECK(c);
-    }
   }
   return SPCN_OK;
 }

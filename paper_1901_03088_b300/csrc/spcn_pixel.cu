@@ -596,6 +596,7 @@ __device__ __forceinline__ void ladder_pixels(const LadderArgs& a, const char* l
   const unsigned lr = lane_reg();
   const unsigned lane = threadIdx.x & 31u;
   const u64 stride = (u64)gridDim.x * blockDim.x;
+  const f2 NR1 = pk(L.nrho1, L.nrho1), NR2 = pk(L.nrho2, L.nrho2);
   for (u64 base = (u64)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < g.nchunks;
        base += stride) {
     const u64 q = base + lane;
@@ -612,13 +613,16 @@ __device__ __forceinline__ void ladder_pixels(const LadderArgs& a, const char* l
     }
     if (!__any_sync(0xFFFFFFFFu, n > 0)) continue;
 #pragma unroll
-    for (int k = 0; k < kChunk; ++k) {
-      unsigned aR, aG, aB;
-      pixel_addr(w, k, lr, aR, aG, aB);
-      const bool nw = k < n && min(min(aR, aG), aB) < a.wthr;
-      float h1, h2;
-      solve_one<false>(lut, aR, aG, aB, L, h1, h2);
-      body(nw, __float_as_uint(h1), __float_as_uint(h2));
+    for (int k = 0; k < kChunk; k += 2) {   // two pixels per packed lasso (same arithmetic)
+      unsigned aRA, aGA, aBA, aRB, aGB, aBB;
+      pixel_addr(w, k, lr, aRA, aGA, aBA);
+      pixel_addr(w, k + 1, lr, aRB, aGB, aBB);
+      const bool nwA = k < n && min(min(aRA, aGA), aBA) < a.wthr;
+      const bool nwB = k + 1 < n && min(min(aRB, aGB), aBB) < a.wthr;
+      f2 H1, H2;
+      solve_pair<false>(lut, aRA, aGA, aBA, aRB, aGB, aBB, NR1, NR2, L.kappa, H1, H2);
+      body(nwA, __float_as_uint(lo_of(H1)), __float_as_uint(lo_of(H2)));
+      body(nwB, __float_as_uint(hi_of(H1)), __float_as_uint(hi_of(H2)));
     }
   }
 }
@@ -714,12 +718,12 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_select_ladder(LadderArgs a)
                                                                        (32ll << sh0)) : base0);
     const unsigned low1 = !on1 ? 0xFFFFFFFFu : (desc1 ? (unsigned)max(0ll, (long long)base1 + 1ll -
                                                                        (32ll << sh1)) : base1);
+    // distance from the ladder's base in its direction: keys on the other
+    // side wrap around to huge distances and land beyond bin 31
+    const unsigned mul0 = desc0 ? 0xFFFFFFFFu : 1u, mul1 = desc1 ? 0xFFFFFFFFu : 1u;
     ladder_pixels(a, lut, L, low0, low1, [&](bool nw, unsigned k1, unsigned k2) {
-      unsigned b1 = 32u, b2 = 32u;
-      if (nw && on0 && (desc0 ? k1 <= base0 : k1 >= base0))
-        b1 = min((desc0 ? base0 - k1 : k1 - base0) >> sh0, 32u);
-      if (nw && on1 && (desc1 ? k2 <= base1 : k2 >= base1))
-        b2 = min((desc1 ? base1 - k2 : k2 - base1) >> sh1, 32u);
+      const unsigned b1 = nw ? min(((k1 - base0) * mul0) >> sh0, 32u) : 32u;
+      const unsigned b2 = nw ? min(((k2 - base1) * mul1) >> sh1, 32u) : 32u;
       if (on0 && __any_sync(0xFFFFFFFFu, b1 < 32u)) ballot_count(b1, flip, c0);
       if (on1 && __any_sync(0xFFFFFFFFu, b2 < 32u)) ballot_count(b2, flip, c1);
     });
