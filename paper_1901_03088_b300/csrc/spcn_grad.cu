@@ -175,11 +175,12 @@ __device__ __forceinline__ void st2(float* p, float2 v) { __stcs(reinterpret_cas
 
 // One wave of blocks (blockIdx.y = image, so the image's constants are
 // uniform), each looping over its image two pixels at a time (8-byte accesses
-// per plane) when the size and pointers allow it, one pixel otherwise.  The
+// per plane, the next pair's loads in flight while the current pair is
+// computed) when the size and pointers allow it, one pixel otherwise.  The
 // dL/dW_t block sums go to `partials`; the block that finishes last (a
 // ticket that returns to zero) adds them in block order with a fixed tree,
 // so reruns are bit-identical, and writes gwt or the running sum.
-constexpr int kF32BwdBlocksPerSm = 5;
+constexpr int kF32BwdBlocksPerSm = 4;   // 64 registers: room for the prefetched pair
 __global__ void __launch_bounds__(kF32Threads, kF32BwdBlocksPerSm) k_f32_backward(F32Args a) {
   __shared__ double s_red[kF32Threads / 32][6];
   __shared__ int s_last;
@@ -205,9 +206,20 @@ __global__ void __launch_bounds__(kF32Threads, kF32BwdBlocksPerSm) k_f32_backwar
                      reinterpret_cast<uintptr_t>(a.gx)) & 7) == 0;
   const int64_t n2 = vec ? a.hw >> 1 : 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n2; q += stride) {
-    const float2 X0 = ld2(xb + 2 * q), X1 = ld2(xb + a.hw + 2 * q), X2 = ld2(xb + 2 * a.hw + 2 * q);
-    const float2 G0 = ld2(gb + 2 * q), G1 = ld2(gb + a.hw + 2 * q), G2 = ld2(gb + 2 * a.hw + 2 * q);
+  // the next pair's six loads are issued before the current pair is computed
+  int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float2 nX0, nX1, nX2, nG0, nG1, nG2;
+  if (q < n2) {
+    nX0 = ld2(xb + 2 * q); nX1 = ld2(xb + a.hw + 2 * q); nX2 = ld2(xb + 2 * a.hw + 2 * q);
+    nG0 = ld2(gb + 2 * q); nG1 = ld2(gb + a.hw + 2 * q); nG2 = ld2(gb + 2 * a.hw + 2 * q);
+  }
+  for (; q < n2; q += stride) {
+    const float2 X0 = nX0, X1 = nX1, X2 = nX2, G0 = nG0, G1 = nG1, G2 = nG2;
+    const int64_t qn = q + stride;
+    if (qn < n2) {
+      nX0 = ld2(xb + 2 * qn); nX1 = ld2(xb + a.hw + 2 * qn); nX2 = ld2(xb + 2 * a.hw + 2 * qn);
+      nG0 = ld2(gb + 2 * qn); nG1 = ld2(gb + a.hw + 2 * qn); nG2 = ld2(gb + 2 * a.hw + 2 * qn);
+    }
     float2 O0, O1, O2;
     f32_back_px(R, B, wt, l2t0, l2t1, l2t2, X0.x, X1.x, X2.x, G0.x, G1.x, G2.x, gw, O0.x, O1.x, O2.x);
     f32_back_px(R, B, wt, l2t0, l2t1, l2t2, X0.y, X1.y, X2.y, G0.y, G1.y, G2.y, gw, O0.y, O1.y, O2.y);
