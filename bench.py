@@ -42,6 +42,9 @@ WORKLOADS = {
                 patch_size=256, sample_rate=0.01, tgt=2048),
     "tile": dict(width=8192, height=8192, sample_mode="hash", n_patches=200,
                  patch_size=256, sample_rate=0.01, tgt=2048),
+    # a profiling size: 805 MB in and out, several times L2, a few GB on the device
+    "tile16k": dict(width=16384, height=16384, sample_mode="hash", n_patches=200,
+                    patch_size=256, sample_rate=0.01, tgt=2048),
     # differentiable form: a batch of float32 CHW images, forward + backward
     "grad": dict(batch=64, height=256, width=256, tgt=256),
     # batching: 32 slides x 8 tiles, sides log-uniform in [256, 4096], one target
@@ -52,6 +55,8 @@ WORKLOADS = {
                        patch_size=256, sample_rate=0.01),
     "separation_tile": dict(width=8192, height=8192, sample_mode="hash", n_patches=200,
                             patch_size=256, sample_rate=0.01),
+    "separation_tile16k": dict(width=16384, height=16384, sample_mode="hash", n_patches=200,
+                               patch_size=256, sample_rate=0.01),
 }
 METRIC = "gigapixels/s end-to-end normalize (% of HBM roofline); batched & fwd+bwd vs plain"
 # algorithmic bytes per pixel of each timed kernel (reads + writes of the image)
@@ -732,7 +737,7 @@ def run_ours(args, world, rank, local):
         return run_grad(args, world, rank, local)
     if args.workload == "batch":
         return run_batch(args, world, rank, local)
-    if args.workload in ("separation", "separation_tile"):
+    if args.workload.startswith("separation"):
         return run_separation(args, world, rank, local)
     from paper_1901_03088_b300 import build
     build.build()
