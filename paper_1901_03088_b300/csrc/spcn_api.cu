@@ -164,7 +164,7 @@ int stats_ok(const spcn_stats* s, bool signed_p99) {
   return SPCN_OK;
 }
 
-Geometry make_geometry(const spcn_image* img, uint8_t* out, int64_t out_pitch) {
+Geometry make_geometry(const spcn_image* img, uint8_t* out, int64_t out_pitch, int* err) {
   Geometry g;
   memset(&g, 0, sizeof(g));
   g.src = img->data;
@@ -173,6 +173,9 @@ Geometry make_geometry(const spcn_image* img, uint8_t* out, int64_t out_pitch) {
   g.dst_pitch = out ? out_pitch : 0;
   g.width = img->width;
   g.height = img->height;
+  g.src_bytes = (int64_t)(img->height - 1) * img->pitch_bytes + 3ll * img->width;
+  g.dst_bytes = out ? (int64_t)(img->height - 1) * out_pitch + 3ll * img->width : 0;
+  g.err = err;
   g.npx = (int64_t)img->width * img->height;
   const int64_t row = 3ll * img->width;
   const bool contiguous = img->pitch_bytes == row && (!out || out_pitch == row);
@@ -343,7 +346,7 @@ int spcn_stain_percentile(void* ctx, const spcn_image* img, const spcn_stats* st
   DeviceGuard guard(c->device);
   if (!guard.ok) return SPCN_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const Geometry g = make_geometry(img, nullptr, 0);
+  const Geometry g = make_geometry(img, nullptr, 0, c->err);
   const bool pinv = (params->flags & SPCN_FLAG_H_PINV) != 0;
   rc = launch_build_model(c, c->model, st->W, st->i0, params->lambda, nullptr, s, pinv);
   if (rc) return rc;
@@ -372,7 +375,7 @@ int spcn_stain_densities(void* ctx, const spcn_image* img, const spcn_stats* st,
   DeviceGuard guard(c->device);
   if (!guard.ok) return SPCN_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const Geometry g = make_geometry(img, nullptr, 0);
+  const Geometry g = make_geometry(img, nullptr, 0, c->err);
   const bool pinv = (params->flags & SPCN_FLAG_H_PINV) != 0;
   rc = launch_build_model(c, c->model, st->W, st->i0, params->lambda, nullptr, s, pinv);
   if (rc) return rc;
@@ -406,7 +409,7 @@ int spcn_normalize(void* ctx, const spcn_image* src, const spcn_stats* src_st,
   DeviceGuard guard(c->device);
   if (!guard.ok) return SPCN_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const Geometry g = make_geometry(src, out, out_pitch);
+  const Geometry g = make_geometry(src, out, out_pitch, c->err);
   const bool pinv = (params->flags & SPCN_FLAG_H_PINV) != 0;
   rc = launch_build_model(c, c->model, src_st->W, src_st->i0, params->lambda, nullptr, s, pinv);
   if (rc) return rc;
@@ -521,7 +524,7 @@ int spcn_normalize_estimated(void* ctx, const spcn_image* src, const spcn_stats*
   // the basis estimation's final table (estimated basis and i0, this lambda)
   // is the source table; the window comes from the sample P99
   const Model* m = c->model_b;
-  const Geometry g = make_geometry(src, out, out_pitch);
+  const Geometry g = make_geometry(src, out, out_pitch, c->err);
   const bool pinv = (params->flags & SPCN_FLAG_H_PINV) != 0;
   if (params->flags & SPCN_FLAG_P99_SAMPLED) {   // the sample percentile, no pass 1
     rc = launch_scale_from_basis(c, m, &c->bs->sel, &c->bs->status, tgt_st->p99, s);
@@ -567,7 +570,7 @@ int spcn_stain_densities_estimated(void* ctx, const spcn_image* img, const spcn_
   // the basis estimation's final table is the density table
   rc = launch_check_basis(c, c->model_b, &c->bs->status, s);
   if (rc) return rc;
-  const Geometry g = make_geometry(img, nullptr, 0);
+  const Geometry g = make_geometry(img, nullptr, 0, c->err);
   rc = launch_density(c, g, c->model_b, H, h_stride, s, (params->flags & SPCN_FLAG_H_PINV) != 0);
   if (rc) return rc;
   if (st_out) {

@@ -62,19 +62,24 @@ struct SampleArgs {
   int64_t width, height;
   u64 seed;
   uint32_t* out;
-  u64 m;   // draws (all / hash)
+  u64 m;     // draws (all / hash)
+  u64 cap;   // sample entries allocated
+  int* err;
 };
 
 __global__ void k_sample_all(SampleArgs a) {
   const u64 n = (u64)a.width * a.height;
+  if (!SPCN_CHECK(n <= a.cap, a.err)) return;
   for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x)
     a.out[i] = load_pixel(a.data, a.pitch, i % a.width, i / a.width);
 }
 
 __global__ void k_sample_hash(SampleArgs a) {
   const u64 n = (u64)a.width * a.height;
+  if (!SPCN_CHECK(a.m <= a.cap, a.err)) return;
   for (u64 k = (u64)blockIdx.x * blockDim.x + threadIdx.x; k < a.m; k += (u64)gridDim.x * blockDim.x) {
     const u64 idx = sm64_below(a.seed, k, n);
+    if (!SPCN_CHECK(idx < n, a.err)) continue;
     a.out[k] = load_pixel(a.data, a.pitch, idx % a.width, idx / a.width);
   }
 }
@@ -91,6 +96,8 @@ struct PatchArgs {
   int* cand;          // [n_cand] non-white counts, then [n_patches] accepted candidates
   BasisState* bs;
   uint32_t* out;
+  u64 cap;            // sample entries allocated
+  int* err;
 };
 
 __device__ __forceinline__ void patch_origin(const PatchArgs& a, int k, u64* x0, u64* y0) {
@@ -105,6 +112,7 @@ __global__ void k_patch_count(PatchArgs a) {
   const int k = blockIdx.x;
   u64 x0, y0;
   patch_origin(a, k, &x0, &y0);
+  if (!SPCN_CHECK(x0 + (u64)a.P <= (u64)a.width && y0 + (u64)a.P <= (u64)a.height, a.err)) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   unsigned cnt = 0;
   for (int y = warp; y < a.P; y += nwarps) {
@@ -150,6 +158,9 @@ __global__ void k_patch_gather(PatchArgs a) {
   if (p >= a.bs->n_acc) return;
   u64 x0, y0;
   patch_origin(a, a.cand[a.n_cand + p], &x0, &y0);
+  if (!SPCN_CHECK(x0 + (u64)a.P <= (u64)a.width && y0 + (u64)a.P <= (u64)a.height &&
+                  (u64)(p + 1) * (u64)a.P * (u64)a.P <= a.cap, a.err))
+    return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   uint32_t* out = a.out + (u64)p * (u64)a.P * (u64)a.P;
   for (int y = warp * kGatherSplit + part; y < a.P; y += nwarps * kGatherSplit) {
@@ -813,13 +824,15 @@ int launch_estimate_basis(Context* c, const spcn_image* img, const spcn_params* 
   const int big_grid = c->num_sms * 8;
   if (p->sample_mode != SPCN_SAMPLE_PATCHES) {
     SPCN_CUDA_TRY(cudaMemcpyAsync(&bs->m, &m, sizeof(u64), cudaMemcpyHostToDevice, st));
-    SampleArgs s{img->data, img->pitch_bytes, W, H, p->seed, c->sample, m};
+    SampleArgs s{img->data, img->pitch_bytes, W, H, p->seed, c->sample, m, (u64)c->sample_cap,
+                 c->err};
     if (p->sample_mode == SPCN_SAMPLE_ALL) k_sample_all<<<big_grid, 256, 0, st>>>(s);
     else k_sample_hash<<<big_grid, 256, 0, st>>>(s);
     SPCN_LAUNCH_CHECK(c);
   } else {
     PatchArgs pa{img->data, img->pitch_bytes, W, H, p->seed, p->patch_size, p->n_patches,
-                 n_cand, (unsigned)p->white_thresh, c->cand, bs, c->sample};
+                 n_cand, (unsigned)p->white_thresh, c->cand, bs, c->sample, (u64)c->sample_cap,
+                 c->err};
     k_patch_count<<<n_cand, 256, 0, st>>>(pa);
     SPCN_LAUNCH_CHECK(c);
     k_patch_accept<<<1, 32, 0, st>>>(pa);

@@ -237,7 +237,10 @@ __device__ __noinline__ void batch_drain(const uint2* queue, int count, u64 c0, 
         const int k = 2 * (7 - (i & 7)) + (i >> 3);
         const ChunkPos p = chunk_pos(g, c0 + qj);
         const uint8_t* src = g.src + p.src_off + 3 * k;
-        const unsigned r = __ldg(src), gg = __ldg(src + 1), b = __ldg(src + 2);
+        const bool inside = SPCN_CHECK(k < p.n && p.src_off + 3 * (int64_t)k + 3 <= g.src_bytes,
+                                       g.err);
+        const unsigned r = inside ? __ldg(src) : 255u, gg = inside ? __ldg(src + 1) : 255u,
+                       b = inside ? __ldg(src + 2) : 255u;
         float h1, h2;
         solve_one(lut, (r << 8) | lr, (gg << 8) | lr, (b << 8) | lr, L, h1, h2);
         k0 = __float_as_uint(h1);
@@ -489,7 +492,11 @@ template <>
 __device__ __forceinline__ Geometry geometry_as<Geometry>(const Geometry& g) { return g; }
 template <>
 __device__ __forceinline__ FlatGeometry geometry_as<FlatGeometry>(const Geometry& g) {
+#ifdef SPCN_CHECKED
+  return FlatGeometry{g.src, g.dst, (u64)g.npx, g.vec_src, g.vec_dst, g.src_bytes, g.dst_bytes, g.err};
+#else
   return FlatGeometry{g.src, g.dst, (u64)g.npx, g.vec_src, g.vec_dst};
+#endif
 }
 
 // One pass-1 item: chunks [c0, c1) of a tile, by the whole block.
@@ -530,6 +537,7 @@ __device__ __forceinline__ unsigned batch_pass1(const BatchArgs& a, unsigned til
                           c_b1, mask);
         packed = (unsigned)lo_of(mask) | ((unsigned)hi_of(mask) << 16);
       } else {
+        if (SPCN_CHECK(p.src_off + 3 * (int64_t)p.n <= g.src_bytes, g.err))
         packed = open_window_partial(g.src + p.src_off, p.n, lut, lr, L, a.wthr, nk0, lk0, nk1,
                                      lk1, c_nw, c_b0, c_b1);
       }
@@ -924,7 +932,7 @@ static int batch_create(Context* c, int n, const spcn_image* tiles, const spcn_s
   for (int t = 0; t < n; ++t) {
     BatchTile& T = b->tiles[t];
     memset(&T, 0, sizeof(T));
-    T.g = make_geometry(&tiles[t], outs[t], out_pitches[t]);
+    T.g = make_geometry(&tiles[t], outs[t], out_pitches[t], c->err);
     int m = -1;
     for (size_t k = 0; k < rep.size() && m < 0; ++k)
       if (memcmp(tile_stats[rep[k]].W, tile_stats[t].W, sizeof(float) * 6) == 0 &&

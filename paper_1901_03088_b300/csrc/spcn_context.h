@@ -103,7 +103,7 @@ bool params_ok(const spcn_params* p);
 // be negative (pseudo-inverse densities)
 int stats_ok(const spcn_stats* s, bool signed_p99 = false);
 spcn_stats output_target(const spcn_stats* t, const spcn_params* p);   // Eq. 4's target record
-Geometry make_geometry(const spcn_image* img, uint8_t* out, int64_t out_pitch);
+Geometry make_geometry(const spcn_image* img, uint8_t* out, int64_t out_pitch, int* err);
 
 int ensure_sample_capacity(Context* c, size_t n);
 int ensure_candidate_capacity(Context* c, int n);

@@ -40,6 +40,7 @@ struct F32Args {
   float* gwt;             // dL/dW_t (written by the last launch)
   unsigned* ticket;       // last-block ticket (returns to 0 after every launch)
   int first, last;        // this launch is the first / last of its batch
+  int* err;               // the context's error word (bounds-checked build)
   int64_t hw;             // pixels per image
   int batch;              // images in this launch
   float l2i0t[3];         // log2 i0_t
@@ -97,6 +98,7 @@ __device__ __forceinline__ float& comp(float4& v, int k) {
 // image size and pointers allow it, one pixel per step otherwise.
 __global__ void __launch_bounds__(kF32Threads) k_f32_forward(F32Args a) {
   const int b = blockIdx.y;
+  if (!SPCN_CHECK(b < a.batch && b < kF32MaxBatch, a.err)) return;
   const F32Reg R = f32_reg(a.img[b]);
   float wt[6];
 #pragma unroll
@@ -185,6 +187,7 @@ __global__ void __launch_bounds__(kF32Threads, kF32BwdBlocksPerSm) k_f32_backwar
   __shared__ double s_red[kF32Threads / 32][6];
   __shared__ int s_last;
   const int b = blockIdx.y;
+  if (!SPCN_CHECK(b < a.batch && b < kF32MaxBatch, a.err)) return;
   const F32Img& I = a.img[b];
   const F32Reg R = f32_reg(I);
   F32Back B;
@@ -357,6 +360,7 @@ int launch_f32(Context* c, bool backward, const float* x, const float* gy, int b
     a.acc = acc;
     a.gwt = gwt;
     a.ticket = c->f32_ticket;
+    a.err = c->err;
     a.first = l == 0;
     a.last = l == launches - 1;
     a.hw = hw;

@@ -110,6 +110,8 @@ struct Geometry {
   int flat;         // 1: rows are contiguous in both src and dst -> one long row
   int vec_src;      // 16-byte vector loads allowed on full chunks
   int vec_dst;      // 16-byte vector stores allowed on full chunks
+  int64_t src_bytes, dst_bytes;   // extent of each buffer: (height - 1) pitch + 3 width
+  int* err;         // the context's error word (the bounds-checked build records into it)
 };
 
 // ---------------------------------------------------------------- helpers
@@ -128,6 +130,21 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
 __device__ __forceinline__ void record_error(int* err, int code) {
   atomicCAS(err, 0, code);
 }
+
+// Bounds-checked build (-DSPCN_CHECKED, library libspcn_checked.so): device
+// checks of every buffer index and extent that the kernels derive; a failed
+// check records SPCN_ERR_INVALID_ARG in the context's error word (returned by
+// the next synchronising call) and the access is skipped, with no trap.  In
+// the normal build each check is the constant true and compiles away.
+#ifdef SPCN_CHECKED
+__device__ __forceinline__ bool check_or_record(bool ok, int* err) {
+  if (!ok && err) record_error(err, SPCN_ERR_INVALID_ARG);
+  return ok;
+}
+#define SPCN_CHECK(cond, err) (::spcn::check_or_record((cond), (err)))
+#else
+#define SPCN_CHECK(cond, err) (true)
+#endif
 
 // Grid-wide barrier for cooperative launches.  `target` is the arrival count
 // that releases this barrier (k * expected blocks for the k-th barrier).

@@ -228,6 +228,8 @@ __device__ __forceinline__ void drain_queue(const uint2* queue, int count, const
     const uint2 ent = queue[e];
     const ChunkPos p = chunk_pos(g, (u64)ent.x);
     const uint8_t* src = g.src + p.src_off;
+    if (!SPCN_CHECK(ent.x < g.nchunks && p.src_off >= 0 && p.src_off + 48 <= g.src_bytes, g.err))
+      continue;   // queued chunks are full chunks of the image
 #pragma unroll 1
     for (int lane = 0; lane < 2; ++lane) {
       unsigned m = lane ? (ent.y >> 16) : (ent.y & 0xFFFFu);
@@ -337,6 +339,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_window(WindowArgs a) {
                       SPCN_WF(nh0), SPCN_WF(hk0), SPCN_WF(nh1), SPCN_WF(hk1)};
 #undef SPCN_WF
   const Geometry g = a.g;
+  if (!SPCN_CHECK(C.nb0 <= (unsigned)kWinBins && C.nb1 <= (unsigned)kWinBins, g.err)) return;
   const u64 stride = (u64)gridDim.x * blockDim.x;
   const unsigned lane = threadIdx.x & 31u;
   const unsigned lt = (1u << lane) - 1u;
@@ -359,7 +362,8 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_window(WindowArgs a) {
       const ChunkPos p = chunk_pos(g, q);
       load_chunk<false>(g, p, w);
       if (p.n != kChunk) {
-        partial_chunk<PINV>(g.src + p.src_off, p.n, lut, lr, L, C, s_coarse, c_nw, c_b0, c_b1);
+        if (SPCN_CHECK(p.src_off >= 0 && p.src_off + 3 * (int64_t)p.n <= g.src_bytes, g.err))
+          partial_chunk<PINV>(g.src + p.src_off, p.n, lut, lr, L, C, s_coarse, c_nw, c_b0, c_b1);
       } else if (!chunk_white(w, wm, we)) {
         const bool below = !PINV && chunk_below_window(w, lut, lr, C);   // counts only, no lasso
         if (below || wbelow) {
@@ -746,8 +750,9 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_select_ladder(LadderArgs a)
   __syncthreads();
   {
     const unsigned lo0 = S[0].state == 2 ? S[0].lo : 0u, lo1 = S[1].state == 2 ? S[1].lo : 0u;
-    const unsigned w0 = S[0].state == 2 ? S[0].hi - S[0].lo : 0u;
-    const unsigned w1 = S[1].state == 2 ? S[1].hi - S[1].lo : 0u;
+    unsigned w0 = S[0].state == 2 ? S[0].hi - S[0].lo : 0u;
+    unsigned w1 = S[1].state == 2 ? S[1].hi - S[1].lo : 0u;
+    if (!SPCN_CHECK(w0 <= (unsigned)kWinBins && w1 <= (unsigned)kWinBins, a.err)) w0 = w1 = 0u;
     u64* fine = a.fine;
     ladder_pixels(a, lut, L, w0 ? lo0 : 0xFFFFFFFFu, w1 ? lo1 : 0xFFFFFFFFu,
                   [&](bool nw, unsigned k1, unsigned k2) {
@@ -959,6 +964,10 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_density(DensityArgs a)
       density_chunk<PINV>(w, lut, lr, NR1, NR2, L.kappa, HS, h1, h2);
     }
     const u64 px0 = __shfl_sync(0xFFFFFFFFu, p.px, 0);
+#ifdef SPCN_CHECKED
+    const bool inside = !have || SPCN_CHECK(p.px + (u64)p.n <= (u64)g.npx, g.err);
+    if (!__all_sync(0xFFFFFFFFu, inside)) continue;   // a plane index beyond the image: no store
+#endif
     const bool run = __all_sync(0xFFFFFFFFu, have && p.n == kChunk && p.px == px0 + 16u * lane);
     if (run && vec_h && (px0 & 3) == 0) {
       store_plane_coalesced(a.H + px0, h1, stage, lane);

@@ -48,6 +48,10 @@ struct FlatGeometry {
   uint8_t* dst;
   u64 npx;
   int vec_src, vec_dst;
+#ifdef SPCN_CHECKED
+  int64_t src_bytes, dst_bytes;
+  int* err;
+#endif
 };
 
 __device__ __forceinline__ ChunkPos chunk_pos(const FlatGeometry& g, u64 q) {
@@ -72,6 +76,12 @@ __device__ __forceinline__ unsigned byte_at(const unsigned (&w)[12], int i) {
 template <bool STREAM, class G>
 __device__ __forceinline__ void load_chunk(const G& g, const ChunkPos& p,
                                            unsigned (&w)[12]) {
+  if (!SPCN_CHECK(p.src_off >= 0 && p.n >= 0 && p.n <= kChunk &&
+                  p.src_off + 3 * (int64_t)p.n <= g.src_bytes, g.err)) {
+#pragma unroll
+    for (int i = 0; i < 12; ++i) w[i] = 0xFFFFFFFFu;
+    return;
+  }
   const uint8_t* s = g.src + p.src_off;
   if (p.n == kChunk && g.vec_src) {
     const uint4* v = reinterpret_cast<const uint4*>(s);
@@ -98,6 +108,9 @@ __device__ __forceinline__ void load_chunk(const G& g, const ChunkPos& p,
 template <class G>
 __device__ __forceinline__ void store_chunk(const G& g, const ChunkPos& p,
                                             const unsigned (&o)[12]) {
+  if (!SPCN_CHECK(p.dst_off >= 0 && p.n >= 0 && p.n <= kChunk &&
+                  p.dst_off + 3 * (int64_t)p.n <= g.dst_bytes, g.err))
+    return;
   uint8_t* d = g.dst + p.dst_off;
   if (p.n == kChunk && g.vec_dst) {
     uint4* v = reinterpret_cast<uint4*>(d);

@@ -11,7 +11,10 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libspcn.so")
+# SPCN_LIBRARY=checked selects the bounds-checked build (device index checks
+# that report SPCN_ERR_INVALID_ARG); the default is the normal build.
+LIB_PATH = os.path.join(HERE, "libspcn_checked.so" if os.environ.get("SPCN_LIBRARY") == "checked"
+                        else "libspcn.so")
 
 SPCN_OK = 0
 STATUS_NAMES = {
