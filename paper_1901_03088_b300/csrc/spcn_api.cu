@@ -173,9 +173,13 @@ Geometry make_geometry(const spcn_image* img, uint8_t* out, int64_t out_pitch, i
   g.dst_pitch = out ? out_pitch : 0;
   g.width = img->width;
   g.height = img->height;
+#ifdef SPCN_CHECKED
   g.src_bytes = (int64_t)(img->height - 1) * img->pitch_bytes + 3ll * img->width;
   g.dst_bytes = out ? (int64_t)(img->height - 1) * out_pitch + 3ll * img->width : 0;
   g.err = err;
+#else
+  (void)err;
+#endif
   g.npx = (int64_t)img->width * img->height;
   const int64_t row = 3ll * img->width;
   const bool contiguous = img->pitch_bytes == row && (!out || out_pitch == row);

@@ -110,8 +110,10 @@ struct Geometry {
   int flat;         // 1: rows are contiguous in both src and dst -> one long row
   int vec_src;      // 16-byte vector loads allowed on full chunks
   int vec_dst;      // 16-byte vector stores allowed on full chunks
+#ifdef SPCN_CHECKED
   int64_t src_bytes, dst_bytes;   // extent of each buffer: (height - 1) pitch + 3 width
-  int* err;         // the context's error word (the bounds-checked build records into it)
+  int* err;         // the context's error word, where failed device checks are recorded
+#endif
 };
 
 // ---------------------------------------------------------------- helpers
