@@ -535,7 +535,7 @@ int spcn_normalize_estimated(void* ctx, const spcn_image* src, const spcn_stats*
     if (rc) return rc;
   } else {
     Window* wdev = static_cast<Window*>(c->wdev);
-    rc = launch_window_from_basis(c, m, &c->bs->sel, &c->bs->status, wdev, s);
+    rc = launch_window_from_basis(c, m, c->model_b, &c->bs->sel, &c->bs->status, wdev, s);
     if (rc) return rc;
     rc = launch_percentile_passes_dev(c, g, m, params->white_thresh, (double)params->stain_pct,
                                       wdev, tgt_st->p99, s, pinv);

@@ -19,7 +19,8 @@ namespace spcn {
 
 int launch_select_list(Context* c, const uint32_t* items, const u64* n_dev, const Model* m,
                        SelectState* sel, u64* ghist, double pct, cudaStream_t st,
-                       bool pinv = false, unsigned sub = 1);
+                       bool pinv = false, unsigned sub = 1, bool band = false,
+                       const int* units = nullptr);
 
 constexpr int kCompactBlock = 4096;
 constexpr int kCompactThreads = 512;
@@ -891,10 +892,12 @@ int launch_estimate_basis(Context* c, const spcn_image* img, const spcn_params* 
     SPCN_LAUNCH_CHECK(c);
     return SPCN_OK;
   }
-  // hint_only: the percentile only places the search window of an exact
-  // whole-image percentile; every 16th group of four sample pixels suffices
+  // hint_only: the sample only places the search window of an exact
+  // whole-image percentile (a binomial band around the percentile); every
+  // 16th group of four sample pixels suffices
   return launch_select_list(c, c->nw, &bs->n_nw, c->model_b, &bs->sel, c->rhist_b,
-                            (double)p->stain_pct, st, pinv, hint_only ? 16u : 1u);
+                            (double)p->stain_pct, st, pinv, hint_only ? 16u : 1u, hint_only,
+                            p->sample_mode == SPCN_SAMPLE_PATCHES ? &bs->n_acc : nullptr);
 }
 
 // Wait for the estimation launched on `st` and fill the host record.

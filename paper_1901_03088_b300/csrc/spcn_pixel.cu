@@ -815,8 +815,32 @@ struct SelectListArgs {
   int* err;
   long long timeout_ns;
   double pct;
-  unsigned sub;   // 1: the whole list; s > 1: every s-th group of four (a hint only)
+  unsigned sub;      // 1: the whole list; s > 1: every s-th group of four (a hint only)
+  int band;          // select the ends of the binomial band instead of ranks k, k+1
+  const int* units;  // independent sampling units (kept patches), or null: every item
 };
+
+// The band of a hint: a population quantile p lies, with probability about
+// 1 - 6e-5, between the sample's order statistics at p -/+ delta, delta =
+// z sqrt(p (1 - p) / m_eff) with z = 4 (the binomial count below the quantile
+// in an i.i.d. sample).  m_eff is the number of independent sampling units:
+// the visited items of a pixel sample, the kept patches of a patch sample
+// (pixels of one patch are not independent).  delta is capped at kBandMax, so
+// that the window stays affordable when the sample says little.
+constexpr double kBandZ = 4.0;
+constexpr double kBandMax = 0.002;
+__device__ __forceinline__ void band_ranks(u64 n, double pct, double m_eff, u64* r_lo, u64* r_hi) {
+  const double p = pct / 100.0;
+  double d = kBandZ * sqrt(p * (1.0 - p) / fmax(m_eff, 1.0));
+  if (d > kBandMax) d = kBandMax;
+  const double span = (double)(n - 1);
+  double lo = floor((p - d) * span), hi = ceil((p + d) * span);
+  if (lo < 0.0) lo = 0.0;
+  if (hi > span) hi = span;
+  if (lo > hi) lo = hi;
+  *r_lo = (u64)lo;
+  *r_hi = (u64)hi;
+}
 
 // Percentile of the densities of a packed list of non-white pixels (the basis
 // sample, §3.1 item 2), radix select from scratch; with sub > 1 of a regular
@@ -832,7 +856,13 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_select_list(SelectListArgs 
   u64 rank[kTracks];
   int active[kTracks];
   double t;
-  type7_ranks(n, a.pct, &rank[0], &rank[1], &t);
+  if (a.band) {   // tracks 2j, 2j+1: the band's ends; p99 = their midpoint
+    const double m_eff = a.units ? (double)min((u64)max(*a.units, 1), n) : (double)n;
+    band_ranks(n, a.pct, m_eff, &rank[0], &rank[1]);
+    t = 0.5;
+  } else {
+    type7_ranks(n, a.pct, &rank[0], &rank[1], &t);
+  }
   rank[2] = rank[0];
   rank[3] = rank[1];
   for (int i = 0; i < kTracks; ++i) active[i] = 1;
@@ -1063,20 +1093,41 @@ int configure_pixel_kernels(Context* c) {
 // failed estimation is recorded in the error word and leaves no window (the
 // exact fallback then runs; the outputs are computed but the call reports
 // the error).
-__global__ void k_window_from_basis(const Model* m, const SelectState* sample_sel,
-                                    const int* basis_status, Window* w, int* err) {
+// The sample select ran in band mode: per stain, keys 2j and 2j+1 are the
+// sample's order statistics at the ends of the binomial band around the
+// percentile, p99[j] the band's midpoint (all in the sample model's scaled
+// units); the window covers the band in the image model's units.
+__global__ void k_window_from_basis(const Model* m, const Model* sample_model,
+                                    const SelectState* sample_sel, const int* basis_status,
+                                    Window* w, int* err) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
   int st = *basis_status;
   if (st == SPCN_OK) st = m->status;
   if (st != SPCN_OK) record_error(err, st);
+  if (st != SPCN_OK) {
+    *w = window_for(0.0, 0.0);
+    return;
+  }
   const double hs = ldexp(1.0, -m->lasso.hexp);
-  *w = st == SPCN_OK ? window_for(sample_sel->p99[0] * hs, sample_sel->p99[1] * hs)
-                     : window_for(0.0, 0.0);
+  const double hb = (double)sample_model->lasso.hscale;   // sample keys -> densities
+  Window r;
+  unsigned* lo[2] = {&r.lo0, &r.lo1};
+  unsigned* nb[2] = {&r.nb0, &r.nb1};
+  float* nk[2] = {&r.nk0, &r.nk1};
+  float* lk[2] = {&r.lk0, &r.lk1};
+  float* nh[2] = {&r.nh0, &r.nh1};
+  float* hk[2] = {&r.hk0, &r.hk1};
+  for (int j = 0; j < 2; ++j)
+    window_band((double)__uint_as_float(sample_sel->key[2 * j]) * hb * hs,
+                (double)__uint_as_float(sample_sel->key[2 * j + 1]) * hb * hs,
+                sample_sel->p99[j] * hs, lo[j], nb[j], nk[j], lk[j], nh[j], hk[j]);
+  *w = r;
 }
 
-int launch_window_from_basis(Context* c, const Model* m, const SelectState* sample_sel,
-                             const int* basis_status, Window* w, cudaStream_t st) {
-  k_window_from_basis<<<1, 32, 0, st>>>(m, sample_sel, basis_status, w, c->err);
+int launch_window_from_basis(Context* c, const Model* m, const Model* sample_model,
+                             const SelectState* sample_sel, const int* basis_status, Window* w,
+                             cudaStream_t st) {
+  k_window_from_basis<<<1, 32, 0, st>>>(m, sample_model, sample_sel, basis_status, w, c->err);
   SPCN_LAUNCH_CHECK(c);
   return SPCN_OK;
 }
@@ -1256,8 +1307,10 @@ int launch_percentile_passes_dev(Context* c, const Geometry& g, const Model* m, 
 
 int launch_select_list(Context* c, const uint32_t* items, const u64* n_dev, const Model* m,
                        SelectState* sel, u64* ghist, double pct, cudaStream_t st, bool pinv,
-                       unsigned sub) {
+                       unsigned sub, bool band, const int* units) {
   SelectListArgs a;
+  a.band = band ? 1 : 0;
+  a.units = units;
   a.items = items;
   a.n_dev = n_dev;
   a.m = m;

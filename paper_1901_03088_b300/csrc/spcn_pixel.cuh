@@ -723,6 +723,33 @@ __host__ __device__ inline void window_of(double hint, unsigned* lo, unsigned* n
   below_consts(klo + (unsigned)width, nh, hk);
 }
 
+// Window [lo, lo+nb) of FP32 keys covering a band [blo, bhi] of scaled
+// densities (the sample's order statistics around the percentile, see
+// k_select_list), at most kWinBins keys: a wider band is narrowed to kWinBins
+// keys centred on `mid`.  A band that does not start above 0 falls back to
+// window_of(mid).
+__host__ __device__ inline void window_band(double blo, double bhi, double mid, unsigned* lo,
+                                            unsigned* nb, float* nk, float* lk, float* nh,
+                                            float* hk) {
+  if (!(blo > 0.0) || !(bhi >= blo) || !(bhi <= 1.7976931348623157e308) || blo < 0x1p-100) {
+    window_of(mid, lo, nb, nk, lk, nh, hk);
+    return;
+  }
+  unsigned klo = key_of((float)blo), khi = key_of((float)bhi);
+  if (klo == 0u) klo = 1u;   // key 0 (h = 0) is counted below the window
+  if (khi < klo) khi = klo;
+  u64 width = (u64)khi - klo + 1;
+  if (width > (u64)kWinBins) {
+    const unsigned kmid = key_of((float)mid);
+    klo = kmid > (unsigned)(kWinBins / 2) ? kmid - (unsigned)(kWinBins / 2) : 1u;
+    width = kWinBins;
+  }
+  *lo = klo;
+  *nb = (unsigned)width;
+  below_consts(klo, nk, lk);
+  below_consts(klo + (unsigned)width, nh, hk);
+}
+
 __host__ __device__ inline Window window_for(double hint0, double hint1) {
   Window w;
   window_of(hint0, &w.lo0, &w.nb0, &w.nk0, &w.lk0, &w.nh0, &w.hk0);
@@ -731,8 +758,9 @@ __host__ __device__ inline Window window_for(double hint0, double hint1) {
 }
 
 // Host launchers that take a window (spcn_pixel.cu).
-int launch_window_from_basis(Context* c, const Model* m, const SelectState* sample_sel,
-                             const int* basis_status, Window* w, cudaStream_t st);
+int launch_window_from_basis(Context* c, const Model* m, const Model* sample_model,
+                             const SelectState* sample_sel, const int* basis_status, Window* w,
+                             cudaStream_t st);
 // Constants (wm, we) of the conservative all-white test of a full chunk of
 // pass 1: the AND of its twelve words, masked by wm, equals we.
 void white_test_consts(int white_thresh, unsigned* wm, unsigned* we);
