@@ -14,6 +14,8 @@ Workloads (synthetic; the paper's TCGA slides are not available):
   wsi   100000 x 80000 source (8 Gpx, 24 GB in + 24 GB out resident in HBM),
         basis from 200 patches of 256 x 256, 2048 x 2048 target.
   tile  8192 x 8192 source, basis from a 1% SplitMix64 sample, 2048 x 2048 target.
+  pair  512 x 512 source and target, basis from every pixel (the latency of one
+        end-to-end normalisation).
   batch 256 uneven tiles (32 slides x 8, sides log-uniform in [256, 4096]),
         per-slide statistics, one target: the batched persistent launch
         (autotuned, CUDA-graph replays) against 256 sequential plain calls.
@@ -42,6 +44,10 @@ WORKLOADS = {
                 patch_size=256, sample_rate=0.01, tgt=2048),
     "tile": dict(width=8192, height=8192, sample_mode="hash", n_patches=200,
                  patch_size=256, sample_rate=0.01, tgt=2048),
+    # the small pair: 512 x 512 source and target, basis from every pixel;
+    # reported as the latency of one end-to-end normalisation
+    "pair": dict(width=512, height=512, sample_mode="all", n_patches=200,
+                 patch_size=256, sample_rate=0.01, tgt=512),
     # a profiling size: 805 MB in and out, several times L2, a few GB on the device
     "tile16k": dict(width=16384, height=16384, sample_mode="hash", n_patches=200,
                     patch_size=256, sample_rate=0.01, tgt=2048),
@@ -307,6 +313,8 @@ def oracle_params(wl, side, n_patches):
         ps = min(wl["patch_size"], side)      # a crop smaller than a patch takes smaller patches
         return (O.Params(sample_mode="patches", n_patches=n_patches, patch_size=ps, seed=0),
                 wl["n_patches"] * wl["patch_size"] ** 2 / (n_patches * ps * ps))
+    if wl["sample_mode"] == "all":
+        return O.Params(sample_mode="all"), wl["width"] * wl["height"] / (side * side)
     return (O.Params(sample_mode="hash", sample_rate=wl["sample_rate"], seed=0),
             wl["width"] * wl["height"] / (side * side))
 
@@ -331,20 +339,24 @@ def normalize_workload_desc(name, wl):
     """The normalisation workload as both arms name it in their config."""
     return (f"{name}: {wl['width']}x{wl['height']} uint8 RGB source, "
             f"{wl['tgt']}x{wl['tgt']} target, basis from "
-            + (f"{wl['n_patches']} patches of {wl['patch_size']}^2"
-               if wl["sample_mode"] == "patches" else f"{wl['sample_rate']:.0%} hash sample"))
+            + (f"{wl['n_patches']} patches of {wl['patch_size']}^2" if wl["sample_mode"] == "patches"
+               else "every pixel" if wl["sample_mode"] == "all"
+               else f"{wl['sample_rate']:.0%} hash sample"))
 
 
 def normalize_config(name, wl, world):
     """The config object of a normalisation line, the same in both arms."""
     npx = wl["width"] * wl["height"]
+    l2 = (f"inputs ({3 * npx / 1e9:.1f} GB) larger than L2 (126 MB); no flush"
+          if 3 * npx > 126e6 else
+          f"inputs ({3 * npx / 1e6:.2f} MB) fit in L2: a latency measurement, not flushed")
     return {"workload": normalize_workload_desc(name, wl), "pixels_per_step": npx,
-            "parallelism": f"replicas x{world}",
-            "l2": f"inputs ({3 * npx / 1e9:.1f} GB) larger than L2 (126 MB); no flush"}
+            "parallelism": f"replicas x{world}", "l2": l2}
 
 
 def oracle_sample_desc(side, p, basis_scale, wl, parts, cores, scaled_s):
     smp = (f"{p.n_patches} patches of {p.patch_size}^2" if p.sample_mode == "patches"
+           else "every pixel of the crop" if p.sample_mode == "all"
            else f"a {p.sample_rate:.0%} hash sample of the crop")
     return (f"per step: oracle basis estimation from {smp} (one process; scaled "
             f"x{basis_scale:g} to the slide's sample), then the exact non-white P99 and the "
