@@ -220,7 +220,14 @@ int spcn_normalize(void* ctx, const spcn_image* src, const spcn_stats* src_st,
  * estimated statistics, except that the statistics stay on the device (the
  * source table is built from the estimated basis and i0, and the P99 search
  * window from the sample percentile) so there is no host round trip between
- * the two.  The output bytes are those of the two calls in sequence.
+ * the two.  The search window covers a binomial band of the sample's order
+ * statistics around the percentile.  The output bytes are those of the two
+ * calls in sequence.
+ * Without src_st_out the call puts only kernels and memsets into the stream,
+ * every argument passed by value: once the context's sample buffers have the
+ * size the call needs (after a first call with the same sampling) and with
+ * kernel timing off, it can be captured into a CUDA graph; replays use the
+ * pointers, parameters and target statistics of the capture.
  * If src_st_out (host) is non-NULL the call blocks and returns the estimated
  * source statistics there, with p99 = the percentile the scale used (the
  * exact one of the whole source; with SPCN_FLAG_P99_SAMPLED the sample's,

@@ -66,10 +66,13 @@ struct SampleArgs {
   u64 m;     // draws (all / hash)
   u64 cap;   // sample entries allocated
   int* err;
+  u64* m_out;   // the estimation's sample size, written here on the device (no host
+                // operand in the stream, so the call can be captured into a CUDA graph)
 };
 
 __global__ void k_sample_all(SampleArgs a) {
   const u64 n = (u64)a.width * a.height;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *a.m_out = a.m;
   if (!SPCN_CHECK(n <= a.cap, a.err)) return;
   for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x)
     a.out[i] = load_pixel(a.data, a.pitch, i % a.width, i / a.width);
@@ -77,6 +80,7 @@ __global__ void k_sample_all(SampleArgs a) {
 
 __global__ void k_sample_hash(SampleArgs a) {
   const u64 n = (u64)a.width * a.height;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *a.m_out = a.m;
   if (!SPCN_CHECK(a.m <= a.cap, a.err)) return;
   for (u64 k = (u64)blockIdx.x * blockDim.x + threadIdx.x; k < a.m; k += (u64)gridDim.x * blockDim.x) {
     const u64 idx = sm64_below(a.seed, k, n);
@@ -824,9 +828,8 @@ int launch_estimate_basis(Context* c, const spcn_image* img, const spcn_params* 
   SPCN_CUDA_TRY(cudaMemsetAsync(bs, 0, sizeof(BasisState), st));
   const int big_grid = c->num_sms * 8;
   if (p->sample_mode != SPCN_SAMPLE_PATCHES) {
-    SPCN_CUDA_TRY(cudaMemcpyAsync(&bs->m, &m, sizeof(u64), cudaMemcpyHostToDevice, st));
     SampleArgs s{img->data, img->pitch_bytes, W, H, p->seed, c->sample, m, (u64)c->sample_cap,
-                 c->err};
+                 c->err, &bs->m};
     if (p->sample_mode == SPCN_SAMPLE_ALL) k_sample_all<<<big_grid, 256, 0, st>>>(s);
     else k_sample_hash<<<big_grid, 256, 0, st>>>(s);
     SPCN_LAUNCH_CHECK(c);
