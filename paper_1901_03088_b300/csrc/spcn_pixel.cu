@@ -350,42 +350,33 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_window(WindowArgs a) {
   const bool wbelow = !PINV && whites_below((a.wthr >> 8) - 1u, lut, lr, C);
   int qn = 0;   // entries in this warp's hit queue (warp-uniform)
   int ns = 0;   // tissue chunks on this warp's stack (warp-uniform)
-  // every lane of a warp runs the same number of iterations (warp-uniform
-  // loop), so the queue and stack bookkeeping needs only warp-level operations
-  for (u64 base = (u64)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < g.nchunks;
-       base += stride) {
-    const u64 q = base + lane;
-    unsigned w[12];
-    unsigned qi = (unsigned)q;
-    bool tissue = false;
-    if (q < g.nchunks) {
-      const ChunkPos p = chunk_pos(g, q);
-      load_chunk<false>(g, p, w);
-      if (p.n != kChunk) {
-        if (SPCN_CHECK(p.src_off >= 0 && p.src_off + 3 * (int64_t)p.n <= g.src_bytes, g.err))
-          partial_chunk<PINV>(g.src + p.src_off, p.n, lut, lr, L, C, s_coarse, c_nw, c_b0, c_b1);
-      } else if (!chunk_white(w, wm, we)) {
-        const bool below = !PINV && chunk_below_window(w, lut, lr, C);   // counts only, no lasso
-        if (below || wbelow) {
-          // the non-white count; with wbelow a tissue chunk's lasso counts all
-          // 16 pixels below both windows (its white ones included), so its
-          // white pixels are taken off here
-          const float nw = chunk_nonwhite(w, wb);
-          const f2 nb = pk(below ? nw : nw - (float)kChunk, 0.f);
-          c_nw = add2(c_nw, pk(nw, 0.f));
-          c_b0 = add2(c_b0, nb);
-          c_b1 = add2(c_b1, nb);
-        }
-        tissue = !below;
-      }
+  // Counts of a full, not all-white chunk; true when it needs the window
+  // arithmetic (not provably below both window starts).
+  auto classify = [&](const unsigned (&w)[12]) -> bool {
+    const bool below = !PINV && chunk_below_window(w, lut, lr, C);   // counts only, no lasso
+    if (below || wbelow) {
+      // the non-white count; with wbelow a tissue chunk's lasso counts all
+      // 16 pixels below both windows (its white ones included), so its
+      // white pixels are taken off here
+      const float nw = chunk_nonwhite(w, wb);
+      const f2 nb = pk(below ? nw : nw - (float)kChunk, 0.f);
+      c_nw = add2(c_nw, pk(nw, 0.f));
+      c_b0 = add2(c_b0, nb);
+      c_b1 = add2(c_b1, nb);
     }
+    return !below;
+  };
+  // The warp's step after each lane classified its chunk: tissue chunks wait
+  // on the stack until a full warp of them is ready, which then runs the
+  // window arithmetic.
+  auto warp_step = [&](bool tissue, unsigned (&w)[12], unsigned qi) {
     const unsigned ball = __ballot_sync(0xFFFFFFFFu, tissue);
     const int cnt = __popc(ball);
     __syncwarp();   // the stack's previous reads and writes are done
     if (ns + cnt < 32) {   // not a full warp yet: stack them
       if (tissue) stack_put(s_stk, s_stq, ns + __popc(ball & lt), w, qi);
       ns += cnt;
-      continue;
+      return;
     }
     if (!tissue) stack_get(s_stk, s_stq, ns - 1 - __popc(~ball & lt), w, qi);
     ns -= 32 - cnt;
@@ -393,6 +384,55 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_window(WindowArgs a) {
       pass1_chunk<PINV, true>(w, qi, true, lut, lr, NR1, NR2, L, C, g, s_queue, s_coarse, qn, c_nw, c_b0, c_b1);
     else
       pass1_chunk<PINV, false>(w, qi, true, lut, lr, NR1, NR2, L, C, g, s_queue, s_coarse, qn, c_nw, c_b0, c_b1);
+  };
+  // every lane of a warp runs the same number of iterations (warp-uniform
+  // loops), so the queue and stack bookkeeping needs only warp-level operations
+  if (flat_fast(g)) {
+    // one long row, 16-byte aligned, fewer than 2^31 full chunks: 32-bit
+    // chunk indices, no per-chunk position arithmetic; the row's partial
+    // last chunk is counted after the loop
+    const unsigned nfull = (unsigned)((u64)g.npx / kChunk);
+    const unsigned stride32 = gridDim.x * blockDim.x;
+    const uint4* src4 = reinterpret_cast<const uint4*>(g.src);
+    for (unsigned base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < nfull;
+         base += stride32) {
+      const unsigned q = base + lane;
+      unsigned w[12];
+      bool tissue = false;
+      if (q < nfull && SPCN_CHECK((int64_t)(q + 1ull) * (3 * kChunk) <= g.src_bytes, g.err)) {
+        const uint4* v = src4 + 3ull * q;
+        const uint4 x = __ldg(v), y = __ldg(v + 1), z = __ldg(v + 2);
+        w[0] = x.x; w[1] = x.y; w[2] = x.z; w[3] = x.w;
+        w[4] = y.x; w[5] = y.y; w[6] = y.z; w[7] = y.w;
+        w[8] = z.x; w[9] = z.y; w[10] = z.z; w[11] = z.w;
+        tissue = !chunk_white(w, wm, we) && classify(w);
+      }
+      warp_step(tissue, w, q);
+    }
+    const int tail = (int)((u64)g.npx % kChunk);
+    if (tail && (u64)blockIdx.x * blockDim.x + threadIdx.x == (u64)nfull % stride) {
+      const int64_t off = (int64_t)nfull * (3 * kChunk);
+      if (SPCN_CHECK(off + 3 * (int64_t)tail <= g.src_bytes, g.err))
+        partial_chunk<PINV>(g.src + off, tail, lut, lr, L, C, s_coarse, c_nw, c_b0, c_b1);
+    }
+  } else {
+    for (u64 base = (u64)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < g.nchunks;
+         base += stride) {
+      const u64 q = base + lane;
+      unsigned w[12];
+      bool tissue = false;
+      if (q < g.nchunks) {
+        const ChunkPos p = chunk_pos(g, q);
+        load_chunk<false>(g, p, w);
+        if (p.n != kChunk) {
+          if (SPCN_CHECK(p.src_off >= 0 && p.src_off + 3 * (int64_t)p.n <= g.src_bytes, g.err))
+            partial_chunk<PINV>(g.src + p.src_off, p.n, lut, lr, L, C, s_coarse, c_nw, c_b0, c_b1);
+        } else {
+          tissue = !chunk_white(w, wm, we) && classify(w);
+        }
+      }
+      warp_step(tissue, w, (unsigned)q);
+    }
   }
   __syncwarp();
   if (ns > 0) {   // the rest of the stack (fewer than 32)

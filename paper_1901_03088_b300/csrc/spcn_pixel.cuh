@@ -19,6 +19,12 @@ struct ChunkPos {
   int n;            // valid pixels (16 except at row ends)
 };
 
+// One long row, 16-byte aligned, with fewer than 2^31 full chunks: the
+// traversal may use 32-bit chunk indices and plain vector loads.
+__device__ __forceinline__ bool flat_fast(const Geometry& g) {
+  return g.flat && g.vec_src && (u64)g.npx / kChunk < (1ull << 31);
+}
+
 __device__ __forceinline__ ChunkPos chunk_pos(const Geometry& g, u64 q) {
   ChunkPos p;
   if (g.flat) {
