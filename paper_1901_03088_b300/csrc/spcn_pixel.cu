@@ -216,40 +216,34 @@ __device__ void window_select(const WindowArgs& a) {
 }
 
 
-// Window-histogram updates of the queued chunks: each entry is a chunk index
-// and its two base-4 masks; only flagged pixels are recomputed (same
-// arithmetic, same keys), reading their bytes again (still in L2).  Called by
-// one warp for its own queue.
+// Window-histogram updates of queued pixels: each entry is a chunk index and
+// one pixel of that chunk that the packed window test flagged; the pixel is
+// recomputed (same arithmetic, same keys) from its bytes, read again (still
+// in L2).  Lane e takes entry e < count (count <= 32): one step of the warp.
 template <bool PINV>
-__device__ __forceinline__ void drain_queue(const uint2* queue, int count, const Geometry& g,
-                                            const char* lut, unsigned lr, const Lasso& L,
-                                            const WindowConst& a, unsigned* s_coarse) {
-  for (int e = (int)(threadIdx.x & 31u); e < count; e += 32) {
-    const uint2 ent = queue[e];
-    const ChunkPos p = chunk_pos(g, (u64)ent.x);
-    const uint8_t* src = g.src + p.src_off;
-    if (!SPCN_CHECK(ent.x < g.nchunks && p.src_off >= 0 && p.src_off + 48 <= g.src_bytes, g.err))
-      continue;   // queued chunks are full chunks of the image
-#pragma unroll 1
-    for (int lane = 0; lane < 2; ++lane) {
-      unsigned m = lane ? (ent.y >> 16) : (ent.y & 0xFFFFu);
-#pragma unroll 1
-      while (m) {
-        const int bit = __ffs(m) - 1;
-        const int pair = 7 - (bit >> 1);
-        m &= ~(3u << (bit & ~1));
-        const int k = 2 * pair + lane;
-        const unsigned r = __ldg(src + 3 * k), gg = __ldg(src + 3 * k + 1), b = __ldg(src + 3 * k + 2);
-        float h1, h2;
-        solve_one<PINV>(lut, (r << 8) | lr, (gg << 8) | lr, (b << 8) | lr, L, h1, h2);
-        window_hit(a, s_coarse, __float_as_uint(h1) - a.lo0, __float_as_uint(h2) - a.lo1);
-      }
-    }
-  }
+__device__ __forceinline__ void drain_pixels(const uint2* queue, int count, const Geometry& g,
+                                             const char* lut, unsigned lr, const Lasso& L,
+                                             const WindowConst& a, unsigned* s_coarse) {
+  const int e = (int)(threadIdx.x & 31u);
+  if (e >= count) return;
+  const uint2 ent = queue[e];
+  const ChunkPos p = chunk_pos(g, (u64)ent.x);
+  const int64_t off = p.src_off + 3 * (int64_t)ent.y;
+  if (!SPCN_CHECK(ent.x < g.nchunks && ent.y < (unsigned)kChunk && off >= 0 &&
+                  off + 3 <= g.src_bytes, g.err))
+    return;   // queued pixels belong to full chunks of the image
+  const uint8_t* src = g.src + off;
+  const unsigned r = __ldg(src), gg = __ldg(src + 1), b = __ldg(src + 2);
+  float h1, h2;
+  solve_one<PINV>(lut, (r << 8) | lr, (gg << 8) | lr, (b << 8) | lr, L, h1, h2);
+  window_hit(a, s_coarse, __float_as_uint(h1) - a.lo0, __float_as_uint(h2) - a.lo1);
 }
 
 // Window arithmetic of one full chunk per lane (lanes with have = false take
-// no part), then the hit queue: called by the whole warp.
+// no part), then the hit queue: called by the whole warp.  Every flagged
+// pixel becomes one queue entry; each time 32 are waiting they are drained
+// in one step of the warp (the queue holds fewer than 32 before a round of
+// appends, which adds at most 32).
 template <bool PINV, bool WHITES_BELOW>
 __device__ __forceinline__ void pass1_chunk(const unsigned (&w)[12], unsigned qi, bool have,
                                             const char* lut, unsigned lr, f2 NR1, f2 NR2,
@@ -257,22 +251,36 @@ __device__ __forceinline__ void pass1_chunk(const unsigned (&w)[12], unsigned qi
                                             const Geometry& g, uint2* s_queue,
                                             unsigned* s_coarse, int& qn, f2& c_nw, f2& c_b0,
                                             f2& c_b1) {
-  unsigned packed = 0u;
+  // bit 2 (7 - p) + h: pixel 2 p + h lies in a window of either stain
+  unsigned d = 0u;
   if (have) {
     f2 mask;
     window_chunk<PINV, WHITES_BELOW>(w, lut, lr, NR1, NR2, L.kappa, C, c_nw, c_b0, c_b1, mask);
-    packed = (unsigned)lo_of(mask) | ((unsigned)hi_of(mask) << 16);
+    const unsigned m0 = (unsigned)lo_of(mask), m1 = (unsigned)hi_of(mask);
+    d = ((m0 | (m0 >> 1)) & 0x5555u) | (((m1 | (m1 >> 1)) & 0x5555u) << 1);
   }
-  const bool hit = packed != 0u;
-  const unsigned ball = __ballot_sync(0xFFFFFFFFu, hit);
   const unsigned lane = threadIdx.x & 31u;
-  if (hit) s_queue[qn + __popc(ball & ((1u << lane) - 1u))] = make_uint2(qi, packed);
-  qn += __popc(ball);
-  if (qn >= 32) {
-    __syncwarp();
-    drain_queue<PINV>(s_queue, qn, g, lut, lr, L, C, s_coarse);
-    __syncwarp();
-    qn = 0;
+  const unsigned lt = (1u << lane) - 1u;
+  unsigned ball;
+  while ((ball = __ballot_sync(0xFFFFFFFFu, d != 0u)) != 0u) {
+    if (d) {
+      const unsigned bit = (unsigned)__ffs(d) - 1u;
+      d &= d - 1u;
+      s_queue[qn + __popc(ball & lt)] = make_uint2(qi, 2u * (7u - (bit >> 1)) + (bit & 1u));
+    }
+    qn += __popc(ball);
+    if (qn >= 32) {
+      __syncwarp();
+      drain_pixels<PINV>(s_queue, 32, g, lut, lr, L, C, s_coarse);
+      // the rest (fewer than 32) moves to the front
+      const bool mv = lane + 32u < (unsigned)qn;
+      uint2 rest = make_uint2(0u, 0u);
+      if (mv) rest = s_queue[lane + 32u];
+      __syncwarp();
+      if (mv) s_queue[lane] = rest;
+      __syncwarp();
+      qn -= 32;
+    }
   }
 }
 
@@ -447,7 +455,7 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_window(WindowArgs a) {
   }
   if (qn > 0) {
     __syncwarp();
-    drain_queue<PINV>(s_queue, qn, g, lut, lr, L, C, s_coarse);
+    drain_pixels<PINV>(s_queue, qn, g, lut, lr, L, C, s_coarse);
   }
   // per-thread counts are exact in FP32 (fewer than 2^24 pixels per thread).
   // A thread's below counts can be negative (a tissue chunk's white pixels

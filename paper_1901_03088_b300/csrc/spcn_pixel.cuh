@@ -409,8 +409,8 @@ __device__ __forceinline__ float chunk_nonwhite(const unsigned (&w)[12], const W
   return (float)(kChunk - __popc(x & 0xF0F0F0F0u));
 }
 
-constexpr int kWarpQueue = 64;    // queued chunks per warp; drained once 32 are waiting, so the
-                                  // re-read chunks are recent enough to still be in L2
+constexpr int kWarpQueue = 64;    // queue entries per warp; drained as soon as 32 are waiting, so
+                                  // the re-read pixels are recent enough to still be in L2
 
 // ------------------------------------------------------------ radix fallback
 struct ImageSource {
