@@ -22,7 +22,9 @@
 // Window.  Tiles of one slide share the slide's statistics, but each tile's
 // own P99 differs from the slide's by up to about +-25% (tissue content varies
 // from tile to tile), so a narrow two-sided window around the hint misses
-// often.  The window here is open-ended: [kOpenLow * hint, +inf).  Only ranks
+// often.  The window here is open-ended: [lo, +inf), where lo comes from a
+// pilot sample of the tile itself (k_batch_pilot, launched before the batch
+// kernel), or is kOpenLow * hint when the sample is too small.  Only ranks
 // whose density lies below the window start (or a list that overflowed)
 // leave a tile to the exact radix select over its pixels, run by the whole
 // grid after the queue, followed by the tile's pass 2.
@@ -65,9 +67,11 @@ struct BatchTile {
   Geometry g;
   unsigned model;          // index of the tile's table
   unsigned n_items1;       // pass-1 items of the tile
-  unsigned lo[2];          // window start key per stain (keys >= lo are listed)
+  unsigned lo[2];          // window start key per stain (keys >= lo are listed); set by the pilot
   unsigned win[2];         // 0: no window (no hint): the stain takes the exact fallback
   float nk[2], lk[2];      // exact [h~ < lo] test (nk = 0, lk = 1 without a window)
+  unsigned hlo[2], hwin[2];   // the same from the hint alone (kOpenLow * hint)
+  float hnk[2], hlk[2];
   unsigned* keys;          // stain-0 key list; stain 1 at keys + list_cap
   u64 list_cap;            // keys per stain
 };
@@ -408,6 +412,170 @@ __device__ void batch_select(const BatchArgs& a, unsigned tile, unsigned* s_hist
     s->all_resolved = all;
     __threadfence();
     st_release_s32(&S->ready, all ? 1 : 2);
+  }
+}
+
+// ------------------------------------------------------------ window pilot
+// Before the batch kernel, every tile's window start is set from a sample of
+// the tile itself: one chunk from each of kPilotChunks equal strata of the
+// tile's chunk range (every chunk of a smaller tile), the keys of their
+// non-white pixels, and the key at the sample quantile q = p - delta, with
+// p = pct / 100 and delta = 4 sqrt(p (1 - p) / u), u = the sampled chunks that
+// hold a non-white pixel (pixels of one chunk are not independent, so chunks
+// are the units).  The tile's own percentile lies at or above that key
+// unless the sample is off by four standard deviations; a rank below the
+// window start leaves the tile to the exact fallback, so the start changes
+// the speed, never the result.  A stain without a hint keeps no window (the
+// exact fallback); a sample with fewer than kPilotMinUnits tissue chunks
+// keeps the hint's window.  Two 11-bit digits of the key (bits 31-21, then
+// 20-10) are selected in shared memory; the start is the key with the low
+// ten bits cleared, at or below the sample's key.
+constexpr int kPilotChunks = 1024;
+constexpr int kPilotMinUnits = 64;
+constexpr int kPilotThreads = 512;
+constexpr int kPilotBits = 11;
+constexpr int kPilotBins = 1 << kPilotBits;
+
+struct PilotArgs {
+  BatchTile* tiles;
+  const Model* models;
+  unsigned n_tiles;
+  unsigned thr;   // white threshold
+  double pct;
+};
+
+// The H-step of one pixel with the table read from global memory: the
+// arithmetic of solve_one, so the same keys.
+__device__ __forceinline__ void solve_global(const float2* proj, unsigned r, unsigned g,
+                                             unsigned b, const Lasso& L, float& h1, float& h2) {
+  const float2 eR = __ldg(proj + r), eG = __ldg(proj + 256 + g), eB = __ldg(proj + 512 + b);
+  const float D1 = add_sat(eR.x + eG.x, eB.x);
+  const float D2 = add_sat(eR.y + eG.y, eB.y);
+  const float t1 = mul_sat(L.kappa, fmaf(L.nrho1, D2, D1));
+  const float t2 = mul_sat(L.kappa, fmaf(L.nrho2, D1, D2));
+  h1 = fminf(D1, t1);
+  h2 = fminf(D2, t2);
+}
+
+__device__ __forceinline__ unsigned pilot_hash(unsigned t, unsigned i) {
+  unsigned h = t * 0x9E3779B1u + i * 0x85EBCA77u + 0x27D4EB2Fu;
+  h ^= h >> 15;
+  h *= 0x2C1B3C6Du;
+  h ^= h >> 12;
+  h *= 0x297A2D39u;
+  h ^= h >> 15;
+  return h;
+}
+
+__global__ void __launch_bounds__(kPilotThreads) k_batch_pilot(PilotArgs a) {
+  __shared__ unsigned s_hist[2][kPilotBins];
+  __shared__ u64 s_tmp[33];
+  __shared__ int s_idx;
+  __shared__ u64 s_before;
+  __shared__ unsigned s_b1[2];
+  __shared__ u64 s_r[2];
+  __shared__ int s_use;
+  for (unsigned t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
+    BatchTile* T = a.tiles + t;
+    const Geometry g = T->g;
+    const Model* m = a.models + T->model;
+    const Lasso L = m->lasso;
+    const u64 nch = g.nchunks;
+    const unsigned ms = (unsigned)(nch < (u64)kPilotChunks ? nch : (u64)kPilotChunks);
+    // every non-white pixel of the sample: f(key1, key2)
+    auto visit = [&](auto&& f) -> unsigned {
+      unsigned units = 0u;
+      for (unsigned i = threadIdx.x; i < ms; i += blockDim.x) {
+        u64 q = i;
+        if (nch > (u64)kPilotChunks) {
+          const u64 s0 = (u64)i * nch / kPilotChunks, s1 = (u64)(i + 1) * nch / kPilotChunks;
+          q = s0 + pilot_hash(t, i) % (s1 - s0);
+        }
+        const ChunkPos p = chunk_pos(g, q);
+        unsigned w[12];
+        load_chunk<false>(g, p, w);
+        bool any = false;
+#pragma unroll
+        for (int k = 0; k < kChunk; ++k) {
+          if (k >= p.n) break;
+          const unsigned r = byte_at(w, 3 * k), gg = byte_at(w, 3 * k + 1), b = byte_at(w, 3 * k + 2);
+          if (min(r, min(gg, b)) > a.thr) continue;   // white
+          float h1, h2;
+          solve_global(m->proj, r, gg, b, L, h1, h2);
+          f(__float_as_uint(h1), __float_as_uint(h2));
+          any = true;
+        }
+        units += any ? 1u : 0u;
+      }
+      return units;
+    };
+    for (int i = threadIdx.x; i < 2 * kPilotBins; i += blockDim.x) (&s_hist[0][0])[i] = 0u;
+    __syncthreads();
+    // level 1: bits 31-21 of the keys (densities are >= 0: the sign bit is 0)
+    const unsigned my_units = visit([&](unsigned k1, unsigned k2) {
+      atomicAdd(&s_hist[0][k1 >> 21], 1u);
+      atomicAdd(&s_hist[1][k2 >> 21], 1u);
+    });
+    u64 units = 0;
+    block_excl_scan((u64)my_units, s_tmp, &units);
+    u64 nw = 0;
+    {
+      u64 part = 0;
+      for (int i = threadIdx.x; i < kPilotBins; i += blockDim.x) part += s_hist[0][i];
+      block_excl_scan(part, s_tmp, &nw);
+    }
+    if (threadIdx.x == 0) {
+      const double p = a.pct / 100.0;
+      const double q = p - 4.0 * sqrt(p * (1.0 - p) / (double)(units > 0 ? units : 1));
+      s_use = units >= (u64)kPilotMinUnits && q > 0.0 && nw > 0;
+      const u64 r = s_use ? (u64)floor(q * (double)(nw - 1)) : 0;
+      s_r[0] = s_r[1] = r;
+    }
+    __syncthreads();
+    if (s_use) {
+      for (int j = 0; j < 2; ++j) {
+        smem_find_rank(s_hist[j], kPilotBins, s_r[j], &s_idx, &s_before, s_tmp);
+        if (threadIdx.x == 0) {
+          s_b1[j] = (unsigned)max(s_idx, 0);
+          s_r[j] -= s_idx >= 0 ? s_before : 0;
+        }
+        __syncthreads();
+      }
+      for (int i = threadIdx.x; i < 2 * kPilotBins; i += blockDim.x) (&s_hist[0][0])[i] = 0u;
+      __syncthreads();
+      // level 2: bits 20-10 of the keys in the level-1 bin
+      const unsigned b10 = s_b1[0], b11 = s_b1[1];
+      visit([&](unsigned k1, unsigned k2) {
+        if ((k1 >> 21) == b10) atomicAdd(&s_hist[0][(k1 >> 10) & (kPilotBins - 1)], 1u);
+        if ((k2 >> 21) == b11) atomicAdd(&s_hist[1][(k2 >> 10) & (kPilotBins - 1)], 1u);
+      });
+      __syncthreads();
+      for (int j = 0; j < 2; ++j) {
+        smem_find_rank(s_hist[j], kPilotBins, s_r[j], &s_idx, &s_before, s_tmp);
+        if (threadIdx.x == 0) {
+          const unsigned lo = (s_b1[j] << 21) | ((unsigned)max(s_idx, 0) << 10);
+          if (T->hwin[j] && lo > 0u) {
+            T->lo[j] = lo;
+            T->win[j] = 1u;
+            below_consts(lo, &T->nk[j], &T->lk[j]);
+          } else {
+            T->lo[j] = T->hlo[j];
+            T->win[j] = T->hwin[j];
+            T->nk[j] = T->hnk[j];
+            T->lk[j] = T->hlk[j];
+          }
+        }
+        __syncthreads();
+      }
+    } else if (threadIdx.x == 0) {
+      for (int j = 0; j < 2; ++j) {
+        T->lo[j] = T->hlo[j];
+        T->win[j] = T->hwin[j];
+        T->nk[j] = T->hnk[j];
+        T->lk[j] = T->hlk[j];
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -889,6 +1057,17 @@ static void batch_free(Batch* b) {
 static int batch_launch(Batch* b, cudaStream_t st) {
   Context* c = b->c;
   SPCN_CUDA_TRY(cudaMemsetAsync(b->d_state, 0, b->state_bytes, st));
+  {
+    PilotArgs pa;
+    pa.tiles = b->d_tiles;
+    pa.models = b->models;
+    pa.n_tiles = (unsigned)b->n;
+    pa.thr = b->args.thr;
+    pa.pct = b->args.pct;
+    const int pg = std::min(b->n, 4 * c->num_sms);
+    k_batch_pilot<<<pg, kPilotThreads, 0, st>>>(pa);
+    SPCN_LAUNCH_CHECK(c);
+  }
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   SPCN_CUDA_TRY(cudaStreamIsCapturing(st, &cap));
   cudaLaunchConfig_t lc = {};
@@ -960,6 +1139,10 @@ static int batch_create(Context* c, int n, const spcn_image* tiles, const spcn_s
         T.nk[j] = 0.f;
         T.lk[j] = 1.f;
       }
+      T.hlo[j] = T.lo[j];
+      T.hwin[j] = T.win[j];
+      T.hnk[j] = T.nk[j];
+      T.hlk[j] = T.lk[j];
     }
     // room for 1/8 of the pixels per stain (a window from 0.75 P99 holds a
     // few percent; an overflowing list sends the tile to the exact fallback)

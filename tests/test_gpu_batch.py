@@ -116,15 +116,15 @@ def test_batch_window_hints(spcn, ctx, setup, hint):
     p99, _, fallback = b.results(fallback=True)
     b.close()
     assert_same(outs, ref_outs, p99, ref_p99)
-    # the window starts at 0.75 x hint and is open above: a hint far above the
-    # percentile (or none) needs the exact fallback; a hint far below lists
-    # most pixels, and tiles whose list overflows fall back too.  With the
-    # exact hint only tiny tiles can fall back (the type-7 interpolation can
-    # put 0.75 x P99 above the lower of its two order statistics)
-    if hint in ("none", "far_high"):
+    # no hint: no window, every tile takes the exact fallback.  With a hint,
+    # a tile whose pilot sample holds enough tissue chunks starts its window
+    # at the pilot's low quantile whatever the hint, so tiles of 4096 pixels
+    # or more never fall back; smaller tiles start at 0.75 x hint, and fall
+    # back when that lies above their percentile (far_high)
+    big = [f for f, t in zip(fallback, tiles) if t.shape[0] * t.shape[1] >= 4096]
+    if hint == "none":
         assert all(fallback), fallback
-    elif hint == "exact":
-        big = [f for f, t in zip(fallback, tiles) if t.shape[0] * t.shape[1] >= 4096]
+    else:
         assert not any(big), fallback
 
 
