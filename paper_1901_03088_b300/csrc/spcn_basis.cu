@@ -896,8 +896,9 @@ int launch_estimate_basis(Context* c, const spcn_image* img, const spcn_params* 
     return SPCN_OK;
   }
   // hint_only: the sample only places the search window of an exact
-  // whole-image percentile (a binomial band around the percentile); every
-  // 16th group of four sample pixels suffices
+  // whole-image percentile (a binomial band around the percentile); a
+  // regular sub-sample (at most every 16th group of four sample pixels, at
+  // least 2^18 of them) suffices
   return launch_select_list(c, c->nw, &bs->n_nw, c->model_b, &bs->sel, c->rhist_b,
                             (double)p->stain_pct, st, pinv, hint_only ? 16u : 1u, hint_only,
                             p->sample_mode == SPCN_SAMPLE_PATCHES ? &bs->n_acc : nullptr);

@@ -876,6 +876,7 @@ struct SelectListArgs {
 // (pixels of one patch are not independent).  delta is capped at kBandMax, so
 // that the window stays affordable when the sample says little.
 constexpr double kBandZ = 4.0;
+constexpr u64 kListMinVisited = 1ull << 18;
 constexpr double kBandMax = 0.002;
 __device__ __forceinline__ void band_ranks(u64 n, double pct, double m_eff, u64* r_lo, u64* r_hi) {
   const double p = pct / 100.0;
@@ -899,7 +900,10 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_select_list(SelectListArgs 
   unsigned* s_hist = reinterpret_cast<unsigned*>(s_dyn + kLutSmemBytes);
   const u64 n_all = __ldcg(a.n_dev);
   if (n_all == 0 || a.m->status != SPCN_OK) return;   // uniform: every block returns
-  const unsigned sub = (n_all >> 2) >= 64ull * a.sub ? a.sub : 1u;   // small lists: all of it
+  // a regular sub-sample keeps at least kListMinVisited items (a smaller
+  // list is visited whole), so that the band's binomial width stays small
+  const u64 most = n_all / kListMinVisited;
+  const unsigned sub = (unsigned)(most < 1ull ? 1ull : (most < (u64)a.sub ? most : (u64)a.sub));
   const u64 n = ListSource::visited(n_all, sub);
   u64 rank[kTracks];
   int active[kTracks];
