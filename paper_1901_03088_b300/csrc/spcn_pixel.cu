@@ -29,12 +29,14 @@ struct ModelIn {
 
 // Smallest e with 2^e >= 2 * (largest |d_j| any pixel can reach), so that
 // every table sum s*d_j stays within [-1/2, 1/2].  |d_j| <= |v|/|w_j| +
-// lambda/G_jj with |v_c| <= max(log i0_c, log(255/i0_c)).
-__host__ __device__ inline int table_hexp(const float* W, const float* i0, float lambda) {
+// lambda/G_jj with |v_c| <= max(log i0_c, log(255/i0_c)).  la[c] = log i0_c,
+// lb[c] = log(255/i0_c) (computed apart, so that the device can take the six
+// logarithms in parallel).
+__host__ __device__ inline int table_hexp_from_logs(const float* W, const double* la,
+                                                    const double* lb, float lambda) {
   double vv = 0.0;
   for (int c = 0; c < 3; ++c) {
-    const double a = log((double)i0[c]), b = log(255.0 / (double)i0[c]);
-    const double m = a > b ? a : b;
+    const double m = la[c] > lb[c] ? la[c] : lb[c];
     vv += m * m;
   }
   const double vn = sqrt(vv);
@@ -53,10 +55,28 @@ __host__ __device__ inline int table_hexp(const float* W, const float* i0, float
   return e + 1;
 }
 
+__host__ __device__ inline int table_hexp(const float* W, const float* i0, float lambda) {
+  double la[3], lb[3];
+  for (int c = 0; c < 3; ++c) {
+    la[c] = log((double)i0[c]);
+    lb[c] = log(255.0 / (double)i0[c]);
+  }
+  return table_hexp_from_logs(W, la, lb, lambda);
+}
+
+constexpr int kModelThreads = 128;   // table entries per block of k_build_model
+
 // One thread per (channel, intensity): v = log(i0_c / max(i,1)) in FP64, the
 // plain table and the scaled table of the closed-form H-step (rounded once to
-// FP32, never -0).  Thread 0 derives the closed-form coefficients.
-__global__ void k_build_model(Model* m, ModelIn in, const Model* from) {
+// FP32, never -0).  The per-image scalars that need FP64 logarithms or
+// divisions are spread over the lanes of warp 0 (FP64 latency, not
+// throughput, bounds this kernel): each block takes the six logarithms of
+// the table's scale in parallel, and block 0 derives the closed-form
+// coefficients one per lane.
+__global__ void __launch_bounds__(kModelThreads) k_build_model(Model* m, ModelIn in,
+                                                               const Model* from) {
+  __shared__ double s_lg[6];
+  __shared__ int s_hexp;
   float W[6], i0[3];
   const Model* src = from;
   for (int i = 0; i < 6; ++i) W[i] = src ? src->W[i] : in.W[i];
@@ -69,7 +89,17 @@ __global__ void k_build_model(Model* m, ModelIn in, const Model* from) {
   }
   const double det = g11 * g22 - g12 * g12;
   const bool ok = det > 1e-12 && g11 > 0.0 && g22 > 0.0;
-  const int hexp = in.hexp == kHexpAuto ? table_hexp(W, i0, in.lambda) : in.hexp;
+  int hexp = in.hexp;
+  if (hexp == kHexpAuto) {   // uniform
+    if (threadIdx.x < 6) {
+      const int c = threadIdx.x % 3;
+      s_lg[threadIdx.x] = threadIdx.x < 3 ? log((double)i0[c]) : log(255.0 / (double)i0[c]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) s_hexp = table_hexp_from_logs(W, s_lg, s_lg + 3, in.lambda);
+    __syncthreads();
+    hexp = s_hexp;
+  }
   const double s = ldexp(1.0, -hexp);
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e < kLutEntries) {
@@ -87,7 +117,22 @@ __global__ void k_build_model(Model* m, ModelIn in, const Model* from) {
     m->od[e] = (float)v;
     m->proj[e] = make_float2(p0 + 0.f, p1 + 0.f);   // + 0 turns -0 into +0
   }
-  if (e == 0) {
+  if (blockIdx.x != 0) return;
+  // block 0, warp 0: lanes 0-5 the pass-2 projections pa, lanes 6-7 the
+  // offsets pb, lane 8 the lasso record and the status, lane 9 the basis copy
+  const int l = threadIdx.x;
+  if (l < 6) {
+    const int j = l / 3, c = l % 3;
+    const double gjj = j ? g22 : g11;
+    const double pj = in.pinv ? (j ? ((double)W[3 + c] * g11 - (double)W[c] * g12) / det
+                                   : ((double)W[c] * g22 - (double)W[3 + c] * g12) / det)
+                              : (double)W[3 * j + c] / gjj;
+    m->pa[3 * j + c] = ok ? (float)(s * pj) + 0.f : 0.f;
+  } else if (l < 8) {
+    const int j = l - 6;
+    const double gjj = j ? g22 : g11;
+    m->pb[j] = (ok && !in.pinv) ? (float)(-s * (double)in.lambda / gjj) + 0.f : 0.f;
+  } else if (l == 8) {
     Lasso L;
     L.hexp = hexp;
     L.hscale = (float)ldexp(1.0, hexp);
@@ -102,20 +147,9 @@ __global__ void k_build_model(Model* m, ModelIn in, const Model* from) {
       m->status = SPCN_ERR_DEGENERATE_BASIS;
     }
     m->lasso = L;
-    for (int j = 0; j < 2; ++j) {
-      const double gjj = j ? g22 : g11;
-      for (int c = 0; c < 3; ++c) {
-        const double pj = in.pinv ? (j ? ((double)W[3 + c] * g11 - (double)W[c] * g12) / det
-                                       : ((double)W[c] * g22 - (double)W[3 + c] * g12) / det)
-                                  : (double)W[3 * j + c] / gjj;
-        m->pa[3 * j + c] = ok ? (float)(s * pj) + 0.f : 0.f;
-      }
-      m->pb[j] = (ok && !in.pinv) ? (float)(-s * (double)in.lambda / gjj) + 0.f : 0.f;
-    }
-    if (from != m) {
-      for (int i = 0; i < 6; ++i) m->W[i] = W[i];
-      for (int i = 0; i < 3; ++i) m->i0[i] = i0[i];
-    }
+  } else if (l == 9 && from != m) {
+    for (int i = 0; i < 6; ++i) m->W[i] = W[i];
+    for (int i = 0; i < 3; ++i) m->i0[i] = i0[i];
   }
 }
 
@@ -131,7 +165,7 @@ int launch_build_model(Context* c, Model* m, const float* W, const float* i0, fl
   for (int i = 0; i < 3; ++i) in.i0[i] = i0 ? i0[i] : 1.f;
   in.lambda = lambda;
   in.hexp = (W && i0 && !from_device) ? table_hexp(W, i0, lambda) : kHexpAuto;
-  k_build_model<<<kLutEntries / 32, 32, 0, st>>>(m, in, from_device);   // one log per thread
+  k_build_model<<<kLutEntries / kModelThreads, kModelThreads, 0, st>>>(m, in, from_device);
   SPCN_LAUNCH_CHECK(c);
   return SPCN_OK;
 }
