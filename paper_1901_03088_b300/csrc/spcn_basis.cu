@@ -361,33 +361,20 @@ struct SnmfArgs {
 
 // Reduced sums, in this order: A11 A12 A22 | B[R,0] B[R,1] B[G,0] B[G,1]
 // B[B,0] B[B,1] | sum h1, sum h2 | sum |v|^2.
-// The W update runs on one thread per block between two grid barriers, so
-// its dependent FP64 chain is on the critical path of every iteration; an
-// FP64 division or square root costs an order of magnitude more latency than
-// an FMA on this GPU.  Reciprocals and inverse square roots therefore start
-// from the FP32 instruction and take one Newton step in FP64 (relative error
-// about 1.5 e0^2 for a seed error e0 <= 2^-22, i.e. below 1e-13), with the
-// exact FP64 operation outside the range where the FP32 seed is accurate.
-__device__ __forceinline__ double rcp_nr(double x) {
-  if (!(x > 1e-30 && x < 1e30)) return 1.0 / x;
-  const double e = (double)(1.0f / (float)x);
-  return fma(e, fma(-x, e, 1.0), e);            // e (2 - x e)
-}
-__device__ __forceinline__ double rsqrt_nr(double x) {
-  if (!(x > 1e-30 && x < 1e30)) return 1.0 / sqrt(x);
-  const double r = (double)rsqrtf((float)x);
-  return r * fma(-0.5 * x, r * r, 1.5);         // r (3 - x r^2) / 2
-}
+// The W update runs on one thread per block after the grid barrier, so its
+// dependent chain is on the critical path of every iteration; it runs in
+// FP32 from the FP64 totals (FP64 operations are slow and long in latency on
+// this GPU).
 
 __global__ void __launch_bounds__(kSnmfThreads) k_snmf(SnmfArgs a) {
   __shared__ float s_od[kLutEntries];
-  __shared__ double s_W[6];
+  __shared__ float s_W[6];
   __shared__ double s_tot[kAcc];
   __shared__ float s_coef[12];
   __shared__ double s_red[kSnmfThreads / 32][kAcc];
   __shared__ int s_flag;
   __shared__ double s_obj;
-  __shared__ double s_Wp[6];   // the basis the last H-step used (for the objective)
+  __shared__ float s_Wp[6];    // the basis the last H-step used (for the objective)
   __shared__ int s_have;
   const u64 n = a.bs->n_nw;
   if (n == 0) {
@@ -395,7 +382,7 @@ __global__ void __launch_bounds__(kSnmfThreads) k_snmf(SnmfArgs a) {
     return;   // uniform
   }
   for (int i = threadIdx.x; i < kLutEntries; i += blockDim.x) s_od[i] = a.m->od[i];
-  if (threadIdx.x < 6) s_W[threadIdx.x] = a.bs->W[threadIdx.x];
+  if (threadIdx.x < 6) s_W[threadIdx.x] = (float)a.bs->W[threadIdx.x];
   if (threadIdx.x == 0) { s_flag = 0; s_obj = 0.0; s_have = 0; }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -403,26 +390,30 @@ __global__ void __launch_bounds__(kSnmfThreads) k_snmf(SnmfArgs a) {
   unsigned target = 0;
   int it;
   // closed-form H-step coefficients of the current basis (thread 0); -1 in
-  // s_flag when the basis is degenerate
+  // s_flag when the basis is degenerate.  FP32 throughout (the coefficients
+  // are FP32 anyway); the determinant g11 g22 - g12^2 takes the rounding
+  // error of g12^2 back with an FMA, so it stays accurate when the two
+  // columns are nearly parallel (exactly 0 for equal columns)
   auto set_coef = [&]() {
-    double g11 = 0, g22 = 0, g12 = 0;
+    float g11 = 0.f, g22 = 0.f, g12 = 0.f;
     for (int c = 0; c < 3; ++c) {
-      g11 += s_W[c] * s_W[c];
-      g22 += s_W[3 + c] * s_W[3 + c];
-      g12 += s_W[c] * s_W[3 + c];
+      g11 = fmaf(s_W[c], s_W[c], g11);
+      g22 = fmaf(s_W[3 + c], s_W[3 + c], g22);
+      g12 = fmaf(s_W[c], s_W[3 + c], g12);
     }
-    const double det = g11 * g22 - g12 * g12;
-    if (!(det > 1e-12)) {
+    const float q = g12 * g12;
+    const float det = fmaf(g11, g22, -q) - fmaf(g12, g12, -q);
+    if (!(det > 1e-12f)) {
       s_flag = -1;
     } else {
-      const double id = rcp_nr(det);
-      for (int i = 0; i < 6; ++i) s_coef[i] = (float)s_W[i];
-      s_coef[6] = (float)(g22 * id);
-      s_coef[7] = (float)(-g12 * id);
-      s_coef[8] = (float)(-g12 * id);
-      s_coef[9] = (float)(g11 * id);
-      s_coef[10] = (float)rcp_nr(g11);
-      s_coef[11] = (float)rcp_nr(g22);
+      const float id = 1.f / det;
+      for (int i = 0; i < 6; ++i) s_coef[i] = s_W[i];
+      s_coef[6] = g22 * id;
+      s_coef[7] = -g12 * id;
+      s_coef[8] = -g12 * id;
+      s_coef[9] = g11 * id;
+      s_coef[10] = 1.f / g11;
+      s_coef[11] = 1.f / g22;
     }
   };
   if (threadIdx.x == 0) set_coef();
@@ -556,32 +547,40 @@ __global__ void __launch_bounds__(kSnmfThreads) k_snmf(SnmfArgs a) {
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      const double A[2][2] = {{s_tot[0], s_tot[1]}, {s_tot[1], s_tot[2]}};
-      double B[3][2];
-      for (int c = 0; c < 3; ++c) { B[c][0] = s_tot[3 + 2 * c]; B[c][1] = s_tot[4 + 2 * c]; }
-      double W[3][2], Wp[3][2];
+      // The column update in FP32 from the FP64 totals: at the totals'
+      // magnitude its rounding moves W by about 1e-7, far inside the
+      // convergence tolerance and the 1e-5 agreement with the FP64 oracle,
+      // while this serial step runs on one thread of every block and FP64
+      // operations are slow and long in latency on this GPU.
+      const float A[2][2] = {{(float)s_tot[0], (float)s_tot[1]}, {(float)s_tot[1], (float)s_tot[2]}};
+      float B[3][2];
+      for (int c = 0; c < 3; ++c) {
+        B[c][0] = (float)s_tot[3 + 2 * c];
+        B[c][1] = (float)s_tot[4 + 2 * c];
+      }
+      float W[3][2], Wp[3][2];
       for (int c = 0; c < 3; ++c) { W[c][0] = Wp[c][0] = s_W[c]; W[c][1] = Wp[c][1] = s_W[3 + c]; }
       for (int i = 0; i < 6; ++i) s_Wp[i] = s_W[i];   // objective taken at the end
       s_have = 1;
-      const double iA[2] = {rcp_nr(A[0][0]), rcp_nr(A[1][1])};
       int flag = 0;
       for (int j = 0; j < 2 && flag == 0; ++j) {
-        if (!(A[j][j] > 0.0)) continue;
-        double u[3], nu = 0.0;
+        if (!(A[j][j] > 0.f)) continue;
+        const float iA = 1.f / A[j][j];
+        float u[3], nu = 0.f;
         for (int c = 0; c < 3; ++c) {
-          u[c] = W[c][j] + (B[c][j] - (W[c][0] * A[0][j] + W[c][1] * A[1][j])) * iA[j];
-          u[c] = u[c] > 0.0 ? u[c] : 0.0;
-          nu += u[c] * u[c];
+          u[c] = fmaf(B[c][j] - fmaf(W[c][0], A[0][j], W[c][1] * A[1][j]), iA, W[c][j]);
+          u[c] = u[c] > 0.f ? u[c] : 0.f;
+          nu = fmaf(u[c], u[c], nu);
         }
-        if (!(nu > 0.0)) { flag = -1; break; }
-        const double r = rsqrt_nr(nu);
+        if (!(nu > 0.f)) { flag = -1; break; }
+        const float r = 1.f / sqrtf(nu);
         for (int c = 0; c < 3; ++c) W[c][j] = u[c] * r;
       }
-      double dmax = 0.0;
+      float dmax = 0.f;
       for (int c = 0; c < 3; ++c)
-        for (int j = 0; j < 2; ++j) dmax = fmax(dmax, fabs(W[c][j] - Wp[c][j]));
+        for (int j = 0; j < 2; ++j) dmax = fmaxf(dmax, fabsf(W[c][j] - Wp[c][j]));
       for (int c = 0; c < 3; ++c) { s_W[c] = W[c][0]; s_W[3 + c] = W[c][1]; }
-      if (flag == 0 && dmax < a.tol) flag = 1;
+      if (flag == 0 && (double)dmax < a.tol) flag = 1;
       s_flag = flag;
       if (flag == 0) set_coef();   // the next iteration's coefficients
     }
