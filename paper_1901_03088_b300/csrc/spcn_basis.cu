@@ -348,7 +348,7 @@ struct SnmfArgs {
   const uint32_t* nw;
   BasisState* bs;
   Model* m;
-  double* partials;   // [2][gridDim.x][kAcc]
+  unsigned long long* tot;   // [3][kAcc] fixed-point totals, zeroed before the launch
   unsigned* bar;
   int* abort;
   int* err;
@@ -371,7 +371,8 @@ __global__ void __launch_bounds__(kSnmfThreads) k_snmf(SnmfArgs a) {
   __shared__ float s_W[6];
   __shared__ double s_tot[kAcc];
   __shared__ float s_coef[12];
-  __shared__ double s_red[kSnmfThreads / 32][kAcc];
+  __shared__ float s_red[kSnmfThreads / 32][kAcc];
+  __shared__ int s_shift;      // fixed-point scale of this iteration's sums
   __shared__ int s_flag;
   __shared__ double s_obj;
   __shared__ float s_Wp[6];    // the basis the last H-step used (for the objective)
@@ -414,6 +415,18 @@ __global__ void __launch_bounds__(kSnmfThreads) k_snmf(SnmfArgs a) {
       s_coef[9] = g11 * id;
       s_coef[10] = 1.f / g11;
       s_coef[11] = 1.f / g22;
+      // per-pixel bound of the summands: |v_c| <= log 256, and an H-step
+      // density is at most (1/g_jj) log 256 sum_c w_cj (W >= 0)
+      const float vmax = 5.5452f;
+      float hb = 0.f;
+      for (int j = 0; j < 2; ++j) {
+        const float l1 = fabsf(s_W[3 * j]) + fabsf(s_W[3 * j + 1]) + fabsf(s_W[3 * j + 2]);
+        hb = fmaxf(hb, s_coef[10 + j] * vmax * l1);
+      }
+      const double hd = hb, per = fmax(fmax(hd * hd, vmax * hd), fmax(hd, 3.0 * vmax * vmax));
+      int e = 0;
+      frexp((double)n * per + 1.0, &e);   // every |total| < 2^e
+      s_shift = 61 - e;
     }
   };
   if (threadIdx.x == 0) set_coef();
@@ -502,48 +515,35 @@ __global__ void __launch_bounds__(kSnmfThreads) k_snmf(SnmfArgs a) {
     for (int i = 0; i < kAcc; ++i) acc[i] = lo_of(pacc[i]) + hi_of(pacc[i]);
     for (u64 i = (n4 << 2) + (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gstride)
       step(__ldg(a.nw + i));
-    // warp sums in FP32 (a fixed shuffle tree: deterministic), FP64 from the
-    // warp totals on; FP64 arithmetic is a small fraction of FP32 throughput
-    // on this GPU, so the per-thread work stays in FP32
+    // warp sums in FP32 (a fixed shuffle tree), then fixed point: each warp
+    // sum times 2^s_shift rounded to a 64-bit integer, added exactly over the
+    // block and, with one atomic per sum and block, over the grid.  Integer
+    // sums do not depend on the order, so every block reads the same totals
+    // and reruns are bitwise equal; s_shift leaves the largest total the
+    // basis allows below 2^61, and the rounding (2^-s_shift per warp) is far
+    // below the FP32 warp sums' own
 #pragma unroll
     for (int i = 0; i < kAcc; ++i) {
       float x = acc[i];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-      if (lane == 0) s_red[warp][i] = (double)x;
+      if (lane == 0) s_red[warp][i] = x;
     }
     __syncthreads();
-    double* part = a.partials + (size_t)(it & 1) * gridDim.x * kAcc;
-    if (threadIdx.x < kAcc) {   // a fixed pairwise tree over the warps
-      double x[kSnmfThreads / 32];
+    unsigned long long* tot = a.tot + (size_t)(it % 3) * kAcc;
+    if (threadIdx.x < kAcc) {
+      const double sc = ldexp(1.0, s_shift);
+      long long v = 0;
 #pragma unroll
-      for (int w = 0; w < kSnmfThreads / 32; ++w) x[w] = s_red[w][threadIdx.x];
-#pragma unroll
-      for (int h = kSnmfThreads / 64; h > 0; h >>= 1)
-#pragma unroll
-        for (int w = 0; w < h; ++w) x[w] += x[w + h];
-      part[(size_t)blockIdx.x * kAcc + threadIdx.x] = x[0];
+      for (int w = 0; w < kSnmfThreads / 32; ++w) v += __double2ll_rn((double)s_red[w][threadIdx.x] * sc);
+      atomicAdd(tot + threadIdx.x, (unsigned long long)v);
     }
     target += gridDim.x;
     if (!grid_barrier(a.bar, target, a.abort, a.err, a.timeout_ns)) return;
-    // cross-block sums: warp w < kAcc adds accumulator w over all blocks in a
-    // fixed order (lane-strided partial sums, then a fixed shuffle tree), so
-    // every block gets bit-identical totals and reruns are deterministic
-    if (warp < kAcc) {
-      double x = 0.0;
-      for (unsigned b0 = lane; b0 < gridDim.x; b0 += 32u * 8u) {   // eight loads in flight
-        double v[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const unsigned b = b0 + 32u * k;
-          v[k] = b < gridDim.x ? __ldcg(part + (size_t)b * kAcc + warp) : 0.0;
-        }
-#pragma unroll
-        for (int k = 0; k < 8; ++k) x += v[k];
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-      if (lane == 0) s_tot[warp] = x;
+    if (threadIdx.x < kAcc) {
+      s_tot[threadIdx.x] = (double)(long long)__ldcg(tot + threadIdx.x) * ldexp(1.0, -s_shift);
+      // the buffer of iteration it + 2, read by every block before this barrier
+      if (blockIdx.x == 0) a.tot[(size_t)((it + 2) % 3) * kAcc + threadIdx.x] = 0ull;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -864,7 +864,8 @@ int launch_estimate_basis(Context* c, const spcn_image* img, const spcn_params* 
   sa.nw = c->nw;
   sa.bs = bs;
   sa.m = c->model_b;
-  sa.partials = c->partials;
+  sa.tot = reinterpret_cast<unsigned long long*>(c->partials);
+  SPCN_CUDA_TRY(cudaMemsetAsync(sa.tot, 0, sizeof(unsigned long long) * 3 * kAcc, st));
   sa.bar = &c->sel->barrier;
   sa.abort = &c->sel->abort;
   sa.err = c->err;
