@@ -479,8 +479,8 @@ __device__ bool radix_select(const Src& src, const char* lut, const Lasso& L, Se
   __shared__ unsigned s_prefix[kTracks];
   __shared__ u64 s_r[kTracks];
   __shared__ int s_act[kTracks];
-  __shared__ int s_idx;
-  __shared__ u64 s_before;
+  __shared__ int s_idx4[kTracks];
+  __shared__ u64 s_before4[kTracks];
   __shared__ u64 s_tmp[33];
   if (threadIdx.x == 0) {
     for (int t = 0; t < kTracks; ++t) {
@@ -532,20 +532,26 @@ __device__ bool radix_select(const Src& src, const char* lut, const Lasso& L, Se
       if (s_hist[i]) atomicAdd(gh + i, (u64)s_hist[i]);
     target += gridDim.x;
     if (!grid_barrier(bar, target, &s->abort, err, timeout_ns)) return false;
-    for (int t = 0; t < kTracks; ++t) {
-      if (!s_act[t]) continue;
-      block_find_rank(gh + (size_t)own[t] * kRadixBins, kRadixBins, s_r[t], &s_idx, &s_before, s_tmp);
-      if (threadIdx.x == 0) {
-        if (s_idx < 0) {         // fewer pixels than the rank: cannot happen
+    {   // the digit of every active track at once
+      const u64* const hs[kTracks] = {gh + (size_t)own[0] * kRadixBins, gh + (size_t)own[1] * kRadixBins,
+                                      gh + (size_t)own[2] * kRadixBins, gh + (size_t)own[3] * kRadixBins};
+      const u64 rr[kTracks] = {s_r[0], s_r[1], s_r[2], s_r[3]};
+      const int aa[kTracks] = {s_act[0], s_act[1], s_act[2], s_act[3]};
+      block_find_rank4(hs, kRadixBins, rr, aa, s_idx4, s_before4, s_tmp);
+    }
+    if (threadIdx.x == 0) {
+      for (int t = 0; t < kTracks; ++t) {
+        if (!s_act[t]) continue;
+        if (s_idx4[t] < 0) {     // fewer pixels than the rank: cannot happen
           record_error(err, SPCN_ERR_CUDA);
           s_act[t] = 0;
         } else {
-          s_prefix[t] |= (unsigned)s_idx << shift;
-          s_r[t] -= s_before;
+          s_prefix[t] |= (unsigned)s_idx4[t] << shift;
+          s_r[t] -= s_before4[t];
         }
       }
-      __syncthreads();
     }
+    __syncthreads();
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     for (int t = 0; t < kTracks; ++t)
