@@ -411,20 +411,29 @@ __device__ __forceinline__ void block_find_rank(const u64* cnt, int n, u64 r, in
 }
 
 // block_find_rank for the four tracks at once: a quarter of the block per
-// track (blockDim.x a multiple of 128), histogram cnt[t] of n bins and rank
-// r[t] for the tracks with act[t] set.
-// s_idx[t] = -1 if the track's total is <= r[t].  Whole block must call.
+// track (blockDim.x a multiple of 128), histogram cnt[t] of n <= 16 *
+// blockDim.x / 4 bins and rank r[t] for the tracks with act[t] set.  Each
+// thread's bins are loaded once, all in flight together, and kept in
+// registers for the search.  s_idx[t] = -1 if the track's total is <= r[t].
+// Whole block must call.
+constexpr int kFindPer = 16;
 __device__ __forceinline__ void block_find_rank4(const u64* const (&cnt)[4], int n,
                                                  const u64 (&r)[4], const int (&act)[4],
                                                  int* s_idx, u64* s_before, u64* s_wsum) {
   const int group = (int)blockDim.x >> 2;
   const int t = (int)threadIdx.x / group, sub = (int)threadIdx.x % group;
   const int per = (n + group - 1) / group;
-  const int beg = min(n, sub * per), end = min(n, beg + per);
+  const int beg = sub * per;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  u64 v[kFindPer];
   u64 local = 0;
-  if (act[t])
-    for (int i = beg; i < end; ++i) local += __ldcg(cnt[t] + i);
+#pragma unroll
+  for (int k = 0; k < kFindPer; ++k) {
+    const int i = beg + k;
+    v[k] = (act[t] && k < per && i < n) ? __ldcg(cnt[t] + i) : 0ull;
+  }
+#pragma unroll
+  for (int k = 0; k < kFindPer; ++k) local += v[k];
   const u64 incl = warp_incl_scan(local);
   if (sub == 0) s_idx[t] = -1;
   if (lane == 31) s_wsum[warp] = incl;
@@ -433,11 +442,15 @@ __device__ __forceinline__ void block_find_rank4(const u64* const (&cnt)[4], int
   for (int w = t * (group >> 5); w < warp; ++w) excl += s_wsum[w];
   if (act[t] && local > 0 && excl <= r[t] && r[t] < excl + local) {
     u64 c = excl;
-    for (int i = beg; i < end; ++i) {
-      const u64 x = __ldcg(cnt[t] + i);
-      if (r[t] < c + x) { s_idx[t] = i; s_before[t] = c; break; }
-      c += x;
+    int found = -1;
+    u64 bef = 0;
+#pragma unroll
+    for (int k = 0; k < kFindPer; ++k) {
+      if (found < 0 && r[t] < c + v[k]) { found = beg + k; bef = c; }
+      c += v[k];
     }
+    s_idx[t] = found;
+    s_before[t] = bef;
   }
   __syncthreads();
 }
