@@ -423,10 +423,10 @@ __global__ void __launch_bounds__(kSnmfThreads) k_snmf(SnmfArgs a) {
         const float l1 = fabsf(s_W[3 * j]) + fabsf(s_W[3 * j + 1]) + fabsf(s_W[3 * j + 2]);
         hb = fmaxf(hb, s_coef[10 + j] * vmax * l1);
       }
-      const double hd = hb, per = fmax(fmax(hd * hd, vmax * hd), fmax(hd, 3.0 * vmax * vmax));
+      const float per = fmaxf(fmaxf(hb * hb, vmax * hb), fmaxf(hb, 3.f * vmax * vmax));
       int e = 0;
-      frexp((double)n * per + 1.0, &e);   // every |total| < 2^e
-      s_shift = 61 - e;
+      frexpf((float)n * per * 1.0001f + 1.f, &e);   // every |total| < 2^e
+      s_shift = max(61 - e, -120);   // 2^s_shift stays a normal FP32 number
     }
   };
   if (threadIdx.x == 0) set_coef();
@@ -532,10 +532,11 @@ __global__ void __launch_bounds__(kSnmfThreads) k_snmf(SnmfArgs a) {
     __syncthreads();
     unsigned long long* tot = a.tot + (size_t)(it % 3) * kAcc;
     if (threadIdx.x < kAcc) {
-      const double sc = ldexp(1.0, s_shift);
+      // x 2^s is exact in FP32 (a power of two), then rounded to an integer
+      const float sc = ldexpf(1.f, s_shift);
       long long v = 0;
 #pragma unroll
-      for (int w = 0; w < kSnmfThreads / 32; ++w) v += __double2ll_rn((double)s_red[w][threadIdx.x] * sc);
+      for (int w = 0; w < kSnmfThreads / 32; ++w) v += __float2ll_rn(s_red[w][threadIdx.x] * sc);
       atomicAdd(tot + threadIdx.x, (unsigned long long)v);
     }
     target += gridDim.x;
