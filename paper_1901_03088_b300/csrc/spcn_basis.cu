@@ -5,9 +5,9 @@
 //   compaction     stable split of the sample into non-white and bright lists;
 //   i0             80th percentile per channel of <= 100000 bright pixels;
 //   sparse NMF     one cooperative persistent kernel: per-pixel closed-form
-//                  H-step, block-reduced Gram sums, a grid barrier, and the
-//                  exact column update of W computed identically by every
-//                  block in FP64;
+//                  H-step, Gram sums added exactly in 64-bit fixed point, a
+//                  grid barrier, and the exact column update of W computed
+//                  identically by every block;
 //   ordering       hematoxylin = larger OD(red) - OD(blue);
 //   sample P99     exact radix select over the non-white sample.
 #include <math.h>
@@ -267,19 +267,11 @@ struct I0Args {
   int cap;
   double pct;
   int fixed255;       // §2.1 Eq. 1's original i0 = 255 instead of the estimate
+  double w0[6];       // the initial basis: column-normalised Ruifrok-Johnston H&E vectors
 };
 
 constexpr int kI0Threads = 256;
 constexpr int kI0Blocks = 64;
-
-__device__ double hist_rank_value(const unsigned* h, u64 rank) {
-  u64 c = 0;
-  for (int v = 0; v < 256; ++v) {
-    c += h[v];
-    if (rank < c) return (double)v;
-  }
-  return 255.0;
-}
 
 // Per channel, the type-7 percentile of every ceil(n/cap)-th bright sample
 // pixel (sample order), from 256-bin histograms (exact for 8-bit values).
@@ -314,31 +306,57 @@ __global__ void __launch_bounds__(kI0Threads) k_i0(I0Args a) {
   __syncthreads();
   if (!s_last) return;
   __threadfence();
+  // the last block: thread v holds bin v of each channel; a block scan gives
+  // every bin's cumulative count, and the thread whose bin holds rank k (and
+  // k + 1) of a channel records its value
+  __shared__ unsigned s_wt[3][kI0Threads / 32];
+  __shared__ int s_rv[3][2];
+  const int v = threadIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const double pos = kept > 0 ? (double)(kept - 1) * (a.pct / 100.0) : 0.0;
+  u64 k = (u64)floor(pos);
+  if (kept > 0 && k > kept - 1) k = kept - 1;
+  unsigned cnt[3], incl[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    cnt[c] = __ldcg(a.hist + 256 * c + v);
+    unsigned x = cnt[c];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x += y;
+    }
+    incl[c] = x;
+    if (lane == 31) s_wt[c][warp] = x;
+  }
+  if (v < 6) s_rv[v / 2][v % 2] = 255;
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    u64 before = 0;
+    for (int w = 0; w < warp; ++w) before += s_wt[c][w];
+    const u64 hi = before + incl[c], lo = hi - cnt[c];
+    for (int j = 0; j < 2; ++j) {
+      const u64 r = k + (u64)j;
+      if (cnt[c] > 0 && lo <= r && r < hi) s_rv[c][j] = v;
+    }
+  }
+  __syncthreads();
   if (threadIdx.x < 3) {
     const int c = threadIdx.x;
-    unsigned h[256];
-    for (int v = 0; v < 256; ++v) h[v] = __ldcg(a.hist + 256 * c + v);
     double val = 255.0;
     if (kept > 0 && !a.fixed255) {
-      const double pos = (double)(kept - 1) * (a.pct / 100.0);
-      u64 k = (u64)floor(pos);
-      if (k > kept - 1) k = kept - 1;
       const double t = pos - (double)k;
-      const double lo = hist_rank_value(h, k);
-      const double hi = (k + 1 < kept) ? hist_rank_value(h, k + 1) : lo;
+      const double lo = (double)s_rv[c][0];
+      const double hi = (k + 1 < kept) ? (double)s_rv[c][1] : lo;
       val = (k + 1 < kept) ? __dadd_rn(lo, __dmul_rn(t, __dsub_rn(hi, lo))) : lo;
     }
     a.m->i0[c] = (float)val;
   }
   if (threadIdx.x == 0) {
-    const double h[3] = {0.650, 0.704, 0.286}, e[3] = {0.072, 0.990, 0.105};
-    const double nh = sqrt(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
-    const double ne = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
-    for (int c = 0; c < 3; ++c) {
-      a.bs->W[c] = h[c] / nh;
-      a.bs->W[3 + c] = e[c] / ne;
-      a.m->W[c] = (float)(h[c] / nh);
-      a.m->W[3 + c] = (float)(e[c] / ne);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {   // static indices: the parameter stays in parameter space
+      a.bs->W[i] = a.w0[i];
+      a.m->W[i] = (float)a.w0[i];
     }
   }
 }
@@ -855,7 +873,16 @@ int launch_estimate_basis(Context* c, const spcn_image* img, const spcn_params* 
   SPCN_LAUNCH_CHECK(c);
   SPCN_CUDA_TRY(cudaMemsetAsync(bs->i0_hist, 0, sizeof(bs->i0_hist) + sizeof(bs->i0_ticket), st));
   I0Args ia{c->br, bs, c->model_b, bs->i0_hist, &bs->i0_ticket, p->i0_max_samples,
-            (double)p->i0_pct, (p->flags & SPCN_FLAG_I0_255) ? 1 : 0};
+            (double)p->i0_pct, (p->flags & SPCN_FLAG_I0_255) ? 1 : 0, {}};
+  {   // §3.1: the Ruifrok-Johnston H&E vectors, each normalised to unit length
+    const double h[3] = {0.650, 0.704, 0.286}, e[3] = {0.072, 0.990, 0.105};
+    const double nh = sqrt(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
+    const double ne = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+    for (int c = 0; c < 3; ++c) {
+      ia.w0[c] = h[c] / nh;
+      ia.w0[3 + c] = e[c] / ne;
+    }
+  }
   k_i0<<<kI0Blocks, kI0Threads, 0, st>>>(ia);
   SPCN_LAUNCH_CHECK(c);
   rc = launch_build_model(c, c->model_b, nullptr, nullptr, p->lambda, c->model_b, st);
