@@ -411,43 +411,53 @@ __device__ __forceinline__ void block_find_rank(const u64* cnt, int n, u64 r, in
 }
 
 // block_find_rank for the four tracks at once: a quarter of the block per
-// track (blockDim.x a multiple of 128), histogram cnt[t] of n <= 16 *
-// blockDim.x / 4 bins and rank r[t] for the tracks with act[t] set.  Each
-// thread's bins are loaded once, all in flight together, and kept in
-// registers for the search.  s_idx[t] = -1 if the track's total is <= r[t].
-// Whole block must call.
-constexpr int kFindPer = 16;
+// track (blockDim.x a multiple of 128), histogram cnt[t] of n bins and rank
+// r[t] for the tracks with act[t] set.  Each thread's bins (at most
+// kFindPer of them are kept in registers for the search; more are read
+// again) are loaded once, all in flight together.  s_idx[t] = -1 if the
+// track's total is <= r[t].  Whole block must call.
+constexpr int kFindPer = 8;
 __device__ __forceinline__ void block_find_rank4(const u64* const (&cnt)[4], int n,
                                                  const u64 (&r)[4], const int (&act)[4],
                                                  int* s_idx, u64* s_before, u64* s_wsum) {
   const int group = (int)blockDim.x >> 2;
   const int t = (int)threadIdx.x / group, sub = (int)threadIdx.x % group;
   const int per = (n + group - 1) / group;
-  const int beg = sub * per;
+  const int beg = min(n, sub * per), end = min(n, beg + per);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // this thread's track, by selects (an array indexed at run time would live
+  // in local memory)
+  const u64* ct = t == 0 ? cnt[0] : (t == 1 ? cnt[1] : (t == 2 ? cnt[2] : cnt[3]));
+  const u64 rt = t == 0 ? r[0] : (t == 1 ? r[1] : (t == 2 ? r[2] : r[3]));
+  const int at = t == 0 ? act[0] : (t == 1 ? act[1] : (t == 2 ? act[2] : act[3]));
   u64 v[kFindPer];
   u64 local = 0;
 #pragma unroll
   for (int k = 0; k < kFindPer; ++k) {
-    const int i = beg + k;
-    v[k] = (act[t] && k < per && i < n) ? __ldcg(cnt[t] + i) : 0ull;
+    v[k] = (at && beg + k < end) ? __ldcg(ct + beg + k) : 0ull;
+    local += v[k];
   }
-#pragma unroll
-  for (int k = 0; k < kFindPer; ++k) local += v[k];
+  if (at)
+    for (int i = beg + kFindPer; i < end; ++i) local += __ldcg(ct + i);
   const u64 incl = warp_incl_scan(local);
   if (sub == 0) s_idx[t] = -1;
   if (lane == 31) s_wsum[warp] = incl;
   __syncthreads();
   u64 excl = incl - local;
   for (int w = t * (group >> 5); w < warp; ++w) excl += s_wsum[w];
-  if (act[t] && local > 0 && excl <= r[t] && r[t] < excl + local) {
+  if (at && local > 0 && excl <= rt && rt < excl + local) {
     u64 c = excl;
     int found = -1;
     u64 bef = 0;
 #pragma unroll
     for (int k = 0; k < kFindPer; ++k) {
-      if (found < 0 && r[t] < c + v[k]) { found = beg + k; bef = c; }
+      if (found < 0 && rt < c + v[k]) { found = beg + k; bef = c; }
       c += v[k];
+    }
+    for (int i = beg + kFindPer; found < 0 && i < end; ++i) {
+      const u64 x = __ldcg(ct + i);
+      if (rt < c + x) { found = i; bef = c; }
+      c += x;
     }
     s_idx[t] = found;
     s_before[t] = bef;
