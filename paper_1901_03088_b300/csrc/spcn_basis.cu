@@ -442,8 +442,9 @@ __global__ void __launch_bounds__(kSnmfThreads) k_snmf(SnmfArgs a) {
         hb = fmaxf(hb, s_coef[10 + j] * vmax * l1);
       }
       const float per = fmaxf(fmaxf(hb * hb, vmax * hb), fmaxf(hb, 3.f * vmax * vmax));
-      int e = 0;
-      frexpf((float)n * per * 1.0001f + 1.f, &e);   // every |total| < 2^e
+      const float bound = (float)n * per * 1.0001f + 1.f;
+      int e = 128;                   // a bound beyond FP32 (a near-singular basis)
+      if (bound < 3.0e38f) frexpf(bound, &e);   // every |total| < 2^e
       s_shift = max(61 - e, -120);   // 2^s_shift stays a normal FP32 number
     }
   };
