@@ -395,12 +395,15 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_window(WindowArgs a) {
   // Counts of a full, not all-white chunk; true when it needs the window
   // arithmetic (not provably below both window starts).
   auto classify = [&](const unsigned (&w)[12]) -> bool {
-    const bool below = !PINV && chunk_below_window(w, lut, lr, C);   // counts only, no lasso
+    // the non-white count and the per-channel minima of the density bound
+    // from the same regrouped words
+    unsigned rg, bb;
+    const float nw = chunk_nonwhite_min(w, wb, &rg, &bb);
+    const bool below = !PINV && below_bound(rg, bb, lut, lr, C);   // counts only, no lasso
     if (below || wbelow) {
-      // the non-white count; with wbelow a tissue chunk's lasso counts all
-      // 16 pixels below both windows (its white ones included), so its
-      // white pixels are taken off here
-      const float nw = chunk_nonwhite(w, wb);
+      // with wbelow a tissue chunk's lasso counts all 16 pixels below both
+      // windows (its white ones included), so its white pixels are taken
+      // off here
       const f2 nb = pk(below ? nw : nw - (float)kChunk, 0.f);
       c_nw = add2(c_nw, pk(nw, 0.f));
       c_b0 = add2(c_b0, nb);

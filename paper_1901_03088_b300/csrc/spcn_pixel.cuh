@@ -409,6 +409,47 @@ __device__ __forceinline__ float chunk_nonwhite(const unsigned (&w)[12], const W
   return (float)(kChunk - __popc(x & 0xF0F0F0F0u));
 }
 
+// chunk_nonwhite and, from the same regrouped words, the chunk's
+// per-channel minima in the layout of chunk_channel_min (R in byte 1 and G in
+// byte 3 of *rg, B in byte 1 of *bb).  Per group of four pixels the six
+// words a, P, Q (pixels 0-1) and C8, Q2, P2 (pixels 2-3) carry, in the high
+// bytes of their 16-bit lanes, the channels (G0, R1), (R0, G1), (B0, B1),
+// (B2, G3), (R2, R3) and (G2, B3); 16-bit minima over the groups keep those
+// high bytes' minima per word type, and six lane swaps and minima gather
+// them by channel.
+__device__ __forceinline__ float chunk_nonwhite_min(const unsigned (&w)[12], const WhiteBytes& t,
+                                                    unsigned* rg, unsigned* bb) {
+  unsigned f[4];
+  unsigned ka = 0u, kp = 0u, kq = 0u, kc = 0u, kq2 = 0u, kp2 = 0u;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const unsigned a = w[3 * j], b = w[3 * j + 1], c = w[3 * j + 2];
+    const unsigned P = __byte_perm(a, b, 0x4400u), Q = __byte_perm(a, b, 0x5520u);
+    const unsigned C8 = c << 8, Q2 = __byte_perm(b, c, 0x5520u), P2 = __byte_perm(b, c, 0x7330u);
+    const unsigned m01 = min_u16x2(min_u16x2(a, P), Q);
+    const unsigned m23 = min_u16x2(min_u16x2(C8, Q2), P2);
+    const unsigned z = __byte_perm(m01, m23, 0x7531u);   // the four pixels' minima
+    const unsigned s = (z & 0x7F7F7F7Fu) + t.k;
+    f[j] = (z & (s | t.m)) | (s & t.m);   // bit 7 of each byte: the pixel is white
+    if (j == 0) {
+      ka = a; kp = P; kq = Q; kc = C8; kq2 = Q2; kp2 = P2;
+    } else {
+      ka = min_u16x2(ka, a); kp = min_u16x2(kp, P); kq = min_u16x2(kq, Q);
+      kc = min_u16x2(kc, C8); kq2 = min_u16x2(kq2, Q2); kp2 = min_u16x2(kp2, P2);
+    }
+  }
+  const unsigned x1 = min_u16x2(__byte_perm(ka, 0u, 0x1032u), kp);    // (R, G)
+  const unsigned y = min_u16x2(kc, __byte_perm(kp2, 0u, 0x1032u));    // (B, G)
+  const unsigned r2 = min_u16x2(kq2, __byte_perm(kq2, 0u, 0x1032u));  // (R, R)
+  const unsigned b2 = min_u16x2(kq, __byte_perm(kq, 0u, 0x1032u));    // (B, B)
+  *rg = min_u16x2(x1, __byte_perm(r2, y, 0x7610u));                   // (R, G)
+  *bb = min_u16x2(y, b2);                                              // (B, -)
+  unsigned x = (f[0] & 0x80808080u) | ((f[1] >> 1) & 0x7F7F7F7Fu);
+  x = (x & 0xC0C0C0C0u) | ((f[2] >> 2) & 0x3F3F3F3Fu);
+  x = (x & 0xE0E0E0E0u) | ((f[3] >> 3) & 0x1F1F1F1Fu);
+  return (float)(kChunk - __popc(x & 0xF0F0F0F0u));
+}
+
 constexpr int kWarpQueue = 64;    // queue entries per warp; drained as soon as 32 are waiting, so
                                   // the re-read pixels are recent enough to still be in L2
 
