@@ -309,9 +309,17 @@ int spcn_estimate_basis_noalloc(const spcn_image* img, const spcn_params* params
 
 typedef enum {
   SPCN_SCHED_PHASED = 0,       /* all pass-1 items, then all pass-2 items */
-  SPCN_SCHED_INTERLEAVED = 1   /* groups of about group_px pixels: pass 1 of group g+1
+  SPCN_SCHED_INTERLEAVED = 1,  /* groups of about group_px pixels: pass 1 of group g+1
                                   is queued before pass 2 of group g, so pass 2
                                   rereads recently read tiles */
+  SPCN_SCHED_STAGED = 2        /* separate launches, each with the whole shared memory
+                                  and register budget of its pass: pass 1 of every
+                                  tile (with the single-image chunk skips and
+                                  per-warp stack), the per-tile selects, pass 2 of
+                                  every tile, then the cooperative kernel for the
+                                  exact fallback only; items of item_chunks chunks,
+                                  the tiles of one table adjacent.  Needs fewer
+                                  than 2^32 chunks per tile (else INVALID_ARG) */
 } spcn_schedule;
 
 typedef struct {

@@ -90,7 +90,9 @@ struct BatchTileState {
 
 // Run-wide state (zeroed before every run).
 struct BatchRunState {
-  unsigned next;           // work-queue ticket
+  unsigned next;           // work-queue ticket (staged schedule: pass-1 items)
+  unsigned next2;          // staged schedule: pass-2 items
+  unsigned n_fallback;     // tiles left to the exact fallback (counted by the selects)
   unsigned barrier;        // grid barrier counter of the fallback phase
   int abort;               // a wait gave up
   int err;                 // first error of the run
@@ -115,6 +117,7 @@ struct BatchArgs {
   unsigned n_items, n_tiles;
   unsigned wthr;           // (white threshold + 1) << 8, compared with table offsets
   unsigned thr;            // white threshold
+  unsigned wm, we;         // all-white test of a full chunk: (AND of its words & wm) == we
   double pct;
   double tgt0, tgt1;       // target percentiles
   float Wt[6];             // target basis
@@ -410,6 +413,7 @@ __device__ void batch_select(const BatchArgs& a, unsigned tile, unsigned* s_hist
       for (int i = 0; i < 6; ++i) S->M[i] = recon_coef(a.Wt, s->scale, hs, i);
     }
     s->all_resolved = all;
+    if (!all) atomicAdd(&a.run->n_fallback, 1u);
     __threadfence();
     st_release_s32(&S->ready, all ? 1 : 2);
   }
@@ -800,6 +804,9 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch(BatchArgs a) {
   __shared__ int s_go, s_sel_tile;
   __shared__ unsigned s_piece;
   __shared__ float s_M[6];
+  // staged schedule (empty queue): the selects are done and counted the
+  // tiles left to the fallback; none, nothing to do (the same in every block)
+  if (a.n_items == 0 && __ldcg(&a.run->n_fallback) == 0u) return;
   const unsigned lr = lane_reg();
   int cur_table = -1;   // table in shared memory: 2 * model + (1: optical densities, 0: projected)
   // Thread 0 runs the queue one item ahead: the next item's descriptor is
@@ -874,6 +881,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch(BatchArgs a) {
   // tiles whose ranks the windows missed: exact radix select over the whole
   // grid, then their pass 2 (tile order; the ready words are final here)
   if (!grid_barrier(&a.run->barrier, gridDim.x, &a.run->abort, &a.run->err, a.timeout_ns)) return;
+  if (__ldcg(&a.run->n_fallback) == 0u) return;   // final after the barrier; the same everywhere
   unsigned target = gridDim.x;
   for (unsigned t = 0; t < a.n_tiles; ++t) {
     BatchTileState* S = a.state + t;
@@ -921,6 +929,403 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch(BatchArgs a) {
   }
 }
 
+// ------------------------------------------------------------ staged schedule
+// SPCN_SCHED_STAGED runs the batch as separate launches, each with the whole
+// shared memory and register budget for its own pass:
+//   k_batch_pilot  window starts (above);
+//   k_batch_p1     pass 1 of every tile with the single-image chunk handling:
+//                  all-white chunks dropped, chunks provably below both
+//                  window starts counted without densities, the others kept
+//                  on a per-warp stack until a full warp of them runs the
+//                  closed-form H-step, and every pixel at or above a window
+//                  start queued, recomputed and its keys appended to the
+//                  tile's lists (with the first-digit histograms);
+//   k_batch_sel    one block per tile: batch_select over the lists;
+//   k_batch_p2     pass 2 of every tile whose percentile is known;
+//   k_batch        with an empty queue: only the exact fallback of the tiles
+//                  whose ranks missed their window.
+// Blocks claim items (chunk ranges of one tile; the tiles of one table are
+// adjacent in the list) from a ticket.  All warps of a block work on the same
+// item, so the current tile's constants live in shared memory and a table is
+// loaded only when the model changes.  A warp's stack and hit queue hold
+// chunks of one tile: they are emptied when the block moves to another tile.
+constexpr size_t kStagedQueueBytes = sizeof(uint2) * kWarpQueue * kWarps;
+constexpr size_t kStagedStackBytes =
+    (3 * sizeof(uint4) + sizeof(unsigned)) * kChunkStack * kWarps;
+constexpr int kStagedKeyBuf = 96;   // keys per stain buffered per warp (flushed above 64)
+constexpr size_t kStagedKeyBytes = sizeof(unsigned) * 2 * kStagedKeyBuf * kWarps;
+constexpr size_t kStagedSmem =
+    kLutSmemBytes + kStagedQueueBytes + kStagedStackBytes + kStagedKeyBytes;
+constexpr size_t kSelectSmem = sizeof(unsigned) * 2 * kSelBins;
+
+// The current tile of a k_batch_p1 block.
+struct StagedTile {
+  WindowConst C;      // [h~ < lo] tests of the tile's window starts; the upper
+                      // tests are constant 1 (the windows are open above)
+  unsigned* list0;    // key lists (stain 1 at list0 + cap)
+  unsigned* list1;
+  u64* list_n;        // keys appended per stain
+  unsigned* hist;     // first-digit histograms (stain 1 at hist + kSelBins)
+  SelectState* sel;   // the tile's counts
+  u64 cap;
+};
+
+// The warp's buffered keys appended to the tile's lists (flush_keys: one
+// atomic reservation per stain) and the buffers emptied.  Called by the whole
+// warp; kc0 and kc1 are warp-uniform.
+__device__ __forceinline__ void staged_flush_keys(unsigned* kb, int& kc0, int& kc1,
+                                                  const StagedTile& t) {
+  __syncwarp();
+  flush_keys(kb, kc0, t.list0, t.cap, t.list_n, t.hist, t.C.lo0);
+  flush_keys(kb + kStagedKeyBuf, kc1, t.list1, t.cap, t.list_n + 1, t.hist + kSelBins, t.C.lo1);
+  __syncwarp();
+  kc0 = kc1 = 0;
+}
+
+// Keys of up to 32 queued pixels (lane e takes entry e < count: the tile's
+// chunk index and the pixel in the chunk).  The pixel is read again (still in
+// L2) and its densities recomputed with solve_one, so its keys are those of
+// every other pass; keys at or above a window start go to the warp's key
+// buffers (kb: stain 0, kb + kStagedKeyBuf: stain 1), flushed to the lists
+// once more than kStagedKeyBuf - 32 wait.  Called by the whole warp.
+template <class G>
+__device__ __forceinline__ void staged_drain(const uint2* queue, int count, const G& g,
+                                             const char* lut, unsigned lr, const Lasso& L,
+                                             const StagedTile& t, unsigned* kb, int& kc0,
+                                             int& kc1) {
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned lt = (1u << lane) - 1u;
+  unsigned k0 = 0u, k1 = 0u;
+  bool in0 = false, in1 = false;
+  if ((int)lane < count) {
+    const uint2 ent = queue[lane];
+    const ChunkPos p = chunk_pos(g, (u64)ent.x);
+    const int k = (int)ent.y;
+    if (SPCN_CHECK(k < p.n && p.src_off >= 0 && p.src_off + 3 * (int64_t)k + 3 <= g.src_bytes,
+                   g.err)) {
+      const uint8_t* src = g.src + p.src_off + 3 * k;
+      const unsigned r = __ldg(src), gg = __ldg(src + 1), b = __ldg(src + 2);
+      float h1, h2;
+      solve_one(lut, (r << 8) | lr, (gg << 8) | lr, (b << 8) | lr, L, h1, h2);
+      k0 = __float_as_uint(h1);
+      k1 = __float_as_uint(h2);
+      in0 = k0 >= t.C.lo0;
+      in1 = k1 >= t.C.lo1;
+    }
+  }
+  const unsigned b0 = __ballot_sync(0xFFFFFFFFu, in0), b1 = __ballot_sync(0xFFFFFFFFu, in1);
+  if (in0) kb[kc0 + __popc(b0 & lt)] = k0;
+  if (in1) kb[kStagedKeyBuf + kc1 + __popc(b1 & lt)] = k1;
+  kc0 += __popc(b0);
+  kc1 += __popc(b1);
+  if (kc0 > kStagedKeyBuf - 32 || kc1 > kStagedKeyBuf - 32) staged_flush_keys(kb, kc0, kc1, t);
+}
+
+// Queue the flagged pixels of the warp's chunks: bit 2 (7 - p) + h of d marks
+// pixel 2 p + h of the lane's chunk qi.  Every 32 waiting entries are drained
+// in one step of the warp.  Called by the whole warp; qn is warp-uniform.
+template <class G>
+__device__ __forceinline__ void staged_queue(unsigned d, unsigned qi, uint2* s_queue, int& qn,
+                                             const G& g, const char* lut, unsigned lr,
+                                             const Lasso& L, const StagedTile& t, unsigned* kb,
+                                             int& kc0, int& kc1) {
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned lt = (1u << lane) - 1u;
+  unsigned ball;
+  while ((ball = __ballot_sync(0xFFFFFFFFu, d != 0u)) != 0u) {
+    if (d) {
+      const unsigned bit = (unsigned)__ffs(d) - 1u;
+      d &= d - 1u;
+      s_queue[qn + __popc(ball & lt)] = make_uint2(qi, 2u * (7u - (bit >> 1)) + (bit & 1u));
+    }
+    qn += __popc(ball);
+    if (qn >= 32) {
+      __syncwarp();
+      staged_drain(s_queue, 32, g, lut, lr, L, t, kb, kc0, kc1);
+      const bool mv = lane + 32u < (unsigned)qn;
+      uint2 rest = make_uint2(0u, 0u);
+      if (mv) rest = s_queue[lane + 32u];
+      __syncwarp();
+      if (mv) s_queue[lane] = rest;
+      __syncwarp();
+      qn -= 32;
+    }
+  }
+}
+
+// A row's last chunk when it holds fewer than 16 pixels, pixel by pixel: the
+// counts (the padding bytes are not pixels) and the flags of its pixels at
+// or above a window start, in the layout of staged_queue.
+__device__ __forceinline__ unsigned staged_partial(const uint8_t* src, int n, const char* lut,
+                                                   unsigned lr, const Lasso& L,
+                                                   const WindowConst& C, f2& c_nw, f2& c_b0,
+                                                   f2& c_b1) {
+  float nw = 0.f, b0 = 0.f, b1 = 0.f;
+  unsigned d = 0u;
+#pragma unroll 1
+  for (int k = 0; k < n; ++k) {
+    const unsigned aR = ((unsigned)__ldg(src + 3 * k) << 8) | lr;
+    const unsigned aG = ((unsigned)__ldg(src + 3 * k + 1) << 8) | lr;
+    const unsigned aB = ((unsigned)__ldg(src + 3 * k + 2) << 8) | lr;
+    if (min(min(aR, aG), aB) >= C.wthr) continue;   // white
+    float h1, h2;
+    solve_one(lut, aR, aG, aB, L, h1, h2);
+    const float B0 = fma_sat(h1, C.nk0, C.lk0), B1 = fma_sat(h2, C.nk1, C.lk1);
+    nw += 1.f;
+    b0 += B0;
+    b1 += B1;
+    if (B0 + B1 < 2.f) d |= 1u << (2 * (7 - (k >> 1)) + (k & 1));
+  }
+  c_nw = add2(c_nw, pk(nw, 0.f));
+  c_b0 = add2(c_b0, pk(b0, 0.f));
+  c_b1 = add2(c_b1, pk(b1, 0.f));
+  return d;
+}
+
+// A warp's counts added to the tile's totals, then zeroed.  Per-thread counts
+// are exact in FP32 (one item holds fewer than 2^24 pixels per thread); a
+// thread's below counts can be negative (a stacked chunk's white pixels are
+// taken off by the lane that classified it and counted by the lane that runs
+// its H-step), and the 32-bit warp sums, sign-extended, add up modulo 2^64 to
+// the tile's exact totals.
+__device__ __forceinline__ void staged_counts(SelectState* sel, f2& c_nw, f2& c_b0, f2& c_b1) {
+  const int v0 = __reduce_add_sync(0xFFFFFFFFu, (int)lo_of(c_nw) + (int)hi_of(c_nw));
+  const int v1 = __reduce_add_sync(0xFFFFFFFFu, (int)lo_of(c_b0) + (int)hi_of(c_b0));
+  const int v2 = __reduce_add_sync(0xFFFFFFFFu, (int)lo_of(c_b1) + (int)hi_of(c_b1));
+  if ((threadIdx.x & 31u) == 0u) {
+    if (v0) atomicAdd(&sel->n_nw, (u64)(long long)v0);
+    if (v1) atomicAdd(&sel->below[0], (u64)(long long)v1);
+    if (v2) atomicAdd(&sel->below[1], (u64)(long long)v2);
+  }
+  c_nw = c_b0 = c_b1 = pk(0.f, 0.f);
+}
+
+// Pass 1 of every tile (staged schedule).  One block per SM; items from the
+// run's first ticket.
+template <class G>
+__global__ void __launch_bounds__(kBatchThreads, 1) k_batch_p1(BatchArgs a) {
+  extern __shared__ __align__(16) char s_dyn[];
+  char* lut = s_dyn;
+  const unsigned warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+  const unsigned lt = (1u << lane) - 1u;
+  uint2* s_queue = reinterpret_cast<uint2*>(s_dyn + kLutSmemBytes) + warp * kWarpQueue;
+  char* stk = s_dyn + kLutSmemBytes + kStagedQueueBytes;
+  uint4* s_stk = reinterpret_cast<uint4*>(stk) + warp * (3 * kChunkStack);
+  unsigned* s_stq =
+      reinterpret_cast<unsigned*>(stk + sizeof(uint4) * 3 * kChunkStack * kWarps) +
+      warp * kChunkStack;
+  unsigned* s_kb = reinterpret_cast<unsigned*>(stk + kStagedStackBytes) + warp * 2 * kStagedKeyBuf;
+  __shared__ BatchItem s_item;
+  __shared__ unsigned s_piece;
+  __shared__ StagedTile s_t;
+  __shared__ G s_g;
+  __shared__ Lasso s_L;
+  const unsigned lr = lane_reg();
+  const WhiteBytes wb = white_bytes(a.thr);
+  int cur_tile = -1, cur_model = -1;
+  bool wbelow = false;   // every white pixel of the tile lies below both window starts
+  int qn = 0;            // entries in this warp's hit queue (warp-uniform)
+  int ns = 0;            // chunks on this warp's stack (warp-uniform)
+  int kc0 = 0, kc1 = 0;  // keys in this warp's buffers (warp-uniform)
+  f2 c_nw = pk(0.f, 0.f), c_b0 = c_nw, c_b1 = c_nw;
+  // the window arithmetic of a warp of tissue chunks (lanes with have =
+  // false take no part), then the hit queue
+  auto lasso = [&](const unsigned (&w)[12], unsigned qi, bool have) {
+    unsigned d = 0u;
+    if (have) {
+      const f2 NR1 = pk(s_L.nrho1, s_L.nrho1), NR2 = pk(s_L.nrho2, s_L.nrho2);
+      f2 mask;
+      if (wbelow)
+        window_chunk<false, true>(w, lut, lr, NR1, NR2, s_L.kappa, s_t.C, c_nw, c_b0, c_b1, mask);
+      else
+        window_chunk<false, false>(w, lut, lr, NR1, NR2, s_L.kappa, s_t.C, c_nw, c_b0, c_b1,
+                                   mask);
+      const unsigned m0 = (unsigned)lo_of(mask), m1 = (unsigned)hi_of(mask);
+      d = ((m0 | (m0 >> 1)) & 0x5555u) | (((m1 | (m1 >> 1)) & 0x5555u) << 1);
+    }
+    staged_queue(d, qi, s_queue, qn, s_g, lut, lr, s_L, s_t, s_kb, kc0, kc1);
+  };
+  // counts of a full, not all-white chunk; true when it needs the H-step
+  // (not provably below both window starts)
+  auto classify = [&](const unsigned (&w)[12]) -> bool {
+    unsigned rg, bb;
+    const float nw = chunk_nonwhite_min(w, wb, &rg, &bb);
+    const bool below = below_bound(rg, bb, lut, lr, s_t.C);
+    if (below || wbelow) {
+      const f2 nb = pk(below ? nw : nw - (float)kChunk, 0.f);
+      c_nw = add2(c_nw, pk(nw, 0.f));
+      c_b0 = add2(c_b0, nb);
+      c_b1 = add2(c_b1, nb);
+    }
+    return !below;
+  };
+  // tissue chunks wait on the stack until a full warp of them is ready
+  auto warp_step = [&](bool tissue, unsigned (&w)[12], unsigned qi) {
+    const unsigned ball = __ballot_sync(0xFFFFFFFFu, tissue);
+    const int cnt = __popc(ball);
+    __syncwarp();   // the stack's previous reads and writes are done
+    if (ns + cnt < 32) {
+      if (tissue) stack_put(s_stk, s_stq, ns + __popc(ball & lt), w, qi);
+      ns += cnt;
+      return;
+    }
+    if (!tissue) stack_get(s_stk, s_stq, ns - 1 - __popc(~ball & lt), w, qi);
+    ns -= 32 - cnt;
+    lasso(w, qi, true);
+  };
+  // the rest of the warp's stack and queue, and its counts, before the block
+  // moves to another tile
+  auto flush_tile = [&]() {
+    __syncwarp();
+    if (ns > 0) {
+      const bool have = lane < (unsigned)ns;
+      unsigned w[12];
+      unsigned qi = 0u;
+      if (have) stack_get(s_stk, s_stq, (int)lane, w, qi);
+      lasso(w, qi, have);
+      ns = 0;
+    }
+    if (qn > 0) {
+      __syncwarp();
+      staged_drain(s_queue, qn, s_g, lut, lr, s_L, s_t, s_kb, kc0, kc1);
+      qn = 0;
+    }
+    staged_flush_keys(s_kb, kc0, kc1, s_t);
+    staged_counts(s_t.sel, c_nw, c_b0, c_b1);
+  };
+  // thread 0 claims tickets one item ahead: the atomic's latency overlaps the
+  // current item
+  unsigned t_next = 0u;
+  if (threadIdx.x == 0) t_next = atomicAdd(&a.run->next, 1u);
+  for (;;) {
+    if (threadIdx.x == 0) {
+      BatchItem it{};
+      it.tile = ~0u;
+      if (t_next < a.n_items) {
+        it = a.items[t_next];
+        t_next = atomicAdd(&a.run->next, 1u);
+      }
+      s_item = it;
+      s_piece = 0u;
+    }
+    __syncthreads();
+    const unsigned tile = s_item.tile;
+    const u64 c0 = s_item.c0, c1 = s_item.c1;
+    const unsigned model = s_item.model;
+    if ((int)tile != cur_tile && cur_tile >= 0) flush_tile();
+    if (tile == ~0u) break;
+    if ((int)tile != cur_tile) {
+      __syncthreads();   // every warp is done with the previous tile's table and constants
+      if ((int)model != cur_model) {
+        load_lut(a.models + model, lut);   // ends with a block barrier
+        cur_model = (int)model;
+      }
+      if (threadIdx.x == 0) {
+        const BatchTile* T = a.tiles + tile;
+        BatchTileState* S = a.state + tile;
+        StagedTile st;
+        st.C = WindowConst{nullptr, a.wthr, T->win[0] ? T->lo[0] : 0xFFFFFFFFu,
+                           T->win[1] ? T->lo[1] : 0xFFFFFFFFu, 0u, 0u, T->nk[0], T->lk[0],
+                           T->nk[1], T->lk[1], 0.f, 1.f, 0.f, 1.f};
+        st.list0 = T->keys;
+        st.list1 = T->keys + T->list_cap;
+        st.list_n = S->list_n;
+        st.hist = a.hist1 + (size_t)tile * 2 * kSelBins;
+        st.sel = &S->sel;
+        st.cap = T->list_cap;
+        s_t = st;
+        s_g = geometry_as<G>(T->g);
+        s_L = a.models[model].lasso;
+      }
+      __syncthreads();
+      cur_tile = (int)tile;
+      wbelow = whites_below(a.thr, lut, lr, s_t.C);
+    }
+    // the item's chunks, 32 per warp step, in pieces claimed from a shared
+    // counter (a warp that spends time on its stack or queue takes fewer)
+    for (;;) {
+      unsigned piece = 0u;
+      if (lane == 0) piece = atomicAdd(&s_piece, 1u);
+      const u64 base = c0 + 32ull * __shfl_sync(0xFFFFFFFFu, piece, 0);
+      if (base >= c1) break;
+      const u64 q = base + lane;
+      unsigned w[12];
+      bool tissue = false;
+      unsigned dpart = 0u;
+      if (q < c1) {
+        const ChunkPos p = chunk_pos(s_g, q);
+        load_chunk<false>(s_g, p, w);
+        if (p.n == kChunk) {
+          tissue = !chunk_white(w, a.wm, a.we) && classify(w);
+        } else if (SPCN_CHECK(p.src_off >= 0 && p.src_off + 3 * (int64_t)p.n <= s_g.src_bytes,
+                              s_g.err)) {
+          dpart = staged_partial(s_g.src + p.src_off, p.n, lut, lr, s_L, s_t.C, c_nw, c_b0, c_b1);
+        }
+      }
+      warp_step(tissue, w, (unsigned)q);
+      if (__any_sync(0xFFFFFFFFu, dpart != 0u))
+        staged_queue(dpart, (unsigned)q, s_queue, qn, s_g, lut, lr, s_L, s_t, s_kb, kc0, kc1);
+    }
+    staged_counts(s_t.sel, c_nw, c_b0, c_b1);
+    __syncthreads();   // the item is done: s_item and s_piece may be rewritten
+  }
+}
+
+// The percentiles of every tile from its key lists (staged schedule).
+__global__ void __launch_bounds__(kBatchThreads) k_batch_sel(BatchArgs a) {
+  extern __shared__ __align__(16) char s_dyn[];
+  __shared__ u64 s_tmp[33];
+  for (unsigned t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
+    batch_select(a, t, reinterpret_cast<unsigned*>(s_dyn), s_tmp);
+    __syncthreads();
+  }
+}
+
+// Pass 2 of every tile whose percentile the lists gave (staged schedule);
+// items from the run's second ticket, the optical-density table reloaded when
+// the model changes.
+template <class G>
+__global__ void __launch_bounds__(kBatchThreads, 1) k_batch_p2(BatchArgs a) {
+  extern __shared__ __align__(16) char s_dyn[];
+  char* lut = s_dyn;
+  __shared__ BatchItem s_item;
+  __shared__ float s_M[6];
+  __shared__ int s_go;
+  int cur_model = -1;
+  unsigned t_next = 0u;   // thread 0: tickets claimed one item ahead
+  if (threadIdx.x == 0) t_next = atomicAdd(&a.run->next2, 1u);
+  for (;;) {
+    if (threadIdx.x == 0) {
+      BatchItem it{};
+      it.tile = ~0u;
+      if (t_next < a.n_items) {
+        it = a.items[t_next];
+        t_next = atomicAdd(&a.run->next2, 1u);
+      }
+      int go = 0;
+      if (it.tile != ~0u) {
+        const BatchTileState* S = a.state + it.tile;
+        go = __ldcg(&S->ready) == 1;
+        if (go)
+          for (int i = 0; i < 6; ++i) s_M[i] = __ldcg(&S->M[i]);
+      }
+      s_item = it;
+      s_go = go;
+    }
+    __syncthreads();
+    const BatchItem item = s_item;
+    if (item.tile == ~0u) break;
+    if (s_go) {
+      if ((int)item.model != cur_model) {
+        load_od_lut(a.models + item.model, lut);   // ends with a block barrier
+        cur_model = (int)item.model;
+      }
+      batch_pass2<G>(a, item.tile, item.c0, item.c1, lut, s_M);
+    }
+    __syncthreads();   // the item is done: shared words and the table may be rewritten
+  }
+}
+
 // ------------------------------------------------------------ host side
 struct Batch {
   Context* c = nullptr;
@@ -938,6 +1343,8 @@ struct Batch {
   unsigned* keys = nullptr;
   u64* rhist = nullptr;
   int grid = 0;
+  int grid_p1 = 0, grid_p2 = 0, grid_sel = 0;   // staged schedule
+  u64 max_chunks = 0;            // chunks of the largest tile
   bool flat = false;             // every tile contiguous: launch the flat instantiation
   BatchArgs args{};
   spcn_batch_config cfg{};
@@ -957,10 +1364,29 @@ static int configure_batch_kernel(Context* c, int* grid) {
   return SPCN_OK;
 }
 
+template <class G>
+static int configure_staged_kernels(Context* c, int* grid_p1, int* grid_p2) {
+  SPCN_CUDA_TRY(cudaFuncSetAttribute(k_batch_p1<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kStagedSmem));
+  SPCN_CUDA_TRY(cudaFuncSetAttribute(k_batch_p2<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kLutSmemBytes));
+  int o1 = 0, o2 = 0;
+  SPCN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_batch_p1<G>, kBatchThreads,
+                                                              kStagedSmem));
+  SPCN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, k_batch_p2<G>, kBatchThreads,
+                                                              kLutSmemBytes));
+  if (o1 < 1 || o2 < 1) return SPCN_ERR_CUDA;
+  *grid_p1 = c->num_sms * o1;
+  *grid_p2 = c->num_sms * o2;
+  return SPCN_OK;
+}
+
 static bool config_ok(const spcn_batch_config* cfg) {
   if (!cfg) return false;
   if (cfg->item_chunks < kPassThreads || cfg->item_chunks % kPassThreads != 0) return false;
-  if (cfg->schedule != SPCN_SCHED_PHASED && cfg->schedule != SPCN_SCHED_INTERLEAVED) return false;
+  if (cfg->schedule != SPCN_SCHED_PHASED && cfg->schedule != SPCN_SCHED_INTERLEAVED &&
+      cfg->schedule != SPCN_SCHED_STAGED)
+    return false;
   if (cfg->schedule == SPCN_SCHED_INTERLEAVED && cfg->group_px < 1) return false;
   return true;
 }
@@ -986,7 +1412,7 @@ static void build_items(const Batch* b, const spcn_batch_config& cfg, std::vecto
       out->push_back({(unsigned)t, pass, b->tiles[t].model, n1, c0, std::min(nch, c0 + S)});
     if (pass == 1) (*n_items1)[t] = n1;
   };
-  if (cfg.schedule == SPCN_SCHED_PHASED) {
+  if (cfg.schedule == SPCN_SCHED_PHASED || cfg.schedule == SPCN_SCHED_STAGED) {
     // pass 2 needs no particular order: tiles sharing a table go together
     // (fewer table reloads), largest first within a table
     std::vector<int> rank(b->n_models, -1), order2 = order;
@@ -996,6 +1422,30 @@ static void build_items(const Batch* b, const spcn_batch_config& cfg, std::vecto
     std::stable_sort(order2.begin(), order2.end(), [&](int x, int y) {
       return rank[b->tiles[x].model] < rank[b->tiles[y].model];
     });
+    if (cfg.schedule == SPCN_SCHED_STAGED) {
+      // one list of chunk ranges, read by both passes, the tiles of one table
+      // together (the staged pass 1 also reloads its table per model).  Item
+      // sizes are guided: item_chunks while the rest of the list holds more
+      // than two such items per block of the pass-1 grid, then the rest
+      // divided by twice the blocks (at least 1024 chunks), so the blocks
+      // finish each pass together
+      const u64 blocks2 = 2 * (u64)std::max(1, b->grid_p1);
+      u64 rest = 0;
+      for (int t : order2) rest += b->tiles[t].g.nchunks;
+      for (int t : order2) {
+        const u64 nch = b->tiles[t].g.nchunks;
+        u64 c0 = 0;
+        while (c0 < nch) {
+          const u64 guided = std::max<u64>(1024, rest / blocks2);
+          const u64 size = std::min<u64>(S, guided);
+          const u64 c1 = std::min(nch, c0 + size);
+          out->push_back({(unsigned)t, 1u, b->tiles[t].model, 0u, c0, c1});
+          rest -= c1 - c0;
+          c0 = c1;
+        }
+      }
+      return;
+    }
     for (int t : order) emit(t, 1);
     for (int t : order2) emit(t, 2);
     return;
@@ -1021,6 +1471,8 @@ static void build_items(const Batch* b, const spcn_batch_config& cfg, std::vecto
 }
 
 static int apply_config(Batch* b, const spcn_batch_config& cfg) {
+  // the staged pass 1 queues 32-bit chunk indices of a tile
+  if (cfg.schedule == SPCN_SCHED_STAGED && b->max_chunks >= (1ull << 32)) return SPCN_ERR_INVALID_ARG;
   std::vector<BatchItem> items;
   std::vector<unsigned> n1;
   build_items(b, cfg, &items, &n1);
@@ -1070,6 +1522,11 @@ static int batch_launch(Batch* b, cudaStream_t st) {
   }
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   SPCN_CUDA_TRY(cudaStreamIsCapturing(st, &cap));
+  const bool staged = b->cfg.schedule == SPCN_SCHED_STAGED;
+  // staged: the fused kernel runs with an empty queue (only the exact
+  // fallback of tiles whose ranks missed their window)
+  BatchArgs fa = b->args;
+  if (staged) fa.n_items = 0;
   cudaLaunchConfig_t lc = {};
   lc.gridDim = dim3((unsigned)b->grid);
   lc.blockDim = dim3(kBatchThreads);
@@ -1080,19 +1537,37 @@ static int batch_launch(Batch* b, cudaStream_t st) {
   attr[0].val.cooperative = 1;
   lc.attrs = attr;
   lc.numAttrs = 1;
-  cudaError_t e;
+  int launched = 0;
   // contiguous tiles only: the flat traversal (fewer registers per loop)
-  auto launch = [&]() {
-    return b->flat ? cudaLaunchKernelEx(&lc, k_batch<FlatGeometry>, b->args)
-                   : cudaLaunchKernelEx(&lc, k_batch<Geometry>, b->args);
+  auto launch = [&]() -> cudaError_t {
+    if (staged) {
+      if (b->flat)
+        k_batch_p1<FlatGeometry><<<b->grid_p1, kBatchThreads, kStagedSmem, st>>>(b->args);
+      else
+        k_batch_p1<Geometry><<<b->grid_p1, kBatchThreads, kStagedSmem, st>>>(b->args);
+      ++launched;
+      k_batch_sel<<<b->grid_sel, kBatchThreads, kSelectSmem, st>>>(b->args);
+      ++launched;
+      if (b->flat)
+        k_batch_p2<FlatGeometry><<<b->grid_p2, kBatchThreads, kLutSmemBytes, st>>>(b->args);
+      else
+        k_batch_p2<Geometry><<<b->grid_p2, kBatchThreads, kLutSmemBytes, st>>>(b->args);
+      ++launched;
+      const cudaError_t e0 = cudaGetLastError();
+      if (e0 != cudaSuccess) return e0;
+    }
+    ++launched;
+    return b->flat ? cudaLaunchKernelEx(&lc, k_batch<FlatGeometry>, fa)
+                   : cudaLaunchKernelEx(&lc, k_batch<Geometry>, fa);
   };
+  cudaError_t e;
   if (cap == cudaStreamCaptureStatusNone) {
     TimedLaunch tl(c, SPCN_KERNEL_BATCH, st);
     e = launch();
   } else {
     e = launch();
   }
-  c->launches++;
+  c->launches += launched;
   if (e != cudaSuccess) return SPCN_ERR_CUDA;
   return SPCN_OK;
 }
@@ -1168,10 +1643,17 @@ static int batch_create(Context* c, int n, const spcn_image* tiles, const spcn_s
     if (rc) return fail(rc);
   }
   b->flat = true;
-  for (const BatchTile& T : b->tiles) b->flat = b->flat && T.g.flat;
+  for (const BatchTile& T : b->tiles) {
+    b->flat = b->flat && T.g.flat;
+    b->max_chunks = std::max(b->max_chunks, (u64)T.g.nchunks);
+  }
   rc = b->flat ? configure_batch_kernel<FlatGeometry>(c, &b->grid)
                : configure_batch_kernel<Geometry>(c, &b->grid);
   if (rc) return fail(rc);
+  rc = b->flat ? configure_staged_kernels<FlatGeometry>(c, &b->grid_p1, &b->grid_p2)
+               : configure_staged_kernels<Geometry>(c, &b->grid_p1, &b->grid_p2);
+  if (rc) return fail(rc);
+  b->grid_sel = std::min(n, 4 * c->num_sms);
   BatchArgs& a = b->args;
   a.tiles = b->d_tiles;
   a.state = reinterpret_cast<BatchTileState*>(b->d_state + kRunStateBytes);
@@ -1183,15 +1665,19 @@ static int batch_create(Context* c, int n, const spcn_image* tiles, const spcn_s
   a.n_tiles = (unsigned)n;
   a.wthr = ((unsigned)params->white_thresh + 1u) << 8;
   a.thr = (unsigned)params->white_thresh;
+  white_test_consts(params->white_thresh, &a.wm, &a.we);
   a.pct = (double)params->stain_pct;
   a.tgt0 = tgt->p99[0];
   a.tgt1 = tgt->p99[1];
   for (int i = 0; i < 6; ++i) a.Wt[i] = tgt->W[i];
   for (int i = 0; i < 3; ++i) a.l2i0[i] = (float)log2((double)tgt->i0[i]);
   a.timeout_ns = c->timeout_ns;
+  // default schedule: the staged launches (fastest on the benchmark's
+  // 256-tile batch), else the fused one
   spcn_batch_config cfg{};
-  cfg.item_chunks = 16 * kPassThreads;
-  cfg.schedule = SPCN_SCHED_PHASED;
+  const bool staged_ok = b->max_chunks < (1ull << 32);
+  cfg.item_chunks = (staged_ok ? 32 : 16) * kPassThreads;
+  cfg.schedule = staged_ok ? SPCN_SCHED_STAGED : SPCN_SCHED_PHASED;
   cfg.group_px = 0;
   rc = apply_config(b, cfg);
   if (rc) return fail(rc);
@@ -1298,7 +1784,7 @@ int spcn_batch_tune(void* batch, int32_t reps, spcn_batch_config* trials, int32_
   if (!guard.ok) return SPCN_ERR_CUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   // candidates: item sizes (2K-64K chunks) x (phased, interleaved groups of
-  // 16 Mpx); sizes above the largest tile's chunk count are skipped
+  // 16 Mpx, staged); sizes above the largest tile's chunk count are skipped
   u64 max_chunks = 0;
   for (const BatchTile& T : b->tiles) max_chunks = std::max(max_chunks, (u64)T.g.nchunks);
   std::vector<spcn_batch_config> cand;
@@ -1312,6 +1798,11 @@ int spcn_batch_tune(void* batch, int32_t reps, spcn_batch_config* trials, int32_
     c1.schedule = SPCN_SCHED_INTERLEAVED;
     c1.group_px = 16ll << 20;
     cand.push_back(c1);
+    if (max_chunks < (1ull << 32)) {
+      spcn_batch_config c2 = c0;
+      c2.schedule = SPCN_SCHED_STAGED;
+      cand.push_back(c2);
+    }
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   SPCN_CUDA_TRY(cudaEventCreate(&e0));

@@ -132,6 +132,10 @@ constexpr size_t kRadixSmem = kLutSmemBytes + sizeof(unsigned) * kTracks * kRadi
 // the density pass stages one plane of a warp's 512 pixels (2 KB per warp)
 constexpr size_t kDensitySmem = kLutSmemBytes + 2048 * (kPassThreads / 32);
 
+// Constants of the conservative all-white test of a full chunk (pass 1):
+// (AND of its words & wm) == we.
+void white_test_consts(int T, unsigned* wm, unsigned* we);
+
 int configure_pixel_kernels(Context* c);
 int configure_basis_kernels(Context* c);
 int configure_grad_kernels(Context* c);

@@ -65,6 +65,20 @@ def sequential(ctx, tiles, stats, tgt, p):
     return outs, p99
 
 
+# the fused persistent launch and the staged launches, at the default item size
+SCHEDS = ["phased", "staged"]
+
+
+def run_batch(spcn, ctx, tiles, stats, tgt, outs, p, sched):
+    """Create a batch under schedule `sched`, run it once; (p99, status, fallback)."""
+    b = spcn.Batch(ctx, tiles, stats, tgt, outs, p)
+    b.set_config(16 * 1024, sched)
+    b.run()
+    res = b.results(fallback=True)
+    b.close()
+    return res
+
+
 def assert_same(outs, ref_outs, p99, ref_p99):
     for i, (a, b) in enumerate(zip(outs, ref_outs)):
         assert torch.equal(a, b), f"tile {i}: {(a != b).sum().item()} bytes differ"
@@ -79,9 +93,15 @@ def test_batch_equals_sequential_calls(spcn, ctx, setup):
     p99, status = spcn.normalize_batched(ctx, tiles, stats, tgt, outs, p)
     assert status == [0] * len(tiles)
     assert_same(outs, ref_outs, p99, ref_p99)
+    for sched in SCHEDS:
+        outs = [torch.empty_like(t) for t in tiles]
+        p99, status, _ = run_batch(spcn, ctx, tiles, stats, tgt, outs, p, sched)
+        assert status == [0] * len(tiles)
+        assert_same(outs, ref_outs, p99, ref_p99)
 
 
-def test_batch_pitched_tiles(spcn, ctx, setup):
+@pytest.mark.parametrize("sched", SCHEDS)
+def test_batch_pitched_tiles(spcn, ctx, setup, sched):
     # tiles as views into wider buffers at odd byte offsets (generic traversal)
     tiles, stats, tgt, p = setup
     views, outs = [], []
@@ -94,12 +114,13 @@ def test_batch_pitched_tiles(spcn, ctx, setup):
         ob = torch.zeros((h, 3 * w + 19), dtype=torch.uint8, device="cuda")
         outs.append(torch.as_strided(ob, (h, w, 3), (ob.shape[1], 3, 1), storage_offset=3))
     ref_outs, ref_p99 = sequential(ctx, tiles, stats, tgt, p)
-    p99, status = spcn.normalize_batched(ctx, views, stats, tgt, outs, p)
+    p99, status, _ = run_batch(spcn, ctx, views, stats, tgt, outs, p, sched)
     assert_same(outs, ref_outs, p99, ref_p99)
 
 
+@pytest.mark.parametrize("sched", SCHEDS)
 @pytest.mark.parametrize("hint", ["none", "far_low", "far_high", "exact"])
-def test_batch_window_hints(spcn, ctx, setup, hint):
+def test_batch_window_hints(spcn, ctx, setup, hint, sched):
     # no hint or a misleading one sends tiles to the exact fallback; results stay identical
     tiles, stats, tgt, p = setup
     ref_outs, ref_p99 = sequential(ctx, tiles, stats, tgt, p)
@@ -111,10 +132,7 @@ def test_batch_window_hints(spcn, ctx, setup, hint):
         s.p99[0], s.p99[1] = base[0] * f, base[1] * f
         hs.append(s)
     outs = [torch.empty_like(t) for t in tiles]
-    b = spcn.Batch(ctx, tiles, hs, tgt, outs, p)
-    b.run()
-    p99, _, fallback = b.results(fallback=True)
-    b.close()
+    p99, _, fallback = run_batch(spcn, ctx, tiles, hs, tgt, outs, p, sched)
     assert_same(outs, ref_outs, p99, ref_p99)
     # no hint: no window, every tile takes the exact fallback.  With a hint,
     # a tile whose pilot sample holds enough tissue chunks starts its window
@@ -130,7 +148,7 @@ def test_batch_window_hints(spcn, ctx, setup, hint):
 
 @pytest.mark.parametrize("item_chunks,schedule,group_px", [
     (1024, "phased", 0), (8192, "phased", 0), (1024, "interleaved", 200_000),
-    (2048, "interleaved", 1)])
+    (2048, "interleaved", 1), (1024, "staged", 0), (8192, "staged", 0)])
 def test_batch_schedules_and_graph_replay(spcn, ctx, setup, item_chunks, schedule, group_px):
     tiles, stats, tgt, p = setup
     ref_outs, ref_p99 = sequential(ctx, tiles, stats, tgt, p)
@@ -175,7 +193,8 @@ def test_batch_tuner(spcn, ctx, setup):
     b.close()
 
 
-def test_batch_no_tissue_and_list_overflow(spcn, ctx, setup):
+@pytest.mark.parametrize("sched", SCHEDS)
+def test_batch_no_tissue_and_list_overflow(spcn, ctx, setup, sched):
     tiles, stats, tgt, p = setup
     white = torch.full((50, 70, 3), 255, dtype=torch.uint8, device="cuda")
     flat = torch.empty((90, 130, 3), dtype=torch.uint8, device="cuda")
@@ -188,7 +207,7 @@ def test_batch_no_tissue_and_list_overflow(spcn, ctx, setup):
     btiles = [tiles[5], white, flat, tiles[9]]
     bstats = [stats[5], stats[0], st_flat, stats[9]]
     outs = [torch.empty_like(t) for t in btiles]
-    p99, status = spcn.normalize_batched(ctx, btiles, bstats, tgt, outs, p)
+    p99, status, _ = run_batch(spcn, ctx, btiles, bstats, tgt, outs, p, sched)
     assert status == [0, -4, 0, 0]
     ref_w = ctx.normalize(white, stats[0], tgt, p)
     with pytest.raises(spcn.SpcnError) as e:
@@ -227,8 +246,9 @@ def test_batch_rejects_overlapping_output(spcn, ctx, setup):
     assert e.value.kind == "INVALID_ARG"
 
 
+@pytest.mark.parametrize("sched", SCHEDS)
 @pytest.mark.parametrize("thresh", [220, 255])
-def test_batch_white_regions(spcn, ctx, setup, thresh):
+def test_batch_white_regions(spcn, ctx, setup, thresh, sched):
     """Tiles with large white regions (blob background plus painted white
     rectangles) and ragged widths: pass 1 drops all-white chunks and counts
     row-end partial chunks pixel by pixel; at threshold 255 no pixel is white
@@ -254,6 +274,6 @@ def test_batch_white_regions(spcn, ctx, setup, thresh):
     p = spcn.params(white_thresh=thresh)
     ref_outs, ref_p99 = sequential(ctx, tiles, stats, tgt, p)
     outs = [torch.empty_like(t) for t in tiles]
-    p99, status = spcn.normalize_batched(ctx, tiles, stats, tgt, outs, p)
+    p99, status, _ = run_batch(spcn, ctx, tiles, stats, tgt, outs, p, sched)
     assert status == [0] * len(tiles)
     assert_same(outs, ref_outs, p99, ref_p99)
