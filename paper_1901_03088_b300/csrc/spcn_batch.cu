@@ -86,6 +86,8 @@ struct BatchTileState {
   int fallback;            // 1: the percentile needed the exact fallback
   float M[6];              // pass-2 coefficients (recon_coef), set with ready = 1
   int pad2[2];
+  u64 srank[kTracks];      // grid-wide select: each track's rank within its first-digit bin
+  int sbin[kTracks];       // and that bin (-1: the track is not resolved from the lists)
 };
 
 // Run-wide state (zeroed before every run).
@@ -112,6 +114,9 @@ struct BatchArgs {
   const BatchItem* items;
   const Model* models;
   unsigned* hist1;         // per tile and stain: first-digit histogram of listed keys
+  unsigned* hist2;         // grid-wide select: per tile and track, second-digit histogram
+  const BatchItem* p2_items;  // staged pass 2: each block's segments (chunk ranges of one tile),
+  const unsigned* p2_first;   // block b's at [p2_first[b], p2_first[b + 1])
   u64* rhist;
   BatchRunState* run;
   unsigned n_items, n_tiles;
@@ -1281,48 +1286,311 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_sel(BatchArgs a) {
   }
 }
 
-// Pass 2 of every tile whose percentile the lists gave (staged schedule);
-// items from the run's second ticket, the optical-density table reloaded when
-// the model changes.
+// ------------------------------------------------------------ grid-wide select
+// The staged schedule's per-tile select in three launches, so that a large
+// tile's lists are read by the whole grid rather than by one block:
+//   k_sel_first  one block per tile: the ranks, and for each track the bin of
+//                the pass-1 first-digit histogram that holds its rank (tiles
+//                without tissue, or with no rank in the lists, are finished
+//                here); the tile's second-digit histograms zeroed;
+//   k_sel_count  the whole grid: every list in segments of kSelSeg keys,
+//                each key of a track's bin counted in that track's
+//                second-digit histogram (tracks of one stain that share the
+//                bin share the histogram);
+//   k_sel_final  one block per tile: the second digits, the percentiles and
+//                the pass-2 coefficients, exactly as batch_select.
+constexpr int kSelThreads = 512;
+constexpr int kSelSeg = 4096;             // keys per segment of k_sel_count
+static_assert(kSelSeg % (4 * kSelThreads) == 0, "whole vectors per thread");
+constexpr int kGridSelMaxTiles = 1024;    // second-digit histograms: 64 KB per tile
+
+__device__ __forceinline__ void finish_no_tissue(const BatchArgs& a, unsigned tile) {
+  const BatchTile* T = a.tiles + tile;
+  BatchTileState* S = a.state + tile;
+  SelectState* s = &S->sel;
+  S->status = SPCN_ERR_NO_TISSUE;
+  for (int t = 0; t < kTracks; ++t) { s->key[t] = 0; s->resolved[t] = 1; }
+  s->p99[0] = s->p99[1] = 0.0;
+  s->scale[0] = s->scale[1] = 1.0;
+  s->t = 0.0;
+  s->all_resolved = 1;
+  const float hs = a.models[T->model].lasso.hscale;
+  for (int i = 0; i < 6; ++i) S->M[i] = recon_coef(a.Wt, s->scale, hs, i);
+  __threadfence();
+  st_release_s32(&S->ready, 1);
+}
+
+__global__ void __launch_bounds__(kSelThreads) k_sel_first(BatchArgs a) {
+  __shared__ unsigned s_hist[kSelBins];
+  __shared__ u64 s_tmp[33];
+  __shared__ int s_idx;
+  __shared__ u64 s_before;
+  __shared__ int s_bin[kTracks];
+  __shared__ u64 s_rr[kTracks];
+  for (unsigned tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
+    const BatchTile* T = a.tiles + tile;
+    BatchTileState* S = a.state + tile;
+    SelectState* s = &S->sel;
+    const u64 n = __ldcg(&s->n_nw);
+    if (n == 0) {   // uniform across the block
+      if (threadIdx.x == 0) finish_no_tissue(a, tile);
+      __syncthreads();
+      continue;
+    }
+    if (threadIdx.x == 0) {
+      set_ranks(s, n, a.pct);
+      for (int j = 0; j < 2; ++j) { s->lo[j] = T->lo[j]; s->nb[j] = 0u; }
+      for (int t = 0; t < kTracks; ++t) { s_bin[t] = -1; s_rr[t] = s->rank[t]; }
+    }
+    __syncthreads();
+    for (int j = 0; j < 2; ++j) {
+      const u64 cnt = __ldcg(&S->list_n[j]);
+      const u64 below = __ldcg(&s->below[j]);
+      bool in[2];
+      for (int u = 0; u < 2; ++u) {
+        const u64 r = s_rr[2 * j + u];
+        in[u] = T->win[j] && cnt <= T->list_cap && r >= below && r - below < cnt;
+      }
+      if (!in[0] && !in[1]) continue;   // uniform across the block
+      const unsigned* h1 = a.hist1 + ((size_t)tile * 2 + j) * kSelBins;
+      for (int i = threadIdx.x; i < kSelBins; i += blockDim.x) s_hist[i] = __ldcg(h1 + i);
+      __syncthreads();
+      for (int u = 0; u < 2; ++u) {
+        if (!in[u]) continue;
+        smem_find_rank(s_hist, kSelBins, s_rr[2 * j + u] - below, &s_idx, &s_before, s_tmp);
+        if (threadIdx.x == 0 && s_idx >= 0 && s_idx < kSelBins - 1) {
+          s_bin[2 * j + u] = s_idx;
+          s_rr[2 * j + u] = s_rr[2 * j + u] - below - s_before;
+        }
+        __syncthreads();
+      }
+    }
+    // zero the histograms the count will fill (a stain's second track shares
+    // the first one's when both lie in the same bin)
+    for (int t = 0; t < kTracks; ++t) {
+      const bool own = s_bin[t] >= 0 && !((t & 1) && s_bin[t] == s_bin[t - 1]);
+      if (!own) continue;   // uniform
+      unsigned* h2 = a.hist2 + ((size_t)tile * kTracks + t) * kSelBins;
+      for (int i = threadIdx.x; i < kSelBins; i += blockDim.x) h2[i] = 0u;
+    }
+    if (threadIdx.x == 0) {
+      int any = 0;
+      for (int t = 0; t < kTracks; ++t) {
+        S->sbin[t] = s_bin[t];
+        S->srank[t] = s_rr[t];
+        any |= s_bin[t] >= 0;
+        s->resolved[t] = 0;
+      }
+      if (!any) {   // nothing in the lists: the exact fallback
+        s->all_resolved = 0;
+        atomicAdd(&a.run->n_fallback, 1u);
+        __threadfence();
+        st_release_s32(&S->ready, 2);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Pair metadata of k_sel_count, one per (tile, stain).
+struct SelPair {
+  unsigned lo;
+  int b0, b1;      // first-digit bins of the stain's two tracks (-1: none)
+  unsigned n;      // listed keys (0: nothing to count)
+};
+
+__device__ __forceinline__ unsigned sel_segments(unsigned n) {
+  return (n + kSelSeg - 1) / kSelSeg;
+}
+
+// Every list in segments of kSelSeg keys, numbered over all pairs (a block
+// scan gives each pair's first segment); block b takes segments b, b + G, ...
+// and finds a segment's pair by binary search.
+__global__ void __launch_bounds__(kSelThreads) k_sel_count(BatchArgs a) {
+  extern __shared__ __align__(16) char s_dyn[];
+  const unsigned np = 2 * a.n_tiles;
+  SelPair* s_pair = reinterpret_cast<SelPair*>(s_dyn);
+  unsigned* s_seg = reinterpret_cast<unsigned*>(s_pair + np);   // np + 1 entries
+  __shared__ u64 s_tmp[33];
+  const unsigned per = (np + blockDim.x - 1) / blockDim.x;
+  const unsigned p0 = min(np, threadIdx.x * per), p1 = min(np, p0 + per);
+  unsigned local = 0;
+  for (unsigned p = p0; p < p1; ++p) {
+    const unsigned tile = p >> 1, j = p & 1u;
+    const BatchTileState* S = a.state + tile;
+    SelPair sp;
+    sp.lo = a.tiles[tile].lo[j];
+    sp.b0 = __ldcg(&S->sbin[2 * j]);
+    sp.b1 = __ldcg(&S->sbin[2 * j + 1]);
+    const u64 cnt = __ldcg(&S->list_n[j]);
+    sp.n = (__ldcg(&S->ready) == 0 && (sp.b0 >= 0 || sp.b1 >= 0)) ? (unsigned)cnt : 0u;
+    s_pair[p] = sp;
+    local += sel_segments(sp.n);
+  }
+  u64 total = 0;
+  unsigned run = (unsigned)block_excl_scan((u64)local, s_tmp, &total);
+  for (unsigned p = p0; p < p1; ++p) {
+    s_seg[p] = run;
+    run += sel_segments(s_pair[p].n);
+  }
+  if (threadIdx.x == 0) s_seg[np] = (unsigned)total;
+  __syncthreads();
+  for (unsigned gs = blockIdx.x; gs < (unsigned)total; gs += gridDim.x) {
+    // the pair: the last p with s_seg[p] <= gs (it holds segments)
+    unsigned lo = 0u, hi = np;   // s_seg[lo] <= gs < s_seg[hi]
+    while (hi - lo > 1u) {
+      const unsigned mid = (lo + hi) >> 1;
+      if (s_seg[mid] <= gs) lo = mid; else hi = mid;
+    }
+    const unsigned p = lo, k = gs - s_seg[p];
+    const SelPair sp = s_pair[p];
+    const unsigned tile = p >> 1, j = p & 1u;
+    const unsigned* list = a.tiles[tile].keys + (u64)j * a.tiles[tile].list_cap;
+    unsigned* h0 = a.hist2 + ((size_t)tile * kTracks + 2 * j) * kSelBins;
+    unsigned* h1 = (sp.b1 >= 0 && sp.b1 != sp.b0) ? h0 + kSelBins : h0;
+    auto count = [&](unsigned key) {
+      const unsigned d = key - sp.lo;
+      const int hb = (int)min(d >> kSelBits, (unsigned)(kSelBins - 1));
+      const unsigned low = d & (kSelBins - 1);
+      if (hb == sp.b0) red_add_u32(h0 + low, 1u);
+      else if (hb == sp.b1) red_add_u32(h1 + low, 1u);
+    };
+    // the segment's keys as 16-byte vectors (lists and segments start on
+    // 16-byte boundaries), every load issued before the counting; a last
+    // partial vector key by key
+    const unsigned i0 = k * kSelSeg, i1 = min(sp.n, i0 + kSelSeg);
+    const uint4* v = reinterpret_cast<const uint4*>(list + i0);
+    const unsigned nv = (i1 - i0) / 4;
+    constexpr int kVec = kSelSeg / 4 / kSelThreads;   // vectors per thread
+    uint4 x[kVec];
+#pragma unroll
+    for (int r = 0; r < kVec; ++r) {
+      const unsigned vi = threadIdx.x + (unsigned)r * blockDim.x;
+      x[r] = vi < nv ? __ldcg(v + vi) : make_uint4(0u, 0u, 0u, 0u);
+    }
+#pragma unroll
+    for (int r = 0; r < kVec; ++r) {
+      if (threadIdx.x + (unsigned)r * blockDim.x < nv) {
+        count(x[r].x); count(x[r].y); count(x[r].z); count(x[r].w);
+      }
+    }
+    for (unsigned i = i0 + 4 * nv + threadIdx.x; i < i1; i += blockDim.x) count(__ldcg(list + i));
+  }
+}
+
+__global__ void __launch_bounds__(kSelThreads) k_sel_final(BatchArgs a) {
+  __shared__ unsigned s_hist[kSelBins];
+  __shared__ u64 s_tmp[33];
+  __shared__ int s_idx;
+  __shared__ u64 s_before;
+  __shared__ int s_res[kTracks];
+  for (unsigned tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
+    const BatchTile* T = a.tiles + tile;
+    BatchTileState* S = a.state + tile;
+    SelectState* s = &S->sel;
+    if (__ldcg(&S->ready) != 0) continue;   // finished by k_sel_first (uniform)
+    if (threadIdx.x < kTracks) s_res[threadIdx.x] = 0;
+    for (int t = 0; t < kTracks; ++t) {
+      const int bin = __ldcg(&S->sbin[t]);
+      if (bin < 0) continue;   // uniform
+      const int src = ((t & 1) && bin == __ldcg(&S->sbin[t - 1])) ? t - 1 : t;
+      const unsigned* h2 = a.hist2 + ((size_t)tile * kTracks + src) * kSelBins;
+      __syncthreads();
+      for (int i = threadIdx.x; i < kSelBins; i += blockDim.x) s_hist[i] = __ldcg(h2 + i);
+      __syncthreads();
+      smem_find_rank(s_hist, kSelBins, __ldcg(&S->srank[t]), &s_idx, &s_before, s_tmp);
+      if (threadIdx.x == 0 && s_idx >= 0) {
+        s->key[t] = T->lo[t >> 1] + ((unsigned)bin << kSelBits) + (unsigned)s_idx;
+        s_res[t] = 1;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int all = 1;
+      for (int t = 0; t < kTracks; ++t) { s->resolved[t] = s_res[t]; all &= s_res[t]; }
+      if (all) {
+        const float hs = a.models[T->model].lasso.hscale;
+        finish_percentiles(s, a.tgt0, a.tgt1, hs);
+        for (int i = 0; i < 6; ++i) S->M[i] = recon_coef(a.Wt, s->scale, hs, i);
+      }
+      s->all_resolved = all;
+      if (!all) atomicAdd(&a.run->n_fallback, 1u);
+      __threadfence();
+      st_release_s32(&S->ready, all ? 1 : 2);
+    }
+    __syncthreads();
+  }
+}
+
+// Pass 2 of every tile whose percentile the lists gave (staged schedule).
+// The work per chunk is the same everywhere, so the chunks of all tiles (the
+// tiles in table order) are split into equal contiguous shares, one per
+// block, each a short list of segments (chunk ranges of one tile) built when
+// the batch is created: a block crosses few tile boundaries, loads a table
+// when the model changes and streams its share without waits between items.  For batches of
+// at most kP2PreloadTiles tiles every tile's coefficients are read into
+// shared memory once.
+struct P2Tile {
+  float M[6];
+  int go;          // 1: the percentile is known (else the exact fallback finishes the tile)
+};
+constexpr int kP2PreloadTiles = 2048;
+constexpr size_t kP2Smem = kLutSmemBytes + sizeof(P2Tile) * kP2PreloadTiles;
+
 template <class G>
 __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_p2(BatchArgs a) {
   extern __shared__ __align__(16) char s_dyn[];
   char* lut = s_dyn;
-  __shared__ BatchItem s_item;
-  __shared__ float s_M[6];
-  __shared__ int s_go;
-  int cur_model = -1;
-  unsigned t_next = 0u;   // thread 0: tickets claimed one item ahead
-  if (threadIdx.x == 0) t_next = atomicAdd(&a.run->next2, 1u);
+  P2Tile* s_tiles = reinterpret_cast<P2Tile*>(s_dyn + kLutSmemBytes);
+  __shared__ __align__(16) BatchItem s_items[2];   // current segment and the prefetched next one
+  __shared__ P2Tile s_one;                          // the current tile's, without preloading
+  const bool pre = a.n_tiles <= (unsigned)kP2PreloadTiles;
+  int cur_model = -1, cur = 0;
+  // thread 0 walks the block's segments, copying the next descriptor into
+  // shared memory one segment ahead
+  unsigned i_next = 0u, i_end = 0u;
+  if (threadIdx.x == 0) {
+    i_next = a.p2_first[blockIdx.x];
+    i_end = a.p2_first[blockIdx.x + 1];
+    if (i_next < i_end) copy_item_async(&s_items[1], a.p2_items + i_next++);
+    else s_items[1].tile = ~0u;
+  }
+  if (pre) {
+    for (unsigned t = threadIdx.x; t < a.n_tiles; t += blockDim.x) {
+      const BatchTileState* S = a.state + t;
+      P2Tile pt;
+      pt.go = __ldcg(&S->ready) == 1;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) pt.M[i] = pt.go ? __ldcg(&S->M[i]) : 0.f;
+      s_tiles[t] = pt;
+    }
+  }
   for (;;) {
+    cur ^= 1;
     if (threadIdx.x == 0) {
-      BatchItem it{};
-      it.tile = ~0u;
-      if (t_next < a.n_items) {
-        it = a.items[t_next];
-        t_next = atomicAdd(&a.run->next2, 1u);
+      cp_async_wait_all();
+      BatchItem* nx = &s_items[cur ^ 1];   // read by nobody until the next loop top
+      const unsigned tile = s_items[cur].tile;
+      if (tile != ~0u && i_next < i_end) copy_item_async(nx, a.p2_items + i_next++);
+      else nx->tile = ~0u;
+      if (!pre && tile != ~0u) {
+        const BatchTileState* S = a.state + tile;
+        s_one.go = __ldcg(&S->ready) == 1;
+        for (int i = 0; i < 6; ++i) s_one.M[i] = s_one.go ? __ldcg(&S->M[i]) : 0.f;
       }
-      int go = 0;
-      if (it.tile != ~0u) {
-        const BatchTileState* S = a.state + it.tile;
-        go = __ldcg(&S->ready) == 1;
-        if (go)
-          for (int i = 0; i < 6; ++i) s_M[i] = __ldcg(&S->M[i]);
-      }
-      s_item = it;
-      s_go = go;
     }
     __syncthreads();
-    const BatchItem item = s_item;
+    const BatchItem item = s_items[cur];
     if (item.tile == ~0u) break;
-    if (s_go) {
+    const P2Tile* pt = pre ? s_tiles + item.tile : &s_one;
+    if (pt->go) {
       if ((int)item.model != cur_model) {
         load_od_lut(a.models + item.model, lut);   // ends with a block barrier
         cur_model = (int)item.model;
       }
-      batch_pass2<G>(a, item.tile, item.c0, item.c1, lut, s_M);
+      batch_pass2<G>(a, item.tile, item.c0, item.c1, lut, pt->M);
     }
-    __syncthreads();   // the item is done: shared words and the table may be rewritten
+    __syncthreads();   // the segment is done: shared words and the table may be rewritten
   }
 }
 
@@ -1341,6 +1609,9 @@ struct Batch {
   char* d_state = nullptr;       // BatchRunState, then n BatchTileState
   size_t state_bytes = 0;
   unsigned* keys = nullptr;
+  unsigned* hist2 = nullptr;     // grid-wide select (batches of at most kGridSelMaxTiles)
+  BatchItem* p2_items = nullptr; // staged pass 2: each block's segments
+  unsigned* p2_first = nullptr;
   u64* rhist = nullptr;
   int grid = 0;
   int grid_p1 = 0, grid_p2 = 0, grid_sel = 0;   // staged schedule
@@ -1369,12 +1640,12 @@ static int configure_staged_kernels(Context* c, int* grid_p1, int* grid_p2) {
   SPCN_CUDA_TRY(cudaFuncSetAttribute(k_batch_p1<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)kStagedSmem));
   SPCN_CUDA_TRY(cudaFuncSetAttribute(k_batch_p2<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kLutSmemBytes));
+                                     (int)kP2Smem));
   int o1 = 0, o2 = 0;
   SPCN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_batch_p1<G>, kBatchThreads,
                                                               kStagedSmem));
   SPCN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, k_batch_p2<G>, kBatchThreads,
-                                                              kLutSmemBytes));
+                                                              kP2Smem));
   if (o1 < 1 || o2 < 1) return SPCN_ERR_CUDA;
   *grid_p1 = c->num_sms * o1;
   *grid_p2 = c->num_sms * o2;
@@ -1389,6 +1660,24 @@ static bool config_ok(const spcn_batch_config* cfg) {
     return false;
   if (cfg->schedule == SPCN_SCHED_INTERLEAVED && cfg->group_px < 1) return false;
   return true;
+}
+
+// Tiles grouped by table (tables in the order of their largest tile), largest
+// first within a table.
+static std::vector<int> table_order(const Batch* b) {
+  std::vector<int> order(b->n);
+  for (int t = 0; t < b->n; ++t) order[t] = t;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    return b->tiles[x].g.npx > b->tiles[y].g.npx;
+  });
+  std::vector<int> rank(b->n_models, -1), order2 = order;
+  int r = 0;
+  for (int t : order)
+    if (rank[b->tiles[t].model] < 0) rank[b->tiles[t].model] = r++;
+  std::stable_sort(order2.begin(), order2.end(), [&](int x, int y) {
+    return rank[b->tiles[x].model] < rank[b->tiles[y].model];
+  });
+  return order2;
 }
 
 // Work queue of a schedule.  Every pass-1 item of a tile precedes the tile's
@@ -1415,19 +1704,14 @@ static void build_items(const Batch* b, const spcn_batch_config& cfg, std::vecto
   if (cfg.schedule == SPCN_SCHED_PHASED || cfg.schedule == SPCN_SCHED_STAGED) {
     // pass 2 needs no particular order: tiles sharing a table go together
     // (fewer table reloads), largest first within a table
-    std::vector<int> rank(b->n_models, -1), order2 = order;
-    int r = 0;
-    for (int t : order)
-      if (rank[b->tiles[t].model] < 0) rank[b->tiles[t].model] = r++;
-    std::stable_sort(order2.begin(), order2.end(), [&](int x, int y) {
-      return rank[b->tiles[x].model] < rank[b->tiles[y].model];
-    });
+    const std::vector<int> order2 = table_order(b);
     if (cfg.schedule == SPCN_SCHED_STAGED) {
-      // one list of chunk ranges, read by both passes, the tiles of one table
-      // together (the staged pass 1 also reloads its table per model).  Item
+      // pass-1 chunk ranges (pass 2 splits the chunks statically), the tiles
+      // of one table together (the staged pass 1 reloads its table per
+      // model).  Item
       // sizes are guided: item_chunks while the rest of the list holds more
       // than two such items per block of the pass-1 grid, then the rest
-      // divided by twice the blocks (at least 1024 chunks), so the blocks
+      // divided by twice the blocks (at least 4096 chunks), so the blocks
       // finish each pass together
       const u64 blocks2 = 2 * (u64)std::max(1, b->grid_p1);
       u64 rest = 0;
@@ -1436,7 +1720,7 @@ static void build_items(const Batch* b, const spcn_batch_config& cfg, std::vecto
         const u64 nch = b->tiles[t].g.nchunks;
         u64 c0 = 0;
         while (c0 < nch) {
-          const u64 guided = std::max<u64>(1024, rest / blocks2);
+          const u64 guided = std::max<u64>(4096, rest / blocks2);
           const u64 size = std::min<u64>(S, guided);
           const u64 c1 = std::min(nch, c0 + size);
           out->push_back({(unsigned)t, 1u, b->tiles[t].model, 0u, c0, c1});
@@ -1500,7 +1784,8 @@ static int apply_config(Batch* b, const spcn_batch_config& cfg) {
 }
 
 static void batch_free(Batch* b) {
-  void* ptrs[] = {b->models, b->d_tiles, b->d_items, b->d_state, b->keys, b->rhist};
+  void* ptrs[] = {b->models, b->d_tiles, b->d_items, b->d_state, b->keys, b->hist2,
+                  b->p2_items, b->p2_first, b->rhist};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete b;
@@ -1546,12 +1831,23 @@ static int batch_launch(Batch* b, cudaStream_t st) {
       else
         k_batch_p1<Geometry><<<b->grid_p1, kBatchThreads, kStagedSmem, st>>>(b->args);
       ++launched;
-      k_batch_sel<<<b->grid_sel, kBatchThreads, kSelectSmem, st>>>(b->args);
-      ++launched;
+      if (b->hist2) {
+        k_sel_first<<<b->grid_sel, kSelThreads, 0, st>>>(b->args);
+        k_sel_count<<<2 * c->num_sms, kSelThreads,
+                      (sizeof(SelPair) + sizeof(unsigned)) * 2 * b->n + sizeof(unsigned), st>>>(
+            b->args);
+        k_sel_final<<<b->grid_sel, kSelThreads, 0, st>>>(b->args);
+        launched += 3;
+      } else {
+        k_batch_sel<<<b->grid_sel, kBatchThreads, kSelectSmem, st>>>(b->args);
+        ++launched;
+      }
+      const size_t p2_smem =
+          kLutSmemBytes + (b->n <= kP2PreloadTiles ? sizeof(P2Tile) * (size_t)b->n : 0);
       if (b->flat)
-        k_batch_p2<FlatGeometry><<<b->grid_p2, kBatchThreads, kLutSmemBytes, st>>>(b->args);
+        k_batch_p2<FlatGeometry><<<b->grid_p2, kBatchThreads, p2_smem, st>>>(b->args);
       else
-        k_batch_p2<Geometry><<<b->grid_p2, kBatchThreads, kLutSmemBytes, st>>>(b->args);
+        k_batch_p2<Geometry><<<b->grid_p2, kBatchThreads, p2_smem, st>>>(b->args);
       ++launched;
       const cudaError_t e0 = cudaGetLastError();
       if (e0 != cudaSuccess) return e0;
@@ -1637,6 +1933,9 @@ static int batch_create(Context* c, int n, const spcn_image* tiles, const spcn_s
   for (BatchTile& T : b->tiles) T.keys = b->keys + reinterpret_cast<uintptr_t>(T.keys);
   if (cudaMalloc(&b->rhist, sizeof(u64) * 3 * kTracks * kRadixBins) != cudaSuccess)
     return fail(SPCN_ERR_OOM);
+  if (n <= kGridSelMaxTiles &&
+      cudaMalloc(&b->hist2, sizeof(unsigned) * kTracks * kSelBins * (size_t)n) != cudaSuccess)
+    return fail(SPCN_ERR_OOM);
   for (size_t k = 0; k < rep.size(); ++k) {
     rc = launch_build_model(c, b->models + k, tile_stats[rep[k]].W, tile_stats[rep[k]].i0,
                             params->lambda, nullptr, nullptr);
@@ -1654,11 +1953,48 @@ static int batch_create(Context* c, int n, const spcn_image* tiles, const spcn_s
                : configure_staged_kernels<Geometry>(c, &b->grid_p1, &b->grid_p2);
   if (rc) return fail(rc);
   b->grid_sel = std::min(n, 4 * c->num_sms);
+  {
+    // staged pass 2: the chunks of all tiles (in table order) in equal
+    // contiguous shares, one per block, each cut at tile boundaries into
+    // segments
+    const std::vector<int> ord = table_order(b);
+    u64 total = 0;
+    for (int t : ord) total += b->tiles[t].g.nchunks;
+    std::vector<BatchItem> segs;
+    std::vector<unsigned> first(b->grid_p2 + 1);
+    size_t k = 0;
+    u64 tile0 = 0;   // first chunk of tile ord[k] in the order
+    for (int blk = 0; blk < b->grid_p2; ++blk) {
+      first[blk] = (unsigned)segs.size();
+      u64 c = total * (u64)blk / (u64)b->grid_p2;
+      const u64 e = total * (u64)(blk + 1) / (u64)b->grid_p2;
+      while (c < e) {
+        while (tile0 + b->tiles[ord[k]].g.nchunks <= c) tile0 += b->tiles[ord[k++]].g.nchunks;
+        const BatchTile& T = b->tiles[ord[k]];
+        const u64 stop = std::min(e, tile0 + T.g.nchunks);
+        segs.push_back({(unsigned)ord[k], 2u, T.model, 0u, c - tile0, stop - tile0});
+        c = stop;
+      }
+    }
+    first[b->grid_p2] = (unsigned)segs.size();
+    if (cudaMalloc(&b->p2_items, sizeof(BatchItem) * std::max<size_t>(1, segs.size())) !=
+            cudaSuccess ||
+        cudaMalloc(&b->p2_first, sizeof(unsigned) * first.size()) != cudaSuccess)
+      return fail(SPCN_ERR_OOM);
+    if ((!segs.empty() && cudaMemcpy(b->p2_items, segs.data(), sizeof(BatchItem) * segs.size(),
+                                     cudaMemcpyHostToDevice) != cudaSuccess) ||
+        cudaMemcpy(b->p2_first, first.data(), sizeof(unsigned) * first.size(),
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail(SPCN_ERR_CUDA);
+  }
   BatchArgs& a = b->args;
   a.tiles = b->d_tiles;
   a.state = reinterpret_cast<BatchTileState*>(b->d_state + kRunStateBytes);
   a.hist1 = reinterpret_cast<unsigned*>(b->d_state + kRunStateBytes +
                                         sizeof(BatchTileState) * (size_t)n);
+  a.hist2 = b->hist2;
+  a.p2_items = b->p2_items;
+  a.p2_first = b->p2_first;
   a.run = reinterpret_cast<BatchRunState*>(b->d_state);
   a.models = b->models;
   a.rhist = b->rhist;

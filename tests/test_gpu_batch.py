@@ -239,6 +239,28 @@ def test_batch_against_oracle(spcn, ctx, setup):
             assert abs(p99[k][j] - p_src[j]) <= 1e-5 * max(p_src[j], 1e-30)
 
 
+def test_batch_many_tiles(spcn, ctx, setup):
+    """More tiles than the grid-wide select (1024) and pass 2's preloaded
+    tile table (2048) take: the staged schedule's percentiles then come from
+    one block per tile and pass 2 reads each item's tile state.  Small tiles
+    of every shape; bit-identical to sequential calls."""
+    _, slide_stats, tgt, p = setup
+    g = torch.Generator(device="cpu")
+    g.manual_seed(5)
+    tiles, stats = [], []
+    for k in range(2100):
+        h = int(torch.randint(8, 48, (1,), generator=g))
+        w = int(torch.randint(8, 48, (1,), generator=g))
+        tiles.append(synth.make_image_torch(h, w, 9000 + k, W=synth.stain_basis(2000 + k % 4),
+                                            device="cuda", blobs=False))
+        stats.append(slide_stats[k % 4])
+    ref_outs, ref_p99 = sequential(ctx, tiles, stats, tgt, p)
+    outs = [torch.empty_like(t) for t in tiles]
+    p99, status, _ = run_batch(spcn, ctx, tiles, stats, tgt, outs, p, "staged")
+    assert status == [0] * len(tiles)
+    assert_same(outs, ref_outs, p99, ref_p99)
+
+
 def test_batch_rejects_overlapping_output(spcn, ctx, setup):
     tiles, stats, tgt, p = setup
     with pytest.raises(spcn.SpcnError) as e:
