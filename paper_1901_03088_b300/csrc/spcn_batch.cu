@@ -429,9 +429,10 @@ __device__ void batch_select(const BatchArgs& a, unsigned tile, unsigned* s_hist
 // the tile itself: one chunk from each of kPilotChunks equal strata of the
 // tile's chunk range (every chunk of a smaller tile), the keys of their
 // non-white pixels, and the key at the sample quantile q = p - delta, with
-// p = pct / 100 and delta = 4 sqrt(p (1 - p) / u), u = the sampled chunks that
-// hold a non-white pixel (pixels of one chunk are not independent, so chunks
-// are the units).  The tile's own percentile lies at or above that key
+// p = pct / 100 and delta four standard deviations of the sample proportion,
+// the variance taken from the sample's own between-chunk spread (a cluster
+// sample: pixels of one chunk are not independent; see the design effect
+// below), per stain.  The tile's own percentile lies at or above that key
 // unless the sample is off by four standard deviations; a rank below the
 // window start leaves the tile to the exact fallback, so the start changes
 // the speed, never the result.  A stain without a hint keeps no window (the
@@ -491,8 +492,9 @@ __global__ void __launch_bounds__(kPilotThreads) k_batch_pilot(PilotArgs a) {
     const Lasso L = m->lasso;
     const u64 nch = g.nchunks;
     const unsigned ms = (unsigned)(nch < (u64)kPilotChunks ? nch : (u64)kPilotChunks);
-    // every non-white pixel of the sample: f(key1, key2)
-    auto visit = [&](auto&& f) -> unsigned {
+    // every non-white pixel of the sample: f(key1, key2), then end() after
+    // each sampled chunk
+    auto visit = [&](auto&& f, auto&& end) -> unsigned {
       unsigned units = 0u;
       for (unsigned i = threadIdx.x; i < ms; i += blockDim.x) {
         u64 q = i;
@@ -514,17 +516,19 @@ __global__ void __launch_bounds__(kPilotThreads) k_batch_pilot(PilotArgs a) {
           f(__float_as_uint(h1), __float_as_uint(h2));
           any = true;
         }
+        end();
         units += any ? 1u : 0u;
       }
       return units;
     };
+    auto none = [] {};
     for (int i = threadIdx.x; i < 2 * kPilotBins; i += blockDim.x) (&s_hist[0][0])[i] = 0u;
     __syncthreads();
     // level 1: bits 31-21 of the keys (densities are >= 0: the sign bit is 0)
     const unsigned my_units = visit([&](unsigned k1, unsigned k2) {
       atomicAdd(&s_hist[0][k1 >> 21], 1u);
       atomicAdd(&s_hist[1][k2 >> 21], 1u);
-    });
+    }, none);
     u64 units = 0;
     block_excl_scan((u64)my_units, s_tmp, &units);
     u64 nw = 0;
@@ -533,12 +537,64 @@ __global__ void __launch_bounds__(kPilotThreads) k_batch_pilot(PilotArgs a) {
       for (int i = threadIdx.x; i < kPilotBins; i += blockDim.x) part += s_hist[0][i];
       block_excl_scan(part, s_tmp, &nw);
     }
+    // The margin delta = 4 sigma of the sample quantile, from the sample's own
+    // between-chunk variance (pixels of one chunk are not independent): at
+    // a provisional threshold t (the level-1 bin of the sample's percentile),
+    // a_i = pixels of chunk i at or above t, m_i = its non-white pixels, p^ =
+    // sum a / sum m, and the ratio estimator's variance sum (a_i - p^ m_i)^2
+    // / (u (u - 1) mbar^2) over p^ (1 - p^) / sum m is the design effect d,
+    // clamped to [1, 16] (independent pixels .. whole chunks as units); then
+    // sigma^2 = d p (1 - p) / sum m.  Without an estimate (p^ of 0 or 1) the
+    // chunks are the units: sigma^2 = p (1 - p) / u.
+    if (threadIdx.x == 0) s_r[0] = nw > 0 ? (u64)floor(a.pct / 100.0 * (double)(nw - 1)) : 0;
+    __syncthreads();
+    for (int j = 0; j < 2; ++j) {
+      smem_find_rank(s_hist[j], kPilotBins, s_r[0], &s_idx, &s_before, s_tmp);
+      if (threadIdx.x == 0) s_b1[j] = (unsigned)max(s_idx, 0) << 21;
+      __syncthreads();
+    }
+    const unsigned t0 = s_b1[0], t1 = s_b1[1];
+    unsigned cm = 0u, ca0 = 0u, ca1 = 0u;   // the current chunk's counts
+    u64 sm = 0, smm = 0, sa0 = 0, saa0 = 0, sam0 = 0, sa1 = 0, saa1 = 0, sam1 = 0;
+    visit([&](unsigned k1, unsigned k2) {
+      ++cm;
+      ca0 += k1 >= t0 ? 1u : 0u;
+      ca1 += k2 >= t1 ? 1u : 0u;
+    }, [&] {
+      sm += cm; smm += (u64)cm * cm;
+      sa0 += ca0; saa0 += (u64)ca0 * ca0; sam0 += (u64)ca0 * cm;
+      sa1 += ca1; saa1 += (u64)ca1 * ca1; sam1 += (u64)ca1 * cm;
+      cm = ca0 = ca1 = 0u;
+    });
+    sm = block_sum(sm, s_tmp);
+    smm = block_sum(smm, s_tmp);
+    sa0 = block_sum(sa0, s_tmp);
+    saa0 = block_sum(saa0, s_tmp);
+    sam0 = block_sum(sam0, s_tmp);
+    sa1 = block_sum(sa1, s_tmp);
+    saa1 = block_sum(saa1, s_tmp);
+    sam1 = block_sum(sam1, s_tmp);
     if (threadIdx.x == 0) {
       const double p = a.pct / 100.0;
-      const double q = p - 4.0 * sqrt(p * (1.0 - p) / (double)(units > 0 ? units : 1));
-      s_use = units >= (u64)kPilotMinUnits && q > 0.0 && nw > 0;
-      const u64 r = s_use ? (u64)floor(q * (double)(nw - 1)) : 0;
-      s_r[0] = s_r[1] = r;
+      const double M = (double)sm, U = (double)units;
+      const u64 SA[2] = {sa0, sa1}, SAA[2] = {saa0, saa1}, SAM[2] = {sam0, sam1};
+      int use = units >= (u64)kPilotMinUnits && nw > 0;
+      for (int j = 0; j < 2; ++j) {
+        double var = p * (1.0 - p) / (U > 0.0 ? U : 1.0);   // chunks as units
+        const double ph = M > 0.0 ? (double)SA[j] / M : 0.0;
+        if (units >= 2 && ph > 0.0 && ph < 1.0) {
+          const double mbar = M / U;
+          const double ss = (double)SAA[j] - 2.0 * ph * (double)SAM[j] + ph * ph * (double)smm;
+          const double v = ss / (U * (U - 1.0) * mbar * mbar);
+          double d = v / (ph * (1.0 - ph) / M);
+          d = d < 1.0 ? 1.0 : (d > (double)kChunk ? (double)kChunk : d);
+          var = d * p * (1.0 - p) / M;
+        }
+        const double q = p - 4.0 * sqrt(var);
+        use = use && q > 0.0;
+        s_r[j] = q > 0.0 && nw > 0 ? (u64)floor(q * (double)(nw - 1)) : 0;
+      }
+      s_use = use;
     }
     __syncthreads();
     if (s_use) {
@@ -557,7 +613,7 @@ __global__ void __launch_bounds__(kPilotThreads) k_batch_pilot(PilotArgs a) {
       visit([&](unsigned k1, unsigned k2) {
         if ((k1 >> 21) == b10) atomicAdd(&s_hist[0][(k1 >> 10) & (kPilotBins - 1)], 1u);
         if ((k2 >> 21) == b11) atomicAdd(&s_hist[1][(k2 >> 10) & (kPilotBins - 1)], 1u);
-      });
+      }, none);
       __syncthreads();
       for (int j = 0; j < 2; ++j) {
         smem_find_rank(s_hist[j], kPilotBins, s_r[j], &s_idx, &s_before, s_tmp);
@@ -1120,7 +1176,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_p1(BatchArgs a) {
       reinterpret_cast<unsigned*>(stk + sizeof(uint4) * 3 * kChunkStack * kWarps) +
       warp * kChunkStack;
   unsigned* s_kb = reinterpret_cast<unsigned*>(stk + kStagedStackBytes) + warp * 2 * kStagedKeyBuf;
-  __shared__ BatchItem s_item;
+  __shared__ __align__(16) BatchItem s_items[2];   // current item and the prefetched next one
   __shared__ unsigned s_piece;
   __shared__ StagedTile s_t;
   __shared__ G s_g;
@@ -1198,25 +1254,34 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_p1(BatchArgs a) {
     staged_flush_keys(s_kb, kc0, kc1, s_t);
     staged_counts(s_t.sel, c_nw, c_b0, c_b1);
   };
-  // thread 0 claims tickets one item ahead: the atomic's latency overlaps the
-  // current item
+  // thread 0 runs the queue one item ahead: the next item's descriptor is
+  // copied into shared memory asynchronously (cp.async) and the ticket of the
+  // one after it is in flight while the block works
   unsigned t_next = 0u;
-  if (threadIdx.x == 0) t_next = atomicAdd(&a.run->next, 1u);
+  int cur = 0;
+  if (threadIdx.x == 0) {
+    const unsigned t1 = atomicAdd(&a.run->next, 1u);
+    if (t1 < a.n_items) copy_item_async(&s_items[1], a.items + t1);
+    else s_items[1].tile = ~0u;
+    t_next = atomicAdd(&a.run->next, 1u);
+  }
   for (;;) {
+    cur ^= 1;
     if (threadIdx.x == 0) {
-      BatchItem it{};
-      it.tile = ~0u;
-      if (t_next < a.n_items) {
-        it = a.items[t_next];
+      cp_async_wait_all();
+      BatchItem* nx = &s_items[cur ^ 1];   // read by nobody until the next loop top
+      if (s_items[cur].tile != ~0u && t_next < a.n_items) {
+        copy_item_async(nx, a.items + t_next);
         t_next = atomicAdd(&a.run->next, 1u);
+      } else {
+        nx->tile = ~0u;
       }
-      s_item = it;
       s_piece = 0u;
     }
     __syncthreads();
-    const unsigned tile = s_item.tile;
-    const u64 c0 = s_item.c0, c1 = s_item.c1;
-    const unsigned model = s_item.model;
+    const unsigned tile = s_items[cur].tile;
+    const u64 c0 = s_items[cur].c0, c1 = s_items[cur].c1;
+    const unsigned model = s_items[cur].model;
     if ((int)tile != cur_tile && cur_tile >= 0) flush_tile();
     if (tile == ~0u) break;
     if ((int)tile != cur_tile) {
@@ -1272,7 +1337,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_p1(BatchArgs a) {
         staged_queue(dpart, (unsigned)q, s_queue, qn, s_g, lut, lr, s_L, s_t, s_kb, kc0, kc1);
     }
     staged_counts(s_t.sel, c_nw, c_b0, c_b1);
-    __syncthreads();   // the item is done: s_item and s_piece may be rewritten
+    __syncthreads();   // the item is done: s_items and s_piece may be rewritten
   }
 }
 
