@@ -454,11 +454,12 @@ struct PilotArgs {
   double pct;
 };
 
-// The H-step of one pixel with the table read from global memory: the
-// arithmetic of solve_one, so the same keys.
-__device__ __forceinline__ void solve_global(const float2* proj, unsigned r, unsigned g,
+// The H-step of one pixel from an unreplicated copy of the projected table
+// (channel-major, 256 entries each): the arithmetic of solve_one, so the same
+// keys.
+__device__ __forceinline__ void solve_table(const float2* proj, unsigned r, unsigned g,
                                              unsigned b, const Lasso& L, float& h1, float& h2) {
-  const float2 eR = __ldg(proj + r), eG = __ldg(proj + 256 + g), eB = __ldg(proj + 512 + b);
+  const float2 eR = proj[r], eG = proj[256 + g], eB = proj[512 + b];
   const float D1 = add_sat(eR.x + eG.x, eB.x);
   const float D2 = add_sat(eR.y + eG.y, eB.y);
   const float t1 = mul_sat(L.kappa, fmaf(L.nrho1, D2, D1));
@@ -477,8 +478,33 @@ __device__ __forceinline__ unsigned pilot_hash(unsigned t, unsigned i) {
   return h;
 }
 
+// Block-wide sums of eight per-thread counts at once (one barrier round);
+// every thread receives the totals.
+__device__ __forceinline__ void block_sum8(u64 (&v)[8], u64 (*s_part)[8]) {
+  const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xFFFFFFFFu, v[i], o);
+  }
+  __syncthreads();   // s_part is free
+  if (lane == 0) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s_part[warp][i] = v[i];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    u64 t = 0;
+    for (unsigned w = 0; w < (blockDim.x >> 5); ++w) t += s_part[w][i];
+    v[i] = t;
+  }
+}
+
 __global__ void __launch_bounds__(kPilotThreads) k_batch_pilot(PilotArgs a) {
   __shared__ unsigned s_hist[2][kPilotBins];
+  __shared__ float2 s_proj[kLutEntries];          // the tile's projected table
+  __shared__ u64 s_part[kPilotThreads / 32][8];
   __shared__ u64 s_tmp[33];
   __shared__ int s_idx;
   __shared__ u64 s_before;
@@ -490,6 +516,9 @@ __global__ void __launch_bounds__(kPilotThreads) k_batch_pilot(PilotArgs a) {
     const Geometry g = T->g;
     const Model* m = a.models + T->model;
     const Lasso L = m->lasso;
+    __syncthreads();   // the previous tile's table is no longer read
+    for (int i = threadIdx.x; i < kLutEntries; i += blockDim.x) s_proj[i] = m->proj[i];
+    __syncthreads();
     const u64 nch = g.nchunks;
     const unsigned ms = (unsigned)(nch < (u64)kPilotChunks ? nch : (u64)kPilotChunks);
     // every non-white pixel of the sample: f(key1, key2), then end() after
@@ -512,7 +541,7 @@ __global__ void __launch_bounds__(kPilotThreads) k_batch_pilot(PilotArgs a) {
           const unsigned r = byte_at(w, 3 * k), gg = byte_at(w, 3 * k + 1), b = byte_at(w, 3 * k + 2);
           if (min(r, min(gg, b)) > a.thr) continue;   // white
           float h1, h2;
-          solve_global(m->proj, r, gg, b, L, h1, h2);
+          solve_table(s_proj, r, gg, b, L, h1, h2);
           f(__float_as_uint(h1), __float_as_uint(h2));
           any = true;
         }
@@ -566,14 +595,12 @@ __global__ void __launch_bounds__(kPilotThreads) k_batch_pilot(PilotArgs a) {
       sa1 += ca1; saa1 += (u64)ca1 * ca1; sam1 += (u64)ca1 * cm;
       cm = ca0 = ca1 = 0u;
     });
-    sm = block_sum(sm, s_tmp);
-    smm = block_sum(smm, s_tmp);
-    sa0 = block_sum(sa0, s_tmp);
-    saa0 = block_sum(saa0, s_tmp);
-    sam0 = block_sum(sam0, s_tmp);
-    sa1 = block_sum(sa1, s_tmp);
-    saa1 = block_sum(saa1, s_tmp);
-    sam1 = block_sum(sam1, s_tmp);
+    {
+      u64 v[8] = {sm, smm, sa0, saa0, sam0, sa1, saa1, sam1};
+      block_sum8(v, s_part);
+      sm = v[0]; smm = v[1]; sa0 = v[2]; saa0 = v[3]; sam0 = v[4]; sa1 = v[5]; saa1 = v[6];
+      sam1 = v[7];
+    }
     if (threadIdx.x == 0) {
       const double p = a.pct / 100.0;
       const double M = (double)sm, U = (double)units;
