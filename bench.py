@@ -552,9 +552,11 @@ def run_grad(args, world, rank, local, leg=False):
 
 def run_batch(args, world, rank, local, leg=False):
     """256 uneven tiles from 32 slides (own source statistics each), one
-    target: one cooperative persistent launch per step (schedule from the
-    library's autotuner, replayed from a CUDA graph), against the same tiles
-    normalised by 256 sequential spcn_normalize calls.  As a leg of the
+    target: one batch run per step (the library's staged schedule: window
+    pilot, pass 1 of every tile, per-tile selects, pass 2, and the exact
+    fallback launch that returns at once when no tile missed its window),
+    replayed from a CUDA graph, against the same tiles normalised by 256
+    sequential spcn_normalize calls.  As a leg of the
     default run it returns a summary instead of printing a line."""
     import numpy as np
     import torch
@@ -656,7 +658,7 @@ def run_batch(args, world, rank, local, leg=False):
                "outputs_identical_to_plain": identical,
                "tiles_exact_fallback": sum(fallback), "schedule": b.config,
                "tune_s": round(tune_s, 2),
-               "timing": "CUDA-graph replays of one cooperative persistent launch vs "
+               "timing": f"CUDA-graph replays of one batch run ({per_run} launches) vs "
                          f"{len(tiles)} sequential spcn_normalize calls, CUDA events",
                "gpu_launches_per_step": per_run, "clocks": clocks}
         b.close()
@@ -722,7 +724,7 @@ def run_batch(args, world, rank, local, leg=False):
                         f"per-slide statistics (1% hash sample of a {wl['slide_sample']}^2 slide "
                         f"sample), {wl['tgt']}x{wl['tgt']} target",
             "pixels_per_step": npx, "parallelism": f"replicas x{world}",
-            "timing": "CUDA-graph replays of one cooperative persistent launch",
+            "timing": f"CUDA-graph replays of one batch run ({per_run} launches)",
             "l2": f"inputs ({3 * npx / 1e9:.2f} GB) larger than L2 (126 MB); no flush",
             "schedule": best, "tuner_trials": trials, "tune_s": round(tune_s, 2),
             "create_ms": round(create_ms, 2), "generate_s": round(gen_s, 2),
@@ -734,7 +736,7 @@ def run_batch(args, world, rank, local, leg=False):
             "tiles_exact_fallback": sum(fallback),
             "kernel_ms": round(k_ms, 4),
         },
-        "roofline": {"bound": "hbm", "kernel": "k_batch", "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "hbm", "kernel": "batch run (k_batch_p1, k_sel_*, k_batch_p2, k_batch)", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
                      "bytes_per_px": 9, "traffic": read_traffic("batch", "batch")},
         "roofline_step": {"bytes_per_px": 9, "achieved": 9 * npx / (ms / 1e3) / 1e9,

@@ -293,19 +293,25 @@ int spcn_estimate_basis_noalloc(const spcn_image* img, const spcn_params* params
  * Batched normalisation (§3.2: a batch of source images normalised to one
  * target).  Many tiles of any sizes, each with its own source statistics (W,
  * i0; p99 only guides the search window, as in spcn_normalize), are
- * normalised to one target by ONE cooperative persistent launch.  Every
- * tile's output bytes and percentiles are identical to what spcn_normalize
- * gives for that tile alone; only the schedule differs.
+ * normalised to one target by a fixed short sequence of launches on one
+ * stream, whatever the number of tiles.  Every tile's output bytes and
+ * percentiles are identical to what spcn_normalize gives for that tile
+ * alone; only the schedule differs.
  *
  * A batch object fixes the tile table (pointers, sizes, pitches, statistics,
  * outputs) and owns the device state of a run; spcn_batch_run can then be
  * repeated, and captured into a CUDA graph, as long as the buffers it names
- * stay allocated.  The launch works through a queue of work items of
+ * stay allocated.  A run first sets each tile's window start from a sample
+ * of the tile (one block per tile).  Work is then split into items of
  * `item_chunks` 16-pixel chunks: pass-1 items (densities, non-white count,
- * keys inside the P99 window), then pass-2 items (reconstruction) of tiles
- * whose percentile is known.  The last block to finish a tile's pass 1
- * selects its percentile; tiles whose ranks fell outside the window are
- * finished after the queue by an exact radix select over the whole grid. */
+ * keys at or above the window start), then pass-2 items (reconstruction) of
+ * tiles whose percentile is known.  The default schedule (SPCN_SCHED_STAGED)
+ * runs pass 1, the per-tile selects and pass 2 as separate launches; the
+ * other two run every item in one cooperative persistent launch, where the
+ * last block to finish a tile's pass 1 selects its percentile.  Tiles whose
+ * ranks fell below the window start are finished at the end of the run by an
+ * exact radix select over the whole grid (a cooperative launch that returns
+ * at once when no tile needs it). */
 
 typedef enum {
   SPCN_SCHED_PHASED = 0,       /* all pass-1 items, then all pass-2 items */
@@ -346,9 +352,12 @@ int spcn_batch_create(void* ctx, int32_t n, const spcn_image* tiles,
                       const spcn_params* params, uint8_t* const* outs,
                       const int64_t* out_pitches, void** batch);
 
-/* Normalise every tile of the batch: one memset of the batch state and one
- * cooperative kernel launch on `stream`.  Asynchronous, allocates nothing and
- * may be captured into a CUDA graph.  Errors: INVALID_ARG, CUDA. */
+/* Normalise every tile of the batch on `stream`: one memset of the batch
+ * state, the window-start launch, then the launches of the configured
+ * schedule (SPCN_SCHED_STAGED: pass 1, three select launches, pass 2 and the
+ * cooperative fallback launch; the other schedules: one cooperative launch).
+ * Asynchronous, allocates nothing and may be captured into a CUDA graph.
+ * Errors: INVALID_ARG, CUDA. */
 int spcn_batch_run(void* batch, void* stream);
 
 /* Wait for the batch's last run on `stream` and read its results: p99_out
@@ -403,7 +412,7 @@ typedef enum {
   SPCN_KERNEL_DENSITY = 3,  /* density output pass */
   SPCN_KERNEL_F32_FWD = 4,  /* differentiable forward (float images) */
   SPCN_KERNEL_F32_BWD = 5,  /* differentiable backward (float images) */
-  SPCN_KERNEL_BATCH = 6,    /* batched persistent launch (spcn_batch_run) */
+  SPCN_KERNEL_BATCH = 6,    /* the launches of spcn_batch_run after the window start */
   SPCN_KERNEL_LADDER = 7,   /* window-miss recovery: counting passes over key ladders */
   SPCN_KERNEL_COUNT = 8
 } spcn_kernel;
