@@ -323,9 +323,11 @@ typedef enum {
                                   tile (with the single-image chunk skips and
                                   per-warp stack), the per-tile selects, pass 2 of
                                   every tile, then the cooperative kernel for the
-                                  exact fallback only; items of item_chunks chunks,
-                                  the tiles of one table adjacent.  Needs fewer
-                                  than 2^32 chunks per tile (else INVALID_ARG) */
+                                  exact fallback only.  Both passes split the chunks
+                                  of all tiles (the tiles of one table adjacent)
+                                  into equal contiguous shares, one per block, so
+                                  item_chunks has no effect.  Needs fewer than
+                                  2^32 chunks per tile (else INVALID_ARG) */
 } spcn_schedule;
 
 typedef struct {

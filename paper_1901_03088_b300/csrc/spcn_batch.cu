@@ -115,8 +115,10 @@ struct BatchArgs {
   const Model* models;
   unsigned* hist1;         // per tile and stain: first-digit histogram of listed keys
   unsigned* hist2;         // grid-wide select: per tile and track, second-digit histogram
-  const BatchItem* p2_items;  // staged pass 2: each block's segments (chunk ranges of one tile),
-  const unsigned* p2_first;   // block b's at [p2_first[b], p2_first[b + 1])
+  const BatchItem* p1_items;  // staged pass 1: each block's segments (chunk ranges of one tile),
+  const unsigned* p1_first;   // block b's at [p1_first[b], p1_first[b + 1])
+  const BatchItem* p2_items;  // staged pass 2: the same for its grid
+  const unsigned* p2_first;
   u64* rhist;
   BatchRunState* run;
   unsigned n_items, n_tiles;
@@ -1281,28 +1283,23 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_p1(BatchArgs a) {
     staged_flush_keys(s_kb, kc0, kc1, s_t);
     staged_counts(s_t.sel, c_nw, c_b0, c_b1);
   };
-  // thread 0 runs the queue one item ahead: the next item's descriptor is
-  // copied into shared memory asynchronously (cp.async) and the ticket of the
-  // one after it is in flight while the block works
-  unsigned t_next = 0u;
+  // thread 0 walks the block's segments, copying the next descriptor into
+  // shared memory one segment ahead (cp.async)
+  unsigned i_next = 0u, i_end = 0u;
   int cur = 0;
   if (threadIdx.x == 0) {
-    const unsigned t1 = atomicAdd(&a.run->next, 1u);
-    if (t1 < a.n_items) copy_item_async(&s_items[1], a.items + t1);
+    i_next = a.p1_first[blockIdx.x];
+    i_end = a.p1_first[blockIdx.x + 1];
+    if (i_next < i_end) copy_item_async(&s_items[1], a.p1_items + i_next++);
     else s_items[1].tile = ~0u;
-    t_next = atomicAdd(&a.run->next, 1u);
   }
   for (;;) {
     cur ^= 1;
     if (threadIdx.x == 0) {
       cp_async_wait_all();
       BatchItem* nx = &s_items[cur ^ 1];   // read by nobody until the next loop top
-      if (s_items[cur].tile != ~0u && t_next < a.n_items) {
-        copy_item_async(nx, a.items + t_next);
-        t_next = atomicAdd(&a.run->next, 1u);
-      } else {
-        nx->tile = ~0u;
-      }
+      if (s_items[cur].tile != ~0u && i_next < i_end) copy_item_async(nx, a.p1_items + i_next++);
+      else nx->tile = ~0u;
       s_piece = 0u;
     }
     __syncthreads();
@@ -1702,6 +1699,8 @@ struct Batch {
   size_t state_bytes = 0;
   unsigned* keys = nullptr;
   unsigned* hist2 = nullptr;     // grid-wide select (batches of at most kGridSelMaxTiles)
+  BatchItem* p1_items = nullptr; // staged pass 1: each block's segments
+  unsigned* p1_first = nullptr;
   BatchItem* p2_items = nullptr; // staged pass 2: each block's segments
   unsigned* p2_first = nullptr;
   u64* rhist = nullptr;
@@ -1779,6 +1778,8 @@ static void build_items(const Batch* b, const spcn_batch_config& cfg, std::vecto
   const u64 S = (u64)cfg.item_chunks;
   out->clear();
   n_items1->assign(b->n, 0u);
+  // the staged passes take static shares (build_shares), not queue items
+  if (cfg.schedule == SPCN_SCHED_STAGED) return;
   // largest tiles first: their list selects end early, and the small tiles
   // even out the end of each pass
   std::vector<int> order(b->n);
@@ -1793,35 +1794,10 @@ static void build_items(const Batch* b, const spcn_batch_config& cfg, std::vecto
       out->push_back({(unsigned)t, pass, b->tiles[t].model, n1, c0, std::min(nch, c0 + S)});
     if (pass == 1) (*n_items1)[t] = n1;
   };
-  if (cfg.schedule == SPCN_SCHED_PHASED || cfg.schedule == SPCN_SCHED_STAGED) {
+  if (cfg.schedule == SPCN_SCHED_PHASED) {
     // pass 2 needs no particular order: tiles sharing a table go together
     // (fewer table reloads), largest first within a table
     const std::vector<int> order2 = table_order(b);
-    if (cfg.schedule == SPCN_SCHED_STAGED) {
-      // pass-1 chunk ranges (pass 2 splits the chunks statically), the tiles
-      // of one table together (the staged pass 1 reloads its table per
-      // model).  Item
-      // sizes are guided: item_chunks while the rest of the list holds more
-      // than two such items per block of the pass-1 grid, then the rest
-      // divided by twice the blocks (at least 4096 chunks), so the blocks
-      // finish each pass together
-      const u64 blocks2 = 2 * (u64)std::max(1, b->grid_p1);
-      u64 rest = 0;
-      for (int t : order2) rest += b->tiles[t].g.nchunks;
-      for (int t : order2) {
-        const u64 nch = b->tiles[t].g.nchunks;
-        u64 c0 = 0;
-        while (c0 < nch) {
-          const u64 guided = std::max<u64>(4096, rest / blocks2);
-          const u64 size = std::min<u64>(S, guided);
-          const u64 c1 = std::min(nch, c0 + size);
-          out->push_back({(unsigned)t, 1u, b->tiles[t].model, 0u, c0, c1});
-          rest -= c1 - c0;
-          c0 = c1;
-        }
-      }
-      return;
-    }
     for (int t : order) emit(t, 1);
     for (int t : order2) emit(t, 2);
     return;
@@ -1861,8 +1837,9 @@ static int apply_config(Batch* b, const spcn_batch_config& cfg) {
     b->items_cap = items.size();
   }
   for (int t = 0; t < b->n; ++t) b->tiles[t].n_items1 = n1[t];
-  SPCN_CUDA_TRY(cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(BatchItem),
-                           cudaMemcpyHostToDevice));
+  if (!items.empty())
+    SPCN_CUDA_TRY(cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(BatchItem),
+                             cudaMemcpyHostToDevice));
   SPCN_CUDA_TRY(cudaMemcpy(b->d_tiles, b->tiles.data(), b->tiles.size() * sizeof(BatchTile),
                            cudaMemcpyHostToDevice));
   // a pageable copy may return before it lands: finish it before any launch
@@ -1877,7 +1854,7 @@ static int apply_config(Batch* b, const spcn_batch_config& cfg) {
 
 static void batch_free(Batch* b) {
   void* ptrs[] = {b->models, b->d_tiles, b->d_items, b->d_state, b->keys, b->hist2,
-                  b->p2_items, b->p2_first, b->rhist};
+                  b->p1_items, b->p1_first, b->p2_items, b->p2_first, b->rhist};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete b;
@@ -1957,6 +1934,43 @@ static int batch_launch(Batch* b, cudaStream_t st) {
   }
   c->launches += launched;
   if (e != cudaSuccess) return SPCN_ERR_CUDA;
+  return SPCN_OK;
+}
+
+// The staged passes' static schedule: the chunks of all tiles (in table
+// order) in equal contiguous shares, one per block of a grid of `grid`
+// blocks, each cut at tile boundaries into segments; block b's segments are
+// (*items)[(*first)[b] .. (*first)[b + 1]).  A block crosses few tile and
+// table boundaries and takes no tickets.
+static int build_shares(Batch* b, int grid, unsigned pass, BatchItem** items, unsigned** first) {
+  const std::vector<int> ord = table_order(b);
+  u64 total = 0;
+  for (int t : ord) total += b->tiles[t].g.nchunks;
+  std::vector<BatchItem> segs;
+  std::vector<unsigned> fst(grid + 1);
+  size_t k = 0;
+  u64 tile0 = 0;   // first chunk of tile ord[k] in the order
+  for (int blk = 0; blk < grid; ++blk) {
+    fst[blk] = (unsigned)segs.size();
+    u64 c = total * (u64)blk / (u64)grid;
+    const u64 e = total * (u64)(blk + 1) / (u64)grid;
+    while (c < e) {
+      while (tile0 + b->tiles[ord[k]].g.nchunks <= c) tile0 += b->tiles[ord[k++]].g.nchunks;
+      const BatchTile& T = b->tiles[ord[k]];
+      const u64 stop = std::min(e, tile0 + T.g.nchunks);
+      segs.push_back({(unsigned)ord[k], pass, T.model, 0u, c - tile0, stop - tile0});
+      c = stop;
+    }
+  }
+  fst[grid] = (unsigned)segs.size();
+  if (cudaMalloc(items, sizeof(BatchItem) * std::max<size_t>(1, segs.size())) != cudaSuccess ||
+      cudaMalloc(first, sizeof(unsigned) * fst.size()) != cudaSuccess)
+    return SPCN_ERR_OOM;
+  if ((!segs.empty() && cudaMemcpy(*items, segs.data(), sizeof(BatchItem) * segs.size(),
+                                   cudaMemcpyHostToDevice) != cudaSuccess) ||
+      cudaMemcpy(*first, fst.data(), sizeof(unsigned) * fst.size(), cudaMemcpyHostToDevice) !=
+          cudaSuccess)
+    return SPCN_ERR_CUDA;
   return SPCN_OK;
 }
 
@@ -2045,46 +2059,17 @@ static int batch_create(Context* c, int n, const spcn_image* tiles, const spcn_s
                : configure_staged_kernels<Geometry>(c, &b->grid_p1, &b->grid_p2);
   if (rc) return fail(rc);
   b->grid_sel = std::min(n, 4 * c->num_sms);
-  {
-    // staged pass 2: the chunks of all tiles (in table order) in equal
-    // contiguous shares, one per block, each cut at tile boundaries into
-    // segments
-    const std::vector<int> ord = table_order(b);
-    u64 total = 0;
-    for (int t : ord) total += b->tiles[t].g.nchunks;
-    std::vector<BatchItem> segs;
-    std::vector<unsigned> first(b->grid_p2 + 1);
-    size_t k = 0;
-    u64 tile0 = 0;   // first chunk of tile ord[k] in the order
-    for (int blk = 0; blk < b->grid_p2; ++blk) {
-      first[blk] = (unsigned)segs.size();
-      u64 c = total * (u64)blk / (u64)b->grid_p2;
-      const u64 e = total * (u64)(blk + 1) / (u64)b->grid_p2;
-      while (c < e) {
-        while (tile0 + b->tiles[ord[k]].g.nchunks <= c) tile0 += b->tiles[ord[k++]].g.nchunks;
-        const BatchTile& T = b->tiles[ord[k]];
-        const u64 stop = std::min(e, tile0 + T.g.nchunks);
-        segs.push_back({(unsigned)ord[k], 2u, T.model, 0u, c - tile0, stop - tile0});
-        c = stop;
-      }
-    }
-    first[b->grid_p2] = (unsigned)segs.size();
-    if (cudaMalloc(&b->p2_items, sizeof(BatchItem) * std::max<size_t>(1, segs.size())) !=
-            cudaSuccess ||
-        cudaMalloc(&b->p2_first, sizeof(unsigned) * first.size()) != cudaSuccess)
-      return fail(SPCN_ERR_OOM);
-    if ((!segs.empty() && cudaMemcpy(b->p2_items, segs.data(), sizeof(BatchItem) * segs.size(),
-                                     cudaMemcpyHostToDevice) != cudaSuccess) ||
-        cudaMemcpy(b->p2_first, first.data(), sizeof(unsigned) * first.size(),
-                   cudaMemcpyHostToDevice) != cudaSuccess)
-      return fail(SPCN_ERR_CUDA);
-  }
+  rc = build_shares(b, b->grid_p1, 1u, &b->p1_items, &b->p1_first);
+  if (rc == SPCN_OK) rc = build_shares(b, b->grid_p2, 2u, &b->p2_items, &b->p2_first);
+  if (rc) return fail(rc);
   BatchArgs& a = b->args;
   a.tiles = b->d_tiles;
   a.state = reinterpret_cast<BatchTileState*>(b->d_state + kRunStateBytes);
   a.hist1 = reinterpret_cast<unsigned*>(b->d_state + kRunStateBytes +
                                         sizeof(BatchTileState) * (size_t)n);
   a.hist2 = b->hist2;
+  a.p1_items = b->p1_items;
+  a.p1_first = b->p1_first;
   a.p2_items = b->p2_items;
   a.p2_first = b->p2_first;
   a.run = reinterpret_cast<BatchRunState*>(b->d_state);
@@ -2212,7 +2197,8 @@ int spcn_batch_tune(void* batch, int32_t reps, spcn_batch_config* trials, int32_
   if (!guard.ok) return SPCN_ERR_CUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   // candidates: item sizes (2K-64K chunks) x (phased, interleaved groups of
-  // 16 Mpx, staged); sizes above the largest tile's chunk count are skipped
+  // 16 Mpx), sizes above the largest tile's chunk count skipped, and the
+  // staged schedule (static shares: the item size does not change it)
   u64 max_chunks = 0;
   for (const BatchTile& T : b->tiles) max_chunks = std::max(max_chunks, (u64)T.g.nchunks);
   std::vector<spcn_batch_config> cand;
@@ -2226,11 +2212,12 @@ int spcn_batch_tune(void* batch, int32_t reps, spcn_batch_config* trials, int32_
     c1.schedule = SPCN_SCHED_INTERLEAVED;
     c1.group_px = 16ll << 20;
     cand.push_back(c1);
-    if (max_chunks < (1ull << 32)) {
-      spcn_batch_config c2 = c0;
-      c2.schedule = SPCN_SCHED_STAGED;
-      cand.push_back(c2);
-    }
+  }
+  if (max_chunks < (1ull << 32)) {
+    spcn_batch_config c2{};
+    c2.item_chunks = 32 * kPassThreads;
+    c2.schedule = SPCN_SCHED_STAGED;
+    cand.push_back(c2);
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   SPCN_CUDA_TRY(cudaEventCreate(&e0));

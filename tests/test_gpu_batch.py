@@ -299,3 +299,55 @@ def test_batch_white_regions(spcn, ctx, setup, thresh, sched):
     p99, status, _ = run_batch(spcn, ctx, tiles, stats, tgt, outs, p, sched)
     assert status == [0] * len(tiles)
     assert_same(outs, ref_outs, p99, ref_p99)
+
+
+def test_batch_at_benchmark_tile_sizes_against_oracle(spcn, ctx):
+    """The three largest tiles of the benchmark's 256-tile layout (about
+    3700 x 3600 px each, blob images of 13.4, 11.6 and 10.7 Mpx) and five of
+    its small ones, with per-slide statistics from a 1% hash sample of a
+    2048^2 slide sample, under the default (staged) schedule: every tile's
+    percentile within 1e-5 of the oracle's exact FP64 P99 over all of its
+    non-white pixels, and 20000 seeded pixels per tile within 1 of the
+    oracle's normalisation on >= 99.99% of them."""
+    layout = synth.batch_layout(32, 8, 256, 4096, seed=3)
+    by_size = sorted(range(len(layout)), key=lambda k: layout[k][1] * layout[k][2])
+    pick = by_size[-3:] + by_size[:5]
+    p = spcn.params(sample_mode="hash", sample_rate=0.01, seed=0)
+    slide_st = {}
+    for k in pick:
+        s = layout[k][0]
+        if s not in slide_st:
+            smp = synth.make_image_torch(2048, 2048, 2100 + s, W=synth.stain_basis(2000 + s),
+                                         device="cuda", blobs=True)
+            slide_st[s] = ctx.estimate_basis(smp, p)
+    tiles = [synth.make_image_torch(layout[k][1], layout[k][2], 3000 + k,
+                                    W=synth.stain_basis(2000 + layout[k][0]), device="cuda",
+                                    blobs=True) for k in pick]
+    stats = [slide_st[layout[k][0]] for k in pick]
+    tgt_img = synth.make_image_torch(2048, 2048, 1, device="cuda", blobs=True)
+    tgt = ctx.estimate_basis(tgt_img, p)
+    tgt.p99[0], tgt.p99[1] = ctx.stain_percentile(tgt_img, tgt, p)
+    outs = [torch.empty_like(t) for t in tiles]
+    b = spcn.Batch(ctx, tiles, stats, tgt, outs, p)
+    assert b.config["schedule"] == "staged"
+    b.run()
+    p99, status, fallback = b.results(fallback=True)
+    b.close()
+    assert status == [0] * len(tiles)
+    Wt = np.asarray(np.array(tgt.basis, np.float32), np.float64)
+    i0t = np.asarray(np.array(tgt.i0[:], np.float32), np.float64)
+    rng = np.random.default_rng(17)
+    for k, (t, st) in enumerate(zip(tiles, stats)):
+        img = t.cpu().numpy()
+        W = np.asarray(np.array(st.basis, np.float32), np.float64)
+        i0 = np.asarray(np.array(st.i0[:], np.float32), np.float64)
+        p_src = O.stain_percentile(img, W, i0)
+        for j in range(2):
+            assert abs(p99[k][j] - p_src[j]) <= 1e-5 * max(p_src[j], 1e-30), (k, j, p99[k], p_src)
+        n = min(20000, img.shape[0] * img.shape[1])
+        flat = rng.choice(img.shape[0] * img.shape[1], size=n, replace=False)
+        px = img.reshape(-1, 3)[flat][None]
+        ref = O.to_uint8(O.normalize_float(px, W, i0, p_src, Wt, i0t, np.array(tgt.p99[:])))[0]
+        got = outs[k].cpu().numpy().reshape(-1, 3)[flat]
+        diff = np.abs(got.astype(int) - ref.astype(int))
+        assert np.mean(np.any(diff > 1, axis=-1)) <= 1e-4, (k, diff.max())
