@@ -997,10 +997,64 @@ __global__ void __launch_bounds__(kPassThreads, 1) k_pass_recon(ReconArgs a) {
     K.L2[c] = pk(a.l2i0[c], a.l2i0[c]);
   }
   const f2 NR1 = pk(L.nrho1, L.nrho1), NR2 = pk(L.nrho2, L.nrho2);
-  for_each_chunk<true, true>(a.g, [&](const unsigned (&w)[12], const ChunkPos& p) {
+  const Geometry& g = a.g;
+  if (flat_fast(g) && g.vec_dst) {
+    // one long row, source and output 16-byte aligned, fewer than 2^31 full
+    // chunks: 32-bit chunk indices and plain vector accesses, the next
+    // chunk's loads in flight while the current one is computed (two
+    // register buffers); the row's partial last chunk after the loop
+    const unsigned nfull = (unsigned)((u64)g.npx / kChunk);
+    const unsigned stride32 = gridDim.x * blockDim.x;
+    const uint4* src4 = reinterpret_cast<const uint4*>(g.src);
+    uint4* dst4 = reinterpret_cast<uint4*>(g.dst);
+    auto ld = [&](unsigned q, unsigned (&w)[12]) {
+      if (!SPCN_CHECK((int64_t)(q + 1ull) * (3 * kChunk) <= g.src_bytes, g.err)) {
+#pragma unroll
+        for (int i = 0; i < 12; ++i) w[i] = 0xFFFFFFFFu;
+        return;
+      }
+      const uint4* v = src4 + 3ull * q;
+      const uint4 x = __ldcs(v), y = __ldcs(v + 1), z = __ldcs(v + 2);
+      w[0] = x.x; w[1] = x.y; w[2] = x.z; w[3] = x.w;
+      w[4] = y.x; w[5] = y.y; w[6] = y.z; w[7] = y.w;
+      w[8] = z.x; w[9] = z.y; w[10] = z.z; w[11] = z.w;
+    };
+    auto run = [&](unsigned q, const unsigned (&w)[12]) {
+      unsigned o[12];
+      recon_chunk<PINV>(w, lut, lr, P, NR1, NR2, L.kappa, K, o);
+      if (!SPCN_CHECK((int64_t)(q + 1ull) * (3 * kChunk) <= g.dst_bytes, g.err)) return;
+      uint4* v = dst4 + 3ull * q;
+      __stcs(v, make_uint4(o[0], o[1], o[2], o[3]));
+      __stcs(v + 1, make_uint4(o[4], o[5], o[6], o[7]));
+      __stcs(v + 2, make_uint4(o[8], o[9], o[10], o[11]));
+    };
+    unsigned q = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned wa[12], wb[12];
+    if (q < nfull) ld(q, wa);
+    while (q < nfull) {
+      unsigned qn = q + stride32;
+      if (qn < nfull) ld(qn, wb);
+      run(q, wa);
+      q = qn;
+      if (q >= nfull) break;
+      qn = q + stride32;
+      if (qn < nfull) ld(qn, wa);
+      run(q, wb);
+      q = qn;
+    }
+    if ((u64)g.npx % kChunk && (u64)blockIdx.x * blockDim.x + threadIdx.x == nfull % stride32) {
+      const ChunkPos p = chunk_pos(g, (u64)nfull);
+      unsigned w[12], o[12];
+      load_chunk<true>(g, p, w);
+      recon_chunk<PINV>(w, lut, lr, P, NR1, NR2, L.kappa, K, o);
+      store_chunk(g, p, o);
+    }
+    return;
+  }
+  for_each_chunk<true, true>(g, [&](const unsigned (&w)[12], const ChunkPos& p) {
     unsigned o[12];
     recon_chunk<PINV>(w, lut, lr, P, NR1, NR2, L.kappa, K, o);
-    store_chunk(a.g, p, o);
+    store_chunk(g, p, o);
   });
 }
 
