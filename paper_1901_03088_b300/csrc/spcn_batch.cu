@@ -748,6 +748,11 @@ __device__ __forceinline__ ReconConst recon_const(const float* s_M, const float*
   return K;
 }
 
+// Contiguous image (one long row) whose source is 16-byte aligned: full
+// chunks may be addressed by index with vector loads.
+__device__ __forceinline__ bool flat_src(const FlatGeometry& g) { return g.vec_src; }
+__device__ __forceinline__ bool flat_src(const Geometry& g) { return g.flat && g.vec_src; }
+
 template <class G>
 __device__ __forceinline__ G geometry_as(const Geometry& g);
 template <>
@@ -1335,6 +1340,9 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_p1(BatchArgs a) {
       cur_tile = (int)tile;
       wbelow = whites_below(a.thr, lut, lr, s_t.C);
     }
+    // chunks below vfull are full chunks of a contiguous tile whose source
+    // is 16-byte aligned (0: the general traversal for every chunk)
+    const u64 vfull = flat_src(s_g) ? (u64)s_g.npx / kChunk : 0ull;
     // the item's chunks, 32 per warp step, in pieces claimed from a shared
     // counter (a warp that spends time on its stack or queue takes fewer)
     for (;;) {
@@ -1346,7 +1354,17 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_p1(BatchArgs a) {
       unsigned w[12];
       bool tissue = false;
       unsigned dpart = 0u;
-      if (q < c1) {
+      if (q < c1 && q < vfull) {
+        // full chunk of a contiguous, 16-byte aligned tile: plain vector loads
+        if (SPCN_CHECK((int64_t)(q + 1) * (3 * kChunk) <= s_g.src_bytes, s_g.err)) {
+          const uint4* v = reinterpret_cast<const uint4*>(s_g.src) + 3 * q;
+          const uint4 x = __ldg(v), y = __ldg(v + 1), z = __ldg(v + 2);
+          w[0] = x.x; w[1] = x.y; w[2] = x.z; w[3] = x.w;
+          w[4] = y.x; w[5] = y.y; w[6] = y.z; w[7] = y.w;
+          w[8] = z.x; w[9] = z.y; w[10] = z.z; w[11] = z.w;
+          tissue = !chunk_white(w, a.wm, a.we) && classify(w);
+        }
+      } else if (q < c1) {
         const ChunkPos p = chunk_pos(s_g, q);
         load_chunk<false>(s_g, p, w);
         if (p.n == kChunk) {
