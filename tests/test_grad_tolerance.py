@@ -8,7 +8,9 @@ once to FP32).  Against |dL/dx| floored at 1e-3 its largest error is still
 above 1e-4, so that measure cannot bound an FP32 kernel; against
 max(|dL/dx|, S) the same evaluation stays below 1e-6, far inside 1e-4.  An
 FP64 evaluation of the same chain meets either measure, so the gap is FP32
-rounding, not the measure.  The images are those of the GPU gradient test
+rounding, not the measure.  Even the chain in FP64 arithmetic fails the
+floored measure once y carries the half-unit rounding error of any FP32
+output: the floored bound at 1e-4 asks for a y more exact than FP32 holds.  The images are those of the GPU gradient test
 (synthetic, seeds 600-607)."""
 import numpy as np
 
@@ -34,7 +36,12 @@ def _chain(dtype, X, GY, Y, H, Ws, s, Wt):
     return np.where(X > 1.0, -gvs / np.maximum(X, 1.0).astype(T), T(0)).astype(np.float64)
 
 
-def _errors(dtype):
+def _errors(dtype, y_ulps=None):
+    """Floored and condition-scaled errors of dL/dx from _chain in `dtype`.
+    y_ulps: the chain (then in FP64) starts from the exact y rounded to FP32
+    and moved by that many FP32 units in the last place, with a seeded random
+    sign per value (an FP32 output's error, at the given size)."""
+    rng = np.random.default_rng(99)
     naive, cond = [], []
     Wt = np.float32(synth.stain_basis(1)).astype(np.float64)
     i0t = np.array([255.0, 254.0, 252.0])
@@ -49,6 +56,10 @@ def _errors(dtype):
             Y, H = O.normalize_float_pixels(X, Ws, i0s, s, Wt, i0t)
             GX, _ = O.normalize_grad(X, gy[b], Ws, i0s, s, Wt, i0t)
             y = Y.astype(np.float32) if dtype == np.float32 else Y
+            if y_ulps is not None:
+                y32 = Y.astype(np.float32)
+                y = y32.astype(np.float64) + y_ulps * np.spacing(y32).astype(np.float64) * \
+                    rng.choice([-1.0, 1.0], size=Y.shape)
             gx = _chain(dtype, X, gy[b], y, H, Ws, s, Wt)
             S = condition_scale(X, gy[b], Y, H, Ws, s, Wt)
             ok = (kkt_margin(X, H, Ws, i0s, 0.1, O.optical_density) >= 1e-2)[None, :] & (X > 1.01)
@@ -67,3 +78,15 @@ def test_fp32_chain_fails_the_floored_measure_but_not_the_condition_scaled_one()
 def test_fp64_chain_meets_both_measures():
     naive, cond = _errors(np.float64)
     assert naive.max() <= 1e-10 and cond.max() <= 1e-12
+
+
+def test_floored_measure_fails_with_an_exact_chain_from_any_fp32_y():
+    """The chain in FP64 arithmetic from a y that is off by half a unit in the
+    last place of FP32 (the rounding bound of any FP32 output; the kernel's
+    ex2.approx has a bound of about 2): the floored measure still exceeds
+    1e-4, so no kernel whose y is FP32 can meet it, while the
+    condition-scaled measure stays three orders of magnitude inside it."""
+    for ulps in (0.5, 2.0):
+        naive, cond = _errors(np.float64, y_ulps=ulps)
+        assert naive.max() > 1e-4
+        assert cond.max() <= 1e-6
