@@ -72,6 +72,7 @@ struct BatchTile {
   float nk[2], lk[2];      // exact [h~ < lo] test (nk = 0, lk = 1 without a window)
   unsigned hlo[2], hwin[2];   // the same from the hint alone (kOpenLow * hint)
   float hnk[2], hlk[2];
+  unsigned hkey[2];        // key of the hint itself (the pilot's design-effect threshold)
   unsigned* keys;          // stain-0 key list; stain 1 at keys + list_cap
   u64 list_cap;            // keys per stain
 };
@@ -447,6 +448,8 @@ constexpr int kPilotMinUnits = 64;
 constexpr int kPilotThreads = 512;
 constexpr int kPilotBits = 11;
 constexpr int kPilotBins = 1 << kPilotBits;
+static_assert((kPilotChunks + kPilotThreads - 1) / kPilotThreads * kChunk * kChunk < (1 << 30),
+              "a thread's pilot sums fit 32 bits");
 
 struct PilotArgs {
   BatchTile* tiles;
@@ -503,7 +506,7 @@ __device__ __forceinline__ void block_sum8(u64 (&v)[8], u64 (*s_part)[8]) {
   }
 }
 
-__global__ void __launch_bounds__(kPilotThreads) k_batch_pilot(PilotArgs a) {
+__global__ void __launch_bounds__(kPilotThreads, 2) k_batch_pilot(PilotArgs a) {
   __shared__ unsigned s_hist[2][kPilotBins];
   __shared__ float2 s_proj[kLutEntries];          // the tile's projected table
   __shared__ u64 s_part[kPilotThreads / 32][8];
@@ -555,11 +558,36 @@ __global__ void __launch_bounds__(kPilotThreads) k_batch_pilot(PilotArgs a) {
     auto none = [] {};
     for (int i = threadIdx.x; i < 2 * kPilotBins; i += blockDim.x) (&s_hist[0][0])[i] = 0u;
     __syncthreads();
-    // level 1: bits 31-21 of the keys (densities are >= 0: the sign bit is 0)
+    // The margin delta = 4 sigma of the sample quantile, from the sample's own
+    // between-chunk variance (pixels of one chunk are not independent): at
+    // a provisional threshold t (the hint's key: the tile's percentile is
+    // near its slide's), a_i = pixels of chunk i at or above t, m_i = its
+    // non-white pixels, p^ = sum a / sum m, and the ratio estimator's
+    // variance sum (a_i - p^ m_i)^2 / (u (u - 1) mbar^2) over p^ (1 - p^) /
+    // sum m is the design effect d, clamped to [1, 16] (independent pixels ..
+    // whole chunks as units); then sigma^2 = d p (1 - p) / sum m.  Without an
+    // estimate (p^ of 0 or 1) the chunks are the units: sigma^2 = p (1 - p) /
+    // u.  The chunk sums are taken in the same visit as the level-1
+    // histograms: bits 31-21 of the keys (densities are >= 0: the sign bit
+    // is 0).
+    const unsigned t0 = T->hwin[0] ? T->hkey[0] : 0xFFFFFFFFu;
+    const unsigned t1 = T->hwin[1] ? T->hkey[1] : 0xFFFFFFFFu;
+    unsigned cm = 0u, ca0 = 0u, ca1 = 0u;   // the current chunk's counts
+    // this thread's sums over its chunks (at most kPilotChunks / blockDim.x
+    // chunks of 16 pixels: 32-bit sums are exact)
+    unsigned sm = 0, smm = 0, sa0 = 0, saa0 = 0, sam0 = 0, sa1 = 0, saa1 = 0, sam1 = 0;
     const unsigned my_units = visit([&](unsigned k1, unsigned k2) {
       atomicAdd(&s_hist[0][k1 >> 21], 1u);
       atomicAdd(&s_hist[1][k2 >> 21], 1u);
-    }, none);
+      ++cm;
+      ca0 += k1 >= t0 ? 1u : 0u;
+      ca1 += k2 >= t1 ? 1u : 0u;
+    }, [&] {
+      sm += cm; smm += cm * cm;
+      sa0 += ca0; saa0 += ca0 * ca0; sam0 += ca0 * cm;
+      sa1 += ca1; saa1 += ca1 * ca1; sam1 += ca1 * cm;
+      cm = ca0 = ca1 = 0u;
+    });
     u64 units = 0;
     block_excl_scan((u64)my_units, s_tmp, &units);
     u64 nw = 0;
@@ -568,52 +596,19 @@ __global__ void __launch_bounds__(kPilotThreads) k_batch_pilot(PilotArgs a) {
       for (int i = threadIdx.x; i < kPilotBins; i += blockDim.x) part += s_hist[0][i];
       block_excl_scan(part, s_tmp, &nw);
     }
-    // The margin delta = 4 sigma of the sample quantile, from the sample's own
-    // between-chunk variance (pixels of one chunk are not independent): at
-    // a provisional threshold t (the level-1 bin of the sample's percentile),
-    // a_i = pixels of chunk i at or above t, m_i = its non-white pixels, p^ =
-    // sum a / sum m, and the ratio estimator's variance sum (a_i - p^ m_i)^2
-    // / (u (u - 1) mbar^2) over p^ (1 - p^) / sum m is the design effect d,
-    // clamped to [1, 16] (independent pixels .. whole chunks as units); then
-    // sigma^2 = d p (1 - p) / sum m.  Without an estimate (p^ of 0 or 1) the
-    // chunks are the units: sigma^2 = p (1 - p) / u.
-    if (threadIdx.x == 0) s_r[0] = nw > 0 ? (u64)floor(a.pct / 100.0 * (double)(nw - 1)) : 0;
-    __syncthreads();
-    for (int j = 0; j < 2; ++j) {
-      smem_find_rank(s_hist[j], kPilotBins, s_r[0], &s_idx, &s_before, s_tmp);
-      if (threadIdx.x == 0) s_b1[j] = (unsigned)max(s_idx, 0) << 21;
-      __syncthreads();
-    }
-    const unsigned t0 = s_b1[0], t1 = s_b1[1];
-    unsigned cm = 0u, ca0 = 0u, ca1 = 0u;   // the current chunk's counts
-    u64 sm = 0, smm = 0, sa0 = 0, saa0 = 0, sam0 = 0, sa1 = 0, saa1 = 0, sam1 = 0;
-    visit([&](unsigned k1, unsigned k2) {
-      ++cm;
-      ca0 += k1 >= t0 ? 1u : 0u;
-      ca1 += k2 >= t1 ? 1u : 0u;
-    }, [&] {
-      sm += cm; smm += (u64)cm * cm;
-      sa0 += ca0; saa0 += (u64)ca0 * ca0; sam0 += (u64)ca0 * cm;
-      sa1 += ca1; saa1 += (u64)ca1 * ca1; sam1 += (u64)ca1 * cm;
-      cm = ca0 = ca1 = 0u;
-    });
-    {
-      u64 v[8] = {sm, smm, sa0, saa0, sam0, sa1, saa1, sam1};
-      block_sum8(v, s_part);
-      sm = v[0]; smm = v[1]; sa0 = v[2]; saa0 = v[3]; sam0 = v[4]; sa1 = v[5]; saa1 = v[6];
-      sam1 = v[7];
-    }
+    u64 v[8] = {sm, smm, sa0, saa0, sam0, sa1, saa1, sam1};
+    block_sum8(v, s_part);
     if (threadIdx.x == 0) {
       const double p = a.pct / 100.0;
-      const double M = (double)sm, U = (double)units;
-      const u64 SA[2] = {sa0, sa1}, SAA[2] = {saa0, saa1}, SAM[2] = {sam0, sam1};
+      const double M = (double)v[0], U = (double)units;
+      const u64 SA[2] = {v[2], v[5]}, SAA[2] = {v[3], v[6]}, SAM[2] = {v[4], v[7]};
       int use = units >= (u64)kPilotMinUnits && nw > 0;
       for (int j = 0; j < 2; ++j) {
         double var = p * (1.0 - p) / (U > 0.0 ? U : 1.0);   // chunks as units
         const double ph = M > 0.0 ? (double)SA[j] / M : 0.0;
         if (units >= 2 && ph > 0.0 && ph < 1.0) {
           const double mbar = M / U;
-          const double ss = (double)SAA[j] - 2.0 * ph * (double)SAM[j] + ph * ph * (double)smm;
+          const double ss = (double)SAA[j] - 2.0 * ph * (double)SAM[j] + ph * ph * (double)v[1];
           const double v = ss / (U * (U - 1.0) * mbar * mbar);
           double d = v / (ph * (1.0 - ph) / M);
           d = d < 1.0 ? 1.0 : (d > (double)kChunk ? (double)kChunk : d);
@@ -2024,6 +2019,8 @@ static int batch_create(Context* c, int n, const spcn_image* tiles, const spcn_s
       float f = (float)h;
       unsigned key = 0u;
       memcpy(&key, &f, 4);
+      const float fh = (float)(tile_stats[t].p99[j] * hs);
+      memcpy(&T.hkey[j], &fh, 4);
       if (h > 0x1p-100 && std::isfinite(h) && key > 0u) {
         T.win[j] = 1u;
         T.lo[j] = key;
