@@ -657,6 +657,9 @@ def run_batch(args, world, rank, local, leg=False):
                "roofline_frac": achieved / peak, "roofline_bytes_per_px": 9,
                "outputs_identical_to_plain": identical,
                "tiles_exact_fallback": sum(fallback), "schedule": b.config,
+               "fused_launch_ms": min((t["ms"] for t in trials
+                                       if t["schedule"] in ("phased", "interleaved")),
+                                      default=None),
                "tune_s": round(tune_s, 2),
                "timing": f"CUDA-graph replays of one batch run ({per_run} launches) vs "
                          f"{len(tiles)} sequential spcn_normalize calls, CUDA events",
