@@ -103,6 +103,12 @@ struct PatchArgs {
   uint32_t* out;
   u64 cap;            // sample entries allocated
   int* err;
+  // per-patch compaction (null: the sample is gathered and compacted apart):
+  int ng;             // row groups of kPatchGroupRows rows per patch
+  int* gcnt;          // [n_cand][ng] non-white pixels per row group
+  u64* goff;          // [2][n_patches] list offsets of each kept patch (non-white, bright)
+  uint32_t* nw;       // the non-white and bright lists
+  uint32_t* br;
 };
 
 __device__ __forceinline__ void patch_origin(const PatchArgs& a, int k, u64* x0, u64* y0) {
@@ -110,8 +116,12 @@ __device__ __forceinline__ void patch_origin(const PatchArgs& a, int k, u64* x0,
   *y0 = sm64_below(a.seed, 2ull * (u64)k + 1ull, (u64)(a.height - a.P + 1));
 }
 
-// One block per candidate patch: its non-white pixel count (rows by warps,
-// columns by lanes, no per-pixel division).
+// Rows per group of the per-patch compaction: one warp compacts one group.
+constexpr int kPatchGroupRows = 4;
+
+// One block per candidate patch: its non-white pixel count (row groups by
+// warps, columns by lanes, no per-pixel division), and with gcnt the count
+// of every row group.
 __global__ void k_patch_count(PatchArgs a) {
   __shared__ u64 s_tmp[33];
   const int k = blockIdx.x;
@@ -119,39 +129,118 @@ __global__ void k_patch_count(PatchArgs a) {
   patch_origin(a, k, &x0, &y0);
   if (!SPCN_CHECK(x0 + (u64)a.P <= (u64)a.width && y0 + (u64)a.P <= (u64)a.height, a.err)) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int ng = (a.P + kPatchGroupRows - 1) / kPatchGroupRows;
   unsigned cnt = 0;
-  for (int y = warp; y < a.P; y += nwarps) {
-    const uint8_t* row = a.data + (int64_t)(y0 + (u64)y) * a.pitch + (int64_t)(x0 * 3);
-    for (int x = lane; x < a.P; x += 32) {
-      const unsigned r = row[3 * x], g = row[3 * x + 1], b = row[3 * x + 2];
-      cnt += min(r, min(g, b)) <= a.thr ? 1u : 0u;
+  for (int gi = warp; gi < ng; gi += nwarps) {
+    unsigned gc = 0;
+    const int y1 = min(a.P, (gi + 1) * kPatchGroupRows);
+    for (int y = gi * kPatchGroupRows; y < y1; ++y) {
+      const uint8_t* row = a.data + (int64_t)(y0 + (u64)y) * a.pitch + (int64_t)(x0 * 3);
+      for (int x = lane; x < a.P; x += 32) {
+        const unsigned r = row[3 * x], g = row[3 * x + 1], b = row[3 * x + 2];
+        gc += min(r, min(g, b)) <= a.thr ? 1u : 0u;
+      }
     }
+    gc = __reduce_add_sync(0xFFFFFFFFu, gc);
+    if (a.gcnt && lane == 0) a.gcnt[(size_t)k * ng + gi] = (int)gc;
+    cnt += lane == 0 ? gc : 0u;
   }
   const u64 tot = block_sum(cnt, s_tmp);
   if (threadIdx.x == 0) a.cand[k] = (int)tot;
 }
 
 // Keep candidates, in order, while at least half their pixels are non-white:
-// one warp scans them 32 at a time (ballot + prefix counts), the same list as
-// a sequential scan.
-__global__ void k_patch_accept(PatchArgs a) {
-  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
-  const unsigned lane = threadIdx.x;
+// warp 0 scans them 32 at a time (ballot + prefix counts), the same list as
+// a sequential scan.  With goff the whole block then places every kept row
+// group in the non-white and bright lists: exclusive prefix sums of the
+// groups' counts in sample order (kept patches in order, groups in order).
+constexpr int kAcceptThreads = 1024;
+__global__ void __launch_bounds__(kAcceptThreads) k_patch_accept(PatchArgs a) {
+  __shared__ u64 s_tmp[33];
+  __shared__ int s_n;
+  const unsigned lane = threadIdx.x & 31u;
   const long long need = (long long)a.P * a.P;
-  int n = 0;
-  for (int k0 = 0; k0 < a.n_cand && n < a.n_patches; k0 += 32) {
-    const int k = k0 + (int)lane;
-    const bool ok = k < a.n_cand && 2ll * a.cand[k] >= need;
-    const unsigned ball = __ballot_sync(0xFFFFFFFFu, ok);
-    const int pos = n + __popc(ball & ((1u << lane) - 1u));
-    if (ok && pos < a.n_patches) a.cand[a.n_cand + pos] = k;
-    n += __popc(ball);
+  if (threadIdx.x < 32) {
+    int n = 0;
+    for (int k0 = 0; k0 < a.n_cand && n < a.n_patches; k0 += 32) {
+      const int k = k0 + (int)lane;
+      const bool ok = k < a.n_cand && 2ll * a.cand[k] >= need;
+      const unsigned ball = __ballot_sync(0xFFFFFFFFu, ok);
+      const int pos = n + __popc(ball & ((1u << lane) - 1u));
+      if (ok && pos < a.n_patches) a.cand[a.n_cand + pos] = k;
+      n += __popc(ball);
+    }
+    if (n > a.n_patches) n = a.n_patches;
+    if (lane == 0) {
+      s_n = n;
+      a.bs->n_acc = n;
+      a.bs->m = (u64)n * (u64)need;
+      if (n == 0) a.bs->status = SPCN_ERR_NO_TISSUE;
+    }
   }
-  if (n > a.n_patches) n = a.n_patches;
-  if (lane == 0) {
-    a.bs->n_acc = n;
-    a.bs->m = (u64)n * (u64)need;
-    if (n == 0) a.bs->status = SPCN_ERR_NO_TISSUE;
+  __syncthreads();
+  if (!a.goff) return;
+  // per kept patch, in order: non-white pixels = the candidate's count
+  const int n = s_n;
+  const int per = (n + (int)blockDim.x - 1) / (int)blockDim.x;
+  const int p0 = min(n, (int)threadIdx.x * per), p1 = min(n, p0 + per);
+  u64 lnw = 0;
+  for (int q = p0; q < p1; ++q) lnw += (u64)a.cand[a.cand[a.n_cand + q]];
+  u64 tnw;
+  u64 onw = block_excl_scan(lnw, s_tmp, &tnw);
+  u64 obr = (u64)p0 * (u64)need - onw;   // the rest of the earlier patches' pixels
+  for (int q = p0; q < p1; ++q) {
+    const u64 c = (u64)a.cand[a.cand[a.n_cand + q]];
+    a.goff[q] = onw;
+    a.goff[a.n_patches + q] = obr;
+    onw += c;
+    obr += (u64)need - c;
+  }
+  if (threadIdx.x == 0) {
+    a.bs->n_nw = tnw;
+    a.bs->n_br = (u64)n * (u64)need - tnw;
+  }
+}
+
+// One warp per kept row group: its pixels in raster order, each appended to
+// the non-white or the bright list (ballot + prefix counts) after the
+// patch's earlier groups (their counts summed by the warp), so both lists are
+// the stable split of the gathered sample.
+constexpr int kCompactWarps = 8;
+__global__ void __launch_bounds__(32 * kCompactWarps) k_patch_compact(PatchArgs a) {
+  const unsigned lane = threadIdx.x & 31u, lt = (1u << lane) - 1u;
+  const u64 idx = (u64)blockIdx.x * kCompactWarps + (threadIdx.x >> 5);
+  const int p = (int)(idx / (u64)a.ng), gi = (int)(idx % (u64)a.ng);
+  if (p >= a.bs->n_acc) return;
+  const int k = a.cand[a.n_cand + p];
+  u64 x0, y0;
+  patch_origin(a, k, &x0, &y0);
+  unsigned before = 0;   // non-white pixels of the patch's groups before this one
+  for (int g = (int)lane; g < gi; g += 32) before += (unsigned)a.gcnt[(size_t)k * a.ng + g];
+  before = __reduce_add_sync(0xFFFFFFFFu, before);
+  u64 onw = a.goff[p] + before;
+  u64 obr = a.goff[a.n_patches + p] + (u64)gi * kPatchGroupRows * (u64)a.P - before;
+  if (!SPCN_CHECK(x0 + (u64)a.P <= (u64)a.width && y0 + (u64)a.P <= (u64)a.height &&
+                  onw <= a.bs->n_nw && obr <= a.bs->n_br, a.err))
+    return;
+  const int y1 = min(a.P, (gi + 1) * kPatchGroupRows);
+  for (int y = gi * kPatchGroupRows; y < y1; ++y) {
+    const uint8_t* row = a.data + (int64_t)(y0 + (u64)y) * a.pitch + (int64_t)(x0 * 3);
+    for (int x0c = 0; x0c < a.P; x0c += 32) {
+      const int x = x0c + (int)lane;
+      uint32_t v = 0u;
+      bool in_nw = false, in_br = false;
+      if (x < a.P) {
+        v = (uint32_t)row[3 * x] | ((uint32_t)row[3 * x + 1] << 8) | ((uint32_t)row[3 * x + 2] << 16);
+        in_nw = packed_nonwhite(v, a.thr);
+        in_br = !in_nw;
+      }
+      const unsigned bn = __ballot_sync(0xFFFFFFFFu, in_nw), bb = __ballot_sync(0xFFFFFFFFu, in_br);
+      if (in_nw && SPCN_CHECK(onw + __popc(bn & lt) < a.bs->n_nw, a.err)) a.nw[onw + __popc(bn & lt)] = v;
+      if (in_br && SPCN_CHECK(obr + __popc(bb & lt) < a.bs->n_br, a.err)) a.br[obr + __popc(bb & lt)] = v;
+      onw += __popc(bn);
+      obr += __popc(bb);
+    }
   }
 }
 
@@ -844,6 +933,7 @@ int launch_estimate_basis(Context* c, const spcn_image* img, const spcn_params* 
   if (n_cand) { rc = ensure_candidate_capacity(c, n_cand + p->n_patches); if (rc) return rc; }
 
   BasisState* bs = c->bs;
+  bool per_patch = false;   // patch sampling compacted patch by patch (below)
   SPCN_CUDA_TRY(cudaMemsetAsync(bs, 0, sizeof(BasisState), st));
   const int big_grid = c->num_sms * 8;
   if (p->sample_mode != SPCN_SAMPLE_PATCHES) {
@@ -855,23 +945,44 @@ int launch_estimate_basis(Context* c, const spcn_image* img, const spcn_params* 
   } else {
     PatchArgs pa{img->data, img->pitch_bytes, W, H, p->seed, p->patch_size, p->n_patches,
                  n_cand, (unsigned)p->white_thresh, c->cand, bs, c->sample, (u64)c->sample_cap,
-                 c->err};
+                 c->err, 0, nullptr, nullptr, c->nw, c->br};
+    // Per-patch compaction: the kept patches' row groups go straight into
+    // the two lists, so the whole sample is never written.  Its buffer (n
+    // patches of P^2 entries) holds the patch offsets and the group counts
+    // instead (4 n + 4 n ceil(P/4) 32-bit words, which fit for P >= 3).
+    const int ng = (p->patch_size + kPatchGroupRows - 1) / kPatchGroupRows;
+    const u64 words = 4ull * (u64)p->n_patches * (1ull + (u64)ng);
+    per_patch = words <= cap;
+    if (per_patch) {
+      pa.ng = ng;
+      pa.goff = reinterpret_cast<u64*>(c->sample);
+      pa.gcnt = reinterpret_cast<int*>(c->sample + 4ull * (u64)p->n_patches);
+    }
     k_patch_count<<<n_cand, 256, 0, st>>>(pa);
     SPCN_LAUNCH_CHECK(c);
-    k_patch_accept<<<1, 32, 0, st>>>(pa);
+    k_patch_accept<<<1, kAcceptThreads, 0, st>>>(pa);
     SPCN_LAUNCH_CHECK(c);
-    k_patch_gather<<<p->n_patches * kGatherSplit, 256, 0, st>>>(pa);
+    if (per_patch) {
+      const u64 groups = (u64)p->n_patches * (u64)ng;
+      k_patch_compact<<<(unsigned)((groups + kCompactWarps - 1) / kCompactWarps), 32 * kCompactWarps,
+                        0, st>>>(pa);
+      SPCN_LAUNCH_CHECK(c);
+    } else {
+      k_patch_gather<<<p->n_patches * kGatherSplit, 256, 0, st>>>(pa);
+      SPCN_LAUNCH_CHECK(c);
+    }
+  }
+  if (!per_patch) {
+    const u64 nblk = (cap + kCompactBlock - 1) / kCompactBlock;
+    CompactArgs ca{c->sample, bs, (unsigned)p->white_thresh, c->blk, c->blk_off,
+                   (u64)c->blk_cap, c->nw, c->br};
+    k_classify_count<<<(unsigned)nblk, kCompactThreads, 0, st>>>(ca);
+    SPCN_LAUNCH_CHECK(c);
+    k_scan_blocks<<<1, 1024, 0, st>>>(ca);
+    SPCN_LAUNCH_CHECK(c);
+    k_compact<<<(unsigned)nblk, kCompactThreads, 0, st>>>(ca);
     SPCN_LAUNCH_CHECK(c);
   }
-  const u64 nblk = (cap + kCompactBlock - 1) / kCompactBlock;
-  CompactArgs ca{c->sample, bs, (unsigned)p->white_thresh, c->blk, c->blk_off, (u64)c->blk_cap,
-                 c->nw, c->br};
-  k_classify_count<<<(unsigned)nblk, kCompactThreads, 0, st>>>(ca);
-  SPCN_LAUNCH_CHECK(c);
-  k_scan_blocks<<<1, 1024, 0, st>>>(ca);
-  SPCN_LAUNCH_CHECK(c);
-  k_compact<<<(unsigned)nblk, kCompactThreads, 0, st>>>(ca);
-  SPCN_LAUNCH_CHECK(c);
   SPCN_CUDA_TRY(cudaMemsetAsync(bs->i0_hist, 0, sizeof(bs->i0_hist) + sizeof(bs->i0_ticket), st));
   I0Args ia{c->br, bs, c->model_b, bs->i0_hist, &bs->i0_ticket, p->i0_max_samples,
             (double)p->i0_pct, (p->flags & SPCN_FLAG_I0_255) ? 1 : 0, {}};
