@@ -118,6 +118,24 @@ __device__ __forceinline__ void patch_origin(const PatchArgs& a, int k, u64* x0,
 
 // Rows per group of the per-patch compaction: one warp compacts one group.
 constexpr int kPatchGroupRows = 4;
+constexpr int kRowBatch = 8;   // 32-pixel pieces of a row loaded at once by a compacting warp
+
+// Pieces j0 .. j0 + kRowBatch - 1 of a patch row (lane: pixel x = 32 j +
+// lane), packed R | G<<8 | B<<16, and whether each pixel exists (x < P).
+__device__ __forceinline__ void load_row_batch(const uint8_t* row, int P, int j0, unsigned lane,
+                                               uint32_t (&v)[kRowBatch], unsigned& have) {
+  have = 0u;
+#pragma unroll
+  for (int j = 0; j < kRowBatch; ++j) {
+    const int x = 32 * (j0 + j) + (int)lane;
+    v[j] = 0u;
+    if (x < P) {
+      v[j] = (uint32_t)row[3 * x] | ((uint32_t)row[3 * x + 1] << 8) |
+             ((uint32_t)row[3 * x + 2] << 16);
+      have |= 1u << j;
+    }
+  }
+}
 
 // One block per candidate patch: its non-white pixel count (row groups by
 // warps, columns by lanes, no per-pixel division), and with gcnt the count
@@ -226,20 +244,23 @@ __global__ void __launch_bounds__(32 * kCompactWarps) k_patch_compact(PatchArgs 
   const int y1 = min(a.P, (gi + 1) * kPatchGroupRows);
   for (int y = gi * kPatchGroupRows; y < y1; ++y) {
     const uint8_t* row = a.data + (int64_t)(y0 + (u64)y) * a.pitch + (int64_t)(x0 * 3);
-    for (int x0c = 0; x0c < a.P; x0c += 32) {
-      const int x = x0c + (int)lane;
-      uint32_t v = 0u;
-      bool in_nw = false, in_br = false;
-      if (x < a.P) {
-        v = (uint32_t)row[3 * x] | ((uint32_t)row[3 * x + 1] << 8) | ((uint32_t)row[3 * x + 2] << 16);
-        in_nw = packed_nonwhite(v, a.thr);
-        in_br = !in_nw;
+    for (int j0 = 0; 32 * j0 < a.P; j0 += kRowBatch) {
+      uint32_t v[kRowBatch];
+      unsigned have;
+      load_row_batch(row, a.P, j0, lane, v, have);
+#pragma unroll
+      for (int j = 0; j < kRowBatch; ++j) {
+        const bool in_nw = ((have >> j) & 1u) && packed_nonwhite(v[j], a.thr);
+        const bool in_br = ((have >> j) & 1u) && !in_nw;
+        const unsigned bn = __ballot_sync(0xFFFFFFFFu, in_nw);
+        const unsigned bb = __ballot_sync(0xFFFFFFFFu, in_br);
+        if (in_nw && SPCN_CHECK(onw + __popc(bn & lt) < a.bs->n_nw, a.err))
+          a.nw[onw + __popc(bn & lt)] = v[j];
+        if (in_br && SPCN_CHECK(obr + __popc(bb & lt) < a.bs->n_br, a.err))
+          a.br[obr + __popc(bb & lt)] = v[j];
+        onw += __popc(bn);
+        obr += __popc(bb);
       }
-      const unsigned bn = __ballot_sync(0xFFFFFFFFu, in_nw), bb = __ballot_sync(0xFFFFFFFFu, in_br);
-      if (in_nw && SPCN_CHECK(onw + __popc(bn & lt) < a.bs->n_nw, a.err)) a.nw[onw + __popc(bn & lt)] = v;
-      if (in_br && SPCN_CHECK(obr + __popc(bb & lt) < a.bs->n_br, a.err)) a.br[obr + __popc(bb & lt)] = v;
-      onw += __popc(bn);
-      obr += __popc(bb);
     }
   }
 }
