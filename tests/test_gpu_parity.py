@@ -227,6 +227,24 @@ def test_estimate_basis_patches(spcn, ctx):
     assert np.max(np.abs(np.array(g.basis) - o.W)) <= 1e-5
 
 
+@pytest.mark.parametrize("patch_size", [1, 2, 3, 37, 50])
+def test_estimate_basis_patches_odd_sizes_and_sample_order(spcn, ctx, patch_size):
+    """Patch sampling at sizes whose last group of four rows is partial or that
+    are too small for the per-patch split (1, 2: the general compaction).
+    i0 from every k-th bright pixel (a small cap, over a tinted background
+    whose bright pixels differ) depends on the order of the bright list,
+    which must be the sample order: patches in acceptance order, each in
+    raster order."""
+    img = synth.make_image(300, 260, 1011, blobs=True, white=(232.0, 240.0, 247.0))
+    kw = dict(sample_mode="patches", n_patches=30, patch_size=patch_size, seed=8,
+              i0_max_samples=40)
+    o = O.estimate_basis(img, O.Params(**kw))
+    g = ctx.estimate_basis(to_dev(img), spcn.params(**kw))
+    assert g.n_sample == o.n_sample and g.n_nonwhite == o.n_nonwhite and g.n_bright == o.n_bright
+    assert np.array_equal(np.array(g.i0[:], np.float32), np.float32(o.i0))
+    assert np.max(np.abs(np.array(g.basis) - o.W)) <= 1e-5
+
+
 def test_estimate_basis_i0_cap_and_tinted_background(spcn, ctx):
     img = synth.make_image(700, 700, 1007, white=(224.0, 236.0, 250.0))
     p = O.Params(sample_mode="all", i0_max_samples=5000)
