@@ -274,6 +274,11 @@ def test_errors_are_reported(spcn, ctx):
     with pytest.raises(spcn.SpcnError) as e:
         ctx.estimate_basis(white, spcn.params(sample_mode="all"))
     assert e.value.kind == "NO_TISSUE"
+    for size in (16, 2):   # per-patch split and general compaction: no patch kept
+        with pytest.raises(spcn.SpcnError) as e:
+            ctx.estimate_basis(white, spcn.params(sample_mode="patches", n_patches=5,
+                                                  patch_size=size, seed=1))
+        assert e.value.kind == "NO_TISSUE"
     st = spcn.Stats.from_values(synth.stain_basis(1), [255, 255, 255], [1.0, 1.0])
     with pytest.raises(spcn.SpcnError) as e:
         ctx.normalize(white, st, st, return_p99=True)
