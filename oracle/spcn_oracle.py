@@ -69,11 +69,19 @@ Normalising with the P99 that ``estimate_basis`` reports (§3.1 item 2's
 sub-sampled percentile) instead of the exact one is ``normalize`` called with
 those statistics.
 
-Parity pins (tests/test_oracle.py): OD(i0) = 0; KKT conditions of every lasso
-solution; brute-force enumeration on a grid; soft-threshold closed form for
-orthogonal W; lambda = 0 against scipy's NNLS; identity reconstruction;
-planted-basis recovery; objective monotonicity; percentile against
-``np.percentile``; the swap and tinted-background regressions of §4.1.
+Parity pins (tests/test_oracle.py): OD(i0) = 0 and hand-computed OD values;
+KKT conditions of every lasso solution; hand-solved lasso cases;
+brute-force enumeration of the active sets and a grid search on tiny inputs;
+soft-threshold closed form for orthogonal W; lambda = 0 against scipy's NNLS;
+identity reconstruction; planted-basis recovery and permutation invariance;
+objective monotonicity; percentile against ``np.percentile``; published
+SplitMix64 output vectors and exact multiply-high against Python integers;
+round-half-even of exact .5 values in ``to_uint8``; the analytic gradient
+against central differences; each variant option (i0 = 255, blue-only
+ordering, patch median, pseudo-inverse, i0_out_255) against its special
+case; the swap and tinted-background regressions of §4.1.  End-to-end
+quality on real stained slides is not pinned: the paper prints no worked
+example and its images are not available.
 """
 from __future__ import annotations
 
