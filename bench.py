@@ -660,6 +660,8 @@ def run_batch(args, world, rank, local, leg=False):
                "fused_launch_ms": min((t["ms"] for t in trials
                                        if t["schedule"] in ("phased", "interleaved")),
                                       default=None),
+               "persistent_launch_ms": min((t["ms"] for t in trials
+                                            if t["schedule"] == "persistent"), default=None),
                "tune_s": round(tune_s, 2),
                "timing": f"CUDA-graph replays of one batch run ({per_run} launches) vs "
                          f"{len(tiles)} sequential spcn_normalize calls, CUDA events",

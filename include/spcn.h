@@ -318,7 +318,7 @@ typedef enum {
   SPCN_SCHED_INTERLEAVED = 1,  /* groups of about group_px pixels: pass 1 of group g+1
                                   is queued before pass 2 of group g, so pass 2
                                   rereads recently read tiles */
-  SPCN_SCHED_STAGED = 2        /* separate launches, each with the whole shared memory
+  SPCN_SCHED_STAGED = 2,       /* separate launches, each with the whole shared memory
                                   and register budget of its pass: pass 1 of every
                                   tile (with the single-image chunk skips and
                                   per-warp stack), the per-tile selects, pass 2 of
@@ -328,6 +328,15 @@ typedef enum {
                                   into equal contiguous shares, one per block, so
                                   item_chunks has no effect.  Needs fewer than
                                   2^32 chunks per tile (else INVALID_ARG) */
+  SPCN_SCHED_PERSISTENT = 3    /* the staged schedule's steps (window starts, pass 1,
+                                  the per-tile selects, pass 2) as phases of ONE
+                                  cooperative persistent launch, one block per SM,
+                                  separated by grid barriers; the cooperative
+                                  fallback launch follows as in the staged
+                                  schedule.  Needs the grid-wide select (at most
+                                  1024 tiles) and the same block count for both
+                                  passes (else INVALID_ARG); item_chunks has no
+                                  effect */
 } spcn_schedule;
 
 typedef struct {

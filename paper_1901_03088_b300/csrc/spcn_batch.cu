@@ -97,6 +97,7 @@ struct BatchRunState {
   unsigned next2;          // staged schedule: pass-2 items
   unsigned n_fallback;     // tiles left to the exact fallback (counted by the selects)
   unsigned barrier;        // grid barrier counter of the fallback phase
+  unsigned barrier2;       // grid barrier counter of the persistent launch's phases
   int abort;               // a wait gave up
   int err;                 // first error of the run
 };
@@ -448,8 +449,7 @@ constexpr int kPilotMinUnits = 64;
 constexpr int kPilotThreads = 512;
 constexpr int kPilotBits = 11;
 constexpr int kPilotBins = 1 << kPilotBits;
-static_assert((kPilotChunks + kPilotThreads - 1) / kPilotThreads * kChunk * kChunk < (1 << 30),
-              "a thread's pilot sums fit 32 bits");
+static_assert(kPilotChunks * kChunk * kChunk < (1 << 30), "a thread's pilot sums fit 32 bits");
 
 struct PilotArgs {
   BatchTile* tiles;
@@ -506,16 +506,32 @@ __device__ __forceinline__ void block_sum8(u64 (&v)[8], u64 (*s_part)[8]) {
   }
 }
 
-__global__ void __launch_bounds__(kPilotThreads, 2) k_batch_pilot(PilotArgs a) {
-  __shared__ unsigned s_hist[2][kPilotBins];
-  __shared__ float2 s_proj[kLutEntries];          // the tile's projected table
-  __shared__ u64 s_part[kPilotThreads / 32][8];
-  __shared__ u64 s_tmp[33];
-  __shared__ int s_idx;
-  __shared__ u64 s_before;
-  __shared__ unsigned s_b1[2];
-  __shared__ u64 s_r[2];
-  __shared__ int s_use;
+// The pilot's shared memory (a static array of k_batch_pilot, carved from the
+// dynamic shared memory of the persistent launch).
+struct PilotSmem {
+  unsigned hist[2][kPilotBins];
+  float2 proj[kLutEntries];      // the tile's projected table
+  u64 part[32][8];               // per-warp partial sums (up to 32 warps)
+  u64 tmp[33];
+  u64 before;
+  u64 r[2];
+  unsigned b1[2];
+  int idx;
+  int use;
+};
+
+// Window starts of the tiles blockIdx.x, blockIdx.x + gridDim.x, ... (any
+// block size up to 1024 threads).
+__device__ void pilot_tiles(const PilotArgs& a, PilotSmem& sm) {
+  unsigned (&s_hist)[2][kPilotBins] = sm.hist;
+  float2 (&s_proj)[kLutEntries] = sm.proj;
+  u64 (&s_part)[32][8] = sm.part;
+  u64 (&s_tmp)[33] = sm.tmp;
+  int& s_idx = sm.idx;
+  u64& s_before = sm.before;
+  unsigned (&s_b1)[2] = sm.b1;
+  u64 (&s_r)[2] = sm.r;
+  int& s_use = sm.use;
   for (unsigned t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
     BatchTile* T = a.tiles + t;
     const Geometry g = T->g;
@@ -666,6 +682,11 @@ __global__ void __launch_bounds__(kPilotThreads, 2) k_batch_pilot(PilotArgs a) {
     }
     __syncthreads();
   }
+}
+
+__global__ void __launch_bounds__(kPilotThreads, 2) k_batch_pilot(PilotArgs a) {
+  __shared__ PilotSmem sm;
+  pilot_tiles(a, sm);
 }
 
 // Pass 1 on one chunk with open-ended windows.  Per pixel: the non-white flag
@@ -1193,8 +1214,7 @@ __device__ __forceinline__ void staged_counts(SelectState* sel, f2& c_nw, f2& c_
 // Pass 1 of every tile (staged schedule).  One block per SM; items from the
 // run's first ticket.
 template <class G>
-__global__ void __launch_bounds__(kBatchThreads, 1) k_batch_p1(BatchArgs a) {
-  extern __shared__ __align__(16) char s_dyn[];
+__device__ __forceinline__ void p1_phase(const BatchArgs& a, char* s_dyn) {
   char* lut = s_dyn;
   const unsigned warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
   const unsigned lt = (1u << lane) - 1u;
@@ -1378,6 +1398,12 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_p1(BatchArgs a) {
   }
 }
 
+template <class G>
+__global__ void __launch_bounds__(kBatchThreads, 1) k_batch_p1(BatchArgs a) {
+  extern __shared__ __align__(16) char s_dyn[];
+  p1_phase<G>(a, s_dyn);
+}
+
 // The percentiles of every tile from its key lists (staged schedule).
 __global__ void __launch_bounds__(kBatchThreads) k_batch_sel(BatchArgs a) {
   extern __shared__ __align__(16) char s_dyn[];
@@ -1422,13 +1448,26 @@ __device__ __forceinline__ void finish_no_tissue(const BatchArgs& a, unsigned ti
   st_release_s32(&S->ready, 1);
 }
 
-__global__ void __launch_bounds__(kSelThreads) k_sel_first(BatchArgs a) {
-  __shared__ unsigned s_hist[kSelBins];
-  __shared__ u64 s_tmp[33];
-  __shared__ int s_idx;
-  __shared__ u64 s_before;
-  __shared__ int s_bin[kTracks];
-  __shared__ u64 s_rr[kTracks];
+// Shared memory of the per-tile select steps (static arrays of k_sel_first
+// and k_sel_final, carved from the dynamic shared memory of the persistent
+// launch).
+struct SelSmem {
+  unsigned hist[kSelBins];
+  u64 tmp[33];
+  u64 before;
+  u64 rr[kTracks];
+  int bin[kTracks];
+  int res[kTracks];
+  int idx;
+};
+
+__device__ void sel_first_tiles(const BatchArgs& a, SelSmem& sm) {
+  unsigned (&s_hist)[kSelBins] = sm.hist;
+  u64 (&s_tmp)[33] = sm.tmp;
+  int& s_idx = sm.idx;
+  u64& s_before = sm.before;
+  int (&s_bin)[kTracks] = sm.bin;
+  u64 (&s_rr)[kTracks] = sm.rr;
   for (unsigned tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
     const BatchTile* T = a.tiles + tile;
     BatchTileState* S = a.state + tile;
@@ -1494,6 +1533,11 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_first(BatchArgs a) {
   }
 }
 
+__global__ void __launch_bounds__(kSelThreads) k_sel_first(BatchArgs a) {
+  __shared__ SelSmem sm;
+  sel_first_tiles(a, sm);
+}
+
 // Pair metadata of k_sel_count, one per (tile, stain).
 struct SelPair {
   unsigned lo;
@@ -1508,12 +1552,10 @@ __device__ __forceinline__ unsigned sel_segments(unsigned n) {
 // Every list in segments of kSelSeg keys, numbered over all pairs (a block
 // scan gives each pair's first segment); block b takes segments b, b + G, ...
 // and finds a segment's pair by binary search.
-__global__ void __launch_bounds__(kSelThreads) k_sel_count(BatchArgs a) {
-  extern __shared__ __align__(16) char s_dyn[];
+__device__ void sel_count_segments(const BatchArgs& a, char* s_dyn, u64* s_tmp) {
   const unsigned np = 2 * a.n_tiles;
   SelPair* s_pair = reinterpret_cast<SelPair*>(s_dyn);
   unsigned* s_seg = reinterpret_cast<unsigned*>(s_pair + np);   // np + 1 entries
-  __shared__ u64 s_tmp[33];
   const unsigned per = (np + blockDim.x - 1) / blockDim.x;
   const unsigned p0 = min(np, threadIdx.x * per), p1 = min(np, p0 + per);
   unsigned local = 0;
@@ -1580,12 +1622,18 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_count(BatchArgs a) {
   }
 }
 
-__global__ void __launch_bounds__(kSelThreads) k_sel_final(BatchArgs a) {
-  __shared__ unsigned s_hist[kSelBins];
+__global__ void __launch_bounds__(kSelThreads) k_sel_count(BatchArgs a) {
+  extern __shared__ __align__(16) char s_dyn[];
   __shared__ u64 s_tmp[33];
-  __shared__ int s_idx;
-  __shared__ u64 s_before;
-  __shared__ int s_res[kTracks];
+  sel_count_segments(a, s_dyn, s_tmp);
+}
+
+__device__ void sel_final_tiles(const BatchArgs& a, SelSmem& sm) {
+  unsigned (&s_hist)[kSelBins] = sm.hist;
+  u64 (&s_tmp)[33] = sm.tmp;
+  int& s_idx = sm.idx;
+  u64& s_before = sm.before;
+  int (&s_res)[kTracks] = sm.res;
   for (unsigned tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
     const BatchTile* T = a.tiles + tile;
     BatchTileState* S = a.state + tile;
@@ -1624,6 +1672,11 @@ __global__ void __launch_bounds__(kSelThreads) k_sel_final(BatchArgs a) {
   }
 }
 
+__global__ void __launch_bounds__(kSelThreads) k_sel_final(BatchArgs a) {
+  __shared__ SelSmem sm;
+  sel_final_tiles(a, sm);
+}
+
 // Pass 2 of every tile whose percentile the lists gave (staged schedule).
 // The work per chunk is the same everywhere, so the chunks of all tiles (the
 // tiles in table order) are split into equal contiguous shares, one per
@@ -1640,8 +1693,7 @@ constexpr int kP2PreloadTiles = 2048;
 constexpr size_t kP2Smem = kLutSmemBytes + sizeof(P2Tile) * kP2PreloadTiles;
 
 template <class G>
-__global__ void __launch_bounds__(kBatchThreads, 1) k_batch_p2(BatchArgs a) {
-  extern __shared__ __align__(16) char s_dyn[];
+__device__ __forceinline__ void p2_phase(const BatchArgs& a, char* s_dyn) {
   char* lut = s_dyn;
   P2Tile* s_tiles = reinterpret_cast<P2Tile*>(s_dyn + kLutSmemBytes);
   __shared__ __align__(16) BatchItem s_items[2];   // current segment and the prefetched next one
@@ -1696,6 +1748,43 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_batch_p2(BatchArgs a) {
   }
 }
 
+template <class G>
+__global__ void __launch_bounds__(kBatchThreads, 1) k_batch_p2(BatchArgs a) {
+  extern __shared__ __align__(16) char s_dyn[];
+  p2_phase<G>(a, s_dyn);
+}
+
+// ------------------------------------------------------------ persistent schedule
+// SPCN_SCHED_PERSISTENT: the staged schedule's steps as phases of ONE
+// cooperative persistent launch (one block per SM), separated by grid
+// barriers instead of kernel boundaries: window starts, pass 1, the three
+// select steps, pass 2.  Each phase reuses the block's dynamic shared memory
+// (the pass-1 layout is the largest).  Data written in one phase is read in
+// the next after the barrier's acquire.  The exact fallback of tiles whose
+// ranks missed their window stays a separate cooperative launch that returns
+// at once when no tile needs it.
+template <class G>
+__global__ void __launch_bounds__(kBatchThreads, 1) k_batch_persist(BatchArgs a, PilotArgs pa) {
+  extern __shared__ __align__(16) char s_dyn[];
+  __shared__ u64 s_tmp[33];
+  unsigned target = 0;
+  auto sync_grid = [&]() -> bool {
+    target += gridDim.x;
+    return grid_barrier(&a.run->barrier2, target, &a.run->abort, &a.run->err, a.timeout_ns);
+  };
+  pilot_tiles(pa, *reinterpret_cast<PilotSmem*>(s_dyn));
+  if (!sync_grid()) return;
+  p1_phase<G>(a, s_dyn);
+  if (!sync_grid()) return;
+  sel_first_tiles(a, *reinterpret_cast<SelSmem*>(s_dyn));
+  if (!sync_grid()) return;
+  sel_count_segments(a, s_dyn, s_tmp);
+  if (!sync_grid()) return;
+  sel_final_tiles(a, *reinterpret_cast<SelSmem*>(s_dyn));
+  if (!sync_grid()) return;
+  p2_phase<G>(a, s_dyn);
+}
+
 // ------------------------------------------------------------ host side
 struct Batch {
   Context* c = nullptr;
@@ -1719,6 +1808,7 @@ struct Batch {
   u64* rhist = nullptr;
   int grid = 0;
   int grid_p1 = 0, grid_p2 = 0, grid_sel = 0;   // staged schedule
+  bool persist_ok = false;       // the persistent schedule can run (see configure_persist)
   u64 max_chunks = 0;            // chunks of the largest tile
   bool flat = false;             // every tile contiguous: launch the flat instantiation
   BatchArgs args{};
@@ -1756,11 +1846,33 @@ static int configure_staged_kernels(Context* c, int* grid_p1, int* grid_p2) {
   return SPCN_OK;
 }
 
+// The persistent launch holds the pass-1 layout (the largest of its phases'
+// shared memory) with one block per SM; its pass 1 and pass 2 take the
+// static shares built for grid_p1 and grid_p2 blocks, so both must equal its
+// grid, and its select is the grid-wide one (batches with hist2).
+template <class G>
+static int configure_persist(Context* c, Batch* b) {
+  b->persist_ok = false;
+  SPCN_CUDA_TRY(cudaFuncSetAttribute(k_batch_persist<G>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStagedSmem));
+  int occ = 0;
+  SPCN_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_persist<G>,
+                                                              kBatchThreads, kStagedSmem));
+  const size_t sel_count_smem = (sizeof(SelPair) + sizeof(unsigned)) * 2 * (size_t)b->n + 4;
+  const size_t p2_smem =
+      kLutSmemBytes + (b->n <= kP2PreloadTiles ? sizeof(P2Tile) * (size_t)b->n : 0);
+  b->persist_ok = occ >= 1 && b->grid_p1 == c->num_sms && b->grid_p2 == c->num_sms &&
+                  b->hist2 != nullptr && sel_count_smem <= kStagedSmem && p2_smem <= kStagedSmem &&
+                  sizeof(PilotSmem) <= kStagedSmem && sizeof(SelSmem) <= kStagedSmem &&
+                  b->max_chunks < (1ull << 32);
+  return SPCN_OK;
+}
+
 static bool config_ok(const spcn_batch_config* cfg) {
   if (!cfg) return false;
   if (cfg->item_chunks < kPassThreads || cfg->item_chunks % kPassThreads != 0) return false;
   if (cfg->schedule != SPCN_SCHED_PHASED && cfg->schedule != SPCN_SCHED_INTERLEAVED &&
-      cfg->schedule != SPCN_SCHED_STAGED)
+      cfg->schedule != SPCN_SCHED_STAGED && cfg->schedule != SPCN_SCHED_PERSISTENT)
     return false;
   if (cfg->schedule == SPCN_SCHED_INTERLEAVED && cfg->group_px < 1) return false;
   return true;
@@ -1792,7 +1904,7 @@ static void build_items(const Batch* b, const spcn_batch_config& cfg, std::vecto
   out->clear();
   n_items1->assign(b->n, 0u);
   // the staged passes take static shares (build_shares), not queue items
-  if (cfg.schedule == SPCN_SCHED_STAGED) return;
+  if (cfg.schedule == SPCN_SCHED_STAGED || cfg.schedule == SPCN_SCHED_PERSISTENT) return;
   // largest tiles first: their list selects end early, and the small tiles
   // even out the end of each pass
   std::vector<int> order(b->n);
@@ -1838,6 +1950,7 @@ static void build_items(const Batch* b, const spcn_batch_config& cfg, std::vecto
 static int apply_config(Batch* b, const spcn_batch_config& cfg) {
   // the staged pass 1 queues 32-bit chunk indices of a tile
   if (cfg.schedule == SPCN_SCHED_STAGED && b->max_chunks >= (1ull << 32)) return SPCN_ERR_INVALID_ARG;
+  if (cfg.schedule == SPCN_SCHED_PERSISTENT && !b->persist_ok) return SPCN_ERR_INVALID_ARG;
   std::vector<BatchItem> items;
   std::vector<unsigned> n1;
   build_items(b, cfg, &items, &n1);
@@ -1876,13 +1989,14 @@ static void batch_free(Batch* b) {
 static int batch_launch(Batch* b, cudaStream_t st) {
   Context* c = b->c;
   SPCN_CUDA_TRY(cudaMemsetAsync(b->d_state, 0, b->state_bytes, st));
-  {
-    PilotArgs pa;
-    pa.tiles = b->d_tiles;
-    pa.models = b->models;
-    pa.n_tiles = (unsigned)b->n;
-    pa.thr = b->args.thr;
-    pa.pct = b->args.pct;
+  const bool persist = b->cfg.schedule == SPCN_SCHED_PERSISTENT;
+  PilotArgs pa;
+  pa.tiles = b->d_tiles;
+  pa.models = b->models;
+  pa.n_tiles = (unsigned)b->n;
+  pa.thr = b->args.thr;
+  pa.pct = b->args.pct;
+  if (!persist) {   // the persistent launch sets the window starts itself
     const int pg = std::min(b->n, 4 * c->num_sms);
     k_batch_pilot<<<pg, kPilotThreads, 0, st>>>(pa);
     SPCN_LAUNCH_CHECK(c);
@@ -1890,10 +2004,10 @@ static int batch_launch(Batch* b, cudaStream_t st) {
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   SPCN_CUDA_TRY(cudaStreamIsCapturing(st, &cap));
   const bool staged = b->cfg.schedule == SPCN_SCHED_STAGED;
-  // staged: the fused kernel runs with an empty queue (only the exact
-  // fallback of tiles whose ranks missed their window)
+  // staged and persistent: the fused kernel runs with an empty queue (only
+  // the exact fallback of tiles whose ranks missed their window)
   BatchArgs fa = b->args;
-  if (staged) fa.n_items = 0;
+  if (staged || persist) fa.n_items = 0;
   cudaLaunchConfig_t lc = {};
   lc.gridDim = dim3((unsigned)b->grid);
   lc.blockDim = dim3(kBatchThreads);
@@ -1907,6 +2021,16 @@ static int batch_launch(Batch* b, cudaStream_t st) {
   int launched = 0;
   // contiguous tiles only: the flat traversal (fewer registers per loop)
   auto launch = [&]() -> cudaError_t {
+    if (persist) {
+      cudaLaunchConfig_t pc = lc;
+      pc.gridDim = dim3((unsigned)c->num_sms);
+      pc.dynamicSmemBytes = kStagedSmem;
+      const cudaError_t e0 =
+          b->flat ? cudaLaunchKernelEx(&pc, k_batch_persist<FlatGeometry>, b->args, pa)
+                  : cudaLaunchKernelEx(&pc, k_batch_persist<Geometry>, b->args, pa);
+      if (e0 != cudaSuccess) return e0;
+      ++launched;
+    }
     if (staged) {
       if (b->flat)
         k_batch_p1<FlatGeometry><<<b->grid_p1, kBatchThreads, kStagedSmem, st>>>(b->args);
@@ -2076,6 +2200,8 @@ static int batch_create(Context* c, int n, const spcn_image* tiles, const spcn_s
   b->grid_sel = std::min(n, 4 * c->num_sms);
   rc = build_shares(b, b->grid_p1, 1u, &b->p1_items, &b->p1_first);
   if (rc == SPCN_OK) rc = build_shares(b, b->grid_p2, 2u, &b->p2_items, &b->p2_first);
+  if (rc == SPCN_OK)
+    rc = b->flat ? configure_persist<FlatGeometry>(c, b) : configure_persist<Geometry>(c, b);
   if (rc) return fail(rc);
   BatchArgs& a = b->args;
   a.tiles = b->d_tiles;
@@ -2233,6 +2359,12 @@ int spcn_batch_tune(void* batch, int32_t reps, spcn_batch_config* trials, int32_
     c2.item_chunks = 32 * kPassThreads;
     c2.schedule = SPCN_SCHED_STAGED;
     cand.push_back(c2);
+  }
+  if (b->persist_ok) {
+    spcn_batch_config c3{};
+    c3.item_chunks = 32 * kPassThreads;
+    c3.schedule = SPCN_SCHED_PERSISTENT;
+    cand.push_back(c3);
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   SPCN_CUDA_TRY(cudaEventCreate(&e0));

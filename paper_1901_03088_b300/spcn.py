@@ -94,7 +94,7 @@ class BatchConfig(ctypes.Structure):
                 "group_px": int(self.group_px), "ms": float(self.ms)}
 
 
-SCHEDULES = {"phased": 0, "interleaved": 1, "staged": 2}
+SCHEDULES = {"phased": 0, "interleaved": 1, "staged": 2, "persistent": 3}
 SCHEDULES_INV = {v: k for k, v in SCHEDULES.items()}
 
 

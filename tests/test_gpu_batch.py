@@ -65,8 +65,9 @@ def sequential(ctx, tiles, stats, tgt, p):
     return outs, p99
 
 
-# the fused persistent launch and the staged launches, at the default item size
-SCHEDS = ["phased", "staged"]
+# the fused persistent launch, the staged launches and the staged steps as
+# phases of one persistent launch, at the default item size
+SCHEDS = ["phased", "staged", "persistent"]
 
 
 def run_batch(spcn, ctx, tiles, stats, tgt, outs, p, sched):
@@ -148,7 +149,8 @@ def test_batch_window_hints(spcn, ctx, setup, hint, sched):
 
 @pytest.mark.parametrize("item_chunks,schedule,group_px", [
     (1024, "phased", 0), (8192, "phased", 0), (1024, "interleaved", 200_000),
-    (2048, "interleaved", 1), (1024, "staged", 0), (8192, "staged", 0)])
+    (2048, "interleaved", 1), (1024, "staged", 0), (8192, "staged", 0),
+    (1024, "persistent", 0)])
 def test_batch_schedules_and_graph_replay(spcn, ctx, setup, item_chunks, schedule, group_px):
     tiles, stats, tgt, p = setup
     ref_outs, ref_p99 = sequential(ctx, tiles, stats, tgt, p)
