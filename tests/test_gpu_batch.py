@@ -261,6 +261,12 @@ def test_batch_many_tiles(spcn, ctx, setup):
     p99, status, _ = run_batch(spcn, ctx, tiles, stats, tgt, outs, p, "staged")
     assert status == [0] * len(tiles)
     assert_same(outs, ref_outs, p99, ref_p99)
+    # the persistent schedule needs the grid-wide select (at most 1024 tiles)
+    b = spcn.Batch(ctx, tiles, stats, tgt, outs, p)
+    with pytest.raises(spcn.SpcnError) as e:
+        b.set_config(16 * 1024, "persistent")
+    assert e.value.kind == "INVALID_ARG"
+    b.close()
 
 
 def test_batch_rejects_overlapping_output(spcn, ctx, setup):
